@@ -1,0 +1,245 @@
+/* r2g.h -- C ABI of the B300 (sm_103a) R^2-Gaussian X-ray rasterizer and voxelizer.
+ *
+ * The method (arXiv 2405.20693): a scanned object is a sum of radiative 3D
+ * Gaussians G_i(x) = rho_i exp(-1/2 (x-p_i)^T Sigma_i^{-1} (x-p_i)), Sigma_i =
+ * R_i S_i S_i^T R_i^T (Eq. 3, Sec. 4.1), density sigma(x) = sum_i G_i(x) (Eq. 4).
+ * A log-projection pixel is the line integral of sigma (Eq. 1), which splits into
+ * per-Gaussian integrals (Eq. 5).  Each Gaussian is carried into ray space by the
+ * scanner transform W, t and the local-affine Jacobian J of the cone-beam map
+ * (Eq. 6, App. A) and integrated in closed form into a 2D Gaussian of amplitude
+ * rho_hat = mu rho, mu = sqrt(2 pi |Sigma~| / |Sigma^|) (Eq. 7); the image is
+ * the plain sum of those 2D Gaussians (no alpha compositing).  The voxelizer
+ * evaluates Eq. 4 on voxel grids through 8^3 bricks (Sec. 4.2.2).
+ *
+ * Conventions shared by every entry point
+ *  - Pointers named "device" are CUDA device memory owned by the caller.
+ *    Structs passed by pointer (camera, options, grids) are host memory, read
+ *    during the call only.  The library never allocates: scratch lives in a
+ *    caller-owned device workspace whose size the *_workspace_size functions give.
+ *  - Every call is asynchronous on `stream` (a cudaStream_t; NULL is the legacy
+ *    default stream) and never synchronises the host, except the functions
+ *    documented as synchronising (r2g_poll, r2g_*_lists, r2g_raster_pair_count).
+ *  - Gaussian parameters are float32 structure-of-arrays: mean[M][3],
+ *    scale[M][3] (> 0, already activated), quat[M][4] as (w, x, y, z) -- it is
+ *    normalised inside and gradients flow through the normalisation -- and
+ *    rho[M] (any sign).  1 <= M < 2^31.
+ *  - Gradients are ACCUMULATED (+=) into dmean, dscale, dquat, drho.
+ *  - Errors: argument errors are found on the host and returned at once
+ *    (R2G_E_INVAL, nothing launched); a failed launch returns R2G_E_CUDA.  Errors
+ *    found on the device (a list longer than the workspace's key capacity) are
+ *    written to a status word in the workspace and read by r2g_poll.
+ *    r2g_last_error() gives a thread-local message for the last failure.
+ */
+#ifndef R2G_H
+#define R2G_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* r2g_stream; /* identical to cudaStream_t */
+
+typedef enum {
+    R2G_OK = 0,
+    R2G_E_INVAL = 1,    /* bad argument; nothing was launched */
+    R2G_E_CAPACITY = 2, /* more tile/brick list entries than the workspace holds */
+    R2G_E_CUDA = 3,     /* a CUDA call or launch failed */
+    R2G_E_TIMEOUT = 4,  /* reserved: a bounded device-side wait gave up */
+    R2G_E_NUMERIC = 5   /* reserved: non-finite values detected */
+} r2g_status;
+
+/* Detector and beam of one scan (App. A).  Pixel (r, c) has its centre at
+ *   xi  = (c + 1/2 - W/2) * pitch_u + off_u,  eta = (r + 1/2 - H/2) * pitch_v + off_v
+ * on the detector plane, in the same length unit as the Gaussians. */
+typedef struct {
+    int32_t beam;      /* 0 = parallel beam (the L_SO -> infinity limit, J = I); 1 = cone beam */
+    int32_t H, W;      /* detector rows and columns, 1..32768 */
+    float L_SD;        /* source-to-detector distance (cone) */
+    float pitch_u, pitch_v;
+    float off_u, off_v;
+    float near_plane;  /* cone: a Gaussian whose scanner depth u2 <= near_plane is dropped */
+} r2g_camera;
+
+/* Rasterizer options. */
+typedef struct {
+    float Q;             /* pixel gate: a Gaussian adds to a pixel when q = d^T Sigma^^{-1} d <= Q (9 = 3 sigma) */
+    int32_t tile_w;      /* tile shape: 16x16 (default), 8x8 or 32x8 */
+    int32_t tile_h;
+    int32_t count_pairs; /* 1: also count the gated pairs (bookkeeping runs only; slower) */
+} r2g_raster_opts;
+
+/* One voxel grid: the centre of voxel (x, y, z) is origin + (index + 1/2) * voxel;
+ * the volume is stored [Z][Y][X], x fastest. */
+typedef struct {
+    float origin[3];
+    float voxel[3];
+    int32_t dims[3];   /* X, Y, Z, each 1..4096 */
+} r2g_grid;
+
+/* ---------------------------------------------------------------- rasterizer
+ *
+ * Views: a DEVICE float table views[V][12] = W (3x3 row-major) then t (3), the
+ * world->scanner transform u = W p + t of App. A for each projection angle.
+ * Per (Gaussian, view) the library forms, in FP32, in this order (the stated
+ * sequence the per-tile lists are defined by; no fused multiply-add):
+ *   q <- q / |q|;  R(q);  M = R diag(s);  u = W p + t;
+ *   cone:  f = L_SD / u2, j02 = -(f u0)/u2, j12 = -(f u1)/u2, p^ = (f u0, f u1),
+ *          T = [[f W0 + j02 W2], [f W1 + j12 W2]]  (the first two rows of J W);
+ *   parallel: T = [W0; W1], p^ = (u0, u1);
+ *   N = T M;  Sigma^ = N N^T = [[alpha, beta], [beta, gamma]];
+ *   |Sigma^| = sum of the squared 2x2 minors of N (Cauchy-Binet);
+ *   drop if (cone) u2 <= near_plane or |Sigma^| <= 0;
+ *   e_x = sqrt(Q alpha), e_y = sqrt(Q gamma);
+ *   cx = (p^x - off_u)/pitch_u + (W/2 - 1/2),  rx = e_x / pitch_u  (rows alike);
+ *   pixel columns ceil(cx - rx) .. floor(cx + rx) clamped to the detector
+ *   (empty -> dropped); tiles = those columns / tile_w (rows / tile_h).
+ * Every pixel of every listed tile then evaluates the gate q <= Q exactly, so the
+ * image does not depend on the tile shape.  Per-tile lists hold Gaussian ids in
+ * ascending order (stable radix sort), so the forward image is deterministic.
+ * The amplitude uses mu = sqrt(2 pi / (omega^T Sigma^{-1} omega)), omega the unit
+ * direction from the source to the mean (cone) or the beam direction (parallel),
+ * which equals Eq. 7's determinant ratio. */
+
+/* Bytes of workspace for M Gaussians x V views with room for key_capacity
+ * (tile, Gaussian) list entries.  1 <= key_capacity <= 2^32 - 1.  Returns 0 for
+ * invalid arguments. */
+size_t r2g_raster_workspace_size(int64_t M, int32_t V, const r2g_camera* cam, const r2g_raster_opts* opts,
+                                 int64_t key_capacity);
+
+/* Eq. 5 + Eq. 7: image[V][H][W] (device, float32, overwritten) =
+ * sum over Gaussians of rho_hat exp(-q/2) [q <= Q] at each pixel centre.
+ * The workspace keeps the per-view records and tile lists for the matching
+ * r2g_rasterize_backward call.  Sets R2G_E_CAPACITY in the workspace status (see
+ * r2g_poll) when the lists need more than the workspace's key capacity; the image
+ * is then incomplete. */
+r2g_status r2g_rasterize(int64_t M, const float* mean, const float* scale, const float* quat, const float* rho,
+                         int32_t V, const float* views, const r2g_camera* cam, const r2g_raster_opts* opts,
+                         float* image, void* ws, size_t ws_bytes, r2g_stream stream);
+
+/* Gradient of sum(dimage * image) with respect to the parameters, accumulated into
+ * dmean[M][3], dscale[M][3], dquat[M][4], drho[M] (device).  Must follow the
+ * r2g_rasterize call that filled `ws` with the same parameters, views and options,
+ * with no other use of `ws` in between.  Gradient accumulation uses float atomics,
+ * so the last bits may vary from run to run. */
+r2g_status r2g_rasterize_backward(int64_t M, const float* mean, const float* scale, const float* quat,
+                                  const float* rho, int32_t V, const float* views, const r2g_camera* cam,
+                                  const r2g_raster_opts* opts, const float* dimage, float* dmean, float* dscale,
+                                  float* dquat, float* drho, void* ws, size_t ws_bytes, r2g_stream stream);
+
+/* The projection step alone (Eq. 6, Eq. 7; the stated FP32 sequence above), for
+ * inspection and tests: proj[V][M][8] (device) = p^x, p^y (detector units),
+ * alpha, beta, gamma (Sigma^), |Sigma^|, rho_hat, valid (1.0 / 0.0);
+ * rect[V][M][4] (device int32) = pixel columns c_lo, c_hi and rows r_lo, r_hi
+ * of the bound (zeros when dropped).  No workspace. */
+r2g_status r2g_project(int64_t M, const float* mean, const float* scale, const float* quat, const float* rho,
+                       int32_t V, const float* views, const r2g_camera* cam, const r2g_raster_opts* opts,
+                       float* proj, int32_t* rect, r2g_stream stream);
+
+/* The per-tile lists of the last r2g_rasterize on `ws`.  Synchronises `stream`.
+ * ranges[n_tiles][2] (device uint32, [start, end) into ids) with n_tiles =
+ * V * ceil(H/tile_h) * ceil(W/tile_w), tiles numbered (v, ty, tx) row-major;
+ * ids[capacity] (device uint32) = Gaussian id of each entry.  *n_entries (host)
+ * receives the entry count; R2G_E_CAPACITY if it exceeds `capacity` (nothing
+ * copied). */
+r2g_status r2g_raster_lists(int64_t M, int32_t V, const r2g_camera* cam, const r2g_raster_opts* opts,
+                            const void* ws, size_t ws_bytes, uint32_t* ranges, uint32_t* ids, int64_t capacity,
+                            int64_t* n_entries, r2g_stream stream);
+
+/* Count of (pixel, Gaussian) pairs that passed the gate in the last
+ * r2g_rasterize on `ws` -- only when that call had opts->count_pairs = 1 (a
+ * counting run; off in timed runs).  Synchronises `stream`. */
+r2g_status r2g_raster_pair_count(const void* ws, size_t ws_bytes, int64_t* pairs, r2g_stream stream);
+
+/* ---------------------------------------------------------------- voxelizer
+ *
+ * Bricks of 8^3 voxels per grid; a Gaussian is listed in every brick meeting the
+ * voxel-centre box |x_k - p_k| <= sqrt(Q3 Sigma_kk), formed in FP32 as
+ *   Sigma_kk = (M_k0^2 + M_k1^2) + M_k2^2 (M = R diag(s) as above),
+ *   c_k = (p_k - origin_k)/voxel_k - 1/2, r_k = sqrt(Q3 Sigma_kk)/voxel_k,
+ *   voxels ceil(c_k - r_k) .. floor(c_k + r_k) clamped, bricks = voxels / 8.
+ * Each voxel then applies the gate q <= Q3 exactly.  Q3 = 11.345 is the 0.99
+ * quantile of chi^2_3 (the paper's "99% confidence"). */
+
+size_t r2g_voxel_workspace_size(int64_t M, int32_t G, const r2g_grid* grids, int64_t key_capacity);
+
+/* Eq. 4: vol (device float32, overwritten) = the G grids' volumes concatenated in
+ * order, each [Z][Y][X]; V[x] = sum_i rho_i exp(-1/2 (x-p_i)^T Sigma_i^{-1} (x-p_i)) [q <= Q3].
+ * 1 <= G <= 64.  The workspace keeps the brick lists for r2g_voxelize_backward. */
+r2g_status r2g_voxelize(int64_t M, const float* mean, const float* scale, const float* quat, const float* rho,
+                        int32_t G, const r2g_grid* grids, float Q3, float* vol, void* ws, size_t ws_bytes,
+                        r2g_stream stream);
+
+/* Gradient of sum(dvol * vol), accumulated (+=).  Must follow the matching
+ * r2g_voxelize on `ws` (same parameters and grids). */
+r2g_status r2g_voxelize_backward(int64_t M, const float* mean, const float* scale, const float* quat,
+                                 const float* rho, int32_t G, const r2g_grid* grids, float Q3, const float* dvol,
+                                 float* dmean, float* dscale, float* dquat, float* drho, void* ws,
+                                 size_t ws_bytes, r2g_stream stream);
+
+/* Per-brick lists of the last r2g_voxelize on `ws` (synchronises `stream`):
+ * ranges[n_bricks][2], bricks numbered per grid in order, (bz, by, bx) row-major
+ * within a grid; ids[capacity] Gaussian ids; *n_entries the count. */
+r2g_status r2g_voxel_lists(int64_t M, int32_t G, const r2g_grid* grids, const void* ws, size_t ws_bytes,
+                           uint32_t* ranges, uint32_t* ids, int64_t capacity, int64_t* n_entries,
+                           r2g_stream stream);
+
+/* ---------------------------------------------------------------- losses (Eq. 8)
+ *
+ * Projection loss L1 + lambda_ssim (1 - SSIM) over a batch render/meas[V][H][W]
+ * (device): L1 = mean |render - meas| over all V*H*W pixels; SSIM (Wang 2004) with
+ * an 11x11 Gaussian window (sigma 1.5), zero padding, C1 = 1e-4, C2 = 9e-4, mean of
+ * the SSIM map per view, averaged over views.  Writes the loss to *loss (device
+ * float) and d loss / d render to drender[V][H][W] (device, overwritten). */
+size_t r2g_loss_workspace_size(int32_t V, int32_t H, int32_t W);
+r2g_status r2g_projection_loss(int32_t V, int32_t H, int32_t W, const float* render, const float* meas,
+                               float lambda_ssim, float* loss, float* drender, void* ws, size_t ws_bytes,
+                               r2g_stream stream);
+
+/* lambda_tv x anisotropic 3D total variation (Sec. 4.2.3): for each axis, the mean
+ * of |forward difference| over all valid differences, summed over the 3 axes, of
+ * each of G volumes vol[G][D][D][D] (device), summed over the G volumes.  Writes
+ * *loss (device) and dvol (device, overwritten).  2 <= D <= 1024. */
+r2g_status r2g_tv3d(int32_t G, int32_t D, const float* vol, float lambda_tv, float* loss, float* dvol,
+                    r2g_stream stream);
+
+/* ---------------------------------------------------------------- optimizer
+ *
+ * One Adam step (Sec. 5.1) on the raw parameters, given gradients with respect to
+ * the ACTIVATED parameters that the rasterizer/voxelizer consumed.  Raw ->
+ * activated: mean as is, scale = exp(raw_scale), quat as is, rho = softplus(raw_rho).
+ * The step reads the gradients, updates the raw parameters and both moments,
+ * writes the new activated parameters, and zeroes the gradients for the next
+ * iteration.  Learning rate per group: lr0 * final_factor^(it / total_iters);
+ * `it` is the 0-based iteration.  raw, act, grad, m, v are device float32 arrays
+ * of M*11 entries laid out group after group: mean [M][3], scale [M][3],
+ * quat [M][4], rho [M]. */
+typedef struct {
+    float lr0[4];        /* mean, scale, quat, rho: 2e-4, 5e-3, 1e-3, 1e-2 in the paper */
+    float final_factor;  /* 0.1 */
+    int32_t total_iters; /* 30000 */
+    float beta1, beta2, eps;
+} r2g_adam_opts;
+
+r2g_status r2g_adam_step(int64_t M, float* raw, float* act, float* grad, float* m, float* v, int32_t it,
+                         const r2g_adam_opts* opts, r2g_stream stream);
+
+/* ---------------------------------------------------------------- status */
+
+/* Waits for `stream`, then returns the device status of the last call on `ws`
+ * (R2G_OK or R2G_E_CAPACITY) and, if needed_keys is not NULL, the number of list
+ * entries that call needed.  Clears nothing. */
+r2g_status r2g_poll(const void* ws, size_t ws_bytes, r2g_stream stream, int64_t* needed_keys);
+
+/* Thread-local description of the last error returned on this thread. */
+const char* r2g_last_error(void);
+
+/* Library version string. */
+const char* r2g_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* R2G_H */

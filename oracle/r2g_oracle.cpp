@@ -707,20 +707,14 @@ F32Out project_f32(const float* p, const float* s, const float* q, const float* 
     R[2][0] = 2.0f * (xz - wy);
     R[2][1] = 2.0f * (yz + wx);
     R[2][2] = 1.0f - 2.0f * (xx + yy);
-    float Mm[3][3];
+    float Mm[3][3];  // M = R S
     for (int j = 0; j < 3; ++j)
         for (int k = 0; k < 3; ++k) Mm[j][k] = R[j][k] * s[k];
-    float Sg[3][3];
-    for (int j = 0; j < 3; ++j)
-        for (int l = j; l < 3; ++l) {
-            Sg[j][l] = (Mm[j][0] * Mm[l][0] + Mm[j][1] * Mm[l][1]) + Mm[j][2] * Mm[l][2];
-            Sg[l][j] = Sg[j][l];
-        }
     float u[3];
     for (int j = 0; j < 3; ++j)
         u[j] = ((view[3 * j + 0] * p[0] + view[3 * j + 1] * p[1]) + view[3 * j + 2] * p[2]) + view[9 + j];
     o.u2 = u[2];
-    float T[2][3];
+    float T[2][3];  // first two rows of J W
     if (beam == 1) {
         if (!(u[2] > near_plane)) return o;
         const float f = L_SD / u[2];
@@ -740,16 +734,20 @@ F32Out project_f32(const float* p, const float* s, const float* q, const float* 
             T[1][k] = view[1 * 3 + k];
         }
     }
-    float ST[2][3];  // (Sigma t_a)_k for a = 0, 1
+    // N = T M (2x3); Sigma^ = N N^T; |Sigma^| by Cauchy-Binet as a sum of squared 2x2 minors
+    float N[2][3];
     for (int a = 0; a < 2; ++a)
-        for (int k = 0; k < 3; ++k) ST[a][k] = (Sg[k][0] * T[a][0] + Sg[k][1] * T[a][1]) + Sg[k][2] * T[a][2];
-    const float al = (T[0][0] * ST[0][0] + T[0][1] * ST[0][1]) + T[0][2] * ST[0][2];
-    const float be = (T[0][0] * ST[1][0] + T[0][1] * ST[1][1]) + T[0][2] * ST[1][2];
-    const float ga = (T[1][0] * ST[1][0] + T[1][1] * ST[1][1]) + T[1][2] * ST[1][2];
+        for (int k = 0; k < 3; ++k) N[a][k] = (T[a][0] * Mm[0][k] + T[a][1] * Mm[1][k]) + T[a][2] * Mm[2][k];
+    const float al = (N[0][0] * N[0][0] + N[0][1] * N[0][1]) + N[0][2] * N[0][2];
+    const float be = (N[0][0] * N[1][0] + N[0][1] * N[1][1]) + N[0][2] * N[1][2];
+    const float ga = (N[1][0] * N[1][0] + N[1][1] * N[1][1]) + N[1][2] * N[1][2];
+    const float m01 = N[0][0] * N[1][1] - N[0][1] * N[1][0];
+    const float m02 = N[0][0] * N[1][2] - N[0][2] * N[1][0];
+    const float m12 = N[0][1] * N[1][2] - N[0][2] * N[1][1];
     o.sh[0] = al;
     o.sh[1] = be;
     o.sh[2] = ga;
-    o.det = al * ga - be * be;
+    o.det = (m01 * m01 + m02 * m02) + m12 * m12;
     if (!(o.det > 0.0f)) return o;
     const float ex = std::sqrt(Q * al), ey = std::sqrt(Q * ga);
     const float hw = 0.5f * (float)Wd - 0.5f, hh = 0.5f * (float)H - 0.5f;

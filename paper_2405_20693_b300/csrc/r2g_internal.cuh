@@ -1,0 +1,122 @@
+// r2g_internal.cuh -- shared internals of the sm_103a library: errors, the
+// workspace status block, device helpers, and the list-building primitives
+// (count scan, stable radix sort, key ranges) that the rasterizer and the
+// voxelizer both use.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/r2g.h"
+
+#define R2G_API extern "C" __attribute__((visibility("default")))
+
+namespace r2g {
+
+// ---------------------------------------------------------------- errors
+
+void set_error(const char* fmt, ...);
+r2g_status fail(r2g_status s, const char* fmt, ...);
+// R2G_E_CUDA with a message if the last launch failed, else R2G_OK.
+r2g_status check_launch(const char* what);
+
+// ---------------------------------------------------------------- workspace
+
+// Status block at offset 0 of every workspace (256 bytes).
+struct WsStatus {
+    int32_t status;             // R2G_OK or R2G_E_CAPACITY
+    int32_t pad;
+    unsigned long long needed;  // list entries the last call needed
+    unsigned long long n_keys;  // entries actually emitted = min(needed, capacity)
+    unsigned long long pairs;   // gated pairs (counting runs only)
+    unsigned long long reserved[28];
+};
+static_assert(sizeof(WsStatus) == 256, "status block is 256 bytes");
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+// Bump layout over a workspace base pointer.
+struct Layout {
+    size_t off = 0;
+    size_t take(size_t bytes) {
+        const size_t o = off;
+        off = align_up(off + bytes);
+        return o;
+    }
+};
+
+// ---------------------------------------------------------------- list building
+
+constexpr int kScanBlocks = 148 * 4;  // fixed grid of the count scan and the key emission
+constexpr int kSortBlocks = 148 * 8;  // fixed grid of the radix passes
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 1 << kRadixBits;
+
+// Scratch the sort needs (block histograms and digit totals), excluding the two
+// entry buffers.
+size_t sort_scratch_bytes();
+
+// Stable LSD radix sort of status->n_keys 64-bit entries (read on the device) by
+// bits [32, 32 + key_bits).  Returns the buffer that holds the result (a or b).
+uint64_t* radix_sort_u64(uint64_t* a, uint64_t* b, uint32_t* scratch, const WsStatus* status, int key_bits,
+                         cudaStream_t st);
+
+// ranges[k] = [start, end) of key k in the sorted entries (absent keys: [0, 0)).
+void build_ranges(const uint64_t* sorted, const WsStatus* status, uint2* ranges, int64_t n_slots, cudaStream_t st);
+
+inline int bits_for(int64_t n_slots) {
+    int b = 1;
+    while ((int64_t(1) << b) < n_slots) ++b;
+    return b;
+}
+
+// ---------------------------------------------------------------- device helpers
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+constexpr float kLog2e = 1.4426950408889634f;
+
+// Block-wide exclusive scan of one uint32 per thread for a 256-thread block.
+// Returns the exclusive prefix; *total receives the block sum.  smem holds 8 words.
+__device__ __forceinline__ uint32_t block_exclusive_scan_256(uint32_t v, uint32_t* smem, uint32_t* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) smem[warp] = x;
+    __syncthreads();
+    uint32_t wsum = 0, tot = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) {
+        const uint32_t s = smem[w];
+        wsum += (w < warp) ? s : 0u;
+        tot += s;
+    }
+    __syncthreads();
+    *total = tot;
+    return wsum + x - v;
+}
+
+// Block-wide sum of a 64-bit value for a 256-thread block (result valid in all threads).
+__device__ __forceinline__ unsigned long long block_sum_u64_256(unsigned long long v, unsigned long long* smem) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) smem[warp] = v;
+    __syncthreads();
+    unsigned long long t = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) t += smem[w];
+    __syncthreads();
+    return t;
+}
+
+}  // namespace r2g

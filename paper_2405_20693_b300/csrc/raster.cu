@@ -1,0 +1,822 @@
+// raster.cu -- the X-ray rasterizer of R^2-Gaussian on sm_103a: projection
+// (Eq. 6, Eq. 7, App. A), tile binning, the additive splat (Eq. 5, Eq. 7) and
+// its adjoint.
+//
+// Kernels (all FP32 on the CUDA cores; the path is no dense contraction):
+//   k_project      one thread per (view, Gaussian) record: the stated FP32
+//                  sequence for p^, Sigma^ and the tile bound, the rectified
+//                  amplitude rho_hat = mu rho, and a 32-byte splat record
+//                  {cx, cy, A, B, C, rho_hat, rx, ry} in pixel units with the
+//                  conic pre-scaled by -log2(e)/2 so that exp(-q/2) = 2^t.
+//   emit / sort    (tile, Gaussian id) entries, stable radix sort, tile ranges.
+//   k_splat_fwd    one CTA per tile; records are staged through shared memory
+//                  in batches; each thread owns two horizontally adjacent
+//                  pixels and accumulates rho_hat 2^t [t >= Tq]; a warp skips
+//                  records whose row span misses its rows.
+//   k_splat_bwd    one CTA per tile with dL/dI of the tile in shared memory;
+//                  each thread takes one record and walks the pixels of its
+//                  box inside the tile, accumulating six moments
+//                  (sum w, w dx, w dy, w dx^2, w dx dy, w dy^2; w = g e) in
+//                  registers -- no shuffles -- then adds them with two vector
+//                  atomics to the record's slot.
+//   k_project_bwd  one thread per Gaussian, looping over views: moments ->
+//                  gradients of (rho_hat, p^, conic) -> chain rule through the
+//                  projection to d mean, d scale, d quat, d rho.
+#include <math.h>
+
+#include "emit.cuh"
+#include "r2g_internal.cuh"
+
+namespace r2g {
+namespace {
+
+struct CamF {
+    int beam, H, W;
+    float L_SD, pu, pv, ou, ov, near_plane;
+};
+
+struct Params {
+    const float* mean;
+    const float* scale;
+    const float* quat;
+    const float* rho;
+};
+
+// ------------------------------------------------------------------ stated FP32 projection
+// Every step below is one correctly rounded IEEE single operation (the _rn
+// intrinsics are never contracted), in the order the header states.
+
+struct Proj {
+    float R[3][3];
+    float qn[4];
+    float qnorm;
+    float Mm[3][3];
+    float u[3];
+    float f, j02, j12;
+    float T[2][3];
+    float N[2][3];
+    float al, be, ga, det;
+    float phx, phy;
+    bool valid;
+};
+
+__device__ __forceinline__ float fm(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fa(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fs(float a, float b) { return __fsub_rn(a, b); }
+
+__device__ __forceinline__ void rotation(const float q[4], Proj& P) {
+    const float n2 = fa(fa(fa(fm(q[0], q[0]), fm(q[1], q[1])), fm(q[2], q[2])), fm(q[3], q[3]));
+    const float n = __fsqrt_rn(n2);
+    P.qnorm = n;
+    const float w = __fdiv_rn(q[0], n), x = __fdiv_rn(q[1], n), y = __fdiv_rn(q[2], n), z = __fdiv_rn(q[3], n);
+    P.qn[0] = w;
+    P.qn[1] = x;
+    P.qn[2] = y;
+    P.qn[3] = z;
+    const float xx = fm(x, x), yy = fm(y, y), zz = fm(z, z), xy = fm(x, y), xz = fm(x, z), yz = fm(y, z);
+    const float wx = fm(w, x), wy = fm(w, y), wz = fm(w, z);
+    P.R[0][0] = fs(1.0f, fm(2.0f, fa(yy, zz)));
+    P.R[0][1] = fm(2.0f, fs(xy, wz));
+    P.R[0][2] = fm(2.0f, fa(xz, wy));
+    P.R[1][0] = fm(2.0f, fa(xy, wz));
+    P.R[1][1] = fs(1.0f, fm(2.0f, fa(xx, zz)));
+    P.R[1][2] = fm(2.0f, fs(yz, wx));
+    P.R[2][0] = fm(2.0f, fs(xz, wy));
+    P.R[2][1] = fm(2.0f, fa(yz, wx));
+    P.R[2][2] = fs(1.0f, fm(2.0f, fa(xx, yy)));
+}
+
+__device__ __forceinline__ void project_stated(const float p[3], const float s[3], const float q[4],
+                                               const float* __restrict__ view, const CamF& cam, Proj& P) {
+    rotation(q, P);
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) P.Mm[j][k] = fm(P.R[j][k], s[k]);
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+        P.u[j] = fa(fa(fa(fm(view[3 * j], p[0]), fm(view[3 * j + 1], p[1])), fm(view[3 * j + 2], p[2])), view[9 + j]);
+    P.valid = false;
+    if (cam.beam == 1) {
+        if (!(P.u[2] > cam.near_plane)) return;
+        P.f = __fdiv_rn(cam.L_SD, P.u[2]);
+        P.j02 = -__fdiv_rn(fm(P.f, P.u[0]), P.u[2]);
+        P.j12 = -__fdiv_rn(fm(P.f, P.u[1]), P.u[2]);
+        P.phx = fm(P.f, P.u[0]);
+        P.phy = fm(P.f, P.u[1]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            P.T[0][k] = fa(fm(P.f, view[k]), fm(P.j02, view[6 + k]));
+            P.T[1][k] = fa(fm(P.f, view[3 + k]), fm(P.j12, view[6 + k]));
+        }
+    } else {
+        P.f = 1.0f;
+        P.j02 = 0.0f;
+        P.j12 = 0.0f;
+        P.phx = P.u[0];
+        P.phy = P.u[1];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            P.T[0][k] = view[k];
+            P.T[1][k] = view[3 + k];
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            P.N[a][k] = fa(fa(fm(P.T[a][0], P.Mm[0][k]), fm(P.T[a][1], P.Mm[1][k])), fm(P.T[a][2], P.Mm[2][k]));
+    P.al = fa(fa(fm(P.N[0][0], P.N[0][0]), fm(P.N[0][1], P.N[0][1])), fm(P.N[0][2], P.N[0][2]));
+    P.be = fa(fa(fm(P.N[0][0], P.N[1][0]), fm(P.N[0][1], P.N[1][1])), fm(P.N[0][2], P.N[1][2]));
+    P.ga = fa(fa(fm(P.N[1][0], P.N[1][0]), fm(P.N[1][1], P.N[1][1])), fm(P.N[1][2], P.N[1][2]));
+    const float m01 = fs(fm(P.N[0][0], P.N[1][1]), fm(P.N[0][1], P.N[1][0]));
+    const float m02 = fs(fm(P.N[0][0], P.N[1][2]), fm(P.N[0][2], P.N[1][0]));
+    const float m12 = fs(fm(P.N[0][1], P.N[1][2]), fm(P.N[0][2], P.N[1][1]));
+    P.det = fa(fa(fm(m01, m01), fm(m02, m02)), fm(m12, m12));
+    P.valid = P.det > 0.0f;
+}
+
+__device__ __forceinline__ float ceil_clamped(float x, int n) {
+    if (!(x > -1.0f)) return -1.0f;
+    if (x > (float)n) return (float)n;
+    return ceilf(x);
+}
+__device__ __forceinline__ float floor_clamped(float x, int n) {
+    if (!(x > -1.0f)) return -1.0f;
+    if (x > (float)n) return (float)n;
+    return floorf(x);
+}
+
+struct Bound {
+    float cx, cy, rx, ry;
+    int c0, c1, r0, r1;
+    bool ok;
+};
+
+__device__ __forceinline__ Bound pixel_bound(const Proj& P, const CamF& cam, float Q) {
+    Bound b;
+    const float ex = __fsqrt_rn(fm(Q, P.al)), ey = __fsqrt_rn(fm(Q, P.ga));
+    const float hw = fs(fm(0.5f, (float)cam.W), 0.5f), hh = fs(fm(0.5f, (float)cam.H), 0.5f);
+    b.cx = fa(__fdiv_rn(fs(P.phx, cam.ou), cam.pu), hw);
+    b.cy = fa(__fdiv_rn(fs(P.phy, cam.ov), cam.pv), hh);
+    b.rx = __fdiv_rn(ex, cam.pu);
+    b.ry = __fdiv_rn(ey, cam.pv);
+    b.c0 = max(0, (int)ceil_clamped(fs(b.cx, b.rx), cam.W));
+    b.c1 = min(cam.W - 1, (int)floor_clamped(fa(b.cx, b.rx), cam.W));
+    b.r0 = max(0, (int)ceil_clamped(fs(b.cy, b.ry), cam.H));
+    b.r1 = min(cam.H - 1, (int)floor_clamped(fa(b.cy, b.ry), cam.H));
+    b.ok = P.valid && b.c0 <= b.c1 && b.r0 <= b.r1;
+    return b;
+}
+
+// omega^T Sigma^{-1} omega with omega the unit source->mean direction (cone) or
+// the beam direction (parallel), in the Gaussian's local frame.
+__device__ __forceinline__ float kappa_of(const Proj& P, const float s[3], const float* __restrict__ view,
+                                          const CamF& cam, float om[3], float v[3]) {
+    if (cam.beam == 1) {
+        const float l = sqrtf(P.u[0] * P.u[0] + P.u[1] * P.u[1] + P.u[2] * P.u[2]);
+        const float n0 = P.u[0] / l, n1 = P.u[1] / l, n2 = P.u[2] / l;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) om[k] = view[k] * n0 + view[3 + k] * n1 + view[6 + k] * n2;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) om[k] = view[6 + k];
+    }
+    float kap = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        v[k] = P.R[0][k] * om[0] + P.R[1][k] * om[1] + P.R[2][k] * om[2];
+        kap += v[k] * v[k] / (s[k] * s[k]);
+    }
+    return kap;
+}
+
+__device__ __forceinline__ void load_gaussian(const Params& G, long long i, float p[3], float s[3], float q[4]) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        p[k] = G.mean[3 * i + k];
+        s[k] = G.scale[3 * i + k];
+    }
+    const float4 qq = reinterpret_cast<const float4*>(G.quat)[i];
+    q[0] = qq.x;
+    q[1] = qq.y;
+    q[2] = qq.z;
+    q[3] = qq.w;
+}
+
+constexpr float kTwoPi = 6.283185307179586f;
+
+// ------------------------------------------------------------------ K1: project
+
+__global__ void __launch_bounds__(256) k_project(Params G, const float* __restrict__ views, CamF cam, float Q,
+                                                 int TW, int TH, long long M, long long n_rec,
+                                                 float4* __restrict__ rec, uint2* __restrict__ rect,
+                                                 float* __restrict__ proj_out, int* __restrict__ rect_out) {
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_rec) return;
+    const long long v = r / M, i = r - v * M;
+    const float* view = views + 12 * v;
+    float p[3], s[3], q[4];
+    load_gaussian(G, i, p, s, q);
+    Proj P;
+    project_stated(p, s, q, view, cam, P);
+    const Bound b = pixel_bound(P, cam, Q);
+    float rhohat = 0.0f;
+    if (b.ok) {
+        float om[3], vv[3];
+        const float kap = kappa_of(P, s, view, cam, om, vv);
+        rhohat = sqrtf(kTwoPi / kap) * G.rho[i];
+    }
+    if (rec) {
+        float4 a, c;
+        if (b.ok) {
+            const float id = 1.0f / P.det;
+            const float ca = P.ga * id * cam.pu * cam.pu;      // conic in pixel units
+            const float cb = -P.be * id * cam.pu * cam.pv;
+            const float cc = P.al * id * cam.pv * cam.pv;
+            a = make_float4(b.cx, b.cy, -0.5f * kLog2e * ca, -kLog2e * cb);
+            c = make_float4(-0.5f * kLog2e * cc, rhohat, b.rx, b.ry);
+        } else {
+            a = make_float4(0.f, 0.f, 0.f, 0.f);
+            c = make_float4(0.f, 0.f, -1.f, -1.f);
+        }
+        rec[2 * r] = a;
+        rec[2 * r + 1] = c;
+        uint2 rc;
+        if (b.ok) {
+            rc.x = (uint32_t)(b.c0 / TW) | ((uint32_t)(b.c1 / TW) << 16);
+            rc.y = (uint32_t)(b.r0 / TH) | ((uint32_t)(b.r1 / TH) << 16);
+        } else {
+            rc.x = 0xffffu;  // lo > hi: no tiles
+            rc.y = 0xffffu;
+        }
+        rect[r] = rc;
+    }
+    if (proj_out) {
+        float* o = proj_out + 8 * r;
+        o[0] = P.phx;
+        o[1] = P.phy;
+        o[2] = P.al;
+        o[3] = P.be;
+        o[4] = P.ga;
+        o[5] = P.det;
+        o[6] = rhohat;
+        o[7] = b.ok ? 1.0f : 0.0f;
+        int* o2 = rect_out + 4 * r;
+        o2[0] = b.ok ? b.c0 : 0;
+        o2[1] = b.ok ? b.c1 : 0;
+        o2[2] = b.ok ? b.r0 : 0;
+        o2[3] = b.ok ? b.r1 : 0;
+    }
+}
+
+// ------------------------------------------------------------------ K2: tile keys
+
+struct TileOp {
+    const uint2* rect;
+    long long M;
+    int tiles_x, tiles_per_view;
+
+    __device__ __forceinline__ uint32_t count(long long r) const {
+        const uint2 rc = rect[r];
+        const int x0 = rc.x & 0xffff, x1 = rc.x >> 16, y0 = rc.y & 0xffff, y1 = rc.y >> 16;
+        return (x1 >= x0 && y1 >= y0) ? (uint32_t)((x1 - x0 + 1) * (y1 - y0 + 1)) : 0u;
+    }
+    __device__ __forceinline__ void emit(long long r, uint64_t* out, unsigned long long off,
+                                         unsigned long long cap) const {
+        const uint2 rc = rect[r];
+        const int x0 = rc.x & 0xffff, x1 = rc.x >> 16, y0 = rc.y & 0xffff, y1 = rc.y >> 16;
+        const long long v = r / M, i = r - v * M;
+        const uint32_t base = (uint32_t)(v * tiles_per_view);
+        for (int ty = y0; ty <= y1; ++ty)
+            for (int tx = x0; tx <= x1; ++tx) {
+                if (off < cap) out[off] = ((uint64_t)(base + (uint32_t)(ty * tiles_x + tx)) << 32) | (uint64_t)i;
+                ++off;
+            }
+    }
+};
+
+// ------------------------------------------------------------------ K3: splat forward
+
+template <int TW, int TH, bool COUNT>
+__global__ void __launch_bounds__(TW * TH / 2) k_splat_fwd(const float4* __restrict__ rec,
+                                                           const uint2* __restrict__ ranges,
+                                                           const uint64_t* __restrict__ sorted, long long M,
+                                                           int tiles_x, int tiles_per_view, int H, int W, float Tq,
+                                                           float* __restrict__ image, WsStatus* st) {
+    constexpr int NT = TW * TH / 2;  // threads; two pixels each
+    constexpr int TPR = TW / 2;      // threads per pixel row
+    constexpr int RPW = 32 / TPR;    // pixel rows per warp
+    static_assert(32 % TPR == 0 && NT % 32 == 0, "tile shape");
+    __shared__ float4 s_a[NT];
+    __shared__ float4 s_b[NT];
+    const int tile = blockIdx.x;
+    const int v = tile / tiles_per_view;
+    const int lt = tile - v * tiles_per_view;
+    const int ty = lt / tiles_x, tx = lt - ty * tiles_x;
+    const int lx = (threadIdx.x % TPR) * 2, ly = threadIdx.x / TPR;
+    const int px = tx * TW + lx, py = ty * TH + ly;
+    const int warp = threadIdx.x >> 5;
+    const float wr0 = (float)(ty * TH + warp * RPW), wr1 = wr0 + (float)(RPW - 1);
+    const float fx = (float)px, fy = (float)py;
+    const float4* vrec = rec + 2 * (size_t)v * (size_t)M;
+    float acc0 = 0.0f, acc1 = 0.0f;
+    unsigned int cnt = 0;
+    const uint2 rg = ranges[tile];
+    for (uint32_t base = rg.x; base < rg.y; base += NT) {
+        const int n = min((uint32_t)NT, rg.y - base);
+        __syncthreads();
+        if ((int)threadIdx.x < n) {
+            const uint32_t gid = (uint32_t)sorted[base + threadIdx.x];
+            s_a[threadIdx.x] = vrec[2 * (size_t)gid];
+            s_b[threadIdx.x] = vrec[2 * (size_t)gid + 1];
+        }
+        __syncthreads();
+        for (int j = 0; j < n; ++j) {
+            const float4 a = s_a[j];  // cx, cy, A, B
+            const float4 b = s_b[j];  // C, rho_hat, rx, ry
+            if (a.y + b.w < wr0 || a.y - b.w > wr1) continue;  // warp-uniform row cull
+            const float dy = fy - a.y;
+            const float bdy = a.w * dy;
+            const float cdy2 = b.x * dy * dy;
+            const float dx0 = fx - a.x;
+            const float dx1 = dx0 + 1.0f;
+            const float t0 = fmaf(fmaf(a.z, dx0, bdy), dx0, cdy2);
+            const float t1 = fmaf(fmaf(a.z, dx1, bdy), dx1, cdy2);
+            const float e0 = ex2_approx(t0);
+            const float e1 = ex2_approx(t1);
+            acc0 = (t0 >= Tq) ? fmaf(b.y, e0, acc0) : acc0;
+            acc1 = (t1 >= Tq) ? fmaf(b.y, e1, acc1) : acc1;
+            if (COUNT) cnt += (t0 >= Tq && px < W && py < H) + (t1 >= Tq && px + 1 < W && py < H);
+        }
+    }
+    if (py < H) {
+        float* row = image + ((size_t)v * H + py) * W;
+        if (px < W) row[px] = acc0;
+        if (px + 1 < W) row[px + 1] = acc1;
+    }
+    if (COUNT) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(&st->pairs, (unsigned long long)cnt);
+    }
+}
+
+// ------------------------------------------------------------------ K5: splat backward
+
+constexpr int kBwdThreads = 128;
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(kBwdThreads) k_splat_bwd(const float4* __restrict__ rec,
+                                                           const uint2* __restrict__ ranges,
+                                                           const uint64_t* __restrict__ sorted, long long M,
+                                                           int tiles_x, int tiles_per_view, int H, int W, float Tq,
+                                                           const float* __restrict__ dimage,
+                                                           float4* __restrict__ mom) {
+    __shared__ float s_g[TH][TW];
+    const int tile = blockIdx.x;
+    const int v = tile / tiles_per_view;
+    const int lt = tile - v * tiles_per_view;
+    const int ty = lt / tiles_x, tx = lt - ty * tiles_x;
+    const int X0 = tx * TW, Y0 = ty * TH;
+    for (int k = threadIdx.x; k < TW * TH; k += kBwdThreads) {
+        const int r = k / TW, c = k - r * TW;
+        const int gy = Y0 + r, gx = X0 + c;
+        s_g[r][c] = (gy < H && gx < W) ? dimage[((size_t)v * H + gy) * W + gx] : 0.0f;
+    }
+    __syncthreads();
+    const uint2 rg = ranges[tile];
+    const float4* vrec = rec + 2 * (size_t)v * (size_t)M;
+    float4* vmom = mom + 2 * (size_t)v * (size_t)M;
+    for (uint32_t e = rg.x + threadIdx.x; e < rg.y; e += kBwdThreads) {
+        const uint32_t gid = (uint32_t)sorted[e];
+        const float4 a = vrec[2 * (size_t)gid];
+        const float4 b = vrec[2 * (size_t)gid + 1];
+        const int c0 = max(X0, (int)ceilf(a.x - b.z)), c1 = min(X0 + TW - 1, (int)floorf(a.x + b.z));
+        const int r0 = max(Y0, (int)ceilf(a.y - b.w)), r1 = min(Y0 + TH - 1, (int)floorf(a.y + b.w));
+        float S0 = 0.f, Sx = 0.f, Sy = 0.f, Sxx = 0.f, Sxy = 0.f, Syy = 0.f;
+        for (int r = r0; r <= r1; ++r) {
+            const float dy = (float)r - a.y;
+            const float bdy = a.w * dy;
+            const float cdy2 = b.x * dy * dy;
+            const float* grow = &s_g[r - Y0][0];
+            for (int c = c0; c <= c1; ++c) {
+                const float dx = (float)c - a.x;
+                const float t = fmaf(fmaf(a.z, dx, bdy), dx, cdy2);
+                if (t >= Tq) {
+                    const float w = grow[c - X0] * ex2_approx(t);
+                    const float wx = w * dx;
+                    S0 += w;
+                    Sx += wx;
+                    Sy = fmaf(w, dy, Sy);
+                    Sxx = fmaf(wx, dx, Sxx);
+                    Sxy = fmaf(wx, dy, Sxy);
+                    Syy = fmaf(w * dy, dy, Syy);
+                }
+            }
+        }
+        if (S0 != 0.f || Sx != 0.f || Sy != 0.f || Sxx != 0.f || Sxy != 0.f || Syy != 0.f) {
+            atomicAdd(&vmom[2 * (size_t)gid], make_float4(S0, Sx, Sy, Sxx));
+            atomicAdd(reinterpret_cast<float2*>(&vmom[2 * (size_t)gid + 1]), make_float2(Sxy, Syy));
+        }
+    }
+}
+
+// ------------------------------------------------------------------ K6: projection backward
+
+// dL/dR (full 3x3) -> dL/dq through R(q / |q|).
+__device__ __forceinline__ void quat_grad(const float qn[4], float qnorm, const float g[3][3], float dq[4]) {
+    const float w = qn[0], x = qn[1], y = qn[2], z = qn[3];
+    float dw = 0.f, dx = 0.f, dy = 0.f, dz = 0.f;
+    dy -= 4.f * y * g[0][0]; dz -= 4.f * z * g[0][0];
+    dx += 2.f * y * g[0][1]; dy += 2.f * x * g[0][1]; dw -= 2.f * z * g[0][1]; dz -= 2.f * w * g[0][1];
+    dx += 2.f * z * g[0][2]; dz += 2.f * x * g[0][2]; dw += 2.f * y * g[0][2]; dy += 2.f * w * g[0][2];
+    dx += 2.f * y * g[1][0]; dy += 2.f * x * g[1][0]; dw += 2.f * z * g[1][0]; dz += 2.f * w * g[1][0];
+    dx -= 4.f * x * g[1][1]; dz -= 4.f * z * g[1][1];
+    dy += 2.f * z * g[1][2]; dz += 2.f * y * g[1][2]; dw -= 2.f * x * g[1][2]; dx -= 2.f * w * g[1][2];
+    dx += 2.f * z * g[2][0]; dz += 2.f * x * g[2][0]; dw -= 2.f * y * g[2][0]; dy -= 2.f * w * g[2][0];
+    dy += 2.f * z * g[2][1]; dz += 2.f * y * g[2][1]; dw += 2.f * x * g[2][1]; dx += 2.f * w * g[2][1];
+    dx -= 4.f * x * g[2][2]; dy -= 4.f * y * g[2][2];
+    const float dot = w * dw + x * dx + y * dy + z * dz;
+    dq[0] = (dw - w * dot) / qnorm;
+    dq[1] = (dx - x * dot) / qnorm;
+    dq[2] = (dy - y * dot) / qnorm;
+    dq[3] = (dz - z * dot) / qnorm;
+}
+
+__global__ void __launch_bounds__(128) k_project_bwd(Params G, const float* __restrict__ views, CamF cam, float Q,
+                                                     long long M, int V, const float4* __restrict__ rec,
+                                                     const float4* __restrict__ mom, float* __restrict__ dmean,
+                                                     float* __restrict__ dscale, float* __restrict__ dquat,
+                                                     float* __restrict__ drho) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    float p[3], s[3], q[4];
+    load_gaussian(G, i, p, s, q);
+    const float rho = G.rho[i];
+    float gp[3] = {0.f, 0.f, 0.f}, gs[3] = {0.f, 0.f, 0.f}, gR[3][3] = {{0.f}}, grho = 0.f;
+    Proj P;
+    bool have_rot = false;
+    for (int v = 0; v < V; ++v) {
+        const size_t r = (size_t)v * (size_t)M + (size_t)i;
+        const float4 m0 = mom[2 * r];
+        const float4 m1 = mom[2 * r + 1];
+        if (m0.x == 0.f && m0.y == 0.f && m0.z == 0.f && m0.w == 0.f && m1.x == 0.f && m1.y == 0.f) continue;
+        const float rhohat = rec[2 * r + 1].y;
+        const float* view = views + 12 * v;
+        project_stated(p, s, q, view, cam, P);
+        have_rot = true;
+        // --- moments -> gradients of the pixel-unit record
+        const float D = P.det, id = 1.0f / D;
+        const float ca = P.ga * id, cb = -P.be * id, cc = P.al * id;  // conic, detector units
+        const float pa = ca * cam.pu * cam.pu, pb = cb * cam.pu * cam.pv, pc = cc * cam.pv * cam.pv;
+        const float S0 = m0.x, Sx = m0.y, Sy = m0.z, Sxx = m0.w, Sxy = m1.x, Syy = m1.y;
+        const float d_rhohat = S0;
+        const float d_cx = rhohat * (pa * Sx + pb * Sy);
+        const float d_cy = rhohat * (pb * Sx + pc * Sy);
+        const float d_pa = -0.5f * rhohat * Sxx, d_pb = -rhohat * Sxy, d_pc = -0.5f * rhohat * Syy;
+        // --- to detector units
+        const float d_phx = d_cx / cam.pu, d_phy = d_cy / cam.pv;
+        const float d_a = d_pa * cam.pu * cam.pu, d_b = d_pb * cam.pu * cam.pv, d_c = d_pc * cam.pv * cam.pv;
+        // --- conic (a, b, c) = (gamma, -beta, alpha) / D  ->  Sigma^ (alpha, beta, gamma)
+        const float al = P.al, be = P.be, ga = P.ga, iD2 = id * id;
+        const float d_al = (-ga * ga * d_a + be * ga * d_b - be * be * d_c) * iD2;
+        const float d_be = (2.f * be * ga * d_a - (al * ga + be * be) * d_b + 2.f * al * be * d_c) * iD2;
+        const float d_ga = (-be * be * d_a + al * be * d_b - al * al * d_c) * iD2;
+        // --- Sigma^ = N N^T
+        float dN[2][3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            dN[0][k] = 2.f * d_al * P.N[0][k] + d_be * P.N[1][k];
+            dN[1][k] = d_be * P.N[0][k] + 2.f * d_ga * P.N[1][k];
+        }
+        // --- N = T M
+        float dT[2][3], dM[3][3];
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) dT[a][j] = dN[a][0] * P.Mm[j][0] + dN[a][1] * P.Mm[j][1] + dN[a][2] * P.Mm[j][2];
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) dM[j][k] = P.T[0][j] * dN[0][k] + P.T[1][j] * dN[1][k];
+        // --- M = R diag(s)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                gR[j][k] += dM[j][k] * s[k];
+                gs[k] += dM[j][k] * P.R[j][k];
+            }
+        // --- rho_hat = mu rho, mu = sqrt(2 pi / kappa)
+        float om[3], vv[3];
+        const float kap = kappa_of(P, s, view, cam, om, vv);
+        const float mu = sqrtf(kTwoPi / kap);
+        grho += d_rhohat * mu;
+        const float d_kap = -0.5f * d_rhohat * rho * mu / kap;
+        float dv[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float is2 = 1.0f / (s[k] * s[k]);
+            dv[k] = 2.f * d_kap * vv[k] * is2;
+            gs[k] += -2.f * d_kap * vv[k] * vv[k] * is2 / s[k];
+        }
+        float dom[3];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) gR[j][k] += om[j] * dv[k];
+            dom[j] = P.R[j][0] * dv[0] + P.R[j][1] * dv[1] + P.R[j][2] * dv[2];
+        }
+        // --- scanner-space mean
+        float du[3] = {0.f, 0.f, 0.f};
+        if (cam.beam == 1) {
+            const float L = cam.L_SD, u0 = P.u[0], u1 = P.u[1], u2 = P.u[2];
+            const float iu2 = 1.0f / u2;
+            // T rows: f W0 + j02 W2, f W1 + j12 W2
+            float d_f = 0.f, d_j02 = 0.f, d_j12 = 0.f;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                d_f += dT[0][k] * view[k] + dT[1][k] * view[3 + k];
+                d_j02 += dT[0][k] * view[6 + k];
+                d_j12 += dT[1][k] * view[6 + k];
+            }
+            const float f = P.f;
+            // f = L/u2, j02 = -L u0/u2^2, j12 = -L u1/u2^2, p^ = (f u0, f u1)
+            du[0] += -d_j02 * f * iu2 + d_phx * f;
+            du[1] += -d_j12 * f * iu2 + d_phy * f;
+            du[2] += -d_f * f * iu2 + 2.f * (d_j02 * u0 + d_j12 * u1) * f * iu2 * iu2 -
+                     (d_phx * u0 + d_phy * u1) * f * iu2;
+            (void)L;
+            // omega = W^T u/|u|
+            const float l = sqrtf(u0 * u0 + u1 * u1 + u2 * u2), il = 1.0f / l;
+            const float n[3] = {u0 * il, u1 * il, u2 * il};
+            float dn[3];
+#pragma unroll
+            for (int j = 0; j < 3; ++j) dn[j] = view[3 * j] * dom[0] + view[3 * j + 1] * dom[1] + view[3 * j + 2] * dom[2];
+            const float nd = n[0] * dn[0] + n[1] * dn[1] + n[2] * dn[2];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) du[k] += (dn[k] - n[k] * nd) * il;
+        } else {
+            du[0] += d_phx;
+            du[1] += d_phy;
+        }
+        // --- u = W p + t
+#pragma unroll
+        for (int k = 0; k < 3; ++k) gp[k] += view[k] * du[0] + view[3 + k] * du[1] + view[6 + k] * du[2];
+    }
+    if (!have_rot) return;
+    float gq[4];
+    quat_grad(P.qn, P.qnorm, gR, gq);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        dmean[3 * i + k] += gp[k];
+        dscale[3 * i + k] += gs[k];
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) dquat[4 * i + k] += gq[k];
+    drho[i] += grho;
+}
+
+// ------------------------------------------------------------------ host side
+
+struct RasterLayout {
+    size_t status, rec, rect, partials, ranges, mom, scratch, a, b, fixed;
+    int tiles_x, tiles_y, tiles_per_view;
+    long long n_tiles, n_rec;
+};
+
+bool valid_tile(int tw, int th) { return (tw == 16 && th == 16) || (tw == 8 && th == 8) || (tw == 32 && th == 8); }
+
+r2g_status check_args(int64_t M, int32_t V, const r2g_camera* cam, const r2g_raster_opts* opts) {
+    if (!cam || !opts) return fail(R2G_E_INVAL, "camera and options must not be NULL");
+    if (M < 1 || M >= (int64_t(1) << 31)) return fail(R2G_E_INVAL, "M = %lld out of range [1, 2^31)", (long long)M);
+    if (V < 1) return fail(R2G_E_INVAL, "V = %d must be >= 1", V);
+    if ((long long)M * V >= (1ll << 31)) return fail(R2G_E_INVAL, "M * V = %lld must be < 2^31", (long long)M * V);
+    if (cam->beam != 0 && cam->beam != 1) return fail(R2G_E_INVAL, "beam must be 0 or 1");
+    if (cam->H < 1 || cam->W < 1 || cam->H > 32768 || cam->W > 32768)
+        return fail(R2G_E_INVAL, "detector %d x %d out of range", cam->H, cam->W);
+    if (!(cam->pitch_u > 0.f) || !(cam->pitch_v > 0.f)) return fail(R2G_E_INVAL, "pitches must be > 0");
+    if (cam->beam == 1 && !(cam->L_SD > 0.f)) return fail(R2G_E_INVAL, "cone beam needs L_SD > 0");
+    if (!valid_tile(opts->tile_w, opts->tile_h))
+        return fail(R2G_E_INVAL, "tile %dx%d not one of 16x16, 8x8, 32x8", opts->tile_w, opts->tile_h);
+    if (!(opts->Q > 0.f)) return fail(R2G_E_INVAL, "Q must be > 0");
+    const long long tx = (cam->W + opts->tile_w - 1) / opts->tile_w, ty = (cam->H + opts->tile_h - 1) / opts->tile_h;
+    if ((long long)V * tx * ty >= (1ll << 31)) return fail(R2G_E_INVAL, "too many tiles");
+    return R2G_OK;
+}
+
+RasterLayout raster_layout(int64_t M, int32_t V, const r2g_camera* cam, const r2g_raster_opts* opts) {
+    RasterLayout L;
+    L.tiles_x = (cam->W + opts->tile_w - 1) / opts->tile_w;
+    L.tiles_y = (cam->H + opts->tile_h - 1) / opts->tile_h;
+    L.tiles_per_view = L.tiles_x * L.tiles_y;
+    L.n_tiles = (long long)V * L.tiles_per_view;
+    L.n_rec = (long long)M * V;
+    Layout lay;
+    L.status = lay.take(sizeof(WsStatus));
+    L.rec = lay.take(32 * (size_t)L.n_rec);
+    L.rect = lay.take(8 * (size_t)L.n_rec);
+    L.partials = lay.take(8 * (size_t)kScanBlocks);
+    L.ranges = lay.take(8 * (size_t)L.n_tiles);
+    L.mom = lay.take(32 * (size_t)L.n_rec);
+    L.scratch = lay.take(sort_scratch_bytes());
+    L.fixed = lay.off;
+    return L;
+}
+
+// key capacity held by ws_bytes (multiple of 32 entries so both buffers stay aligned)
+long long capacity_of(const RasterLayout& L, size_t ws_bytes) {
+    if (ws_bytes <= L.fixed) return 0;
+    const size_t half = (ws_bytes - L.fixed) / 2;
+    long long cap = (long long)(half / 256) * 32;
+    if (cap > 0xffffffe0ll) cap = 0xffffffe0ll;
+    return cap;
+}
+
+CamF camf(const r2g_camera* c) {
+    CamF f;
+    f.beam = c->beam;
+    f.H = c->H;
+    f.W = c->W;
+    f.L_SD = c->L_SD;
+    f.pu = c->pitch_u;
+    f.pv = c->pitch_v;
+    f.ou = c->off_u;
+    f.ov = c->off_v;
+    f.near_plane = c->near_plane;
+    return f;
+}
+
+template <bool COUNT>
+void launch_fwd(int tw, int th, const float4* rec, const uint2* ranges, const uint64_t* sorted, long long M,
+                const RasterLayout& L, int H, int W, float Tq, float* image, WsStatus* st, cudaStream_t s) {
+    const unsigned grid = (unsigned)L.n_tiles;
+    if (tw == 16 && th == 16)
+        k_splat_fwd<16, 16, COUNT><<<grid, 128, 0, s>>>(rec, ranges, sorted, M, L.tiles_x, L.tiles_per_view, H, W, Tq,
+                                                        image, st);
+    else if (tw == 8 && th == 8)
+        k_splat_fwd<8, 8, COUNT><<<grid, 32, 0, s>>>(rec, ranges, sorted, M, L.tiles_x, L.tiles_per_view, H, W, Tq,
+                                                     image, st);
+    else
+        k_splat_fwd<32, 8, COUNT><<<grid, 128, 0, s>>>(rec, ranges, sorted, M, L.tiles_x, L.tiles_per_view, H, W, Tq,
+                                                       image, st);
+}
+
+void launch_bwd(int tw, int th, const float4* rec, const uint2* ranges, const uint64_t* sorted, long long M,
+                const RasterLayout& L, int H, int W, float Tq, const float* dimage, float4* mom, cudaStream_t s) {
+    const unsigned grid = (unsigned)L.n_tiles;
+    if (tw == 16 && th == 16)
+        k_splat_bwd<16, 16><<<grid, kBwdThreads, 0, s>>>(rec, ranges, sorted, M, L.tiles_x, L.tiles_per_view, H, W,
+                                                         Tq, dimage, mom);
+    else if (tw == 8 && th == 8)
+        k_splat_bwd<8, 8><<<grid, kBwdThreads, 0, s>>>(rec, ranges, sorted, M, L.tiles_x, L.tiles_per_view, H, W,
+                                                       Tq, dimage, mom);
+    else
+        k_splat_bwd<32, 8><<<grid, kBwdThreads, 0, s>>>(rec, ranges, sorted, M, L.tiles_x, L.tiles_per_view, H, W,
+                                                        Tq, dimage, mom);
+}
+
+uint64_t* sorted_buffer(char* base, const RasterLayout& L, long long cap) {
+    uint64_t* a = reinterpret_cast<uint64_t*>(base + L.fixed);
+    uint64_t* b = reinterpret_cast<uint64_t*>(base + L.fixed + align_up(8 * (size_t)cap));
+    const int bits = bits_for(L.n_tiles);
+    const int passes = (bits + kRadixBits - 1) / kRadixBits;
+    return (passes & 1) ? b : a;
+}
+
+}  // namespace
+}  // namespace r2g
+
+using namespace r2g;
+
+R2G_API size_t r2g_raster_workspace_size(int64_t M, int32_t V, const r2g_camera* cam, const r2g_raster_opts* opts,
+                                         int64_t key_capacity) {
+    if (check_args(M, V, cam, opts) != R2G_OK) return 0;
+    if (key_capacity < 1 || key_capacity > 0xffffffe0ll) {
+        fail(R2G_E_INVAL, "key_capacity %lld out of range", (long long)key_capacity);
+        return 0;
+    }
+    const RasterLayout L = raster_layout(M, V, cam, opts);
+    return L.fixed + 2 * align_up(8 * (size_t)key_capacity);
+}
+
+R2G_API r2g_status r2g_project(int64_t M, const float* mean, const float* scale, const float* quat, const float* rho,
+                               int32_t V, const float* views, const r2g_camera* cam, const r2g_raster_opts* opts,
+                               float* proj, int32_t* rect, r2g_stream stream) {
+    r2g_status e = check_args(M, V, cam, opts);
+    if (e) return e;
+    if (!mean || !scale || !quat || !rho || !views || !proj || !rect)
+        return fail(R2G_E_INVAL, "NULL device pointer");
+    if (reinterpret_cast<uintptr_t>(quat) % 16) return fail(R2G_E_INVAL, "quat must be 16-byte aligned");
+    const long long n = (long long)M * V;
+    Params G{mean, scale, quat, rho};
+    k_project<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(G, views, camf(cam), opts->Q, opts->tile_w,
+                                                                opts->tile_h, M, n, nullptr, nullptr, proj, rect);
+    return check_launch("r2g_project");
+}
+
+R2G_API r2g_status r2g_rasterize(int64_t M, const float* mean, const float* scale, const float* quat,
+                                 const float* rho, int32_t V, const float* views, const r2g_camera* cam,
+                                 const r2g_raster_opts* opts, float* image, void* ws, size_t ws_bytes,
+                                 r2g_stream stream) {
+    r2g_status e = check_args(M, V, cam, opts);
+    if (e) return e;
+    if (!mean || !scale || !quat || !rho || !views || !image || !ws) return fail(R2G_E_INVAL, "NULL pointer");
+    if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(R2G_E_INVAL, "workspace must be 256-byte aligned");
+    if (reinterpret_cast<uintptr_t>(quat) % 16) return fail(R2G_E_INVAL, "quat must be 16-byte aligned");
+    const RasterLayout L = raster_layout(M, V, cam, opts);
+    const long long cap = capacity_of(L, ws_bytes);
+    if (cap < 32) return fail(R2G_E_INVAL, "workspace of %zu bytes holds no list entries", ws_bytes);
+    char* base = static_cast<char*>(ws);
+    WsStatus* st = reinterpret_cast<WsStatus*>(base + L.status);
+    float4* rec = reinterpret_cast<float4*>(base + L.rec);
+    uint2* rect = reinterpret_cast<uint2*>(base + L.rect);
+    auto* partials = reinterpret_cast<unsigned long long*>(base + L.partials);
+    uint2* ranges = reinterpret_cast<uint2*>(base + L.ranges);
+    uint32_t* scratch = reinterpret_cast<uint32_t*>(base + L.scratch);
+    uint64_t* a = reinterpret_cast<uint64_t*>(base + L.fixed);
+    uint64_t* b = reinterpret_cast<uint64_t*>(base + L.fixed + align_up(8 * (size_t)cap));
+    cudaMemsetAsync(st, 0, sizeof(WsStatus), stream);
+    Params G{mean, scale, quat, rho};
+    const CamF cf = camf(cam);
+    k_project<<<(unsigned)((L.n_rec + 255) / 256), 256, 0, stream>>>(G, views, cf, opts->Q, opts->tile_w,
+                                                                      opts->tile_h, M, L.n_rec, rec, rect, nullptr,
+                                                                      nullptr);
+    TileOp op{rect, M, L.tiles_x, L.tiles_per_view};
+    emit_lists(op, L.n_rec, partials, st, a, (unsigned long long)cap, stream);
+    uint64_t* sorted = radix_sort_u64(a, b, scratch, st, bits_for(L.n_tiles), stream);
+    build_ranges(sorted, st, ranges, L.n_tiles, stream);
+    const float Tq = -0.5f * kLog2e * opts->Q;
+    if (opts->count_pairs)
+        launch_fwd<true>(opts->tile_w, opts->tile_h, rec, ranges, sorted, M, L, cam->H, cam->W, Tq, image, st, stream);
+    else
+        launch_fwd<false>(opts->tile_w, opts->tile_h, rec, ranges, sorted, M, L, cam->H, cam->W, Tq, image, st,
+                          stream);
+    return check_launch("r2g_rasterize");
+}
+
+R2G_API r2g_status r2g_rasterize_backward(int64_t M, const float* mean, const float* scale, const float* quat,
+                                          const float* rho, int32_t V, const float* views, const r2g_camera* cam,
+                                          const r2g_raster_opts* opts, const float* dimage, float* dmean,
+                                          float* dscale, float* dquat, float* drho, void* ws, size_t ws_bytes,
+                                          r2g_stream stream) {
+    r2g_status e = check_args(M, V, cam, opts);
+    if (e) return e;
+    if (!mean || !scale || !quat || !rho || !views || !dimage || !dmean || !dscale || !dquat || !drho || !ws)
+        return fail(R2G_E_INVAL, "NULL pointer");
+    if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(R2G_E_INVAL, "workspace must be 256-byte aligned");
+    if (reinterpret_cast<uintptr_t>(quat) % 16) return fail(R2G_E_INVAL, "quat must be 16-byte aligned");
+    const RasterLayout L = raster_layout(M, V, cam, opts);
+    const long long cap = capacity_of(L, ws_bytes);
+    if (cap < 32) return fail(R2G_E_INVAL, "workspace of %zu bytes holds no list entries", ws_bytes);
+    char* base = static_cast<char*>(ws);
+    const float4* rec = reinterpret_cast<const float4*>(base + L.rec);
+    const uint2* ranges = reinterpret_cast<const uint2*>(base + L.ranges);
+    float4* mom = reinterpret_cast<float4*>(base + L.mom);
+    const uint64_t* sorted = sorted_buffer(base, L, cap);
+    cudaMemsetAsync(mom, 0, 32 * (size_t)L.n_rec, stream);
+    const float Tq = -0.5f * kLog2e * opts->Q;
+    launch_bwd(opts->tile_w, opts->tile_h, rec, ranges, sorted, M, L, cam->H, cam->W, Tq, dimage, mom, stream);
+    Params G{mean, scale, quat, rho};
+    k_project_bwd<<<(unsigned)((M + 127) / 128), 128, 0, stream>>>(G, views, camf(cam), opts->Q, M, V, rec, mom,
+                                                                    dmean, dscale, dquat, drho);
+    return check_launch("r2g_rasterize_backward");
+}
+
+R2G_API r2g_status r2g_raster_lists(int64_t M, int32_t V, const r2g_camera* cam, const r2g_raster_opts* opts,
+                                    const void* ws, size_t ws_bytes, uint32_t* ranges_out, uint32_t* ids,
+                                    int64_t capacity, int64_t* n_entries, r2g_stream stream) {
+    r2g_status e = check_args(M, V, cam, opts);
+    if (e) return e;
+    if (!ws || !ranges_out || !ids || !n_entries) return fail(R2G_E_INVAL, "NULL pointer");
+    const RasterLayout L = raster_layout(M, V, cam, opts);
+    const long long cap = capacity_of(L, ws_bytes);
+    const char* base = static_cast<const char*>(ws);
+    WsStatus st;
+    if (cudaMemcpyAsync(&st, base + L.status, sizeof(st), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess)
+        return fail(R2G_E_CUDA, "reading the workspace status failed");
+    *n_entries = (int64_t)st.needed;
+    if (st.status == R2G_E_CAPACITY) return fail(R2G_E_CAPACITY, "lists overflowed the workspace");
+    if ((long long)st.n_keys > capacity) return fail(R2G_E_CAPACITY, "ids buffer too small");
+    const uint64_t* sorted = sorted_buffer(const_cast<char*>(base), L, cap);
+    if (cudaMemcpyAsync(ranges_out, base + L.ranges, 8 * (size_t)L.n_tiles, cudaMemcpyDeviceToDevice, stream) !=
+            cudaSuccess ||
+        (st.n_keys > 0 &&
+         cudaMemcpy2DAsync(ids, 4, sorted, 8, 4, (size_t)st.n_keys, cudaMemcpyDeviceToDevice, stream) !=
+             cudaSuccess) ||
+        cudaStreamSynchronize(stream) != cudaSuccess)
+        return fail(R2G_E_CUDA, "copying the lists failed");
+    return R2G_OK;
+}
+
+R2G_API r2g_status r2g_raster_pair_count(const void* ws, size_t ws_bytes, int64_t* pairs, r2g_stream stream) {
+    if (!ws || !pairs || ws_bytes < sizeof(WsStatus)) return fail(R2G_E_INVAL, "bad workspace or NULL pointer");
+    WsStatus st;
+    if (cudaMemcpyAsync(&st, ws, sizeof(st), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess)
+        return fail(R2G_E_CUDA, "reading the workspace status failed");
+    *pairs = (int64_t)st.pairs;
+    return R2G_OK;
+}
