@@ -18,7 +18,7 @@
  *    caller-owned device workspace whose size the *_workspace_size functions give.
  *  - Every call is asynchronous on `stream` (a cudaStream_t; NULL is the legacy
  *    default stream) and never synchronises the host, except the functions
- *    documented as synchronising (r2g_poll, r2g_*_lists, r2g_raster_pair_count).
+ *    documented as synchronising (r2g_poll, r2g_*_lists, r2g_pair_count).
  *  - Gaussian parameters are float32 structure-of-arrays: mean[M][3],
  *    scale[M][3] (> 0, already activated), quat[M][4] as (w, x, y, z) -- it is
  *    normalised inside and gradients flow through the normalisation -- and
@@ -148,10 +148,11 @@ r2g_status r2g_raster_lists(int64_t M, int32_t V, const r2g_camera* cam, const r
                             const void* ws, size_t ws_bytes, uint32_t* ranges, uint32_t* ids, int64_t capacity,
                             int64_t* n_entries, r2g_stream stream);
 
-/* Count of (pixel, Gaussian) pairs that passed the gate in the last
- * r2g_rasterize on `ws` -- only when that call had opts->count_pairs = 1 (a
- * counting run; off in timed runs).  Synchronises `stream`. */
-r2g_status r2g_raster_pair_count(const void* ws, size_t ws_bytes, int64_t* pairs, r2g_stream stream);
+/* Count of (pixel or voxel, Gaussian) pairs that passed the gate in the last
+ * counting call on `ws`: r2g_rasterize with opts->count_pairs = 1, or
+ * r2g_voxelize_counted.  Bookkeeping for throughput figures; timed runs do not
+ * count.  Synchronises `stream`. */
+r2g_status r2g_pair_count(const void* ws, size_t ws_bytes, int64_t* pairs, r2g_stream stream);
 
 /* ---------------------------------------------------------------- voxelizer
  *
@@ -171,6 +172,12 @@ size_t r2g_voxel_workspace_size(int64_t M, int32_t G, const r2g_grid* grids, int
 r2g_status r2g_voxelize(int64_t M, const float* mean, const float* scale, const float* quat, const float* rho,
                         int32_t G, const r2g_grid* grids, float Q3, float* vol, void* ws, size_t ws_bytes,
                         r2g_stream stream);
+
+/* r2g_voxelize that also counts the gated (voxel, Gaussian) pairs (read them with
+ * r2g_pair_count). */
+r2g_status r2g_voxelize_counted(int64_t M, const float* mean, const float* scale, const float* quat,
+                                const float* rho, int32_t G, const r2g_grid* grids, float Q3, float* vol, void* ws,
+                                size_t ws_bytes, r2g_stream stream);
 
 /* Gradient of sum(dvol * vol), accumulated (+=).  Must follow the matching
  * r2g_voxelize on `ws` (same parameters and grids). */
@@ -201,9 +208,11 @@ r2g_status r2g_projection_loss(int32_t V, int32_t H, int32_t W, const float* ren
 /* lambda_tv x anisotropic 3D total variation (Sec. 4.2.3): for each axis, the mean
  * of |forward difference| over all valid differences, summed over the 3 axes, of
  * each of G volumes vol[G][D][D][D] (device), summed over the G volumes.  Writes
- * *loss (device) and dvol (device, overwritten).  2 <= D <= 1024. */
-r2g_status r2g_tv3d(int32_t G, int32_t D, const float* vol, float lambda_tv, float* loss, float* dvol,
-                    r2g_stream stream);
+ * *loss (device) and dvol (device, overwritten).  2 <= D <= 1024.  The loss is
+ * reduced in a fixed order through a workspace of r2g_tv_workspace_size bytes. */
+size_t r2g_tv_workspace_size(int32_t G, int32_t D);
+r2g_status r2g_tv3d(int32_t G, int32_t D, const float* vol, float lambda_tv, float* loss, float* dvol, void* ws,
+                    size_t ws_bytes, r2g_stream stream);
 
 /* ---------------------------------------------------------------- optimizer
  *
@@ -214,8 +223,9 @@ r2g_status r2g_tv3d(int32_t G, int32_t D, const float* vol, float lambda_tv, flo
  * writes the new activated parameters, and zeroes the gradients for the next
  * iteration.  Learning rate per group: lr0 * final_factor^(it / total_iters);
  * `it` is the 0-based iteration.  raw, act, grad, m, v are device float32 arrays
- * of M*11 entries laid out group after group: mean [M][3], scale [M][3],
- * quat [M][4], rho [M]. */
+ * of M*11 entries laid out group after group: quat [M][4], mean [M][3],
+ * scale [M][3], rho [M] (quat first, so that it keeps the 16-byte alignment the
+ * rasterizer needs). */
 typedef struct {
     float lr0[4];        /* mean, scale, quat, rho: 2e-4, 5e-3, 1e-3, 1e-2 in the paper */
     float final_factor;  /* 0.1 */

@@ -45,6 +45,16 @@ R2G_API r2g_status r2g_poll(const void* ws, size_t ws_bytes, r2g_stream stream, 
     return (r2g_status)st.status;
 }
 
+R2G_API r2g_status r2g_pair_count(const void* ws, size_t ws_bytes, int64_t* pairs, r2g_stream stream) {
+    if (!ws || !pairs || ws_bytes < sizeof(WsStatus)) return fail(R2G_E_INVAL, "bad workspace or NULL pointer");
+    WsStatus st;
+    if (cudaMemcpyAsync(&st, ws, sizeof(st), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess)
+        return fail(R2G_E_CUDA, "reading the workspace status failed");
+    *pairs = (int64_t)st.pairs;
+    return R2G_OK;
+}
+
 R2G_API const char* r2g_last_error(void) { return g_msg; }
 
 R2G_API const char* r2g_version(void) { return "r2g 0.1 (sm_103a)"; }

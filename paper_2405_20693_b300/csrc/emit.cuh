@@ -26,7 +26,7 @@ __global__ void __launch_bounds__(256) k_count_chunks(Op op, long long n_rec, un
 }
 
 // One block of 1024 threads; nb <= 1024.  partials become exclusive offsets.
-__global__ void __launch_bounds__(1024) k_scan_chunks(unsigned long long* partials, int nb, WsStatus* st,
+static __global__ void __launch_bounds__(1024) k_scan_chunks(unsigned long long* partials, int nb, WsStatus* st,
                                                       unsigned long long capacity) {
     __shared__ unsigned long long wsum[32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;

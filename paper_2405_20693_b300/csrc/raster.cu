@@ -89,6 +89,7 @@ __device__ __forceinline__ void rotation(const float q[4], Proj& P) {
 __device__ __forceinline__ void project_stated(const float p[3], const float s[3], const float q[4],
                                                const float* __restrict__ view, const CamF& cam, Proj& P) {
     rotation(q, P);
+    P.phx = P.phy = P.al = P.be = P.ga = P.det = 0.0f;
 #pragma unroll
     for (int j = 0; j < 3; ++j)
 #pragma unroll
@@ -811,12 +812,3 @@ R2G_API r2g_status r2g_raster_lists(int64_t M, int32_t V, const r2g_camera* cam,
     return R2G_OK;
 }
 
-R2G_API r2g_status r2g_raster_pair_count(const void* ws, size_t ws_bytes, int64_t* pairs, r2g_stream stream) {
-    if (!ws || !pairs || ws_bytes < sizeof(WsStatus)) return fail(R2G_E_INVAL, "bad workspace or NULL pointer");
-    WsStatus st;
-    if (cudaMemcpyAsync(&st, ws, sizeof(st), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
-        cudaStreamSynchronize(stream) != cudaSuccess)
-        return fail(R2G_E_CUDA, "reading the workspace status failed");
-    *pairs = (int64_t)st.pairs;
-    return R2G_OK;
-}

@@ -1,0 +1,618 @@
+// voxel.cu -- the differentiable voxelizer of R^2-Gaussian on sm_103a (Eq. 4,
+// Sec. 4.2.2): sigma(x) = sum_i G_i(x) at the voxel centres of one or more grids,
+// through 8^3 bricks, and its adjoint.
+//
+//   k_vox_project  one thread per (grid, Gaussian) record: the stated FP32 brick
+//                  bound and a 64-byte record {c, rho; A..F; rx, ry, rz} in voxel
+//                  units, the quadratic form pre-scaled by -log2(e)/2.
+//   emit / sort    (brick, Gaussian id) entries, stable radix sort, brick ranges.
+//   k_vox_fwd      one CTA (128 threads) per brick; records staged in shared
+//                  memory; each thread owns a run of 4 voxels along x; a warp
+//                  (two z-slices) skips records whose z span misses it.
+//   k_vox_bwd      one CTA per brick with dL/dV of the brick in shared memory;
+//                  one thread per record walks its box inside the brick and
+//                  accumulates ten moments in registers, then three vector atomics.
+//   k_vox_chain    one thread per Gaussian, looping over grids: moments ->
+//                  d rho, d mean, d Sigma^{-1} -> d scale, d quat.
+#include <math.h>
+
+#include "emit.cuh"
+#include "r2g_internal.cuh"
+
+namespace r2g {
+namespace {
+
+constexpr int kMaxGrids = 64;
+constexpr int kB = 8;  // brick edge
+
+struct GridF {
+    float o[3], v[3];
+    int dims[3], nb[3];
+    long long brick_base, vol_base;
+};
+
+struct Grids {
+    GridF g[kMaxGrids];
+    int G;
+    long long n_bricks;
+};
+
+struct Params {
+    const float* mean;
+    const float* scale;
+    const float* quat;
+    const float* rho;
+};
+
+__device__ __forceinline__ float fm(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fa(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fs(float a, float b) { return __fsub_rn(a, b); }
+
+__device__ __forceinline__ void rotation(const float q[4], float R[3][3], float qn[4], float& n) {
+    const float n2 = fa(fa(fa(fm(q[0], q[0]), fm(q[1], q[1])), fm(q[2], q[2])), fm(q[3], q[3]));
+    n = __fsqrt_rn(n2);
+    const float w = __fdiv_rn(q[0], n), x = __fdiv_rn(q[1], n), y = __fdiv_rn(q[2], n), z = __fdiv_rn(q[3], n);
+    qn[0] = w;
+    qn[1] = x;
+    qn[2] = y;
+    qn[3] = z;
+    const float xx = fm(x, x), yy = fm(y, y), zz = fm(z, z), xy = fm(x, y), xz = fm(x, z), yz = fm(y, z);
+    const float wx = fm(w, x), wy = fm(w, y), wz = fm(w, z);
+    R[0][0] = fs(1.0f, fm(2.0f, fa(yy, zz)));
+    R[0][1] = fm(2.0f, fs(xy, wz));
+    R[0][2] = fm(2.0f, fa(xz, wy));
+    R[1][0] = fm(2.0f, fa(xy, wz));
+    R[1][1] = fs(1.0f, fm(2.0f, fa(xx, zz)));
+    R[1][2] = fm(2.0f, fs(yz, wx));
+    R[2][0] = fm(2.0f, fs(xz, wy));
+    R[2][1] = fm(2.0f, fa(yz, wx));
+    R[2][2] = fs(1.0f, fm(2.0f, fa(xx, yy)));
+}
+
+__device__ __forceinline__ float ceil_clamped(float x, int n) {
+    if (!(x > -1.0f)) return -1.0f;
+    if (x > (float)n) return (float)n;
+    return ceilf(x);
+}
+__device__ __forceinline__ float floor_clamped(float x, int n) {
+    if (!(x > -1.0f)) return -1.0f;
+    if (x > (float)n) return (float)n;
+    return floorf(x);
+}
+
+__device__ __forceinline__ void load_gaussian(const Params& G, long long i, float p[3], float s[3], float q[4]) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        p[k] = G.mean[3 * i + k];
+        s[k] = G.scale[3 * i + k];
+    }
+    const float4 qq = reinterpret_cast<const float4*>(G.quat)[i];
+    q[0] = qq.x;
+    q[1] = qq.y;
+    q[2] = qq.z;
+    q[3] = qq.w;
+}
+
+// Sigma^{-1} = R diag(1/s^2) R^T
+__device__ __forceinline__ void precision(const float R[3][3], const float s[3], float P[3][3]) {
+    const float is2[3] = {1.0f / (s[0] * s[0]), 1.0f / (s[1] * s[1]), 1.0f / (s[2] * s[2])};
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) P[j][k] = R[j][0] * R[k][0] * is2[0] + R[j][1] * R[k][1] * is2[1] + R[j][2] * R[k][2] * is2[2];
+}
+
+// ------------------------------------------------------------------ records + brick bound
+
+__global__ void __launch_bounds__(256) k_vox_project(Params G, const __grid_constant__ Grids grids, float Q3,
+                                                     long long M, float4* __restrict__ rec,
+                                                     uint4* __restrict__ rect) {
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= M * grids.G) return;
+    const int g = (int)(r / M);
+    const long long i = r - (long long)g * M;
+    const GridF& gf = grids.g[g];
+    float p[3], s[3], q[4], R[3][3], qn[4], qnorm;
+    load_gaussian(G, i, p, s, q);
+    rotation(q, R, qn, qnorm);
+    float Mm[3][3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) Mm[j][k] = fm(R[j][k], s[k]);
+    int lo[3], hi[3];
+    float c[3], rr[3];
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float skk = fa(fa(fm(Mm[k][0], Mm[k][0]), fm(Mm[k][1], Mm[k][1])), fm(Mm[k][2], Mm[k][2]));
+        const float e = __fsqrt_rn(fm(Q3, skk));
+        c[k] = fs(__fdiv_rn(fs(p[k], gf.o[k]), gf.v[k]), 0.5f);
+        rr[k] = __fdiv_rn(e, gf.v[k]);
+        lo[k] = max(0, (int)ceil_clamped(fs(c[k], rr[k]), gf.dims[k]));
+        hi[k] = min(gf.dims[k] - 1, (int)floor_clamped(fa(c[k], rr[k]), gf.dims[k]));
+        ok = ok && lo[k] <= hi[k];
+    }
+    float P[3][3];
+    precision(R, s, P);
+    const float h = -0.5f * kLog2e;
+    const float vx = gf.v[0], vy = gf.v[1], vz = gf.v[2];
+    float4* o = rec + 4 * r;
+    o[0] = make_float4(c[0], c[1], c[2], G.rho[i]);
+    o[1] = make_float4(h * P[0][0] * vx * vx, h * P[1][1] * vy * vy, h * P[2][2] * vz * vz, 2.f * h * P[0][1] * vx * vy);
+    o[2] = make_float4(2.f * h * P[0][2] * vx * vz, 2.f * h * P[1][2] * vy * vz, 0.f, 0.f);
+    o[3] = make_float4(rr[0], rr[1], rr[2], ok ? 1.f : 0.f);
+    uint4 rc;
+    if (ok) {
+        rc.x = (uint32_t)(lo[0] / kB) | ((uint32_t)(hi[0] / kB) << 16);
+        rc.y = (uint32_t)(lo[1] / kB) | ((uint32_t)(hi[1] / kB) << 16);
+        rc.z = (uint32_t)(lo[2] / kB) | ((uint32_t)(hi[2] / kB) << 16);
+    } else {
+        rc.x = rc.y = rc.z = 0xffffu;
+    }
+    rc.w = 0;
+    rect[r] = rc;
+}
+
+// The emit needs per-grid brick numbering; it gets the table by value.
+struct BrickEmitOp {
+    const uint4* rect;
+    long long M;
+    long long brick_base[kMaxGrids];
+    int nbx[kMaxGrids], nby[kMaxGrids];
+
+    __device__ __forceinline__ uint32_t count(long long r) const {
+        const uint4 rc = rect[r];
+        const int x0 = rc.x & 0xffff, x1 = rc.x >> 16, y0 = rc.y & 0xffff, y1 = rc.y >> 16;
+        const int z0 = rc.z & 0xffff, z1 = rc.z >> 16;
+        return (x1 >= x0 && y1 >= y0 && z1 >= z0) ? (uint32_t)((x1 - x0 + 1) * (y1 - y0 + 1) * (z1 - z0 + 1)) : 0u;
+    }
+    __device__ __forceinline__ void emit(long long r, uint64_t* out, unsigned long long off,
+                                         unsigned long long cap) const {
+        const uint4 rc = rect[r];
+        const int x0 = rc.x & 0xffff, x1 = rc.x >> 16, y0 = rc.y & 0xffff, y1 = rc.y >> 16;
+        const int z0 = rc.z & 0xffff, z1 = rc.z >> 16;
+        const int g = (int)(r / M);
+        const long long i = r - (long long)g * M;
+        const long long bb = brick_base[g];
+        const int nx = nbx[g], ny = nby[g];
+        for (int bz = z0; bz <= z1; ++bz)
+            for (int by = y0; by <= y1; ++by)
+                for (int bx = x0; bx <= x1; ++bx) {
+                    const uint32_t key = (uint32_t)(bb + ((long long)bz * ny + by) * nx + bx);
+                    if (off < cap) out[off] = ((uint64_t)key << 32) | (uint64_t)i;
+                    ++off;
+                }
+    }
+};
+
+__device__ __forceinline__ int grid_of_brick(const Grids& grids, long long brick) {
+    int g = 0;
+    while (g + 1 < grids.G && grids.g[g + 1].brick_base <= brick) ++g;
+    return g;
+}
+
+// ------------------------------------------------------------------ forward
+
+constexpr int kVoxThreads = 128;
+
+template <bool COUNT>
+__global__ void __launch_bounds__(kVoxThreads) k_vox_fwd(const float4* __restrict__ rec,
+                                                         const uint2* __restrict__ ranges,
+                                                         const uint64_t* __restrict__ sorted, long long M,
+                                                         const __grid_constant__ Grids grids, float Tq,
+                                                         float* __restrict__ vol, WsStatus* st) {
+    __shared__ float4 s_r[kVoxThreads][4];
+    const long long brick = blockIdx.x;
+    const int g = grid_of_brick(grids, brick);
+    const GridF& gf = grids.g[g];
+    const long long lb = brick - gf.brick_base;
+    const int bx = (int)(lb % gf.nb[0]);
+    const int by = (int)((lb / gf.nb[0]) % gf.nb[1]);
+    const int bz = (int)(lb / ((long long)gf.nb[0] * gf.nb[1]));
+    const int t = threadIdx.x;
+    const int x0 = bx * kB + (t & 1) * 4, y = by * kB + ((t >> 1) & 7), z = bz * kB + (t >> 4);
+    const int warp = t >> 5;
+    const float zw0 = (float)(bz * kB + 2 * warp), zw1 = zw0 + 1.0f;
+    const float fx0 = (float)x0, fy = (float)y, fz = (float)z;
+    const float4* grec = rec + 4 * (size_t)g * (size_t)M;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    unsigned int cnt = 0;
+    const uint2 rg = ranges[brick];
+    for (uint32_t base = rg.x; base < rg.y; base += kVoxThreads) {
+        const int n = min((uint32_t)kVoxThreads, rg.y - base);
+        __syncthreads();
+        if (t < n) {
+            const uint32_t gid = (uint32_t)sorted[base + t];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) s_r[t][k] = grec[4 * (size_t)gid + k];
+        }
+        __syncthreads();
+        for (int j = 0; j < n; ++j) {
+            const float4 r0 = s_r[j][0];  // cx, cy, cz, rho
+            const float4 r3 = s_r[j][3];  // rx, ry, rz, ok
+            if (r0.z + r3.z < zw0 || r0.z - r3.z > zw1) continue;  // warp-uniform z cull
+            const float4 r1 = s_r[j][1];  // A, B, C, D
+            const float4 r2 = s_r[j][2];  // E, F
+            const float dy = fy - r0.y, dz = fz - r0.z;
+            const float base_q = fmaf(r1.y * dy, dy, fmaf(r1.z * dz, dz, r2.y * dy * dz));
+            const float lin = fmaf(r1.w, dy, r2.x * dz);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float dx = fx0 + (float)k - r0.x;
+                const float tq = fmaf(fmaf(r1.x, dx, lin), dx, base_q);
+                const float e = ex2_approx(tq);
+                acc[k] = (tq >= Tq) ? fmaf(r0.w, e, acc[k]) : acc[k];
+                if (COUNT) cnt += (tq >= Tq && x0 + k < gf.dims[0] && y < gf.dims[1] && z < gf.dims[2]);
+            }
+        }
+    }
+    if (y < gf.dims[1] && z < gf.dims[2]) {
+        float* row = vol + gf.vol_base + ((long long)z * gf.dims[1] + y) * gf.dims[0];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (x0 + k < gf.dims[0]) row[x0 + k] = acc[k];
+    }
+    if (COUNT) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        if ((t & 31) == 0 && cnt) atomicAdd(&st->pairs, (unsigned long long)cnt);
+    }
+}
+
+// ------------------------------------------------------------------ backward
+
+__global__ void __launch_bounds__(kVoxThreads) k_vox_bwd(const float4* __restrict__ rec,
+                                                         const uint2* __restrict__ ranges,
+                                                         const uint64_t* __restrict__ sorted, long long M,
+                                                         const __grid_constant__ Grids grids, float Tq,
+                                                         const float* __restrict__ dvol, float4* __restrict__ mom) {
+    __shared__ float s_g[kB][kB][kB];
+    const long long brick = blockIdx.x;
+    const int g = grid_of_brick(grids, brick);
+    const GridF& gf = grids.g[g];
+    const long long lb = brick - gf.brick_base;
+    const int bx = (int)(lb % gf.nb[0]);
+    const int by = (int)((lb / gf.nb[0]) % gf.nb[1]);
+    const int bz = (int)(lb / ((long long)gf.nb[0] * gf.nb[1]));
+    const int X0 = bx * kB, Y0 = by * kB, Z0 = bz * kB;
+    for (int k = threadIdx.x; k < kB * kB * kB; k += kVoxThreads) {
+        const int lz = k >> 6, ly = (k >> 3) & 7, lx = k & 7;
+        const int x = X0 + lx, y = Y0 + ly, z = Z0 + lz;
+        s_g[lz][ly][lx] = (x < gf.dims[0] && y < gf.dims[1] && z < gf.dims[2])
+                              ? dvol[gf.vol_base + ((long long)z * gf.dims[1] + y) * gf.dims[0] + x]
+                              : 0.0f;
+    }
+    __syncthreads();
+    const uint2 rg = ranges[brick];
+    const float4* grec = rec + 4 * (size_t)g * (size_t)M;
+    float4* gmom = mom + 3 * (size_t)g * (size_t)M;
+    for (uint32_t e = rg.x + threadIdx.x; e < rg.y; e += kVoxThreads) {
+        const uint32_t gid = (uint32_t)sorted[e];
+        const float4 r0 = grec[4 * (size_t)gid], r1 = grec[4 * (size_t)gid + 1];
+        const float4 r2 = grec[4 * (size_t)gid + 2], r3 = grec[4 * (size_t)gid + 3];
+        const int xa = max(X0, (int)ceilf(r0.x - r3.x)), xb = min(X0 + kB - 1, (int)floorf(r0.x + r3.x));
+        const int ya = max(Y0, (int)ceilf(r0.y - r3.y)), yb = min(Y0 + kB - 1, (int)floorf(r0.y + r3.y));
+        const int za = max(Z0, (int)ceilf(r0.z - r3.z)), zb = min(Z0 + kB - 1, (int)floorf(r0.z + r3.z));
+        float S0 = 0.f, Sx = 0.f, Sy = 0.f, Sz = 0.f;
+        float Sxx = 0.f, Syy = 0.f, Szz = 0.f, Sxy = 0.f, Sxz = 0.f, Syz = 0.f;
+        for (int z = za; z <= zb; ++z) {
+            const float dz = (float)z - r0.z;
+            for (int y = ya; y <= yb; ++y) {
+                const float dy = (float)y - r0.y;
+                const float base_q = fmaf(r1.y * dy, dy, fmaf(r1.z * dz, dz, r2.y * dy * dz));
+                const float lin = fmaf(r1.w, dy, r2.x * dz);
+                const float* grow = &s_g[z - Z0][y - Y0][0];
+                for (int x = xa; x <= xb; ++x) {
+                    const float dx = (float)x - r0.x;
+                    const float tq = fmaf(fmaf(r1.x, dx, lin), dx, base_q);
+                    if (tq >= Tq) {
+                        const float w = grow[x - X0] * ex2_approx(tq);
+                        const float wx = w * dx, wy = w * dy;
+                        S0 += w;
+                        Sx += wx;
+                        Sy += wy;
+                        Sz = fmaf(w, dz, Sz);
+                        Sxx = fmaf(wx, dx, Sxx);
+                        Syy = fmaf(wy, dy, Syy);
+                        Szz = fmaf(w * dz, dz, Szz);
+                        Sxy = fmaf(wx, dy, Sxy);
+                        Sxz = fmaf(wx, dz, Sxz);
+                        Syz = fmaf(wy, dz, Syz);
+                    }
+                }
+            }
+        }
+        if (S0 != 0.f || Sx != 0.f || Sy != 0.f || Sz != 0.f || Sxx != 0.f || Syy != 0.f || Szz != 0.f) {
+            atomicAdd(&gmom[3 * (size_t)gid], make_float4(S0, Sx, Sy, Sz));
+            atomicAdd(&gmom[3 * (size_t)gid + 1], make_float4(Sxx, Syy, Szz, Sxy));
+            atomicAdd(reinterpret_cast<float2*>(&gmom[3 * (size_t)gid + 2]), make_float2(Sxz, Syz));
+        }
+    }
+}
+
+__device__ __forceinline__ void quat_grad(const float qn[4], float qnorm, const float g[3][3], float dq[4]) {
+    const float w = qn[0], x = qn[1], y = qn[2], z = qn[3];
+    float dw = 0.f, dx = 0.f, dy = 0.f, dz = 0.f;
+    dy -= 4.f * y * g[0][0]; dz -= 4.f * z * g[0][0];
+    dx += 2.f * y * g[0][1]; dy += 2.f * x * g[0][1]; dw -= 2.f * z * g[0][1]; dz -= 2.f * w * g[0][1];
+    dx += 2.f * z * g[0][2]; dz += 2.f * x * g[0][2]; dw += 2.f * y * g[0][2]; dy += 2.f * w * g[0][2];
+    dx += 2.f * y * g[1][0]; dy += 2.f * x * g[1][0]; dw += 2.f * z * g[1][0]; dz += 2.f * w * g[1][0];
+    dx -= 4.f * x * g[1][1]; dz -= 4.f * z * g[1][1];
+    dy += 2.f * z * g[1][2]; dz += 2.f * y * g[1][2]; dw -= 2.f * x * g[1][2]; dx -= 2.f * w * g[1][2];
+    dx += 2.f * z * g[2][0]; dz += 2.f * x * g[2][0]; dw -= 2.f * y * g[2][0]; dy -= 2.f * w * g[2][0];
+    dy += 2.f * z * g[2][1]; dz += 2.f * y * g[2][1]; dw += 2.f * x * g[2][1]; dx += 2.f * w * g[2][1];
+    dx -= 4.f * x * g[2][2]; dy -= 4.f * y * g[2][2];
+    const float dot = w * dw + x * dx + y * dy + z * dz;
+    dq[0] = (dw - w * dot) / qnorm;
+    dq[1] = (dx - x * dot) / qnorm;
+    dq[2] = (dy - y * dot) / qnorm;
+    dq[3] = (dz - z * dot) / qnorm;
+}
+
+__global__ void __launch_bounds__(128) k_vox_chain(Params G, const __grid_constant__ Grids grids, long long M,
+                                                   const float4* __restrict__ mom, float* __restrict__ dmean,
+                                                   float* __restrict__ dscale, float* __restrict__ dquat,
+                                                   float* __restrict__ drho) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    float p[3], s[3], q[4], R[3][3], qn[4], qnorm;
+    load_gaussian(G, i, p, s, q);
+    rotation(q, R, qn, qnorm);
+    float P[3][3];
+    precision(R, s, P);
+    const float rho = G.rho[i];
+    float gp[3] = {0.f, 0.f, 0.f}, dP[3][3] = {{0.f}}, grho = 0.f;
+    bool any = false;
+    for (int g = 0; g < grids.G; ++g) {
+        const size_t r = (size_t)g * (size_t)M + (size_t)i;
+        const float4 m0 = mom[3 * r], m1 = mom[3 * r + 1], m2 = mom[3 * r + 2];
+        if (m0.x == 0.f && m0.y == 0.f && m0.z == 0.f && m0.w == 0.f && m1.x == 0.f && m1.y == 0.f && m1.z == 0.f &&
+            m1.w == 0.f && m2.x == 0.f && m2.y == 0.f)
+            continue;
+        any = true;
+        const GridF& gf = grids.g[g];
+        const float v[3] = {gf.v[0], gf.v[1], gf.v[2]};
+        const float S1[3] = {m0.y, m0.z, m0.w};
+        const float S2[3][3] = {{m1.x, m1.w, m2.x}, {m1.w, m1.y, m2.y}, {m2.x, m2.y, m1.z}};
+        grho += m0.x;
+        // d c = rho P_vox S1, c_k = (p_k - o_k)/v_k - 1/2, P_vox_jk = P_jk v_j v_k
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            float dc = 0.f;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) dc += P[j][k] * v[j] * v[k] * S1[k];
+            gp[j] += rho * dc / v[j];
+        }
+        // d P_jk = -1/2 rho S2_jk v_j v_k
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) dP[j][k] += -0.5f * rho * S2[j][k] * v[j] * v[k];
+    }
+    if (!any) return;
+    // P = N N^T, N = R diag(1/s): dN = (dP + dP^T) N
+    float gR[3][3], gs[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            float dN = 0.f;
+#pragma unroll
+            for (int m = 0; m < 3; ++m) dN += (dP[j][m] + dP[m][j]) * R[m][k] / s[k];
+            gR[j][k] = dN / s[k];
+            gs[k] += -dN * R[j][k] / (s[k] * s[k]);
+        }
+    float gq[4];
+    quat_grad(qn, qnorm, gR, gq);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        dmean[3 * i + k] += gp[k];
+        dscale[3 * i + k] += gs[k];
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) dquat[4 * i + k] += gq[k];
+    drho[i] += grho;
+}
+
+// ------------------------------------------------------------------ host side
+
+struct VoxLayout {
+    size_t status, rec, rect, partials, ranges, mom, scratch, fixed;
+    long long n_rec, n_bricks, n_vox;
+};
+
+r2g_status make_grids(int32_t G, const r2g_grid* grids, Grids& out) {
+    if (G < 1 || G > kMaxGrids) return fail(R2G_E_INVAL, "G = %d out of range [1, %d]", G, kMaxGrids);
+    if (!grids) return fail(R2G_E_INVAL, "grids must not be NULL");
+    out.G = G;
+    long long bb = 0, vb = 0;
+    for (int g = 0; g < G; ++g) {
+        GridF& f = out.g[g];
+        for (int k = 0; k < 3; ++k) {
+            if (grids[g].dims[k] < 1 || grids[g].dims[k] > 4096)
+                return fail(R2G_E_INVAL, "grid %d dims[%d] = %d out of range", g, k, grids[g].dims[k]);
+            if (!(grids[g].voxel[k] > 0.f)) return fail(R2G_E_INVAL, "grid %d voxel size must be > 0", g);
+            f.o[k] = grids[g].origin[k];
+            f.v[k] = grids[g].voxel[k];
+            f.dims[k] = grids[g].dims[k];
+            f.nb[k] = (f.dims[k] + kB - 1) / kB;
+        }
+        f.brick_base = bb;
+        f.vol_base = vb;
+        bb += (long long)f.nb[0] * f.nb[1] * f.nb[2];
+        vb += (long long)f.dims[0] * f.dims[1] * f.dims[2];
+    }
+    if (bb >= (1ll << 31)) return fail(R2G_E_INVAL, "too many bricks");
+    out.n_bricks = bb;
+    for (int g = G; g < kMaxGrids; ++g) out.g[g] = out.g[G - 1];
+    return R2G_OK;
+}
+
+VoxLayout vox_layout(int64_t M, const Grids& grids) {
+    VoxLayout L;
+    L.n_rec = (long long)M * grids.G;
+    L.n_bricks = grids.n_bricks;
+    Layout lay;
+    L.status = lay.take(sizeof(WsStatus));
+    L.rec = lay.take(64 * (size_t)L.n_rec);
+    L.rect = lay.take(16 * (size_t)L.n_rec);
+    L.partials = lay.take(8 * (size_t)kScanBlocks);
+    L.ranges = lay.take(8 * (size_t)L.n_bricks);
+    L.mom = lay.take(48 * (size_t)L.n_rec);
+    L.scratch = lay.take(sort_scratch_bytes());
+    L.fixed = lay.off;
+    return L;
+}
+
+long long vox_capacity(const VoxLayout& L, size_t ws_bytes) {
+    if (ws_bytes <= L.fixed) return 0;
+    long long cap = (long long)(((ws_bytes - L.fixed) / 2) / 256) * 32;
+    if (cap > 0xffffffe0ll) cap = 0xffffffe0ll;
+    return cap;
+}
+
+uint64_t* vox_sorted(char* base, const VoxLayout& L, long long cap) {
+    uint64_t* a = reinterpret_cast<uint64_t*>(base + L.fixed);
+    uint64_t* b = reinterpret_cast<uint64_t*>(base + L.fixed + align_up(8 * (size_t)cap));
+    const int passes = (bits_for(L.n_bricks) + kRadixBits - 1) / kRadixBits;
+    return (passes & 1) ? b : a;
+}
+
+r2g_status check_params(int64_t M, const float* mean, const float* scale, const float* quat, const float* rho) {
+    if (M < 1 || M >= (int64_t(1) << 31)) return fail(R2G_E_INVAL, "M = %lld out of range", (long long)M);
+    if (!mean || !scale || !quat || !rho) return fail(R2G_E_INVAL, "NULL parameter pointer");
+    if (reinterpret_cast<uintptr_t>(quat) % 16) return fail(R2G_E_INVAL, "quat must be 16-byte aligned");
+    return R2G_OK;
+}
+
+}  // namespace
+}  // namespace r2g
+
+using namespace r2g;
+
+R2G_API size_t r2g_voxel_workspace_size(int64_t M, int32_t G, const r2g_grid* grids, int64_t key_capacity) {
+    Grids gr;
+    if (M < 1 || M >= (int64_t(1) << 31) || make_grids(G, grids, gr) != R2G_OK) return 0;
+    if ((long long)M * G >= (1ll << 31)) return 0;
+    if (key_capacity < 1 || key_capacity > 0xffffffe0ll) return 0;
+    const VoxLayout L = vox_layout(M, gr);
+    return L.fixed + 2 * align_up(8 * (size_t)key_capacity);
+}
+
+namespace r2g {
+namespace {
+r2g_status voxelize_impl(int64_t M, const float* mean, const float* scale, const float* quat, const float* rho,
+                         int32_t G, const r2g_grid* grids, float Q3, float* vol, void* ws, size_t ws_bytes,
+                         cudaStream_t stream, bool count) {
+    r2g_status e = check_params(M, mean, scale, quat, rho);
+    if (e) return e;
+    Grids gr;
+    if ((e = make_grids(G, grids, gr))) return e;
+    if ((long long)M * G >= (1ll << 31)) return fail(R2G_E_INVAL, "M * G must be < 2^31");
+    if (!(Q3 > 0.f)) return fail(R2G_E_INVAL, "Q3 must be > 0");
+    if (!vol || !ws) return fail(R2G_E_INVAL, "NULL pointer");
+    if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(R2G_E_INVAL, "workspace must be 256-byte aligned");
+    const VoxLayout L = vox_layout(M, gr);
+    const long long cap = vox_capacity(L, ws_bytes);
+    if (cap < 32) return fail(R2G_E_INVAL, "workspace of %zu bytes holds no list entries", ws_bytes);
+    char* base = static_cast<char*>(ws);
+    WsStatus* st = reinterpret_cast<WsStatus*>(base + L.status);
+    float4* rec = reinterpret_cast<float4*>(base + L.rec);
+    uint4* rect = reinterpret_cast<uint4*>(base + L.rect);
+    auto* partials = reinterpret_cast<unsigned long long*>(base + L.partials);
+    uint2* ranges = reinterpret_cast<uint2*>(base + L.ranges);
+    uint32_t* scratch = reinterpret_cast<uint32_t*>(base + L.scratch);
+    uint64_t* a = reinterpret_cast<uint64_t*>(base + L.fixed);
+    uint64_t* b = reinterpret_cast<uint64_t*>(base + L.fixed + align_up(8 * (size_t)cap));
+    cudaMemsetAsync(st, 0, sizeof(WsStatus), stream);
+    Params P{mean, scale, quat, rho};
+    k_vox_project<<<(unsigned)((L.n_rec + 255) / 256), 256, 0, stream>>>(P, gr, Q3, M, rec, rect);
+    BrickEmitOp op;
+    op.rect = rect;
+    op.M = M;
+    for (int g = 0; g < kMaxGrids; ++g) {
+        op.brick_base[g] = gr.g[g].brick_base;
+        op.nbx[g] = gr.g[g].nb[0];
+        op.nby[g] = gr.g[g].nb[1];
+    }
+    emit_lists(op, L.n_rec, partials, st, a, (unsigned long long)cap, stream);
+    uint64_t* sorted = radix_sort_u64(a, b, scratch, st, bits_for(L.n_bricks), stream);
+    build_ranges(sorted, st, ranges, L.n_bricks, stream);
+    const float Tq = -0.5f * kLog2e * Q3;
+    if (count)
+        k_vox_fwd<true><<<(unsigned)L.n_bricks, kVoxThreads, 0, stream>>>(rec, ranges, sorted, M, gr, Tq, vol, st);
+    else
+        k_vox_fwd<false><<<(unsigned)L.n_bricks, kVoxThreads, 0, stream>>>(rec, ranges, sorted, M, gr, Tq, vol, st);
+    return check_launch("r2g_voxelize");
+}
+}  // namespace
+}  // namespace r2g
+
+R2G_API r2g_status r2g_voxelize(int64_t M, const float* mean, const float* scale, const float* quat,
+                                const float* rho, int32_t G, const r2g_grid* grids, float Q3, float* vol, void* ws,
+                                size_t ws_bytes, r2g_stream stream) {
+    return voxelize_impl(M, mean, scale, quat, rho, G, grids, Q3, vol, ws, ws_bytes, stream, false);
+}
+
+R2G_API r2g_status r2g_voxelize_counted(int64_t M, const float* mean, const float* scale, const float* quat,
+                                        const float* rho, int32_t G, const r2g_grid* grids, float Q3, float* vol,
+                                        void* ws, size_t ws_bytes, r2g_stream stream) {
+    return voxelize_impl(M, mean, scale, quat, rho, G, grids, Q3, vol, ws, ws_bytes, stream, true);
+}
+
+
+R2G_API r2g_status r2g_voxelize_backward(int64_t M, const float* mean, const float* scale, const float* quat,
+                                         const float* rho, int32_t G, const r2g_grid* grids, float Q3,
+                                         const float* dvol, float* dmean, float* dscale, float* dquat, float* drho,
+                                         void* ws, size_t ws_bytes, r2g_stream stream) {
+    r2g_status e = check_params(M, mean, scale, quat, rho);
+    if (e) return e;
+    Grids gr;
+    if ((e = make_grids(G, grids, gr))) return e;
+    if ((long long)M * G >= (1ll << 31)) return fail(R2G_E_INVAL, "M * G must be < 2^31");
+    if (!dvol || !dmean || !dscale || !dquat || !drho || !ws) return fail(R2G_E_INVAL, "NULL pointer");
+    if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(R2G_E_INVAL, "workspace must be 256-byte aligned");
+    const VoxLayout L = vox_layout(M, gr);
+    const long long cap = vox_capacity(L, ws_bytes);
+    if (cap < 32) return fail(R2G_E_INVAL, "workspace of %zu bytes holds no list entries", ws_bytes);
+    char* base = static_cast<char*>(ws);
+    const float4* rec = reinterpret_cast<const float4*>(base + L.rec);
+    const uint2* ranges = reinterpret_cast<const uint2*>(base + L.ranges);
+    float4* mom = reinterpret_cast<float4*>(base + L.mom);
+    const uint64_t* sorted = vox_sorted(base, L, cap);
+    cudaMemsetAsync(mom, 0, 48 * (size_t)L.n_rec, stream);
+    const float Tq = -0.5f * kLog2e * Q3;
+    k_vox_bwd<<<(unsigned)L.n_bricks, kVoxThreads, 0, stream>>>(rec, ranges, sorted, M, gr, Tq, dvol, mom);
+    Params P{mean, scale, quat, rho};
+    k_vox_chain<<<(unsigned)((M + 127) / 128), 128, 0, stream>>>(P, gr, M, mom, dmean, dscale, dquat, drho);
+    return check_launch("r2g_voxelize_backward");
+}
+
+R2G_API r2g_status r2g_voxel_lists(int64_t M, int32_t G, const r2g_grid* grids, const void* ws, size_t ws_bytes,
+                                   uint32_t* ranges_out, uint32_t* ids, int64_t capacity, int64_t* n_entries,
+                                   r2g_stream stream) {
+    Grids gr;
+    r2g_status e = make_grids(G, grids, gr);
+    if (e) return e;
+    if (M < 1 || !ws || !ranges_out || !ids || !n_entries) return fail(R2G_E_INVAL, "bad argument");
+    const VoxLayout L = vox_layout(M, gr);
+    const long long cap = vox_capacity(L, ws_bytes);
+    const char* base = static_cast<const char*>(ws);
+    WsStatus st;
+    if (cudaMemcpyAsync(&st, base + L.status, sizeof(st), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess)
+        return fail(R2G_E_CUDA, "reading the workspace status failed");
+    *n_entries = (int64_t)st.needed;
+    if (st.status == R2G_E_CAPACITY) return fail(R2G_E_CAPACITY, "lists overflowed the workspace");
+    if ((long long)st.n_keys > capacity) return fail(R2G_E_CAPACITY, "ids buffer too small");
+    const uint64_t* sorted = vox_sorted(const_cast<char*>(base), L, cap);
+    if (cudaMemcpyAsync(ranges_out, base + L.ranges, 8 * (size_t)L.n_bricks, cudaMemcpyDeviceToDevice, stream) !=
+            cudaSuccess ||
+        (st.n_keys > 0 &&
+         cudaMemcpy2DAsync(ids, 4, sorted, 8, 4, (size_t)st.n_keys, cudaMemcpyDeviceToDevice, stream) !=
+             cudaSuccess) ||
+        cudaStreamSynchronize(stream) != cudaSuccess)
+        return fail(R2G_E_CUDA, "copying the lists failed");
+    return R2G_OK;
+}

@@ -1,0 +1,233 @@
+"""Workspaces, autograd bridge and the training step built on the C ABI.
+
+Everything numeric runs in libr2g.so; this module sizes and owns the device
+workspaces (torch uint8 tensors), grows a workspace when the device reports
+that the per-tile / per-brick lists did not fit, and chains the calls of one
+training iteration (Eq. 8): rasterize -> L1 + D-SSIM -> voxelize a TV patch ->
+TV -> both backward passes -> fused Adam.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import r2g
+
+Q_PIXEL = 9.0        # 3-sigma pixel gate
+Q_VOXEL = 11.345     # chi^2_3 0.99 quantile: the paper's "99% confidence" brick culling
+LAMBDA_SSIM = 0.25   # Sec. 5.1
+LAMBDA_TV = 0.05     # Sec. 5.1
+
+
+def _bytes(n: int, device) -> torch.Tensor:
+    return torch.empty(int(n), dtype=torch.uint8, device=device)
+
+
+class Rasterizer:
+    """Owns the workspace of one (M, V, camera, tile) configuration."""
+
+    def __init__(self, M: int, V: int, cam, Q=Q_PIXEL, tile=(16, 16), device="cuda", capacity=None):
+        self.M, self.V = int(M), int(V)
+        self.cam = r2g.camera(cam)
+        self.opts = r2g.raster_opts(Q, tile)
+        self.copts = r2g.raster_opts(Q, tile, count_pairs=True)
+        self.device = device
+        self.capacity = int(capacity or max(1 << 16, 4 * self.M * self.V))
+        self.ws = None
+        self._alloc()
+
+    def _alloc(self):
+        n = r2g.r2g_raster_workspace_size(self.M, self.V, self.cam, self.opts, self.capacity)
+        self.ws = _bytes(n, self.device)
+
+    def forward(self, mean, scale, quat, rho, views, image=None, check=True, count=False):
+        """Image [V, H, W].  check=True polls the device status (one sync) and re-runs
+        with a larger workspace if the lists overflowed."""
+        if image is None:
+            image = torch.empty((self.V, self.cam.H, self.cam.W), dtype=torch.float32, device=self.device)
+        while True:
+            r2g.r2g_rasterize(mean, scale, quat, rho, views, self.cam, self.copts if count else self.opts, image,
+                              self.ws)
+            if not check:
+                return image
+            st, needed = r2g.r2g_poll(self.ws)
+            if st == r2g.R2G_OK:
+                return image
+            self.capacity = int(needed * 1.25) + 1024
+            self._alloc()
+
+    def backward(self, mean, scale, quat, rho, views, dimage, dmean, dscale, dquat, drho):
+        r2g.r2g_rasterize_backward(mean, scale, quat, rho, views, self.cam, self.opts, dimage.contiguous(), dmean,
+                                   dscale, dquat, drho, self.ws)
+
+    def pair_count(self) -> int:
+        return r2g.r2g_pair_count(self.ws)
+
+
+class Voxelizer:
+    """Owns the workspace of one (M, grids) configuration."""
+
+    def __init__(self, M: int, gdescs, Q3=Q_VOXEL, device="cuda", capacity=None):
+        self.M = int(M)
+        self.gd = np.atleast_2d(np.asarray(gdescs, dtype=np.float64))
+        self.grids = r2g.grids(self.gd)
+        self.Q3 = float(Q3)
+        self.device = device
+        self.n_vox = int(sum(int(d[6] * d[7] * d[8]) for d in self.gd))
+        self.capacity = int(capacity or max(1 << 16, 2 * self.M * len(self.gd)))
+        self._alloc()
+
+    def _alloc(self):
+        n = r2g.r2g_voxel_workspace_size(self.M, self.grids, self.capacity)
+        self.ws = _bytes(n, self.device)
+
+    def set_grids(self, gdescs):
+        """Same grid count and sizes, new origins (e.g. a new TV patch position)."""
+        gd = np.atleast_2d(np.asarray(gdescs, dtype=np.float64))
+        assert gd.shape == self.gd.shape and np.all(gd[:, 6:] == self.gd[:, 6:])
+        self.gd = gd
+        self.grids = r2g.grids(gd)
+
+    def forward(self, mean, scale, quat, rho, vol=None, check=True, count=False):
+        if vol is None:
+            vol = torch.empty(self.n_vox, dtype=torch.float32, device=self.device)
+        while True:
+            r2g.r2g_voxelize(mean, scale, quat, rho, self.grids, self.Q3, vol, self.ws, counted=count)
+            if not check:
+                return vol
+            st, needed = r2g.r2g_poll(self.ws)
+            if st == r2g.R2G_OK:
+                return vol
+            self.capacity = int(needed * 1.25) + 1024
+            self._alloc()
+
+    def backward(self, mean, scale, quat, rho, dvol, dmean, dscale, dquat, drho):
+        r2g.r2g_voxelize_backward(mean, scale, quat, rho, self.grids, self.Q3, dvol.contiguous(), dmean, dscale,
+                                  dquat, drho, self.ws)
+
+    def pair_count(self) -> int:
+        return r2g.r2g_pair_count(self.ws)
+
+
+# ----------------------------------------------------------------------------- autograd bridge
+
+
+class _RasterizeFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, mean, scale, quat, rho, views, rast):
+        ctx.rast = rast
+        ctx.save_for_backward(mean, scale, quat, rho, views)
+        return rast.forward(mean.detach(), scale.detach(), quat.detach(), rho.detach(), views)
+
+    @staticmethod
+    def backward(ctx, dimage):
+        mean, scale, quat, rho, views = ctx.saved_tensors
+        g = [torch.zeros_like(t) for t in (mean, scale, quat, rho)]
+        ctx.rast.backward(mean, scale, quat, rho, views, dimage.float(), *g)
+        return (*g, None, None)
+
+
+class _VoxelizeFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, mean, scale, quat, rho, vox):
+        ctx.vox = vox
+        ctx.save_for_backward(mean, scale, quat, rho)
+        return vox.forward(mean.detach(), scale.detach(), quat.detach(), rho.detach())
+
+    @staticmethod
+    def backward(ctx, dvol):
+        mean, scale, quat, rho = ctx.saved_tensors
+        g = [torch.zeros_like(t) for t in (mean, scale, quat, rho)]
+        ctx.vox.backward(mean, scale, quat, rho, dvol.float(), *g)
+        return (*g, None)
+
+
+def rasterize(mean, scale, quat, rho, views, rast: Rasterizer):
+    """Differentiable X-ray projection (Eq. 5, Eq. 7): [V, H, W]."""
+    return _RasterizeFn.apply(mean, scale, quat, rho, views, rast)
+
+
+def voxelize(mean, scale, quat, rho, vox: Voxelizer):
+    """Differentiable density query (Eq. 4): concatenated grid volumes."""
+    return _VoxelizeFn.apply(mean, scale, quat, rho, vox)
+
+
+# ----------------------------------------------------------------------------- training state
+
+
+def inv_softplus(y: np.ndarray) -> np.ndarray:
+    return y + np.log(-np.expm1(-y))
+
+
+class TrainState:
+    """Gaussian parameters, gradients and Adam moments, resident on the device in the
+    C ABI's flat layout [quat 4M | mean 3M | scale 3M | rho M]."""
+
+    def __init__(self, G, device="cuda"):
+        M = G.M
+        self.M = M
+        raw = np.concatenate([np.asarray(G.quat, np.float64).ravel(), np.asarray(G.mean, np.float64).ravel(),
+                              np.log(np.asarray(G.scale, np.float64)).ravel(),
+                              inv_softplus(np.maximum(np.asarray(G.rho, np.float64), 1e-6)).ravel()])
+        self.raw = torch.tensor(raw, dtype=torch.float32, device=device)
+        act = np.concatenate([np.asarray(G.quat, np.float64).ravel(), np.asarray(G.mean, np.float64).ravel(),
+                              np.asarray(G.scale, np.float64).ravel(),
+                              np.maximum(np.asarray(G.rho, np.float64), 1e-6).ravel()])
+        self.act = torch.tensor(act, dtype=torch.float32, device=device)
+        self.grad = torch.zeros_like(self.act)
+        self.m = torch.zeros_like(self.act)
+        self.v = torch.zeros_like(self.act)
+
+    def views_of(self, t):
+        M = self.M
+        return t[0:4 * M].view(M, 4), t[4 * M:7 * M].view(M, 3), t[7 * M:10 * M].view(M, 3), t[10 * M:11 * M]
+
+    def params(self):
+        """(mean, scale, quat, rho) views of the activated parameters."""
+        q, m, s, r = self.views_of(self.act)
+        return m, s, q, r
+
+    def grads(self):
+        q, m, s, r = self.views_of(self.grad)
+        return m, s, q, r
+
+
+class TrainStep:
+    """One iteration of Eq. 8 on one projection view and one D^3 TV patch."""
+
+    def __init__(self, state: TrainState, views: torch.Tensor, meas: torch.Tensor, cam, D=32, n_out=256,
+                 tile=(16, 16), total_iters=30000, device="cuda"):
+        self.s = state
+        self.views = views            # [V, 12] device
+        self.meas = meas              # [V, H, W] device
+        self.cam = cam
+        self.D = D
+        self.n_out = n_out
+        self.rast = Rasterizer(state.M, 1, cam, tile=tile, device=device)
+        from .inputs import patch_grid
+        self._patch = patch_grid
+        self.vox = Voxelizer(state.M, patch_grid((0, 0, 0), D, n_out), device=device)
+        self.image = torch.empty((1, cam.H, cam.W), dtype=torch.float32, device=device)
+        self.dimage = torch.empty_like(self.image)
+        self.vol = torch.empty(D ** 3, dtype=torch.float32, device=device)
+        self.dvol = torch.empty_like(self.vol)
+        self.loss = torch.zeros(2, dtype=torch.float32, device=device)
+        self.loss_ws = _bytes(r2g.r2g_loss_workspace_size(1, cam.H, cam.W), device)
+        self.tv_ws = _bytes(r2g.r2g_tv_workspace_size(1, D), device)
+        self.adam = r2g.adam_opts(total_iters=total_iters)
+
+    def run(self, it: int, view: int, offset, check=False):
+        """One full iteration; returns nothing (loss stays on the device in self.loss)."""
+        mean, scale, quat, rho = self.s.params()
+        dmean, dscale, dquat, drho = self.s.grads()
+        v = self.views[view:view + 1]
+        self.rast.forward(mean, scale, quat, rho, v, self.image, check=check)
+        r2g.r2g_projection_loss(self.image, self.meas[view:view + 1], LAMBDA_SSIM, self.loss[0:1], self.dimage,
+                                self.loss_ws)
+        self.vox.set_grids(self._patch(offset, self.D, self.n_out))
+        self.vox.forward(mean, scale, quat, rho, self.vol, check=check)
+        r2g.r2g_tv3d(self.vol.view(1, self.D, self.D, self.D), LAMBDA_TV, self.loss[1:2],
+                     self.dvol.view(1, self.D, self.D, self.D), self.tv_ws)
+        self.rast.backward(mean, scale, quat, rho, v, self.dimage, dmean, dscale, dquat, drho)
+        self.vox.backward(mean, scale, quat, rho, self.dvol, dmean, dscale, dquat, drho)
+        r2g.r2g_adam_step(self.s.raw, self.s.act, self.s.grad, self.s.m, self.s.v, it, self.adam)

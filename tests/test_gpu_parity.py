@@ -1,0 +1,282 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from gpu_util import (assert_grads_close, assert_values_close, config1, cone_small, dev, dev_set, host)
+from oracle import core, losses
+from paper_2405_20693_b300 import build, engine, r2g
+from paper_2405_20693_b300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+Q9 = engine.Q_PIXEL
+Q3 = engine.Q_VOXEL
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    r2g.lib()
+    torch.cuda.init()
+
+
+def _project(G, views, cam, tile=(16, 16)):
+    mean, scale, quat, rho = dev_set(G)
+    M, V = G.M, views.shape[0]
+    proj = torch.empty((V, M, 8), dtype=torch.float32, device="cuda")
+    rect = torch.empty((V, M, 4), dtype=torch.int32, device="cuda")
+    r2g.r2g_project(mean, scale, quat, rho, dev(views), r2g.camera(cam), r2g.raster_opts(Q9, tile), proj, rect)
+    torch.cuda.synchronize()
+    return proj.cpu().numpy(), rect.cpu().numpy()
+
+
+@pytest.mark.parametrize("case", ["parallel", "cone"])
+def test_projection_bit_exact_with_stated_fp32_sequence(case):
+    G, cam, views = config1() if case == "parallel" else cone_small()
+    proj, rect = _project(G, views, cam)
+    of, oi = core.project_f32(G, views, cam, Q9, (16, 16))
+    valid = oi[..., 0] == 1
+    assert np.array_equal(proj[..., 7] == 1.0, valid)
+    # p^, Sigma^ and |Sigma^| are bit-identical where the record is kept
+    for k in range(6):
+        assert np.array_equal(proj[..., k][valid].view(np.uint32), of[..., k][valid].view(np.uint32)), k
+    assert np.array_equal(rect[valid], oi[..., 1:5][valid])
+    # rho_hat against the FP64 oracle's mu * rho (Eq. 7)
+    pr = core.project(G, views, cam)
+    rel = np.abs(proj[..., 6][valid] - pr[..., 9][valid]) / np.abs(pr[..., 9][valid]).max()
+    assert rel.max() < 1e-5
+
+
+def _lists_gpu(rast, M, V):
+    n_tiles = V * ((rast.cam.H + rast.opts.tile_h - 1) // rast.opts.tile_h) * \
+        ((rast.cam.W + rast.opts.tile_w - 1) // rast.opts.tile_w)
+    ranges = torch.empty((n_tiles, 2), dtype=torch.int32, device="cuda")
+    ids = torch.empty(rast.capacity, dtype=torch.int32, device="cuda")
+    n = r2g.r2g_raster_lists(M, V, rast.cam, rast.opts, rast.ws, ranges, ids)
+    return ranges.cpu().numpy().view(np.uint32), ids[:n].cpu().numpy().view(np.uint32), n
+
+
+@pytest.mark.parametrize("case,tile", [("parallel", (16, 16)), ("cone", (16, 16)), ("cone", (8, 8)),
+                                       ("parallel", (32, 8))])
+def test_tile_lists_bit_exact(case, tile):
+    G, cam, views = config1() if case == "parallel" else cone_small()
+    rast = engine.Rasterizer(G.M, views.shape[0], cam, tile=tile, capacity=1024)  # forces a regrow
+    rast.forward(*dev_set(G), dev(views))
+    ranges, ids, n = _lists_gpu(rast, G.M, views.shape[0])
+    ref = core.tile_lists_f32(G, views, cam, Q9, tile)
+    assert n == sum(len(v) for v in ref.values())
+    for t in range(ranges.shape[0]):
+        a, b = ranges[t]
+        got = ids[a:b].astype(np.int64)
+        exp = ref.get(t, np.zeros(0, np.int64))
+        assert np.array_equal(got, exp), t  # same ids, ascending (stable sort)
+
+
+@pytest.mark.parametrize("case", ["config1", "cone"])
+def test_rasterize_matches_oracle(case):
+    G, cam, views = config1() if case == "config1" else cone_small()
+    rast = engine.Rasterizer(G.M, views.shape[0], cam)
+    img = rast.forward(*dev_set(G), dev(views), count=True)
+    torch.cuda.synchronize()
+    ref, pairs, band = core.render(G, views, cam, Q=Q9, want_band=True)
+    assert_values_close(host(img), ref, band, case)
+    # gated pair count agrees up to gate-band flips
+    got = rast.pair_count()
+    assert abs(got - pairs) <= max(10, 1e-4 * pairs), (got, pairs)
+
+
+def test_tile_shape_does_not_change_the_image():
+    G, cam, views = cone_small()
+    imgs = []
+    for tile in ((16, 16), (8, 8), (32, 8)):
+        rast = engine.Rasterizer(G.M, views.shape[0], cam, tile=tile)
+        imgs.append(host(rast.forward(*dev_set(G), dev(views))))
+    for k in (1, 2):
+        assert np.abs(imgs[k] - imgs[0]).max() <= 1e-6 * np.abs(imgs[0]).max()
+
+
+def test_rasterize_ragged_detector_and_empty_cases():
+    """Detector not a multiple of the tile, Gaussians off the detector, behind the
+    near plane, and one tiny Gaussian (degenerate sizes)."""
+    g = I.rng(31)
+    M = 400
+    mean = g.uniform(-0.9, 0.9, (M, 3))
+    mean[:20] = [50.0, 0.0, 0.0]           # far outside: dropped by the bound
+    mean[20:25] = [7.9, 0.0, 0.0]           # at/behind the source for view 0: near plane
+    scale = np.exp(g.uniform(math.log(0.003), math.log(0.1), (M, 3)))
+    scale[30] = [1e-4, 1e-4, 1e-4]
+    quat = I.random_quats(g, M)
+    rho = g.uniform(-0.5, 1.0, M)           # any sign
+    G = I.GaussianSet(mean, scale, quat, rho).astype(np.float32)
+    cam = I.cone_camera(37, 53, pitch=I.CONE_PITCH * 10)
+    views = I.view_table(np.deg2rad([0.0, 100.0]), I.CONE_L_SO)
+    rast = engine.Rasterizer(M, 2, cam)
+    img = rast.forward(*dev_set(G), dev(views))
+    ref, _, band = core.render(G, views, cam, Q=Q9, want_band=True)
+    assert_values_close(host(img), ref, band, "ragged")
+    # a set whose every Gaussian misses the detector renders zeros
+    Gz = I.GaussianSet(np.full((5, 3), 40.0, np.float32), scale[:5].astype(np.float32), quat[:5].astype(np.float32),
+                       rho[:5].astype(np.float32))
+    rz = engine.Rasterizer(5, 2, cam)
+    assert float(rz.forward(*dev_set(Gz), dev(views)).abs().max()) == 0.0
+
+
+@pytest.mark.parametrize("case", ["config1", "cone"])
+def test_rasterize_backward_matches_oracle_adjoint(case):
+    G, cam, views = config1() if case == "config1" else cone_small(M=1500)
+    V = views.shape[0]
+    dimg = I.rng(5).standard_normal((V, cam.H, cam.W)).astype(np.float32)
+    rast = engine.Rasterizer(G.M, V, cam)
+    mean, scale, quat, rho = dev_set(G)
+    vv = dev(views)
+    rast.forward(mean, scale, quat, rho, vv)
+    g = [torch.zeros_like(t) for t in (mean, scale, quat, rho)]
+    rast.backward(mean, scale, quat, rho, vv, dev(dimg), *g)
+    torch.cuda.synchronize()
+    ref = core.render_backward(G, views, cam, dimg, Q=Q9)
+    for name, a, b in zip(("mean", "scale", "quat", "rho"), g, ref):
+        assert_grads_close(host(a), b, f"{case} d{name}")
+
+
+def test_config1_l1_gradient_against_oracle_targets():
+    """Config 1 end to end: targets are the oracle's render of a second (seed 1) set;
+    L1 loss gradients flow through the CUDA rasterizer backward."""
+    G, cam, views = config1()
+    target, _ = core.render(I.uniform_gaussians(2000, 1), views, cam, Q=Q9)
+    rast = engine.Rasterizer(G.M, 4, cam)
+    mean, scale, quat, rho = dev_set(G)
+    vv = dev(views)
+    img = rast.forward(mean, scale, quat, rho, vv)
+    ref_img, _ = core.render(G, views, cam, Q=Q9)
+    # sign decided on the oracle's image (FP64) so both sides use the same dL/dI
+    dimg = (np.sign(ref_img - target) / ref_img.size).astype(np.float32)
+    g = [torch.zeros_like(t) for t in (mean, scale, quat, rho)]
+    rast.backward(mean, scale, quat, rho, vv, dev(dimg), *g)
+    ref = core.render_backward(G, views, cam, dimg, Q=Q9)
+    for name, a, b in zip(("mean", "scale", "quat", "rho"), g, ref):
+        assert_grads_close(host(a), b, f"L1 d{name}")
+    assert abs(float(img.sum()) - ref_img.sum()) <= 1e-4 * np.abs(ref_img).sum()
+
+
+# ----------------------------------------------------------------------------- voxelizer
+
+
+def _grids_small():
+    return np.stack([I.cube_grid(32), I.patch_grid((100, 37, 64), 32, 256), I.grid_desc((-0.3, -0.2, -0.5),
+                     (0.05, 0.04, 0.06), (13, 7, 10))])
+
+
+def _f32grid(gd):
+    return np.asarray(gd, dtype=np.float32).astype(np.float64)
+
+
+def test_voxelize_matches_oracle_and_brick_lists_bit_exact():
+    G, _, _ = config1()
+    gd = _f32grid(_grids_small())
+    vox = engine.Voxelizer(G.M, gd, capacity=1024)
+    vol = vox.forward(*dev_set(G), count=True)
+    torch.cuda.synchronize()
+    ref, pairs, band = core.voxelize(G, gd, Q3, want_band=True)
+    assert_values_close(host(vol), ref, band, "voxelize")
+    assert abs(vox.pair_count() - pairs) <= max(10, 1e-4 * pairs)
+    nb = sum(((int(d[6]) + 7) // 8) * ((int(d[7]) + 7) // 8) * ((int(d[8]) + 7) // 8) for d in gd)
+    ranges = torch.empty((nb, 2), dtype=torch.int32, device="cuda")
+    ids = torch.empty(vox.capacity, dtype=torch.int32, device="cuda")
+    n = r2g.r2g_voxel_lists(G.M, vox.grids, vox.ws, ranges, ids)
+    ranges = ranges.cpu().numpy().view(np.uint32)
+    ids = ids[:n].cpu().numpy().view(np.uint32)
+    refl = core.brick_lists_f32(G, gd, Q3)
+    assert n == sum(len(v) for v in refl.values())
+    for b in range(nb):
+        s, e = ranges[b]
+        assert np.array_equal(ids[s:e].astype(np.int64), refl.get(b, np.zeros(0, np.int64))), b
+
+
+def test_voxelize_backward_matches_oracle_adjoint():
+    G = I.uniform_gaussians(600, 3, 0.02, 0.12)
+    gd = _f32grid(_grids_small())
+    vox = engine.Voxelizer(G.M, gd)
+    mean, scale, quat, rho = dev_set(G)
+    vox.forward(mean, scale, quat, rho)
+    dvol = I.rng(6).standard_normal(vox.n_vox).astype(np.float32)
+    g = [torch.zeros_like(t) for t in (mean, scale, quat, rho)]
+    vox.backward(mean, scale, quat, rho, dev(dvol), *g)
+    ref = core.voxelize_backward(G, gd, dvol, Q3)
+    for name, a, b in zip(("mean", "scale", "quat", "rho"), g, ref):
+        assert_grads_close(host(a), b, f"vox d{name}")
+
+
+# ----------------------------------------------------------------------------- losses, optimizer
+
+
+def test_projection_loss_matches_oracle():
+    g = I.rng(8)
+    x = g.uniform(0, 2, (2, 70, 45)).astype(np.float32)
+    y = (x + 0.2 * g.standard_normal(x.shape)).astype(np.float32)
+    xd, yd = dev(x), dev(y)
+    loss = torch.zeros(1, device="cuda")
+    grad = torch.empty_like(xd)
+    ws = torch.empty(r2g.r2g_loss_workspace_size(2, 70, 45), dtype=torch.uint8, device="cuda")
+    r2g.r2g_projection_loss(xd, yd, 0.25, loss, grad, ws)
+    L, G = losses.projection_loss(x, y, 0.25)
+    assert abs(float(loss) - L) <= 1e-5 * abs(L)
+    assert np.abs(host(grad) - G).max() <= 1e-4 * np.abs(G).max()
+
+
+def test_tv_matches_oracle():
+    v = I.rng(9).standard_normal((2, 12, 12, 12)).astype(np.float32)
+    vd = dev(v)
+    loss = torch.zeros(1, device="cuda")
+    grad = torch.empty_like(vd)
+    ws = torch.empty(r2g.r2g_tv_workspace_size(2, 12), dtype=torch.uint8, device="cuda")
+    r2g.r2g_tv3d(vd, 0.05, loss, grad, ws)
+    L = sum(losses.tv3d(v[k])[0] for k in range(2))
+    G = np.stack([losses.tv3d(v[k])[1] for k in range(2)])
+    assert abs(float(loss) - L) <= 1e-5 * abs(L)
+    assert np.abs(host(grad) - G).max() <= 1e-6 * np.abs(G).max()
+
+
+def test_adam_matches_oracle():
+    G = I.uniform_gaussians(333, 10)
+    st = engine.TrainState(G)
+    q, m_, s, r = st.views_of(st.grad)
+    gr = I.rng(11)
+    gact = {"mean": gr.standard_normal((333, 3)), "scale": gr.standard_normal((333, 3)),
+            "quat": gr.standard_normal((333, 4)), "rho": gr.standard_normal(333)}
+    m_.copy_(dev(gact["mean"]))
+    s.copy_(dev(gact["scale"]))
+    q.copy_(dev(gact["quat"]))
+    r.copy_(dev(gact["rho"]))
+    rq, rm, rs, rr = (host(t) for t in st.views_of(st.raw))
+    raw = {"mean": rm, "scale": rs, "quat": rq, "rho": rr}
+    mo = {k: np.zeros_like(v) for k, v in raw.items()}
+    vo = {k: np.zeros_like(v) for k, v in raw.items()}
+    for it in range(3):
+        r2g.r2g_adam_step(st.raw, st.act, st.grad, st.m, st.v, it, r2g.adam_opts())
+        act = losses.adam_step(raw, gact, mo, vo, it)
+        aq, am, as_, ar = (host(t) for t in st.views_of(st.act))
+        for k, a in (("mean", am), ("scale", as_), ("quat", aq), ("rho", ar)):
+            assert np.abs(a - act[k]).max() <= 1e-5 * max(1.0, np.abs(act[k]).max()), (it, k)
+        assert float(st.grad.abs().max()) == 0.0
+        # re-load the same activated gradients for the next step
+        m_.copy_(dev(gact["mean"]))
+        s.copy_(dev(gact["scale"]))
+        q.copy_(dev(gact["quat"]))
+        r.copy_(dev(gact["rho"]))
+
+
+def test_capacity_overflow_is_reported_and_recovered():
+    G, cam, views = cone_small()
+    rast = engine.Rasterizer(G.M, views.shape[0], cam, capacity=64)
+    mean, scale, quat, rho = dev_set(G)
+    img = torch.empty((views.shape[0], cam.H, cam.W), device="cuda")
+    r2g.r2g_rasterize(mean, scale, quat, rho, dev(views), rast.cam, rast.opts, img, rast.ws)
+    st, needed = r2g.r2g_poll(rast.ws)
+    assert st == r2g.R2G_E_CAPACITY and needed > 64
+    out = rast.forward(mean, scale, quat, rho, dev(views))  # grows and re-runs
+    assert rast.capacity >= needed
+    ref, _, band = core.render(G, views, cam, Q=Q9, want_band=True)
+    assert_values_close(host(out), ref, band, "after regrow")
