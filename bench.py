@@ -1,0 +1,397 @@
+#!/usr/bin/env python
+"""Benchmark of the R^2-Gaussian hot path on B300: fwd+bwd Gaussian-pixel evals/s.
+
+One step = one training iteration of the one-scan cone-beam workload (50,000
+Gaussians initialised from a seeded 40-ellipsoid 256^3 phantom; source-to-origin
+1000 mm, source-to-detector 1500 mm, 50 views over 360 deg, 512^2 detector at
+0.8 mm): rasterize one view, L1 + 0.25 D-SSIM, voxelize a random 32^3 TV patch
+with weight 0.05, full backward through both, fused Adam -- all in libr2g.so.
+The metric counts the (pixel, Gaussian) and (voxel, Gaussian) pairs that pass
+the gates in that step, once, over the device time of the whole step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun as independent replicas (one scan per rank, no data
+exchange: the path has nothing to reduce across scans); value = all ranks'
+pairs / the slowest rank's time.  --impl reference times the FP64 CPU oracle on
+the same workload (a bounded number of full steps) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd Gaussian-pixel evals/s"
+N_VIEWS, M_GAUSS, D_TV, N_OUT = 50, 50_000, 32, 256
+SM_COUNT = 148
+MUFU_PER_CLK = 16          # ex2 per SM per clock
+FP32_PER_CLK = 128         # FP32 lanes per SM per clock
+OPS_FWD, OPS_BWD = 6, 14   # algorithmic FP32 ops per gated pair (forward, backward)
+
+
+def peaks():
+    p = {"hbm_gbs": 6400.0, "sm_max_mhz": 2032.0, "source": "fallback"}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            m = json.load(f)
+        p.update(hbm_gbs=float(m["hbm_gbs"]), sm_max_mhz=float(m.get("sm_max_mhz", 2032.0)), source="measured")
+    except Exception:
+        pass
+    return p
+
+
+# ----------------------------------------------------------------------------- workload
+
+
+def make_workload(seed: int, device):
+    """The one-scan workload: phantom, init, geometry and measured projections."""
+    from paper_2405_20693_b300 import inputs as I
+
+    ph, vol = I.normalised_phantom(seed, N_OUT)
+    G = I.init_from_volume(vol, I.cube_grid(N_OUT), M_GAUSS, seed)
+    cam = I.cone_camera(512, 512)
+    views = I.view_table(I.even_angles(N_VIEWS), I.CONE_L_SO)
+    meas = I.phantom_projections(ph, views, cam, device=device).astype(np.float32)
+    return G, cam, views, meas
+
+
+def step_sequence(seed: int, n: int):
+    g = np.random.Generator(np.random.PCG64(seed + 2))
+    vs = g.integers(0, N_VIEWS, n)
+    offs = g.integers(0, N_OUT - D_TV + 1, (n, 3))
+    return [(int(vs[k]), tuple(int(x) for x in offs[k])) for k in range(n)]
+
+
+# ----------------------------------------------------------------------------- clocks
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.idx = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ----------------------------------------------------------------------------- reference arm / CPU baseline
+
+
+def oracle_steps(G, cam, views, meas, seq, n_steps):
+    """Full training steps of the FP64 oracle (forward, losses, adjoints) on the host:
+    returns (pairs, seconds)."""
+    from oracle import core, losses
+    from paper_2405_20693_b300 import inputs as I
+
+    pairs, t0 = 0, time.perf_counter()
+    for k in range(n_steps):
+        v, off = seq[k % len(seq)]
+        img, pp = core.render(G, views[v:v + 1], cam, Q=9.0)
+        L, dimg = losses.projection_loss(img, meas[v:v + 1].astype(np.float64), 0.25)
+        gd = I.patch_grid(off, D_TV, N_OUT)
+        vol, vp = core.voxelize(G, gd, 11.345)
+        Ltv, dvol = losses.tv3d(vol.reshape(D_TV, D_TV, D_TV), 0.05)
+        core.render_backward(G, views[v:v + 1], cam, dimg, Q=9.0)
+        core.voxelize_backward(G, gd, dvol.ravel(), 11.345)
+        pairs += pp + vp
+    return pairs, time.perf_counter() - t0
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    G, cam, views, meas = make_workload(0, None if not _has_cuda() else "cuda")
+    seq = step_sequence(0, args.warmup + args.steps)
+    oracle_steps(G, cam, views, meas, seq, args.warmup)
+    pairs, secs = oracle_steps(G, cam, views, meas, seq[args.warmup:], args.steps)
+    value = pairs / secs
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "one cone-beam scan, 50k Gaussians, 512^2 x 50 views, 1 view + 32^3 TV patch "
+                                   "per step", "oracle": "FP64 C++ scatter form + numpy losses, single thread"},
+            "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} full training steps of the same workload"},
+            "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def _has_cuda():
+    try:
+        import torch
+
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+# ----------------------------------------------------------------------------- our arm
+
+
+def source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2405_20693_b300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel sources; else None."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+            t = json.load(f)
+        if t.get("source_hash") != source_hash():
+            return None
+        return t["kernels"].get(kernel)
+    except Exception:
+        return None
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    from paper_2405_20693_b300 import build, engine, r2g
+
+    build.build()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    seed = rank * 1000
+    G, cam, views_np, meas_np = make_workload(seed, dev)
+    state = engine.TrainState(G, device=dev)
+    views = torch.as_tensor(views_np, device=dev)
+    meas = torch.as_tensor(meas_np, device=dev)
+    step = engine.TrainStep(state, views, meas, cam, D=D_TV, n_out=N_OUT, device=dev)
+    seq = step_sequence(seed, args.warmup + args.steps)
+    stream = torch.cuda.current_stream()
+
+    # warm-up (the first call sizes the workspaces)
+    for k in range(args.warmup):
+        v, off = seq[k]
+        step.run(k, v, off, check=(k == 0))
+    torch.cuda.synchronize()
+
+    # algorithmic pairs of every timed step (counting runs, untimed, on the current state)
+    mean, scale, quat, rho = state.params()
+    pix_pairs, vox_pairs = [], []
+    for k in range(args.warmup, args.warmup + args.steps):
+        v, off = seq[k]
+        step.rast.forward(mean, scale, quat, rho, views[v:v + 1], step.image, check=True, count=True)
+        pix_pairs.append(step.rast.pair_count())
+        from paper_2405_20693_b300 import inputs as I
+
+        step.vox.set_grids(I.patch_grid(off, D_TV, N_OUT))
+        step.vox.forward(mean, scale, quat, rho, step.vol, check=True, count=True)
+        vox_pairs.append(step.vox.pair_count())
+    total_pairs = float(sum(pix_pairs) + sum(vox_pairs))
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 126 MB L2
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    r2g.r2g_profile_enable(True, 64 * args.steps + 64)
+    r2g.r2g_profile_reset()
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        gpu_id = str(local_rank)
+    clock = ClockSampler(gpu_id)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clock.start()
+    launches0 = r2g.r2g_launch_count()
+    for j in range(args.steps):
+        k = args.warmup + j
+        v, off = seq[k]
+        flush.zero_()
+        evs[j][0].record(stream)
+        step.run(k, v, off, check=False)
+        evs[j][1].record(stream)
+    torch.cuda.synchronize()
+    launches = r2g.r2g_launch_count() - launches0
+    clocks = clock.stop()
+    r2g.r2g_profile_enable(False)
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    st_r, _ = r2g.r2g_poll(step.rast.ws)
+    st_v, _ = r2g.r2g_poll(step.vox.ws)
+    assert st_r == r2g.R2G_OK and st_v == r2g.R2G_OK, "list capacity overflow inside the timed region"
+    prof = {}
+    for kid, name in enumerate(r2g.PROFILE_KERNELS):
+        n, t = r2g.r2g_profile_read(kid)
+        if n:
+            prof[name] = {"launches": n, "ms": t}
+
+    if dist:
+        tt = torch.tensor([ms, total_pairs], dtype=torch.float64, device=dev)
+        mx = tt.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
+        ms_job, pairs_job = float(mx[0]), float(tt[1])
+    else:
+        ms_job, pairs_job = ms, total_pairs
+    value = pairs_job / (ms_job * 1e-3)
+
+    # end to end through the public API: per step, the measured view goes host -> device
+    # from pinned memory and the loss comes back
+    meas_host = torch.from_numpy(meas_np).pin_memory()
+    e2e_views = torch.zeros_like(meas[:1])
+    step_e2e = engine.TrainStep(state, views, e2e_views, cam, D=D_TV, n_out=N_OUT, device=dev)
+    step_e2e.run(0, seq[0][0], seq[0][1], check=True)
+    loss_host = torch.empty(2, dtype=torch.float32).pin_memory()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for j in range(args.steps):
+        k = args.warmup + j
+        v, off = seq[k]
+        e2e_views.copy_(meas_host[v:v + 1], non_blocking=True)
+        # the e2e step sees the uploaded view as view index 0 of a one-view table
+        step_e2e.views = views[v:v + 1]
+        step_e2e.run(k, 0, off, check=False)
+        loss_host.copy_(step_e2e.loss, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        tt = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt[0])
+    e2e_value = pairs_job / e2e_s
+
+    if rank == 0:
+        pk = peaks()
+        f = pk["sm_max_mhz"] * 1e6
+        mufu_peak = SM_COUNT * MUFU_PER_CLK * f
+        fp32_peak = SM_COUNT * FP32_PER_CLK * f
+        per_step_pix = sum(pix_pairs) / args.steps
+        per_step_vox = sum(vox_pairs) / args.steps
+        # roofline of the kernel with the largest device time
+        dom = max(prof, key=lambda k: prof[k]["ms"]) if prof else None
+        roof = None
+        if dom in ("splat_fwd", "splat_bwd", "vox_fwd", "vox_bwd"):
+            units = per_step_pix if dom.startswith("splat") else per_step_vox
+            ops = OPS_FWD if dom.endswith("fwd") else OPS_BWD
+            peak = min(mufu_peak, fp32_peak / ops) / 1e9
+            avg_s = prof[dom]["ms"] / prof[dom]["launches"] * 1e-3
+            ach = units / avg_s / 1e9
+            roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak, "unit": "Gpair/s",
+                    "frac": ach / peak, "traffic": ncu_traffic(dom),
+                    "peak_note": f"min(MUFU ex2 {MUFU_PER_CLK}/clk/SM, FP32 {FP32_PER_CLK}/clk/SM / {ops} ops) "
+                                 f"x {SM_COUNT} SMs x {pk['sm_max_mhz']:.0f} MHz"}
+        elif dom is not None:
+            roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                    "frac": None, "traffic": ncu_traffic(dom)}
+        # CPU baseline: the oracle on two full steps of the same workload
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            p, s = oracle_steps(G, cam, views_np, meas_np, seq[args.warmup:], 2)
+            cpu = {"value": p / s, "unit": "pairs/s", "cores": 1, "kind": "oracle",
+                   "sample": "2 full training steps of the same workload (FP64 oracle, single thread, "
+                             "initial parameters)"}
+        line = {
+            "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_job / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "one cone-beam scan: 50k Gaussians from a seeded 40-ellipsoid 256^3 phantom, "
+                                   "L_SO 1000 mm, L_SD 1500 mm, 50 views x 512^2 at 0.8 mm; per step 1 view "
+                                   "(L1+0.25 D-SSIM) + one 32^3 TV patch (0.05), full backward, Adam",
+                       "pixel_pairs_per_step": per_step_pix, "voxel_pairs_per_step": per_step_vox,
+                       "l2": "flushed (256 MB write) before every timed step", "parallelism": f"replicas x{world}",
+                       "tile": "16x16", "bricks": "8^3"},
+            "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": 4 * cam.H * cam.W,
+                    "d2h_bytes_per_step": 8},
+            "gpu_launches": int(launches),
+            "roofline": roof,
+            "kernels_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items()},
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -243,6 +243,23 @@ r2g_status r2g_adam_step(int64_t M, float* raw, float* act, float* grad, float* 
  * entries that call needed.  Clears nothing. */
 r2g_status r2g_poll(const void* ws, size_t ws_bytes, r2g_stream stream, int64_t* needed_keys);
 
+/* ---------------------------------------------------------------- measurement
+ *
+ * Optional timing of the library's own kernels: when enabled, every call records
+ * a CUDA event pair on its stream around each hot kernel (or kernel group):
+ * 0 project, 1 emit (count+scan+emit), 2 sort (all radix passes), 3 ranges,
+ * 4 splat_fwd, 5 splat_bwd, 6 project_bwd, 7 vox_project, 8 vox_fwd, 9 vox_bwd,
+ * 10 vox_chain, 11 loss, 12 tv, 13 adam.  Not for use inside stream capture.
+ * max_spans bounds the recorded pairs (events are created once, here). */
+r2g_status r2g_profile_enable(int32_t on, int32_t max_spans);
+r2g_status r2g_profile_reset(void);
+/* Launch count and summed device time (ms) of one kernel id since the last reset;
+ * waits for the recorded events. */
+r2g_status r2g_profile_read(int32_t kernel, int64_t* launches, double* total_ms);
+const char* r2g_profile_name(int32_t kernel);
+/* Total number of CUDA kernels this library has launched in this process. */
+int64_t r2g_launch_count(void);
+
 /* Thread-local description of the last error returned on this thread. */
 const char* r2g_last_error(void);
 

@@ -63,6 +63,9 @@ R2G_API r2g_status r2g_adam_step(int64_t M, float* raw, float* act, float* grad,
     const long long n = 11 * (long long)M;
     long long blocks = (n + 255) / 256;
     if (blocks > 148 * 16) blocks = 148 * 16;
+    prof_begin(P_ADAM, stream);
     k_adam<<<(unsigned)blocks, 256, 0, stream>>>(a, raw, act, grad, m, v);
+    prof_end(P_ADAM, stream);
+    note_launches(1);
     return check_launch("r2g_adam_step");
 }

@@ -312,6 +312,7 @@ R2G_API r2g_status r2g_projection_loss(int32_t V, int32_t H, int32_t W, const fl
     float* dxy = reinterpret_cast<float*>(base + L.dxy);
     float* partials = reinterpret_cast<float*>(base + L.partials);
     const int tpv = L.tiles_x * L.tiles_y;
+    prof_begin(P_LOSS, stream);
     k_ssim_maps<<<(unsigned)L.n_tiles, 256, 0, stream>>>(render, meas, H, W, L.tiles_x, tpv, win, dmu, dxx, dxy,
                                                           partials);
     const double N = (double)V * H * W;
@@ -319,6 +320,8 @@ R2G_API r2g_status r2g_projection_loss(int32_t V, int32_t H, int32_t W, const fl
                                                           (float)(1.0 / N), (float)(lambda_ssim / N), drender);
     k_finalize<<<1, 256, 0, stream>>>(partials, (int)L.n_tiles, 0, (float)(1.0 / N), lambda_ssim, (float)(1.0 / N),
                                       loss);
+    prof_end(P_LOSS, stream);
+    note_launches(3);
     return check_launch("r2g_projection_loss");
 }
 
@@ -339,7 +342,10 @@ R2G_API r2g_status r2g_tv3d(int32_t G, int32_t D, const float* vol, float lambda
     float* partials = static_cast<float*>(ws);
     // every axis has D^2 (D - 1) forward differences
     const float inv_cnt = (float)(1.0 / ((double)D * D * (D - 1)));
+    prof_begin(P_TV, stream);
     k_tv3d<<<(unsigned)blocks, 256, 0, stream>>>(vol, D, n, inv_cnt, lambda_tv, dvol, partials);
     k_finalize<<<1, 256, 0, stream>>>(partials, (int)blocks, 1, lambda_tv * inv_cnt, 0.f, 0.f, loss);
+    prof_end(P_TV, stream);
+    note_launches(2);
     return check_launch("r2g_tv3d");
 }

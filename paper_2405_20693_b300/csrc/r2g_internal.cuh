@@ -20,6 +20,18 @@ r2g_status fail(r2g_status s, const char* fmt, ...);
 // R2G_E_CUDA with a message if the last launch failed, else R2G_OK.
 r2g_status check_launch(const char* what);
 
+// ---------------------------------------------------------------- profiling
+// Optional CUDA-event pairs around each hot kernel (or kernel group), enabled by
+// r2g_profile_enable; off by default.  Also a count of kernel launches.
+
+enum ProfKernel : int {
+    P_PROJECT = 0, P_EMIT, P_SORT, P_RANGES, P_SPLAT_FWD, P_SPLAT_BWD, P_PROJECT_BWD,
+    P_VOX_PROJECT, P_VOX_FWD, P_VOX_BWD, P_VOX_CHAIN, P_LOSS, P_TV, P_ADAM, P_COUNT
+};
+void prof_begin(int k, cudaStream_t s);
+void prof_end(int k, cudaStream_t s);
+void note_launches(int n);
+
 // ---------------------------------------------------------------- workspace
 
 // Status block at offset 0 of every workspace (256 bytes).

@@ -714,6 +714,7 @@ R2G_API r2g_status r2g_project(int64_t M, const float* mean, const float* scale,
     Params G{mean, scale, quat, rho};
     k_project<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(G, views, camf(cam), opts->Q, opts->tile_w,
                                                                 opts->tile_h, M, n, nullptr, nullptr, proj, rect);
+    note_launches(1);
     return check_launch("r2g_project");
 }
 
@@ -741,19 +742,30 @@ R2G_API r2g_status r2g_rasterize(int64_t M, const float* mean, const float* scal
     cudaMemsetAsync(st, 0, sizeof(WsStatus), stream);
     Params G{mean, scale, quat, rho};
     const CamF cf = camf(cam);
+    prof_begin(P_PROJECT, stream);
     k_project<<<(unsigned)((L.n_rec + 255) / 256), 256, 0, stream>>>(G, views, cf, opts->Q, opts->tile_w,
                                                                       opts->tile_h, M, L.n_rec, rec, rect, nullptr,
                                                                       nullptr);
+    prof_end(P_PROJECT, stream);
     TileOp op{rect, M, L.tiles_x, L.tiles_per_view};
+    prof_begin(P_EMIT, stream);
     emit_lists(op, L.n_rec, partials, st, a, (unsigned long long)cap, stream);
+    prof_end(P_EMIT, stream);
+    prof_begin(P_SORT, stream);
     uint64_t* sorted = radix_sort_u64(a, b, scratch, st, bits_for(L.n_tiles), stream);
+    prof_end(P_SORT, stream);
+    prof_begin(P_RANGES, stream);
     build_ranges(sorted, st, ranges, L.n_tiles, stream);
+    prof_end(P_RANGES, stream);
     const float Tq = -0.5f * kLog2e * opts->Q;
+    prof_begin(P_SPLAT_FWD, stream);
     if (opts->count_pairs)
         launch_fwd<true>(opts->tile_w, opts->tile_h, rec, ranges, sorted, M, L, cam->H, cam->W, Tq, image, st, stream);
     else
         launch_fwd<false>(opts->tile_w, opts->tile_h, rec, ranges, sorted, M, L, cam->H, cam->W, Tq, image, st,
                           stream);
+    prof_end(P_SPLAT_FWD, stream);
+    note_launches(1 + 3 + 3 * ((bits_for(L.n_tiles) + kRadixBits - 1) / kRadixBits) + 1 + 1);
     return check_launch("r2g_rasterize");
 }
 
@@ -778,10 +790,15 @@ R2G_API r2g_status r2g_rasterize_backward(int64_t M, const float* mean, const fl
     const uint64_t* sorted = sorted_buffer(base, L, cap);
     cudaMemsetAsync(mom, 0, 32 * (size_t)L.n_rec, stream);
     const float Tq = -0.5f * kLog2e * opts->Q;
+    prof_begin(P_SPLAT_BWD, stream);
     launch_bwd(opts->tile_w, opts->tile_h, rec, ranges, sorted, M, L, cam->H, cam->W, Tq, dimage, mom, stream);
+    prof_end(P_SPLAT_BWD, stream);
     Params G{mean, scale, quat, rho};
+    prof_begin(P_PROJECT_BWD, stream);
     k_project_bwd<<<(unsigned)((M + 127) / 128), 128, 0, stream>>>(G, views, camf(cam), opts->Q, M, V, rec, mom,
                                                                     dmean, dscale, dquat, drho);
+    prof_end(P_PROJECT_BWD, stream);
+    note_launches(2);
     return check_launch("r2g_rasterize_backward");
 }
 

@@ -527,7 +527,9 @@ r2g_status voxelize_impl(int64_t M, const float* mean, const float* scale, const
     uint64_t* b = reinterpret_cast<uint64_t*>(base + L.fixed + align_up(8 * (size_t)cap));
     cudaMemsetAsync(st, 0, sizeof(WsStatus), stream);
     Params P{mean, scale, quat, rho};
+    prof_begin(P_VOX_PROJECT, stream);
     k_vox_project<<<(unsigned)((L.n_rec + 255) / 256), 256, 0, stream>>>(P, gr, Q3, M, rec, rect);
+    prof_end(P_VOX_PROJECT, stream);
     BrickEmitOp op;
     op.rect = rect;
     op.M = M;
@@ -536,14 +538,23 @@ r2g_status voxelize_impl(int64_t M, const float* mean, const float* scale, const
         op.nbx[g] = gr.g[g].nb[0];
         op.nby[g] = gr.g[g].nb[1];
     }
+    prof_begin(P_EMIT, stream);
     emit_lists(op, L.n_rec, partials, st, a, (unsigned long long)cap, stream);
+    prof_end(P_EMIT, stream);
+    prof_begin(P_SORT, stream);
     uint64_t* sorted = radix_sort_u64(a, b, scratch, st, bits_for(L.n_bricks), stream);
+    prof_end(P_SORT, stream);
+    prof_begin(P_RANGES, stream);
     build_ranges(sorted, st, ranges, L.n_bricks, stream);
+    prof_end(P_RANGES, stream);
     const float Tq = -0.5f * kLog2e * Q3;
+    note_launches(1 + 3 + 3 * ((bits_for(L.n_bricks) + kRadixBits - 1) / kRadixBits) + 1 + 1);
+    prof_begin(P_VOX_FWD, stream);
     if (count)
         k_vox_fwd<true><<<(unsigned)L.n_bricks, kVoxThreads, 0, stream>>>(rec, ranges, sorted, M, gr, Tq, vol, st);
     else
         k_vox_fwd<false><<<(unsigned)L.n_bricks, kVoxThreads, 0, stream>>>(rec, ranges, sorted, M, gr, Tq, vol, st);
+    prof_end(P_VOX_FWD, stream);
     return check_launch("r2g_voxelize");
 }
 }  // namespace
@@ -583,9 +594,14 @@ R2G_API r2g_status r2g_voxelize_backward(int64_t M, const float* mean, const flo
     const uint64_t* sorted = vox_sorted(base, L, cap);
     cudaMemsetAsync(mom, 0, 48 * (size_t)L.n_rec, stream);
     const float Tq = -0.5f * kLog2e * Q3;
+    prof_begin(P_VOX_BWD, stream);
     k_vox_bwd<<<(unsigned)L.n_bricks, kVoxThreads, 0, stream>>>(rec, ranges, sorted, M, gr, Tq, dvol, mom);
+    prof_end(P_VOX_BWD, stream);
     Params P{mean, scale, quat, rho};
+    prof_begin(P_VOX_CHAIN, stream);
     k_vox_chain<<<(unsigned)((M + 127) / 128), 128, 0, stream>>>(P, gr, M, mom, dmean, dscale, dquat, drho);
+    prof_end(P_VOX_CHAIN, stream);
+    note_launches(2);
     return check_launch("r2g_voxelize_backward");
 }
 

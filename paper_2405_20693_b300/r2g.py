@@ -111,6 +111,11 @@ def lib():
             "r2g_tv3d": (_I32, [_I32, _I32, _P, _F, _P, _P, _P, _SZ, _P]),
             "r2g_adam_step": (_I32, [_I64, _P, _P, _P, _P, _P, _I32, _P, _P]),
             "r2g_poll": (_I32, [_P, _SZ, _P, _P]),
+            "r2g_profile_enable": (_I32, [_I32, _I32]),
+            "r2g_profile_reset": (_I32, []),
+            "r2g_profile_read": (_I32, [_I32, _P, _P]),
+            "r2g_profile_name": (ctypes.c_char_p, [_I32]),
+            "r2g_launch_count": (_I64, []),
             "r2g_last_error": (ctypes.c_char_p, []),
             "r2g_version": (ctypes.c_char_p, []),
         }
@@ -277,6 +282,33 @@ def r2g_adam_step(raw, act, grad, m, v, it: int, opts: AdamOpts, stream=None):
     M = raw.numel() // 11
     _check(lib().r2g_adam_step(M, _ptr(raw), _ptr(act), _ptr(grad), _ptr(m), _ptr(v), int(it), ctypes.byref(opts),
                                _stream(stream)))
+
+
+PROFILE_KERNELS = ("project", "emit", "sort", "ranges", "splat_fwd", "splat_bwd", "project_bwd", "vox_project",
+                   "vox_fwd", "vox_bwd", "vox_chain", "loss", "tv", "adam")
+
+
+def r2g_profile_enable(on: bool, max_spans: int = 4096):
+    _check(lib().r2g_profile_enable(int(on), int(max_spans)))
+
+
+def r2g_profile_reset():
+    _check(lib().r2g_profile_reset())
+
+
+def r2g_profile_read(kernel: int) -> tuple[int, float]:
+    n = ctypes.c_int64(0)
+    ms = ctypes.c_double(0.0)
+    _check(lib().r2g_profile_read(int(kernel), ctypes.byref(n), ctypes.byref(ms)))
+    return int(n.value), float(ms.value)
+
+
+def r2g_profile_name(kernel: int) -> str:
+    return lib().r2g_profile_name(int(kernel)).decode()
+
+
+def r2g_launch_count() -> int:
+    return int(lib().r2g_launch_count())
 
 
 def r2g_version() -> str:
