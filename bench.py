@@ -298,7 +298,9 @@ def run_ours(args, rank, world, local_rank):
     meas_host = torch.from_numpy(meas_np).pin_memory()
     e2e_views = torch.zeros_like(meas[:1])
     step_e2e = engine.TrainStep(state, views, e2e_views, cam, D=D_TV, n_out=N_OUT, device=dev)
-    step_e2e.run(0, seq[0][0], seq[0][1], check=True)
+    step_e2e.views = views[seq[0][0]:seq[0][0] + 1]
+    e2e_views.copy_(meas[seq[0][0]:seq[0][0] + 1])
+    step_e2e.run(0, 0, seq[0][1], check=True)
     loss_host = torch.empty(2, dtype=torch.float32).pin_memory()
     torch.cuda.synchronize()
     if dist:
