@@ -214,6 +214,19 @@ size_t r2g_tv_workspace_size(int32_t G, int32_t D);
 r2g_status r2g_tv3d(int32_t G, int32_t D, const float* vol, float lambda_tv, float* loss, float* dvol, void* ws,
                     size_t ws_bytes, r2g_stream stream);
 
+/* The same TV loss and gradient as r2g_tv3d, for callers that cannot allocate
+ * device memory where they call it (a host that fixes the device budget up front,
+ * a real-time loop that must not stall on an allocation, a plugin that only
+ * receives input and output buffers).  No workspace argument: the partial sums go
+ * to a fixed 256 KiB array inside the library, so G * D^3 <= 16777216 voxels
+ * (larger volumes return R2G_E_INVAL; use r2g_tv3d).  Nothing is allocated.
+ * The first call on each device looks up that array's device address once
+ * (cudaGetSymbolAddress) -- make it before any stream capture.  Calls share the
+ * array: calls that overlap on the GPU race; calls ordered on one stream do not.
+ * The paper has no counterpart to this entry point. */
+r2g_status r2g_tv3d_noalloc(int32_t G, int32_t D, const float* vol, float lambda_tv, float* loss, float* dvol,
+                            r2g_stream stream);
+
 /* ---------------------------------------------------------------- optimizer
  *
  * One Adam step (Sec. 5.1) on the raw parameters, given gradients with respect to

@@ -109,6 +109,7 @@ def lib():
             "r2g_projection_loss": (_I32, [_I32, _I32, _I32, _P, _P, _F, _P, _P, _P, _SZ, _P]),
             "r2g_tv_workspace_size": (_SZ, [_I32, _I32]),
             "r2g_tv3d": (_I32, [_I32, _I32, _P, _F, _P, _P, _P, _SZ, _P]),
+            "r2g_tv3d_noalloc": (_I32, [_I32, _I32, _P, _F, _P, _P, _P]),
             "r2g_adam_step": (_I32, [_I64, _P, _P, _P, _P, _P, _I32, _P, _P]),
             "r2g_poll": (_I32, [_P, _SZ, _P, _P]),
             "r2g_profile_enable": (_I32, [_I32, _I32]),
@@ -275,6 +276,12 @@ def r2g_tv3d(vol, lambda_tv, loss, dvol, ws, stream=None):
     G, D = vol.shape[0], vol.shape[1]
     _check(lib().r2g_tv3d(G, D, _ptr(vol), float(lambda_tv), _ptr(loss), _ptr(dvol), _ptr(ws), ws.numel(),
                           _stream(stream)))
+
+
+def r2g_tv3d_noalloc(vol, lambda_tv, loss, dvol, stream=None):
+    _f32(vol, loss, dvol)
+    G, D = vol.shape[0], vol.shape[1]
+    _check(lib().r2g_tv3d_noalloc(G, D, _ptr(vol), float(lambda_tv), _ptr(loss), _ptr(dvol), _stream(stream)))
 
 
 def r2g_adam_step(raw, act, grad, m, v, it: int, opts: AdamOpts, stream=None):
