@@ -9,6 +9,7 @@
 // scatter in which each 256-element round is ranked with warp match masks so
 // the order of equal digits is kept (stability makes every per-key list come out
 // in ascending Gaussian id).
+#include "emit.cuh"
 #include "r2g_internal.cuh"
 
 namespace r2g {
@@ -43,23 +44,46 @@ __global__ void __launch_bounds__(256) k_radix_hist(const uint64_t* __restrict__
 
 // One block per digit: offset of (digit, block) = entries of smaller digits +
 // entries of this digit in earlier blocks.  Overwrites hist in place.
-__global__ void __launch_bounds__(256) k_radix_offsets(uint32_t* __restrict__ hist,
-                                                       const uint32_t* __restrict__ digit_total, int nblocks) {
-    __shared__ uint32_t sm[8];
-    const int d = blockIdx.x;
-    uint32_t part = 0;
-    for (int k = threadIdx.x; k < d; k += 256) part += digit_total[k];
-    uint32_t base;
-    block_exclusive_scan_256(part, sm, &base);
-    uint32_t running = base;
+__global__ void __launch_bounds__(1024) k_radix_offsets(uint32_t* __restrict__ hist,
+                                                        const uint32_t* __restrict__ digit_total, int nblocks) {
+    __shared__ uint32_t wsum[32];
+    __shared__ uint32_t s_base;
+    const int d = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (warp == 0) {
+        uint32_t part = 0;
+        for (int k = lane; k < d; k += 32) part += digit_total[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        if (lane == 0) s_base = part;
+    }
+    __syncthreads();
+    uint32_t running = s_base;
     uint32_t* row = hist + (size_t)d * nblocks;
-    for (int c = 0; c < nblocks; c += 256) {
-        const int idx = c + threadIdx.x;
+    for (int c = 0; c < nblocks; c += 1024) {
+        const int idx = c + tid;
         const uint32_t v = idx < nblocks ? row[idx] : 0u;
-        uint32_t tot;
-        const uint32_t ex = block_exclusive_scan_256(v, sm, &tot);
-        if (idx < nblocks) row[idx] = running + ex;
-        running += tot;
+        uint32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t w = wsum[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            wsum[lane] = w;
+        }
+        __syncthreads();
+        const uint32_t before = (warp > 0 ? wsum[warp - 1] : 0u) + x - v;
+        if (idx < nblocks) row[idx] = running + before;
+        running += wsum[31];
+        __syncthreads();
     }
 }
 
@@ -120,16 +144,49 @@ __global__ void __launch_bounds__(256) k_ranges(const uint64_t* __restrict__ s, 
 
 }  // namespace
 
-size_t sort_scratch_bytes() { return ((size_t)kRadix * kSortBlocks + (size_t)kRadix * kMaxPasses) * sizeof(uint32_t); }
+size_t sort_scratch_bytes() {
+    return ((size_t)kRadix * kSortBlocksMax + (size_t)kRadix * kMaxPasses) * sizeof(uint32_t);
+}
+
+int sort_blocks_for(long long capacity) {
+    long long nb = (capacity + 4095) / 4096;  // about 4096 entries (16 rounds) per block when full
+    if (nb < 148) nb = 148;
+    if (nb > kSortBlocksMax) nb = kSortBlocksMax;
+    return (int)nb;
+}
+
+namespace {
+struct ItemOp {
+    const uint2* ranges;
+    uint32_t* item_off;
+    __device__ __forceinline__ uint32_t count(long long t) const {
+        const uint2 r = ranges[t];
+        return (r.y - r.x + kChunk - 1) / kChunk;
+    }
+    __device__ __forceinline__ void emit(long long t, uint64_t* out, unsigned long long off,
+                                         unsigned long long cap) const {
+        const uint32_t n = count(t);
+        item_off[t] = (uint32_t)off;
+        for (uint32_t c = 0; c < n; ++c)
+            if (off + c < cap) out[off + c] = ((uint64_t)t << 32) | c;
+    }
+};
+}  // namespace
+
+void build_items(const uint2* ranges, long long n_slots, WsStatus* item_status, uint32_t* item_off, uint64_t* items,
+                 long long items_cap, unsigned long long* partials, cudaStream_t st) {
+    cudaMemsetAsync(item_status, 0, sizeof(WsStatus), st);
+    emit_lists(ItemOp{ranges, item_off}, n_slots, partials, item_status, items, (unsigned long long)items_cap, st);
+}
 
 uint64_t* radix_sort_u64(uint64_t* a, uint64_t* b, uint32_t* scratch, const WsStatus* status, int key_bits,
-                         cudaStream_t st) {
+                         int nb, cudaStream_t st) {
     if (key_bits < 1) key_bits = 1;
     if (key_bits > 32) key_bits = 32;
     const int passes = (key_bits + kRadixBits - 1) / kRadixBits;
     const int bpp = (key_bits + passes - 1) / passes;
     uint32_t* hist = scratch;
-    uint32_t* totals = scratch + (size_t)kRadix * kSortBlocks;
+    uint32_t* totals = scratch + (size_t)kRadix * kSortBlocksMax;
     cudaMemsetAsync(totals, 0, sizeof(uint32_t) * kRadix * kMaxPasses, st);
     uint64_t* src = a;
     uint64_t* dst = b;
@@ -137,9 +194,9 @@ uint64_t* radix_sort_u64(uint64_t* a, uint64_t* b, uint32_t* scratch, const WsSt
         const int shift = 32 + p * bpp;
         const uint32_t mask = (1u << bpp) - 1u;
         uint32_t* tot = totals + (size_t)kRadix * p;
-        k_radix_hist<<<kSortBlocks, 256, 0, st>>>(src, status, hist, tot, shift, mask);
-        k_radix_offsets<<<kRadix, 256, 0, st>>>(hist, tot, kSortBlocks);
-        k_radix_scatter<<<kSortBlocks, 256, 0, st>>>(src, dst, hist, status, shift, mask);
+        k_radix_hist<<<nb, 256, 0, st>>>(src, status, hist, tot, shift, mask);
+        k_radix_offsets<<<1u << bpp, 1024, 0, st>>>(hist, tot, nb);
+        k_radix_scatter<<<nb, 256, 0, st>>>(src, dst, hist, status, shift, mask);
         uint64_t* t = src;
         src = dst;
         dst = t;
@@ -149,7 +206,7 @@ uint64_t* radix_sort_u64(uint64_t* a, uint64_t* b, uint32_t* scratch, const WsSt
 
 void build_ranges(const uint64_t* sorted, const WsStatus* status, uint2* ranges, int64_t n_slots, cudaStream_t st) {
     cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)n_slots, st);
-    k_ranges<<<kSortBlocks, 256, 0, st>>>(sorted, status, ranges, (unsigned long long)n_slots);
+    k_ranges<<<148 * 8, 256, 0, st>>>(sorted, status, ranges, (unsigned long long)n_slots);
 }
 
 }  // namespace r2g

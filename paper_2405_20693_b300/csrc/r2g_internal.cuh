@@ -60,8 +60,9 @@ struct Layout {
 
 // ---------------------------------------------------------------- list building
 
-constexpr int kScanBlocks = 148 * 4;  // fixed grid of the count scan and the key emission
-constexpr int kSortBlocks = 148 * 8;  // fixed grid of the radix passes
+constexpr int kScanBlocks = 148 * 4;     // fixed grid of the count scan and the key emission
+constexpr int kSortBlocksMax = 148 * 16; // largest grid of the radix passes
+constexpr int kChunk = 128;              // list entries per work item (tile or brick, chunk)
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
 
@@ -69,10 +70,24 @@ constexpr int kRadix = 1 << kRadixBits;
 // entry buffers.
 size_t sort_scratch_bytes();
 
+// Grid of the radix passes for a given entry capacity (fixed per workspace, so
+// the launch sequence does not depend on device data).
+int sort_blocks_for(long long capacity);
+
 // Stable LSD radix sort of status->n_keys 64-bit entries (read on the device) by
 // bits [32, 32 + key_bits).  Returns the buffer that holds the result (a or b).
 uint64_t* radix_sort_u64(uint64_t* a, uint64_t* b, uint32_t* scratch, const WsStatus* status, int key_bits,
-                         cudaStream_t st);
+                         int sort_blocks, cudaStream_t st);
+
+// Work items: every key's range is cut into chunks of kChunk entries; item =
+// (key << 32) | chunk index, in key order.  item_off[key] = index of the key's
+// first item (written for non-empty keys).  item_status->n_keys = item count.
+// items must hold items_capacity(n_slots, capacity) entries.
+inline long long items_capacity(long long n_slots, long long capacity) {
+    return n_slots + (capacity + kChunk - 1) / kChunk + 1;
+}
+void build_items(const uint2* ranges, long long n_slots, WsStatus* item_status, uint32_t* item_off, uint64_t* items,
+                 long long items_cap, unsigned long long* partials, cudaStream_t st);
 
 // ranges[k] = [start, end) of key k in the sorted entries (absent keys: [0, 0)).
 void build_ranges(const uint64_t* sorted, const WsStatus* status, uint2* ranges, int64_t n_slots, cudaStream_t st);

@@ -302,16 +302,23 @@ struct TileOp {
 template <int TW, int TH, bool COUNT>
 __global__ void __launch_bounds__(TW * TH / 2) k_splat_fwd(const float4* __restrict__ rec,
                                                            const uint2* __restrict__ ranges,
-                                                           const uint64_t* __restrict__ sorted, long long M,
-                                                           int tiles_x, int tiles_per_view, int H, int W, float Tq,
+                                                           const uint64_t* __restrict__ sorted,
+                                                           const uint64_t* __restrict__ items,
+                                                           const WsStatus* __restrict__ item_st,
+                                                           float* __restrict__ partial, long long M, int tiles_x,
+                                                           int tiles_per_view, int H, int W, float Tq,
                                                            float* __restrict__ image, WsStatus* st) {
     constexpr int NT = TW * TH / 2;  // threads; two pixels each
     constexpr int TPR = TW / 2;      // threads per pixel row
     constexpr int RPW = 32 / TPR;    // pixel rows per warp
-    static_assert(32 % TPR == 0 && NT % 32 == 0, "tile shape");
+    static_assert(32 % TPR == 0 && NT % 32 == 0 && kChunk % NT == 0, "tile shape");
     __shared__ float4 s_a[NT];
     __shared__ float4 s_b[NT];
-    const int tile = blockIdx.x;
+    const unsigned long long it = blockIdx.x;
+    if (it >= item_st->n_keys) return;
+    const uint64_t item = items[it];
+    const int tile = (int)(item >> 32);
+    const uint32_t chunk = (uint32_t)item;
     const int v = tile / tiles_per_view;
     const int lt = tile - v * tiles_per_view;
     const int ty = lt / tiles_x, tx = lt - ty * tiles_x;
@@ -324,8 +331,11 @@ __global__ void __launch_bounds__(TW * TH / 2) k_splat_fwd(const float4* __restr
     float acc0 = 0.0f, acc1 = 0.0f;
     unsigned int cnt = 0;
     const uint2 rg = ranges[tile];
-    for (uint32_t base = rg.x; base < rg.y; base += NT) {
-        const int n = min((uint32_t)NT, rg.y - base);
+    const uint32_t start = rg.x + chunk * kChunk;
+    const uint32_t end = min(start + (uint32_t)kChunk, rg.y);
+    const uint32_t nch = (rg.y - rg.x + kChunk - 1) / kChunk;
+    for (uint32_t base = start; base < end; base += NT) {
+        const int n = min((uint32_t)NT, end - base);
         __syncthreads();
         if ((int)threadIdx.x < n) {
             const uint32_t gid = (uint32_t)sorted[base + threadIdx.x];
@@ -351,15 +361,44 @@ __global__ void __launch_bounds__(TW * TH / 2) k_splat_fwd(const float4* __restr
             if (COUNT) cnt += (t0 >= Tq && px < W && py < H) + (t1 >= Tq && px + 1 < W && py < H);
         }
     }
-    if (py < H) {
-        float* row = image + ((size_t)v * H + py) * W;
-        if (px < W) row[px] = acc0;
-        if (px + 1 < W) row[px + 1] = acc1;
+    if (nch == 1) {
+        if (py < H) {
+            float* row = image + ((size_t)v * H + py) * W;
+            if (px < W) row[px] = acc0;
+            if (px + 1 < W) row[px + 1] = acc1;
+        }
+    } else {
+        float* p = partial + it * (size_t)(TW * TH) + ly * TW + lx;
+        p[0] = acc0;
+        p[1] = acc1;
     }
     if (COUNT) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
         if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(&st->pairs, (unsigned long long)cnt);
+    }
+}
+
+// Tiles whose list spans several chunks: sum the chunk images in chunk order.
+// Tiles with an empty list get zeros (no work item writes them).
+template <int TW, int TH>
+__global__ void __launch_bounds__(128) k_splat_reduce(const uint2* __restrict__ ranges,
+                                                      const uint32_t* __restrict__ item_off,
+                                                      const float* __restrict__ partial, int tiles_x,
+                                                      int tiles_per_view, int H, int W, float* __restrict__ image) {
+    const int tile = blockIdx.x;
+    const uint2 rg = ranges[tile];
+    const uint32_t nch = (rg.y - rg.x + kChunk - 1) / kChunk;
+    if (nch == 1) return;
+    const int v = tile / tiles_per_view;
+    const int lt = tile - v * tiles_per_view;
+    const int ty = lt / tiles_x, tx = lt - ty * tiles_x;
+    const float* base = partial + (nch ? (size_t)item_off[tile] * (TW * TH) : 0);
+    for (int p = threadIdx.x; p < TW * TH; p += 128) {
+        float s = 0.0f;
+        for (uint32_t c = 0; c < nch; ++c) s += base[(size_t)c * (TW * TH) + p];
+        const int gy = ty * TH + p / TW, gx = tx * TW + p % TW;
+        if (gy < H && gx < W) image[((size_t)v * H + gy) * W + gx] = s;
     }
 }
 
@@ -370,12 +409,19 @@ constexpr int kBwdThreads = 128;
 template <int TW, int TH>
 __global__ void __launch_bounds__(kBwdThreads) k_splat_bwd(const float4* __restrict__ rec,
                                                            const uint2* __restrict__ ranges,
-                                                           const uint64_t* __restrict__ sorted, long long M,
+                                                           const uint64_t* __restrict__ sorted,
+                                                           const uint64_t* __restrict__ items,
+                                                           const WsStatus* __restrict__ item_st, long long M,
                                                            int tiles_x, int tiles_per_view, int H, int W, float Tq,
                                                            const float* __restrict__ dimage,
                                                            float4* __restrict__ mom) {
+    static_assert(kChunk == kBwdThreads, "one record per thread");
     __shared__ float s_g[TH][TW];
-    const int tile = blockIdx.x;
+    const unsigned long long it = blockIdx.x;
+    if (it >= item_st->n_keys) return;
+    const uint64_t item = items[it];
+    const int tile = (int)(item >> 32);
+    const uint32_t chunk = (uint32_t)item;
     const int v = tile / tiles_per_view;
     const int lt = tile - v * tiles_per_view;
     const int ty = lt / tiles_x, tx = lt - ty * tiles_x;
@@ -389,7 +435,8 @@ __global__ void __launch_bounds__(kBwdThreads) k_splat_bwd(const float4* __restr
     const uint2 rg = ranges[tile];
     const float4* vrec = rec + 2 * (size_t)v * (size_t)M;
     float4* vmom = mom + 2 * (size_t)v * (size_t)M;
-    for (uint32_t e = rg.x + threadIdx.x; e < rg.y; e += kBwdThreads) {
+    const uint32_t e = rg.x + chunk * kChunk + threadIdx.x;
+    if (e < rg.y) {
         const uint32_t gid = (uint32_t)sorted[e];
         const float4 a = vrec[2 * (size_t)gid];
         const float4 b = vrec[2 * (size_t)gid + 1];
@@ -582,7 +629,7 @@ __global__ void __launch_bounds__(128) k_project_bwd(Params G, const float* __re
 // ------------------------------------------------------------------ host side
 
 struct RasterLayout {
-    size_t status, rec, rect, partials, ranges, mom, scratch, a, b, fixed;
+    size_t status, rec, rect, partials, ranges, mom, scratch, item_status, item_off, fixed;
     int tiles_x, tiles_y, tiles_per_view;
     long long n_tiles, n_rec;
 };
@@ -622,16 +669,42 @@ RasterLayout raster_layout(int64_t M, int32_t V, const r2g_camera* cam, const r2
     L.ranges = lay.take(8 * (size_t)L.n_tiles);
     L.mom = lay.take(32 * (size_t)L.n_rec);
     L.scratch = lay.take(sort_scratch_bytes());
+    L.item_status = lay.take(sizeof(WsStatus));
+    L.item_off = lay.take(4 * (size_t)L.n_tiles);
     L.fixed = lay.off;
     return L;
 }
 
-// key capacity held by ws_bytes (multiple of 32 entries so both buffers stay aligned)
-long long capacity_of(const RasterLayout& L, size_t ws_bytes) {
+// Capacity-dependent tail: two entry buffers, the work items and the per-item
+// chunk images of the forward pass.
+struct Tail {
+    size_t a, b, items, partial, end;
+    long long icap;
+};
+
+Tail raster_tail(const RasterLayout& L, long long cap, int tile_px) {
+    Tail t;
+    t.icap = items_capacity(L.n_tiles, cap);
+    Layout lay;
+    lay.off = L.fixed;
+    t.a = lay.take(8 * (size_t)cap);
+    t.b = lay.take(8 * (size_t)cap);
+    t.items = lay.take(8 * (size_t)t.icap);
+    t.partial = lay.take(4 * (size_t)tile_px * (size_t)t.icap);
+    t.end = lay.off;
+    return t;
+}
+
+// Largest key capacity (a multiple of 32) whose tail fits in ws_bytes.
+long long capacity_of(const RasterLayout& L, size_t ws_bytes, int tile_px) {
     if (ws_bytes <= L.fixed) return 0;
-    const size_t half = (ws_bytes - L.fixed) / 2;
-    long long cap = (long long)(half / 256) * 32;
+    const double per = 16.0 + (8.0 + 4.0 * tile_px) / kChunk;
+    const double fixed_tail = (double)L.n_tiles * (8.0 + 4.0 * tile_px) + 4096.0;
+    double est = ((double)(ws_bytes - L.fixed) - fixed_tail) / per;
+    long long cap = est > 0 ? ((long long)est / 32) * 32 : 0;
     if (cap > 0xffffffe0ll) cap = 0xffffffe0ll;
+    while (cap + 32 <= 0xffffffe0ll && raster_tail(L, cap + 32, tile_px).end <= ws_bytes) cap += 32;
+    while (cap > 0 && raster_tail(L, cap, tile_px).end > ws_bytes) cap -= 32;
     return cap;
 }
 
@@ -649,41 +722,56 @@ CamF camf(const r2g_camera* c) {
     return f;
 }
 
+struct FwdArgs {
+    const float4* rec;
+    const uint2* ranges;
+    const uint64_t* sorted;
+    const uint64_t* items;
+    const WsStatus* item_st;
+    float* partial;
+    const uint32_t* item_off;
+};
+
+template <int TW, int TH, bool COUNT>
+void fwd_shape(const FwdArgs& f, long long M, const RasterLayout& L, long long icap, int H, int W, float Tq,
+               float* image, WsStatus* st, cudaStream_t s) {
+    k_splat_fwd<TW, TH, COUNT><<<(unsigned)icap, TW * TH / 2, 0, s>>>(f.rec, f.ranges, f.sorted, f.items, f.item_st,
+                                                                       f.partial, M, L.tiles_x, L.tiles_per_view, H,
+                                                                       W, Tq, image, st);
+    k_splat_reduce<TW, TH><<<(unsigned)L.n_tiles, 128, 0, s>>>(f.ranges, f.item_off, f.partial, L.tiles_x,
+                                                                 L.tiles_per_view, H, W, image);
+}
+
 template <bool COUNT>
-void launch_fwd(int tw, int th, const float4* rec, const uint2* ranges, const uint64_t* sorted, long long M,
-                const RasterLayout& L, int H, int W, float Tq, float* image, WsStatus* st, cudaStream_t s) {
-    const unsigned grid = (unsigned)L.n_tiles;
+void launch_fwd(int tw, int th, const FwdArgs& f, long long M, const RasterLayout& L, long long icap, int H, int W,
+                float Tq, float* image, WsStatus* st, cudaStream_t s) {
     if (tw == 16 && th == 16)
-        k_splat_fwd<16, 16, COUNT><<<grid, 128, 0, s>>>(rec, ranges, sorted, M, L.tiles_x, L.tiles_per_view, H, W, Tq,
-                                                        image, st);
+        fwd_shape<16, 16, COUNT>(f, M, L, icap, H, W, Tq, image, st, s);
     else if (tw == 8 && th == 8)
-        k_splat_fwd<8, 8, COUNT><<<grid, 32, 0, s>>>(rec, ranges, sorted, M, L.tiles_x, L.tiles_per_view, H, W, Tq,
-                                                     image, st);
+        fwd_shape<8, 8, COUNT>(f, M, L, icap, H, W, Tq, image, st, s);
     else
-        k_splat_fwd<32, 8, COUNT><<<grid, 128, 0, s>>>(rec, ranges, sorted, M, L.tiles_x, L.tiles_per_view, H, W, Tq,
-                                                       image, st);
+        fwd_shape<32, 8, COUNT>(f, M, L, icap, H, W, Tq, image, st, s);
 }
 
-void launch_bwd(int tw, int th, const float4* rec, const uint2* ranges, const uint64_t* sorted, long long M,
-                const RasterLayout& L, int H, int W, float Tq, const float* dimage, float4* mom, cudaStream_t s) {
-    const unsigned grid = (unsigned)L.n_tiles;
+void launch_bwd(int tw, int th, const float4* rec, const uint2* ranges, const uint64_t* sorted,
+                const uint64_t* items, const WsStatus* item_st, long long icap, long long M, const RasterLayout& L,
+                int H, int W, float Tq, const float* dimage, float4* mom, cudaStream_t s) {
+    const unsigned grid = (unsigned)icap;
     if (tw == 16 && th == 16)
-        k_splat_bwd<16, 16><<<grid, kBwdThreads, 0, s>>>(rec, ranges, sorted, M, L.tiles_x, L.tiles_per_view, H, W,
-                                                         Tq, dimage, mom);
+        k_splat_bwd<16, 16><<<grid, kBwdThreads, 0, s>>>(rec, ranges, sorted, items, item_st, M, L.tiles_x,
+                                                         L.tiles_per_view, H, W, Tq, dimage, mom);
     else if (tw == 8 && th == 8)
-        k_splat_bwd<8, 8><<<grid, kBwdThreads, 0, s>>>(rec, ranges, sorted, M, L.tiles_x, L.tiles_per_view, H, W,
-                                                       Tq, dimage, mom);
+        k_splat_bwd<8, 8><<<grid, kBwdThreads, 0, s>>>(rec, ranges, sorted, items, item_st, M, L.tiles_x,
+                                                       L.tiles_per_view, H, W, Tq, dimage, mom);
     else
-        k_splat_bwd<32, 8><<<grid, kBwdThreads, 0, s>>>(rec, ranges, sorted, M, L.tiles_x, L.tiles_per_view, H, W,
-                                                        Tq, dimage, mom);
+        k_splat_bwd<32, 8><<<grid, kBwdThreads, 0, s>>>(rec, ranges, sorted, items, item_st, M, L.tiles_x,
+                                                        L.tiles_per_view, H, W, Tq, dimage, mom);
 }
 
-uint64_t* sorted_buffer(char* base, const RasterLayout& L, long long cap) {
-    uint64_t* a = reinterpret_cast<uint64_t*>(base + L.fixed);
-    uint64_t* b = reinterpret_cast<uint64_t*>(base + L.fixed + align_up(8 * (size_t)cap));
+uint64_t* sorted_buffer(char* base, const RasterLayout& L, const Tail& t) {
     const int bits = bits_for(L.n_tiles);
     const int passes = (bits + kRadixBits - 1) / kRadixBits;
-    return (passes & 1) ? b : a;
+    return reinterpret_cast<uint64_t*>(base + ((passes & 1) ? t.b : t.a));
 }
 
 }  // namespace
@@ -699,7 +787,7 @@ R2G_API size_t r2g_raster_workspace_size(int64_t M, int32_t V, const r2g_camera*
         return 0;
     }
     const RasterLayout L = raster_layout(M, V, cam, opts);
-    return L.fixed + 2 * align_up(8 * (size_t)key_capacity);
+    return raster_tail(L, key_capacity, opts->tile_w * opts->tile_h).end;
 }
 
 R2G_API r2g_status r2g_project(int64_t M, const float* mean, const float* scale, const float* quat, const float* rho,
@@ -728,8 +816,10 @@ R2G_API r2g_status r2g_rasterize(int64_t M, const float* mean, const float* scal
     if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(R2G_E_INVAL, "workspace must be 256-byte aligned");
     if (reinterpret_cast<uintptr_t>(quat) % 16) return fail(R2G_E_INVAL, "quat must be 16-byte aligned");
     const RasterLayout L = raster_layout(M, V, cam, opts);
-    const long long cap = capacity_of(L, ws_bytes);
+    const int tpx = opts->tile_w * opts->tile_h;
+    const long long cap = capacity_of(L, ws_bytes, tpx);
     if (cap < 32) return fail(R2G_E_INVAL, "workspace of %zu bytes holds no list entries", ws_bytes);
+    const Tail T = raster_tail(L, cap, tpx);
     char* base = static_cast<char*>(ws);
     WsStatus* st = reinterpret_cast<WsStatus*>(base + L.status);
     float4* rec = reinterpret_cast<float4*>(base + L.rec);
@@ -737,8 +827,12 @@ R2G_API r2g_status r2g_rasterize(int64_t M, const float* mean, const float* scal
     auto* partials = reinterpret_cast<unsigned long long*>(base + L.partials);
     uint2* ranges = reinterpret_cast<uint2*>(base + L.ranges);
     uint32_t* scratch = reinterpret_cast<uint32_t*>(base + L.scratch);
-    uint64_t* a = reinterpret_cast<uint64_t*>(base + L.fixed);
-    uint64_t* b = reinterpret_cast<uint64_t*>(base + L.fixed + align_up(8 * (size_t)cap));
+    uint64_t* a = reinterpret_cast<uint64_t*>(base + T.a);
+    uint64_t* b = reinterpret_cast<uint64_t*>(base + T.b);
+    WsStatus* item_st = reinterpret_cast<WsStatus*>(base + L.item_status);
+    uint32_t* item_off = reinterpret_cast<uint32_t*>(base + L.item_off);
+    uint64_t* items = reinterpret_cast<uint64_t*>(base + T.items);
+    float* partial = reinterpret_cast<float*>(base + T.partial);
     cudaMemsetAsync(st, 0, sizeof(WsStatus), stream);
     Params G{mean, scale, quat, rho};
     const CamF cf = camf(cam);
@@ -752,20 +846,21 @@ R2G_API r2g_status r2g_rasterize(int64_t M, const float* mean, const float* scal
     emit_lists(op, L.n_rec, partials, st, a, (unsigned long long)cap, stream);
     prof_end(P_EMIT, stream);
     prof_begin(P_SORT, stream);
-    uint64_t* sorted = radix_sort_u64(a, b, scratch, st, bits_for(L.n_tiles), stream);
+    uint64_t* sorted = radix_sort_u64(a, b, scratch, st, bits_for(L.n_tiles), sort_blocks_for(cap), stream);
     prof_end(P_SORT, stream);
     prof_begin(P_RANGES, stream);
     build_ranges(sorted, st, ranges, L.n_tiles, stream);
+    build_items(ranges, L.n_tiles, item_st, item_off, items, T.icap, partials, stream);
     prof_end(P_RANGES, stream);
     const float Tq = -0.5f * kLog2e * opts->Q;
     prof_begin(P_SPLAT_FWD, stream);
+    const FwdArgs fa{rec, ranges, sorted, items, item_st, partial, item_off};
     if (opts->count_pairs)
-        launch_fwd<true>(opts->tile_w, opts->tile_h, rec, ranges, sorted, M, L, cam->H, cam->W, Tq, image, st, stream);
+        launch_fwd<true>(opts->tile_w, opts->tile_h, fa, M, L, T.icap, cam->H, cam->W, Tq, image, st, stream);
     else
-        launch_fwd<false>(opts->tile_w, opts->tile_h, rec, ranges, sorted, M, L, cam->H, cam->W, Tq, image, st,
-                          stream);
+        launch_fwd<false>(opts->tile_w, opts->tile_h, fa, M, L, T.icap, cam->H, cam->W, Tq, image, st, stream);
     prof_end(P_SPLAT_FWD, stream);
-    note_launches(1 + 3 + 3 * ((bits_for(L.n_tiles) + kRadixBits - 1) / kRadixBits) + 1 + 1);
+    note_launches(1 + 3 + 3 * ((bits_for(L.n_tiles) + kRadixBits - 1) / kRadixBits) + 1 + 3 + 2);
     return check_launch("r2g_rasterize");
 }
 
@@ -781,17 +876,22 @@ R2G_API r2g_status r2g_rasterize_backward(int64_t M, const float* mean, const fl
     if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(R2G_E_INVAL, "workspace must be 256-byte aligned");
     if (reinterpret_cast<uintptr_t>(quat) % 16) return fail(R2G_E_INVAL, "quat must be 16-byte aligned");
     const RasterLayout L = raster_layout(M, V, cam, opts);
-    const long long cap = capacity_of(L, ws_bytes);
+    const int tpx = opts->tile_w * opts->tile_h;
+    const long long cap = capacity_of(L, ws_bytes, tpx);
     if (cap < 32) return fail(R2G_E_INVAL, "workspace of %zu bytes holds no list entries", ws_bytes);
+    const Tail T = raster_tail(L, cap, tpx);
     char* base = static_cast<char*>(ws);
     const float4* rec = reinterpret_cast<const float4*>(base + L.rec);
     const uint2* ranges = reinterpret_cast<const uint2*>(base + L.ranges);
     float4* mom = reinterpret_cast<float4*>(base + L.mom);
-    const uint64_t* sorted = sorted_buffer(base, L, cap);
+    const uint64_t* sorted = sorted_buffer(base, L, T);
+    const uint64_t* items = reinterpret_cast<const uint64_t*>(base + T.items);
+    const WsStatus* item_st = reinterpret_cast<const WsStatus*>(base + L.item_status);
     cudaMemsetAsync(mom, 0, 32 * (size_t)L.n_rec, stream);
     const float Tq = -0.5f * kLog2e * opts->Q;
     prof_begin(P_SPLAT_BWD, stream);
-    launch_bwd(opts->tile_w, opts->tile_h, rec, ranges, sorted, M, L, cam->H, cam->W, Tq, dimage, mom, stream);
+    launch_bwd(opts->tile_w, opts->tile_h, rec, ranges, sorted, items, item_st, T.icap, M, L, cam->H, cam->W, Tq,
+               dimage, mom, stream);
     prof_end(P_SPLAT_BWD, stream);
     Params G{mean, scale, quat, rho};
     prof_begin(P_PROJECT_BWD, stream);
@@ -809,7 +909,10 @@ R2G_API r2g_status r2g_raster_lists(int64_t M, int32_t V, const r2g_camera* cam,
     if (e) return e;
     if (!ws || !ranges_out || !ids || !n_entries) return fail(R2G_E_INVAL, "NULL pointer");
     const RasterLayout L = raster_layout(M, V, cam, opts);
-    const long long cap = capacity_of(L, ws_bytes);
+    const int tpx = opts->tile_w * opts->tile_h;
+    const long long cap = capacity_of(L, ws_bytes, tpx);
+    if (cap < 32) return fail(R2G_E_INVAL, "workspace of %zu bytes holds no list entries", ws_bytes);
+    const Tail T = raster_tail(L, cap, tpx);
     const char* base = static_cast<const char*>(ws);
     WsStatus st;
     if (cudaMemcpyAsync(&st, base + L.status, sizeof(st), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
@@ -818,7 +921,7 @@ R2G_API r2g_status r2g_raster_lists(int64_t M, int32_t V, const r2g_camera* cam,
     *n_entries = (int64_t)st.needed;
     if (st.status == R2G_E_CAPACITY) return fail(R2G_E_CAPACITY, "lists overflowed the workspace");
     if ((long long)st.n_keys > capacity) return fail(R2G_E_CAPACITY, "ids buffer too small");
-    const uint64_t* sorted = sorted_buffer(const_cast<char*>(base), L, cap);
+    const uint64_t* sorted = sorted_buffer(const_cast<char*>(base), L, T);
     if (cudaMemcpyAsync(ranges_out, base + L.ranges, 8 * (size_t)L.n_tiles, cudaMemcpyDeviceToDevice, stream) !=
             cudaSuccess ||
         (st.n_keys > 0 &&

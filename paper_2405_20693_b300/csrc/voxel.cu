@@ -199,11 +199,19 @@ constexpr int kVoxThreads = 128;
 template <bool COUNT>
 __global__ void __launch_bounds__(kVoxThreads) k_vox_fwd(const float4* __restrict__ rec,
                                                          const uint2* __restrict__ ranges,
-                                                         const uint64_t* __restrict__ sorted, long long M,
+                                                         const uint64_t* __restrict__ sorted,
+                                                         const uint64_t* __restrict__ items,
+                                                         const WsStatus* __restrict__ item_st,
+                                                         float* __restrict__ partial, long long M,
                                                          const __grid_constant__ Grids grids, float Tq,
                                                          float* __restrict__ vol, WsStatus* st) {
+    static_assert(kChunk == kVoxThreads, "one staging batch per item");
     __shared__ float4 s_r[kVoxThreads][4];
-    const long long brick = blockIdx.x;
+    const unsigned long long it = blockIdx.x;
+    if (it >= item_st->n_keys) return;
+    const uint64_t item = items[it];
+    const long long brick = (long long)(item >> 32);
+    const uint32_t chunk = (uint32_t)item;
     const int g = grid_of_brick(grids, brick);
     const GridF& gf = grids.g[g];
     const long long lb = brick - gf.brick_base;
@@ -219,8 +227,11 @@ __global__ void __launch_bounds__(kVoxThreads) k_vox_fwd(const float4* __restric
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
     unsigned int cnt = 0;
     const uint2 rg = ranges[brick];
-    for (uint32_t base = rg.x; base < rg.y; base += kVoxThreads) {
-        const int n = min((uint32_t)kVoxThreads, rg.y - base);
+    const uint32_t start = rg.x + chunk * kChunk;
+    const uint32_t end = min(start + (uint32_t)kChunk, rg.y);
+    const uint32_t nch = (rg.y - rg.x + kChunk - 1) / kChunk;
+    for (uint32_t base = start; base < end; base += kVoxThreads) {
+        const int n = min((uint32_t)kVoxThreads, end - base);
         __syncthreads();
         if (t < n) {
             const uint32_t gid = (uint32_t)sorted[base + t];
@@ -247,11 +258,16 @@ __global__ void __launch_bounds__(kVoxThreads) k_vox_fwd(const float4* __restric
             }
         }
     }
-    if (y < gf.dims[1] && z < gf.dims[2]) {
-        float* row = vol + gf.vol_base + ((long long)z * gf.dims[1] + y) * gf.dims[0];
+    if (nch == 1) {
+        if (y < gf.dims[1] && z < gf.dims[2]) {
+            float* row = vol + gf.vol_base + ((long long)z * gf.dims[1] + y) * gf.dims[0];
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-            if (x0 + k < gf.dims[0]) row[x0 + k] = acc[k];
+            for (int k = 0; k < 4; ++k)
+                if (x0 + k < gf.dims[0]) row[x0 + k] = acc[k];
+        }
+    } else {
+        float4* p = reinterpret_cast<float4*>(partial + it * (size_t)(kB * kB * kB)) + t;
+        *p = make_float4(acc[0], acc[1], acc[2], acc[3]);
     }
     if (COUNT) {
 #pragma unroll
@@ -260,15 +276,59 @@ __global__ void __launch_bounds__(kVoxThreads) k_vox_fwd(const float4* __restric
     }
 }
 
+// Bricks whose list spans several chunks: sum the chunk volumes in chunk order.
+// Bricks with an empty list get zeros (no work item writes them).
+__global__ void __launch_bounds__(kVoxThreads) k_vox_reduce(const uint2* __restrict__ ranges,
+                                                            const uint32_t* __restrict__ item_off,
+                                                            const float* __restrict__ partial,
+                                                            const __grid_constant__ Grids grids,
+                                                            float* __restrict__ vol) {
+    const long long brick = blockIdx.x;
+    const uint2 rg = ranges[brick];
+    const uint32_t nch = (rg.y - rg.x + kChunk - 1) / kChunk;
+    if (nch == 1) return;
+    const int g = grid_of_brick(grids, brick);
+    const GridF& gf = grids.g[g];
+    const long long lb = brick - gf.brick_base;
+    const int bx = (int)(lb % gf.nb[0]);
+    const int by = (int)((lb / gf.nb[0]) % gf.nb[1]);
+    const int bz = (int)(lb / ((long long)gf.nb[0] * gf.nb[1]));
+    const int t = threadIdx.x;
+    const int x0 = bx * kB + (t & 1) * 4, y = by * kB + ((t >> 1) & 7), z = bz * kB + (t >> 4);
+    const float4* base =
+        reinterpret_cast<const float4*>(partial + (nch ? (size_t)item_off[brick] * (kB * kB * kB) : 0)) + t;
+    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (uint32_t c = 0; c < nch; ++c) {
+        const float4 p = base[(size_t)c * (kB * kB * kB / 4)];
+        s.x += p.x;
+        s.y += p.y;
+        s.z += p.z;
+        s.w += p.w;
+    }
+    if (y < gf.dims[1] && z < gf.dims[2]) {
+        float* row = vol + gf.vol_base + ((long long)z * gf.dims[1] + y) * gf.dims[0];
+        const float a[4] = {s.x, s.y, s.z, s.w};
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (x0 + k < gf.dims[0]) row[x0 + k] = a[k];
+    }
+}
+
 // ------------------------------------------------------------------ backward
 
 __global__ void __launch_bounds__(kVoxThreads) k_vox_bwd(const float4* __restrict__ rec,
                                                          const uint2* __restrict__ ranges,
-                                                         const uint64_t* __restrict__ sorted, long long M,
+                                                         const uint64_t* __restrict__ sorted,
+                                                         const uint64_t* __restrict__ items,
+                                                         const WsStatus* __restrict__ item_st, long long M,
                                                          const __grid_constant__ Grids grids, float Tq,
                                                          const float* __restrict__ dvol, float4* __restrict__ mom) {
     __shared__ float s_g[kB][kB][kB];
-    const long long brick = blockIdx.x;
+    const unsigned long long it = blockIdx.x;
+    if (it >= item_st->n_keys) return;
+    const uint64_t item = items[it];
+    const long long brick = (long long)(item >> 32);
+    const uint32_t chunk = (uint32_t)item;
     const int g = grid_of_brick(grids, brick);
     const GridF& gf = grids.g[g];
     const long long lb = brick - gf.brick_base;
@@ -287,7 +347,8 @@ __global__ void __launch_bounds__(kVoxThreads) k_vox_bwd(const float4* __restric
     const uint2 rg = ranges[brick];
     const float4* grec = rec + 4 * (size_t)g * (size_t)M;
     float4* gmom = mom + 3 * (size_t)g * (size_t)M;
-    for (uint32_t e = rg.x + threadIdx.x; e < rg.y; e += kVoxThreads) {
+    const uint32_t e = rg.x + chunk * kChunk + threadIdx.x;
+    if (e < rg.y) {
         const uint32_t gid = (uint32_t)sorted[e];
         const float4 r0 = grec[4 * (size_t)gid], r1 = grec[4 * (size_t)gid + 1];
         const float4 r2 = grec[4 * (size_t)gid + 2], r3 = grec[4 * (size_t)gid + 3];
@@ -418,7 +479,7 @@ __global__ void __launch_bounds__(128) k_vox_chain(Params G, const __grid_consta
 // ------------------------------------------------------------------ host side
 
 struct VoxLayout {
-    size_t status, rec, rect, partials, ranges, mom, scratch, fixed;
+    size_t status, rec, rect, partials, ranges, mom, scratch, item_status, item_off, fixed;
     long long n_rec, n_bricks, n_vox;
 };
 
@@ -461,22 +522,45 @@ VoxLayout vox_layout(int64_t M, const Grids& grids) {
     L.ranges = lay.take(8 * (size_t)L.n_bricks);
     L.mom = lay.take(48 * (size_t)L.n_rec);
     L.scratch = lay.take(sort_scratch_bytes());
+    L.item_status = lay.take(sizeof(WsStatus));
+    L.item_off = lay.take(4 * (size_t)L.n_bricks);
     L.fixed = lay.off;
     return L;
 }
 
+struct VTail {
+    size_t a, b, items, partial, end;
+    long long icap;
+};
+
+VTail vox_tail(const VoxLayout& L, long long cap) {
+    VTail t;
+    t.icap = items_capacity(L.n_bricks, cap);
+    Layout lay;
+    lay.off = L.fixed;
+    t.a = lay.take(8 * (size_t)cap);
+    t.b = lay.take(8 * (size_t)cap);
+    t.items = lay.take(8 * (size_t)t.icap);
+    t.partial = lay.take(4 * (size_t)(kB * kB * kB) * (size_t)t.icap);
+    t.end = lay.off;
+    return t;
+}
+
 long long vox_capacity(const VoxLayout& L, size_t ws_bytes) {
     if (ws_bytes <= L.fixed) return 0;
-    long long cap = (long long)(((ws_bytes - L.fixed) / 2) / 256) * 32;
+    const double per = 16.0 + (8.0 + 4.0 * kB * kB * kB) / kChunk;
+    const double fixed_tail = (double)L.n_bricks * (8.0 + 4.0 * kB * kB * kB) + 4096.0;
+    const double est = ((double)(ws_bytes - L.fixed) - fixed_tail) / per;
+    long long cap = est > 0 ? ((long long)est / 32) * 32 : 0;
     if (cap > 0xffffffe0ll) cap = 0xffffffe0ll;
+    while (cap + 32 <= 0xffffffe0ll && vox_tail(L, cap + 32).end <= ws_bytes) cap += 32;
+    while (cap > 0 && vox_tail(L, cap).end > ws_bytes) cap -= 32;
     return cap;
 }
 
-uint64_t* vox_sorted(char* base, const VoxLayout& L, long long cap) {
-    uint64_t* a = reinterpret_cast<uint64_t*>(base + L.fixed);
-    uint64_t* b = reinterpret_cast<uint64_t*>(base + L.fixed + align_up(8 * (size_t)cap));
+uint64_t* vox_sorted(char* base, const VoxLayout& L, const VTail& t) {
     const int passes = (bits_for(L.n_bricks) + kRadixBits - 1) / kRadixBits;
-    return (passes & 1) ? b : a;
+    return reinterpret_cast<uint64_t*>(base + ((passes & 1) ? t.b : t.a));
 }
 
 r2g_status check_params(int64_t M, const float* mean, const float* scale, const float* quat, const float* rho) {
@@ -497,7 +581,7 @@ R2G_API size_t r2g_voxel_workspace_size(int64_t M, int32_t G, const r2g_grid* gr
     if ((long long)M * G >= (1ll << 31)) return 0;
     if (key_capacity < 1 || key_capacity > 0xffffffe0ll) return 0;
     const VoxLayout L = vox_layout(M, gr);
-    return L.fixed + 2 * align_up(8 * (size_t)key_capacity);
+    return vox_tail(L, key_capacity).end;
 }
 
 namespace r2g {
@@ -516,6 +600,7 @@ r2g_status voxelize_impl(int64_t M, const float* mean, const float* scale, const
     const VoxLayout L = vox_layout(M, gr);
     const long long cap = vox_capacity(L, ws_bytes);
     if (cap < 32) return fail(R2G_E_INVAL, "workspace of %zu bytes holds no list entries", ws_bytes);
+    const VTail T = vox_tail(L, cap);
     char* base = static_cast<char*>(ws);
     WsStatus* st = reinterpret_cast<WsStatus*>(base + L.status);
     float4* rec = reinterpret_cast<float4*>(base + L.rec);
@@ -523,8 +608,12 @@ r2g_status voxelize_impl(int64_t M, const float* mean, const float* scale, const
     auto* partials = reinterpret_cast<unsigned long long*>(base + L.partials);
     uint2* ranges = reinterpret_cast<uint2*>(base + L.ranges);
     uint32_t* scratch = reinterpret_cast<uint32_t*>(base + L.scratch);
-    uint64_t* a = reinterpret_cast<uint64_t*>(base + L.fixed);
-    uint64_t* b = reinterpret_cast<uint64_t*>(base + L.fixed + align_up(8 * (size_t)cap));
+    uint64_t* a = reinterpret_cast<uint64_t*>(base + T.a);
+    uint64_t* b = reinterpret_cast<uint64_t*>(base + T.b);
+    WsStatus* item_st = reinterpret_cast<WsStatus*>(base + L.item_status);
+    uint32_t* item_off = reinterpret_cast<uint32_t*>(base + L.item_off);
+    uint64_t* items = reinterpret_cast<uint64_t*>(base + T.items);
+    float* partial = reinterpret_cast<float*>(base + T.partial);
     cudaMemsetAsync(st, 0, sizeof(WsStatus), stream);
     Params P{mean, scale, quat, rho};
     prof_begin(P_VOX_PROJECT, stream);
@@ -542,18 +631,22 @@ r2g_status voxelize_impl(int64_t M, const float* mean, const float* scale, const
     emit_lists(op, L.n_rec, partials, st, a, (unsigned long long)cap, stream);
     prof_end(P_EMIT, stream);
     prof_begin(P_SORT, stream);
-    uint64_t* sorted = radix_sort_u64(a, b, scratch, st, bits_for(L.n_bricks), stream);
+    uint64_t* sorted = radix_sort_u64(a, b, scratch, st, bits_for(L.n_bricks), sort_blocks_for(cap), stream);
     prof_end(P_SORT, stream);
     prof_begin(P_RANGES, stream);
     build_ranges(sorted, st, ranges, L.n_bricks, stream);
+    build_items(ranges, L.n_bricks, item_st, item_off, items, T.icap, partials, stream);
     prof_end(P_RANGES, stream);
     const float Tq = -0.5f * kLog2e * Q3;
-    note_launches(1 + 3 + 3 * ((bits_for(L.n_bricks) + kRadixBits - 1) / kRadixBits) + 1 + 1);
+    note_launches(1 + 3 + 3 * ((bits_for(L.n_bricks) + kRadixBits - 1) / kRadixBits) + 1 + 3 + 2);
     prof_begin(P_VOX_FWD, stream);
     if (count)
-        k_vox_fwd<true><<<(unsigned)L.n_bricks, kVoxThreads, 0, stream>>>(rec, ranges, sorted, M, gr, Tq, vol, st);
+        k_vox_fwd<true><<<(unsigned)T.icap, kVoxThreads, 0, stream>>>(rec, ranges, sorted, items, item_st, partial, M,
+                                                                       gr, Tq, vol, st);
     else
-        k_vox_fwd<false><<<(unsigned)L.n_bricks, kVoxThreads, 0, stream>>>(rec, ranges, sorted, M, gr, Tq, vol, st);
+        k_vox_fwd<false><<<(unsigned)T.icap, kVoxThreads, 0, stream>>>(rec, ranges, sorted, items, item_st, partial,
+                                                                        M, gr, Tq, vol, st);
+    k_vox_reduce<<<(unsigned)L.n_bricks, kVoxThreads, 0, stream>>>(ranges, item_off, partial, gr, vol);
     prof_end(P_VOX_FWD, stream);
     return check_launch("r2g_voxelize");
 }
@@ -587,15 +680,19 @@ R2G_API r2g_status r2g_voxelize_backward(int64_t M, const float* mean, const flo
     const VoxLayout L = vox_layout(M, gr);
     const long long cap = vox_capacity(L, ws_bytes);
     if (cap < 32) return fail(R2G_E_INVAL, "workspace of %zu bytes holds no list entries", ws_bytes);
+    const VTail T = vox_tail(L, cap);
     char* base = static_cast<char*>(ws);
     const float4* rec = reinterpret_cast<const float4*>(base + L.rec);
     const uint2* ranges = reinterpret_cast<const uint2*>(base + L.ranges);
     float4* mom = reinterpret_cast<float4*>(base + L.mom);
-    const uint64_t* sorted = vox_sorted(base, L, cap);
+    const uint64_t* sorted = vox_sorted(base, L, T);
+    const uint64_t* items = reinterpret_cast<const uint64_t*>(base + T.items);
+    const WsStatus* item_st = reinterpret_cast<const WsStatus*>(base + L.item_status);
     cudaMemsetAsync(mom, 0, 48 * (size_t)L.n_rec, stream);
     const float Tq = -0.5f * kLog2e * Q3;
     prof_begin(P_VOX_BWD, stream);
-    k_vox_bwd<<<(unsigned)L.n_bricks, kVoxThreads, 0, stream>>>(rec, ranges, sorted, M, gr, Tq, dvol, mom);
+    k_vox_bwd<<<(unsigned)T.icap, kVoxThreads, 0, stream>>>(rec, ranges, sorted, items, item_st, M, gr, Tq, dvol,
+                                                             mom);
     prof_end(P_VOX_BWD, stream);
     Params P{mean, scale, quat, rho};
     prof_begin(P_VOX_CHAIN, stream);
@@ -614,6 +711,8 @@ R2G_API r2g_status r2g_voxel_lists(int64_t M, int32_t G, const r2g_grid* grids, 
     if (M < 1 || !ws || !ranges_out || !ids || !n_entries) return fail(R2G_E_INVAL, "bad argument");
     const VoxLayout L = vox_layout(M, gr);
     const long long cap = vox_capacity(L, ws_bytes);
+    if (cap < 32) return fail(R2G_E_INVAL, "workspace of %zu bytes holds no list entries", ws_bytes);
+    const VTail T = vox_tail(L, cap);
     const char* base = static_cast<const char*>(ws);
     WsStatus st;
     if (cudaMemcpyAsync(&st, base + L.status, sizeof(st), cudaMemcpyDeviceToHost, stream) != cudaSuccess ||
@@ -622,7 +721,7 @@ R2G_API r2g_status r2g_voxel_lists(int64_t M, int32_t G, const r2g_grid* grids, 
     *n_entries = (int64_t)st.needed;
     if (st.status == R2G_E_CAPACITY) return fail(R2G_E_CAPACITY, "lists overflowed the workspace");
     if ((long long)st.n_keys > capacity) return fail(R2G_E_CAPACITY, "ids buffer too small");
-    const uint64_t* sorted = vox_sorted(const_cast<char*>(base), L, cap);
+    const uint64_t* sorted = vox_sorted(const_cast<char*>(base), L, T);
     if (cudaMemcpyAsync(ranges_out, base + L.ranges, 8 * (size_t)L.n_bricks, cudaMemcpyDeviceToDevice, stream) !=
             cudaSuccess ||
         (st.n_keys > 0 &&
