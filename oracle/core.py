@@ -48,13 +48,15 @@ def lib():
             L.orc_render_cs.restype = None
             L.orc_render_cs.argtypes = [i64, _D, _D, _D, _D, _D, i32, _D, dbl, i32, i64, i32, dbl, _D]
             L.orc_render_backward.restype = None
-            L.orc_render_backward.argtypes = [i64, _D, _D, _D, _D, _D, i32, _D, dbl, _D, _D, _D, _D, _D]
+            L.orc_render_backward.argtypes = [i64, _D, _D, _D, _D, _D, i32, _D, dbl, _D, _D, _D, _D, _D, _D, _D, _D,
+                                              _D]
             L.orc_voxelize.restype = i64
             L.orc_voxelize.argtypes = [i64, _D, _D, _D, _D, _D, i32, dbl, i32, _D, _D]
             L.orc_voxelize_cs.restype = None
             L.orc_voxelize_cs.argtypes = [i64, _D, _D, _D, _D, _D, i32, dbl, i32, i64, i32, dbl, _D]
             L.orc_voxelize_backward.restype = None
-            L.orc_voxelize_backward.argtypes = [i64, _D, _D, _D, _D, _D, i32, dbl, _D, _D, _D, _D, _D]
+            L.orc_voxelize_backward.argtypes = [i64, _D, _D, _D, _D, _D, i32, dbl, _D, _D, _D, _D, _D, _D, _D, _D,
+                                                _D]
             L.orc_render_exact.restype = None
             L.orc_render_exact.argtypes = [i64, _D, _D, _D, _D, _D, i32, _D, _D]
             L.orc_ray_pair.restype = None
@@ -137,16 +139,22 @@ def render_cs(G, views, cam, Q, kind, i, comp, h=1e-20):
     return out
 
 
-def render_backward(G, views, cam, dimg, Q=9.0):
-    """Hand adjoint: returns (dmean, dscale, dquat, drho) in float64."""
+def _grad_arrays(M):
+    return np.zeros((M, 3)), np.zeros((M, 3)), np.zeros((M, 4)), np.zeros(M)
+
+
+def render_backward(G, views, cam, dimg, Q=9.0, want_band=False):
+    """Hand adjoint: (dmean, dscale, dquat, drho) in float64; with want_band also the
+    per-parameter gate-band bound (summed |contribution| of pairs with |q - Q| <= 1e-4 Q)."""
     g = _G(G)
     views = _d(views)
     cv = _camv(cam)
     dimg = _d(dimg)
-    dm, ds, dq, dr = np.zeros((g.M, 3)), np.zeros((g.M, 3)), np.zeros((g.M, 4)), np.zeros(g.M)
+    out = _grad_arrays(g.M)
+    band = _grad_arrays(g.M) if want_band else (None,) * 4
     lib().orc_render_backward(g.M, *g.ptrs(), _p(views), views.shape[0], _p(cv), float(Q), _p(dimg),
-                              _p(dm), _p(ds), _p(dq), _p(dr))
-    return dm, ds, dq, dr
+                              *(_p(a) for a in out), *((_p(a) if a is not None else None) for a in band))
+    return (out, band) if want_band else out
 
 
 def render_exact(G, views, cam):
@@ -202,14 +210,16 @@ def voxelize_cs(G, gdescs, Q3, kind, i, comp, h=1e-20):
     return out
 
 
-def voxelize_backward(G, gdescs, dvol, Q3=11.345):
+def voxelize_backward(G, gdescs, dvol, Q3=11.345, want_band=False):
     g = _G(G)
     gd, ng, n = _grids(gdescs)
     dvol = _d(dvol).ravel()
     assert dvol.size == n
-    dm, ds, dq, dr = np.zeros((g.M, 3)), np.zeros((g.M, 3)), np.zeros((g.M, 4)), np.zeros(g.M)
-    lib().orc_voxelize_backward(g.M, *g.ptrs(), _p(gd), ng, float(Q3), _p(dvol), _p(dm), _p(ds), _p(dq), _p(dr))
-    return dm, ds, dq, dr
+    out = _grad_arrays(g.M)
+    band = _grad_arrays(g.M) if want_band else (None,) * 4
+    lib().orc_voxelize_backward(g.M, *g.ptrs(), _p(gd), ng, float(Q3), _p(dvol), *(_p(a) for a in out),
+                                *((_p(a) if a is not None else None) for a in band))
+    return (out, band) if want_band else out
 
 
 # ----------------------------------------------------------------------------- R32 replica

@@ -326,10 +326,97 @@ void sigma_backward(const M3<double>& dSigma, const M3<double>& R, const double*
     quat_backward(qn, qnorm, dR, dq);
 }
 
+// Chain rule from the record gradient drec = d(rho_hat, p^x, p^y, a, b, c) of one
+// (Gaussian, view) to the parameters of Gaussian i (accumulated into g).
+void chain_record(const Proj<double>& P, const M3<double>& Sigma, const M3<double>& R, const double qn[4],
+                  double qnorm, const M3<double>& Wm, const Cam& cam, const ParamsT<double>& G, int64_t i,
+                  const double drec[6], Grad g, int64_t oi) {
+    const double d_rhohat = drec[0], d_ph0 = drec[1], d_ph1 = drec[2], da = drec[3], db = drec[4], dc = drec[5];
+    const double a = P.conic[0], b = P.conic[1], c = P.conic[2];
+    // rho_hat = mu rho
+    g.rho[oi] += d_rhohat * P.mu;
+    const double dmu = d_rhohat * G.rho[i];
+    // mu = sqrt(2 pi d3 / d2)
+    const double dd3 = dmu * P.mu / (2.0 * P.d3);
+    const double dd2 = -dmu * P.mu / (2.0 * P.d2);
+    // conic = Sigma^^{-1}: full-matrix gradient Gc = [[da, db/2], [db/2, dc]];
+    // dL/dSigma^ = -C Gc C with C the conic.
+    const double C2[2][2] = {{a, b}, {b, c}};
+    const double Gc[2][2] = {{da, 0.5 * db}, {0.5 * db, dc}};
+    double T1[2][2], dSh[2][2];
+    for (int p = 0; p < 2; ++p)
+        for (int q2 = 0; q2 < 2; ++q2) T1[p][q2] = C2[p][0] * Gc[0][q2] + C2[p][1] * Gc[1][q2];
+    for (int p = 0; p < 2; ++p)
+        for (int q2 = 0; q2 < 2; ++q2) dSh[p][q2] = -(T1[p][0] * C2[0][q2] + T1[p][1] * C2[1][q2]);
+    // d2 = |Sigma^|: d d2 / d Sigma^ = cofactor(Sigma^) = [[gamma, -beta], [-beta, alpha]]
+    dSh[0][0] += dd2 * P.sh[2];
+    dSh[1][1] += dd2 * P.sh[0];
+    dSh[0][1] += -dd2 * P.sh[1];
+    dSh[1][0] += -dd2 * P.sh[1];
+    // Sigma~ gradient: top-left block from Sigma^, plus d3 = |Sigma~| (cofactor)
+    M3<double> dSt{};
+    for (int p = 0; p < 2; ++p)
+        for (int q2 = 0; q2 < 2; ++q2) dSt.a[p][q2] += dSh[p][q2];
+    M3<double> cof = cofactor(P.St);
+    for (int p = 0; p < 3; ++p)
+        for (int q2 = 0; q2 < 3; ++q2) dSt.a[p][q2] += dd3 * cof.a[p][q2];
+    // Sigma~ = A Sigma A^T:  dA = (G + G^T) A Sigma,  dSigma = A^T G A
+    M3<double> Gs2;
+    for (int p = 0; p < 3; ++p)
+        for (int q2 = 0; q2 < 3; ++q2) Gs2.a[p][q2] = dSt.a[p][q2] + dSt.a[q2][p];
+    M3<double> dA = mul(mul(Gs2, P.A), Sigma);
+    M3<double> dSigma = mul(mul(transpose(P.A), dSt), P.A);
+    // A = J W: dJ = dA W^T
+    M3<double> dJ = mul(dA, transpose(Wm));
+    double du[3] = {0, 0, 0};
+    const double u0 = P.u[0], u1 = P.u[1], u2 = P.u[2];
+    if (cam.beam == 1) {
+        const double L = cam.L_SD;
+        const double l = std::sqrt(u0 * u0 + u1 * u1 + u2 * u2);
+        du[2] += -(dJ.a[0][0] + dJ.a[1][1]) * L / (u2 * u2);
+        du[0] += -dJ.a[0][2] * L / (u2 * u2);
+        du[2] += dJ.a[0][2] * 2.0 * L * u0 / (u2 * u2 * u2);
+        du[1] += -dJ.a[1][2] * L / (u2 * u2);
+        du[2] += dJ.a[1][2] * 2.0 * L * u1 / (u2 * u2 * u2);
+        // third row u/l
+        const double n[3] = {u0 / l, u1 / l, u2 / l};
+        const double g3[3] = {dJ.a[2][0], dJ.a[2][1], dJ.a[2][2]};
+        const double nd = n[0] * g3[0] + n[1] * g3[1] + n[2] * g3[2];
+        for (int k = 0; k < 3; ++k) du[k] += (g3[k] - n[k] * nd) / l;
+        // p^ = L (u0/u2, u1/u2)
+        du[0] += d_ph0 * L / u2;
+        du[1] += d_ph1 * L / u2;
+        du[2] += -(d_ph0 * u0 + d_ph1 * u1) * L / (u2 * u2);
+    } else {
+        du[0] += d_ph0;
+        du[1] += d_ph1;
+    }
+    // u = W p + t
+    for (int k = 0; k < 3; ++k) g.mean[3 * oi + k] += Wm.a[0][k] * du[0] + Wm.a[1][k] * du[1] + Wm.a[2][k] * du[2];
+    sigma_backward(dSigma, R, &G.scale[3 * i], qn, qnorm, &g.scale[3 * oi], &g.quat[4 * oi]);
+}
+
+// Record gradient of one (pixel, Gaussian) pair with dL/dI = gI.
+inline void pair_record_grad(const Proj<double>& P, double dx, double dy, double q, double gI, double out[6]) {
+    const double a = P.conic[0], b = P.conic[1], c = P.conic[2];
+    const double e = std::exp(-0.5 * q);
+    const double dq = -0.5 * gI * P.rhohat * e;
+    out[0] = gI * e;
+    out[1] = -dq * (2 * a * dx + 2 * b * dy);
+    out[2] = -dq * (2 * b * dx + 2 * c * dy);
+    out[3] = dq * dx * dx;
+    out[4] = dq * 2 * dx * dy;
+    out[5] = dq * dy * dy;
+}
+
+// band (optional): per parameter, the summed |gradient contribution| of the pairs
+// whose q lies within 1e-4 Q of the gate -- the most an FP32 gate decision can move
+// that parameter's gradient.
 void render_backward(const Params& Pm, const double* views, int V, const Cam& cam, double Q,
-                     const double* dimg, Grad g) {
+                     const double* dimg, Grad g, const Grad* band) {
     const int H = cam.H, Wd = cam.W;
     const ParamsT<double> G = widen<double>(Pm);
+    std::vector<double> tm(3), ts(3), tq(4), tr(1);
     for (int v = 0; v < V; ++v) {
         const double* view = views + 12 * v;
         M3<double> Wm;
@@ -346,88 +433,35 @@ void render_backward(const Params& Pm, const double* views, int V, const Cam& ca
             centre_range(P.ph[0], std::sqrt(Q * P.sh[0]), cam.pitch_u, cam.off_u, Wd, c0, c1);
             centre_range(P.ph[1], std::sqrt(Q * P.sh[2]), cam.pitch_v, cam.off_v, H, r0, r1);
             const double a = P.conic[0], b = P.conic[1], c = P.conic[2];
-            double d_rhohat = 0, d_ph0 = 0, d_ph1 = 0, da = 0, db = 0, dc = 0;
+            double drec[6] = {0, 0, 0, 0, 0, 0};
             for (int r = r0; r <= r1; ++r) {
                 const double dy = pix_eta(r, cam) - P.ph[1];
                 for (int cc = c0; cc <= c1; ++cc) {
                     const double dx = pix_xi(cc, cam) - P.ph[0];
                     const double q = a * dx * dx + 2 * b * dx * dy + c * dy * dy;
-                    if (!(q <= Q)) continue;
                     const double gI = dIv[(int64_t)r * Wd + cc];
-                    const double e = std::exp(-0.5 * q);
-                    d_rhohat += gI * e;
-                    const double dq = -0.5 * gI * P.rhohat * e;
-                    da += dq * dx * dx;
-                    db += dq * 2 * dx * dy;
-                    dc += dq * dy * dy;
-                    const double ddx = dq * (2 * a * dx + 2 * b * dy);
-                    const double ddy = dq * (2 * b * dx + 2 * c * dy);
-                    d_ph0 -= ddx;
-                    d_ph1 -= ddy;
+                    double pr[6];
+                    if (band && std::fabs(q - Q) <= 1e-4 * Q) {
+                        pair_record_grad(P, dx, dy, q, gI, pr);
+                        std::fill(tm.begin(), tm.end(), 0.0);
+                        std::fill(ts.begin(), ts.end(), 0.0);
+                        std::fill(tq.begin(), tq.end(), 0.0);
+                        tr[0] = 0.0;
+                        const Grad tg{tm.data(), ts.data(), tq.data(), tr.data()};
+                        chain_record(P, Sigma, R, qn, qnorm, Wm, cam, G, i, pr, tg, 0);
+                        for (int k = 0; k < 3; ++k) {
+                            band->mean[3 * i + k] += std::fabs(tm[k]);
+                            band->scale[3 * i + k] += std::fabs(ts[k]);
+                        }
+                        for (int k = 0; k < 4; ++k) band->quat[4 * i + k] += std::fabs(tq[k]);
+                        band->rho[i] += std::fabs(tr[0]);
+                    }
+                    if (!(q <= Q)) continue;
+                    pair_record_grad(P, dx, dy, q, gI, pr);
+                    for (int k = 0; k < 6; ++k) drec[k] += pr[k];
                 }
             }
-            // rho_hat = mu rho
-            g.rho[i] += d_rhohat * P.mu;
-            const double dmu = d_rhohat * G.rho[i];
-            // mu = sqrt(2 pi d3 / d2)
-            const double dd3 = dmu * P.mu / (2.0 * P.d3);
-            const double dd2 = -dmu * P.mu / (2.0 * P.d2);
-            // conic = Sigma^^{-1}: full-matrix gradient Gc = [[da, db/2], [db/2, dc]];
-            // dL/dSigma^ = -C Gc C with C the conic.
-            const double C2[2][2] = {{a, b}, {b, c}};
-            const double Gc[2][2] = {{da, 0.5 * db}, {0.5 * db, dc}};
-            double T1[2][2], dSh[2][2];
-            for (int p = 0; p < 2; ++p)
-                for (int q2 = 0; q2 < 2; ++q2) T1[p][q2] = C2[p][0] * Gc[0][q2] + C2[p][1] * Gc[1][q2];
-            for (int p = 0; p < 2; ++p)
-                for (int q2 = 0; q2 < 2; ++q2) dSh[p][q2] = -(T1[p][0] * C2[0][q2] + T1[p][1] * C2[1][q2]);
-            // d2 = |Sigma^|: d d2 / d Sigma^ = cofactor(Sigma^) = [[gamma, -beta], [-beta, alpha]]
-            dSh[0][0] += dd2 * P.sh[2];
-            dSh[1][1] += dd2 * P.sh[0];
-            dSh[0][1] += -dd2 * P.sh[1];
-            dSh[1][0] += -dd2 * P.sh[1];
-            // Sigma~ gradient: top-left block from Sigma^, plus d3 = |Sigma~| (cofactor)
-            M3<double> dSt{};
-            for (int p = 0; p < 2; ++p)
-                for (int q2 = 0; q2 < 2; ++q2) dSt.a[p][q2] += dSh[p][q2];
-            M3<double> cof = cofactor(P.St);
-            for (int p = 0; p < 3; ++p)
-                for (int q2 = 0; q2 < 3; ++q2) dSt.a[p][q2] += dd3 * cof.a[p][q2];
-            // Sigma~ = A Sigma A^T:  dA = (G + G^T) A Sigma,  dSigma = A^T G A
-            M3<double> Gs2;
-            for (int p = 0; p < 3; ++p)
-                for (int q2 = 0; q2 < 3; ++q2) Gs2.a[p][q2] = dSt.a[p][q2] + dSt.a[q2][p];
-            M3<double> dA = mul(mul(Gs2, P.A), Sigma);
-            M3<double> dSigma = mul(mul(transpose(P.A), dSt), P.A);
-            // A = J W: dJ = dA W^T
-            M3<double> dJ = mul(dA, transpose(Wm));
-            double du[3] = {0, 0, 0};
-            const double u0 = P.u[0], u1 = P.u[1], u2 = P.u[2];
-            if (cam.beam == 1) {
-                const double L = cam.L_SD;
-                const double l = std::sqrt(u0 * u0 + u1 * u1 + u2 * u2);
-                du[2] += -(dJ.a[0][0] + dJ.a[1][1]) * L / (u2 * u2);
-                du[0] += -dJ.a[0][2] * L / (u2 * u2);
-                du[2] += dJ.a[0][2] * 2.0 * L * u0 / (u2 * u2 * u2);
-                du[1] += -dJ.a[1][2] * L / (u2 * u2);
-                du[2] += dJ.a[1][2] * 2.0 * L * u1 / (u2 * u2 * u2);
-                // third row u/l
-                const double n[3] = {u0 / l, u1 / l, u2 / l};
-                const double g3[3] = {dJ.a[2][0], dJ.a[2][1], dJ.a[2][2]};
-                const double nd = n[0] * g3[0] + n[1] * g3[1] + n[2] * g3[2];
-                for (int k = 0; k < 3; ++k) du[k] += (g3[k] - n[k] * nd) / l;
-                // p^ = L (u0/u2, u1/u2)
-                du[0] += d_ph0 * L / u2;
-                du[1] += d_ph1 * L / u2;
-                du[2] += -(d_ph0 * u0 + d_ph1 * u1) * L / (u2 * u2);
-            } else {
-                du[0] += d_ph0;
-                du[1] += d_ph1;
-            }
-            // u = W p + t
-            for (int k = 0; k < 3; ++k)
-                g.mean[3 * i + k] += Wm.a[0][k] * du[0] + Wm.a[1][k] * du[1] + Wm.a[2][k] * du[2];
-            sigma_backward(dSigma, R, &G.scale[3 * i], qn, qnorm, &g.scale[3 * i], &g.quat[4 * i]);
+            chain_record(P, Sigma, R, qn, qnorm, Wm, cam, G, i, drec, g, i);
         }
     }
 }
@@ -510,9 +544,23 @@ int64_t voxelize(const ParamsT<T>& Gp, int64_t M, const std::vector<GridSpec>& g
     return pairs;
 }
 
+// Chain from (d rho, d p, d P) of one Gaussian (P = Sigma^{-1}) to its parameters.
+void vox_chain(const M3<double>& P, const M3<double>& R, const double qn[4], double qnorm, const double* s,
+               double drho, const double dp[3], const M3<double>& dP, Grad g, int64_t oi) {
+    g.rho[oi] += drho;
+    for (int k = 0; k < 3; ++k) g.mean[3 * oi + k] += dp[k];
+    // P = Sigma^{-1}: dSigma = -P^T dP P^T
+    M3<double> Pt = transpose(P);
+    M3<double> dSigma = mul(mul(Pt, dP), Pt);
+    for (int j = 0; j < 3; ++j)
+        for (int k = 0; k < 3; ++k) dSigma.a[j][k] = -dSigma.a[j][k];
+    sigma_backward(dSigma, R, s, qn, qnorm, &g.scale[3 * oi], &g.quat[4 * oi]);
+}
+
 void voxelize_backward(const Params& Pm, const std::vector<GridSpec>& grids, double Q3, const double* dvol,
-                       Grad g) {
+                       Grad g, const Grad* band) {
     const ParamsT<double> Gp = widen<double>(Pm);
+    double tm[3], ts[3], tq[4], tr[1];
     int64_t off = 0;
     for (const GridSpec& gs : grids) {
         const int X = gs.dims[0], Y = gs.dims[1], Z = gs.dims[2];
@@ -547,27 +595,42 @@ void voxelize_backward(const Params& Pm, const std::vector<GridSpec>& grids, dou
                         double q = 0.0;
                         for (int j = 0; j < 3; ++j)
                             for (int k = 0; k < 3; ++k) q += d[j] * P.a[j][k] * d[k];
-                        if (!(q <= Q3)) continue;
+                        const bool in_band = band && std::fabs(q - Q3) <= 1e-4 * Q3;
+                        if (!(q <= Q3) && !in_band) continue;
                         const double gv = dV[((int64_t)z * Y + y) * X + x];
                         const double e = std::exp(-0.5 * q);
-                        drho += gv * e;
+                        // one pair: d rho = g e; q = d^T P d, d = x - p:
+                        // dq/dp = -(P + P^T) d, dq/dP_jk = d_j d_k
                         const double dq = -0.5 * gv * rho * e;
-                        // q = d^T P d, d = x - p: dq/dp = -(P + P^T) d, dq/dP_jk = d_j d_k
+                        double pdp[3];
+                        M3<double> pdP{};
                         for (int j = 0; j < 3; ++j) {
                             double Pd = 0;
                             for (int k = 0; k < 3; ++k) Pd += (P.a[j][k] + P.a[k][j]) * d[k];
-                            dp[j] -= dq * Pd;
-                            for (int k = 0; k < 3; ++k) dP.a[j][k] += dq * d[j] * d[k];
+                            pdp[j] = -dq * Pd;
+                            for (int k = 0; k < 3; ++k) pdP.a[j][k] = dq * d[j] * d[k];
+                        }
+                        if (in_band) {
+                            std::fill(tm, tm + 3, 0.0);
+                            std::fill(ts, ts + 3, 0.0);
+                            std::fill(tq, tq + 4, 0.0);
+                            tr[0] = 0.0;
+                            vox_chain(P, R, qn, qnorm, &Gp.scale[3 * i], gv * e, pdp, pdP, Grad{tm, ts, tq, tr}, 0);
+                            for (int k = 0; k < 3; ++k) {
+                                band->mean[3 * i + k] += std::fabs(tm[k]);
+                                band->scale[3 * i + k] += std::fabs(ts[k]);
+                            }
+                            for (int k = 0; k < 4; ++k) band->quat[4 * i + k] += std::fabs(tq[k]);
+                            band->rho[i] += std::fabs(tr[0]);
+                        }
+                        if (!(q <= Q3)) continue;
+                        drho += gv * e;
+                        for (int j = 0; j < 3; ++j) {
+                            dp[j] += pdp[j];
+                            for (int k = 0; k < 3; ++k) dP.a[j][k] += pdP.a[j][k];
                         }
                     }
-            g.rho[i] += drho;
-            for (int k = 0; k < 3; ++k) g.mean[3 * i + k] += dp[k];
-            // P = Sigma^{-1}: dSigma = -P^T dP P^T
-            M3<double> Pt = transpose(P);
-            M3<double> dSigma = mul(mul(Pt, dP), Pt);
-            for (int j = 0; j < 3; ++j)
-                for (int k = 0; k < 3; ++k) dSigma.a[j][k] = -dSigma.a[j][k];
-            sigma_backward(dSigma, R, &Gp.scale[3 * i], qn, qnorm, &g.scale[3 * i], &g.quat[4 * i]);
+            vox_chain(P, R, qn, qnorm, &Gp.scale[3 * i], drho, dp, dP, g, i);
         }
         off += (int64_t)X * Y * Z;
     }
@@ -861,11 +924,15 @@ void orc_render_cs(int64_t M, const double* mean, const double* scale, const dou
     for (size_t k = 0; k < img.size(); ++k) out[k] = img[k].imag() / h;
 }
 
+// band_* may be NULL (no gate-band bound wanted).
 void orc_render_backward(int64_t M, const double* mean, const double* scale, const double* quat,
                          const double* rho, const double* views, int V, const double* camv, double Q,
-                         const double* dimg, double* dmean, double* dscale, double* dquat, double* drho) {
+                         const double* dimg, double* dmean, double* dscale, double* dquat, double* drho,
+                         double* band_mean, double* band_scale, double* band_quat, double* band_rho) {
     const Params P{M, mean, scale, quat, rho};
-    render_backward(P, views, V, make_cam(camv), Q, dimg, Grad{dmean, dscale, dquat, drho});
+    const Grad band{band_mean, band_scale, band_quat, band_rho};
+    render_backward(P, views, V, make_cam(camv), Q, dimg, Grad{dmean, dscale, dquat, drho},
+                    band_mean ? &band : nullptr);
 }
 
 // grids: [G][9] = origin(3), voxel(3), dims(3: X, Y, Z); volumes concatenated.
@@ -897,13 +964,16 @@ void orc_voxelize_cs(int64_t M, const double* mean, const double* scale, const d
     for (int64_t k = 0; k < n; ++k) out[k] = vol[k].imag() / h;
 }
 
+// band_* may be NULL (no gate-band bound wanted).
 void orc_voxelize_backward(int64_t M, const double* mean, const double* scale, const double* quat,
                            const double* rho, const double* gdesc, int G, double Q3, const double* dvol,
-                           double* dmean, double* dscale, double* dquat, double* drho) {
+                           double* dmean, double* dscale, double* dquat, double* drho, double* band_mean,
+                           double* band_scale, double* band_quat, double* band_rho) {
     const Params P{M, mean, scale, quat, rho};
     std::vector<GridSpec> grids;
     grids_from(gdesc, G, grids);
-    voxelize_backward(P, grids, Q3, dvol, Grad{dmean, dscale, dquat, drho});
+    const Grad band{band_mean, band_scale, band_quat, band_rho};
+    voxelize_backward(P, grids, Q3, dvol, Grad{dmean, dscale, dquat, drho}, band_mean ? &band : nullptr);
 }
 
 // O2 over a detector: exact, untruncated, all pixels x all Gaussians.

@@ -37,17 +37,26 @@ def assert_values_close(gpu, ref, band, label=""):
     return err.max() / scale, int((band > 0).sum())
 
 
-def assert_grads_close(gpu, ref, label=""):
-    """Per parameter group: ||g - g_ref||_inf / ||g_ref||_inf <= 1e-3, and per element
-    relative error <= 1e-3 where |g_ref| >= 1e-2 ||g_ref||_inf."""
+def assert_grads_close(gpu, ref, label="", band=None, zero_scale=None):
+    """Per parameter group: ||g - g_ref||_inf <= 1e-3 ||g_ref||_inf, and per element
+    |g - g_ref| <= 1e-3 |g_ref| where |g_ref| >= 1e-2 ||g_ref||_inf.  Both are widened by
+    the oracle's gate-band bound (the summed |contribution| of pairs whose q is within
+    1e-4 Q of the gate, which an FP32 gate may count on the other side).  A group that
+    is exactly zero in the oracle (e.g. rotations of isotropic Gaussians) must be
+    below 1e-6 zero_scale on the GPU."""
     gpu = np.asarray(gpu, dtype=np.float64)
     ref = np.asarray(ref, dtype=np.float64)
+    band = np.zeros_like(ref) if band is None else np.asarray(band, dtype=np.float64)
     n = np.abs(ref).max()
-    assert n > 0, label
-    rel = np.abs(gpu - ref).max() / n
+    if n == 0:
+        assert zero_scale is not None, f"{label}: zero reference"
+        assert np.abs(gpu).max() <= 1e-6 * zero_scale, f"{label}: {np.abs(gpu).max():.3e} where 0 expected"
+        return 0.0, 0.0
+    err = np.abs(gpu - ref)
+    rel = (err - band).max() / n
     assert rel <= TOL_GRAD, f"{label}: group error {rel:.3e}"
     big = np.abs(ref) >= 1e-2 * n
-    el = (np.abs(gpu - ref)[big] / np.abs(ref)[big]).max() if big.any() else 0.0
+    el = ((err - 1.001 * band)[big] / np.abs(ref)[big]).max() if big.any() else 0.0
     assert el <= TOL_GRAD, f"{label}: element error {el:.3e}"
     return rel, el
 
@@ -69,3 +78,23 @@ def cone_small(M=3000, seed=7, H=96, W=112, V=3):
     cam.off_u = 0.5 * pitch  # exercise a detector offset
     views = I.view_table(np.deg2rad(np.arange(V) * (360.0 / V) + 11.0), I.CONE_L_SO)
     return G, cam, views
+
+
+def config2():
+    """The one-scan workload at full size: 50k Gaussians initialised from the seeded
+    256^3 phantom, cone beam 1000/1500 mm, 50 views over 360 deg, 512^2 at 0.8 mm."""
+    ph, vol = I.normalised_phantom(0, 256)
+    G = I.init_from_volume(vol, I.cube_grid(256), 50_000, 0)
+    cam = I.cone_camera(512, 512)
+    views = I.view_table(I.even_angles(50), I.CONE_L_SO)
+    return G, cam, views, ph, vol
+
+
+def config3(M=500_000, V=75):
+    """Differentiation at scale: 500k Gaussians sampled from the phantom support,
+    per-axis scales log-U[0.002, 0.05], random rotations, rho = 0.15 V(p); 75 views."""
+    ph, vol = I.normalised_phantom(0, 256)
+    G = I.init_from_volume(vol, I.cube_grid(256), M, 3, scale_override=(0.002, 0.05), random_rot=True)
+    cam = I.cone_camera(512, 512)
+    views = I.view_table(I.even_angles(V), I.CONE_L_SO)
+    return G, cam, views, ph, vol

@@ -136,9 +136,9 @@ def test_rasterize_backward_matches_oracle_adjoint(case):
     g = [torch.zeros_like(t) for t in (mean, scale, quat, rho)]
     rast.backward(mean, scale, quat, rho, vv, dev(dimg), *g)
     torch.cuda.synchronize()
-    ref = core.render_backward(G, views, cam, dimg, Q=Q9)
-    for name, a, b in zip(("mean", "scale", "quat", "rho"), g, ref):
-        assert_grads_close(host(a), b, f"{case} d{name}")
+    ref, band = core.render_backward(G, views, cam, dimg, Q=Q9, want_band=True)
+    for name, a, b, bd in zip(("mean", "scale", "quat", "rho"), g, ref, band):
+        assert_grads_close(host(a), b, f"{case} d{name}", band=bd)
 
 
 def test_config1_l1_gradient_against_oracle_targets():
@@ -155,9 +155,9 @@ def test_config1_l1_gradient_against_oracle_targets():
     dimg = (np.sign(ref_img - target) / ref_img.size).astype(np.float32)
     g = [torch.zeros_like(t) for t in (mean, scale, quat, rho)]
     rast.backward(mean, scale, quat, rho, vv, dev(dimg), *g)
-    ref = core.render_backward(G, views, cam, dimg, Q=Q9)
-    for name, a, b in zip(("mean", "scale", "quat", "rho"), g, ref):
-        assert_grads_close(host(a), b, f"L1 d{name}")
+    ref, band = core.render_backward(G, views, cam, dimg, Q=Q9, want_band=True)
+    for name, a, b, bd in zip(("mean", "scale", "quat", "rho"), g, ref, band):
+        assert_grads_close(host(a), b, f"L1 d{name}", band=bd)
     assert abs(float(img.sum()) - ref_img.sum()) <= 1e-4 * np.abs(ref_img).sum()
 
 
@@ -204,9 +204,9 @@ def test_voxelize_backward_matches_oracle_adjoint():
     dvol = I.rng(6).standard_normal(vox.n_vox).astype(np.float32)
     g = [torch.zeros_like(t) for t in (mean, scale, quat, rho)]
     vox.backward(mean, scale, quat, rho, dev(dvol), *g)
-    ref = core.voxelize_backward(G, gd, dvol, Q3)
-    for name, a, b in zip(("mean", "scale", "quat", "rho"), g, ref):
-        assert_grads_close(host(a), b, f"vox d{name}")
+    ref, band = core.voxelize_backward(G, gd, dvol, Q3, want_band=True)
+    for name, a, b, bd in zip(("mean", "scale", "quat", "rho"), g, ref, band):
+        assert_grads_close(host(a), b, f"vox d{name}", band=bd)
 
 
 # ----------------------------------------------------------------------------- losses, optimizer
