@@ -9,7 +9,6 @@
 // scatter in which each 256-element round is ranked with warp match masks so
 // the order of equal digits is kept (stability makes every per-key list come out
 // in ascending Gaussian id).
-#include "emit.cuh"
 #include "r2g_internal.cuh"
 
 namespace r2g {
@@ -130,18 +129,6 @@ __global__ void __launch_bounds__(256) k_radix_scatter(const uint64_t* __restric
     }
 }
 
-__global__ void __launch_bounds__(256) k_ranges(const uint64_t* __restrict__ s, const WsStatus* __restrict__ st,
-                                                uint2* __restrict__ ranges, unsigned long long n_slots) {
-    const unsigned long long n = st->n_keys;
-    for (unsigned long long i = (unsigned long long)blockIdx.x * 256 + threadIdx.x; i < n;
-         i += (unsigned long long)gridDim.x * 256) {
-        const uint32_t k = (uint32_t)(s[i] >> 32);
-        if (k >= n_slots) continue;
-        if (i == 0 || (uint32_t)(s[i - 1] >> 32) != k) ranges[k].x = (uint32_t)i;
-        if (i + 1 == n || (uint32_t)(s[i + 1] >> 32) != k) ranges[k].y = (uint32_t)(i + 1);
-    }
-}
-
 }  // namespace
 
 size_t sort_scratch_bytes() {
@@ -153,30 +140,6 @@ int sort_blocks_for(long long capacity) {
     if (nb < 148) nb = 148;
     if (nb > kSortBlocksMax) nb = kSortBlocksMax;
     return (int)nb;
-}
-
-namespace {
-struct ItemOp {
-    const uint2* ranges;
-    uint32_t* item_off;
-    __device__ __forceinline__ uint32_t count(long long t) const {
-        const uint2 r = ranges[t];
-        return (r.y - r.x + kChunk - 1) / kChunk;
-    }
-    __device__ __forceinline__ void emit(long long t, uint64_t* out, unsigned long long off,
-                                         unsigned long long cap) const {
-        const uint32_t n = count(t);
-        item_off[t] = (uint32_t)off;
-        for (uint32_t c = 0; c < n; ++c)
-            if (off + c < cap) out[off + c] = ((uint64_t)t << 32) | c;
-    }
-};
-}  // namespace
-
-void build_items(const uint2* ranges, long long n_slots, WsStatus* item_status, uint32_t* item_off, uint64_t* items,
-                 long long items_cap, unsigned long long* partials, cudaStream_t st) {
-    cudaMemsetAsync(item_status, 0, sizeof(WsStatus), st);
-    emit_lists(ItemOp{ranges, item_off}, n_slots, partials, item_status, items, (unsigned long long)items_cap, st);
 }
 
 uint64_t* radix_sort_u64(uint64_t* a, uint64_t* b, uint32_t* scratch, const WsStatus* status, int key_bits,
@@ -204,9 +167,49 @@ uint64_t* radix_sort_u64(uint64_t* a, uint64_t* b, uint32_t* scratch, const WsSt
     return src;
 }
 
-void build_ranges(const uint64_t* sorted, const WsStatus* status, uint2* ranges, int64_t n_slots, cudaStream_t st) {
-    cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)n_slots, st);
-    k_ranges<<<148 * 8, 256, 0, st>>>(sorted, status, ranges, (unsigned long long)n_slots);
+namespace {
+
+// At the first entry of every key: find the key's end by binary search, write its
+// range, and claim ceil(n / kChunk) consecutive work items with one atomic.  The
+// order in which keys claim their items varies from run to run, but each key's
+// items are contiguous and numbered by chunk, so every consumer that combines a
+// key's chunks does so in chunk order.
+__global__ void __launch_bounds__(256) k_ranges_items(const uint64_t* __restrict__ s,
+                                                      const WsStatus* __restrict__ st, uint2* __restrict__ ranges,
+                                                      unsigned long long n_slots, WsStatus* __restrict__ item_st,
+                                                      uint32_t* __restrict__ item_off, uint64_t* __restrict__ items,
+                                                      unsigned long long items_cap) {
+    const unsigned long long n = st->n_keys;
+    for (unsigned long long i = (unsigned long long)blockIdx.x * 256 + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * 256) {
+        const uint32_t k = (uint32_t)(s[i] >> 32);
+        if (k >= n_slots) continue;
+        if (i != 0 && (uint32_t)(s[i - 1] >> 32) == k) continue;
+        unsigned long long lo = i + 1, hi = n;  // first index whose key differs
+        while (lo < hi) {
+            const unsigned long long mid = (lo + hi) >> 1;
+            if ((uint32_t)(s[mid] >> 32) == k) lo = mid + 1;
+            else hi = mid;
+        }
+        ranges[k] = make_uint2((uint32_t)i, (uint32_t)lo);
+        const uint32_t nch = (uint32_t)((lo - i + kChunk - 1) / kChunk);
+        const unsigned long long base = atomicAdd(&item_st->n_keys, (unsigned long long)nch);
+        item_off[k] = (uint32_t)base;
+        for (uint32_t c = 0; c < nch; ++c)
+            if (base + c < items_cap) items[base + c] = ((uint64_t)k << 32) | c;
+    }
+}
+
+}  // namespace
+
+void build_ranges_items(const uint64_t* sorted, const WsStatus* status, uint2* ranges, int64_t n_slots,
+                        WsStatus* item_status, uint32_t* item_off, uint64_t* items, long long items_cap,
+                        cudaStream_t st) {
+    // ranges and the item status block are adjacent in every workspace: one clear
+    cudaMemsetAsync(ranges, 0, reinterpret_cast<char*>(item_status) - reinterpret_cast<char*>(ranges) +
+                                   sizeof(WsStatus), st);
+    k_ranges_items<<<148 * 8, 256, 0, st>>>(sorted, status, ranges, (unsigned long long)n_slots, item_status,
+                                            item_off, items, (unsigned long long)items_cap);
 }
 
 }  // namespace r2g

@@ -12,7 +12,9 @@
 //                 filtered with the same window (the adjoint of a zero-padded
 //                 symmetric filter is itself) and combined with x, y and the L1
 //                 sign into d loss / d render.
-//   k_finalize    one CTA sums the per-CTA partials in a fixed order (deterministic).
+//                 Its block 0 also sums the per-tile partials of k_ssim_maps in a
+//                 fixed order into the loss (deterministic).
+//   k_finalize    (TV) one CTA sums the per-CTA partials in a fixed order.
 // 3D TV: k_tv3d forms each voxel's gradient from its six neighbours and a CTA
 // partial of the loss; k_finalize sums the partials.
 #include <math.h>
@@ -128,9 +130,11 @@ __global__ void __launch_bounds__(256) k_ssim_grad(const float* __restrict__ x, 
                                                    int W, int tiles_x, int tiles_per_view, const Win win,
                                                    const float* __restrict__ dmu, const float* __restrict__ dxx,
                                                    const float* __restrict__ dxy, float l1_scale, float ssim_scale,
-                                                   float* __restrict__ grad) {
+                                                   float* __restrict__ grad, const float* __restrict__ partials,
+                                                   int n_tiles, float lam, double inv_n, float* __restrict__ loss) {
     __shared__ float s[3][kE][kE + 1];
     __shared__ float h[3][kE][kT + 1];
+    __shared__ double red[2][256];
     const int tile = blockIdx.x;
     const int v = tile / tiles_per_view, lt = tile - v * tiles_per_view;
     const int ty = lt / tiles_x, tx = lt - ty * tiles_x;
@@ -178,6 +182,26 @@ __global__ void __launch_bounds__(256) k_ssim_grad(const float* __restrict__ x, 
         const float d = xv - yv;
         const float sgn = (d > 0.f) ? 1.f : ((d < 0.f) ? -1.f : 0.f);
         grad[o] = l1_scale * sgn - ssim_scale * (b0 + 2.f * xv * b1 + yv * b2);
+    }
+    // The per-tile partial sums come from the previous kernel, so any one block can
+    // form the loss: block 0 sums them in a fixed order.
+    if (blockIdx.x == 0) {
+        double sS = 0.0, sL1 = 0.0;
+        for (int k = threadIdx.x; k < n_tiles; k += 256) {
+            sS += partials[2 * k];
+            sL1 += partials[2 * k + 1];
+        }
+        red[0][threadIdx.x] = sS;
+        red[1][threadIdx.x] = sL1;
+        __syncthreads();
+        for (int o = 128; o > 0; o >>= 1) {
+            if ((int)threadIdx.x < o) {
+                red[0][threadIdx.x] += red[0][threadIdx.x + o];
+                red[1][threadIdx.x] += red[1][threadIdx.x + o];
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) *loss = (float)(inv_n * red[1][0] + lam * (1.0 - inv_n * red[0][0]));
     }
 }
 
@@ -317,11 +341,10 @@ R2G_API r2g_status r2g_projection_loss(int32_t V, int32_t H, int32_t W, const fl
                                                           partials);
     const double N = (double)V * H * W;
     k_ssim_grad<<<(unsigned)L.n_tiles, 256, 0, stream>>>(render, meas, H, W, L.tiles_x, tpv, win, dmu, dxx, dxy,
-                                                          (float)(1.0 / N), (float)(lambda_ssim / N), drender);
-    k_finalize<<<1, 256, 0, stream>>>(partials, (int)L.n_tiles, 0, (float)(1.0 / N), lambda_ssim, (float)(1.0 / N),
-                                      loss);
+                                                          (float)(1.0 / N), (float)(lambda_ssim / N), drender,
+                                                          partials, (int)L.n_tiles, lambda_ssim, 1.0 / N, loss);
     prof_end(P_LOSS, stream);
-    note_launches(3);
+    note_launches(2);
     return check_launch("r2g_projection_loss");
 }
 

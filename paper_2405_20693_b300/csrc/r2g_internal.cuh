@@ -80,17 +80,19 @@ uint64_t* radix_sort_u64(uint64_t* a, uint64_t* b, uint32_t* scratch, const WsSt
                          int sort_blocks, cudaStream_t st);
 
 // Work items: every key's range is cut into chunks of kChunk entries; item =
-// (key << 32) | chunk index, in key order.  item_off[key] = index of the key's
-// first item (written for non-empty keys).  item_status->n_keys = item count.
-// items must hold items_capacity(n_slots, capacity) entries.
+// (key << 32) | chunk index; a key's items are consecutive.  item_off[key] = index
+// of the key's first item (written for non-empty keys); item_status->n_keys = item
+// count.  items must hold items_capacity(n_slots, capacity) entries.
 inline long long items_capacity(long long n_slots, long long capacity) {
     return n_slots + (capacity + kChunk - 1) / kChunk + 1;
 }
-void build_items(const uint2* ranges, long long n_slots, WsStatus* item_status, uint32_t* item_off, uint64_t* items,
-                 long long items_cap, unsigned long long* partials, cudaStream_t st);
+// ranges[k] = [start, end) of key k in the sorted entries (absent keys: [0, 0)), and
+// the work items, in one pass over the sorted entries.  item_status must
+// directly follow the ranges array in the workspace (one clear covers both).
+void build_ranges_items(const uint64_t* sorted, const WsStatus* status, uint2* ranges, int64_t n_slots,
+                        WsStatus* item_status, uint32_t* item_off, uint64_t* items, long long items_cap,
+                        cudaStream_t st);
 
-// ranges[k] = [start, end) of key k in the sorted entries (absent keys: [0, 0)).
-void build_ranges(const uint64_t* sorted, const WsStatus* status, uint2* ranges, int64_t n_slots, cudaStream_t st);
 
 inline int bits_for(int64_t n_slots) {
     int b = 1;

@@ -9,10 +9,13 @@
 //                  {cx, cy, A, B, C, rho_hat, rx, ry} in pixel units with the
 //                  conic pre-scaled by -log2(e)/2 so that exp(-q/2) = 2^t.
 //   emit / sort    (tile, Gaussian id) entries, stable radix sort, tile ranges.
-//   k_splat_fwd    one CTA per tile; records are staged through shared memory
-//                  in batches; each thread owns two horizontally adjacent
-//                  pixels and accumulates rho_hat 2^t [t >= Tq]; a warp skips
-//                  records whose row span misses its rows.
+//   k_splat_fwd    one CTA per work item (a tile and a chunk of <= 128 of its
+//                  records); records are staged through shared memory; each
+//                  lane owns 4 (2 for 8x8 tiles) horizontally adjacent pixels and
+//                  accumulates rho_hat 2^t [t >= Tq]; a warp owns an 8-row block
+//                  and skips records whose box misses it.  Tiles with several
+//                  chunks write per-chunk images that k_splat_reduce sums in
+//                  chunk order.
 //   k_splat_bwd    one CTA per tile with dL/dI of the tile in shared memory;
 //                  each thread takes one record and walks the pixels of its
 //                  box inside the tile, accumulating six moments
@@ -299,19 +302,29 @@ struct TileOp {
 
 // ------------------------------------------------------------------ K3: splat forward
 
+// Pixels per lane of the forward splat for a tile shape (a warp owns an 8-row block
+// 4 * PX pixels wide).
+template <int TW, int TH>
+struct FwdShape {
+    static constexpr int PX = (TW * TH >= 256) ? 4 : 2;
+    static constexpr int NT = TW * TH / PX;
+};
+
 template <int TW, int TH, bool COUNT>
-__global__ void __launch_bounds__(TW * TH / 2) k_splat_fwd(const float4* __restrict__ rec,
-                                                           const uint2* __restrict__ ranges,
-                                                           const uint64_t* __restrict__ sorted,
-                                                           const uint64_t* __restrict__ items,
-                                                           const WsStatus* __restrict__ item_st,
-                                                           float* __restrict__ partial, long long M, int tiles_x,
-                                                           int tiles_per_view, int H, int W, float Tq,
-                                                           float* __restrict__ image, WsStatus* st) {
-    constexpr int NT = TW * TH / 2;  // threads; two pixels each
-    constexpr int TPR = TW / 2;      // threads per pixel row
-    constexpr int RPW = 32 / TPR;    // pixel rows per warp
-    static_assert(32 % TPR == 0 && NT % 32 == 0 && kChunk % NT == 0, "tile shape");
+__global__ void __launch_bounds__(FwdShape<TW, TH>::NT) k_splat_fwd(const float4* __restrict__ rec,
+                                                                    const uint2* __restrict__ ranges,
+                                                                    const uint64_t* __restrict__ sorted,
+                                                                    const uint64_t* __restrict__ items,
+                                                                    const WsStatus* __restrict__ item_st,
+                                                                    float* __restrict__ partial, long long M,
+                                                                    int tiles_x, int tiles_per_view, int H, int W,
+                                                                    float Tq, float* __restrict__ image,
+                                                                    WsStatus* st) {
+    constexpr int PX = FwdShape<TW, TH>::PX;  // pixels per lane, along x
+    constexpr int NT = FwdShape<TW, TH>::NT;  // threads
+    constexpr int BW = 4 * PX;                // warp block: 8 rows x BW columns
+    constexpr int WPR = TW / BW;              // warp blocks per tile row
+    static_assert(TW % BW == 0 && TH % 8 == 0 && kChunk % NT == 0 && NT % 32 == 0, "tile shape");
     __shared__ float4 s_a[NT];
     __shared__ float4 s_b[NT];
     const unsigned long long it = blockIdx.x;
@@ -322,13 +335,17 @@ __global__ void __launch_bounds__(TW * TH / 2) k_splat_fwd(const float4* __restr
     const int v = tile / tiles_per_view;
     const int lt = tile - v * tiles_per_view;
     const int ty = lt / tiles_x, tx = lt - ty * tiles_x;
-    const int lx = (threadIdx.x % TPR) * 2, ly = threadIdx.x / TPR;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int bx = (warp % WPR) * BW, by = (warp / WPR) * 8;
+    const int lx = bx + (lane & 3) * PX, ly = by + (lane >> 2);
     const int px = tx * TW + lx, py = ty * TH + ly;
-    const int warp = threadIdx.x >> 5;
-    const float wr0 = (float)(ty * TH + warp * RPW), wr1 = wr0 + (float)(RPW - 1);
+    const float wx0 = (float)(tx * TW + bx), wx1 = wx0 + (float)(BW - 1);
+    const float wy0 = (float)(ty * TH + by), wy1 = wy0 + 7.0f;
     const float fx = (float)px, fy = (float)py;
     const float4* vrec = rec + 2 * (size_t)v * (size_t)M;
-    float acc0 = 0.0f, acc1 = 0.0f;
+    float acc[PX];
+#pragma unroll
+    for (int k = 0; k < PX; ++k) acc[k] = 0.0f;
     unsigned int cnt = 0;
     const uint2 rg = ranges[tile];
     const uint32_t start = rg.x + chunk * kChunk;
@@ -346,36 +363,38 @@ __global__ void __launch_bounds__(TW * TH / 2) k_splat_fwd(const float4* __restr
         for (int j = 0; j < n; ++j) {
             const float4 a = s_a[j];  // cx, cy, A, B
             const float4 b = s_b[j];  // C, rho_hat, rx, ry
-            if (a.y + b.w < wr0 || a.y - b.w > wr1) continue;  // warp-uniform row cull
+            // warp-uniform cull: the record's box misses this warp's block
+            if (a.y + b.w < wy0 || a.y - b.w > wy1 || a.x + b.z < wx0 || a.x - b.z > wx1) continue;
             const float dy = fy - a.y;
             const float bdy = a.w * dy;
             const float cdy2 = b.x * dy * dy;
             const float dx0 = fx - a.x;
-            const float dx1 = dx0 + 1.0f;
-            const float t0 = fmaf(fmaf(a.z, dx0, bdy), dx0, cdy2);
-            const float t1 = fmaf(fmaf(a.z, dx1, bdy), dx1, cdy2);
-            const float e0 = ex2_approx(t0);
-            const float e1 = ex2_approx(t1);
-            acc0 = (t0 >= Tq) ? fmaf(b.y, e0, acc0) : acc0;
-            acc1 = (t1 >= Tq) ? fmaf(b.y, e1, acc1) : acc1;
-            if (COUNT) cnt += (t0 >= Tq && px < W && py < H) + (t1 >= Tq && px + 1 < W && py < H);
+#pragma unroll
+            for (int k = 0; k < PX; ++k) {
+                const float dx = dx0 + (float)k;
+                const float t = fmaf(fmaf(a.z, dx, bdy), dx, cdy2);
+                const float e = ex2_approx(t);
+                acc[k] = (t >= Tq) ? fmaf(b.y, e, acc[k]) : acc[k];
+                if (COUNT) cnt += (t >= Tq && px + k < W && py < H);
+            }
         }
     }
     if (nch == 1) {
         if (py < H) {
             float* row = image + ((size_t)v * H + py) * W;
-            if (px < W) row[px] = acc0;
-            if (px + 1 < W) row[px + 1] = acc1;
+#pragma unroll
+            for (int k = 0; k < PX; ++k)
+                if (px + k < W) row[px + k] = acc[k];
         }
     } else {
         float* p = partial + it * (size_t)(TW * TH) + ly * TW + lx;
-        p[0] = acc0;
-        p[1] = acc1;
+#pragma unroll
+        for (int k = 0; k < PX; ++k) p[k] = acc[k];
     }
     if (COUNT) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-        if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(&st->pairs, (unsigned long long)cnt);
+        if (lane == 0 && cnt) atomicAdd(&st->pairs, (unsigned long long)cnt);
     }
 }
 
@@ -406,6 +425,23 @@ __global__ void __launch_bounds__(128) k_splat_reduce(const uint2* __restrict__ 
 
 constexpr int kBwdThreads = 128;
 
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
+}
+
+// One CTA per work item (<= 128 records of one tile).  Each record's pixel box
+// inside the tile is a w x h rectangle of n = w h pixels.  Within a warp the
+// n-sums of its 32 records are split into 32 equal contiguous ranges of
+// (record, pixel) pairs, one per lane, so every lane does the same number of
+// pair evaluations whatever the record sizes.  A lane keeps the six moments of
+// its current record in registers and adds them to the record's slot (two
+// vector atomics) when it leaves the record or its range ends.
 template <int TW, int TH>
 __global__ void __launch_bounds__(kBwdThreads) k_splat_bwd(const float4* __restrict__ rec,
                                                            const uint2* __restrict__ ranges,
@@ -416,7 +452,11 @@ __global__ void __launch_bounds__(kBwdThreads) k_splat_bwd(const float4* __restr
                                                            const float* __restrict__ dimage,
                                                            float4* __restrict__ mom) {
     static_assert(kChunk == kBwdThreads, "one record per thread");
-    __shared__ float s_g[TH][TW];
+    __shared__ float s_g[TH * TW];
+    __shared__ float4 s_ra[kChunk], s_rb[kChunk];
+    __shared__ int4 s_box[kChunk];       // c0, r0 (tile-local), w, n
+    __shared__ uint32_t s_gid[kChunk];
+    __shared__ uint32_t s_excl[kChunk];  // warp-exclusive prefix of n
     const unsigned long long it = blockIdx.x;
     if (it >= item_st->n_keys) return;
     const uint64_t item = items[it];
@@ -429,45 +469,99 @@ __global__ void __launch_bounds__(kBwdThreads) k_splat_bwd(const float4* __restr
     for (int k = threadIdx.x; k < TW * TH; k += kBwdThreads) {
         const int r = k / TW, c = k - r * TW;
         const int gy = Y0 + r, gx = X0 + c;
-        s_g[r][c] = (gy < H && gx < W) ? dimage[((size_t)v * H + gy) * W + gx] : 0.0f;
+        s_g[k] = (gy < H && gx < W) ? dimage[((size_t)v * H + gy) * W + gx] : 0.0f;
     }
-    __syncthreads();
     const uint2 rg = ranges[tile];
     const float4* vrec = rec + 2 * (size_t)v * (size_t)M;
     float4* vmom = mom + 2 * (size_t)v * (size_t)M;
-    const uint32_t e = rg.x + chunk * kChunk + threadIdx.x;
+    const int j = threadIdx.x, lane = j & 31, wbase = j & ~31;
+    const uint32_t e = rg.x + chunk * kChunk + j;
+    uint32_t n = 0;
     if (e < rg.y) {
         const uint32_t gid = (uint32_t)sorted[e];
         const float4 a = vrec[2 * (size_t)gid];
         const float4 b = vrec[2 * (size_t)gid + 1];
-        const int c0 = max(X0, (int)ceilf(a.x - b.z)), c1 = min(X0 + TW - 1, (int)floorf(a.x + b.z));
-        const int r0 = max(Y0, (int)ceilf(a.y - b.w)), r1 = min(Y0 + TH - 1, (int)floorf(a.y + b.w));
-        float S0 = 0.f, Sx = 0.f, Sy = 0.f, Sxx = 0.f, Sxy = 0.f, Syy = 0.f;
-        for (int r = r0; r <= r1; ++r) {
-            const float dy = (float)r - a.y;
-            const float bdy = a.w * dy;
-            const float cdy2 = b.x * dy * dy;
-            const float* grow = &s_g[r - Y0][0];
-            for (int c = c0; c <= c1; ++c) {
-                const float dx = (float)c - a.x;
-                const float t = fmaf(fmaf(a.z, dx, bdy), dx, cdy2);
-                if (t >= Tq) {
-                    const float w = grow[c - X0] * ex2_approx(t);
-                    const float wx = w * dx;
-                    S0 += w;
-                    Sx += wx;
-                    Sy = fmaf(w, dy, Sy);
-                    Sxx = fmaf(wx, dx, Sxx);
-                    Sxy = fmaf(wx, dy, Sxy);
-                    Syy = fmaf(w * dy, dy, Syy);
-                }
-            }
+        const int c0 = max(0, (int)ceilf(a.x - b.z) - X0), c1 = min(TW - 1, (int)floorf(a.x + b.z) - X0);
+        const int r0 = max(0, (int)ceilf(a.y - b.w) - Y0), r1 = min(TH - 1, (int)floorf(a.y + b.w) - Y0);
+        const int w = c1 - c0 + 1, h = r1 - r0 + 1;
+        n = (w > 0 && h > 0) ? (uint32_t)(w * h) : 0u;
+        s_ra[j] = a;
+        s_rb[j] = b;
+        s_box[j] = make_int4(c0, r0, max(w, 1), (int)n);
+        s_gid[j] = gid;
+    } else {
+        s_box[j] = make_int4(0, 0, 1, 0);
+        s_gid[j] = 0;
+    }
+    const uint32_t incl = warp_incl_scan(n);
+    s_excl[j] = incl - n;
+    const uint32_t T = __shfl_sync(0xffffffffu, incl, 31);
+    __syncthreads();
+    const uint32_t per = (T + 31) >> 5;
+    const uint32_t p0 = lane * per, p1 = min(T, p0 + per);
+    if (p0 >= p1) return;
+    // the record holding pair p0: the largest k with excl_k <= p0 (it is non-empty)
+    int lo = 0, hi = 31;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_excl[wbase + mid] <= p0) lo = mid;
+        else hi = mid - 1;
+    }
+    int k = lo;
+    float4 a = s_ra[wbase + k], b = s_rb[wbase + k];
+    int4 box = s_box[wbase + k];
+    uint32_t rec_end = s_excl[wbase + k] + (uint32_t)box.w;
+    int li = (int)(p0 - s_excl[wbase + k]);
+    int row = li / box.z, col = li - row * box.z;
+    float dy = (float)(Y0 + box.y + row) - a.y;
+    float dx = (float)(X0 + box.x + col) - a.x;
+    float bdy = a.w * dy, cdy2 = b.x * dy * dy;
+    const float* grow = s_g + (box.y + row) * TW + box.x;
+    float S0 = 0.f, Sx = 0.f, Sy = 0.f, Sxx = 0.f, Sxy = 0.f, Syy = 0.f;
+    for (uint32_t p = p0; p < p1; ++p) {
+        const float t = fmaf(fmaf(a.z, dx, bdy), dx, cdy2);
+        const float ev = ex2_approx(t);
+        const float w = (t >= Tq) ? grow[col] * ev : 0.0f;
+        const float wx = w * dx, wy = w * dy;
+        S0 += w;
+        Sx += wx;
+        Sy += wy;
+        Sxx = fmaf(wx, dx, Sxx);
+        Sxy = fmaf(wx, dy, Sxy);
+        Syy = fmaf(wy, dy, Syy);
+        ++col;
+        dx += 1.0f;
+        if (col == box.z) {  // next row of the box
+            col = 0;
+            dx -= (float)box.z;
+            dy += 1.0f;
+            grow += TW;
+            bdy = a.w * dy;
+            cdy2 = b.x * dy * dy;
         }
-        if (S0 != 0.f || Sx != 0.f || Sy != 0.f || Sxx != 0.f || Sxy != 0.f || Syy != 0.f) {
+        if (p + 1 == rec_end && p + 1 < p1) {  // next record
+            const uint32_t gid = s_gid[wbase + k];
             atomicAdd(&vmom[2 * (size_t)gid], make_float4(S0, Sx, Sy, Sxx));
             atomicAdd(reinterpret_cast<float2*>(&vmom[2 * (size_t)gid + 1]), make_float2(Sxy, Syy));
+            S0 = Sx = Sy = Sxx = Sxy = Syy = 0.f;
+            do {
+                ++k;
+            } while (s_box[wbase + k].w == 0);
+            a = s_ra[wbase + k];
+            b = s_rb[wbase + k];
+            box = s_box[wbase + k];
+            rec_end += (uint32_t)box.w;
+            col = 0;
+            dy = (float)(Y0 + box.y) - a.y;
+            dx = (float)(X0 + box.x) - a.x;
+            bdy = a.w * dy;
+            cdy2 = b.x * dy * dy;
+            grow = s_g + box.y * TW + box.x;
         }
     }
+    const uint32_t gid = s_gid[wbase + k];
+    atomicAdd(&vmom[2 * (size_t)gid], make_float4(S0, Sx, Sy, Sxx));
+    atomicAdd(reinterpret_cast<float2*>(&vmom[2 * (size_t)gid + 1]), make_float2(Sxy, Syy));
 }
 
 // ------------------------------------------------------------------ K6: projection backward
@@ -667,9 +761,9 @@ RasterLayout raster_layout(int64_t M, int32_t V, const r2g_camera* cam, const r2
     L.rect = lay.take(8 * (size_t)L.n_rec);
     L.partials = lay.take(8 * (size_t)kScanBlocks);
     L.ranges = lay.take(8 * (size_t)L.n_tiles);
+    L.item_status = lay.take(sizeof(WsStatus));  // directly after the ranges (cleared together)
     L.mom = lay.take(32 * (size_t)L.n_rec);
     L.scratch = lay.take(sort_scratch_bytes());
-    L.item_status = lay.take(sizeof(WsStatus));
     L.item_off = lay.take(4 * (size_t)L.n_tiles);
     L.fixed = lay.off;
     return L;
@@ -735,7 +829,8 @@ struct FwdArgs {
 template <int TW, int TH, bool COUNT>
 void fwd_shape(const FwdArgs& f, long long M, const RasterLayout& L, long long icap, int H, int W, float Tq,
                float* image, WsStatus* st, cudaStream_t s) {
-    k_splat_fwd<TW, TH, COUNT><<<(unsigned)icap, TW * TH / 2, 0, s>>>(f.rec, f.ranges, f.sorted, f.items, f.item_st,
+    k_splat_fwd<TW, TH, COUNT><<<(unsigned)icap, FwdShape<TW, TH>::NT, 0, s>>>(f.rec, f.ranges, f.sorted, f.items,
+                                                                                f.item_st,
                                                                        f.partial, M, L.tiles_x, L.tiles_per_view, H,
                                                                        W, Tq, image, st);
     k_splat_reduce<TW, TH><<<(unsigned)L.n_tiles, 128, 0, s>>>(f.ranges, f.item_off, f.partial, L.tiles_x,
@@ -849,8 +944,7 @@ R2G_API r2g_status r2g_rasterize(int64_t M, const float* mean, const float* scal
     uint64_t* sorted = radix_sort_u64(a, b, scratch, st, bits_for(L.n_tiles), sort_blocks_for(cap), stream);
     prof_end(P_SORT, stream);
     prof_begin(P_RANGES, stream);
-    build_ranges(sorted, st, ranges, L.n_tiles, stream);
-    build_items(ranges, L.n_tiles, item_st, item_off, items, T.icap, partials, stream);
+    build_ranges_items(sorted, st, ranges, L.n_tiles, item_st, item_off, items, T.icap, stream);
     prof_end(P_RANGES, stream);
     const float Tq = -0.5f * kLog2e * opts->Q;
     prof_begin(P_SPLAT_FWD, stream);
@@ -860,7 +954,7 @@ R2G_API r2g_status r2g_rasterize(int64_t M, const float* mean, const float* scal
     else
         launch_fwd<false>(opts->tile_w, opts->tile_h, fa, M, L, T.icap, cam->H, cam->W, Tq, image, st, stream);
     prof_end(P_SPLAT_FWD, stream);
-    note_launches(1 + 3 + 3 * ((bits_for(L.n_tiles) + kRadixBits - 1) / kRadixBits) + 1 + 3 + 2);
+    note_launches(1 + 3 + 3 * ((bits_for(L.n_tiles) + kRadixBits - 1) / kRadixBits) + 1 + 2);
     return check_launch("r2g_rasterize");
 }
 

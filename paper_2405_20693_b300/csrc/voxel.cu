@@ -316,6 +316,21 @@ __global__ void __launch_bounds__(kVoxThreads) k_vox_reduce(const uint2* __restr
 
 // ------------------------------------------------------------------ backward
 
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
+}
+
+// One CTA per work item (<= 128 records of one brick).  Each record's voxel box
+// inside the brick is w x h x d; within a warp the box sizes of its 32 records are
+// split into 32 equal contiguous ranges of (record, voxel) pairs, one per lane; a
+// lane keeps its current record's ten moments in registers and adds them to the
+// record's slot (three vector atomics) when it leaves the record or its range ends.
 __global__ void __launch_bounds__(kVoxThreads) k_vox_bwd(const float4* __restrict__ rec,
                                                          const uint2* __restrict__ ranges,
                                                          const uint64_t* __restrict__ sorted,
@@ -323,7 +338,12 @@ __global__ void __launch_bounds__(kVoxThreads) k_vox_bwd(const float4* __restric
                                                          const WsStatus* __restrict__ item_st, long long M,
                                                          const __grid_constant__ Grids grids, float Tq,
                                                          const float* __restrict__ dvol, float4* __restrict__ mom) {
-    __shared__ float s_g[kB][kB][kB];
+    static_assert(kChunk == kVoxThreads, "one record per thread");
+    __shared__ float s_g[kB * kB * kB];
+    __shared__ float4 s_r0[kChunk], s_r1[kChunk], s_r2[kChunk];
+    __shared__ int4 s_box[kChunk];      // x0 | y0 << 8 | z0 << 16, w, wh, n
+    __shared__ uint32_t s_gid[kChunk];
+    __shared__ uint32_t s_excl[kChunk];
     const unsigned long long it = blockIdx.x;
     if (it >= item_st->n_keys) return;
     const uint64_t item = items[it];
@@ -339,57 +359,128 @@ __global__ void __launch_bounds__(kVoxThreads) k_vox_bwd(const float4* __restric
     for (int k = threadIdx.x; k < kB * kB * kB; k += kVoxThreads) {
         const int lz = k >> 6, ly = (k >> 3) & 7, lx = k & 7;
         const int x = X0 + lx, y = Y0 + ly, z = Z0 + lz;
-        s_g[lz][ly][lx] = (x < gf.dims[0] && y < gf.dims[1] && z < gf.dims[2])
-                              ? dvol[gf.vol_base + ((long long)z * gf.dims[1] + y) * gf.dims[0] + x]
-                              : 0.0f;
+        s_g[k] = (x < gf.dims[0] && y < gf.dims[1] && z < gf.dims[2])
+                     ? dvol[gf.vol_base + ((long long)z * gf.dims[1] + y) * gf.dims[0] + x]
+                     : 0.0f;
     }
-    __syncthreads();
     const uint2 rg = ranges[brick];
     const float4* grec = rec + 4 * (size_t)g * (size_t)M;
     float4* gmom = mom + 3 * (size_t)g * (size_t)M;
-    const uint32_t e = rg.x + chunk * kChunk + threadIdx.x;
+    const int j = threadIdx.x, lane = j & 31, wbase = j & ~31;
+    const uint32_t e = rg.x + chunk * kChunk + j;
+    uint32_t n = 0;
     if (e < rg.y) {
         const uint32_t gid = (uint32_t)sorted[e];
         const float4 r0 = grec[4 * (size_t)gid], r1 = grec[4 * (size_t)gid + 1];
         const float4 r2 = grec[4 * (size_t)gid + 2], r3 = grec[4 * (size_t)gid + 3];
-        const int xa = max(X0, (int)ceilf(r0.x - r3.x)), xb = min(X0 + kB - 1, (int)floorf(r0.x + r3.x));
-        const int ya = max(Y0, (int)ceilf(r0.y - r3.y)), yb = min(Y0 + kB - 1, (int)floorf(r0.y + r3.y));
-        const int za = max(Z0, (int)ceilf(r0.z - r3.z)), zb = min(Z0 + kB - 1, (int)floorf(r0.z + r3.z));
-        float S0 = 0.f, Sx = 0.f, Sy = 0.f, Sz = 0.f;
-        float Sxx = 0.f, Syy = 0.f, Szz = 0.f, Sxy = 0.f, Sxz = 0.f, Syz = 0.f;
-        for (int z = za; z <= zb; ++z) {
-            const float dz = (float)z - r0.z;
-            for (int y = ya; y <= yb; ++y) {
-                const float dy = (float)y - r0.y;
-                const float base_q = fmaf(r1.y * dy, dy, fmaf(r1.z * dz, dz, r2.y * dy * dz));
-                const float lin = fmaf(r1.w, dy, r2.x * dz);
-                const float* grow = &s_g[z - Z0][y - Y0][0];
-                for (int x = xa; x <= xb; ++x) {
-                    const float dx = (float)x - r0.x;
-                    const float tq = fmaf(fmaf(r1.x, dx, lin), dx, base_q);
-                    if (tq >= Tq) {
-                        const float w = grow[x - X0] * ex2_approx(tq);
-                        const float wx = w * dx, wy = w * dy;
-                        S0 += w;
-                        Sx += wx;
-                        Sy += wy;
-                        Sz = fmaf(w, dz, Sz);
-                        Sxx = fmaf(wx, dx, Sxx);
-                        Syy = fmaf(wy, dy, Syy);
-                        Szz = fmaf(w * dz, dz, Szz);
-                        Sxy = fmaf(wx, dy, Sxy);
-                        Sxz = fmaf(wx, dz, Sxz);
-                        Syz = fmaf(wy, dz, Syz);
-                    }
-                }
+        const int xa = max(0, (int)ceilf(r0.x - r3.x) - X0), xb = min(kB - 1, (int)floorf(r0.x + r3.x) - X0);
+        const int ya = max(0, (int)ceilf(r0.y - r3.y) - Y0), yb = min(kB - 1, (int)floorf(r0.y + r3.y) - Y0);
+        const int za = max(0, (int)ceilf(r0.z - r3.z) - Z0), zb = min(kB - 1, (int)floorf(r0.z + r3.z) - Z0);
+        const int w = xb - xa + 1, h = yb - ya + 1, d = zb - za + 1;
+        n = (w > 0 && h > 0 && d > 0) ? (uint32_t)(w * h * d) : 0u;
+        s_r0[j] = r0;
+        s_r1[j] = r1;
+        s_r2[j] = r2;
+        s_box[j] = make_int4(n ? (xa | (ya << 8) | (za << 16)) : 0, max(w, 1), max(w, 1) * max(h, 1), (int)n);
+        s_gid[j] = gid;
+    } else {
+        s_box[j] = make_int4(0, 1, 1, 0);
+        s_gid[j] = 0;
+    }
+    const uint32_t incl = warp_incl_scan(n);
+    s_excl[j] = incl - n;
+    const uint32_t T = __shfl_sync(0xffffffffu, incl, 31);
+    __syncthreads();
+    const uint32_t per = (T + 31) >> 5;
+    const uint32_t p0 = lane * per, p1 = min(T, p0 + per);
+    if (p0 >= p1) return;
+    int lo = 0, hi = 31;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_excl[wbase + mid] <= p0) lo = mid;
+        else hi = mid - 1;
+    }
+    int k = lo;
+    float4 r0 = s_r0[wbase + k], r1 = s_r1[wbase + k], r2 = s_r2[wbase + k];
+    int4 box = s_box[wbase + k];
+    uint32_t rec_end = s_excl[wbase + k] + (uint32_t)box.w;
+    int li = (int)(p0 - s_excl[wbase + k]);
+    int zz = li / box.z;
+    int rem = li - zz * box.z;
+    int yy = rem / box.y;
+    int xx = rem - yy * box.y;
+    int xa = box.x & 0xff, ya = (box.x >> 8) & 0xff, za = box.x >> 16;
+    int cy = yy;  // rows done inside the current z-slice
+    float dx = (float)(X0 + xa + xx) - r0.x;
+    float dy = (float)(Y0 + ya + yy) - r0.y;
+    float dz = (float)(Z0 + za + zz) - r0.z;
+    float base_q = fmaf(r1.y * dy, dy, fmaf(r1.z * dz, dz, r2.y * dy * dz));
+    float lin = fmaf(r1.w, dy, r2.x * dz);
+    const float* grow = s_g + ((za + zz) * kB + (ya + yy)) * kB + xa;
+    float S0 = 0.f, Sx = 0.f, Sy = 0.f, Sz = 0.f, Sxx = 0.f, Syy = 0.f, Szz = 0.f, Sxy = 0.f, Sxz = 0.f, Syz = 0.f;
+    for (uint32_t p = p0; p < p1; ++p) {
+        const float tq = fmaf(fmaf(r1.x, dx, lin), dx, base_q);
+        const float ev = ex2_approx(tq);
+        const float w = (tq >= Tq) ? grow[xx] * ev : 0.0f;
+        const float wx = w * dx, wy = w * dy, wz = w * dz;
+        S0 += w;
+        Sx += wx;
+        Sy += wy;
+        Sz += wz;
+        Sxx = fmaf(wx, dx, Sxx);
+        Syy = fmaf(wy, dy, Syy);
+        Szz = fmaf(wz, dz, Szz);
+        Sxy = fmaf(wx, dy, Sxy);
+        Sxz = fmaf(wx, dz, Sxz);
+        Syz = fmaf(wy, dz, Syz);
+        ++xx;
+        dx += 1.0f;
+        if (xx == box.y) {  // next row (and slice) of the box
+            xx = 0;
+            dx -= (float)box.y;
+            ++cy;
+            dy += 1.0f;
+            grow += kB;
+            if (cy * box.y == box.z) {
+                cy = 0;
+                dy -= (float)(box.z / box.y);
+                dz += 1.0f;
+                grow += kB * kB - (box.z / box.y) * kB;
             }
+            base_q = fmaf(r1.y * dy, dy, fmaf(r1.z * dz, dz, r2.y * dy * dz));
+            lin = fmaf(r1.w, dy, r2.x * dz);
         }
-        if (S0 != 0.f || Sx != 0.f || Sy != 0.f || Sz != 0.f || Sxx != 0.f || Syy != 0.f || Szz != 0.f) {
+        if (p + 1 == rec_end && p + 1 < p1) {  // next record
+            const uint32_t gid = s_gid[wbase + k];
             atomicAdd(&gmom[3 * (size_t)gid], make_float4(S0, Sx, Sy, Sz));
             atomicAdd(&gmom[3 * (size_t)gid + 1], make_float4(Sxx, Syy, Szz, Sxy));
             atomicAdd(reinterpret_cast<float2*>(&gmom[3 * (size_t)gid + 2]), make_float2(Sxz, Syz));
+            S0 = Sx = Sy = Sz = Sxx = Syy = Szz = Sxy = Sxz = Syz = 0.f;
+            do {
+                ++k;
+            } while (s_box[wbase + k].w == 0);
+            r0 = s_r0[wbase + k];
+            r1 = s_r1[wbase + k];
+            r2 = s_r2[wbase + k];
+            box = s_box[wbase + k];
+            rec_end += (uint32_t)box.w;
+            xa = box.x & 0xff;
+            ya = (box.x >> 8) & 0xff;
+            za = box.x >> 16;
+            xx = 0;
+            cy = 0;
+            dx = (float)(X0 + xa) - r0.x;
+            dy = (float)(Y0 + ya) - r0.y;
+            dz = (float)(Z0 + za) - r0.z;
+            base_q = fmaf(r1.y * dy, dy, fmaf(r1.z * dz, dz, r2.y * dy * dz));
+            lin = fmaf(r1.w, dy, r2.x * dz);
+            grow = s_g + (za * kB + ya) * kB + xa;
         }
     }
+    const uint32_t gid = s_gid[wbase + k];
+    atomicAdd(&gmom[3 * (size_t)gid], make_float4(S0, Sx, Sy, Sz));
+    atomicAdd(&gmom[3 * (size_t)gid + 1], make_float4(Sxx, Syy, Szz, Sxy));
+    atomicAdd(reinterpret_cast<float2*>(&gmom[3 * (size_t)gid + 2]), make_float2(Sxz, Syz));
 }
 
 __device__ __forceinline__ void quat_grad(const float qn[4], float qnorm, const float g[3][3], float dq[4]) {
@@ -520,9 +611,9 @@ VoxLayout vox_layout(int64_t M, const Grids& grids) {
     L.rect = lay.take(16 * (size_t)L.n_rec);
     L.partials = lay.take(8 * (size_t)kScanBlocks);
     L.ranges = lay.take(8 * (size_t)L.n_bricks);
+    L.item_status = lay.take(sizeof(WsStatus));  // directly after the ranges (cleared together)
     L.mom = lay.take(48 * (size_t)L.n_rec);
     L.scratch = lay.take(sort_scratch_bytes());
-    L.item_status = lay.take(sizeof(WsStatus));
     L.item_off = lay.take(4 * (size_t)L.n_bricks);
     L.fixed = lay.off;
     return L;
@@ -634,11 +725,10 @@ r2g_status voxelize_impl(int64_t M, const float* mean, const float* scale, const
     uint64_t* sorted = radix_sort_u64(a, b, scratch, st, bits_for(L.n_bricks), sort_blocks_for(cap), stream);
     prof_end(P_SORT, stream);
     prof_begin(P_RANGES, stream);
-    build_ranges(sorted, st, ranges, L.n_bricks, stream);
-    build_items(ranges, L.n_bricks, item_st, item_off, items, T.icap, partials, stream);
+    build_ranges_items(sorted, st, ranges, L.n_bricks, item_st, item_off, items, T.icap, stream);
     prof_end(P_RANGES, stream);
     const float Tq = -0.5f * kLog2e * Q3;
-    note_launches(1 + 3 + 3 * ((bits_for(L.n_bricks) + kRadixBits - 1) / kRadixBits) + 1 + 3 + 2);
+    note_launches(1 + 3 + 3 * ((bits_for(L.n_bricks) + kRadixBits - 1) / kRadixBits) + 1 + 2);
     prof_begin(P_VOX_FWD, stream);
     if (count)
         k_vox_fwd<true><<<(unsigned)T.icap, kVoxThreads, 0, stream>>>(rec, ranges, sorted, items, item_st, partial, M,
