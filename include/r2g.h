@@ -256,6 +256,52 @@ r2g_status r2g_adam_step(int64_t M, float* raw, float* act, float* grad, float* 
  * entries that call needed.  Clears nothing. */
 r2g_status r2g_poll(const void* ws, size_t ws_bytes, r2g_stream stream, int64_t* needed_keys);
 
+/* ---------------------------------------------------------------- training step
+ *
+ * One iteration of Eq. 8 for one scan (rasterize one view, L1 + lambda_ssim
+ * D-SSIM against its measurement, voxelize one D^3 TV patch, lambda_tv TV, both
+ * backward passes, Adam), launched on `stream` with no host synchronisation.
+ * Every per-iteration choice comes from a DEVICE round entry, read when the
+ * kernels run, so a sequence of r2g_train_step calls over many scans can be
+ * captured once in a CUDA graph and replayed each round after rewriting the
+ * entries.  Workspaces are sized for M Gaussians x 1 view (raster), 1 grid of D^3
+ * (voxel), 1 x H x W (loss) and 1 x D (TV); list overflow is reported in the
+ * raster/voxel workspace status (r2g_poll). */
+typedef struct {
+    int32_t view;      /* index of the view (and measured projection) this iteration */
+    int32_t it;        /* 0-based iteration for the learning-rate schedule and bias correction */
+    float origin[3];   /* origin of the TV patch grid */
+    int32_t pad[3];
+} r2g_round_entry;
+
+typedef struct {
+    int64_t M;
+    float *raw, *act, *grad, *adam_m, *adam_v;  /* device [11 M]: quat | mean | scale | rho (see r2g_adam_step) */
+    int32_t V;                                  /* views in the scan */
+    const float* views;                         /* device [V][12] */
+    const float* meas;                          /* device [V][H][W] measured log projections */
+    r2g_camera cam;
+    r2g_raster_opts ropts;
+    float Q3;                                   /* voxel gate */
+    int32_t D;                                  /* TV patch edge in voxels */
+    float voxel;                                /* TV patch voxel size (the output volume's spacing) */
+    float lambda_ssim, lambda_tv;
+    r2g_adam_opts adam;
+    float *image, *dimage;                      /* device [H][W] */
+    float *vol, *dvol;                          /* device [D^3] */
+    float* loss;                                /* device [2]: projection loss, TV loss */
+    void* raster_ws;
+    size_t raster_ws_bytes;
+    void* voxel_ws;
+    size_t voxel_ws_bytes;
+    void* loss_ws;
+    size_t loss_ws_bytes;
+    void* tv_ws;
+    size_t tv_ws_bytes;
+} r2g_job;
+
+r2g_status r2g_train_step(const r2g_job* job, const r2g_round_entry* entry, r2g_stream stream);
+
 /* ---------------------------------------------------------------- measurement
  *
  * Optional timing of the library's own kernels: when enabled, every call records

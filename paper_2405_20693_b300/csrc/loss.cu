@@ -36,7 +36,10 @@ struct Win {
 constexpr float kC1 = 1e-4f;      // (0.01 L)^2, L = 1
 constexpr float kC2 = 9e-4f;      // (0.03 L)^2
 
-__global__ void __launch_bounds__(256) k_ssim_maps(const float* __restrict__ x, const float* __restrict__ y, int H,
+// meas_sel (optional, device): view v of the batch is compared with measurement
+// meas_sel[v] of y.
+__global__ void __launch_bounds__(256) k_ssim_maps(const float* __restrict__ x, const float* __restrict__ y,
+                                                   const int* __restrict__ meas_sel, int H,
                                                    int W, int tiles_x, int tiles_per_view, const Win win,
                                                    float* __restrict__ dmu,
                                                    float* __restrict__ dxx, float* __restrict__ dxy,
@@ -49,7 +52,7 @@ __global__ void __launch_bounds__(256) k_ssim_maps(const float* __restrict__ x, 
     const int ty = lt / tiles_x, tx = lt - ty * tiles_x;
     const int Y0 = ty * kT - kR, X0 = tx * kT - kR;
     const float* xv = x + (size_t)v * H * W;
-    const float* yv = y + (size_t)v * H * W;
+    const float* yv = y + (size_t)(meas_sel ? meas_sel[v] : v) * H * W;
     for (int k = threadIdx.x; k < kE * kE; k += 256) {
         const int r = k / kE, c = k - r * kE;
         const int gy = Y0 + r, gx = X0 + c;
@@ -126,7 +129,8 @@ __global__ void __launch_bounds__(256) k_ssim_maps(const float* __restrict__ x, 
     }
 }
 
-__global__ void __launch_bounds__(256) k_ssim_grad(const float* __restrict__ x, const float* __restrict__ y, int H,
+__global__ void __launch_bounds__(256) k_ssim_grad(const float* __restrict__ x, const float* __restrict__ y,
+                                                   const int* __restrict__ meas_sel, int H,
                                                    int W, int tiles_x, int tiles_per_view, const Win win,
                                                    const float* __restrict__ dmu, const float* __restrict__ dxx,
                                                    const float* __restrict__ dxy, float l1_scale, float ssim_scale,
@@ -178,7 +182,7 @@ __global__ void __launch_bounds__(256) k_ssim_grad(const float* __restrict__ x, 
             b2 = fmaf(w, h[2][r + j][c], b2);
         }
         const size_t o = vb + (size_t)gy * W + gx;
-        const float xv = x[o], yv = y[o];
+        const float xv = x[o], yv = y[(size_t)(meas_sel ? meas_sel[v] : v) * H * W + (size_t)gy * W + gx];
         const float d = xv - yv;
         const float sgn = (d > 0.f) ? 1.f : ((d < 0.f) ? -1.f : 0.f);
         grad[o] = l1_scale * sgn - ssim_scale * (b0 + 2.f * xv * b1 + yv * b2);
@@ -320,9 +324,9 @@ R2G_API size_t r2g_loss_workspace_size(int32_t V, int32_t H, int32_t W) {
     return loss_layout(V, H, W).fixed;
 }
 
-R2G_API r2g_status r2g_projection_loss(int32_t V, int32_t H, int32_t W, const float* render, const float* meas,
-                                       float lambda_ssim, float* loss, float* drender, void* ws, size_t ws_bytes,
-                                       r2g_stream stream) {
+r2g_status r2g::projection_loss_impl(int32_t V, int32_t H, int32_t W, const float* render, const float* meas,
+                                     const int* meas_sel, float lambda_ssim, float* loss, float* drender, void* ws,
+                                     size_t ws_bytes, cudaStream_t stream) {
     if (V < 1 || H < 1 || W < 1 || H > 32768 || W > 32768) return fail(R2G_E_INVAL, "bad image shape");
     if (!render || !meas || !loss || !drender || !ws) return fail(R2G_E_INVAL, "NULL pointer");
     if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(R2G_E_INVAL, "workspace must be 256-byte aligned");
@@ -337,15 +341,22 @@ R2G_API r2g_status r2g_projection_loss(int32_t V, int32_t H, int32_t W, const fl
     float* partials = reinterpret_cast<float*>(base + L.partials);
     const int tpv = L.tiles_x * L.tiles_y;
     prof_begin(P_LOSS, stream);
-    k_ssim_maps<<<(unsigned)L.n_tiles, 256, 0, stream>>>(render, meas, H, W, L.tiles_x, tpv, win, dmu, dxx, dxy,
-                                                          partials);
+    k_ssim_maps<<<(unsigned)L.n_tiles, 256, 0, stream>>>(render, meas, meas_sel, H, W, L.tiles_x, tpv, win, dmu,
+                                                          dxx, dxy, partials);
     const double N = (double)V * H * W;
-    k_ssim_grad<<<(unsigned)L.n_tiles, 256, 0, stream>>>(render, meas, H, W, L.tiles_x, tpv, win, dmu, dxx, dxy,
+    k_ssim_grad<<<(unsigned)L.n_tiles, 256, 0, stream>>>(render, meas, meas_sel, H, W, L.tiles_x, tpv, win, dmu,
+                                                          dxx, dxy,
                                                           (float)(1.0 / N), (float)(lambda_ssim / N), drender,
                                                           partials, (int)L.n_tiles, lambda_ssim, 1.0 / N, loss);
     prof_end(P_LOSS, stream);
     note_launches(2);
     return check_launch("r2g_projection_loss");
+}
+
+R2G_API r2g_status r2g_projection_loss(int32_t V, int32_t H, int32_t W, const float* render, const float* meas,
+                                       float lambda_ssim, float* loss, float* drender, void* ws, size_t ws_bytes,
+                                       r2g_stream stream) {
+    return projection_loss_impl(V, H, W, render, meas, nullptr, lambda_ssim, loss, drender, ws, ws_bytes, stream);
 }
 
 R2G_API size_t r2g_tv_workspace_size(int32_t G, int32_t D) {

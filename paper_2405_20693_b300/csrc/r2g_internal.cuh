@@ -100,6 +100,28 @@ inline int bits_for(int64_t n_slots) {
     return b;
 }
 
+// ---------------------------------------------------------------- internal entry points
+// The public calls with device-side selectors for the graph-capturable training
+// step: view_sel picks views (and measured projections) by an index read on the
+// device; origin_dev overrides grid origins; it_dev supplies Adam's iteration.
+
+r2g_status rasterize_impl(int64_t M, const float* mean, const float* scale, const float* quat, const float* rho,
+                          int32_t V, const float* views, const int* view_sel, const r2g_camera* cam,
+                          const r2g_raster_opts* opts, float* image, void* ws, size_t ws_bytes, cudaStream_t stream);
+r2g_status rasterize_backward_impl(int64_t M, const float* mean, const float* scale, const float* quat,
+                                   const float* rho, int32_t V, const float* views, const int* view_sel,
+                                   const r2g_camera* cam, const r2g_raster_opts* opts, const float* dimage,
+                                   float* dmean, float* dscale, float* dquat, float* drho, void* ws, size_t ws_bytes,
+                                   cudaStream_t stream);
+r2g_status voxelize_impl(int64_t M, const float* mean, const float* scale, const float* quat, const float* rho,
+                         int32_t G, const r2g_grid* grids, const float* origin_dev, float Q3, float* vol, void* ws,
+                         size_t ws_bytes, cudaStream_t stream, bool count);
+r2g_status projection_loss_impl(int32_t V, int32_t H, int32_t W, const float* render, const float* meas,
+                                const int* meas_sel, float lambda_ssim, float* loss, float* drender, void* ws,
+                                size_t ws_bytes, cudaStream_t stream);
+r2g_status adam_impl(int64_t M, float* raw, float* act, float* grad, float* m, float* v, int32_t it,
+                     const int* it_dev, const r2g_adam_opts* opts, cudaStream_t stream);
+
 // ---------------------------------------------------------------- device helpers
 
 __device__ __forceinline__ float ex2_approx(float x) {

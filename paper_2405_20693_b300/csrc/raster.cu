@@ -212,14 +212,16 @@ constexpr float kTwoPi = 6.283185307179586f;
 
 // ------------------------------------------------------------------ K1: project
 
-__global__ void __launch_bounds__(256) k_project(Params G, const float* __restrict__ views, CamF cam, float Q,
-                                                 int TW, int TH, long long M, long long n_rec,
-                                                 float4* __restrict__ rec, uint2* __restrict__ rect,
-                                                 float* __restrict__ proj_out, int* __restrict__ rect_out) {
+// view_sel (optional, device): view v of this call is views[view_sel[v]].
+__global__ void __launch_bounds__(256) k_project(Params G, const float* __restrict__ views,
+                                                 const int* __restrict__ view_sel, CamF cam, float Q, int TW, int TH,
+                                                 long long M, long long n_rec, float4* __restrict__ rec,
+                                                 uint2* __restrict__ rect, float* __restrict__ proj_out,
+                                                 int* __restrict__ rect_out) {
     const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_rec) return;
     const long long v = r / M, i = r - v * M;
-    const float* view = views + 12 * v;
+    const float* view = views + 12 * (view_sel ? (long long)view_sel[v] : v);
     float p[3], s[3], q[4];
     load_gaussian(G, i, p, s, q);
     Proj P;
@@ -586,7 +588,8 @@ __device__ __forceinline__ void quat_grad(const float qn[4], float qnorm, const 
     dq[3] = (dz - z * dot) / qnorm;
 }
 
-__global__ void __launch_bounds__(128) k_project_bwd(Params G, const float* __restrict__ views, CamF cam, float Q,
+__global__ void __launch_bounds__(128) k_project_bwd(Params G, const float* __restrict__ views,
+                                                     const int* __restrict__ view_sel, CamF cam, float Q,
                                                      long long M, int V, const float4* __restrict__ rec,
                                                      const float4* __restrict__ mom, float* __restrict__ dmean,
                                                      float* __restrict__ dscale, float* __restrict__ dquat,
@@ -605,7 +608,7 @@ __global__ void __launch_bounds__(128) k_project_bwd(Params G, const float* __re
         const float4 m1 = mom[2 * r + 1];
         if (m0.x == 0.f && m0.y == 0.f && m0.z == 0.f && m0.w == 0.f && m1.x == 0.f && m1.y == 0.f) continue;
         const float rhohat = rec[2 * r + 1].y;
-        const float* view = views + 12 * v;
+        const float* view = views + 12 * (view_sel ? view_sel[v] : v);
         project_stated(p, s, q, view, cam, P);
         have_rot = true;
         // --- moments -> gradients of the pixel-unit record
@@ -895,16 +898,16 @@ R2G_API r2g_status r2g_project(int64_t M, const float* mean, const float* scale,
     if (reinterpret_cast<uintptr_t>(quat) % 16) return fail(R2G_E_INVAL, "quat must be 16-byte aligned");
     const long long n = (long long)M * V;
     Params G{mean, scale, quat, rho};
-    k_project<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(G, views, camf(cam), opts->Q, opts->tile_w,
+    k_project<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(G, views, nullptr, camf(cam), opts->Q, opts->tile_w,
                                                                 opts->tile_h, M, n, nullptr, nullptr, proj, rect);
     note_launches(1);
     return check_launch("r2g_project");
 }
 
-R2G_API r2g_status r2g_rasterize(int64_t M, const float* mean, const float* scale, const float* quat,
-                                 const float* rho, int32_t V, const float* views, const r2g_camera* cam,
-                                 const r2g_raster_opts* opts, float* image, void* ws, size_t ws_bytes,
-                                 r2g_stream stream) {
+r2g_status r2g::rasterize_impl(int64_t M, const float* mean, const float* scale, const float* quat,
+                               const float* rho, int32_t V, const float* views, const int* view_sel,
+                               const r2g_camera* cam, const r2g_raster_opts* opts, float* image, void* ws,
+                               size_t ws_bytes, cudaStream_t stream) {
     r2g_status e = check_args(M, V, cam, opts);
     if (e) return e;
     if (!mean || !scale || !quat || !rho || !views || !image || !ws) return fail(R2G_E_INVAL, "NULL pointer");
@@ -932,9 +935,9 @@ R2G_API r2g_status r2g_rasterize(int64_t M, const float* mean, const float* scal
     Params G{mean, scale, quat, rho};
     const CamF cf = camf(cam);
     prof_begin(P_PROJECT, stream);
-    k_project<<<(unsigned)((L.n_rec + 255) / 256), 256, 0, stream>>>(G, views, cf, opts->Q, opts->tile_w,
-                                                                      opts->tile_h, M, L.n_rec, rec, rect, nullptr,
-                                                                      nullptr);
+    k_project<<<(unsigned)((L.n_rec + 255) / 256), 256, 0, stream>>>(G, views, view_sel, cf, opts->Q,
+                                                                      opts->tile_w, opts->tile_h, M, L.n_rec, rec,
+                                                                      rect, nullptr, nullptr);
     prof_end(P_PROJECT, stream);
     TileOp op{rect, M, L.tiles_x, L.tiles_per_view};
     prof_begin(P_EMIT, stream);
@@ -958,11 +961,18 @@ R2G_API r2g_status r2g_rasterize(int64_t M, const float* mean, const float* scal
     return check_launch("r2g_rasterize");
 }
 
-R2G_API r2g_status r2g_rasterize_backward(int64_t M, const float* mean, const float* scale, const float* quat,
-                                          const float* rho, int32_t V, const float* views, const r2g_camera* cam,
-                                          const r2g_raster_opts* opts, const float* dimage, float* dmean,
-                                          float* dscale, float* dquat, float* drho, void* ws, size_t ws_bytes,
-                                          r2g_stream stream) {
+R2G_API r2g_status r2g_rasterize(int64_t M, const float* mean, const float* scale, const float* quat,
+                                 const float* rho, int32_t V, const float* views, const r2g_camera* cam,
+                                 const r2g_raster_opts* opts, float* image, void* ws, size_t ws_bytes,
+                                 r2g_stream stream) {
+    return rasterize_impl(M, mean, scale, quat, rho, V, views, nullptr, cam, opts, image, ws, ws_bytes, stream);
+}
+
+r2g_status r2g::rasterize_backward_impl(int64_t M, const float* mean, const float* scale, const float* quat,
+                                        const float* rho, int32_t V, const float* views, const int* view_sel,
+                                        const r2g_camera* cam, const r2g_raster_opts* opts, const float* dimage,
+                                        float* dmean, float* dscale, float* dquat, float* drho, void* ws,
+                                        size_t ws_bytes, cudaStream_t stream) {
     r2g_status e = check_args(M, V, cam, opts);
     if (e) return e;
     if (!mean || !scale || !quat || !rho || !views || !dimage || !dmean || !dscale || !dquat || !drho || !ws)
@@ -989,11 +999,20 @@ R2G_API r2g_status r2g_rasterize_backward(int64_t M, const float* mean, const fl
     prof_end(P_SPLAT_BWD, stream);
     Params G{mean, scale, quat, rho};
     prof_begin(P_PROJECT_BWD, stream);
-    k_project_bwd<<<(unsigned)((M + 127) / 128), 128, 0, stream>>>(G, views, camf(cam), opts->Q, M, V, rec, mom,
-                                                                    dmean, dscale, dquat, drho);
+    k_project_bwd<<<(unsigned)((M + 127) / 128), 128, 0, stream>>>(G, views, view_sel, camf(cam), opts->Q, M, V,
+                                                                    rec, mom, dmean, dscale, dquat, drho);
     prof_end(P_PROJECT_BWD, stream);
     note_launches(2);
     return check_launch("r2g_rasterize_backward");
+}
+
+R2G_API r2g_status r2g_rasterize_backward(int64_t M, const float* mean, const float* scale, const float* quat,
+                                          const float* rho, int32_t V, const float* views, const r2g_camera* cam,
+                                          const r2g_raster_opts* opts, const float* dimage, float* dmean,
+                                          float* dscale, float* dquat, float* drho, void* ws, size_t ws_bytes,
+                                          r2g_stream stream) {
+    return rasterize_backward_impl(M, mean, scale, quat, rho, V, views, nullptr, cam, opts, dimage, dmean, dscale,
+                                   dquat, drho, ws, ws_bytes, stream);
 }
 
 R2G_API r2g_status r2g_raster_lists(int64_t M, int32_t V, const r2g_camera* cam, const r2g_raster_opts* opts,

@@ -104,14 +104,18 @@ __device__ __forceinline__ void precision(const float R[3][3], const float s[3],
 
 // ------------------------------------------------------------------ records + brick bound
 
-__global__ void __launch_bounds__(256) k_vox_project(Params G, const __grid_constant__ Grids grids, float Q3,
-                                                     long long M, float4* __restrict__ rec,
-                                                     uint4* __restrict__ rect) {
+// origin_dev (optional, device): grid g's origin is origin_dev[3g .. 3g+2].
+__global__ void __launch_bounds__(256) k_vox_project(Params G, const __grid_constant__ Grids grids,
+                                                     const float* __restrict__ origin_dev, float Q3, long long M,
+                                                     float4* __restrict__ rec, uint4* __restrict__ rect) {
     const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= M * grids.G) return;
     const int g = (int)(r / M);
     const long long i = r - (long long)g * M;
     const GridF& gf = grids.g[g];
+    float org[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) org[k] = origin_dev ? origin_dev[3 * g + k] : gf.o[k];
     float p[3], s[3], q[4], R[3][3], qn[4], qnorm;
     load_gaussian(G, i, p, s, q);
     rotation(q, R, qn, qnorm);
@@ -127,7 +131,7 @@ __global__ void __launch_bounds__(256) k_vox_project(Params G, const __grid_cons
     for (int k = 0; k < 3; ++k) {
         const float skk = fa(fa(fm(Mm[k][0], Mm[k][0]), fm(Mm[k][1], Mm[k][1])), fm(Mm[k][2], Mm[k][2]));
         const float e = __fsqrt_rn(fm(Q3, skk));
-        c[k] = fs(__fdiv_rn(fs(p[k], gf.o[k]), gf.v[k]), 0.5f);
+        c[k] = fs(__fdiv_rn(fs(p[k], org[k]), gf.v[k]), 0.5f);
         rr[k] = __fdiv_rn(e, gf.v[k]);
         lo[k] = max(0, (int)ceil_clamped(fs(c[k], rr[k]), gf.dims[k]));
         hi[k] = min(gf.dims[k] - 1, (int)floor_clamped(fa(c[k], rr[k]), gf.dims[k]));
@@ -676,10 +680,9 @@ R2G_API size_t r2g_voxel_workspace_size(int64_t M, int32_t G, const r2g_grid* gr
 }
 
 namespace r2g {
-namespace {
 r2g_status voxelize_impl(int64_t M, const float* mean, const float* scale, const float* quat, const float* rho,
-                         int32_t G, const r2g_grid* grids, float Q3, float* vol, void* ws, size_t ws_bytes,
-                         cudaStream_t stream, bool count) {
+                         int32_t G, const r2g_grid* grids, const float* origin_dev, float Q3, float* vol, void* ws,
+                         size_t ws_bytes, cudaStream_t stream, bool count) {
     r2g_status e = check_params(M, mean, scale, quat, rho);
     if (e) return e;
     Grids gr;
@@ -708,7 +711,7 @@ r2g_status voxelize_impl(int64_t M, const float* mean, const float* scale, const
     cudaMemsetAsync(st, 0, sizeof(WsStatus), stream);
     Params P{mean, scale, quat, rho};
     prof_begin(P_VOX_PROJECT, stream);
-    k_vox_project<<<(unsigned)((L.n_rec + 255) / 256), 256, 0, stream>>>(P, gr, Q3, M, rec, rect);
+    k_vox_project<<<(unsigned)((L.n_rec + 255) / 256), 256, 0, stream>>>(P, gr, origin_dev, Q3, M, rec, rect);
     prof_end(P_VOX_PROJECT, stream);
     BrickEmitOp op;
     op.rect = rect;
@@ -740,19 +743,18 @@ r2g_status voxelize_impl(int64_t M, const float* mean, const float* scale, const
     prof_end(P_VOX_FWD, stream);
     return check_launch("r2g_voxelize");
 }
-}  // namespace
 }  // namespace r2g
 
 R2G_API r2g_status r2g_voxelize(int64_t M, const float* mean, const float* scale, const float* quat,
                                 const float* rho, int32_t G, const r2g_grid* grids, float Q3, float* vol, void* ws,
                                 size_t ws_bytes, r2g_stream stream) {
-    return voxelize_impl(M, mean, scale, quat, rho, G, grids, Q3, vol, ws, ws_bytes, stream, false);
+    return voxelize_impl(M, mean, scale, quat, rho, G, grids, nullptr, Q3, vol, ws, ws_bytes, stream, false);
 }
 
 R2G_API r2g_status r2g_voxelize_counted(int64_t M, const float* mean, const float* scale, const float* quat,
                                         const float* rho, int32_t G, const r2g_grid* grids, float Q3, float* vol,
                                         void* ws, size_t ws_bytes, r2g_stream stream) {
-    return voxelize_impl(M, mean, scale, quat, rho, G, grids, Q3, vol, ws, ws_bytes, stream, true);
+    return voxelize_impl(M, mean, scale, quat, rho, G, grids, nullptr, Q3, vol, ws, ws_bytes, stream, true);
 }
 
 

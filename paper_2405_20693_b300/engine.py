@@ -231,3 +231,157 @@ class TrainStep:
         self.rast.backward(mean, scale, quat, rho, v, self.dimage, dmean, dscale, dquat, drho)
         self.vox.backward(mean, scale, quat, rho, self.dvol, dmean, dscale, dquat, drho)
         r2g.r2g_adam_step(self.s.raw, self.s.act, self.s.grad, self.s.m, self.s.v, it, self.adam)
+
+
+# ----------------------------------------------------------------------------- multi-scan batching
+
+
+class Scan:
+    """One reconstruction job resident on the device: parameters, Adam state,
+    views, measured projections, step buffers and workspaces, and the C job
+    descriptor for r2g_train_step."""
+
+    def __init__(self, G, views_np, meas_np, cam, n_out=256, D=32, tile=(16, 16), total_iters=30000,
+                 device="cuda", headroom=1.5):
+        self.state = TrainState(G, device=device)
+        self.M = G.M
+        self.cam = cam
+        self.D = D
+        self.n_out = n_out
+        self.views = torch.as_tensor(np.ascontiguousarray(views_np, np.float32), device=device)
+        self.meas = torch.as_tensor(np.ascontiguousarray(meas_np, np.float32), device=device)
+        self.V = int(self.views.shape[0])
+        self.image = torch.empty((1, cam.H, cam.W), dtype=torch.float32, device=device)
+        self.dimage = torch.empty_like(self.image)
+        self.vol = torch.empty(D ** 3, dtype=torch.float32, device=device)
+        self.dvol = torch.empty_like(self.vol)
+        self.loss = torch.zeros(2, dtype=torch.float32, device=device)
+        self.rast = Rasterizer(self.M, 1, cam, tile=tile, device=device)
+        from .inputs import patch_grid
+
+        self.vox = Voxelizer(self.M, patch_grid((0, 0, 0), D, n_out), device=device)
+        self.loss_ws = _bytes(r2g.r2g_loss_workspace_size(1, cam.H, cam.W), device)
+        self.tv_ws = _bytes(r2g.r2g_tv_workspace_size(1, D), device)
+        self.adam = r2g.adam_opts(total_iters=total_iters)
+        self._size_workspaces(headroom)
+        self.job = self._make_job()
+
+    def _size_workspaces(self, headroom):
+        """Size the list workspaces on a spread of views and patch positions with
+        checked runs, then add headroom: the captured graph cannot regrow them."""
+        from .inputs import patch_grid
+
+        mean, scale, quat, rho = self.state.params()
+        need_r, need_v = 0, 0
+        for v in np.linspace(0, self.V - 1, min(self.V, 6)).astype(int):
+            self.rast.forward(mean, scale, quat, rho, self.views[v:v + 1], self.image, check=True)
+            need_r = max(need_r, r2g.r2g_poll(self.rast.ws)[1])
+        for off in ((0, 0, 0), ((self.n_out - self.D) // 2,) * 3, (self.n_out - self.D,) * 3):
+            self.vox.set_grids(patch_grid(off, self.D, self.n_out))
+            self.vox.forward(mean, scale, quat, rho, self.vol, check=True)
+            need_v = max(need_v, r2g.r2g_poll(self.vox.ws)[1])
+        self.rast.capacity = int(need_r * headroom) + 4096
+        self.rast._alloc()
+        self.vox.capacity = int(need_v * headroom) + 4096
+        self.vox._alloc()
+
+    def _make_job(self):
+        s = self.state
+        J = r2g.Job()
+        J.M = self.M
+        J.raw, J.act, J.grad = s.raw.data_ptr(), s.act.data_ptr(), s.grad.data_ptr()
+        J.adam_m, J.adam_v = s.m.data_ptr(), s.v.data_ptr()
+        J.V = self.V
+        J.views, J.meas = self.views.data_ptr(), self.meas.data_ptr()
+        J.cam = self.rast.cam
+        J.ropts = self.rast.opts
+        J.Q3 = Q_VOXEL
+        J.D = self.D
+        J.voxel = 2.0 / self.n_out
+        J.lambda_ssim, J.lambda_tv = LAMBDA_SSIM, LAMBDA_TV
+        J.adam = self.adam
+        J.image, J.dimage = self.image.data_ptr(), self.dimage.data_ptr()
+        J.vol, J.dvol, J.loss = self.vol.data_ptr(), self.dvol.data_ptr(), self.loss.data_ptr()
+        J.raster_ws, J.raster_ws_bytes = self.rast.ws.data_ptr(), self.rast.ws.numel()
+        J.voxel_ws, J.voxel_ws_bytes = self.vox.ws.data_ptr(), self.vox.ws.numel()
+        J.loss_ws, J.loss_ws_bytes = self.loss_ws.data_ptr(), self.loss_ws.numel()
+        J.tv_ws, J.tv_ws_bytes = self.tv_ws.data_ptr(), self.tv_ws.numel()
+        return J
+
+    def overflowed(self) -> bool:
+        return r2g.r2g_poll(self.rast.ws)[0] != r2g.R2G_OK or r2g.r2g_poll(self.vox.ws)[0] != r2g.R2G_OK
+
+
+class BatchTrainer:
+    """Runs one training iteration of every resident scan per round.
+
+    The per-round choices (view, TV patch origin, iteration) live in a device round
+    table [J][8] (r2g_round_entry) filled from pinned host memory by a copy that is
+    part of the round.  With graph=True the whole round -- the table upload and
+    every scan's r2g_train_step, spread over n_streams branches -- is captured once
+    as a CUDA graph and replayed; with graph=False the same calls are issued
+    eagerly on the same streams."""
+
+    def __init__(self, scans, n_streams=4, graph=True, seed=0, device="cuda"):
+        self.scans = list(scans)
+        self.J = len(self.scans)
+        self.device = device
+        self.table_host = torch.zeros((self.J, 8), dtype=torch.int32).pin_memory()
+        self.table_dev = torch.zeros((self.J, 8), dtype=torch.int32, device=device)
+        self.streams = [torch.cuda.Stream(device=device) for _ in range(max(1, n_streams))]
+        self.rng = np.random.Generator(np.random.PCG64(seed + 2))
+        self.it = [0] * self.J
+        self.graph = None
+        self.use_graph = graph
+        self.elem = ctypes_sizeof_entry()
+
+    def _fill(self, active=None):
+        t = self.table_host.numpy()
+        f = t.view(np.float32)
+        for j, sc in enumerate(self.scans):
+            v = int(self.rng.integers(0, sc.V))
+            off = self.rng.integers(0, sc.n_out - sc.D + 1, 3)
+            t[j, 0] = v
+            t[j, 1] = self.it[j]
+            f[j, 2:5] = -1.0 + off * (2.0 / sc.n_out)
+            if active is None or j in active:
+                self.it[j] += 1
+
+    def _issue(self):
+        main = torch.cuda.current_stream()
+        self.table_dev.copy_(self.table_host, non_blocking=True)
+        base = self.table_dev.data_ptr()
+        for j, sc in enumerate(self.scans):
+            s = self.streams[j % len(self.streams)]
+            s.wait_stream(main)
+            with torch.cuda.stream(s):
+                r2g.r2g_train_step(sc.job, base + j * self.elem, s)
+        for s in self.streams:
+            main.wait_stream(s)
+
+    def round(self):
+        """One iteration of every scan.  The host table is rewritten only after the
+        previous round has finished.  With graph=True the first round runs eagerly
+        (which also loads every kernel) and is then captured; later rounds replay."""
+        torch.cuda.current_stream().synchronize()
+        self._fill()
+        if not self.use_graph:
+            self._issue()
+            return
+        if self.graph is None:
+            self._issue()
+            torch.cuda.synchronize()
+            self.graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(self.graph):
+                self._issue()
+            return
+        self.graph.replay()
+
+    def losses(self):
+        return torch.stack([sc.loss for sc in self.scans]).cpu().numpy()
+
+
+def ctypes_sizeof_entry() -> int:
+    import ctypes
+
+    return ctypes.sizeof(r2g.RoundEntry)

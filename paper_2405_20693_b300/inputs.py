@@ -343,3 +343,44 @@ def random_init(M: int, seed: int, radius=0.9, half_height=0.9, rho=0.05) -> Gau
     scale = np.repeat(s[:, None], 3, axis=1)
     quat = np.tile(np.array([1.0, 0, 0, 0]), (M, 1))
     return GaussianSet(mean, scale, quat, np.full(M, rho)).astype(np.float32)
+
+
+# --------------------------------------------------------------------------- multi-scan workload
+
+
+@dataclass
+class ScanSpec:
+    """One scan of the uneven multi-scan workload."""
+
+    seed: int
+    M: int
+    V: int
+    det: int      # detector edge in pixels (the detector always spans 409.6 mm)
+    n_out: int    # output volume edge in voxels (TV patch spacing 2 / n_out)
+
+
+def batched_specs(n_scans: int = 16, seed: int = 5):
+    """Gaussian counts log-uniform in [5k, 300k]; 25, 50 or 75 views; 256^2 or 512^2
+    detectors; 128^3 or 256^3 output volumes."""
+    g = rng(seed)
+    out = []
+    for j in range(n_scans):
+        M = int(round(math.exp(g.uniform(math.log(5e3), math.log(3e5)))))
+        V = int(g.choice([25, 50, 75]))
+        det = int(g.choice([256, 512]))
+        n_out = int(g.choice([128, 256]))
+        out.append(ScanSpec(100 + j, M, V, det, n_out))
+    return out
+
+
+def make_scan(spec: ScanSpec, device=None):
+    """Phantom (seed spec.seed), cone-beam geometry with the detector scaled to
+    409.6 mm, measured projections, and the random initialisation (means in the
+    inscribed cylinder, 3-NN isotropic scales, density 0.05).  Returns
+    (gaussians, camera, views, measured projections, phantom volume)."""
+    ph, vol = normalised_phantom(spec.seed, spec.n_out)
+    cam = cone_camera(spec.det, spec.det, pitch=CONE_PITCH * 512 / spec.det)
+    views = view_table(even_angles(spec.V), CONE_L_SO)
+    meas = phantom_projections(ph, views, cam, device=device).astype(np.float32)
+    G = random_init(spec.M, spec.seed)
+    return G, cam, views, meas, vol

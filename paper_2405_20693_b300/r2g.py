@@ -47,6 +47,24 @@ class AdamOpts(ctypes.Structure):
                 ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float)]
 
 
+class RoundEntry(ctypes.Structure):
+    _fields_ = [("view", ctypes.c_int32), ("it", ctypes.c_int32), ("origin", ctypes.c_float * 3),
+                ("pad", ctypes.c_int32 * 3)]
+
+
+class Job(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int64), ("raw", ctypes.c_void_p), ("act", ctypes.c_void_p),
+                ("grad", ctypes.c_void_p), ("adam_m", ctypes.c_void_p), ("adam_v", ctypes.c_void_p),
+                ("V", ctypes.c_int32), ("views", ctypes.c_void_p), ("meas", ctypes.c_void_p), ("cam", Camera),
+                ("ropts", RasterOpts), ("Q3", ctypes.c_float), ("D", ctypes.c_int32), ("voxel", ctypes.c_float),
+                ("lambda_ssim", ctypes.c_float), ("lambda_tv", ctypes.c_float), ("adam", AdamOpts),
+                ("image", ctypes.c_void_p), ("dimage", ctypes.c_void_p), ("vol", ctypes.c_void_p),
+                ("dvol", ctypes.c_void_p), ("loss", ctypes.c_void_p), ("raster_ws", ctypes.c_void_p),
+                ("raster_ws_bytes", ctypes.c_size_t), ("voxel_ws", ctypes.c_void_p),
+                ("voxel_ws_bytes", ctypes.c_size_t), ("loss_ws", ctypes.c_void_p),
+                ("loss_ws_bytes", ctypes.c_size_t), ("tv_ws", ctypes.c_void_p), ("tv_ws_bytes", ctypes.c_size_t)]
+
+
 def camera(cam) -> Camera:
     """Camera struct from an ``inputs.Camera``-like object."""
     return Camera(int(cam.beam), int(cam.H), int(cam.W), float(cam.L_SD), float(cam.pitch_u), float(cam.pitch_v),
@@ -112,6 +130,7 @@ def lib():
             "r2g_tv3d_noalloc": (_I32, [_I32, _I32, _P, _F, _P, _P, _P]),
             "r2g_adam_step": (_I32, [_I64, _P, _P, _P, _P, _P, _I32, _P, _P]),
             "r2g_poll": (_I32, [_P, _SZ, _P, _P]),
+            "r2g_train_step": (_I32, [_P, _P, _P]),
             "r2g_profile_enable": (_I32, [_I32, _I32]),
             "r2g_profile_reset": (_I32, []),
             "r2g_profile_read": (_I32, [_I32, _P, _P]),
@@ -316,6 +335,12 @@ def r2g_profile_name(kernel: int) -> str:
 
 def r2g_launch_count() -> int:
     return int(lib().r2g_launch_count())
+
+
+def r2g_train_step(job: Job, entry_ptr: int, stream=None):
+    """One training iteration of one scan; entry_ptr is the device address of its
+    round entry (r2g_round_entry)."""
+    _check(lib().r2g_train_step(ctypes.byref(job), ctypes.c_void_p(int(entry_ptr)), _stream(stream)))
 
 
 def r2g_version() -> str:

@@ -1,0 +1,104 @@
+"""The fused training step (r2g_train_step) against the oracle's composition of the
+same step, and the batched, graph-captured multi-scan round against the same
+scans run one at a time."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_util import TOL_GRAD, dev, host
+from oracle import core, losses
+from paper_2405_20693_b300 import build, engine, r2g
+from paper_2405_20693_b300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+
+
+def small_scan(seed, M, det, V=8, n_out=64):
+    spec = I.ScanSpec(seed, M, V, det, n_out)
+    G, cam, views, meas, vol = I.make_scan(spec, device="cuda")
+    return G, cam, views, meas
+
+
+def entry_table(rows):
+    t = np.zeros((len(rows), 8), np.int32)
+    f = t.view(np.float32)
+    for j, (v, it, origin) in enumerate(rows):
+        t[j, 0], t[j, 1] = v, it
+        f[j, 2:5] = origin
+    return torch.as_tensor(t, device="cuda")
+
+
+def test_train_step_matches_oracle_composition():
+    """One iteration (view 3, TV patch at a fixed origin) from a fresh state: the
+    losses match the oracle's, and Adam's first moment -- (1 - beta1) times the
+    raw-parameter gradient after one step -- matches the oracle's adjoints chained
+    through the activations, within the gradient tolerance plus the gate band."""
+    G, cam, views, meas = small_scan(200, 3000, 128)
+    sc = engine.Scan(G, views, meas, cam, n_out=64, D=16)
+    act_before = [host(t) for t in sc.state.views_of(sc.state.act)]  # quat, mean, scale, rho
+    raw_before = [host(t) for t in sc.state.views_of(sc.state.raw)]
+    origin = (-0.25, -0.5, 0.0)
+    table = entry_table([(3, 0, origin)])
+    r2g.r2g_train_step(sc.job, table.data_ptr(), torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    Ga = I.GaussianSet(act_before[1], act_before[2], act_before[0], act_before[3])
+    img, _ = core.render(Ga, views[3:4], cam, Q=engine.Q_PIXEL)
+    L1, dimg = losses.projection_loss(img, meas[3:4], engine.LAMBDA_SSIM)
+    gd = np.asarray(I.grid_desc(origin, (2 / 64,) * 3, (16, 16, 16)), np.float32).astype(np.float64)
+    vol, _ = core.voxelize(Ga, gd, engine.Q_VOXEL)
+    Ltv, dvol = losses.tv3d(vol.reshape(16, 16, 16), engine.LAMBDA_TV)
+    loss = host(sc.loss)
+    assert abs(loss[0] - L1) <= 1e-4 * abs(L1)
+    assert abs(loss[1] - Ltv) <= 1e-4 * abs(Ltv) + 1e-7
+    (gr, br) = core.render_backward(Ga, views[3:4], cam, dimg, Q=engine.Q_PIXEL, want_band=True)
+    (gv, bv) = core.voxelize_backward(Ga, gd, dvol.ravel(), engine.Q_VOXEL, want_band=True)
+    # activated -> raw chain: scale = exp(raw), rho = softplus(raw)
+    sig = 1.0 / (1.0 + np.exp(-raw_before[3].astype(np.float64)))
+    chain = {"quat": 1.0, "mean": 1.0, "scale": act_before[2], "rho": sig}
+    ref = {"mean": gr[0] + gv[0], "scale": gr[1] + gv[1], "quat": gr[2] + gv[2], "rho": gr[3] + gv[3]}
+    band = {"mean": br[0] + bv[0], "scale": br[1] + bv[1], "quat": br[2] + bv[2], "rho": br[3] + bv[3]}
+    mq, mm, ms, mr = (host(t) / 0.1 for t in sc.state.views_of(sc.state.m))
+    for name, got in (("quat", mq), ("mean", mm), ("scale", ms), ("rho", mr)):
+        want = ref[name] * chain[name]
+        bd = band[name] * np.abs(chain[name])
+        n = np.abs(want).max()
+        assert (np.abs(got - want) - bd).max() <= TOL_GRAD * n, name
+
+
+def _run_alone(G, cam, views, meas, rows):
+    sc = engine.Scan(G, views, meas, cam, n_out=64, D=16)
+    for r in rows:
+        t = entry_table([r])
+        r2g.r2g_train_step(sc.job, t.data_ptr(), torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    return sc
+
+
+def test_batched_graph_round_equals_scans_alone():
+    """Three uneven scans trained together (one CUDA graph per round, four streams)
+    give each scan the same parameters as training it alone with the same choices."""
+    setups = [small_scan(210, 4000, 128), small_scan(211, 1500, 64, V=5), small_scan(212, 9000, 128, V=11)]
+    scans = [engine.Scan(G, v, m, c, n_out=64, D=16) for (G, c, v, m) in setups]
+    bt = engine.BatchTrainer(scans, n_streams=4, graph=True, seed=7)
+    history = []
+    for _ in range(4):
+        bt.round()
+        history.append(host(bt.table_dev).copy())
+    torch.cuda.synchronize()
+    for j, (G, cam, views, meas) in enumerate(setups):
+        rows = []
+        for h in history:
+            f = h.view(np.float32)
+            rows.append((int(h[j, 0]), int(h[j, 1]), tuple(float(x) for x in f[j, 2:5])))
+        alone = _run_alone(G, cam, views, meas, rows)
+        a = host(scans[j].state.act)
+        b = host(alone.state.act)
+        # identical arithmetic up to the order of float atomics in the backward passes
+        assert np.abs(a - b).max() <= 1e-4 * max(1.0, np.abs(b).max()), j
+        assert np.allclose(host(scans[j].loss), host(alone.loss), rtol=1e-4, atol=1e-7), j
+    assert [bt.it[j] for j in range(3)] == [4, 4, 4]
