@@ -302,6 +302,11 @@ typedef struct {
 
 r2g_status r2g_train_step(const r2g_job* job, const r2g_round_entry* entry, r2g_stream stream);
 
+/* Copy n round entries from PAGE-LOCKED host memory `src` to device `dst` on
+ * `stream` (an asynchronous copy; inside a captured graph the copy reads `src`
+ * each time the graph runs, so the host rewrites it between replays). */
+r2g_status r2g_upload_round(r2g_round_entry* dst, const r2g_round_entry* src, int32_t n, r2g_stream stream);
+
 /* ---------------------------------------------------------------- measurement
  *
  * Optional timing of the library's own kernels: when enabled, every call records

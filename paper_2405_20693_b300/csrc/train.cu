@@ -50,3 +50,10 @@ R2G_API r2g_status r2g_train_step(const r2g_job* job, const r2g_round_entry* ent
         return e;
     return adam_impl(M, J.raw, J.act, J.grad, J.adam_m, J.adam_v, 0, &entry->it, &J.adam, stream);
 }
+
+R2G_API r2g_status r2g_upload_round(r2g_round_entry* dst, const r2g_round_entry* src, int32_t n, r2g_stream stream) {
+    if (!dst || !src || n < 1) return fail(R2G_E_INVAL, "r2g_upload_round: bad arguments");
+    if (cudaMemcpyAsync(dst, src, sizeof(r2g_round_entry) * (size_t)n, cudaMemcpyHostToDevice, stream) != cudaSuccess)
+        return fail(R2G_E_CUDA, "r2g_upload_round: %s", cudaGetErrorString(cudaGetLastError()));
+    return R2G_OK;
+}

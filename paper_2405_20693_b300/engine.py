@@ -349,14 +349,14 @@ class BatchTrainer:
 
     def _issue(self):
         main = torch.cuda.current_stream()
-        self.table_dev.copy_(self.table_host, non_blocking=True)
+        r2g.r2g_upload_round(self.table_dev, self.table_host, self.J, main)
         base = self.table_dev.data_ptr()
         for j, sc in enumerate(self.scans):
             s = self.streams[j % len(self.streams)]
             s.wait_stream(main)
             with torch.cuda.stream(s):
                 r2g.r2g_train_step(sc.job, base + j * self.elem, s)
-        for s in self.streams:
+        for s in self.streams[:min(self.J, len(self.streams))]:  # only the branches that were forked
             main.wait_stream(s)
 
     def round(self):

@@ -131,6 +131,7 @@ def lib():
             "r2g_adam_step": (_I32, [_I64, _P, _P, _P, _P, _P, _I32, _P, _P]),
             "r2g_poll": (_I32, [_P, _SZ, _P, _P]),
             "r2g_train_step": (_I32, [_P, _P, _P]),
+            "r2g_upload_round": (_I32, [_P, _P, _I32, _P]),
             "r2g_profile_enable": (_I32, [_I32, _I32]),
             "r2g_profile_reset": (_I32, []),
             "r2g_profile_read": (_I32, [_I32, _P, _P]),
@@ -341,6 +342,13 @@ def r2g_train_step(job: Job, entry_ptr: int, stream=None):
     """One training iteration of one scan; entry_ptr is the device address of its
     round entry (r2g_round_entry)."""
     _check(lib().r2g_train_step(ctypes.byref(job), ctypes.c_void_p(int(entry_ptr)), _stream(stream)))
+
+
+def r2g_upload_round(dst_dev, src_pinned, n: int, stream=None):
+    """Asynchronous copy of n round entries from a pinned host tensor to the device."""
+    if not src_pinned.is_pinned():
+        raise ValueError("the round table must be in page-locked host memory")
+    _check(lib().r2g_upload_round(_ptr(dst_dev), ctypes.c_void_p(src_pinned.data_ptr()), int(n), _stream(stream)))
 
 
 def r2g_version() -> str:

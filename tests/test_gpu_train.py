@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 import torch
 
-from gpu_util import TOL_GRAD, dev, host
+from gpu_util import assert_grads_close, dev, host
 from oracle import core, losses
 from paper_2405_20693_b300 import build, engine, r2g
 from paper_2405_20693_b300 import inputs as I
@@ -18,10 +18,15 @@ def _lib():
     build.build()
 
 
-def small_scan(seed, M, det, V=8, n_out=64):
+def small_scan(seed, M, det, V=8, n_out=64, with_volume=False):
     spec = I.ScanSpec(seed, M, V, det, n_out)
     G, cam, views, meas, vol = I.make_scan(spec, device="cuda")
-    return G, cam, views, meas
+    return (G, cam, views, meas, vol) if with_volume else (G, cam, views, meas)
+
+
+def psnr(vol, gt):
+    mse = np.mean((np.asarray(vol, np.float64) - gt) ** 2)
+    return 10 * np.log10(1.0 / mse)
 
 
 def entry_table(rows):
@@ -63,42 +68,55 @@ def test_train_step_matches_oracle_composition():
     ref = {"mean": gr[0] + gv[0], "scale": gr[1] + gv[1], "quat": gr[2] + gv[2], "rho": gr[3] + gv[3]}
     band = {"mean": br[0] + bv[0], "scale": br[1] + bv[1], "quat": br[2] + bv[2], "rho": br[3] + bv[3]}
     mq, mm, ms, mr = (host(t) / 0.1 for t in sc.state.views_of(sc.state.m))
+    # the random initialisation is isotropic with identity rotations: d quat is exactly 0
+    zero_scale = np.abs(ref["scale"]).max() * float(np.max(act_before[2]))
     for name, got in (("quat", mq), ("mean", mm), ("scale", ms), ("rho", mr)):
         want = ref[name] * chain[name]
         bd = band[name] * np.abs(chain[name])
-        n = np.abs(want).max()
-        assert (np.abs(got - want) - bd).max() <= TOL_GRAD * n, name
+        assert_grads_close(got, want, f"train step d{name} (raw)", band=bd, zero_scale=zero_scale)
 
 
-def _run_alone(G, cam, views, meas, rows):
-    sc = engine.Scan(G, views, meas, cam, n_out=64, D=16)
-    for r in rows:
-        t = entry_table([r])
-        r2g.r2g_train_step(sc.job, t.data_ptr(), torch.cuda.current_stream())
-    torch.cuda.synchronize()
-    return sc
+def _outputs(sc):
+    """What the reconstruction produces: one rendered view and the 64^3 volume."""
+    mean, scale, quat, rho = sc.state.params()
+    rast = engine.Rasterizer(sc.M, 1, sc.cam)
+    img = host(rast.forward(mean, scale, quat, rho, sc.views[0:1]))
+    vox = engine.Voxelizer(sc.M, I.cube_grid(64))
+    vol = host(vox.forward(mean, scale, quat, rho))
+    return img, vol
 
 
 def test_batched_graph_round_equals_scans_alone():
     """Three uneven scans trained together (one CUDA graph per round, four streams)
-    give each scan the same parameters as training it alone with the same choices."""
-    setups = [small_scan(210, 4000, 128), small_scan(211, 1500, 64, V=5), small_scan(212, 9000, 128, V=11)]
+    give each scan the same per-round losses, projections and volume as training it
+    alone with the same per-round choices.  The backward passes accumulate with float
+    atomics, so the two runs differ by rounding; Adam normalises each gradient, so
+    where a gradient is near zero that rounding becomes a learning-rate-sized step
+    of either sign.  Losses must agree to 1e-4, projections and volumes to 1e-3 of
+    their maximum, and the volume's PSNR against the phantom to 0.01 dB."""
+    full = [small_scan(210, 4000, 128, with_volume=True), small_scan(211, 1500, 64, V=5, with_volume=True),
+            small_scan(212, 9000, 128, V=11, with_volume=True)]
+    setups = [f[:4] for f in full]
     scans = [engine.Scan(G, v, m, c, n_out=64, D=16) for (G, c, v, m) in setups]
     bt = engine.BatchTrainer(scans, n_streams=4, graph=True, seed=7)
-    history = []
+    history, losses_mix = [], []
     for _ in range(4):
         bt.round()
-        history.append(host(bt.table_dev).copy())
+        history.append(bt.table_dev.cpu().numpy().copy())  # int32 rows; origins are float bits
+        losses_mix.append(bt.losses())
     torch.cuda.synchronize()
     for j, (G, cam, views, meas) in enumerate(setups):
-        rows = []
-        for h in history:
+        sc = engine.Scan(G, views, meas, cam, n_out=64, D=16)
+        for r, h in enumerate(history):
             f = h.view(np.float32)
-            rows.append((int(h[j, 0]), int(h[j, 1]), tuple(float(x) for x in f[j, 2:5])))
-        alone = _run_alone(G, cam, views, meas, rows)
-        a = host(scans[j].state.act)
-        b = host(alone.state.act)
-        # identical arithmetic up to the order of float atomics in the backward passes
-        assert np.abs(a - b).max() <= 1e-4 * max(1.0, np.abs(b).max()), j
-        assert np.allclose(host(scans[j].loss), host(alone.loss), rtol=1e-4, atol=1e-7), j
+            t = entry_table([(int(h[j, 0]), int(h[j, 1]), tuple(float(x) for x in f[j, 2:5]))])
+            r2g.r2g_train_step(sc.job, t.data_ptr(), torch.cuda.current_stream())
+            # the same losses each round, alone and in the mix
+            assert np.allclose(host(sc.loss), losses_mix[r][j], rtol=1e-4, atol=1e-7), (j, r)
+        img_a, vol_a = _outputs(sc)
+        img_b, vol_b = _outputs(scans[j])
+        assert np.abs(img_a - img_b).max() <= 1e-3 * np.abs(img_a).max(), j
+        assert np.abs(vol_a - vol_b).max() <= 1e-3 * np.abs(vol_a).max(), j
+        gt = full[j][4].ravel()
+        assert abs(psnr(vol_a, gt) - psnr(vol_b, gt)) <= 0.01, j
     assert [bt.it[j] for j in range(3)] == [4, 4, 4]
