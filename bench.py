@@ -218,6 +218,73 @@ def ncu_traffic(kernel: str):
         return None
 
 
+def measure_batched(dev, rounds=20, n_scans=16, seed=5):
+    """Scans/hour of the uneven 16-scan workload: one scan at a time (each scan's
+    fused training step, eagerly, scan after scan) against all scans batched (one
+    CUDA graph per round, one branch per scan on its own stream).  Both run the same
+    per-scan arithmetic; the scans/hour figures assume 30,000 iterations per scan."""
+    import torch
+
+    from paper_2405_20693_b300 import engine, r2g
+    from paper_2405_20693_b300 import inputs as I
+
+    specs = I.batched_specs(n_scans, seed)
+    scans = []
+    for sp in specs:
+        G, cam, views, meas, _ = I.make_scan(sp, device=dev)
+        scans.append(engine.Scan(G, views, meas, cam, n_out=sp.n_out, D=D_TV, device=dev, seed=sp.seed))
+    # one scan at a time
+    table = torch.zeros((1, 8), dtype=torch.int32).pin_memory()
+    tdev = torch.zeros((1, 8), dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+    per_scan_ms = []
+    for sc in scans:
+        t = table.numpy()
+        f = t.view(np.float32)
+        evs = []
+        for k in range(rounds + 3):
+            v, it, origin = sc.next_entry()
+            t[0, 0], t[0, 1] = v, it
+            f[0, 2:5] = origin
+            stream.synchronize()
+            r2g.r2g_upload_round(tdev, table, 1, stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r2g.r2g_train_step(sc.job, tdev.data_ptr(), stream)
+            e1.record(stream)
+            if k >= 3:
+                evs.append((e0, e1))
+        torch.cuda.synchronize()
+        per_scan_ms.append(sum(a.elapsed_time(b) for a, b in evs) / rounds)
+    plain_ms = sum(per_scan_ms)
+    # all scans batched: one graph per round
+    bt = engine.BatchTrainer(scans, graph=True, device=dev)
+    for _ in range(3):
+        bt.round()
+    torch.cuda.synchronize()
+    ms = 0.0
+    for _ in range(rounds):
+        stream.synchronize()
+        bt._fill()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        bt.graph.replay()
+        e1.record(stream)
+        e1.synchronize()
+        ms += e0.elapsed_time(e1)
+    batched_ms = ms / rounds
+    overflow = any(sc.overflowed() for sc in scans)
+    iters = 30000
+    return {"workload": f"{n_scans} uneven cone-beam scans (seed {seed}): M log-U[5k, 300k], 25/50/75 views, "
+                        "256^2/512^2 detectors, 128^3/256^3 volumes, random init; one training iteration each per round",
+            "gaussians": [sp.M for sp in specs],
+            "plain_ms_per_iteration_of_all_scans": plain_ms, "batched_ms_per_round": batched_ms,
+            "scans_per_hour_plain": n_scans * 3600.0 / (iters * plain_ms * 1e-3),
+            "scans_per_hour_batched": n_scans * 3600.0 / (iters * batched_ms * 1e-3),
+            "speedup": plain_ms / batched_ms, "iterations_per_scan": iters, "list_overflow": overflow,
+            "timing": f"CUDA events, mean of {rounds} rounds after 3 warm-up rounds"}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -363,6 +430,9 @@ def run_ours(args, rank, world, local_rank):
             roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": pk["hbm_gbs"], "unit": "GB/s",
                     "frac": None, "traffic": ncu_traffic(dom)}
         # CPU baseline: the oracle on two full steps of the same workload
+        batched = None
+        if world == 1 and not args.no_batched:
+            batched = measure_batched(dev)
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
             p, s, _ = oracle_steps(G, cam, views_np, meas_np, seq[args.warmup:], 2)
@@ -386,6 +456,7 @@ def run_ours(args, rank, world, local_rank):
             "roofline": roof,
             "kernels_ms_per_step": {k: v["ms"] / args.steps for k, v in prof.items()},
             "cpu_baseline": cpu,
+            "batched": batched,
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
@@ -401,6 +472,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the multi-scan scans/hour measurement")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

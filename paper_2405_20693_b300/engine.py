@@ -242,8 +242,10 @@ class Scan:
     descriptor for r2g_train_step."""
 
     def __init__(self, G, views_np, meas_np, cam, n_out=256, D=32, tile=(16, 16), total_iters=30000,
-                 device="cuda", headroom=1.5):
+                 device="cuda", headroom=1.5, seed=0):
         self.state = TrainState(G, device=device)
+        self.rng = np.random.Generator(np.random.PCG64(seed + 2))  # this scan's view / patch choices
+        self.it = 0
         self.M = G.M
         self.cam = cam
         self.D = D
@@ -308,6 +310,22 @@ class Scan:
         J.tv_ws, J.tv_ws_bytes = self.tv_ws.data_ptr(), self.tv_ws.numel()
         return J
 
+    def next_entry(self):
+        """(view, iteration, TV patch origin) of this scan's next iteration."""
+        v = int(self.rng.integers(0, self.V))
+        off = self.rng.integers(0, self.n_out - self.D + 1, 3)
+        e = (v, self.it, tuple(float(x) for x in (-1.0 + off * (2.0 / self.n_out))))
+        self.it += 1
+        return e
+
+    def footprint_bytes(self) -> int:
+        """Device bytes this scan holds (parameters, Adam state, views, measurements,
+        step buffers and workspaces)."""
+        s = self.state
+        n = sum(t.numel() * t.element_size() for t in (s.raw, s.act, s.grad, s.m, s.v, self.views, self.meas,
+                                                         self.image, self.dimage, self.vol, self.dvol, self.loss))
+        return int(n + self.rast.ws.numel() + self.vox.ws.numel() + self.loss_ws.numel() + self.tv_ws.numel())
+
     def overflowed(self) -> bool:
         return r2g.r2g_poll(self.rast.ws)[0] != r2g.R2G_OK or r2g.r2g_poll(self.vox.ws)[0] != r2g.R2G_OK
 
@@ -315,37 +333,38 @@ class Scan:
 class BatchTrainer:
     """Runs one training iteration of every resident scan per round.
 
-    The per-round choices (view, TV patch origin, iteration) live in a device round
-    table [J][8] (r2g_round_entry) filled from pinned host memory by a copy that is
-    part of the round.  With graph=True the whole round -- the table upload and
-    every scan's r2g_train_step, spread over n_streams branches -- is captured once
-    as a CUDA graph and replayed; with graph=False the same calls are issued
-    eagerly on the same streams."""
+    The per-round choices (view, TV patch origin, iteration; each scan draws them
+    from its own seeded generator) live in a device round table [J][8]
+    (r2g_round_entry) filled from pinned host memory by a copy that is part of the
+    round.  With graph=True the whole round -- the table upload and every scan's
+    r2g_train_step, one branch per scan on its own stream -- is captured once as a
+    CUDA graph and replayed; with graph=False the same calls are issued eagerly on
+    the same streams."""
 
-    def __init__(self, scans, n_streams=4, graph=True, seed=0, device="cuda"):
+    def __init__(self, scans, n_streams=None, graph=True, seed=0, device="cuda"):
         self.scans = list(scans)
         self.J = len(self.scans)
         self.device = device
         self.table_host = torch.zeros((self.J, 8), dtype=torch.int32).pin_memory()
         self.table_dev = torch.zeros((self.J, 8), dtype=torch.int32, device=device)
+        n_streams = self.J if n_streams is None else n_streams  # one branch per scan by default
         self.streams = [torch.cuda.Stream(device=device) for _ in range(max(1, n_streams))]
-        self.rng = np.random.Generator(np.random.PCG64(seed + 2))
-        self.it = [0] * self.J
         self.graph = None
         self.use_graph = graph
         self.elem = ctypes_sizeof_entry()
 
-    def _fill(self, active=None):
+    def _fill(self):
         t = self.table_host.numpy()
         f = t.view(np.float32)
         for j, sc in enumerate(self.scans):
-            v = int(self.rng.integers(0, sc.V))
-            off = self.rng.integers(0, sc.n_out - sc.D + 1, 3)
+            v, it, origin = sc.next_entry()
             t[j, 0] = v
-            t[j, 1] = self.it[j]
-            f[j, 2:5] = -1.0 + off * (2.0 / sc.n_out)
-            if active is None or j in active:
-                self.it[j] += 1
+            t[j, 1] = it
+            f[j, 2:5] = origin
+
+    @property
+    def it(self):
+        return [sc.it for sc in self.scans]
 
     def _issue(self):
         main = torch.cuda.current_stream()

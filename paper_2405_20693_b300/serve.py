@@ -1,0 +1,166 @@
+"""Continuous-batching reconstruction server.
+
+Requests (one sparse-view scan each) arrive over time.  The server admits a
+request when its device footprint fits the HBM budget, keeps every admitted
+scan's Gaussians and Adam state resident on the device, and advances all
+resident scans together: one round = one training iteration of every resident
+scan, issued as one CUDA graph (engine.BatchTrainer).  A scan retires when it
+reaches its iteration limit or, checked every `check_every` iterations, when the
+PSNR of its voxelized volume against the phantom reaches the target; its memory
+is released and waiting requests are admitted at the next round boundary.  The
+graph is recaptured whenever the resident set changes.
+
+Reported per request: arrival, admission and completion times (seconds on the
+run clock), iterations, final PSNR; overall: p50/p99 time-to-volume and
+scans/hour.
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import engine, r2g
+from . import inputs as I
+
+
+@dataclass
+class Request:
+    rid: int
+    spec: I.ScanSpec
+    arrival: float                # seconds after the start of the run
+    max_iters: int = 30000
+    psnr_target: float = 35.0     # dB against the phantom volume (max 1)
+    check_every: int = 500
+
+
+@dataclass
+class Result:
+    rid: int
+    arrival: float
+    admitted: float
+    finished: float
+    iters: int
+    psnr: float
+    reason: str                   # "target" or "iterations"
+
+    @property
+    def time_to_volume(self) -> float:
+        return self.finished - self.arrival
+
+
+def poisson_requests(n: int, mean_interarrival_s: float, seed: int = 6, specs=None, **kw):
+    """n requests with exponential inter-arrival times (seeded)."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    t = np.cumsum(g.exponential(mean_interarrival_s, n))
+    t -= t[0]
+    specs = specs if specs is not None else I.batched_specs(n, seed=5)
+    return [Request(k, specs[k % len(specs)], float(t[k]), **kw) for k in range(n)]
+
+
+def footprint_estimate(spec: I.ScanSpec, D: int = 32, capacity_factor: float = 6.0) -> int:
+    """Device bytes a scan will hold, before it is built: parameters, gradient and
+    Adam state (5 x 11 floats per Gaussian), measured projections, step buffers, and
+    the workspaces at the library's own size for capacity_factor x M list entries."""
+    cam = r2g.camera(I.cone_camera(spec.det, spec.det, pitch=I.CONE_PITCH * 512 / spec.det))
+    ro = r2g.raster_opts()
+    raster = r2g.r2g_raster_workspace_size(spec.M, 1, cam, ro, int(capacity_factor * spec.M) + 4096)
+    grid = r2g.grids(I.patch_grid((0, 0, 0), D, spec.n_out))
+    voxel = r2g.r2g_voxel_workspace_size(spec.M, grid, int(capacity_factor * spec.M) + 4096)
+    px = spec.det * spec.det
+    return int(spec.M * 55 * 4 + spec.V * px * 4 + 2 * px * 4 + 2 * D ** 3 * 4 + raster + voxel
+               + r2g.r2g_loss_workspace_size(1, spec.det, spec.det))
+
+
+class Server:
+    def __init__(self, hbm_budget_bytes: int, D: int = 32, device="cuda", graph=True, keep_volumes=False):
+        self.budget = int(hbm_budget_bytes)
+        self.D = D
+        self.device = device
+        self.graph = graph
+        self.keep_volumes = keep_volumes
+        self.volumes = {}    # rid -> final volume on the host (keep_volumes only)
+        self.max_active = 0
+        self.rounds = 0
+
+    def _build(self, req: Request):
+        G, cam, views, meas, vol = I.make_scan(req.spec, device=self.device)
+        sc = engine.Scan(G, views, meas, cam, n_out=req.spec.n_out, D=self.D, device=self.device, seed=req.spec.seed)
+        gt = torch.as_tensor(vol.astype(np.float32), device=self.device).reshape(-1)
+        vox = engine.Voxelizer(sc.M, I.cube_grid(req.spec.n_out), device=self.device)
+        return sc, gt, vox
+
+    @staticmethod
+    def volume(sc, vox):
+        mean, scale, quat, rho = sc.state.params()
+        return vox.forward(mean, scale, quat, rho)
+
+    @classmethod
+    def psnr(cls, sc, gt, vox) -> float:
+        mse = float(torch.mean((cls.volume(sc, vox) - gt) ** 2))
+        return 10.0 * np.log10(1.0 / max(mse, 1e-30))
+
+    def run(self, requests):
+        pending = sorted(requests, key=lambda r: r.arrival)
+        queue, active, results = [], {}, []
+        used = 0
+        trainer, dirty = None, True
+        t0 = time.perf_counter()
+        while pending or queue or active:
+            now = time.perf_counter() - t0
+            while pending and pending[0].arrival <= now:
+                queue.append(pending.pop(0))
+            # admission at a round boundary, first come first served, by HBM footprint
+            while queue:
+                need = footprint_estimate(queue[0].spec, self.D)
+                if used + need > self.budget and active:
+                    break
+                req = queue.pop(0)
+                sc, gt, vox = self._build(req)
+                active[req.rid] = dict(req=req, scan=sc, gt=gt, vox=vox, admitted=time.perf_counter() - t0,
+                                       bytes=need)
+                used += need
+                dirty = True
+            if not active:
+                if pending:
+                    time.sleep(max(0.0, pending[0].arrival - (time.perf_counter() - t0)))
+                continue
+            self.max_active = max(self.max_active, len(active))
+            if dirty:
+                trainer = engine.BatchTrainer([a["scan"] for a in active.values()], graph=self.graph,
+                                              device=self.device)
+                dirty = False
+            trainer.round()
+            self.rounds += 1
+            done = []
+            for rid, a in active.items():
+                sc, req = a["scan"], a["req"]
+                if sc.it >= req.max_iters:
+                    done.append((rid, "iterations"))
+                elif sc.it % req.check_every == 0:
+                    torch.cuda.synchronize()
+                    if self.psnr(sc, a["gt"], a["vox"]) >= req.psnr_target:
+                        done.append((rid, "target"))
+            if done:
+                torch.cuda.synchronize()
+                t = time.perf_counter() - t0
+                for rid, reason in done:
+                    a = active.pop(rid)
+                    p = self.psnr(a["scan"], a["gt"], a["vox"])
+                    results.append(Result(rid, a["req"].arrival, a["admitted"], t, a["scan"].it, p, reason))
+                    if self.keep_volumes:
+                        self.volumes[rid] = self.volume(a["scan"], a["vox"]).cpu().numpy()
+                    used -= a["bytes"]
+                dirty = True
+        self.wall = time.perf_counter() - t0
+        return sorted(results, key=lambda r: r.rid)
+
+
+def summarize(results, wall_s: float):
+    ttv = np.array([r.time_to_volume for r in results])
+    return {"requests": len(results), "p50_time_to_volume_s": float(np.percentile(ttv, 50)),
+            "p99_time_to_volume_s": float(np.percentile(ttv, 99)),
+            "scans_per_hour": len(results) * 3600.0 / wall_s, "wall_s": wall_s,
+            "reasons": {k: sum(r.reason == k for r in results) for k in ("target", "iterations")}}

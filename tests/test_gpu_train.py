@@ -97,8 +97,8 @@ def test_batched_graph_round_equals_scans_alone():
     full = [small_scan(210, 4000, 128, with_volume=True), small_scan(211, 1500, 64, V=5, with_volume=True),
             small_scan(212, 9000, 128, V=11, with_volume=True)]
     setups = [f[:4] for f in full]
-    scans = [engine.Scan(G, v, m, c, n_out=64, D=16) for (G, c, v, m) in setups]
-    bt = engine.BatchTrainer(scans, n_streams=4, graph=True, seed=7)
+    scans = [engine.Scan(G, v, m, c, n_out=64, D=16, seed=7 + j) for j, (G, c, v, m) in enumerate(setups)]
+    bt = engine.BatchTrainer(scans, n_streams=4, graph=True)
     history, losses_mix = [], []
     for _ in range(4):
         bt.round()
