@@ -34,6 +34,7 @@ class Request:
     max_iters: int = 30000
     psnr_target: float = 35.0     # dB against the phantom volume (max 1)
     check_every: int = 500
+    data: tuple | None = None     # prepared (gaussians, camera, views, measured projections, phantom volume)
 
 
 @dataclass
@@ -86,7 +87,7 @@ class Server:
         self.rounds = 0
 
     def _build(self, req: Request):
-        G, cam, views, meas, vol = I.make_scan(req.spec, device=self.device)
+        G, cam, views, meas, vol = req.data if req.data is not None else I.make_scan(req.spec, device=self.device)
         sc = engine.Scan(G, views, meas, cam, n_out=req.spec.n_out, D=self.D, device=self.device, seed=req.spec.seed)
         gt = torch.as_tensor(vol.astype(np.float32), device=self.device).reshape(-1)
         vox = engine.Voxelizer(sc.M, I.cube_grid(req.spec.n_out), device=self.device)
