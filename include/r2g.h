@@ -316,6 +316,10 @@ r2g_status r2g_upload_round(r2g_round_entry* dst, const r2g_round_entry* src, in
  * 10 vox_chain, 11 loss, 12 tv, 13 adam.  Not for use inside stream capture.
  * max_spans bounds the recorded pairs (events are created once, here). */
 r2g_status r2g_profile_enable(int32_t on, int32_t max_spans);
+/* Restrict recording to the kernel ids whose bit is set in kernel_mask (bit k =
+ * id k; all bits set by default), so that a timed run can bracket only the
+ * kernel it reports without event records around every other one. */
+r2g_status r2g_profile_select(uint32_t kernel_mask);
 r2g_status r2g_profile_reset(void);
 /* Launch count and summed device time (ms) of one kernel id since the last reset;
  * waits for the recorded events. */

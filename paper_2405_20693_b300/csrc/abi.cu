@@ -42,6 +42,7 @@ const char* const kProfNames[P_COUNT] = {"project",    "emit",       "sort",    
 std::atomic<long long> g_launches{0};
 std::mutex g_prof_mu;
 bool g_prof_on = false;
+uint32_t g_prof_mask = 0xffffffffu;
 std::vector<cudaEvent_t> g_events;
 size_t g_next = 0;
 struct Span {
@@ -56,7 +57,7 @@ void note_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); 
 
 void prof_begin(int k, cudaStream_t s) {
     std::lock_guard<std::mutex> lk(g_prof_mu);
-    if (!g_prof_on) return;
+    if (!g_prof_on || !((g_prof_mask >> k) & 1u)) return;
     if (g_next + 2 > g_events.size()) {
         g_overflow = true;
         g_open[k] = (size_t)-1;
@@ -68,7 +69,7 @@ void prof_begin(int k, cudaStream_t s) {
 
 void prof_end(int k, cudaStream_t s) {
     std::lock_guard<std::mutex> lk(g_prof_mu);
-    if (!g_prof_on || g_open[k] == (size_t)-1) return;
+    if (!g_prof_on || !((g_prof_mask >> k) & 1u) || g_open[k] == (size_t)-1) return;
     if (g_next + 1 > g_events.size()) {
         g_overflow = true;
         return;
@@ -94,6 +95,12 @@ R2G_API r2g_status r2g_profile_enable(int32_t on, int32_t max_spans) {
         }
     }
     g_prof_on = on != 0;
+    return R2G_OK;
+}
+
+R2G_API r2g_status r2g_profile_select(uint32_t kernel_mask) {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_mask = kernel_mask;
     return R2G_OK;
 }
 

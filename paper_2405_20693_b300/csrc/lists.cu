@@ -170,7 +170,7 @@ uint64_t* radix_sort_u64(uint64_t* a, uint64_t* b, uint32_t* scratch, const WsSt
 namespace {
 
 // At the first entry of every key: find the key's end by binary search, write its
-// range, and claim ceil(n / kChunk) consecutive work items with one atomic.  The
+// range, and claim ceil(n / chunk) consecutive work items with one atomic.  The
 // order in which keys claim their items varies from run to run, but each key's
 // items are contiguous and numbered by chunk, so every consumer that combines a
 // key's chunks does so in chunk order.
@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(256) k_ranges_items(const uint64_t* __restrict
                                                       const WsStatus* __restrict__ st, uint2* __restrict__ ranges,
                                                       unsigned long long n_slots, WsStatus* __restrict__ item_st,
                                                       uint32_t* __restrict__ item_off, uint64_t* __restrict__ items,
-                                                      unsigned long long items_cap) {
+                                                      unsigned long long items_cap, uint32_t chunk) {
     const unsigned long long n = st->n_keys;
     for (unsigned long long i = (unsigned long long)blockIdx.x * 256 + threadIdx.x; i < n;
          i += (unsigned long long)gridDim.x * 256) {
@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(256) k_ranges_items(const uint64_t* __restrict
             else hi = mid;
         }
         ranges[k] = make_uint2((uint32_t)i, (uint32_t)lo);
-        const uint32_t nch = (uint32_t)((lo - i + kChunk - 1) / kChunk);
+        const uint32_t nch = (uint32_t)((lo - i + chunk - 1) / chunk);
         const unsigned long long base = atomicAdd(&item_st->n_keys, (unsigned long long)nch);
         item_off[k] = (uint32_t)base;
         for (uint32_t c = 0; c < nch; ++c)
@@ -203,13 +203,13 @@ __global__ void __launch_bounds__(256) k_ranges_items(const uint64_t* __restrict
 }  // namespace
 
 void build_ranges_items(const uint64_t* sorted, const WsStatus* status, uint2* ranges, int64_t n_slots,
-                        WsStatus* item_status, uint32_t* item_off, uint64_t* items, long long items_cap,
+                        WsStatus* item_status, uint32_t* item_off, uint64_t* items, long long items_cap, int chunk,
                         cudaStream_t st) {
     // ranges and the item status block are adjacent in every workspace: one clear
     cudaMemsetAsync(ranges, 0, reinterpret_cast<char*>(item_status) - reinterpret_cast<char*>(ranges) +
                                    sizeof(WsStatus), st);
     k_ranges_items<<<148 * 8, 256, 0, st>>>(sorted, status, ranges, (unsigned long long)n_slots, item_status,
-                                            item_off, items, (unsigned long long)items_cap);
+                                            item_off, items, (unsigned long long)items_cap, (uint32_t)chunk);
 }
 
 }  // namespace r2g

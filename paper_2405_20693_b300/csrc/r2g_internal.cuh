@@ -62,7 +62,8 @@ struct Layout {
 
 constexpr int kScanBlocks = 148 * 4;     // fixed grid of the count scan and the key emission
 constexpr int kSortBlocksMax = 148 * 16; // largest grid of the radix passes
-constexpr int kChunk = 128;              // list entries per work item (tile or brick, chunk)
+constexpr int kChunk = 128;              // list entries per tile work item
+constexpr int kVoxChunk = 32;            // list entries per brick work item
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
 
@@ -79,18 +80,19 @@ int sort_blocks_for(long long capacity);
 uint64_t* radix_sort_u64(uint64_t* a, uint64_t* b, uint32_t* scratch, const WsStatus* status, int key_bits,
                          int sort_blocks, cudaStream_t st);
 
-// Work items: every key's range is cut into chunks of kChunk entries; item =
-// (key << 32) | chunk index; a key's items are consecutive.  item_off[key] = index
-// of the key's first item (written for non-empty keys); item_status->n_keys = item
-// count.  items must hold items_capacity(n_slots, capacity) entries.
-inline long long items_capacity(long long n_slots, long long capacity) {
-    return n_slots + (capacity + kChunk - 1) / kChunk + 1;
+// Work items: every key's range is cut into chunks of `chunk` entries (kChunk for
+// tiles, kVoxChunk for bricks); item = (key << 32) | chunk index; a key's items
+// are consecutive.  item_off[key] = index of the key's first item (written for
+// non-empty keys); item_status->n_keys = item count.  items must hold
+// items_capacity(n_slots, capacity, chunk) entries.
+inline long long items_capacity(long long n_slots, long long capacity, int chunk) {
+    return n_slots + (capacity + chunk - 1) / chunk + 1;
 }
 // ranges[k] = [start, end) of key k in the sorted entries (absent keys: [0, 0)), and
 // the work items, in one pass over the sorted entries.  item_status must
 // directly follow the ranges array in the workspace (one clear covers both).
 void build_ranges_items(const uint64_t* sorted, const WsStatus* status, uint2* ranges, int64_t n_slots,
-                        WsStatus* item_status, uint32_t* item_off, uint64_t* items, long long items_cap,
+                        WsStatus* item_status, uint32_t* item_off, uint64_t* items, long long items_cap, int chunk,
                         cudaStream_t st);
 
 

@@ -781,7 +781,7 @@ struct Tail {
 
 Tail raster_tail(const RasterLayout& L, long long cap, int tile_px) {
     Tail t;
-    t.icap = items_capacity(L.n_tiles, cap);
+    t.icap = items_capacity(L.n_tiles, cap, kChunk);
     Layout lay;
     lay.off = L.fixed;
     t.a = lay.take(8 * (size_t)cap);
@@ -947,7 +947,7 @@ r2g_status r2g::rasterize_impl(int64_t M, const float* mean, const float* scale,
     uint64_t* sorted = radix_sort_u64(a, b, scratch, st, bits_for(L.n_tiles), sort_blocks_for(cap), stream);
     prof_end(P_SORT, stream);
     prof_begin(P_RANGES, stream);
-    build_ranges_items(sorted, st, ranges, L.n_tiles, item_st, item_off, items, T.icap, stream);
+    build_ranges_items(sorted, st, ranges, L.n_tiles, item_st, item_off, items, T.icap, kChunk, stream);
     prof_end(P_RANGES, stream);
     const float Tq = -0.5f * kLog2e * opts->Q;
     prof_begin(P_SPLAT_FWD, stream);

@@ -6,15 +6,19 @@
 //                  bound and a 64-byte record {c, rho; A..F; rx, ry, rz} in voxel
 //                  units, the quadratic form pre-scaled by -log2(e)/2.
 //   emit / sort    (brick, Gaussian id) entries, stable radix sort, brick ranges.
-//   k_vox_fwd      one CTA (128 threads) per brick; records staged in shared
-//                  memory; each thread owns a run of 4 voxels along x; a warp
-//                  (two z-slices) skips records whose z span misses it.
-//   k_vox_bwd      one CTA per brick with dL/dV of the brick in shared memory;
-//                  one thread per record walks its box inside the brick and
-//                  accumulates ten moments in registers, then three vector atomics.
+//   k_vox_fwd      one CTA (128 threads) per work item (a brick's list cut into
+//                  chunks of 32 records); records staged in shared memory; each
+//                  thread owns a run of 4 voxels along x; a warp (two z-slices)
+//                  skips records whose z span misses it; multi-chunk bricks are
+//                  summed in chunk order by k_vox_reduce.
+//   k_vox_bwd      one CTA per group of 16 consecutive sorted entries; the
+//                  group's (record, voxel) pairs split evenly over its 128 lanes;
+//                  ten moments per record in registers, three vector atomics.
 //   k_vox_chain    one thread per Gaussian, looping over grids: moments ->
 //                  d rho, d mean, d Sigma^{-1} -> d scale, d quat.
 #include <math.h>
+
+#include <algorithm>
 
 #include "emit.cuh"
 #include "r2g_internal.cuh"
@@ -209,7 +213,7 @@ __global__ void __launch_bounds__(kVoxThreads) k_vox_fwd(const float4* __restric
                                                          float* __restrict__ partial, long long M,
                                                          const __grid_constant__ Grids grids, float Tq,
                                                          float* __restrict__ vol, WsStatus* st) {
-    static_assert(kChunk == kVoxThreads, "one staging batch per item");
+    static_assert(kVoxChunk <= kVoxThreads, "one staging batch per item");
     __shared__ float4 s_r[kVoxThreads][4];
     const unsigned long long it = blockIdx.x;
     if (it >= item_st->n_keys) return;
@@ -231,9 +235,9 @@ __global__ void __launch_bounds__(kVoxThreads) k_vox_fwd(const float4* __restric
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
     unsigned int cnt = 0;
     const uint2 rg = ranges[brick];
-    const uint32_t start = rg.x + chunk * kChunk;
-    const uint32_t end = min(start + (uint32_t)kChunk, rg.y);
-    const uint32_t nch = (rg.y - rg.x + kChunk - 1) / kChunk;
+    const uint32_t start = rg.x + chunk * kVoxChunk;
+    const uint32_t end = min(start + (uint32_t)kVoxChunk, rg.y);
+    const uint32_t nch = (rg.y - rg.x + kVoxChunk - 1) / kVoxChunk;
     for (uint32_t base = start; base < end; base += kVoxThreads) {
         const int n = min((uint32_t)kVoxThreads, end - base);
         __syncthreads();
@@ -289,7 +293,7 @@ __global__ void __launch_bounds__(kVoxThreads) k_vox_reduce(const uint2* __restr
                                                             float* __restrict__ vol) {
     const long long brick = blockIdx.x;
     const uint2 rg = ranges[brick];
-    const uint32_t nch = (rg.y - rg.x + kChunk - 1) / kChunk;
+    const uint32_t nch = (rg.y - rg.x + kVoxChunk - 1) / kVoxChunk;
     if (nch == 1) return;
     const int g = grid_of_brick(grids, brick);
     const GridF& gf = grids.g[g];
@@ -330,161 +334,162 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x) {
     return x;
 }
 
-// One CTA per work item (<= 128 records of one brick).  Each record's voxel box
-// inside the brick is w x h x d; within a warp the box sizes of its 32 records are
-// split into 32 equal contiguous ranges of (record, voxel) pairs, one per lane; a
-// lane keeps its current record's ten moments in registers and adds them to the
-// record's slot (three vector atomics) when it leaves the record or its range ends.
+constexpr int kVoxGroup = 16;  // sorted list entries per backward CTA
+
+// One CTA per group of kVoxGroup consecutive sorted entries, whatever their
+// bricks (a grid-stride loop covers every group).  Each record's voxel box inside
+// its brick and the grid is w x h x d; the box sizes of the group's records are
+// split into kVoxThreads equal contiguous ranges of (record, voxel) pairs, one per
+// lane, so a record is shared by several lanes and every lane does the same
+// number of pair evaluations.  A lane keeps its current record's ten moments in
+// registers and adds them to the record's slot (three vector atomics) when it
+// leaves the record or its range ends.  dL/dV is read through the L1 cache.
 __global__ void __launch_bounds__(kVoxThreads) k_vox_bwd(const float4* __restrict__ rec,
-                                                         const uint2* __restrict__ ranges,
                                                          const uint64_t* __restrict__ sorted,
-                                                         const uint64_t* __restrict__ items,
-                                                         const WsStatus* __restrict__ item_st, long long M,
+                                                         const WsStatus* __restrict__ st, long long M,
                                                          const __grid_constant__ Grids grids, float Tq,
                                                          const float* __restrict__ dvol, float4* __restrict__ mom) {
-    static_assert(kChunk == kVoxThreads, "one record per thread");
-    __shared__ float s_g[kB * kB * kB];
-    __shared__ float4 s_r0[kChunk], s_r1[kChunk], s_r2[kChunk];
-    __shared__ int4 s_box[kChunk];      // x0 | y0 << 8 | z0 << 16, w, wh, n
-    __shared__ uint32_t s_gid[kChunk];
-    __shared__ uint32_t s_excl[kChunk];
-    const unsigned long long it = blockIdx.x;
-    if (it >= item_st->n_keys) return;
-    const uint64_t item = items[it];
-    const long long brick = (long long)(item >> 32);
-    const uint32_t chunk = (uint32_t)item;
-    const int g = grid_of_brick(grids, brick);
-    const GridF& gf = grids.g[g];
-    const long long lb = brick - gf.brick_base;
-    const int bx = (int)(lb % gf.nb[0]);
-    const int by = (int)((lb / gf.nb[0]) % gf.nb[1]);
-    const int bz = (int)(lb / ((long long)gf.nb[0] * gf.nb[1]));
-    const int X0 = bx * kB, Y0 = by * kB, Z0 = bz * kB;
-    for (int k = threadIdx.x; k < kB * kB * kB; k += kVoxThreads) {
-        const int lz = k >> 6, ly = (k >> 3) & 7, lx = k & 7;
-        const int x = X0 + lx, y = Y0 + ly, z = Z0 + lz;
-        s_g[k] = (x < gf.dims[0] && y < gf.dims[1] && z < gf.dims[2])
-                     ? dvol[gf.vol_base + ((long long)z * gf.dims[1] + y) * gf.dims[0] + x]
-                     : 0.0f;
-    }
-    const uint2 rg = ranges[brick];
-    const float4* grec = rec + 4 * (size_t)g * (size_t)M;
-    float4* gmom = mom + 3 * (size_t)g * (size_t)M;
-    const int j = threadIdx.x, lane = j & 31, wbase = j & ~31;
-    const uint32_t e = rg.x + chunk * kChunk + j;
-    uint32_t n = 0;
-    if (e < rg.y) {
-        const uint32_t gid = (uint32_t)sorted[e];
-        const float4 r0 = grec[4 * (size_t)gid], r1 = grec[4 * (size_t)gid + 1];
-        const float4 r2 = grec[4 * (size_t)gid + 2], r3 = grec[4 * (size_t)gid + 3];
-        const int xa = max(0, (int)ceilf(r0.x - r3.x) - X0), xb = min(kB - 1, (int)floorf(r0.x + r3.x) - X0);
-        const int ya = max(0, (int)ceilf(r0.y - r3.y) - Y0), yb = min(kB - 1, (int)floorf(r0.y + r3.y) - Y0);
-        const int za = max(0, (int)ceilf(r0.z - r3.z) - Z0), zb = min(kB - 1, (int)floorf(r0.z + r3.z) - Z0);
-        const int w = xb - xa + 1, h = yb - ya + 1, d = zb - za + 1;
-        n = (w > 0 && h > 0 && d > 0) ? (uint32_t)(w * h * d) : 0u;
-        s_r0[j] = r0;
-        s_r1[j] = r1;
-        s_r2[j] = r2;
-        s_box[j] = make_int4(n ? (xa | (ya << 8) | (za << 16)) : 0, max(w, 1), max(w, 1) * max(h, 1), (int)n);
-        s_gid[j] = gid;
-    } else {
-        s_box[j] = make_int4(0, 1, 1, 0);
-        s_gid[j] = 0;
-    }
-    const uint32_t incl = warp_incl_scan(n);
-    s_excl[j] = incl - n;
-    const uint32_t T = __shfl_sync(0xffffffffu, incl, 31);
-    __syncthreads();
-    const uint32_t per = (T + 31) >> 5;
-    const uint32_t p0 = lane * per, p1 = min(T, p0 + per);
-    if (p0 >= p1) return;
-    int lo = 0, hi = 31;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (s_excl[wbase + mid] <= p0) lo = mid;
-        else hi = mid - 1;
-    }
-    int k = lo;
-    float4 r0 = s_r0[wbase + k], r1 = s_r1[wbase + k], r2 = s_r2[wbase + k];
-    int4 box = s_box[wbase + k];
-    uint32_t rec_end = s_excl[wbase + k] + (uint32_t)box.w;
-    int li = (int)(p0 - s_excl[wbase + k]);
-    int zz = li / box.z;
-    int rem = li - zz * box.z;
-    int yy = rem / box.y;
-    int xx = rem - yy * box.y;
-    int xa = box.x & 0xff, ya = (box.x >> 8) & 0xff, za = box.x >> 16;
-    int cy = yy;  // rows done inside the current z-slice
-    float dx = (float)(X0 + xa + xx) - r0.x;
-    float dy = (float)(Y0 + ya + yy) - r0.y;
-    float dz = (float)(Z0 + za + zz) - r0.z;
-    float base_q = fmaf(r1.y * dy, dy, fmaf(r1.z * dz, dz, r2.y * dy * dz));
-    float lin = fmaf(r1.w, dy, r2.x * dz);
-    const float* grow = s_g + ((za + zz) * kB + (ya + yy)) * kB + xa;
-    float S0 = 0.f, Sx = 0.f, Sy = 0.f, Sz = 0.f, Sxx = 0.f, Syy = 0.f, Szz = 0.f, Sxy = 0.f, Sxz = 0.f, Syz = 0.f;
-    for (uint32_t p = p0; p < p1; ++p) {
-        const float tq = fmaf(fmaf(r1.x, dx, lin), dx, base_q);
-        const float ev = ex2_approx(tq);
-        const float w = (tq >= Tq) ? grow[xx] * ev : 0.0f;
-        const float wx = w * dx, wy = w * dy, wz = w * dz;
-        S0 += w;
-        Sx += wx;
-        Sy += wy;
-        Sz += wz;
-        Sxx = fmaf(wx, dx, Sxx);
-        Syy = fmaf(wy, dy, Syy);
-        Szz = fmaf(wz, dz, Szz);
-        Sxy = fmaf(wx, dy, Sxy);
-        Sxz = fmaf(wx, dz, Sxz);
-        Syz = fmaf(wy, dz, Syz);
-        ++xx;
-        dx += 1.0f;
-        if (xx == box.y) {  // next row (and slice) of the box
-            xx = 0;
-            dx -= (float)box.y;
-            ++cy;
-            dy += 1.0f;
-            grow += kB;
-            if (cy * box.y == box.z) {
-                cy = 0;
-                dy -= (float)(box.z / box.y);
-                dz += 1.0f;
-                grow += kB * kB - (box.z / box.y) * kB;
+    __shared__ float4 s_r1[kVoxGroup], s_r2[kVoxGroup];
+    __shared__ float4 s_d[kVoxGroup];         // dx, dy, dz of the box's first voxel
+    __shared__ int4 s_box[kVoxGroup];         // w, h, n, row stride of the volume
+    __shared__ long long s_goff[kVoxGroup];   // dvol index of the box's first voxel
+    __shared__ int s_slice[kVoxGroup];        // slice stride of the volume
+    __shared__ uint32_t s_ridx[kVoxGroup];    // record index g M + gid
+    __shared__ uint32_t s_excl[kVoxGroup + 1];
+    const unsigned long long n_keys = st->n_keys;
+    const unsigned long long n_groups = (n_keys + kVoxGroup - 1) / kVoxGroup;
+    const int j = threadIdx.x;
+    for (unsigned long long grp = blockIdx.x; grp < n_groups; grp += gridDim.x) {
+        __syncthreads();  // the previous group's records are no longer read
+        if (j < 32) {
+            uint32_t n = 0;
+            const unsigned long long e = grp * kVoxGroup + j;
+            if (j < kVoxGroup && e < n_keys) {
+                const uint64_t ent = sorted[e];
+                const long long brick = (long long)(ent >> 32);
+                const uint32_t gid = (uint32_t)ent;
+                const int g = grid_of_brick(grids, brick);
+                const GridF& gf = grids.g[g];
+                const long long lb = brick - gf.brick_base;
+                const int X0 = (int)(lb % gf.nb[0]) * kB;
+                const int Y0 = (int)((lb / gf.nb[0]) % gf.nb[1]) * kB;
+                const int Z0 = (int)(lb / ((long long)gf.nb[0] * gf.nb[1])) * kB;
+                const size_t r = (size_t)g * (size_t)M + gid;
+                const float4 r0 = rec[4 * r], r1 = rec[4 * r + 1], r2 = rec[4 * r + 2], r3 = rec[4 * r + 3];
+                const int xa = max(0, (int)ceilf(r0.x - r3.x) - X0);
+                const int xb = min(min(kB, gf.dims[0] - X0) - 1, (int)floorf(r0.x + r3.x) - X0);
+                const int ya = max(0, (int)ceilf(r0.y - r3.y) - Y0);
+                const int yb = min(min(kB, gf.dims[1] - Y0) - 1, (int)floorf(r0.y + r3.y) - Y0);
+                const int za = max(0, (int)ceilf(r0.z - r3.z) - Z0);
+                const int zb = min(min(kB, gf.dims[2] - Z0) - 1, (int)floorf(r0.z + r3.z) - Z0);
+                const int w = xb - xa + 1, h = yb - ya + 1, d = zb - za + 1;
+                n = (w > 0 && h > 0 && d > 0) ? (uint32_t)(w * h * d) : 0u;
+                const int x = X0 + xa, y = Y0 + ya, z = Z0 + za;
+                s_r1[j] = r1;
+                s_r2[j] = r2;
+                s_d[j] = make_float4((float)x - r0.x, (float)y - r0.y, (float)z - r0.z, 0.f);
+                s_box[j] = make_int4(max(w, 1), max(h, 1), (int)n, gf.dims[0]);
+                s_slice[j] = gf.dims[0] * gf.dims[1];
+                s_goff[j] = n ? gf.vol_base + ((long long)z * gf.dims[1] + y) * gf.dims[0] + x : 0;
+                s_ridx[j] = (uint32_t)r;
+            } else if (j < kVoxGroup) {
+                s_box[j] = make_int4(1, 1, 0, 0);
             }
-            base_q = fmaf(r1.y * dy, dy, fmaf(r1.z * dz, dz, r2.y * dy * dz));
-            lin = fmaf(r1.w, dy, r2.x * dz);
+            const uint32_t incl = warp_incl_scan(n);
+            if (j < kVoxGroup) s_excl[j] = incl - n;
+            if (j == 31) s_excl[kVoxGroup] = incl;
         }
-        if (p + 1 == rec_end && p + 1 < p1) {  // next record
-            const uint32_t gid = s_gid[wbase + k];
-            atomicAdd(&gmom[3 * (size_t)gid], make_float4(S0, Sx, Sy, Sz));
-            atomicAdd(&gmom[3 * (size_t)gid + 1], make_float4(Sxx, Syy, Szz, Sxy));
-            atomicAdd(reinterpret_cast<float2*>(&gmom[3 * (size_t)gid + 2]), make_float2(Sxz, Syz));
-            S0 = Sx = Sy = Sz = Sxx = Syy = Szz = Sxy = Sxz = Syz = 0.f;
-            do {
-                ++k;
-            } while (s_box[wbase + k].w == 0);
-            r0 = s_r0[wbase + k];
-            r1 = s_r1[wbase + k];
-            r2 = s_r2[wbase + k];
-            box = s_box[wbase + k];
-            rec_end += (uint32_t)box.w;
-            xa = box.x & 0xff;
-            ya = (box.x >> 8) & 0xff;
-            za = box.x >> 16;
-            xx = 0;
-            cy = 0;
-            dx = (float)(X0 + xa) - r0.x;
-            dy = (float)(Y0 + ya) - r0.y;
-            dz = (float)(Z0 + za) - r0.z;
-            base_q = fmaf(r1.y * dy, dy, fmaf(r1.z * dz, dz, r2.y * dy * dz));
-            lin = fmaf(r1.w, dy, r2.x * dz);
-            grow = s_g + (za * kB + ya) * kB + xa;
+        __syncthreads();
+        const uint32_t T = s_excl[kVoxGroup];
+        const uint32_t per = (T + kVoxThreads - 1) / kVoxThreads;
+        const uint32_t p0 = j * per, p1 = min(T, p0 + per);
+        if (p0 >= p1) continue;
+        // the record holding pair p0: the largest k with excl_k <= p0 (it is non-empty)
+        int lo = 0, hi = kVoxGroup - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_excl[mid] <= p0) lo = mid;
+            else hi = mid - 1;
         }
+        int k = lo;
+        float4 r1 = s_r1[k], r2 = s_r2[k], d0 = s_d[k];
+        int4 box = s_box[k];
+        int slice = s_slice[k];
+        uint32_t rec_end = s_excl[k] + (uint32_t)box.z;
+        const int li = (int)(p0 - s_excl[k]);
+        const int zz = li / (box.x * box.y);
+        const int rem = li - zz * box.x * box.y;
+        const int yy = rem / box.x;
+        int xx = rem - yy * box.x;
+        int cy = yy;  // rows done inside the current z-slice
+        float dx = d0.x + (float)xx, dy = d0.y + (float)yy, dz = d0.z + (float)zz;
+        float base_q = fmaf(r1.y * dy, dy, fmaf(r1.z * dz, dz, r2.y * dy * dz));
+        float lin = fmaf(r1.w, dy, r2.x * dz);
+        const float* grow = dvol + s_goff[k] + (long long)zz * slice + (long long)yy * box.w;
+        float S0 = 0.f, Sx = 0.f, Sy = 0.f, Sz = 0.f, Sxx = 0.f, Syy = 0.f, Szz = 0.f, Sxy = 0.f, Sxz = 0.f,
+              Syz = 0.f;
+        for (uint32_t p = p0; p < p1; ++p) {
+            const float tq = fmaf(fmaf(r1.x, dx, lin), dx, base_q);
+            const float ev = ex2_approx(tq);
+            const float w = (tq >= Tq) ? __ldg(grow + xx) * ev : 0.0f;
+            const float wx = w * dx, wy = w * dy, wz = w * dz;
+            S0 += w;
+            Sx += wx;
+            Sy += wy;
+            Sz += wz;
+            Sxx = fmaf(wx, dx, Sxx);
+            Syy = fmaf(wy, dy, Syy);
+            Szz = fmaf(wz, dz, Szz);
+            Sxy = fmaf(wx, dy, Sxy);
+            Sxz = fmaf(wx, dz, Sxz);
+            Syz = fmaf(wy, dz, Syz);
+            ++xx;
+            dx += 1.0f;
+            if (xx == box.x) {  // next row (and slice) of the box
+                xx = 0;
+                dx -= (float)box.x;
+                ++cy;
+                dy += 1.0f;
+                grow += box.w;
+                if (cy == box.y) {
+                    cy = 0;
+                    dy -= (float)box.y;
+                    dz += 1.0f;
+                    grow += slice - (long long)box.y * box.w;
+                }
+                base_q = fmaf(r1.y * dy, dy, fmaf(r1.z * dz, dz, r2.y * dy * dz));
+                lin = fmaf(r1.w, dy, r2.x * dz);
+            }
+            if (p + 1 == rec_end && p + 1 < p1) {  // next record
+                float4* m = mom + 3 * (size_t)s_ridx[k];
+                atomicAdd(&m[0], make_float4(S0, Sx, Sy, Sz));
+                atomicAdd(&m[1], make_float4(Sxx, Syy, Szz, Sxy));
+                atomicAdd(reinterpret_cast<float2*>(&m[2]), make_float2(Sxz, Syz));
+                S0 = Sx = Sy = Sz = Sxx = Syy = Szz = Sxy = Sxz = Syz = 0.f;
+                do {
+                    ++k;
+                } while (s_box[k].z == 0);
+                r1 = s_r1[k];
+                r2 = s_r2[k];
+                d0 = s_d[k];
+                box = s_box[k];
+                slice = s_slice[k];
+                rec_end += (uint32_t)box.z;
+                xx = 0;
+                cy = 0;
+                dx = d0.x;
+                dy = d0.y;
+                dz = d0.z;
+                base_q = fmaf(r1.y * dy, dy, fmaf(r1.z * dz, dz, r2.y * dy * dz));
+                lin = fmaf(r1.w, dy, r2.x * dz);
+                grow = dvol + s_goff[k];
+            }
+        }
+        float4* m = mom + 3 * (size_t)s_ridx[k];
+        atomicAdd(&m[0], make_float4(S0, Sx, Sy, Sz));
+        atomicAdd(&m[1], make_float4(Sxx, Syy, Szz, Sxy));
+        atomicAdd(reinterpret_cast<float2*>(&m[2]), make_float2(Sxz, Syz));
     }
-    const uint32_t gid = s_gid[wbase + k];
-    atomicAdd(&gmom[3 * (size_t)gid], make_float4(S0, Sx, Sy, Sz));
-    atomicAdd(&gmom[3 * (size_t)gid + 1], make_float4(Sxx, Syy, Szz, Sxy));
-    atomicAdd(reinterpret_cast<float2*>(&gmom[3 * (size_t)gid + 2]), make_float2(Sxz, Syz));
 }
 
 __device__ __forceinline__ void quat_grad(const float qn[4], float qnorm, const float g[3][3], float dq[4]) {
@@ -630,7 +635,7 @@ struct VTail {
 
 VTail vox_tail(const VoxLayout& L, long long cap) {
     VTail t;
-    t.icap = items_capacity(L.n_bricks, cap);
+    t.icap = items_capacity(L.n_bricks, cap, kVoxChunk);
     Layout lay;
     lay.off = L.fixed;
     t.a = lay.take(8 * (size_t)cap);
@@ -643,7 +648,7 @@ VTail vox_tail(const VoxLayout& L, long long cap) {
 
 long long vox_capacity(const VoxLayout& L, size_t ws_bytes) {
     if (ws_bytes <= L.fixed) return 0;
-    const double per = 16.0 + (8.0 + 4.0 * kB * kB * kB) / kChunk;
+    const double per = 16.0 + (8.0 + 4.0 * kB * kB * kB) / kVoxChunk;
     const double fixed_tail = (double)L.n_bricks * (8.0 + 4.0 * kB * kB * kB) + 4096.0;
     const double est = ((double)(ws_bytes - L.fixed) - fixed_tail) / per;
     long long cap = est > 0 ? ((long long)est / 32) * 32 : 0;
@@ -728,7 +733,7 @@ r2g_status voxelize_impl(int64_t M, const float* mean, const float* scale, const
     uint64_t* sorted = radix_sort_u64(a, b, scratch, st, bits_for(L.n_bricks), sort_blocks_for(cap), stream);
     prof_end(P_SORT, stream);
     prof_begin(P_RANGES, stream);
-    build_ranges_items(sorted, st, ranges, L.n_bricks, item_st, item_off, items, T.icap, stream);
+    build_ranges_items(sorted, st, ranges, L.n_bricks, item_st, item_off, items, T.icap, kVoxChunk, stream);
     prof_end(P_RANGES, stream);
     const float Tq = -0.5f * kLog2e * Q3;
     note_launches(1 + 3 + 3 * ((bits_for(L.n_bricks) + kRadixBits - 1) / kRadixBits) + 1 + 2);
@@ -775,16 +780,15 @@ R2G_API r2g_status r2g_voxelize_backward(int64_t M, const float* mean, const flo
     const VTail T = vox_tail(L, cap);
     char* base = static_cast<char*>(ws);
     const float4* rec = reinterpret_cast<const float4*>(base + L.rec);
-    const uint2* ranges = reinterpret_cast<const uint2*>(base + L.ranges);
     float4* mom = reinterpret_cast<float4*>(base + L.mom);
     const uint64_t* sorted = vox_sorted(base, L, T);
-    const uint64_t* items = reinterpret_cast<const uint64_t*>(base + T.items);
-    const WsStatus* item_st = reinterpret_cast<const WsStatus*>(base + L.item_status);
+    const WsStatus* st = reinterpret_cast<const WsStatus*>(base + L.status);
     cudaMemsetAsync(mom, 0, 48 * (size_t)L.n_rec, stream);
     const float Tq = -0.5f * kLog2e * Q3;
+    const long long groups = (cap + kVoxGroup - 1) / kVoxGroup;
     prof_begin(P_VOX_BWD, stream);
-    k_vox_bwd<<<(unsigned)T.icap, kVoxThreads, 0, stream>>>(rec, ranges, sorted, items, item_st, M, gr, Tq, dvol,
-                                                             mom);
+    k_vox_bwd<<<(unsigned)std::min<long long>(groups, 148 * 16), kVoxThreads, 0, stream>>>(rec, sorted, st, M, gr,
+                                                                                          Tq, dvol, mom);
     prof_end(P_VOX_BWD, stream);
     Params P{mean, scale, quat, rho};
     prof_begin(P_VOX_CHAIN, stream);

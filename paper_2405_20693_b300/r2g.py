@@ -133,6 +133,7 @@ def lib():
             "r2g_train_step": (_I32, [_P, _P, _P]),
             "r2g_upload_round": (_I32, [_P, _P, _I32, _P]),
             "r2g_profile_enable": (_I32, [_I32, _I32]),
+            "r2g_profile_select": (_I32, [ctypes.c_uint32]),
             "r2g_profile_reset": (_I32, []),
             "r2g_profile_read": (_I32, [_I32, _P, _P]),
             "r2g_profile_name": (ctypes.c_char_p, [_I32]),
@@ -317,6 +318,10 @@ PROFILE_KERNELS = ("project", "emit", "sort", "ranges", "splat_fwd", "splat_bwd"
 
 def r2g_profile_enable(on: bool, max_spans: int = 4096):
     _check(lib().r2g_profile_enable(int(on), int(max_spans)))
+
+
+def r2g_profile_select(kernel_mask: int):
+    _check(lib().r2g_profile_select(int(kernel_mask) & 0xFFFFFFFF))
 
 
 def r2g_profile_reset():
