@@ -233,24 +233,24 @@ def measure_batched(dev, rounds=20, n_scans=16, seed=5):
     for sp in specs:
         G, cam, views, meas, _ = I.make_scan(sp, device=dev)
         scans.append(engine.Scan(G, views, meas, cam, n_out=sp.n_out, D=D_TV, device=dev, seed=sp.seed))
-    # one scan at a time
-    table = torch.zeros((1, 8), dtype=torch.int32).pin_memory()
-    tdev = torch.zeros((1, 8), dtype=torch.int32, device=dev)
+    # one scan at a time: each scan's steps back to back on one stream, their entries
+    # preloaded in a device table so the host only issues the calls
     stream = torch.cuda.current_stream()
+    elem = engine.ctypes_sizeof_entry()
     per_scan_ms = []
     for sc in scans:
-        t = table.numpy()
+        t = np.zeros((rounds + 3, 8), np.int32)
         f = t.view(np.float32)
-        evs = []
         for k in range(rounds + 3):
             v, it, origin = sc.next_entry()
-            t[0, 0], t[0, 1] = v, it
-            f[0, 2:5] = origin
-            stream.synchronize()
-            r2g.r2g_upload_round(tdev, table, 1, stream)
+            t[k, 0], t[k, 1] = v, it
+            f[k, 2:5] = origin
+        tdev = torch.as_tensor(t, device=dev)
+        evs = []
+        for k in range(rounds + 3):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            r2g.r2g_train_step(sc.job, tdev.data_ptr(), stream)
+            r2g.r2g_train_step(sc.job, tdev.data_ptr() + k * elem, stream)
             e1.record(stream)
             if k >= 3:
                 evs.append((e0, e1))
@@ -328,20 +328,29 @@ def run_ours(args, rank, world, local_rank):
         dist.init_process_group("nccl", device_id=dev)
     seed = rank * 1000
     G, cam, views_np, meas_np = make_workload(seed, dev)
-    state = engine.TrainState(G, device=dev)
-    views = torch.as_tensor(views_np, device=dev)
-    meas = torch.as_tensor(meas_np, device=dev)
-    step = engine.TrainStep(state, views, meas, cam, D=D_TV, n_out=N_OUT, device=dev)
+    # the scan's parameters, Adam state, views, measured projections, step buffers and
+    # workspaces stay resident; one step = one r2g_train_step call reading its view,
+    # iteration and TV patch origin from a device table holding every step's entry
+    sc = engine.Scan(G, views_np, meas_np, cam, n_out=N_OUT, D=D_TV, device=dev)
     n_brk = min(args.steps, 200)
-    seq = step_sequence(seed, args.warmup + n_brk + args.steps)
+    n_all = args.warmup + n_brk + args.steps
+    seq = step_sequence(seed, n_all)
+    tab = np.zeros((n_all, 8), np.int32)
+    for k, (v, off) in enumerate(seq):
+        tab[k, 0], tab[k, 1] = v, k
+        tab[k, 2:5] = np.asarray([-1.0 + o * (2.0 / N_OUT) for o in off], np.float32).view(np.int32)
+    table = torch.as_tensor(tab, device=dev)
+    elem = engine.ctypes_sizeof_entry()
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 126 MB L2
 
-    # warm-up (the first call sizes the workspaces)
+    def step(k):
+        r2g.r2g_train_step(sc.job, table.data_ptr() + k * elem, stream)
+
     for k in range(args.warmup):
-        v, off = seq[k]
-        step.run(k, v, off, check=(k == 0))
+        step(k)
     torch.cuda.synchronize()
+    assert not sc.overflowed(), "list capacity overflow in the warm-up"
 
     # per-kernel breakdown, untimed: event pairs around every kernel group of n_brk
     # steps; it names the dominant kernel, the only one bracketed in the timed region
@@ -349,9 +358,8 @@ def run_ours(args, rank, world, local_rank):
     r2g.r2g_profile_select(0xFFFFFFFF)
     r2g.r2g_profile_reset()
     for k in range(args.warmup, args.warmup + n_brk):
-        v, off = seq[k]
         flush.zero_()
-        step.run(k, v, off, check=False)
+        step(k)
     torch.cuda.synchronize()
     breakdown = {}
     for kid, name in enumerate(r2g.PROFILE_KERNELS):
@@ -365,17 +373,18 @@ def run_ours(args, rank, world, local_rank):
     # runs, untimed, on the parameters at the start of the timed region)
     from paper_2405_20693_b300 import inputs as I
 
-    mean, scale, quat, rho = state.params()
+    mean, scale, quat, rho = sc.state.params()
     counted = {}
     for k in range(t0_steps, t0_steps + args.steps):
         v, off = seq[k]
         if (v, off) in counted:
             continue
-        step.rast.forward(mean, scale, quat, rho, views[v:v + 1], step.image, check=True, count=True)
-        pp = step.rast.pair_count()
-        step.vox.set_grids(I.patch_grid(off, D_TV, N_OUT))
-        step.vox.forward(mean, scale, quat, rho, step.vol, check=True, count=True)
-        counted[(v, off)] = (pp, step.vox.pair_count())
+        sc.rast.forward(mean, scale, quat, rho, sc.views[v:v + 1], sc.image, check=True, count=True)
+        pp = sc.rast.pair_count()
+        sc.vox.set_grids(I.patch_grid(off, D_TV, N_OUT))
+        sc.vox.forward(mean, scale, quat, rho, sc.vol, check=True, count=True)
+        counted[(v, off)] = (pp, sc.vox.pair_count())
+    sc.job = sc._make_job()  # a checked run that had to regrow a workspace moved it
     pix_pairs = [counted[seq[k]][0] for k in range(t0_steps, t0_steps + args.steps)]
     vox_pairs = [counted[seq[k]][1] for k in range(t0_steps, t0_steps + args.steps)]
     total_pairs = float(sum(pix_pairs) + sum(vox_pairs))
@@ -395,19 +404,15 @@ def run_ours(args, rank, world, local_rank):
     clock.start()
     launches0 = r2g.r2g_launch_count()
     for j in range(args.steps):
-        k = t0_steps + j
-        v, off = seq[k]
         flush.zero_()
         evs[j][0].record(stream)
-        step.run(k, v, off, check=False)
+        step(t0_steps + j)
         evs[j][1].record(stream)
     torch.cuda.synchronize()
     launches = r2g.r2g_launch_count() - launches0
     clocks = clock.stop()
     ms = sum(a.elapsed_time(b) for a, b in evs)
-    st_r, _ = r2g.r2g_poll(step.rast.ws)
-    st_v, _ = r2g.r2g_poll(step.vox.ws)
-    assert st_r == r2g.R2G_OK and st_v == r2g.R2G_OK, "list capacity overflow inside the timed region"
+    assert not sc.overflowed(), "list capacity overflow inside the timed region"
     n_dom, t_dom = r2g.r2g_profile_read(r2g.PROFILE_KERNELS.index(dom))
     r2g.r2g_profile_enable(False)
     r2g.r2g_profile_select(0xFFFFFFFF)
@@ -422,14 +427,10 @@ def run_ours(args, rank, world, local_rank):
         ms_job, pairs_job = ms, total_pairs
     value = pairs_job / (ms_job * 1e-3)
 
-    # end to end through the public API: per step, the measured view goes host -> device
-    # from pinned memory and the loss comes back
-    meas_host = torch.from_numpy(meas_np).pin_memory()
-    e2e_views = torch.zeros_like(meas[:1])
-    step_e2e = engine.TrainStep(state, views, e2e_views, cam, D=D_TV, n_out=N_OUT, device=dev)
-    step_e2e.views = views[seq[0][0]:seq[0][0] + 1]
-    e2e_views.copy_(meas[seq[0][0]:seq[0][0] + 1])
-    step_e2e.run(0, 0, seq[0][1], check=True)
+    # end to end through the public API: per step, that step's measured view goes
+    # host -> device from pinned memory into the scan's measurement slot, the fused
+    # step runs, and the loss comes back
+    meas_host = torch.from_numpy(np.ascontiguousarray(meas_np, np.float32)).pin_memory()
     loss_host = torch.empty(2, dtype=torch.float32).pin_memory()
     torch.cuda.synchronize()
     if dist:
@@ -437,13 +438,11 @@ def run_ours(args, rank, world, local_rank):
     t0 = time.perf_counter()
     for j in range(args.steps):
         k = t0_steps + j
-        v, off = seq[k]
-        e2e_views.copy_(meas_host[v:v + 1], non_blocking=True)
-        # the e2e step sees the uploaded view as view index 0 of a one-view table
-        step_e2e.views = views[v:v + 1]
-        step_e2e.run(k, 0, off, check=False)
-        loss_host.copy_(step_e2e.loss, non_blocking=True)
-        torch.cuda.current_stream().synchronize()
+        v = seq[k][0]
+        sc.meas[v].copy_(meas_host[v], non_blocking=True)
+        step(k)
+        loss_host.copy_(sc.loss, non_blocking=True)
+        stream.synchronize()
     e2e_s = time.perf_counter() - t0
     if dist:
         tt = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
@@ -473,15 +472,15 @@ def run_ours(args, rank, world, local_rank):
         elif dom is not None:
             roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": pk["hbm_gbs"], "unit": "GB/s",
                     "frac": None, "traffic": ncu_traffic(dom)}
-        # CPU baseline: the oracle on two full steps of the same workload
         batched = None
         serving = None
         if world == 1 and not args.no_batched:
             batched = measure_batched(dev)
             serving = measure_serving(dev)
         cpu = None
+        # CPU baseline: the oracle on two full steps of the same workload
         if world == 1 and not args.no_cpu_baseline:
-            p, s, _ = oracle_steps(G, cam, views_np, meas_np, seq[args.warmup:], 2)
+            p, s, _ = oracle_steps(G, cam, views_np, meas_np, seq[t0_steps:], 2)
             cpu = {"value": p / s, "unit": "pairs/s", "cores": 1, "kind": "oracle",
                    "sample": "2 full training steps of the same workload (FP64 oracle, single thread, "
                              "initial parameters)"}
@@ -503,6 +502,7 @@ def run_ours(args, rank, world, local_rank):
             "kernels_ms_per_step": breakdown,
             "kernels_note": f"breakdown: event pairs around every kernel group over {n_brk} untimed steps; "
                             f"timed region: events around {dom} only",
+            "step_call": "r2g_train_step (one C call per step; entries from a device table)",
             "cpu_baseline": cpu,
             "batched": batched,
             "serving": serving,

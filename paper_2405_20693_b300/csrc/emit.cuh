@@ -1,17 +1,32 @@
 // emit.cuh -- count, scan and emit of (key, Gaussian id) list entries, shared by
-// the rasterizer (key = tile) and the voxelizer (key = brick).
+// the rasterizer (key = tile) and the voxelizer (key = brick), and the list
+// builder that turns them into per-key lists sorted by Gaussian id.
 //
-// An Op supplies, for record r, how many entries it emits (count) and writes them
-// (emit).  Records are split into kScanBlocks contiguous chunks; a first pass sums
-// each chunk, one block scans the chunk sums (and writes the total and the
-// capacity verdict into the status block), and a second pass re-scans each chunk
-// in rounds of 256 records and writes every record's entries at its offset, in
-// record order.  Entries beyond the capacity are not written.
+// An Op supplies, for record r, how many entries it emits (count) and visits them
+// in order (entries(r, f) calls f(key, id) once per entry).  Records are split
+// into kScanBlocks contiguous chunks; a first pass sums each chunk, one block
+// scans the chunk sums (and writes the total and the capacity verdict into the
+// status block), and a second pass re-scans each chunk in rounds of 256 records
+// and writes every record's entries at its offset, in record order.  Entries
+// beyond the capacity are not written.
+//
+// Key spaces of at most kFusedKeys keys (one 512^2 view in 16 x 16 tiles, the
+// bricks of a TV patch) take a fused path: the emission also counts its block's
+// entries per key, one block per key turns the counts into scatter offsets, the
+// key's range and its work items, and a stable scatter (one contiguous run per
+// warp, ranked with warp match masks) writes the sorted lists -- five launches
+// and one pass over the entries.  Larger key spaces take the general stable LSD
+// radix sort and a range pass.
 #pragma once
 
 #include "r2g_internal.cuh"
 
 namespace r2g {
+
+constexpr int kFusedKeys = 1024;
+static_assert((size_t)kFusedKeys * kScanBlocks <= (size_t)kRadix * kSortBlocksMax,
+              "fused histograms fit the sort scratch");
+static_assert(kFusedKeys <= kRadix * 4, "fused key totals fit the sort scratch");
 
 template <class Op>
 __global__ void __launch_bounds__(256) k_count_chunks(Op op, long long n_rec, unsigned long long* partials) {
@@ -26,10 +41,14 @@ __global__ void __launch_bounds__(256) k_count_chunks(Op op, long long n_rec, un
 }
 
 // One block of 1024 threads; nb <= 1024.  partials become exclusive offsets.
+// key_totals (fused path): cleared here, before the emission adds into them.
 static __global__ void __launch_bounds__(1024) k_scan_chunks(unsigned long long* partials, int nb, WsStatus* st,
-                                                      unsigned long long capacity) {
+                                                             unsigned long long capacity, uint32_t* key_totals,
+                                                             int n_keys) {
     __shared__ unsigned long long wsum[32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (key_totals)
+        for (int k = tid; k < n_keys; k += 1024) key_totals[k] = 0;
     const unsigned long long v = tid < nb ? partials[tid] : 0ull;
     unsigned long long x = v;
 #pragma unroll
@@ -59,10 +78,19 @@ static __global__ void __launch_bounds__(1024) k_scan_chunks(unsigned long long*
     }
 }
 
-template <class Op>
+// HIST (fused path): also count the block's written entries per key, then store
+// the counts as hist[key * gridDim.x + block] and add them to key_totals.
+template <class Op, bool HIST>
 __global__ void __launch_bounds__(256) k_emit_chunks(Op op, long long n_rec, const unsigned long long* partials,
-                                                     uint64_t* out, unsigned long long capacity) {
+                                                     uint64_t* out, unsigned long long capacity,
+                                                     uint32_t* __restrict__ hist, uint32_t* __restrict__ key_totals,
+                                                     int n_keys) {
     __shared__ uint32_t sm[8];
+    __shared__ uint32_t h[HIST ? kFusedKeys : 1];
+    if (HIST) {
+        for (int k = threadIdx.x; k < n_keys; k += 256) h[k] = 0;
+        __syncthreads();
+    }
     const long long chunk = (n_rec + gridDim.x - 1) / gridDim.x;
     const long long begin = min(n_rec, (long long)blockIdx.x * chunk);
     const long long end = min(n_rec, begin + chunk);
@@ -72,18 +100,176 @@ __global__ void __launch_bounds__(256) k_emit_chunks(Op op, long long n_rec, con
         const uint32_t c = r < end ? op.count(r) : 0u;
         uint32_t tot;
         const uint32_t ex = block_exclusive_scan_256(c, sm, &tot);
-        if (c) op.emit(r, out, running + ex, capacity);
+        if (c) {
+            unsigned long long off = running + ex;
+            op.entries(r, [&](uint32_t key, uint32_t id) {
+                if (off < capacity) {
+                    out[off] = ((uint64_t)key << 32) | (uint64_t)id;
+                    if (HIST) atomicAdd(&h[key], 1u);
+                }
+                ++off;
+            });
+        }
         running += tot;
+    }
+    if (HIST) {
+        __syncthreads();
+        for (int k = threadIdx.x; k < n_keys; k += 256) {
+            const uint32_t cnt = h[k];
+            hist[(size_t)k * gridDim.x + blockIdx.x] = cnt;
+            if (cnt) atomicAdd(&key_totals[k], cnt);
+        }
     }
 }
 
-// Launch the three steps; the status block must have been cleared by the caller.
+// One block per key k: the scatter offset of (k, emit block b) = entries of
+// smaller keys + entries of key k in earlier blocks (hist rewritten in place),
+// the key's range [start, end) ([0, 0) when empty), its first work item and its
+// ceil(n / chunk) items; the last key's block writes the item count.
+static __global__ void __launch_bounds__(256) k_fused_offsets(uint32_t* __restrict__ hist,
+                                                              const uint32_t* __restrict__ key_totals, int nb,
+                                                              int n_keys, uint32_t chunk, uint2* __restrict__ ranges,
+                                                              uint32_t* __restrict__ item_off,
+                                                              uint64_t* __restrict__ items,
+                                                              unsigned long long items_cap,
+                                                              WsStatus* __restrict__ item_st) {
+    __shared__ uint32_t sm[8];
+    __shared__ uint32_t s_base, s_ibase;
+    const int k = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
+    if (tid < 32) {
+        uint32_t part = 0, ipart = 0;
+        for (int q = lane; q < k; q += 32) {
+            const uint32_t t = key_totals[q];
+            part += t;
+            ipart += (t + chunk - 1) / chunk;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            part += __shfl_xor_sync(0xffffffffu, part, o);
+            ipart += __shfl_xor_sync(0xffffffffu, ipart, o);
+        }
+        if (lane == 0) {
+            s_base = part;
+            s_ibase = ipart;
+        }
+    }
+    __syncthreads();
+    const uint32_t base = s_base, ibase = s_ibase;
+    uint32_t running = base;
+    uint32_t* row = hist + (size_t)k * nb;
+    for (int c = 0; c < nb; c += 256) {  // uniform trip count: the scan syncs the block
+        const int idx = c + tid;
+        const uint32_t v = idx < nb ? row[idx] : 0u;
+        uint32_t tot;
+        const uint32_t ex = block_exclusive_scan_256(v, sm, &tot);
+        if (idx < nb) row[idx] = running + ex;
+        running += tot;
+    }
+    const uint32_t total = key_totals[k];
+    const uint32_t nch = (total + chunk - 1) / chunk;
+    if (tid == 0) {
+        ranges[k] = total ? make_uint2(base, base + total) : make_uint2(0u, 0u);
+        item_off[k] = ibase;
+        if (k == n_keys - 1) item_st->n_keys = (unsigned long long)ibase + nch;
+    }
+    for (uint32_t c = tid; c < nch; c += 256)
+        if (ibase + c < items_cap) items[ibase + c] = ((uint64_t)(uint32_t)k << 32) | c;
+}
+
+// One block per emit block: its entries [start_b, start_{b+1}) (clipped to the
+// written count) go to their sorted positions.  Each warp takes one contiguous
+// run; per-(warp, key) counts and the block's offsets give each warp its base
+// per key; inside a warp, lanes with equal keys are ranked by lane (match mask),
+// so equal keys keep their input order.
+static __global__ void __launch_bounds__(256) k_fused_scatter(const uint64_t* __restrict__ in,
+                                                              uint64_t* __restrict__ out,
+                                                              const uint32_t* __restrict__ offs,
+                                                              const unsigned long long* __restrict__ starts,
+                                                              const WsStatus* __restrict__ st, int n_keys) {
+    __shared__ uint32_t s_h[8][kFusedKeys];
+    const int b = blockIdx.x, nb = gridDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned long long n_written = st->n_keys;
+    const unsigned long long lo = min(starts[b], n_written);
+    const unsigned long long hi = (b + 1 < nb) ? min(starts[b + 1], n_written) : n_written;
+    const unsigned long long per = (hi - lo + 7) / 8;
+    const unsigned long long wlo = min(hi, lo + warp * per), whi = min(hi, wlo + per);
+    for (int k = tid; k < n_keys; k += 256)
+#pragma unroll
+        for (int w = 0; w < 8; ++w) s_h[w][k] = 0;
+    __syncthreads();
+    for (unsigned long long i = wlo + lane; i < whi; i += 32) atomicAdd(&s_h[warp][(uint32_t)(in[i] >> 32)], 1u);
+    __syncthreads();
+    for (int k = tid; k < n_keys; k += 256) {
+        uint32_t run = offs[(size_t)k * nb + b];
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+            const uint32_t c = s_h[w][k];
+            s_h[w][k] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    const uint32_t lt = (1u << lane) - 1u;
+    for (unsigned long long base = wlo; base < whi; base += 32) {
+        const unsigned long long i = base + lane;
+        const bool valid = i < whi;
+        const uint64_t x = valid ? in[i] : 0ull;
+        const uint32_t k = valid ? (uint32_t)(x >> 32) : 0xffffffffu;
+        const uint32_t peers = __match_any_sync(0xffffffffu, k);
+        const uint32_t rank = __popc(peers & lt);
+        const uint32_t pos = valid ? s_h[warp][k] + rank : 0u;
+        __syncwarp();
+        if (valid && rank == 0) s_h[warp][k] += __popc(peers);
+        __syncwarp();
+        if (valid) out[pos] = x;
+    }
+}
+
+// Whether a key space takes the fused path, and where the sorted lists end up.
+inline bool fused_lists(long long n_slots) { return n_slots <= kFusedKeys; }
+inline int list_sort_passes(long long n_slots) {
+    return fused_lists(n_slots) ? 1 : (bits_for(n_slots) + kRadixBits - 1) / kRadixBits;
+}
+
+// Emit, sort and range the lists of n_slots keys; returns the buffer (a or b)
+// holding the sorted entries and adds the kernel launches to *launches.  The
+// status block must have been cleared by the caller.
 template <class Op>
-void emit_lists(const Op& op, long long n_rec, unsigned long long* partials, WsStatus* st, uint64_t* out,
-                unsigned long long capacity, cudaStream_t s) {
+uint64_t* build_lists(const Op& op, long long n_rec, long long n_slots, unsigned long long* partials, WsStatus* st,
+                      uint64_t* a, uint64_t* b, uint32_t* scratch, long long cap, uint2* ranges, WsStatus* item_st,
+                      uint32_t* item_off, uint64_t* items, long long items_cap, int chunk, cudaStream_t s,
+                      int* launches) {
+    const unsigned long long ucap = (unsigned long long)cap;
+    if (fused_lists(n_slots)) {
+        uint32_t* hist = scratch;
+        uint32_t* totals = scratch + (size_t)kRadix * kSortBlocksMax;
+        const int nk = (int)n_slots;
+        prof_begin(P_EMIT, s);
+        k_count_chunks<Op><<<kScanBlocks, 256, 0, s>>>(op, n_rec, partials);
+        k_scan_chunks<<<1, 1024, 0, s>>>(partials, kScanBlocks, st, ucap, totals, nk);
+        k_emit_chunks<Op, true><<<kScanBlocks, 256, 0, s>>>(op, n_rec, partials, a, ucap, hist, totals, nk);
+        prof_end(P_EMIT, s);
+        prof_begin(P_SORT, s);
+        k_fused_offsets<<<nk, 256, 0, s>>>(hist, totals, kScanBlocks, nk, (uint32_t)chunk, ranges, item_off, items,
+                                           (unsigned long long)items_cap, item_st);
+        k_fused_scatter<<<kScanBlocks, 256, 0, s>>>(a, b, hist, partials, st, nk);
+        prof_end(P_SORT, s);
+        *launches += 5;
+        return b;
+    }
+    prof_begin(P_EMIT, s);
     k_count_chunks<Op><<<kScanBlocks, 256, 0, s>>>(op, n_rec, partials);
-    k_scan_chunks<<<1, 1024, 0, s>>>(partials, kScanBlocks, st, capacity);
-    k_emit_chunks<Op><<<kScanBlocks, 256, 0, s>>>(op, n_rec, partials, out, capacity);
+    k_scan_chunks<<<1, 1024, 0, s>>>(partials, kScanBlocks, st, ucap, nullptr, 0);
+    k_emit_chunks<Op, false><<<kScanBlocks, 256, 0, s>>>(op, n_rec, partials, a, ucap, nullptr, nullptr, 0);
+    prof_end(P_EMIT, s);
+    prof_begin(P_SORT, s);
+    uint64_t* sorted = radix_sort_u64(a, b, scratch, st, bits_for(n_slots), sort_blocks_for(cap), s);
+    prof_end(P_SORT, s);
+    prof_begin(P_RANGES, s);
+    build_ranges_items(sorted, st, ranges, n_slots, item_st, item_off, items, items_cap, chunk, s);
+    prof_end(P_RANGES, s);
+    *launches += 3 + 3 * list_sort_passes(n_slots) + 1;
+    return sorted;
 }
 
 }  // namespace r2g

@@ -288,17 +288,14 @@ struct TileOp {
         const int x0 = rc.x & 0xffff, x1 = rc.x >> 16, y0 = rc.y & 0xffff, y1 = rc.y >> 16;
         return (x1 >= x0 && y1 >= y0) ? (uint32_t)((x1 - x0 + 1) * (y1 - y0 + 1)) : 0u;
     }
-    __device__ __forceinline__ void emit(long long r, uint64_t* out, unsigned long long off,
-                                         unsigned long long cap) const {
+    template <class F>
+    __device__ __forceinline__ void entries(long long r, F&& f) const {
         const uint2 rc = rect[r];
         const int x0 = rc.x & 0xffff, x1 = rc.x >> 16, y0 = rc.y & 0xffff, y1 = rc.y >> 16;
         const long long v = r / M, i = r - v * M;
         const uint32_t base = (uint32_t)(v * tiles_per_view);
         for (int ty = y0; ty <= y1; ++ty)
-            for (int tx = x0; tx <= x1; ++tx) {
-                if (off < cap) out[off] = ((uint64_t)(base + (uint32_t)(ty * tiles_x + tx)) << 32) | (uint64_t)i;
-                ++off;
-            }
+            for (int tx = x0; tx <= x1; ++tx) f(base + (uint32_t)(ty * tiles_x + tx), (uint32_t)i);
     }
 };
 
@@ -867,9 +864,7 @@ void launch_bwd(int tw, int th, const float4* rec, const uint2* ranges, const ui
 }
 
 uint64_t* sorted_buffer(char* base, const RasterLayout& L, const Tail& t) {
-    const int bits = bits_for(L.n_tiles);
-    const int passes = (bits + kRadixBits - 1) / kRadixBits;
-    return reinterpret_cast<uint64_t*>(base + ((passes & 1) ? t.b : t.a));
+    return reinterpret_cast<uint64_t*>(base + ((list_sort_passes(L.n_tiles) & 1) ? t.b : t.a));
 }
 
 }  // namespace
@@ -940,15 +935,9 @@ r2g_status r2g::rasterize_impl(int64_t M, const float* mean, const float* scale,
                                                                       rect, nullptr, nullptr);
     prof_end(P_PROJECT, stream);
     TileOp op{rect, M, L.tiles_x, L.tiles_per_view};
-    prof_begin(P_EMIT, stream);
-    emit_lists(op, L.n_rec, partials, st, a, (unsigned long long)cap, stream);
-    prof_end(P_EMIT, stream);
-    prof_begin(P_SORT, stream);
-    uint64_t* sorted = radix_sort_u64(a, b, scratch, st, bits_for(L.n_tiles), sort_blocks_for(cap), stream);
-    prof_end(P_SORT, stream);
-    prof_begin(P_RANGES, stream);
-    build_ranges_items(sorted, st, ranges, L.n_tiles, item_st, item_off, items, T.icap, kChunk, stream);
-    prof_end(P_RANGES, stream);
+    int launches = 0;
+    uint64_t* sorted = build_lists(op, L.n_rec, L.n_tiles, partials, st, a, b, scratch, cap, ranges, item_st,
+                                   item_off, items, T.icap, kChunk, stream, &launches);
     const float Tq = -0.5f * kLog2e * opts->Q;
     prof_begin(P_SPLAT_FWD, stream);
     const FwdArgs fa{rec, ranges, sorted, items, item_st, partial, item_off};
@@ -957,7 +946,7 @@ r2g_status r2g::rasterize_impl(int64_t M, const float* mean, const float* scale,
     else
         launch_fwd<false>(opts->tile_w, opts->tile_h, fa, M, L, T.icap, cam->H, cam->W, Tq, image, st, stream);
     prof_end(P_SPLAT_FWD, stream);
-    note_launches(1 + 3 + 3 * ((bits_for(L.n_tiles) + kRadixBits - 1) / kRadixBits) + 1 + 2);
+    note_launches(1 + launches + 2);
     return check_launch("r2g_rasterize");
 }
 

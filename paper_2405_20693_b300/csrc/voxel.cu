@@ -175,8 +175,8 @@ struct BrickEmitOp {
         const int z0 = rc.z & 0xffff, z1 = rc.z >> 16;
         return (x1 >= x0 && y1 >= y0 && z1 >= z0) ? (uint32_t)((x1 - x0 + 1) * (y1 - y0 + 1) * (z1 - z0 + 1)) : 0u;
     }
-    __device__ __forceinline__ void emit(long long r, uint64_t* out, unsigned long long off,
-                                         unsigned long long cap) const {
+    template <class F>
+    __device__ __forceinline__ void entries(long long r, F&& f) const {
         const uint4 rc = rect[r];
         const int x0 = rc.x & 0xffff, x1 = rc.x >> 16, y0 = rc.y & 0xffff, y1 = rc.y >> 16;
         const int z0 = rc.z & 0xffff, z1 = rc.z >> 16;
@@ -186,11 +186,8 @@ struct BrickEmitOp {
         const int nx = nbx[g], ny = nby[g];
         for (int bz = z0; bz <= z1; ++bz)
             for (int by = y0; by <= y1; ++by)
-                for (int bx = x0; bx <= x1; ++bx) {
-                    const uint32_t key = (uint32_t)(bb + ((long long)bz * ny + by) * nx + bx);
-                    if (off < cap) out[off] = ((uint64_t)key << 32) | (uint64_t)i;
-                    ++off;
-                }
+                for (int bx = x0; bx <= x1; ++bx)
+                    f((uint32_t)(bb + ((long long)bz * ny + by) * nx + bx), (uint32_t)i);
     }
 };
 
@@ -659,8 +656,7 @@ long long vox_capacity(const VoxLayout& L, size_t ws_bytes) {
 }
 
 uint64_t* vox_sorted(char* base, const VoxLayout& L, const VTail& t) {
-    const int passes = (bits_for(L.n_bricks) + kRadixBits - 1) / kRadixBits;
-    return reinterpret_cast<uint64_t*>(base + ((passes & 1) ? t.b : t.a));
+    return reinterpret_cast<uint64_t*>(base + ((list_sort_passes(L.n_bricks) & 1) ? t.b : t.a));
 }
 
 r2g_status check_params(int64_t M, const float* mean, const float* scale, const float* quat, const float* rho) {
@@ -726,17 +722,11 @@ r2g_status voxelize_impl(int64_t M, const float* mean, const float* scale, const
         op.nbx[g] = gr.g[g].nb[0];
         op.nby[g] = gr.g[g].nb[1];
     }
-    prof_begin(P_EMIT, stream);
-    emit_lists(op, L.n_rec, partials, st, a, (unsigned long long)cap, stream);
-    prof_end(P_EMIT, stream);
-    prof_begin(P_SORT, stream);
-    uint64_t* sorted = radix_sort_u64(a, b, scratch, st, bits_for(L.n_bricks), sort_blocks_for(cap), stream);
-    prof_end(P_SORT, stream);
-    prof_begin(P_RANGES, stream);
-    build_ranges_items(sorted, st, ranges, L.n_bricks, item_st, item_off, items, T.icap, kVoxChunk, stream);
-    prof_end(P_RANGES, stream);
+    int launches = 0;
+    uint64_t* sorted = build_lists(op, L.n_rec, L.n_bricks, partials, st, a, b, scratch, cap, ranges, item_st,
+                                   item_off, items, T.icap, kVoxChunk, stream, &launches);
     const float Tq = -0.5f * kLog2e * Q3;
-    note_launches(1 + 3 + 3 * ((bits_for(L.n_bricks) + kRadixBits - 1) / kRadixBits) + 1 + 2);
+    note_launches(1 + launches + 2);
     prof_begin(P_VOX_FWD, stream);
     if (count)
         k_vox_fwd<true><<<(unsigned)T.icap, kVoxThreads, 0, stream>>>(rec, ranges, sorted, items, item_st, partial, M,

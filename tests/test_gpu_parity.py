@@ -23,6 +23,17 @@ def _lib():
     torch.cuda.init()
 
 
+def _case(case):
+    """config1 / parallel: 4 views x 16 tiles; cone: 3 views x 42 tiles -- both take
+    the fused list path (<= 1024 keys); cone25: 25 views x 42 tiles = 1050 keys at
+    16 x 16, the general radix-sort path."""
+    if case in ("parallel", "config1"):
+        return config1()
+    if case == "cone25":
+        return cone_small(M=1500, V=25)
+    return cone_small()
+
+
 def _project(G, views, cam, tile=(16, 16)):
     mean, scale, quat, rho = dev_set(G)
     M, V = G.M, views.shape[0]
@@ -60,9 +71,9 @@ def _lists_gpu(rast, M, V):
 
 
 @pytest.mark.parametrize("case,tile", [("parallel", (16, 16)), ("cone", (16, 16)), ("cone", (8, 8)),
-                                       ("parallel", (32, 8))])
+                                       ("parallel", (32, 8)), ("cone25", (16, 16))])
 def test_tile_lists_bit_exact(case, tile):
-    G, cam, views = config1() if case == "parallel" else cone_small()
+    G, cam, views = _case(case)
     rast = engine.Rasterizer(G.M, views.shape[0], cam, tile=tile, capacity=1024)  # forces a regrow
     rast.forward(*dev_set(G), dev(views))
     ranges, ids, n = _lists_gpu(rast, G.M, views.shape[0])
@@ -75,9 +86,9 @@ def test_tile_lists_bit_exact(case, tile):
         assert np.array_equal(got, exp), t  # same ids, ascending (stable sort)
 
 
-@pytest.mark.parametrize("case", ["config1", "cone"])
+@pytest.mark.parametrize("case", ["config1", "cone", "cone25"])
 def test_rasterize_matches_oracle(case):
-    G, cam, views = config1() if case == "config1" else cone_small()
+    G, cam, views = _case(case)
     rast = engine.Rasterizer(G.M, views.shape[0], cam)
     img = rast.forward(*dev_set(G), dev(views), count=True)
     torch.cuda.synchronize()
@@ -124,9 +135,9 @@ def test_rasterize_ragged_detector_and_empty_cases():
     assert float(rz.forward(*dev_set(Gz), dev(views)).abs().max()) == 0.0
 
 
-@pytest.mark.parametrize("case", ["config1", "cone"])
+@pytest.mark.parametrize("case", ["config1", "cone", "cone25"])
 def test_rasterize_backward_matches_oracle_adjoint(case):
-    G, cam, views = config1() if case == "config1" else cone_small(M=1500)
+    G, cam, views = config1() if case == "config1" else cone_small(M=1500, V=25 if case == "cone25" else 3)
     V = views.shape[0]
     dimg = I.rng(5).standard_normal((V, cam.H, cam.W)).astype(np.float32)
     rast = engine.Rasterizer(G.M, V, cam)
@@ -169,13 +180,21 @@ def _grids_small():
                      (0.05, 0.04, 0.06), (13, 7, 10))])
 
 
+def _grids(kind):
+    """small: 64 + 64 + 4 = 132 bricks (fused list path); large: the same plus a 96^3
+    cube (1728 bricks), 1860 keys in all (general radix-sort path)."""
+    g = _grids_small()
+    return g if kind == "small" else np.concatenate([g, I.cube_grid(96)[None]])
+
+
 def _f32grid(gd):
     return np.asarray(gd, dtype=np.float32).astype(np.float64)
 
 
-def test_voxelize_matches_oracle_and_brick_lists_bit_exact():
+@pytest.mark.parametrize("kind", ["small", "large"])
+def test_voxelize_matches_oracle_and_brick_lists_bit_exact(kind):
     G, _, _ = config1()
-    gd = _f32grid(_grids_small())
+    gd = _f32grid(_grids(kind))
     vox = engine.Voxelizer(G.M, gd, capacity=1024)
     vol = vox.forward(*dev_set(G), count=True)
     torch.cuda.synchronize()
@@ -195,9 +214,10 @@ def test_voxelize_matches_oracle_and_brick_lists_bit_exact():
         assert np.array_equal(ids[s:e].astype(np.int64), refl.get(b, np.zeros(0, np.int64))), b
 
 
-def test_voxelize_backward_matches_oracle_adjoint():
+@pytest.mark.parametrize("kind", ["small", "large"])
+def test_voxelize_backward_matches_oracle_adjoint(kind):
     G = I.uniform_gaussians(600, 3, 0.02, 0.12)
-    gd = _f32grid(_grids_small())
+    gd = _f32grid(_grids(kind))
     vox = engine.Voxelizer(G.M, gd)
     mean, scale, quat, rho = dev_set(G)
     vox.forward(mean, scale, quat, rho)
