@@ -16,12 +16,13 @@
 //                  and skips records whose box misses it.  Tiles with several
 //                  chunks write per-chunk images that k_splat_reduce sums in
 //                  chunk order.
-//   k_splat_bwd    one CTA per tile with dL/dI of the tile in shared memory;
-//                  each thread takes one record and walks the pixels of its
-//                  box inside the tile, accumulating six moments
-//                  (sum w, w dx, w dy, w dx^2, w dx dy, w dy^2; w = g e) in
-//                  registers -- no shuffles -- then adds them with two vector
-//                  atomics to the record's slot.
+//   k_splat_bwd    one CTA per work item with dL/dI of the tile in shared
+//                  memory; the records' boxes are cut into units of kBwdUnit
+//                  pixels along a row and the units split evenly over the 128
+//                  lanes; each lane accumulates six moments (sum w, w dx, w dy,
+//                  w dx^2, w dx dy, w dy^2; w = g e) of its current record in
+//                  registers and adds them with two vector atomics to the
+//                  record's slot.
 //   k_project_bwd  one thread per Gaussian, looping over views: moments ->
 //                  gradients of (rho_hat, p^, conic) -> chain rule through the
 //                  projection to d mean, d scale, d quat, d rho.
@@ -434,14 +435,36 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t x) {
     return x;
 }
 
+// CTA-wide exclusive scan of one value per thread (kBwdThreads = 128 threads).
+__device__ __forceinline__ uint32_t cta_excl_scan_128(uint32_t v, uint32_t* s_w, uint32_t* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t incl = warp_incl_scan(v);
+    if (lane == 31) s_w[warp] = incl;
+    __syncthreads();
+    uint32_t before = 0, tot = 0;
+#pragma unroll
+    for (int w = 0; w < kBwdThreads / 32; ++w) {
+        const uint32_t x = s_w[w];
+        before += (w < warp) ? x : 0u;
+        tot += x;
+    }
+    *total = tot;
+    return before + incl - v;
+}
+
+// Pixels per backward unit (a run of UW pixels along a row of a record's box).
+constexpr int kBwdUnit = 4;
+
 // One CTA per work item (<= 128 records of one tile).  Each record's pixel box
-// inside the tile is a w x h rectangle of n = w h pixels.  Within a warp the
-// n-sums of its 32 records are split into 32 equal contiguous ranges of
-// (record, pixel) pairs, one per lane, so every lane does the same number of
-// pair evaluations whatever the record sizes.  A lane keeps the six moments of
-// its current record in registers and adds them to the record's slot (two
-// vector atomics) when it leaves the record or its range ends.
-template <int TW, int TH>
+// inside the tile, w x h pixels, is cut into rows of ceil(w / UW) units of UW
+// consecutive pixels (the last unit of a row masks the pixels past w).  The units
+// of the CTA's records are split into 128 equal contiguous ranges, one per lane,
+// so every lane evaluates the same number of units whatever the record sizes.  A
+// lane derives each unit's row and column from its index inside the record (no
+// per-row state, so lanes never diverge on row changes), accumulates the six
+// moments of its current record in registers, and adds them to the record's slot
+// (two vector atomics) when it leaves the record or its range ends.
+template <int TW, int TH, int UW>
 __global__ void __launch_bounds__(kBwdThreads) k_splat_bwd(const float4* __restrict__ rec,
                                                            const uint2* __restrict__ ranges,
                                                            const uint64_t* __restrict__ sorted,
@@ -451,11 +474,13 @@ __global__ void __launch_bounds__(kBwdThreads) k_splat_bwd(const float4* __restr
                                                            const float* __restrict__ dimage,
                                                            float4* __restrict__ mom) {
     static_assert(kChunk == kBwdThreads, "one record per thread");
-    __shared__ float s_g[TH * TW];
-    __shared__ float4 s_ra[kChunk], s_rb[kChunk];
-    __shared__ int4 s_box[kChunk];       // c0, r0 (tile-local), w, n
-    __shared__ uint32_t s_gid[kChunk];
-    __shared__ uint32_t s_excl[kChunk];  // warp-exclusive prefix of n
+    static_assert(TW <= 32 && TH <= 16 && UW >= 1 && UW <= 4, "unit decode is exact for these sizes");
+    __shared__ float s_g[TH * TW + UW];    // dL/dI of the tile, then UW zeros read by masked pixels
+    __shared__ float4 s_k1[kChunk];        // A, B, C of the conic; dx of the box's first pixel
+    __shared__ float4 s_k2[kChunk];        // dy of the first row; s_g index of the first pixel; 1/uw; uw
+    __shared__ uint2 s_k3[kChunk];         // box width w in pixels, Gaussian id
+    __shared__ uint32_t s_excl[kChunk + 1];  // exclusive prefix of the unit counts; [kChunk] = total
+    __shared__ uint32_t s_w[kBwdThreads / 32];
     const unsigned long long it = blockIdx.x;
     if (it >= item_st->n_keys) return;
     const uint64_t item = items[it];
@@ -465,15 +490,15 @@ __global__ void __launch_bounds__(kBwdThreads) k_splat_bwd(const float4* __restr
     const int lt = tile - v * tiles_per_view;
     const int ty = lt / tiles_x, tx = lt - ty * tiles_x;
     const int X0 = tx * TW, Y0 = ty * TH;
-    for (int k = threadIdx.x; k < TW * TH; k += kBwdThreads) {
+    for (int k = threadIdx.x; k < TW * TH + UW; k += kBwdThreads) {
         const int r = k / TW, c = k - r * TW;
         const int gy = Y0 + r, gx = X0 + c;
-        s_g[k] = (gy < H && gx < W) ? dimage[((size_t)v * H + gy) * W + gx] : 0.0f;
+        s_g[k] = (k < TW * TH && gy < H && gx < W) ? dimage[((size_t)v * H + gy) * W + gx] : 0.0f;
     }
     const uint2 rg = ranges[tile];
     const float4* vrec = rec + 2 * (size_t)v * (size_t)M;
     float4* vmom = mom + 2 * (size_t)v * (size_t)M;
-    const int j = threadIdx.x, lane = j & 31, wbase = j & ~31;
+    const int j = threadIdx.x;
     const uint32_t e = rg.x + chunk * kChunk + j;
     uint32_t n = 0;
     if (e < rg.y) {
@@ -483,84 +508,79 @@ __global__ void __launch_bounds__(kBwdThreads) k_splat_bwd(const float4* __restr
         const int c0 = max(0, (int)ceilf(a.x - b.z) - X0), c1 = min(TW - 1, (int)floorf(a.x + b.z) - X0);
         const int r0 = max(0, (int)ceilf(a.y - b.w) - Y0), r1 = min(TH - 1, (int)floorf(a.y + b.w) - Y0);
         const int w = c1 - c0 + 1, h = r1 - r0 + 1;
-        n = (w > 0 && h > 0) ? (uint32_t)(w * h) : 0u;
-        s_ra[j] = a;
-        s_rb[j] = b;
-        s_box[j] = make_int4(c0, r0, max(w, 1), (int)n);
-        s_gid[j] = gid;
-    } else {
-        s_box[j] = make_int4(0, 0, 1, 0);
-        s_gid[j] = 0;
+        if (w > 0 && h > 0) {
+            const int uw = (w + UW - 1) / UW;
+            n = (uint32_t)(uw * h);
+            s_k1[j] = make_float4(a.z, a.w, b.x, (float)(X0 + c0) - a.x);
+            s_k2[j] = make_float4((float)(Y0 + r0) - a.y, (float)(r0 * TW + c0), 1.0f / (float)uw, (float)uw);
+            s_k3[j] = make_uint2((uint32_t)w, gid);
+        }
     }
-    const uint32_t incl = warp_incl_scan(n);
-    s_excl[j] = incl - n;
-    const uint32_t T = __shfl_sync(0xffffffffu, incl, 31);
+    uint32_t T;
+    const uint32_t ex = cta_excl_scan_128(n, s_w, &T);
+    s_excl[j] = ex;
+    if (j == 0) s_excl[kChunk] = T;
     __syncthreads();
-    const uint32_t per = (T + 31) >> 5;
-    const uint32_t p0 = lane * per, p1 = min(T, p0 + per);
+    const uint32_t per = (T + kBwdThreads - 1) / kBwdThreads;
+    const uint32_t p0 = j * per, p1 = min(T, p0 + per);
     if (p0 >= p1) return;
-    // the record holding pair p0: the largest k with excl_k <= p0 (it is non-empty)
-    int lo = 0, hi = 31;
+    // the record holding unit p0: the largest k with excl_k <= p0 (it is non-empty)
+    int lo = 0, hi = kChunk - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (s_excl[wbase + mid] <= p0) lo = mid;
+        if (s_excl[mid] <= p0) lo = mid;
         else hi = mid - 1;
     }
     int k = lo;
-    float4 a = s_ra[wbase + k], b = s_rb[wbase + k];
-    int4 box = s_box[wbase + k];
-    uint32_t rec_end = s_excl[wbase + k] + (uint32_t)box.w;
-    int li = (int)(p0 - s_excl[wbase + k]);
-    int row = li / box.z, col = li - row * box.z;
-    float dy = (float)(Y0 + box.y + row) - a.y;
-    float dx = (float)(X0 + box.x + col) - a.x;
-    float bdy = a.w * dy, cdy2 = b.x * dy * dy;
-    const float* grow = s_g + (box.y + row) * TW + box.x;
+    float4 k1 = s_k1[k], k2 = s_k2[k];
+    uint2 k3 = s_k3[k];
+    uint32_t rec_end = s_excl[k + 1];
+    float uf = (float)(p0 - s_excl[k]);  // unit index inside the record
     float S0 = 0.f, Sx = 0.f, Sy = 0.f, Sxx = 0.f, Sxy = 0.f, Syy = 0.f;
     for (uint32_t p = p0; p < p1; ++p) {
-        const float t = fmaf(fmaf(a.z, dx, bdy), dx, cdy2);
-        const float ev = ex2_approx(t);
-        const float w = (t >= Tq) ? grow[col] * ev : 0.0f;
-        const float wx = w * dx, wy = w * dy;
-        S0 += w;
-        Sx += wx;
-        Sy += wy;
-        Sxx = fmaf(wx, dx, Sxx);
-        Sxy = fmaf(wx, dy, Sxy);
-        Syy = fmaf(wy, dy, Syy);
-        ++col;
-        dx += 1.0f;
-        if (col == box.z) {  // next row of the box
-            col = 0;
-            dx -= (float)box.z;
-            dy += 1.0f;
-            grow += TW;
-            bdy = a.w * dy;
-            cdy2 = b.x * dy * dy;
+        // row = floor((u + 1/2) / uw), exact for u < 2^10 and uw <= 16
+        const float rowf = floorf(fmaf(uf, k2.z, 0.5f * k2.z));
+        const float colf = fmaf(-rowf, k2.w, uf) * (float)UW;  // first pixel of the unit, inside the box row
+        const float dx = k1.w + colf;
+        const float dy = k2.x + rowf;
+        const int gi = (int)fmaf(rowf, (float)TW, k2.y + colf);
+        const int left = (int)k3.x - (int)colf;  // pixels of the row from this unit's first on
+        const float bdy = k1.y * dy, cdy2 = k1.z * dy * dy;
+        float Wu = 0.f, Xu = 0.f;
+#pragma unroll
+        for (int q = 0; q < UW; ++q) {
+            const float dxq = dx + (float)q;
+            const float t = fmaf(fmaf(k1.x, dxq, bdy), dxq, cdy2);
+            const float ev = ex2_approx(t);
+            const bool ok = (t >= Tq) && (q == 0 || q < left);
+            const float wq = ok ? s_g[gi + q] * ev : 0.0f;
+            const float aq = wq * dxq;
+            Wu += wq;
+            Xu += aq;
+            Sxx = fmaf(aq, dxq, Sxx);
         }
+        S0 += Wu;
+        Sx += Xu;
+        Sy = fmaf(Wu, dy, Sy);
+        Sxy = fmaf(Xu, dy, Sxy);
+        Syy = fmaf(Wu * dy, dy, Syy);
+        uf += 1.0f;
         if (p + 1 == rec_end && p + 1 < p1) {  // next record
-            const uint32_t gid = s_gid[wbase + k];
-            atomicAdd(&vmom[2 * (size_t)gid], make_float4(S0, Sx, Sy, Sxx));
-            atomicAdd(reinterpret_cast<float2*>(&vmom[2 * (size_t)gid + 1]), make_float2(Sxy, Syy));
+            atomicAdd(&vmom[2 * (size_t)k3.y], make_float4(S0, Sx, Sy, Sxx));
+            atomicAdd(reinterpret_cast<float2*>(&vmom[2 * (size_t)k3.y + 1]), make_float2(Sxy, Syy));
             S0 = Sx = Sy = Sxx = Sxy = Syy = 0.f;
             do {
                 ++k;
-            } while (s_box[wbase + k].w == 0);
-            a = s_ra[wbase + k];
-            b = s_rb[wbase + k];
-            box = s_box[wbase + k];
-            rec_end += (uint32_t)box.w;
-            col = 0;
-            dy = (float)(Y0 + box.y) - a.y;
-            dx = (float)(X0 + box.x) - a.x;
-            bdy = a.w * dy;
-            cdy2 = b.x * dy * dy;
-            grow = s_g + box.y * TW + box.x;
+            } while (s_excl[k + 1] == s_excl[k]);
+            k1 = s_k1[k];
+            k2 = s_k2[k];
+            k3 = s_k3[k];
+            rec_end = s_excl[k + 1];
+            uf = 0.0f;
         }
     }
-    const uint32_t gid = s_gid[wbase + k];
-    atomicAdd(&vmom[2 * (size_t)gid], make_float4(S0, Sx, Sy, Sxx));
-    atomicAdd(reinterpret_cast<float2*>(&vmom[2 * (size_t)gid + 1]), make_float2(Sxy, Syy));
+    atomicAdd(&vmom[2 * (size_t)k3.y], make_float4(S0, Sx, Sy, Sxx));
+    atomicAdd(reinterpret_cast<float2*>(&vmom[2 * (size_t)k3.y + 1]), make_float2(Sxy, Syy));
 }
 
 // ------------------------------------------------------------------ K6: projection backward
@@ -853,13 +873,13 @@ void launch_bwd(int tw, int th, const float4* rec, const uint2* ranges, const ui
                 int H, int W, float Tq, const float* dimage, float4* mom, cudaStream_t s) {
     const unsigned grid = (unsigned)icap;
     if (tw == 16 && th == 16)
-        k_splat_bwd<16, 16><<<grid, kBwdThreads, 0, s>>>(rec, ranges, sorted, items, item_st, M, L.tiles_x,
+        k_splat_bwd<16, 16, kBwdUnit><<<grid, kBwdThreads, 0, s>>>(rec, ranges, sorted, items, item_st, M, L.tiles_x,
                                                          L.tiles_per_view, H, W, Tq, dimage, mom);
     else if (tw == 8 && th == 8)
-        k_splat_bwd<8, 8><<<grid, kBwdThreads, 0, s>>>(rec, ranges, sorted, items, item_st, M, L.tiles_x,
+        k_splat_bwd<8, 8, kBwdUnit><<<grid, kBwdThreads, 0, s>>>(rec, ranges, sorted, items, item_st, M, L.tiles_x,
                                                        L.tiles_per_view, H, W, Tq, dimage, mom);
     else
-        k_splat_bwd<32, 8><<<grid, kBwdThreads, 0, s>>>(rec, ranges, sorted, items, item_st, M, L.tiles_x,
+        k_splat_bwd<32, 8, kBwdUnit><<<grid, kBwdThreads, 0, s>>>(rec, ranges, sorted, items, item_st, M, L.tiles_x,
                                                         L.tiles_per_view, H, W, Tq, dimage, mom);
 }
 
