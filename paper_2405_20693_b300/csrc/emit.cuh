@@ -4,17 +4,17 @@
 //
 // An Op supplies, for record r, how many entries it emits (count) and visits them
 // in order (entries(r, f) calls f(key, id) once per entry).  Records are split
-// into kScanBlocks contiguous chunks; a first pass sums each chunk, one block
-// scans the chunk sums (and writes the total and the capacity verdict into the
-// status block), and a second pass re-scans each chunk in rounds of 256 records
-// and writes every record's entries at its offset, in record order.  Entries
-// beyond the capacity are not written.
+// into contiguous chunks, one per block; a first pass sums each chunk (its last
+// block to finish scans the chunk sums and writes the total and the capacity
+// verdict into the status block), and a second pass re-scans each chunk in
+// rounds of 256 records and writes every record's entries at its offset, in
+// record order.  Entries beyond the capacity are not written.
 //
 // Key spaces of at most kFusedKeys keys (one 512^2 view in 16 x 16 tiles, the
 // bricks of a TV patch) take a fused path: the emission also counts its block's
-// entries per key, one block per key turns the counts into scatter offsets, the
+// entries per key, one warp per key turns the counts into scatter offsets, the
 // key's range and its work items, and a stable scatter (one contiguous run per
-// warp, ranked with warp match masks) writes the sorted lists -- five launches
+// warp, ranked with warp match masks) writes the sorted lists -- four launches
 // and one pass over the entries.  Larger key spaces take the general stable LSD
 // radix sort and a range pass.
 #pragma once
@@ -24,54 +24,79 @@
 namespace r2g {
 
 constexpr int kFusedKeys = 1024;
-static_assert((size_t)kFusedKeys * kScanBlocks <= (size_t)kRadix * kSortBlocksMax,
+constexpr int kFusedBlocks = 148;  // emit / scatter blocks of the fused path
+static_assert(kScanBlocks <= 1024 && kFusedBlocks <= 1024, "the last count block scans <= 1024 chunk sums");
+static_assert((size_t)kFusedKeys * kFusedBlocks <= (size_t)kRadix * kSortBlocksMax,
               "fused histograms fit the sort scratch");
 static_assert(kFusedKeys <= kRadix * 4, "fused key totals fit the sort scratch");
 
-template <class Op>
-__global__ void __launch_bounds__(256) k_count_chunks(Op op, long long n_rec, unsigned long long* partials) {
-    __shared__ unsigned long long sm[8];
-    const long long chunk = (n_rec + gridDim.x - 1) / gridDim.x;
-    const long long begin = min(n_rec, (long long)blockIdx.x * chunk);
-    const long long end = min(n_rec, begin + chunk);
-    unsigned long long s = 0;
-    for (long long r = begin + threadIdx.x; r < end; r += 256) s += op.count(r);
-    s = block_sum_u64_256(s, sm);
-    if (threadIdx.x == 0) partials[blockIdx.x] = s;
-}
-
-// One block of 1024 threads; nb <= 1024.  partials become exclusive offsets.
-// key_totals (fused path): cleared here, before the emission adds into them.
-static __global__ void __launch_bounds__(1024) k_scan_chunks(unsigned long long* partials, int nb, WsStatus* st,
-                                                             unsigned long long capacity, uint32_t* key_totals,
-                                                             int n_keys) {
-    __shared__ unsigned long long wsum[32];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (key_totals)
-        for (int k = tid; k < n_keys; k += 1024) key_totals[k] = 0;
-    const unsigned long long v = tid < nb ? partials[tid] : 0ull;
+// Block-wide exclusive scan of a 64-bit value for a 256-thread block.
+__device__ __forceinline__ unsigned long long block_excl_scan_u64_256(unsigned long long v, unsigned long long* smem,
+                                                                      unsigned long long* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned long long x = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
         if (lane >= o) x += y;
     }
-    if (lane == 31) wsum[warp] = x;
+    if (lane == 31) smem[warp] = x;
     __syncthreads();
-    if (warp == 0) {
-        unsigned long long w = wsum[lane];
+    unsigned long long before = 0, tot = 0;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned long long y = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += y;
-        }
-        wsum[lane] = w;  // inclusive
+    for (int w = 0; w < 8; ++w) {
+        const unsigned long long t = smem[w];
+        before += (w < warp) ? t : 0ull;
+        tot += t;
     }
     __syncthreads();
-    const unsigned long long before = (warp > 0 ? wsum[warp - 1] : 0ull) + x - v;
-    if (tid < nb) partials[tid] = before;
-    if (tid == 0) {
-        const unsigned long long total = wsum[31];
+    *total = tot;
+    return before + x - v;
+}
+
+// Each block sums the entry counts of its contiguous chunk of records.  The last
+// block to finish (arrival counter in the status block, cleared by the caller)
+// turns the gridDim.x <= 1024 chunk sums into exclusive offsets, writes the total
+// and the capacity verdict, and clears key_totals (fused path) for the emission.
+template <class Op>
+__global__ void __launch_bounds__(256) k_count_chunks(Op op, long long n_rec, unsigned long long* partials,
+                                                      WsStatus* st, unsigned long long capacity,
+                                                      uint32_t* key_totals, int n_keys) {
+    __shared__ unsigned long long sm[8];
+    __shared__ int s_last;
+    const long long chunk = (n_rec + gridDim.x - 1) / gridDim.x;
+    const long long begin = min(n_rec, (long long)blockIdx.x * chunk);
+    const long long end = min(n_rec, begin + chunk);
+    unsigned long long s = 0;
+    for (long long r = begin + threadIdx.x; r < end; r += 256) s += op.count(r);
+    s = block_sum_u64_256(s, sm);
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = s;
+        __threadfence();
+        s_last = atomicAdd(&st->blocks_done, 1ull) == (unsigned long long)(gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const int nb = (int)gridDim.x, t = threadIdx.x;
+    unsigned long long v[4], mine = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int i = 4 * t + q;
+        v[q] = i < nb ? __ldcg(partials + i) : 0ull;
+        mine += v[q];
+    }
+    unsigned long long total;
+    unsigned long long run = block_excl_scan_u64_256(mine, sm, &total);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int i = 4 * t + q;
+        if (i < nb) partials[i] = run;
+        run += v[q];
+    }
+    if (key_totals)
+        for (int k = t; k < n_keys; k += 256) key_totals[k] = 0;
+    if (t == 0) {
         st->needed = total;
         st->n_keys = total < capacity ? total : capacity;
         if (total > capacity) st->status = R2G_E_CAPACITY;
@@ -122,10 +147,10 @@ __global__ void __launch_bounds__(256) k_emit_chunks(Op op, long long n_rec, con
     }
 }
 
-// One block per key k: the scatter offset of (k, emit block b) = entries of
+// One warp per key k: the scatter offset of (k, emit block b) = entries of
 // smaller keys + entries of key k in earlier blocks (hist rewritten in place),
 // the key's range [start, end) ([0, 0) when empty), its first work item and its
-// ceil(n / chunk) items; the last key's block writes the item count.
+// ceil(n / chunk) items; the last key's warp writes the item count.
 static __global__ void __launch_bounds__(256) k_fused_offsets(uint32_t* __restrict__ hist,
                                                               const uint32_t* __restrict__ key_totals, int nb,
                                                               int n_keys, uint32_t chunk, uint2* __restrict__ ranges,
@@ -133,46 +158,42 @@ static __global__ void __launch_bounds__(256) k_fused_offsets(uint32_t* __restri
                                                               uint64_t* __restrict__ items,
                                                               unsigned long long items_cap,
                                                               WsStatus* __restrict__ item_st) {
-    __shared__ uint32_t sm[8];
-    __shared__ uint32_t s_base, s_ibase;
-    const int k = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
-    if (tid < 32) {
-        uint32_t part = 0, ipart = 0;
-        for (int q = lane; q < k; q += 32) {
-            const uint32_t t = key_totals[q];
-            part += t;
-            ipart += (t + chunk - 1) / chunk;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            part += __shfl_xor_sync(0xffffffffu, part, o);
-            ipart += __shfl_xor_sync(0xffffffffu, ipart, o);
-        }
-        if (lane == 0) {
-            s_base = part;
-            s_ibase = ipart;
-        }
+    const int lane = threadIdx.x & 31;
+    const int k = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (k >= n_keys) return;
+    uint32_t base = 0, ibase = 0;
+    for (int q = lane; q < k; q += 32) {
+        const uint32_t t = key_totals[q];
+        base += t;
+        ibase += (t + chunk - 1) / chunk;
     }
-    __syncthreads();
-    const uint32_t base = s_base, ibase = s_ibase;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        base += __shfl_xor_sync(0xffffffffu, base, o);
+        ibase += __shfl_xor_sync(0xffffffffu, ibase, o);
+    }
     uint32_t running = base;
     uint32_t* row = hist + (size_t)k * nb;
-    for (int c = 0; c < nb; c += 256) {  // uniform trip count: the scan syncs the block
-        const int idx = c + tid;
+    for (int c = 0; c < nb; c += 32) {
+        const int idx = c + lane;
         const uint32_t v = idx < nb ? row[idx] : 0u;
-        uint32_t tot;
-        const uint32_t ex = block_exclusive_scan_256(v, sm, &tot);
-        if (idx < nb) row[idx] = running + ex;
-        running += tot;
+        uint32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (idx < nb) row[idx] = running + x - v;
+        running += __shfl_sync(0xffffffffu, x, 31);
     }
     const uint32_t total = key_totals[k];
     const uint32_t nch = (total + chunk - 1) / chunk;
-    if (tid == 0) {
+    if (lane == 0) {
         ranges[k] = total ? make_uint2(base, base + total) : make_uint2(0u, 0u);
         item_off[k] = ibase;
         if (k == n_keys - 1) item_st->n_keys = (unsigned long long)ibase + nch;
     }
-    for (uint32_t c = tid; c < nch; c += 256)
+    for (uint32_t c = lane; c < nch; c += 32)
         if (ibase + c < items_cap) items[ibase + c] = ((uint64_t)(uint32_t)k << 32) | c;
 }
 
@@ -245,21 +266,19 @@ uint64_t* build_lists(const Op& op, long long n_rec, long long n_slots, unsigned
         uint32_t* totals = scratch + (size_t)kRadix * kSortBlocksMax;
         const int nk = (int)n_slots;
         prof_begin(P_EMIT, s);
-        k_count_chunks<Op><<<kScanBlocks, 256, 0, s>>>(op, n_rec, partials);
-        k_scan_chunks<<<1, 1024, 0, s>>>(partials, kScanBlocks, st, ucap, totals, nk);
-        k_emit_chunks<Op, true><<<kScanBlocks, 256, 0, s>>>(op, n_rec, partials, a, ucap, hist, totals, nk);
+        k_count_chunks<Op><<<kFusedBlocks, 256, 0, s>>>(op, n_rec, partials, st, ucap, totals, nk);
+        k_emit_chunks<Op, true><<<kFusedBlocks, 256, 0, s>>>(op, n_rec, partials, a, ucap, hist, totals, nk);
         prof_end(P_EMIT, s);
         prof_begin(P_SORT, s);
-        k_fused_offsets<<<nk, 256, 0, s>>>(hist, totals, kScanBlocks, nk, (uint32_t)chunk, ranges, item_off, items,
-                                           (unsigned long long)items_cap, item_st);
-        k_fused_scatter<<<kScanBlocks, 256, 0, s>>>(a, b, hist, partials, st, nk);
+        k_fused_offsets<<<(nk + 7) / 8, 256, 0, s>>>(hist, totals, kFusedBlocks, nk, (uint32_t)chunk, ranges,
+                                                      item_off, items, (unsigned long long)items_cap, item_st);
+        k_fused_scatter<<<kFusedBlocks, 256, 0, s>>>(a, b, hist, partials, st, nk);
         prof_end(P_SORT, s);
-        *launches += 5;
+        *launches += 4;
         return b;
     }
     prof_begin(P_EMIT, s);
-    k_count_chunks<Op><<<kScanBlocks, 256, 0, s>>>(op, n_rec, partials);
-    k_scan_chunks<<<1, 1024, 0, s>>>(partials, kScanBlocks, st, ucap, nullptr, 0);
+    k_count_chunks<Op><<<kScanBlocks, 256, 0, s>>>(op, n_rec, partials, st, ucap, nullptr, 0);
     k_emit_chunks<Op, false><<<kScanBlocks, 256, 0, s>>>(op, n_rec, partials, a, ucap, nullptr, nullptr, 0);
     prof_end(P_EMIT, s);
     prof_begin(P_SORT, s);
@@ -268,7 +287,7 @@ uint64_t* build_lists(const Op& op, long long n_rec, long long n_slots, unsigned
     prof_begin(P_RANGES, s);
     build_ranges_items(sorted, st, ranges, n_slots, item_st, item_off, items, items_cap, chunk, s);
     prof_end(P_RANGES, s);
-    *launches += 3 + 3 * list_sort_passes(n_slots) + 1;
+    *launches += 2 + 3 * list_sort_passes(n_slots) + 1;
     return sorted;
 }
 

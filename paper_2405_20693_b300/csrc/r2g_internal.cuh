@@ -41,7 +41,8 @@ struct WsStatus {
     unsigned long long needed;  // list entries the last call needed
     unsigned long long n_keys;  // entries actually emitted = min(needed, capacity)
     unsigned long long pairs;   // gated pairs (counting runs only)
-    unsigned long long reserved[28];
+    unsigned long long blocks_done;  // arrival counter of the entry count pass
+    unsigned long long reserved[27];
 };
 static_assert(sizeof(WsStatus) == 256, "status block is 256 bytes");
 

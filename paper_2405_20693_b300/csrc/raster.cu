@@ -457,7 +457,10 @@ constexpr int kBwdUnit = 4;
 
 // One CTA per work item (<= 128 records of one tile).  Each record's pixel box
 // inside the tile, w x h pixels, is cut into rows of ceil(w / UW) units of UW
-// consecutive pixels (the last unit of a row masks the pixels past w).  The units
+// consecutive pixels.  The last unit of a row may reach past the box: those
+// pixels lie outside the box, where the gate t >= Tq rejects them exactly as the
+// forward does, or past the tile edge, where the staged dL/dI rows are padded
+// with UW zeros.  The units
 // of the CTA's records are split into 128 equal contiguous ranges, one per lane,
 // so every lane evaluates the same number of units whatever the record sizes.  A
 // lane derives each unit's row and column from its index inside the record (no
@@ -475,10 +478,11 @@ __global__ void __launch_bounds__(kBwdThreads) k_splat_bwd(const float4* __restr
                                                            float4* __restrict__ mom) {
     static_assert(kChunk == kBwdThreads, "one record per thread");
     static_assert(TW <= 32 && TH <= 16 && UW >= 1 && UW <= 4, "unit decode is exact for these sizes");
-    __shared__ float s_g[TH * TW + UW];    // dL/dI of the tile, then UW zeros read by masked pixels
+    constexpr int TWP = TW + UW;          // staged row stride: UW zero columns past the tile edge
+    __shared__ float s_g[TH * TWP];       // dL/dI of the tile
     __shared__ float4 s_k1[kChunk];        // A, B, C of the conic; dx of the box's first pixel
     __shared__ float4 s_k2[kChunk];        // dy of the first row; s_g index of the first pixel; 1/uw; uw
-    __shared__ uint2 s_k3[kChunk];         // box width w in pixels, Gaussian id
+    __shared__ uint32_t s_gid[kChunk];     // Gaussian id
     __shared__ uint32_t s_excl[kChunk + 1];  // exclusive prefix of the unit counts; [kChunk] = total
     __shared__ uint32_t s_w[kBwdThreads / 32];
     const unsigned long long it = blockIdx.x;
@@ -490,10 +494,10 @@ __global__ void __launch_bounds__(kBwdThreads) k_splat_bwd(const float4* __restr
     const int lt = tile - v * tiles_per_view;
     const int ty = lt / tiles_x, tx = lt - ty * tiles_x;
     const int X0 = tx * TW, Y0 = ty * TH;
-    for (int k = threadIdx.x; k < TW * TH + UW; k += kBwdThreads) {
-        const int r = k / TW, c = k - r * TW;
+    for (int k = threadIdx.x; k < TH * TWP; k += kBwdThreads) {
+        const int r = k / TWP, c = k - r * TWP;
         const int gy = Y0 + r, gx = X0 + c;
-        s_g[k] = (k < TW * TH && gy < H && gx < W) ? dimage[((size_t)v * H + gy) * W + gx] : 0.0f;
+        s_g[k] = (c < TW && gy < H && gx < W) ? dimage[((size_t)v * H + gy) * W + gx] : 0.0f;
     }
     const uint2 rg = ranges[tile];
     const float4* vrec = rec + 2 * (size_t)v * (size_t)M;
@@ -512,8 +516,8 @@ __global__ void __launch_bounds__(kBwdThreads) k_splat_bwd(const float4* __restr
             const int uw = (w + UW - 1) / UW;
             n = (uint32_t)(uw * h);
             s_k1[j] = make_float4(a.z, a.w, b.x, (float)(X0 + c0) - a.x);
-            s_k2[j] = make_float4((float)(Y0 + r0) - a.y, (float)(r0 * TW + c0), 1.0f / (float)uw, (float)uw);
-            s_k3[j] = make_uint2((uint32_t)w, gid);
+            s_k2[j] = make_float4((float)(Y0 + r0) - a.y, (float)(r0 * TWP + c0), 1.0f / (float)uw, (float)uw);
+            s_gid[j] = gid;
         }
     }
     uint32_t T;
@@ -533,7 +537,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_splat_bwd(const float4* __restr
     }
     int k = lo;
     float4 k1 = s_k1[k], k2 = s_k2[k];
-    uint2 k3 = s_k3[k];
+    uint32_t gid = s_gid[k];
     uint32_t rec_end = s_excl[k + 1];
     float uf = (float)(p0 - s_excl[k]);  // unit index inside the record
     float S0 = 0.f, Sx = 0.f, Sy = 0.f, Sxx = 0.f, Sxy = 0.f, Syy = 0.f;
@@ -543,8 +547,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_splat_bwd(const float4* __restr
         const float colf = fmaf(-rowf, k2.w, uf) * (float)UW;  // first pixel of the unit, inside the box row
         const float dx = k1.w + colf;
         const float dy = k2.x + rowf;
-        const int gi = (int)fmaf(rowf, (float)TW, k2.y + colf);
-        const int left = (int)k3.x - (int)colf;  // pixels of the row from this unit's first on
+        const int gi = (int)fmaf(rowf, (float)TWP, k2.y + colf);
         const float bdy = k1.y * dy, cdy2 = k1.z * dy * dy;
         float Wu = 0.f, Xu = 0.f;
 #pragma unroll
@@ -552,8 +555,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_splat_bwd(const float4* __restr
             const float dxq = dx + (float)q;
             const float t = fmaf(fmaf(k1.x, dxq, bdy), dxq, cdy2);
             const float ev = ex2_approx(t);
-            const bool ok = (t >= Tq) && (q == 0 || q < left);
-            const float wq = ok ? s_g[gi + q] * ev : 0.0f;
+            const float wq = (t >= Tq) ? s_g[gi + q] * ev : 0.0f;
             const float aq = wq * dxq;
             Wu += wq;
             Xu += aq;
@@ -566,21 +568,21 @@ __global__ void __launch_bounds__(kBwdThreads) k_splat_bwd(const float4* __restr
         Syy = fmaf(Wu * dy, dy, Syy);
         uf += 1.0f;
         if (p + 1 == rec_end && p + 1 < p1) {  // next record
-            atomicAdd(&vmom[2 * (size_t)k3.y], make_float4(S0, Sx, Sy, Sxx));
-            atomicAdd(reinterpret_cast<float2*>(&vmom[2 * (size_t)k3.y + 1]), make_float2(Sxy, Syy));
+            atomicAdd(&vmom[2 * (size_t)gid], make_float4(S0, Sx, Sy, Sxx));
+            atomicAdd(reinterpret_cast<float2*>(&vmom[2 * (size_t)gid + 1]), make_float2(Sxy, Syy));
             S0 = Sx = Sy = Sxx = Sxy = Syy = 0.f;
             do {
                 ++k;
             } while (s_excl[k + 1] == s_excl[k]);
             k1 = s_k1[k];
             k2 = s_k2[k];
-            k3 = s_k3[k];
+            gid = s_gid[k];
             rec_end = s_excl[k + 1];
             uf = 0.0f;
         }
     }
-    atomicAdd(&vmom[2 * (size_t)k3.y], make_float4(S0, Sx, Sy, Sxx));
-    atomicAdd(reinterpret_cast<float2*>(&vmom[2 * (size_t)k3.y + 1]), make_float2(Sxy, Syy));
+    atomicAdd(&vmom[2 * (size_t)gid], make_float4(S0, Sx, Sy, Sxx));
+    atomicAdd(reinterpret_cast<float2*>(&vmom[2 * (size_t)gid + 1]), make_float2(Sxy, Syy));
 }
 
 // ------------------------------------------------------------------ K6: projection backward
