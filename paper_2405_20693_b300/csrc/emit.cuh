@@ -150,10 +150,12 @@ __global__ void __launch_bounds__(256) k_emit_chunks(Op op, long long n_rec, con
 // One warp per key k: the scatter offset of (k, emit block b) = entries of
 // smaller keys + entries of key k in earlier blocks (hist rewritten in place),
 // the key's range [start, end) ([0, 0) when empty), its first work item and its
-// ceil(n / chunk) items; the last key's warp writes the item count.
+// max(1, ceil(n / chunk)) items (an empty key's one item writes its zero output),
+// a cleared chunk arrival counter; the last key's warp writes the item count.
 static __global__ void __launch_bounds__(256) k_fused_offsets(uint32_t* __restrict__ hist,
                                                               const uint32_t* __restrict__ key_totals, int nb,
                                                               int n_keys, uint32_t chunk, uint2* __restrict__ ranges,
+                                                              uint32_t* __restrict__ key_done,
                                                               uint32_t* __restrict__ item_off,
                                                               uint64_t* __restrict__ items,
                                                               unsigned long long items_cap,
@@ -165,7 +167,7 @@ static __global__ void __launch_bounds__(256) k_fused_offsets(uint32_t* __restri
     for (int q = lane; q < k; q += 32) {
         const uint32_t t = key_totals[q];
         base += t;
-        ibase += (t + chunk - 1) / chunk;
+        ibase += t ? (t + chunk - 1) / chunk : 1u;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -187,9 +189,10 @@ static __global__ void __launch_bounds__(256) k_fused_offsets(uint32_t* __restri
         running += __shfl_sync(0xffffffffu, x, 31);
     }
     const uint32_t total = key_totals[k];
-    const uint32_t nch = (total + chunk - 1) / chunk;
+    const uint32_t nch = total ? (total + chunk - 1) / chunk : 1u;
     if (lane == 0) {
         ranges[k] = total ? make_uint2(base, base + total) : make_uint2(0u, 0u);
+        key_done[k] = 0;
         item_off[k] = ibase;
         if (k == n_keys - 1) item_st->n_keys = (unsigned long long)ibase + nch;
     }
@@ -254,12 +257,16 @@ inline int list_sort_passes(long long n_slots) {
 
 // Emit, sort and range the lists of n_slots keys; returns the buffer (a or b)
 // holding the sorted entries and adds the kernel launches to *launches.  The
-// status block must have been cleared by the caller.
+// status block must have been cleared by the caller.  key_done (one chunk
+// arrival counter per key) must lie between the ranges and the item status
+// block, so that the general path's clear of that span zeroes it; the fused path
+// zeroes it and gives every empty key one work item, the general path gives
+// empty keys none (their outputs must be cleared by the caller).
 template <class Op>
 uint64_t* build_lists(const Op& op, long long n_rec, long long n_slots, unsigned long long* partials, WsStatus* st,
-                      uint64_t* a, uint64_t* b, uint32_t* scratch, long long cap, uint2* ranges, WsStatus* item_st,
-                      uint32_t* item_off, uint64_t* items, long long items_cap, int chunk, cudaStream_t s,
-                      int* launches) {
+                      uint64_t* a, uint64_t* b, uint32_t* scratch, long long cap, uint2* ranges, uint32_t* key_done,
+                      WsStatus* item_st, uint32_t* item_off, uint64_t* items, long long items_cap, int chunk,
+                      cudaStream_t s, int* launches) {
     const unsigned long long ucap = (unsigned long long)cap;
     if (fused_lists(n_slots)) {
         uint32_t* hist = scratch;
@@ -271,7 +278,8 @@ uint64_t* build_lists(const Op& op, long long n_rec, long long n_slots, unsigned
         prof_end(P_EMIT, s);
         prof_begin(P_SORT, s);
         k_fused_offsets<<<(nk + 7) / 8, 256, 0, s>>>(hist, totals, kFusedBlocks, nk, (uint32_t)chunk, ranges,
-                                                      item_off, items, (unsigned long long)items_cap, item_st);
+                                                      key_done, item_off, items, (unsigned long long)items_cap,
+                                                      item_st);
         k_fused_scatter<<<kFusedBlocks, 256, 0, s>>>(a, b, hist, partials, st, nk);
         prof_end(P_SORT, s);
         *launches += 4;

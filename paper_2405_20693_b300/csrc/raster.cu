@@ -14,8 +14,8 @@
 //                  lane owns 4 (2 for 8x8 tiles) horizontally adjacent pixels and
 //                  accumulates rho_hat 2^t [t >= Tq]; a warp owns an 8-row block
 //                  and skips records whose box misses it.  Tiles with several
-//                  chunks write per-chunk images that k_splat_reduce sums in
-//                  chunk order.
+//                  chunks write per-chunk images; the last chunk to finish sums
+//                  them in chunk order.  An empty tile's work item writes zeros.
 //   k_splat_bwd    one CTA per work item with dL/dI of the tile in shared
 //                  memory; the records' boxes are cut into units of kBwdUnit
 //                  pixels along a row and the units split evenly over the 128
@@ -316,7 +316,9 @@ __global__ void __launch_bounds__(FwdShape<TW, TH>::NT) k_splat_fwd(const float4
                                                                     const uint64_t* __restrict__ sorted,
                                                                     const uint64_t* __restrict__ items,
                                                                     const WsStatus* __restrict__ item_st,
-                                                                    float* __restrict__ partial, long long M,
+                                                                    float* __restrict__ partial,
+                                                                    const uint32_t* __restrict__ item_off,
+                                                                    uint32_t* __restrict__ key_done, long long M,
                                                                     int tiles_x, int tiles_per_view, int H, int W,
                                                                     float Tq, float* __restrict__ image,
                                                                     WsStatus* st) {
@@ -327,6 +329,7 @@ __global__ void __launch_bounds__(FwdShape<TW, TH>::NT) k_splat_fwd(const float4
     static_assert(TW % BW == 0 && TH % 8 == 0 && kChunk % NT == 0 && NT % 32 == 0, "tile shape");
     __shared__ float4 s_a[NT];
     __shared__ float4 s_b[NT];
+    __shared__ int s_last;
     const unsigned long long it = blockIdx.x;
     if (it >= item_st->n_keys) return;
     const uint64_t item = items[it];
@@ -379,45 +382,35 @@ __global__ void __launch_bounds__(FwdShape<TW, TH>::NT) k_splat_fwd(const float4
             }
         }
     }
-    if (nch == 1) {
-        if (py < H) {
-            float* row = image + ((size_t)v * H + py) * W;
-#pragma unroll
-            for (int k = 0; k < PX; ++k)
-                if (px + k < W) row[px + k] = acc[k];
-        }
-    } else {
-        float* p = partial + it * (size_t)(TW * TH) + ly * TW + lx;
-#pragma unroll
-        for (int k = 0; k < PX; ++k) p[k] = acc[k];
-    }
     if (COUNT) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
         if (lane == 0 && cnt) atomicAdd(&st->pairs, (unsigned long long)cnt);
     }
-}
-
-// Tiles whose list spans several chunks: sum the chunk images in chunk order.
-// Tiles with an empty list get zeros (no work item writes them).
-template <int TW, int TH>
-__global__ void __launch_bounds__(128) k_splat_reduce(const uint2* __restrict__ ranges,
-                                                      const uint32_t* __restrict__ item_off,
-                                                      const float* __restrict__ partial, int tiles_x,
-                                                      int tiles_per_view, int H, int W, float* __restrict__ image) {
-    const int tile = blockIdx.x;
-    const uint2 rg = ranges[tile];
-    const uint32_t nch = (rg.y - rg.x + kChunk - 1) / kChunk;
-    if (nch == 1) return;
-    const int v = tile / tiles_per_view;
-    const int lt = tile - v * tiles_per_view;
-    const int ty = lt / tiles_x, tx = lt - ty * tiles_x;
-    const float* base = partial + (nch ? (size_t)item_off[tile] * (TW * TH) : 0);
-    for (int p = threadIdx.x; p < TW * TH; p += 128) {
-        float s = 0.0f;
-        for (uint32_t c = 0; c < nch; ++c) s += base[(size_t)c * (TW * TH) + p];
-        const int gy = ty * TH + p / TW, gx = tx * TW + p % TW;
-        if (gy < H && gx < W) image[((size_t)v * H + gy) * W + gx] = s;
+    if (nch > 1) {
+        // several chunks: store this chunk's image; the last chunk to finish sums
+        // the tile's chunk images in chunk order
+        float* p = partial + it * (size_t)(TW * TH) + ly * TW + lx;
+#pragma unroll
+        for (int k = 0; k < PX; ++k) p[k] = acc[k];
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) s_last = atomicAdd(&key_done[tile], 1u) == nch - 1;
+        __syncthreads();
+        if (!s_last) return;
+        __threadfence();
+        const float* q = partial + (size_t)item_off[tile] * (TW * TH) + ly * TW + lx;
+#pragma unroll
+        for (int k = 0; k < PX; ++k) acc[k] = 0.0f;
+        for (uint32_t c = 0; c < nch; ++c)
+#pragma unroll
+            for (int k = 0; k < PX; ++k) acc[k] += __ldcg(q + (size_t)c * (TW * TH) + k);
+    }
+    if (py < H) {  // one chunk (or none: an empty tile's item writes zeros), or the sum
+        float* row = image + ((size_t)v * H + py) * W;
+#pragma unroll
+        for (int k = 0; k < PX; ++k)
+            if (px + k < W) row[px + k] = acc[k];
     }
 }
 
@@ -745,7 +738,7 @@ __global__ void __launch_bounds__(128) k_project_bwd(Params G, const float* __re
 // ------------------------------------------------------------------ host side
 
 struct RasterLayout {
-    size_t status, rec, rect, partials, ranges, mom, scratch, item_status, item_off, fixed;
+    size_t status, rec, rect, partials, ranges, key_done, mom, scratch, item_status, item_off, fixed;
     int tiles_x, tiles_y, tiles_per_view;
     long long n_tiles, n_rec;
 };
@@ -783,7 +776,8 @@ RasterLayout raster_layout(int64_t M, int32_t V, const r2g_camera* cam, const r2
     L.rect = lay.take(8 * (size_t)L.n_rec);
     L.partials = lay.take(8 * (size_t)kScanBlocks);
     L.ranges = lay.take(8 * (size_t)L.n_tiles);
-    L.item_status = lay.take(sizeof(WsStatus));  // directly after the ranges (cleared together)
+    L.key_done = lay.take(4 * (size_t)L.n_tiles);  // chunk arrival counters of the forward
+    L.item_status = lay.take(sizeof(WsStatus));     // ranges .. item status are cleared together
     L.mom = lay.take(32 * (size_t)L.n_rec);
     L.scratch = lay.take(sort_scratch_bytes());
     L.item_off = lay.take(4 * (size_t)L.n_tiles);
@@ -846,17 +840,15 @@ struct FwdArgs {
     const WsStatus* item_st;
     float* partial;
     const uint32_t* item_off;
+    uint32_t* key_done;
 };
 
 template <int TW, int TH, bool COUNT>
 void fwd_shape(const FwdArgs& f, long long M, const RasterLayout& L, long long icap, int H, int W, float Tq,
                float* image, WsStatus* st, cudaStream_t s) {
-    k_splat_fwd<TW, TH, COUNT><<<(unsigned)icap, FwdShape<TW, TH>::NT, 0, s>>>(f.rec, f.ranges, f.sorted, f.items,
-                                                                                f.item_st,
-                                                                       f.partial, M, L.tiles_x, L.tiles_per_view, H,
-                                                                       W, Tq, image, st);
-    k_splat_reduce<TW, TH><<<(unsigned)L.n_tiles, 128, 0, s>>>(f.ranges, f.item_off, f.partial, L.tiles_x,
-                                                                 L.tiles_per_view, H, W, image);
+    k_splat_fwd<TW, TH, COUNT><<<(unsigned)icap, FwdShape<TW, TH>::NT, 0, s>>>(
+        f.rec, f.ranges, f.sorted, f.items, f.item_st, f.partial, f.item_off, f.key_done, M, L.tiles_x,
+        L.tiles_per_view, H, W, Tq, image, st);
 }
 
 template <bool COUNT>
@@ -946,9 +938,12 @@ r2g_status r2g::rasterize_impl(int64_t M, const float* mean, const float* scale,
     uint64_t* b = reinterpret_cast<uint64_t*>(base + T.b);
     WsStatus* item_st = reinterpret_cast<WsStatus*>(base + L.item_status);
     uint32_t* item_off = reinterpret_cast<uint32_t*>(base + L.item_off);
+    uint32_t* key_done = reinterpret_cast<uint32_t*>(base + L.key_done);
     uint64_t* items = reinterpret_cast<uint64_t*>(base + T.items);
     float* partial = reinterpret_cast<float*>(base + T.partial);
     cudaMemsetAsync(st, 0, sizeof(WsStatus), stream);
+    // the general list path gives empty tiles no work item: their pixels stay zero
+    if (!fused_lists(L.n_tiles)) cudaMemsetAsync(image, 0, sizeof(float) * (size_t)V * cam->H * cam->W, stream);
     Params G{mean, scale, quat, rho};
     const CamF cf = camf(cam);
     prof_begin(P_PROJECT, stream);
@@ -958,17 +953,17 @@ r2g_status r2g::rasterize_impl(int64_t M, const float* mean, const float* scale,
     prof_end(P_PROJECT, stream);
     TileOp op{rect, M, L.tiles_x, L.tiles_per_view};
     int launches = 0;
-    uint64_t* sorted = build_lists(op, L.n_rec, L.n_tiles, partials, st, a, b, scratch, cap, ranges, item_st,
-                                   item_off, items, T.icap, kChunk, stream, &launches);
+    uint64_t* sorted = build_lists(op, L.n_rec, L.n_tiles, partials, st, a, b, scratch, cap, ranges, key_done,
+                                   item_st, item_off, items, T.icap, kChunk, stream, &launches);
     const float Tq = -0.5f * kLog2e * opts->Q;
     prof_begin(P_SPLAT_FWD, stream);
-    const FwdArgs fa{rec, ranges, sorted, items, item_st, partial, item_off};
+    const FwdArgs fa{rec, ranges, sorted, items, item_st, partial, item_off, key_done};
     if (opts->count_pairs)
         launch_fwd<true>(opts->tile_w, opts->tile_h, fa, M, L, T.icap, cam->H, cam->W, Tq, image, st, stream);
     else
         launch_fwd<false>(opts->tile_w, opts->tile_h, fa, M, L, T.icap, cam->H, cam->W, Tq, image, st, stream);
     prof_end(P_SPLAT_FWD, stream);
-    note_launches(1 + launches + 2);
+    note_launches(1 + launches + 1);
     return check_launch("r2g_rasterize");
 }
 

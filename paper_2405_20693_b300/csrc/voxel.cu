@@ -9,8 +9,9 @@
 //   k_vox_fwd      one CTA (128 threads) per work item (a brick's list cut into
 //                  chunks of 32 records); records staged in shared memory; each
 //                  thread owns a run of 4 voxels along x; a warp (two z-slices)
-//                  skips records whose z span misses it; multi-chunk bricks are
-//                  summed in chunk order by k_vox_reduce.
+//                  skips records whose z span misses it; in a multi-chunk brick
+//                  the last chunk to finish sums the chunk volumes in chunk
+//                  order.  An empty brick's work item writes zeros.
 //   k_vox_bwd      one CTA per group of 16 consecutive sorted entries; the
 //                  group's (record, voxel) pairs split evenly over its 128 lanes;
 //                  ten moments per record in registers, three vector atomics.
@@ -207,11 +208,14 @@ __global__ void __launch_bounds__(kVoxThreads) k_vox_fwd(const float4* __restric
                                                          const uint64_t* __restrict__ sorted,
                                                          const uint64_t* __restrict__ items,
                                                          const WsStatus* __restrict__ item_st,
-                                                         float* __restrict__ partial, long long M,
+                                                         float* __restrict__ partial,
+                                                         const uint32_t* __restrict__ item_off,
+                                                         uint32_t* __restrict__ key_done, long long M,
                                                          const __grid_constant__ Grids grids, float Tq,
                                                          float* __restrict__ vol, WsStatus* st) {
     static_assert(kVoxChunk <= kVoxThreads, "one staging batch per item");
     __shared__ float4 s_r[kVoxThreads][4];
+    __shared__ int s_last;
     const unsigned long long it = blockIdx.x;
     if (it >= item_st->n_keys) return;
     const uint64_t item = items[it];
@@ -263,59 +267,41 @@ __global__ void __launch_bounds__(kVoxThreads) k_vox_fwd(const float4* __restric
             }
         }
     }
-    if (nch == 1) {
-        if (y < gf.dims[1] && z < gf.dims[2]) {
-            float* row = vol + gf.vol_base + ((long long)z * gf.dims[1] + y) * gf.dims[0];
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                if (x0 + k < gf.dims[0]) row[x0 + k] = acc[k];
-        }
-    } else {
-        float4* p = reinterpret_cast<float4*>(partial + it * (size_t)(kB * kB * kB)) + t;
-        *p = make_float4(acc[0], acc[1], acc[2], acc[3]);
-    }
     if (COUNT) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
         if ((t & 31) == 0 && cnt) atomicAdd(&st->pairs, (unsigned long long)cnt);
     }
-}
-
-// Bricks whose list spans several chunks: sum the chunk volumes in chunk order.
-// Bricks with an empty list get zeros (no work item writes them).
-__global__ void __launch_bounds__(kVoxThreads) k_vox_reduce(const uint2* __restrict__ ranges,
-                                                            const uint32_t* __restrict__ item_off,
-                                                            const float* __restrict__ partial,
-                                                            const __grid_constant__ Grids grids,
-                                                            float* __restrict__ vol) {
-    const long long brick = blockIdx.x;
-    const uint2 rg = ranges[brick];
-    const uint32_t nch = (rg.y - rg.x + kVoxChunk - 1) / kVoxChunk;
-    if (nch == 1) return;
-    const int g = grid_of_brick(grids, brick);
-    const GridF& gf = grids.g[g];
-    const long long lb = brick - gf.brick_base;
-    const int bx = (int)(lb % gf.nb[0]);
-    const int by = (int)((lb / gf.nb[0]) % gf.nb[1]);
-    const int bz = (int)(lb / ((long long)gf.nb[0] * gf.nb[1]));
-    const int t = threadIdx.x;
-    const int x0 = bx * kB + (t & 1) * 4, y = by * kB + ((t >> 1) & 7), z = bz * kB + (t >> 4);
-    const float4* base =
-        reinterpret_cast<const float4*>(partial + (nch ? (size_t)item_off[brick] * (kB * kB * kB) : 0)) + t;
-    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (uint32_t c = 0; c < nch; ++c) {
-        const float4 p = base[(size_t)c * (kB * kB * kB / 4)];
-        s.x += p.x;
-        s.y += p.y;
-        s.z += p.z;
-        s.w += p.w;
+    if (nch > 1) {
+        // several chunks: store this chunk's volume; the last chunk to finish sums
+        // the brick's chunk volumes in chunk order
+        float4* p = reinterpret_cast<float4*>(partial + it * (size_t)(kB * kB * kB)) + t;
+        *p = make_float4(acc[0], acc[1], acc[2], acc[3]);
+        __threadfence();
+        __syncthreads();
+        if (t == 0) s_last = atomicAdd(&key_done[brick], 1u) == nch - 1;
+        __syncthreads();
+        if (!s_last) return;
+        __threadfence();
+        const float4* q = reinterpret_cast<const float4*>(partial + (size_t)item_off[brick] * (kB * kB * kB)) + t;
+        float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (uint32_t c = 0; c < nch; ++c) {
+            const float4 u = __ldcg(q + (size_t)c * (kB * kB * kB / 4));
+            sum.x += u.x;
+            sum.y += u.y;
+            sum.z += u.z;
+            sum.w += u.w;
+        }
+        acc[0] = sum.x;
+        acc[1] = sum.y;
+        acc[2] = sum.z;
+        acc[3] = sum.w;
     }
-    if (y < gf.dims[1] && z < gf.dims[2]) {
+    if (y < gf.dims[1] && z < gf.dims[2]) {  // one chunk (or none: zeros), or the sum
         float* row = vol + gf.vol_base + ((long long)z * gf.dims[1] + y) * gf.dims[0];
-        const float a[4] = {s.x, s.y, s.z, s.w};
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-            if (x0 + k < gf.dims[0]) row[x0 + k] = a[k];
+            if (x0 + k < gf.dims[0]) row[x0 + k] = acc[k];
     }
 }
 
@@ -576,7 +562,7 @@ __global__ void __launch_bounds__(128) k_vox_chain(Params G, const __grid_consta
 // ------------------------------------------------------------------ host side
 
 struct VoxLayout {
-    size_t status, rec, rect, partials, ranges, mom, scratch, item_status, item_off, fixed;
+    size_t status, rec, rect, partials, ranges, key_done, mom, scratch, item_status, item_off, fixed;
     long long n_rec, n_bricks, n_vox;
 };
 
@@ -611,13 +597,16 @@ VoxLayout vox_layout(int64_t M, const Grids& grids) {
     VoxLayout L;
     L.n_rec = (long long)M * grids.G;
     L.n_bricks = grids.n_bricks;
+    const GridF& last = grids.g[grids.G - 1];
+    L.n_vox = last.vol_base + (long long)last.dims[0] * last.dims[1] * last.dims[2];
     Layout lay;
     L.status = lay.take(sizeof(WsStatus));
     L.rec = lay.take(64 * (size_t)L.n_rec);
     L.rect = lay.take(16 * (size_t)L.n_rec);
     L.partials = lay.take(8 * (size_t)kScanBlocks);
     L.ranges = lay.take(8 * (size_t)L.n_bricks);
-    L.item_status = lay.take(sizeof(WsStatus));  // directly after the ranges (cleared together)
+    L.key_done = lay.take(4 * (size_t)L.n_bricks);  // chunk arrival counters of the forward
+    L.item_status = lay.take(sizeof(WsStatus));      // ranges .. item status are cleared together
     L.mom = lay.take(48 * (size_t)L.n_rec);
     L.scratch = lay.take(sort_scratch_bytes());
     L.item_off = lay.take(4 * (size_t)L.n_bricks);
@@ -707,9 +696,12 @@ r2g_status voxelize_impl(int64_t M, const float* mean, const float* scale, const
     uint64_t* b = reinterpret_cast<uint64_t*>(base + T.b);
     WsStatus* item_st = reinterpret_cast<WsStatus*>(base + L.item_status);
     uint32_t* item_off = reinterpret_cast<uint32_t*>(base + L.item_off);
+    uint32_t* key_done = reinterpret_cast<uint32_t*>(base + L.key_done);
     uint64_t* items = reinterpret_cast<uint64_t*>(base + T.items);
     float* partial = reinterpret_cast<float*>(base + T.partial);
     cudaMemsetAsync(st, 0, sizeof(WsStatus), stream);
+    // the general list path gives empty bricks no work item: their voxels stay zero
+    if (!fused_lists(L.n_bricks)) cudaMemsetAsync(vol, 0, sizeof(float) * (size_t)L.n_vox, stream);
     Params P{mean, scale, quat, rho};
     prof_begin(P_VOX_PROJECT, stream);
     k_vox_project<<<(unsigned)((L.n_rec + 255) / 256), 256, 0, stream>>>(P, gr, origin_dev, Q3, M, rec, rect);
@@ -723,18 +715,17 @@ r2g_status voxelize_impl(int64_t M, const float* mean, const float* scale, const
         op.nby[g] = gr.g[g].nb[1];
     }
     int launches = 0;
-    uint64_t* sorted = build_lists(op, L.n_rec, L.n_bricks, partials, st, a, b, scratch, cap, ranges, item_st,
-                                   item_off, items, T.icap, kVoxChunk, stream, &launches);
+    uint64_t* sorted = build_lists(op, L.n_rec, L.n_bricks, partials, st, a, b, scratch, cap, ranges, key_done,
+                                   item_st, item_off, items, T.icap, kVoxChunk, stream, &launches);
     const float Tq = -0.5f * kLog2e * Q3;
-    note_launches(1 + launches + 2);
+    note_launches(1 + launches + 1);
     prof_begin(P_VOX_FWD, stream);
     if (count)
-        k_vox_fwd<true><<<(unsigned)T.icap, kVoxThreads, 0, stream>>>(rec, ranges, sorted, items, item_st, partial, M,
-                                                                       gr, Tq, vol, st);
+        k_vox_fwd<true><<<(unsigned)T.icap, kVoxThreads, 0, stream>>>(rec, ranges, sorted, items, item_st, partial,
+                                                                       item_off, key_done, M, gr, Tq, vol, st);
     else
         k_vox_fwd<false><<<(unsigned)T.icap, kVoxThreads, 0, stream>>>(rec, ranges, sorted, items, item_st, partial,
-                                                                        M, gr, Tq, vol, st);
-    k_vox_reduce<<<(unsigned)L.n_bricks, kVoxThreads, 0, stream>>>(ranges, item_off, partial, gr, vol);
+                                                                        item_off, key_done, M, gr, Tq, vol, st);
     prof_end(P_VOX_FWD, stream);
     return check_launch("r2g_voxelize");
 }
