@@ -241,7 +241,7 @@ r2g_status r2g_tv3d_noalloc(int32_t G, int32_t D, const float* vol, float lambda
  * rasterizer needs). */
 typedef struct {
     float lr0[4];        /* mean, scale, quat, rho: 2e-4, 5e-3, 1e-3, 1e-2 in the paper */
-    float final_factor;  /* 0.1 */
+    float final_factor;  /* 0.1; must be > 0 (R2G_E_INVAL otherwise) */
     int32_t total_iters; /* 30000 */
     float beta1, beta2, eps;
 } r2g_adam_opts;
@@ -266,7 +266,10 @@ r2g_status r2g_poll(const void* ws, size_t ws_bytes, r2g_stream stream, int64_t*
  * captured once in a CUDA graph and replayed each round after rewriting the
  * entries.  Workspaces are sized for M Gaussians x 1 view (raster), 1 grid of D^3
  * (voxel), 1 x H x W (loss) and 1 x D (TV); list overflow is reported in the
- * raster/voxel workspace status (r2g_poll). */
+ * raster/voxel workspace status (r2g_poll).  The TV branch runs on a side stream
+ * forked from `stream` and joined back before the gradients are summed; every
+ * `stream` gets its own side stream, created by its first call (so make that
+ * first call outside stream capture) and kept for the life of the process. */
 typedef struct {
     int32_t view;      /* index of the view (and measured projection) this iteration */
     int32_t it;        /* 0-based iteration for the learning-rate schedule and bias correction */

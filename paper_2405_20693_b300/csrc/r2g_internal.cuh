@@ -119,6 +119,13 @@ r2g_status rasterize_backward_impl(int64_t M, const float* mean, const float* sc
 r2g_status voxelize_impl(int64_t M, const float* mean, const float* scale, const float* quat, const float* rho,
                          int32_t G, const r2g_grid* grids, const float* origin_dev, float Q3, float* vol, void* ws,
                          size_t ws_bytes, cudaStream_t stream, bool count);
+// The voxel backward in two parts: the per-record moments (dvol -> moments, in the
+// workspace) and the chain rule (moments -> gradients, added to dmean .. drho).
+constexpr int kVoxBwdMoments = 1, kVoxBwdChain = 2;
+r2g_status voxelize_backward_impl(int64_t M, const float* mean, const float* scale, const float* quat,
+                                  const float* rho, int32_t G, const r2g_grid* grids, float Q3, const float* dvol,
+                                  float* dmean, float* dscale, float* dquat, float* drho, void* ws, size_t ws_bytes,
+                                  cudaStream_t stream, int parts);
 r2g_status projection_loss_impl(int32_t V, int32_t H, int32_t W, const float* render, const float* meas,
                                 const int* meas_sel, float lambda_ssim, float* loss, float* drender, void* ws,
                                 size_t ws_bytes, cudaStream_t stream);

@@ -3,9 +3,52 @@
 // so that a round over many scans can be captured once as a CUDA graph and
 // replayed: rasterize the selected view, L1 + D-SSIM against its measurement,
 // voxelize the TV patch at the selected origin, TV, both backward passes, Adam.
+//
+// The projection branch (rasterize, loss, raster backward) and the TV branch
+// (voxelize, TV, voxel moments) share nothing until their chain rules add into
+// the same gradient arrays, so the TV branch runs on a side stream forked from
+// the caller's stream and joined before the voxel chain rule; the two branches'
+// latency-bound kernels then overlap.  Each caller stream gets its own side
+// stream and event pair (created on first use, kept for the process), so calls
+// on different streams -- the branches of a batched round -- stay independent.
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "r2g_internal.cuh"
 
 using namespace r2g;
+
+namespace {
+
+struct SideStream {
+    cudaStream_t s;
+    cudaEvent_t fork, join;
+};
+
+std::mutex g_side_mu;
+std::map<std::pair<int, cudaStream_t>, SideStream> g_side;
+
+r2g_status side_stream_for(cudaStream_t caller, SideStream** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return fail(R2G_E_CUDA, "r2g_train_step: no current device");
+    std::lock_guard<std::mutex> lk(g_side_mu);
+    const auto key = std::make_pair(dev, caller);
+    auto it = g_side.find(key);
+    if (it == g_side.end()) {
+        SideStream sd{};
+        if (cudaStreamCreateWithFlags(&sd.s, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&sd.fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&sd.join, cudaEventDisableTiming) != cudaSuccess)
+            return fail(R2G_E_CUDA, "r2g_train_step: creating the side stream failed (%s)",
+                        cudaGetErrorString(cudaGetLastError()));
+        it = g_side.emplace(key, sd).first;
+    }
+    *out = &it->second;
+    return R2G_OK;
+}
+
+}  // namespace
 
 R2G_API r2g_status r2g_train_step(const r2g_job* job, const r2g_round_entry* entry, r2g_stream stream) {
     if (!job || !entry) return fail(R2G_E_INVAL, "r2g_train_step: NULL job or round entry");
@@ -31,22 +74,35 @@ R2G_API r2g_status r2g_train_step(const r2g_job* job, const r2g_round_entry* ent
         grid.voxel[k] = J.voxel;
         grid.dims[k] = J.D;
     }
-    r2g_status e;
-    if ((e = rasterize_impl(M, mean, scale, quat, rho, 1, J.views, view_sel, &J.cam, &J.ropts, J.image, J.raster_ws,
-                            J.raster_ws_bytes, stream)))
-        return e;
-    if ((e = projection_loss_impl(1, J.cam.H, J.cam.W, J.image, J.meas, view_sel, J.lambda_ssim, J.loss, J.dimage,
-                                  J.loss_ws, J.loss_ws_bytes, stream)))
-        return e;
-    if ((e = voxelize_impl(M, mean, scale, quat, rho, 1, &grid, entry->origin, J.Q3, J.vol, J.voxel_ws,
-                           J.voxel_ws_bytes, stream, false)))
-        return e;
-    if ((e = r2g_tv3d(1, J.D, J.vol, J.lambda_tv, J.loss + 1, J.dvol, J.tv_ws, J.tv_ws_bytes, stream))) return e;
-    if ((e = rasterize_backward_impl(M, mean, scale, quat, rho, 1, J.views, view_sel, &J.cam, &J.ropts, J.dimage,
-                                     dmean, dscale, dquat, drho, J.raster_ws, J.raster_ws_bytes, stream)))
-        return e;
-    if ((e = r2g_voxelize_backward(M, mean, scale, quat, rho, 1, &grid, J.Q3, J.dvol, dmean, dscale, dquat, drho,
-                                   J.voxel_ws, J.voxel_ws_bytes, stream)))
+    SideStream* side = nullptr;
+    r2g_status e = side_stream_for(stream, &side);
+    if (e) return e;
+    const cudaStream_t tv = side->s;
+    // fork: the TV branch starts after everything already queued on the caller's
+    // stream (the previous iteration's Adam step)
+    if (cudaEventRecord(side->fork, stream) != cudaSuccess || cudaStreamWaitEvent(tv, side->fork, 0) != cudaSuccess)
+        return fail(R2G_E_CUDA, "r2g_train_step: fork failed (%s)", cudaGetErrorString(cudaGetLastError()));
+    r2g_status e_tv = voxelize_impl(M, mean, scale, quat, rho, 1, &grid, entry->origin, J.Q3, J.vol, J.voxel_ws,
+                                    J.voxel_ws_bytes, tv, false);
+    if (!e_tv) e_tv = r2g_tv3d(1, J.D, J.vol, J.lambda_tv, J.loss + 1, J.dvol, J.tv_ws, J.tv_ws_bytes, tv);
+    if (!e_tv)
+        e_tv = voxelize_backward_impl(M, mean, scale, quat, rho, 1, &grid, J.Q3, J.dvol, dmean, dscale, dquat, drho,
+                                      J.voxel_ws, J.voxel_ws_bytes, tv, kVoxBwdMoments);
+    r2g_status e_px = rasterize_impl(M, mean, scale, quat, rho, 1, J.views, view_sel, &J.cam, &J.ropts, J.image,
+                                     J.raster_ws, J.raster_ws_bytes, stream);
+    if (!e_px)
+        e_px = projection_loss_impl(1, J.cam.H, J.cam.W, J.image, J.meas, view_sel, J.lambda_ssim, J.loss, J.dimage,
+                                    J.loss_ws, J.loss_ws_bytes, stream);
+    if (!e_px)
+        e_px = rasterize_backward_impl(M, mean, scale, quat, rho, 1, J.views, view_sel, &J.cam, &J.ropts, J.dimage,
+                                       dmean, dscale, dquat, drho, J.raster_ws, J.raster_ws_bytes, stream);
+    // join (also on error, so that no captured branch is left open)
+    if (cudaEventRecord(side->join, tv) != cudaSuccess || cudaStreamWaitEvent(stream, side->join, 0) != cudaSuccess)
+        return fail(R2G_E_CUDA, "r2g_train_step: join failed (%s)", cudaGetErrorString(cudaGetLastError()));
+    if (e_tv) return e_tv;
+    if (e_px) return e_px;
+    if ((e = voxelize_backward_impl(M, mean, scale, quat, rho, 1, &grid, J.Q3, J.dvol, dmean, dscale, dquat, drho,
+                                    J.voxel_ws, J.voxel_ws_bytes, stream, kVoxBwdChain)))
         return e;
     return adam_impl(M, J.raw, J.act, J.grad, J.adam_m, J.adam_v, 0, &entry->it, &J.adam, stream);
 }

@@ -744,10 +744,11 @@ R2G_API r2g_status r2g_voxelize_counted(int64_t M, const float* mean, const floa
 }
 
 
-R2G_API r2g_status r2g_voxelize_backward(int64_t M, const float* mean, const float* scale, const float* quat,
-                                         const float* rho, int32_t G, const r2g_grid* grids, float Q3,
-                                         const float* dvol, float* dmean, float* dscale, float* dquat, float* drho,
-                                         void* ws, size_t ws_bytes, r2g_stream stream) {
+namespace r2g {
+r2g_status voxelize_backward_impl(int64_t M, const float* mean, const float* scale, const float* quat,
+                                  const float* rho, int32_t G, const r2g_grid* grids, float Q3, const float* dvol,
+                                  float* dmean, float* dscale, float* dquat, float* drho, void* ws, size_t ws_bytes,
+                                  cudaStream_t stream, int parts) {
     r2g_status e = check_params(M, mean, scale, quat, rho);
     if (e) return e;
     Grids gr;
@@ -764,19 +765,33 @@ R2G_API r2g_status r2g_voxelize_backward(int64_t M, const float* mean, const flo
     float4* mom = reinterpret_cast<float4*>(base + L.mom);
     const uint64_t* sorted = vox_sorted(base, L, T);
     const WsStatus* st = reinterpret_cast<const WsStatus*>(base + L.status);
-    cudaMemsetAsync(mom, 0, 48 * (size_t)L.n_rec, stream);
-    const float Tq = -0.5f * kLog2e * Q3;
-    const long long groups = (cap + kVoxGroup - 1) / kVoxGroup;
-    prof_begin(P_VOX_BWD, stream);
-    k_vox_bwd<<<(unsigned)std::min<long long>(groups, 148 * 16), kVoxThreads, 0, stream>>>(rec, sorted, st, M, gr,
-                                                                                          Tq, dvol, mom);
-    prof_end(P_VOX_BWD, stream);
-    Params P{mean, scale, quat, rho};
-    prof_begin(P_VOX_CHAIN, stream);
-    k_vox_chain<<<(unsigned)((M + 127) / 128), 128, 0, stream>>>(P, gr, M, mom, dmean, dscale, dquat, drho);
-    prof_end(P_VOX_CHAIN, stream);
-    note_launches(2);
+    if (parts & kVoxBwdMoments) {
+        cudaMemsetAsync(mom, 0, 48 * (size_t)L.n_rec, stream);
+        const float Tq = -0.5f * kLog2e * Q3;
+        const long long groups = (cap + kVoxGroup - 1) / kVoxGroup;
+        prof_begin(P_VOX_BWD, stream);
+        k_vox_bwd<<<(unsigned)std::min<long long>(groups, 148 * 16), kVoxThreads, 0, stream>>>(rec, sorted, st, M,
+                                                                                              gr, Tq, dvol, mom);
+        prof_end(P_VOX_BWD, stream);
+        note_launches(1);
+    }
+    if (parts & kVoxBwdChain) {
+        Params P{mean, scale, quat, rho};
+        prof_begin(P_VOX_CHAIN, stream);
+        k_vox_chain<<<(unsigned)((M + 127) / 128), 128, 0, stream>>>(P, gr, M, mom, dmean, dscale, dquat, drho);
+        prof_end(P_VOX_CHAIN, stream);
+        note_launches(1);
+    }
     return check_launch("r2g_voxelize_backward");
+}
+}  // namespace r2g
+
+R2G_API r2g_status r2g_voxelize_backward(int64_t M, const float* mean, const float* scale, const float* quat,
+                                         const float* rho, int32_t G, const r2g_grid* grids, float Q3,
+                                         const float* dvol, float* dmean, float* dscale, float* dquat, float* drho,
+                                         void* ws, size_t ws_bytes, r2g_stream stream) {
+    return voxelize_backward_impl(M, mean, scale, quat, rho, G, grids, Q3, dvol, dmean, dscale, dquat, drho, ws,
+                                  ws_bytes, stream, kVoxBwdMoments | kVoxBwdChain);
 }
 
 R2G_API r2g_status r2g_voxel_lists(int64_t M, int32_t G, const r2g_grid* grids, const void* ws, size_t ws_bytes,
