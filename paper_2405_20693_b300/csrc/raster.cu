@@ -218,9 +218,18 @@ __global__ void __launch_bounds__(256) k_project(Params G, const float* __restri
                                                  const int* __restrict__ view_sel, CamF cam, float Q, int TW, int TH,
                                                  long long M, long long n_rec, float4* __restrict__ rec,
                                                  uint2* __restrict__ rect, float* __restrict__ proj_out,
-                                                 int* __restrict__ rect_out) {
+                                                 int* __restrict__ rect_out, WsStatus* __restrict__ st_clear,
+                                                 float4* __restrict__ mom_clear) {
+    // st_clear / mom_clear (optional): this call's status block and every record's
+    // backward moment slot start at zero
+    if (st_clear && blockIdx.x == 0 && threadIdx.x < sizeof(WsStatus) / 8)
+        reinterpret_cast<unsigned long long*>(st_clear)[threadIdx.x] = 0ull;
     const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_rec) return;
+    if (mom_clear) {
+        mom_clear[2 * r] = make_float4(0.f, 0.f, 0.f, 0.f);
+        mom_clear[2 * r + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     const long long v = r / M, i = r - v * M;
     const float* view = views + 12 * (view_sel ? (long long)view_sel[v] : v);
     float p[3], s[3], q[4];
@@ -603,7 +612,7 @@ __device__ __forceinline__ void quat_grad(const float qn[4], float qnorm, const 
 __global__ void __launch_bounds__(128) k_project_bwd(Params G, const float* __restrict__ views,
                                                      const int* __restrict__ view_sel, CamF cam, float Q,
                                                      long long M, int V, const float4* __restrict__ rec,
-                                                     const float4* __restrict__ mom, float* __restrict__ dmean,
+                                                     float4* __restrict__ mom, float* __restrict__ dmean,
                                                      float* __restrict__ dscale, float* __restrict__ dquat,
                                                      float* __restrict__ drho) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -619,6 +628,8 @@ __global__ void __launch_bounds__(128) k_project_bwd(Params G, const float* __re
         const float4 m0 = mom[2 * r];
         const float4 m1 = mom[2 * r + 1];
         if (m0.x == 0.f && m0.y == 0.f && m0.z == 0.f && m0.w == 0.f && m1.x == 0.f && m1.y == 0.f) continue;
+        mom[2 * r] = make_float4(0.f, 0.f, 0.f, 0.f);  // consumed: the next backward starts at zero
+        mom[2 * r + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
         const float rhohat = rec[2 * r + 1].y;
         const float* view = views + 12 * (view_sel ? view_sel[v] : v);
         project_stated(p, s, q, view, cam, P);
@@ -908,7 +919,8 @@ R2G_API r2g_status r2g_project(int64_t M, const float* mean, const float* scale,
     const long long n = (long long)M * V;
     Params G{mean, scale, quat, rho};
     k_project<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(G, views, nullptr, camf(cam), opts->Q, opts->tile_w,
-                                                                opts->tile_h, M, n, nullptr, nullptr, proj, rect);
+                                                                opts->tile_h, M, n, nullptr, nullptr, proj, rect,
+                                                                nullptr, nullptr);
     note_launches(1);
     return check_launch("r2g_project");
 }
@@ -941,15 +953,14 @@ r2g_status r2g::rasterize_impl(int64_t M, const float* mean, const float* scale,
     uint32_t* key_done = reinterpret_cast<uint32_t*>(base + L.key_done);
     uint64_t* items = reinterpret_cast<uint64_t*>(base + T.items);
     float* partial = reinterpret_cast<float*>(base + T.partial);
-    cudaMemsetAsync(st, 0, sizeof(WsStatus), stream);
     // the general list path gives empty tiles no work item: their pixels stay zero
     if (!fused_lists(L.n_tiles)) cudaMemsetAsync(image, 0, sizeof(float) * (size_t)V * cam->H * cam->W, stream);
     Params G{mean, scale, quat, rho};
     const CamF cf = camf(cam);
     prof_begin(P_PROJECT, stream);
-    k_project<<<(unsigned)((L.n_rec + 255) / 256), 256, 0, stream>>>(G, views, view_sel, cf, opts->Q,
-                                                                      opts->tile_w, opts->tile_h, M, L.n_rec, rec,
-                                                                      rect, nullptr, nullptr);
+    k_project<<<(unsigned)((L.n_rec + 255) / 256), 256, 0, stream>>>(
+        G, views, view_sel, cf, opts->Q, opts->tile_w, opts->tile_h, M, L.n_rec, rec, rect, nullptr, nullptr, st,
+        reinterpret_cast<float4*>(base + L.mom));
     prof_end(P_PROJECT, stream);
     TileOp op{rect, M, L.tiles_x, L.tiles_per_view};
     int launches = 0;
@@ -997,7 +1008,6 @@ r2g_status r2g::rasterize_backward_impl(int64_t M, const float* mean, const floa
     const uint64_t* sorted = sorted_buffer(base, L, T);
     const uint64_t* items = reinterpret_cast<const uint64_t*>(base + T.items);
     const WsStatus* item_st = reinterpret_cast<const WsStatus*>(base + L.item_status);
-    cudaMemsetAsync(mom, 0, 32 * (size_t)L.n_rec, stream);
     const float Tq = -0.5f * kLog2e * opts->Q;
     prof_begin(P_SPLAT_BWD, stream);
     launch_bwd(opts->tile_w, opts->tile_h, rec, ranges, sorted, items, item_st, T.icap, M, L, cam->H, cam->W, Tq,

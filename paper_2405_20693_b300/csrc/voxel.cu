@@ -112,9 +112,15 @@ __device__ __forceinline__ void precision(const float R[3][3], const float s[3],
 // origin_dev (optional, device): grid g's origin is origin_dev[3g .. 3g+2].
 __global__ void __launch_bounds__(256) k_vox_project(Params G, const __grid_constant__ Grids grids,
                                                      const float* __restrict__ origin_dev, float Q3, long long M,
-                                                     float4* __restrict__ rec, uint4* __restrict__ rect) {
+                                                     float4* __restrict__ rec, uint4* __restrict__ rect,
+                                                     WsStatus* __restrict__ st_clear, float4* __restrict__ mom_clear) {
+    // this call's status block and every record's backward moment slot start at zero
+    if (blockIdx.x == 0 && threadIdx.x < sizeof(WsStatus) / 8)
+        reinterpret_cast<unsigned long long*>(st_clear)[threadIdx.x] = 0ull;
     const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= M * grids.G) return;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) mom_clear[3 * r + k] = make_float4(0.f, 0.f, 0.f, 0.f);
     const int g = (int)(r / M);
     const long long i = r - (long long)g * M;
     const GridF& gf = grids.g[g];
@@ -495,7 +501,7 @@ __device__ __forceinline__ void quat_grad(const float qn[4], float qnorm, const 
 }
 
 __global__ void __launch_bounds__(128) k_vox_chain(Params G, const __grid_constant__ Grids grids, long long M,
-                                                   const float4* __restrict__ mom, float* __restrict__ dmean,
+                                                   float4* __restrict__ mom, float* __restrict__ dmean,
                                                    float* __restrict__ dscale, float* __restrict__ dquat,
                                                    float* __restrict__ drho) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -514,6 +520,8 @@ __global__ void __launch_bounds__(128) k_vox_chain(Params G, const __grid_consta
         if (m0.x == 0.f && m0.y == 0.f && m0.z == 0.f && m0.w == 0.f && m1.x == 0.f && m1.y == 0.f && m1.z == 0.f &&
             m1.w == 0.f && m2.x == 0.f && m2.y == 0.f)
             continue;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) mom[3 * r + k] = make_float4(0.f, 0.f, 0.f, 0.f);  // consumed
         any = true;
         const GridF& gf = grids.g[g];
         const float v[3] = {gf.v[0], gf.v[1], gf.v[2]};
@@ -699,12 +707,12 @@ r2g_status voxelize_impl(int64_t M, const float* mean, const float* scale, const
     uint32_t* key_done = reinterpret_cast<uint32_t*>(base + L.key_done);
     uint64_t* items = reinterpret_cast<uint64_t*>(base + T.items);
     float* partial = reinterpret_cast<float*>(base + T.partial);
-    cudaMemsetAsync(st, 0, sizeof(WsStatus), stream);
     // the general list path gives empty bricks no work item: their voxels stay zero
     if (!fused_lists(L.n_bricks)) cudaMemsetAsync(vol, 0, sizeof(float) * (size_t)L.n_vox, stream);
     Params P{mean, scale, quat, rho};
     prof_begin(P_VOX_PROJECT, stream);
-    k_vox_project<<<(unsigned)((L.n_rec + 255) / 256), 256, 0, stream>>>(P, gr, origin_dev, Q3, M, rec, rect);
+    k_vox_project<<<(unsigned)((L.n_rec + 255) / 256), 256, 0, stream>>>(
+        P, gr, origin_dev, Q3, M, rec, rect, st, reinterpret_cast<float4*>(base + L.mom));
     prof_end(P_VOX_PROJECT, stream);
     BrickEmitOp op;
     op.rect = rect;
@@ -766,7 +774,6 @@ r2g_status voxelize_backward_impl(int64_t M, const float* mean, const float* sca
     const uint64_t* sorted = vox_sorted(base, L, T);
     const WsStatus* st = reinterpret_cast<const WsStatus*>(base + L.status);
     if (parts & kVoxBwdMoments) {
-        cudaMemsetAsync(mom, 0, 48 * (size_t)L.n_rec, stream);
         const float Tq = -0.5f * kLog2e * Q3;
         const long long groups = (cap + kVoxGroup - 1) / kVoxGroup;
         prof_begin(P_VOX_BWD, stream);
