@@ -1,19 +1,16 @@
 // loss.cu -- the training losses of Eq. 8 on sm_103a, forward and gradient fused.
 //
 // Projection loss L1 + lambda_ssim (1 - SSIM) over [V][H][W]:
-//   k_ssim_maps   one CTA per 32x32 output tile of one view: the tile plus a
-//                 5-pixel halo of render x and measurement y is staged in shared
-//                 memory (zeros outside the image), the 11-tap Gaussian window is
-//                 applied separably to x, y, xx, yy, xy, and each pixel's SSIM
-//                 term S and its partial derivatives with respect to the local
-//                 moments (dS/dmu_x, dS/dE_xx, dS/dE_xy) are formed.  Writes the
-//                 three derivative maps and per-CTA partial sums of S and |x - y|.
-//   k_ssim_grad   one CTA per tile again: the derivative maps plus halo are
-//                 filtered with the same window (the adjoint of a zero-padded
-//                 symmetric filter is itself) and combined with x, y and the L1
-//                 sign into d loss / d render.
-//                 Its block 0 also sums the per-tile partials of k_ssim_maps in a
-//                 fixed order into the loss (deterministic).
+//   k_ssim        one CTA per 32x32 output tile of one view: render x and
+//                 measurement y staged with a 10-pixel halo (zeros outside the
+//                 image), the 11-tap Gaussian window applied separably to x, y,
+//                 xx, yy, xy, each pixel's SSIM term S and its derivatives with
+//                 respect to the local moments (dS/dmu_x, dS/dE_xx, dS/dE_xy) on
+//                 the tile plus a 5-pixel halo, those maps filtered again with
+//                 the window (the adjoint of a zero-padded symmetric filter is
+//                 itself) and combined with x, y and the L1 sign into d loss /
+//                 d render; the last CTA to finish sums the per-tile partials
+//                 in a fixed order into the loss (deterministic).
 //   k_finalize    (TV) one CTA sums the per-CTA partials in a fixed order.
 // 3D TV: k_tv3d forms each voxel's gradient from its six neighbours and a CTA
 // partial of the loss; k_finalize sums the partials.
@@ -26,7 +23,9 @@ namespace {
 
 constexpr int kT = 32;            // output tile edge
 constexpr int kR = 5;             // window radius
-constexpr int kE = kT + 2 * kR;   // staged edge
+constexpr int kM = kT + 2 * kR;   // edge of the SSIM-derivative region (tile + halo)
+constexpr int kS = kT + 4 * kR;   // edge of the staged input region
+constexpr int kSsimThreads = 512;
 
 // Normalised 1D Gaussian window (sigma 1.5), passed by value to each launch.
 struct Win {
@@ -36,176 +35,181 @@ struct Win {
 constexpr float kC1 = 1e-4f;      // (0.01 L)^2, L = 1
 constexpr float kC2 = 9e-4f;      // (0.03 L)^2
 
-// meas_sel (optional, device): view v of the batch is compared with measurement
-// meas_sel[v] of y.
-__global__ void __launch_bounds__(256) k_ssim_maps(const float* __restrict__ x, const float* __restrict__ y,
-                                                   const int* __restrict__ meas_sel, int H,
-                                                   int W, int tiles_x, int tiles_per_view, const Win win,
-                                                   float* __restrict__ dmu,
-                                                   float* __restrict__ dxx, float* __restrict__ dxy,
-                                                   float* __restrict__ partials) {
-    __shared__ float sx[kE][kE + 1], sy[kE][kE + 1];
-    __shared__ float h[5][kE][kT + 1];
-    __shared__ float red[2][8];
+struct SsimSmem {
+    float sx[kS][kS + 1], sy[kS][kS + 1];  // render x and measurement y, zeros outside the image
+    union {
+        float h[5][kS][kM + 1];            // horizontally filtered x, y, xx, yy, xy
+        float g[3][kM][kT + 1];            // horizontally filtered derivative maps
+    } u;
+    float d[3][kM][kM + 1];                // dS/dmu_x, dS/dE_xx, dS/dE_xy (zero outside the image)
+    double red[2][kSsimThreads / 32];
+    int last;
+};
+
+// One CTA per 32 x 32 output tile of one view.  x and y are staged with a
+// 10-pixel halo; the windowed moments and each pixel's SSIM term S and its
+// derivatives with respect to mu_x, E_xx and E_xy are formed on the tile plus a
+// 5-pixel halo (zero outside the image, whose pixels the mean leaves out); those
+// derivative maps are filtered again with the window (the adjoint of a
+// zero-padded symmetric filter is itself) and combined with x, y and the L1 sign
+// into d loss / d render.  Per-tile sums of S and |x - y| go to `partials`; the
+// last CTA to finish (arrival counter cleared before the launch) sums them in
+// tile order into the loss.  meas_sel (optional, device): view v of the batch is
+// compared with measurement meas_sel[v] of y.
+__global__ void __launch_bounds__(kSsimThreads) k_ssim(const float* __restrict__ x, const float* __restrict__ y,
+                                                       const int* __restrict__ meas_sel, int H, int W, int tiles_x,
+                                                       int tiles_per_view, int n_tiles, const Win win,
+                                                       float l1_scale, float ssim_scale, float* __restrict__ grad,
+                                                       float* __restrict__ partials, unsigned int* __restrict__ arrive,
+                                                       float lam, double inv_n, float* __restrict__ loss) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SsimSmem& S = *reinterpret_cast<SsimSmem*>(smem_raw);
+    const int tid = threadIdx.x;
     const int tile = blockIdx.x;
     const int v = tile / tiles_per_view, lt = tile - v * tiles_per_view;
     const int ty = lt / tiles_x, tx = lt - ty * tiles_x;
-    const int Y0 = ty * kT - kR, X0 = tx * kT - kR;
+    const int TY = ty * kT, TX = tx * kT;
     const float* xv = x + (size_t)v * H * W;
     const float* yv = y + (size_t)(meas_sel ? meas_sel[v] : v) * H * W;
-    for (int k = threadIdx.x; k < kE * kE; k += 256) {
-        const int r = k / kE, c = k - r * kE;
-        const int gy = Y0 + r, gx = X0 + c;
+    for (int k = tid; k < kS * kS; k += kSsimThreads) {
+        const int r = k / kS, c = k - r * kS;
+        const int gy = TY - 2 * kR + r, gx = TX - 2 * kR + c;
         const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
-        sx[r][c] = in ? xv[(size_t)gy * W + gx] : 0.f;
-        sy[r][c] = in ? yv[(size_t)gy * W + gx] : 0.f;
+        S.sx[r][c] = in ? xv[(size_t)gy * W + gx] : 0.f;
+        S.sy[r][c] = in ? yv[(size_t)gy * W + gx] : 0.f;
     }
     __syncthreads();
-    // horizontal pass: rows 0..kE-1, output columns 0..kT-1
-    for (int k = threadIdx.x; k < kE * kT; k += 256) {
-        const int r = k / kT, c = k - r * kT;
+    for (int k = tid; k < kS * kM; k += kSsimThreads) {
+        const int r = k / kM, c = k - r * kM;
         float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f;
 #pragma unroll
         for (int j = 0; j < 11; ++j) {
             const float w = win.w[j];
-            const float xa = sx[r][c + j], ya = sy[r][c + j];
+            const float xa = S.sx[r][c + j], ya = S.sy[r][c + j];
             a0 = fmaf(w, xa, a0);
             a1 = fmaf(w, ya, a1);
             a2 = fmaf(w, xa * xa, a2);
             a3 = fmaf(w, ya * ya, a3);
             a4 = fmaf(w, xa * ya, a4);
         }
-        h[0][r][c] = a0;
-        h[1][r][c] = a1;
-        h[2][r][c] = a2;
-        h[3][r][c] = a3;
-        h[4][r][c] = a4;
+        S.u.h[0][r][c] = a0;
+        S.u.h[1][r][c] = a1;
+        S.u.h[2][r][c] = a2;
+        S.u.h[3][r][c] = a3;
+        S.u.h[4][r][c] = a4;
     }
     __syncthreads();
     float sS = 0.f, sL1 = 0.f;
-    for (int k = threadIdx.x; k < kT * kT; k += 256) {
-        const int r = k / kT, c = k - r * kT;
-        float m[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int k = tid; k < kM * kM; k += kSsimThreads) {
+        const int r = k / kM, c = k - r * kM;
+        const int gy = TY - kR + r, gx = TX - kR + c;
+        float dm = 0.f, dxx = 0.f, dxy = 0.f;
+        if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
+            float m[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-        for (int j = 0; j < 11; ++j) {
-            const float w = win.w[j];
+            for (int j = 0; j < 11; ++j) {
+                const float w = win.w[j];
 #pragma unroll
-            for (int q = 0; q < 5; ++q) m[q] = fmaf(w, h[q][r + j][c], m[q]);
-        }
-        const int gy = ty * kT + r, gx = tx * kT + c;
-        if (gy < H && gx < W) {
+                for (int q = 0; q < 5; ++q) m[q] = fmaf(w, S.u.h[q][r + j][c], m[q]);
+            }
             const float mx = m[0], my = m[1];
             const float sxx = m[2] - mx * mx, syy = m[3] - my * my, sxy = m[4] - mx * my;
             const float A1 = 2.f * mx * my + kC1, A2 = 2.f * sxy + kC2;
             const float B1 = mx * mx + my * my + kC1, B2 = sxx + syy + kC2;
             const float iB = 1.f / (B1 * B2);
-            const float S = A1 * A2 * iB;
-            const size_t o = ((size_t)v * H + gy) * W + gx;
-            dmu[o] = (2.f * my * (A2 - A1) - 2.f * mx * S * (B2 - B1)) * iB;
-            dxx[o] = -S / B2;
-            dxy[o] = 2.f * A1 * iB;
-            sS += S;
-            sL1 += fabsf(sx[r + kR][c + kR] - sy[r + kR][c + kR]);
+            const float Sv = A1 * A2 * iB;
+            dm = (2.f * my * (A2 - A1) - 2.f * mx * Sv * (B2 - B1)) * iB;
+            dxx = -Sv / B2;
+            dxy = 2.f * A1 * iB;
+            if (r >= kR && r < kR + kT && c >= kR && c < kR + kT) {  // this tile's own pixels
+                sS += Sv;
+                sL1 += fabsf(S.sx[r + kR][c + kR] - S.sy[r + kR][c + kR]);
+            }
         }
+        S.d[0][r][c] = dm;
+        S.d[1][r][c] = dxx;
+        S.d[2][r][c] = dxy;
+    }
+    __syncthreads();
+    for (int k = tid; k < kM * kT; k += kSsimThreads) {
+        const int r = k / kT, c = k - r * kT;
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+#pragma unroll
+        for (int j = 0; j < 11; ++j) {
+            const float w = win.w[j];
+            a0 = fmaf(w, S.d[0][r][c + j], a0);
+            a1 = fmaf(w, S.d[1][r][c + j], a1);
+            a2 = fmaf(w, S.d[2][r][c + j], a2);
+        }
+        S.u.g[0][r][c] = a0;
+        S.u.g[1][r][c] = a1;
+        S.u.g[2][r][c] = a2;
+    }
+    __syncthreads();
+    for (int k = tid; k < kT * kT; k += kSsimThreads) {
+        const int r = k / kT, c = k - r * kT;
+        const int gy = TY + r, gx = TX + c;
+        if (gy >= H || gx >= W) continue;
+        float b0 = 0.f, b1 = 0.f, b2 = 0.f;
+#pragma unroll
+        for (int j = 0; j < 11; ++j) {
+            const float w = win.w[j];
+            b0 = fmaf(w, S.u.g[0][r + j][c], b0);
+            b1 = fmaf(w, S.u.g[1][r + j][c], b1);
+            b2 = fmaf(w, S.u.g[2][r + j][c], b2);
+        }
+        const float xp = S.sx[r + 2 * kR][c + 2 * kR], yp = S.sy[r + 2 * kR][c + 2 * kR];
+        const float dd = xp - yp;
+        const float sgn = (dd > 0.f) ? 1.f : ((dd < 0.f) ? -1.f : 0.f);
+        grad[((size_t)v * H + gy) * W + gx] = l1_scale * sgn - ssim_scale * (b0 + 2.f * xp * b1 + yp * b2);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         sS += __shfl_xor_sync(0xffffffffu, sS, o);
         sL1 += __shfl_xor_sync(0xffffffffu, sL1, o);
     }
-    if ((threadIdx.x & 31) == 0) {
-        red[0][threadIdx.x >> 5] = sS;
-        red[1][threadIdx.x >> 5] = sL1;
+    if ((tid & 31) == 0) {
+        S.red[0][tid >> 5] = sS;
+        S.red[1][tid >> 5] = sL1;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        float a = 0.f, b = 0.f;
-        for (int w = 0; w < 8; ++w) {
-            a += red[0][w];
-            b += red[1][w];
+    if (tid == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < kSsimThreads / 32; ++w) {
+            a += S.red[0][w];
+            b += S.red[1][w];
         }
-        partials[2 * tile] = a;
-        partials[2 * tile + 1] = b;
-    }
-}
-
-__global__ void __launch_bounds__(256) k_ssim_grad(const float* __restrict__ x, const float* __restrict__ y,
-                                                   const int* __restrict__ meas_sel, int H,
-                                                   int W, int tiles_x, int tiles_per_view, const Win win,
-                                                   const float* __restrict__ dmu, const float* __restrict__ dxx,
-                                                   const float* __restrict__ dxy, float l1_scale, float ssim_scale,
-                                                   float* __restrict__ grad, const float* __restrict__ partials,
-                                                   int n_tiles, float lam, double inv_n, float* __restrict__ loss) {
-    __shared__ float s[3][kE][kE + 1];
-    __shared__ float h[3][kE][kT + 1];
-    __shared__ double red[2][256];
-    const int tile = blockIdx.x;
-    const int v = tile / tiles_per_view, lt = tile - v * tiles_per_view;
-    const int ty = lt / tiles_x, tx = lt - ty * tiles_x;
-    const int Y0 = ty * kT - kR, X0 = tx * kT - kR;
-    const size_t vb = (size_t)v * H * W;
-    for (int k = threadIdx.x; k < kE * kE; k += 256) {
-        const int r = k / kE, c = k - r * kE;
-        const int gy = Y0 + r, gx = X0 + c;
-        const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
-        const size_t o = vb + (size_t)gy * W + gx;
-        s[0][r][c] = in ? dmu[o] : 0.f;
-        s[1][r][c] = in ? dxx[o] : 0.f;
-        s[2][r][c] = in ? dxy[o] : 0.f;
+        partials[2 * tile] = (float)a;
+        partials[2 * tile + 1] = (float)b;
+        __threadfence();
+        S.last = atomicAdd(arrive, 1u) == (unsigned)(n_tiles - 1);
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < kE * kT; k += 256) {
-        const int r = k / kT, c = k - r * kT;
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+    if (!S.last) return;
+    __threadfence();
+    double a = 0.0, b = 0.0;
+    for (int k = tid; k < n_tiles; k += kSsimThreads) {
+        a += __ldcg(partials + 2 * k);
+        b += __ldcg(partials + 2 * k + 1);
+    }
+    __syncthreads();  // S.red is reused
 #pragma unroll
-        for (int j = 0; j < 11; ++j) {
-            const float w = win.w[j];
-            a0 = fmaf(w, s[0][r][c + j], a0);
-            a1 = fmaf(w, s[1][r][c + j], a1);
-            a2 = fmaf(w, s[2][r][c + j], a2);
-        }
-        h[0][r][c] = a0;
-        h[1][r][c] = a1;
-        h[2][r][c] = a2;
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if ((tid & 31) == 0) {
+        S.red[0][tid >> 5] = a;
+        S.red[1][tid >> 5] = b;
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < kT * kT; k += 256) {
-        const int r = k / kT, c = k - r * kT;
-        const int gy = ty * kT + r, gx = tx * kT + c;
-        if (gy >= H || gx >= W) continue;
-        float b0 = 0.f, b1 = 0.f, b2 = 0.f;
-#pragma unroll
-        for (int j = 0; j < 11; ++j) {
-            const float w = win.w[j];
-            b0 = fmaf(w, h[0][r + j][c], b0);
-            b1 = fmaf(w, h[1][r + j][c], b1);
-            b2 = fmaf(w, h[2][r + j][c], b2);
+    if (tid == 0) {
+        double sa = 0.0, sb = 0.0;
+        for (int w = 0; w < kSsimThreads / 32; ++w) {
+            sa += S.red[0][w];
+            sb += S.red[1][w];
         }
-        const size_t o = vb + (size_t)gy * W + gx;
-        const float xv = x[o], yv = y[(size_t)(meas_sel ? meas_sel[v] : v) * H * W + (size_t)gy * W + gx];
-        const float d = xv - yv;
-        const float sgn = (d > 0.f) ? 1.f : ((d < 0.f) ? -1.f : 0.f);
-        grad[o] = l1_scale * sgn - ssim_scale * (b0 + 2.f * xv * b1 + yv * b2);
-    }
-    // The per-tile partial sums come from the previous kernel, so any one block can
-    // form the loss: block 0 sums them in a fixed order.
-    if (blockIdx.x == 0) {
-        double sS = 0.0, sL1 = 0.0;
-        for (int k = threadIdx.x; k < n_tiles; k += 256) {
-            sS += partials[2 * k];
-            sL1 += partials[2 * k + 1];
-        }
-        red[0][threadIdx.x] = sS;
-        red[1][threadIdx.x] = sL1;
-        __syncthreads();
-        for (int o = 128; o > 0; o >>= 1) {
-            if ((int)threadIdx.x < o) {
-                red[0][threadIdx.x] += red[0][threadIdx.x + o];
-                red[1][threadIdx.x] += red[1][threadIdx.x + o];
-            }
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) *loss = (float)(inv_n * red[1][0] + lam * (1.0 - inv_n * red[0][0]));
+        *loss = (float)(inv_n * sb + lam * (1.0 - inv_n * sa));
     }
 }
 
@@ -294,7 +298,7 @@ Win gaussian_window() {
 }
 
 struct LossLayout {
-    size_t dmu, dxx, dxy, partials, fixed;
+    size_t partials, arrive, fixed;
     int tiles_x, tiles_y;
     long long n_tiles;
 };
@@ -304,12 +308,9 @@ LossLayout loss_layout(int V, int H, int W) {
     L.tiles_x = (W + kT - 1) / kT;
     L.tiles_y = (H + kT - 1) / kT;
     L.n_tiles = (long long)V * L.tiles_x * L.tiles_y;
-    const size_t n = (size_t)V * H * W;
     Layout lay;
-    L.dmu = lay.take(4 * n);
-    L.dxx = lay.take(4 * n);
-    L.dxy = lay.take(4 * n);
     L.partials = lay.take(8 * (size_t)L.n_tiles);
+    L.arrive = lay.take(sizeof(unsigned int));
     L.fixed = lay.off;
     return L;
 }
@@ -335,21 +336,29 @@ r2g_status r2g::projection_loss_impl(int32_t V, int32_t H, int32_t W, const floa
     if (L.n_tiles >= (1ll << 31)) return fail(R2G_E_INVAL, "image too large");
     const Win win = gaussian_window();
     char* base = static_cast<char*>(ws);
-    float* dmu = reinterpret_cast<float*>(base + L.dmu);
-    float* dxx = reinterpret_cast<float*>(base + L.dxx);
-    float* dxy = reinterpret_cast<float*>(base + L.dxy);
     float* partials = reinterpret_cast<float*>(base + L.partials);
+    unsigned int* arrive = reinterpret_cast<unsigned int*>(base + L.arrive);
+    // the kernel's shared memory exceeds the 48 KB default: opt in once per device
+    // (idempotent, so racing first calls are harmless)
+    static bool smem_set[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || !smem_set[dev]) {
+        if (cudaFuncSetAttribute(k_ssim, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SsimSmem)) !=
+            cudaSuccess)
+            return fail(R2G_E_CUDA, "r2g_projection_loss: shared memory attribute (%s)",
+                        cudaGetErrorString(cudaGetLastError()));
+        if (dev >= 0 && dev < 64) smem_set[dev] = true;
+    }
     const int tpv = L.tiles_x * L.tiles_y;
-    prof_begin(P_LOSS, stream);
-    k_ssim_maps<<<(unsigned)L.n_tiles, 256, 0, stream>>>(render, meas, meas_sel, H, W, L.tiles_x, tpv, win, dmu,
-                                                          dxx, dxy, partials);
     const double N = (double)V * H * W;
-    k_ssim_grad<<<(unsigned)L.n_tiles, 256, 0, stream>>>(render, meas, meas_sel, H, W, L.tiles_x, tpv, win, dmu,
-                                                          dxx, dxy,
-                                                          (float)(1.0 / N), (float)(lambda_ssim / N), drender,
-                                                          partials, (int)L.n_tiles, lambda_ssim, 1.0 / N, loss);
+    prof_begin(P_LOSS, stream);
+    cudaMemsetAsync(arrive, 0, sizeof(unsigned int), stream);
+    k_ssim<<<(unsigned)L.n_tiles, kSsimThreads, sizeof(SsimSmem), stream>>>(
+        render, meas, meas_sel, H, W, L.tiles_x, tpv, (int)L.n_tiles, win, (float)(1.0 / N), (float)(lambda_ssim / N),
+        drender, partials, arrive, lambda_ssim, 1.0 / N, loss);
     prof_end(P_LOSS, stream);
-    note_launches(2);
+    note_launches(1);
     return check_launch("r2g_projection_loss");
 }
 

@@ -246,6 +246,21 @@ def test_projection_loss_matches_oracle():
     assert np.abs(host(grad) - G).max() <= 1e-4 * np.abs(G).max()
 
 
+def test_projection_loss_full_view_matches_oracle():
+    """One 512 x 512 view (256 tiles of 32 x 32): loss and gradient against the oracle."""
+    g = I.rng(9)
+    x = g.uniform(0, 3, (1, 512, 512)).astype(np.float32)
+    y = (x + 0.1 * g.standard_normal(x.shape)).astype(np.float32)
+    loss = torch.zeros(1, device="cuda")
+    grad = torch.empty((1, 512, 512), device="cuda")
+    ws = torch.empty(r2g.r2g_loss_workspace_size(1, 512, 512), dtype=torch.uint8, device="cuda")
+    for _ in range(2):  # the second call reuses the workspace (arrival counter cleared per call)
+        r2g.r2g_projection_loss(dev(x), dev(y), 0.25, loss, grad, ws)
+        L, G = losses.projection_loss(x, y, 0.25)
+        assert abs(float(loss) - L) <= 1e-5 * abs(L)
+        assert np.abs(host(grad) - G).max() <= 1e-4 * np.abs(G).max()
+
+
 def test_tv_matches_oracle():
     v = I.rng(9).standard_normal((2, 12, 12, 12)).astype(np.float32)
     vd = dev(v)
