@@ -17,9 +17,9 @@
 //                  chunks write per-chunk images; the last chunk to finish sums
 //                  them in chunk order.  An empty tile's work item writes zeros.
 //   k_splat_bwd    one CTA per work item with dL/dI of the tile in shared
-//                  memory; the records' boxes are cut into units of kBwdUnit
-//                  pixels along a row and the units split evenly over the 128
-//                  lanes; each lane accumulates six moments (sum w, w dx, w dy,
+//                  memory; the records' boxes are cut into units of 4 x 2
+//                  pixels and the units split evenly over the 128 lanes; each
+//                  lane accumulates six moments (sum w, w dx, w dy,
 //                  w dx^2, w dx dy, w dy^2; w = g e) of its current record in
 //                  registers and adds them with two vector atomics to the
 //                  record's slot.
@@ -454,22 +454,22 @@ __device__ __forceinline__ uint32_t cta_excl_scan_128(uint32_t v, uint32_t* s_w,
     return before + incl - v;
 }
 
-// Pixels per backward unit (a run of UW pixels along a row of a record's box).
-constexpr int kBwdUnit = 4;
+// Backward unit: UW x UH pixels (columns x rows) of a record's box.
+constexpr int kBwdUnitW = 4, kBwdUnitH = 2;
 
 // One CTA per work item (<= 128 records of one tile).  Each record's pixel box
-// inside the tile, w x h pixels, is cut into rows of ceil(w / UW) units of UW
-// consecutive pixels.  The last unit of a row may reach past the box: those
-// pixels lie outside the box, where the gate t >= Tq rejects them exactly as the
-// forward does, or past the tile edge, where the staged dL/dI rows are padded
-// with UW zeros.  The units
-// of the CTA's records are split into 128 equal contiguous ranges, one per lane,
-// so every lane evaluates the same number of units whatever the record sizes.  A
-// lane derives each unit's row and column from its index inside the record (no
-// per-row state, so lanes never diverge on row changes), accumulates the six
-// moments of its current record in registers, and adds them to the record's slot
-// (two vector atomics) when it leaves the record or its range ends.
-template <int TW, int TH, int UW>
+// inside the tile, w x h pixels, is cut into ceil(h / UH) rows of ceil(w / UW)
+// units of UW x UH pixels.  A unit may reach past the box: those pixels lie
+// outside the box, where the gate t >= Tq rejects them exactly as the forward
+// does, or past the tile edge, where the staged dL/dI is padded with UW zero
+// columns and UH - 1 zero rows.  The units of the CTA's records are split into
+// 128 equal contiguous ranges, one per lane, so every lane evaluates the same
+// number of units whatever the record sizes.  A lane derives each unit's row and
+// column from its index inside the record (no per-row state, so lanes never
+// diverge on row changes), accumulates the six moments of its current record in
+// registers, and adds them to the record's slot (two vector atomics) when it
+// leaves the record or its range ends.
+template <int TW, int TH, int UW, int UH>
 __global__ void __launch_bounds__(kBwdThreads) k_splat_bwd(const float4* __restrict__ rec,
                                                            const uint2* __restrict__ ranges,
                                                            const uint64_t* __restrict__ sorted,
@@ -479,9 +479,11 @@ __global__ void __launch_bounds__(kBwdThreads) k_splat_bwd(const float4* __restr
                                                            const float* __restrict__ dimage,
                                                            float4* __restrict__ mom) {
     static_assert(kChunk == kBwdThreads, "one record per thread");
-    static_assert(TW <= 32 && TH <= 16 && UW >= 1 && UW <= 4, "unit decode is exact for these sizes");
+    static_assert(TW <= 32 && TH <= 16 && UW >= 1 && UW <= 4 && UH >= 1 && UH <= 2,
+                  "unit decode is exact for these sizes");
     constexpr int TWP = TW + UW;          // staged row stride: UW zero columns past the tile edge
-    __shared__ float s_g[TH * TWP];       // dL/dI of the tile
+    constexpr int THP = TH + UH - 1;      // staged rows: UH - 1 zero rows past the tile edge
+    __shared__ float s_g[THP * TWP];      // dL/dI of the tile
     __shared__ float4 s_k1[kChunk];        // A, B, C of the conic; dx of the box's first pixel
     __shared__ float4 s_k2[kChunk];        // dy of the first row; s_g index of the first pixel; 1/uw; uw
     __shared__ uint32_t s_gid[kChunk];     // Gaussian id
@@ -496,10 +498,10 @@ __global__ void __launch_bounds__(kBwdThreads) k_splat_bwd(const float4* __restr
     const int lt = tile - v * tiles_per_view;
     const int ty = lt / tiles_x, tx = lt - ty * tiles_x;
     const int X0 = tx * TW, Y0 = ty * TH;
-    for (int k = threadIdx.x; k < TH * TWP; k += kBwdThreads) {
+    for (int k = threadIdx.x; k < THP * TWP; k += kBwdThreads) {
         const int r = k / TWP, c = k - r * TWP;
         const int gy = Y0 + r, gx = X0 + c;
-        s_g[k] = (c < TW && gy < H && gx < W) ? dimage[((size_t)v * H + gy) * W + gx] : 0.0f;
+        s_g[k] = (r < TH && c < TW && gy < H && gx < W) ? dimage[((size_t)v * H + gy) * W + gx] : 0.0f;
     }
     const uint2 rg = ranges[tile];
     const float4* vrec = rec + 2 * (size_t)v * (size_t)M;
@@ -516,7 +518,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_splat_bwd(const float4* __restr
         const int w = c1 - c0 + 1, h = r1 - r0 + 1;
         if (w > 0 && h > 0) {
             const int uw = (w + UW - 1) / UW;
-            n = (uint32_t)(uw * h);
+            n = (uint32_t)(uw * ((h + UH - 1) / UH));
             s_k1[j] = make_float4(a.z, a.w, b.x, (float)(X0 + c0) - a.x);
             s_k2[j] = make_float4((float)(Y0 + r0) - a.y, (float)(r0 * TWP + c0), 1.0f / (float)uw, (float)uw);
             s_gid[j] = gid;
@@ -544,30 +546,34 @@ __global__ void __launch_bounds__(kBwdThreads) k_splat_bwd(const float4* __restr
     float uf = (float)(p0 - s_excl[k]);  // unit index inside the record
     float S0 = 0.f, Sx = 0.f, Sy = 0.f, Sxx = 0.f, Sxy = 0.f, Syy = 0.f;
     for (uint32_t p = p0; p < p1; ++p) {
-        // row = floor((u + 1/2) / uw), exact for u < 2^10 and uw <= 16
+        // unit row = floor((u + 1/2) / uw), exact for u < 2^10 and uw <= 16
         const float rowf = floorf(fmaf(uf, k2.z, 0.5f * k2.z));
-        const float colf = fmaf(-rowf, k2.w, uf) * (float)UW;  // first pixel of the unit, inside the box row
+        const float colf = fmaf(-rowf, k2.w, uf) * (float)UW;  // first pixel column of the unit in the box
         const float dx = k1.w + colf;
-        const float dy = k2.x + rowf;
-        const int gi = (int)fmaf(rowf, (float)TWP, k2.y + colf);
-        const float bdy = k1.y * dy, cdy2 = k1.z * dy * dy;
-        float Wu = 0.f, Xu = 0.f;
+        const float dy0 = fmaf(rowf, (float)UH, k2.x);
+        const int gi = (int)fmaf(rowf, (float)(UH * TWP), k2.y + colf);
 #pragma unroll
-        for (int q = 0; q < UW; ++q) {
-            const float dxq = dx + (float)q;
-            const float t = fmaf(fmaf(k1.x, dxq, bdy), dxq, cdy2);
-            const float ev = ex2_approx(t);
-            const float wq = (t >= Tq) ? s_g[gi + q] * ev : 0.0f;
-            const float aq = wq * dxq;
-            Wu += wq;
-            Xu += aq;
-            Sxx = fmaf(aq, dxq, Sxx);
+        for (int qy = 0; qy < UH; ++qy) {
+            const float dy = dy0 + (float)qy;
+            const float bdy = k1.y * dy, cdy2 = k1.z * dy * dy;
+            float Wu = 0.f, Xu = 0.f;
+#pragma unroll
+            for (int q = 0; q < UW; ++q) {
+                const float dxq = dx + (float)q;
+                const float t = fmaf(fmaf(k1.x, dxq, bdy), dxq, cdy2);
+                const float ev = ex2_approx(t);
+                const float wq = (t >= Tq) ? s_g[gi + qy * TWP + q] * ev : 0.0f;
+                const float aq = wq * dxq;
+                Wu += wq;
+                Xu += aq;
+                Sxx = fmaf(aq, dxq, Sxx);
+            }
+            S0 += Wu;
+            Sx += Xu;
+            Sy = fmaf(Wu, dy, Sy);
+            Sxy = fmaf(Xu, dy, Sxy);
+            Syy = fmaf(Wu * dy, dy, Syy);
         }
-        S0 += Wu;
-        Sx += Xu;
-        Sy = fmaf(Wu, dy, Sy);
-        Sxy = fmaf(Xu, dy, Sxy);
-        Syy = fmaf(Wu * dy, dy, Syy);
         uf += 1.0f;
         if (p + 1 == rec_end && p + 1 < p1) {  // next record
             atomicAdd(&vmom[2 * (size_t)gid], make_float4(S0, Sx, Sy, Sxx));
@@ -878,13 +884,16 @@ void launch_bwd(int tw, int th, const float4* rec, const uint2* ranges, const ui
                 int H, int W, float Tq, const float* dimage, float4* mom, cudaStream_t s) {
     const unsigned grid = (unsigned)icap;
     if (tw == 16 && th == 16)
-        k_splat_bwd<16, 16, kBwdUnit><<<grid, kBwdThreads, 0, s>>>(rec, ranges, sorted, items, item_st, M, L.tiles_x,
+        k_splat_bwd<16, 16, kBwdUnitW, kBwdUnitH><<<grid, kBwdThreads, 0, s>>>(rec, ranges, sorted, items, item_st,
+                                                                                   M, L.tiles_x,
                                                          L.tiles_per_view, H, W, Tq, dimage, mom);
     else if (tw == 8 && th == 8)
-        k_splat_bwd<8, 8, kBwdUnit><<<grid, kBwdThreads, 0, s>>>(rec, ranges, sorted, items, item_st, M, L.tiles_x,
+        k_splat_bwd<8, 8, kBwdUnitW, kBwdUnitH><<<grid, kBwdThreads, 0, s>>>(rec, ranges, sorted, items, item_st,
+                                                                                   M, L.tiles_x,
                                                        L.tiles_per_view, H, W, Tq, dimage, mom);
     else
-        k_splat_bwd<32, 8, kBwdUnit><<<grid, kBwdThreads, 0, s>>>(rec, ranges, sorted, items, item_st, M, L.tiles_x,
+        k_splat_bwd<32, 8, kBwdUnitW, kBwdUnitH><<<grid, kBwdThreads, 0, s>>>(rec, ranges, sorted, items, item_st,
+                                                                                   M, L.tiles_x,
                                                         L.tiles_per_view, H, W, Tq, dimage, mom);
 }
 
