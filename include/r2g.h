@@ -314,9 +314,11 @@ r2g_status r2g_upload_round(r2g_round_entry* dst, const r2g_round_entry* src, in
  *
  * Optional timing of the library's own kernels: when enabled, every call records
  * a CUDA event pair on its stream around each hot kernel (or kernel group):
- * 0 project, 1 emit (count+scan+emit), 2 sort (all radix passes), 3 ranges,
- * 4 splat_fwd, 5 splat_bwd, 6 project_bwd, 7 vox_project, 8 vox_fwd, 9 vox_bwd,
- * 10 vox_chain, 11 loss, 12 tv, 13 adam.  Not for use inside stream capture.
+ * 0 project, 1 emit (tile entries: count + emit), 2 sort (tile lists: offsets +
+ * scatter, or the radix passes), 3 ranges (radix path only), 4 splat_fwd,
+ * 5 splat_bwd, 6 project_bwd, 7 vox_project, 8 vox_fwd, 9 vox_bwd, 10 vox_chain,
+ * 11 loss, 12 tv, 13 adam, 14-16 the same three list stages for the brick lists.
+ * Not for use inside stream capture.
  * max_spans bounds the recorded pairs (events are created once, here). */
 r2g_status r2g_profile_enable(int32_t on, int32_t max_spans);
 /* Restrict recording to the kernel ids whose bit is set in kernel_mask (bit k =

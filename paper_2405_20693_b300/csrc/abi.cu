@@ -38,7 +38,8 @@ r2g_status check_launch(const char* what) {
 namespace {
 const char* const kProfNames[P_COUNT] = {"project",    "emit",       "sort",      "ranges",   "splat_fwd",
                                          "splat_bwd",  "project_bwd", "vox_project", "vox_fwd", "vox_bwd",
-                                         "vox_chain",  "loss",       "tv",        "adam"};
+                                         "vox_chain",  "loss",       "tv",        "adam",    "vox_emit",
+                                         "vox_sort",   "vox_ranges"};
 std::atomic<long long> g_launches{0};
 std::mutex g_prof_mu;
 bool g_prof_on = false;

@@ -266,35 +266,35 @@ template <class Op>
 uint64_t* build_lists(const Op& op, long long n_rec, long long n_slots, unsigned long long* partials, WsStatus* st,
                       uint64_t* a, uint64_t* b, uint32_t* scratch, long long cap, uint2* ranges, uint32_t* key_done,
                       WsStatus* item_st, uint32_t* item_off, uint64_t* items, long long items_cap, int chunk,
-                      cudaStream_t s, int* launches) {
+                      ListProf prof, cudaStream_t s, int* launches) {
     const unsigned long long ucap = (unsigned long long)cap;
     if (fused_lists(n_slots)) {
         uint32_t* hist = scratch;
         uint32_t* totals = scratch + (size_t)kRadix * kSortBlocksMax;
         const int nk = (int)n_slots;
-        prof_begin(P_EMIT, s);
+        prof_begin(prof.emit, s);
         k_count_chunks<Op><<<kFusedBlocks, 256, 0, s>>>(op, n_rec, partials, st, ucap, totals, nk);
         k_emit_chunks<Op, true><<<kFusedBlocks, 256, 0, s>>>(op, n_rec, partials, a, ucap, hist, totals, nk);
-        prof_end(P_EMIT, s);
-        prof_begin(P_SORT, s);
+        prof_end(prof.emit, s);
+        prof_begin(prof.sort, s);
         k_fused_offsets<<<(nk + 7) / 8, 256, 0, s>>>(hist, totals, kFusedBlocks, nk, (uint32_t)chunk, ranges,
                                                       key_done, item_off, items, (unsigned long long)items_cap,
                                                       item_st);
         k_fused_scatter<<<kFusedBlocks, 256, 0, s>>>(a, b, hist, partials, st, nk);
-        prof_end(P_SORT, s);
+        prof_end(prof.sort, s);
         *launches += 4;
         return b;
     }
-    prof_begin(P_EMIT, s);
+    prof_begin(prof.emit, s);
     k_count_chunks<Op><<<kScanBlocks, 256, 0, s>>>(op, n_rec, partials, st, ucap, nullptr, 0);
     k_emit_chunks<Op, false><<<kScanBlocks, 256, 0, s>>>(op, n_rec, partials, a, ucap, nullptr, nullptr, 0);
-    prof_end(P_EMIT, s);
-    prof_begin(P_SORT, s);
+    prof_end(prof.emit, s);
+    prof_begin(prof.sort, s);
     uint64_t* sorted = radix_sort_u64(a, b, scratch, st, bits_for(n_slots), sort_blocks_for(cap), s);
-    prof_end(P_SORT, s);
-    prof_begin(P_RANGES, s);
+    prof_end(prof.sort, s);
+    prof_begin(prof.ranges, s);
     build_ranges_items(sorted, st, ranges, n_slots, item_st, item_off, items, items_cap, chunk, s);
-    prof_end(P_RANGES, s);
+    prof_end(prof.ranges, s);
     *launches += 2 + 3 * list_sort_passes(n_slots) + 1;
     return sorted;
 }

@@ -335,9 +335,12 @@ __global__ void __launch_bounds__(FwdShape<TW, TH>::NT) k_splat_fwd(const float4
     constexpr int NT = FwdShape<TW, TH>::NT;  // threads
     constexpr int BW = 4 * PX;                // warp block: 8 rows x BW columns
     constexpr int WPR = TW / BW;              // warp blocks per tile row
-    static_assert(TW % BW == 0 && TH % 8 == 0 && kChunk % NT == 0 && NT % 32 == 0, "tile shape");
+    constexpr int NW = NT / 32;               // warps = warp blocks per tile
+    static_assert(TW % BW == 0 && TH % 8 == 0 && kChunk % NT == 0 && NT % 32 == 0 && NW <= 32, "tile shape");
     __shared__ float4 s_a[NT];
     __shared__ float4 s_b[NT];
+    __shared__ uint32_t s_mask[NT];           // bit w: the record's box meets warp w's block
+    __shared__ uint8_t s_list[NW][NT];        // per warp: the batch's records that meet its block
     __shared__ int s_last;
     const unsigned long long it = blockIdx.x;
     if (it >= item_st->n_keys) return;
@@ -351,8 +354,6 @@ __global__ void __launch_bounds__(FwdShape<TW, TH>::NT) k_splat_fwd(const float4
     const int bx = (warp % WPR) * BW, by = (warp / WPR) * 8;
     const int lx = bx + (lane & 3) * PX, ly = by + (lane >> 2);
     const int px = tx * TW + lx, py = ty * TH + ly;
-    const float wx0 = (float)(tx * TW + bx), wx1 = wx0 + (float)(BW - 1);
-    const float wy0 = (float)(ty * TH + by), wy1 = wy0 + 7.0f;
     const float fx = (float)px, fy = (float)py;
     const float4* vrec = rec + 2 * (size_t)v * (size_t)M;
     float acc[PX];
@@ -368,23 +369,47 @@ __global__ void __launch_bounds__(FwdShape<TW, TH>::NT) k_splat_fwd(const float4
         __syncthreads();
         if ((int)threadIdx.x < n) {
             const uint32_t gid = (uint32_t)sorted[base + threadIdx.x];
-            s_a[threadIdx.x] = vrec[2 * (size_t)gid];
-            s_b[threadIdx.x] = vrec[2 * (size_t)gid + 1];
+            const float4 a = vrec[2 * (size_t)gid];      // cx, cy, A, B
+            const float4 b = vrec[2 * (size_t)gid + 1];  // C, rho_hat, rx, ry
+            s_a[threadIdx.x] = a;
+            s_b[threadIdx.x] = b;
+            // the record's pixel box inside the tile, and the warp blocks it meets
+            const int c0 = (int)ceilf(a.x - b.z) - tx * TW, c1 = (int)floorf(a.x + b.z) - tx * TW;
+            const int r0 = (int)ceilf(a.y - b.w) - ty * TH, r1 = (int)floorf(a.y + b.w) - ty * TH;
+            uint32_t mask = 0;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) {
+                const int wbx = (w % WPR) * BW, wby = (w / WPR) * 8;
+                if (c1 >= wbx && c0 <= wbx + BW - 1 && r1 >= wby && r0 <= wby + 7) mask |= 1u << w;
+            }
+            s_mask[threadIdx.x] = mask;
         }
         __syncthreads();
-        for (int j = 0; j < n; ++j) {
-            const float4 a = s_a[j];  // cx, cy, A, B
-            const float4 b = s_b[j];  // C, rho_hat, rx, ry
-            // warp-uniform cull: the record's box misses this warp's block
-            if (a.y + b.w < wy0 || a.y - b.w > wy1 || a.x + b.z < wx0 || a.x - b.z > wx1) continue;
+        // this warp's records of the batch, in batch order
+        int m = 0;
+#pragma unroll
+        for (int c = 0; c < NT / 32; ++c) {
+            const int j = c * 32 + lane;
+            const bool mine = j < n && ((s_mask[j] >> warp) & 1u);
+            const uint32_t bal = __ballot_sync(0xffffffffu, mine);
+            if (mine) s_list[warp][m + __popc(bal & ((1u << lane) - 1u))] = (uint8_t)j;
+            m += __popc(bal);
+        }
+        __syncwarp();
+        for (int q = 0; q < m; ++q) {
+            const int j = s_list[warp][q];
+            const float4 a = s_a[j];
+            const float4 b = s_b[j];
             const float dy = fy - a.y;
             const float bdy = a.w * dy;
             const float cdy2 = b.x * dy * dy;
             const float dx0 = fx - a.x;
+            // t(dx0 + k) = t0 + k (g + A k), g = dt/ddx at dx0
+            const float t0 = fmaf(fmaf(a.z, dx0, bdy), dx0, cdy2);
+            const float g = fmaf(2.0f * a.z, dx0, bdy);
 #pragma unroll
             for (int k = 0; k < PX; ++k) {
-                const float dx = dx0 + (float)k;
-                const float t = fmaf(fmaf(a.z, dx, bdy), dx, cdy2);
+                const float t = k == 0 ? t0 : fmaf((float)k, fmaf(a.z, (float)k, g), t0);
                 const float e = ex2_approx(t);
                 acc[k] = (t >= Tq) ? fmaf(b.y, e, acc[k]) : acc[k];
                 if (COUNT) cnt += (t >= Tq && px + k < W && py < H);
@@ -974,7 +999,8 @@ r2g_status r2g::rasterize_impl(int64_t M, const float* mean, const float* scale,
     TileOp op{rect, M, L.tiles_x, L.tiles_per_view};
     int launches = 0;
     uint64_t* sorted = build_lists(op, L.n_rec, L.n_tiles, partials, st, a, b, scratch, cap, ranges, key_done,
-                                   item_st, item_off, items, T.icap, kChunk, stream, &launches);
+                                   item_st, item_off, items, T.icap, kChunk, ListProf{P_EMIT, P_SORT, P_RANGES},
+                                   stream, &launches);
     const float Tq = -0.5f * kLog2e * opts->Q;
     prof_begin(P_SPLAT_FWD, stream);
     const FwdArgs fa{rec, ranges, sorted, items, item_st, partial, item_off, key_done};

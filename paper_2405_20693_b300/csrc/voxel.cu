@@ -724,7 +724,8 @@ r2g_status voxelize_impl(int64_t M, const float* mean, const float* scale, const
     }
     int launches = 0;
     uint64_t* sorted = build_lists(op, L.n_rec, L.n_bricks, partials, st, a, b, scratch, cap, ranges, key_done,
-                                   item_st, item_off, items, T.icap, kVoxChunk, stream, &launches);
+                                   item_st, item_off, items, T.icap, kVoxChunk,
+                                   ListProf{P_VOX_EMIT, P_VOX_SORT, P_VOX_RANGES}, stream, &launches);
     const float Tq = -0.5f * kLog2e * Q3;
     note_launches(1 + launches + 1);
     prof_begin(P_VOX_FWD, stream);

@@ -313,7 +313,7 @@ def r2g_adam_step(raw, act, grad, m, v, it: int, opts: AdamOpts, stream=None):
 
 
 PROFILE_KERNELS = ("project", "emit", "sort", "ranges", "splat_fwd", "splat_bwd", "project_bwd", "vox_project",
-                   "vox_fwd", "vox_bwd", "vox_chain", "loss", "tv", "adam")
+                   "vox_fwd", "vox_bwd", "vox_chain", "loss", "tv", "adam", "vox_emit", "vox_sort", "vox_ranges")
 
 
 def r2g_profile_enable(on: bool, max_spans: int = 4096):
