@@ -2,21 +2,25 @@
 // the rasterizer (key = tile) and the voxelizer (key = brick), and the list
 // builder that turns them into per-key lists sorted by Gaussian id.
 //
-// An Op supplies, for record r, how many entries it emits (count) and visits them
-// in order (entries(r, f) calls f(key, id) once per entry).  Records are split
-// into contiguous chunks, one per block; a first pass sums each chunk (its last
-// block to finish scans the chunk sums and writes the total and the capacity
-// verdict into the status block), and a second pass re-scans each chunk in
-// rounds of 256 records and writes every record's entries at its offset, in
-// record order.  Entries beyond the capacity are not written.
+// Records are processed in list blocks of 256 threads x L records (L grows with
+// the record count so that there are at most kMaxListBlocks blocks).  The
+// projection kernels run with this blocking: each computes its records' key
+// rectangles, counts the entries of its block and calls list_count_tail, whose
+// last block to finish turns the block counts into exclusive offsets and writes
+// the total and the capacity verdict into the status block.  The emission then
+// re-walks each block's records in rounds of 256 and writes every record's
+// entries at its offset, in record order (an Op supplies, for record r, its entry
+// count and entries(r, f), calling f(key, id) once per entry).  Entries beyond
+// the capacity are not written.
 //
 // Key spaces of at most kFusedKeys keys (one 512^2 view in 16 x 16 tiles, the
 // bricks of a TV patch) take a fused path: the emission also counts its block's
-// entries per key, one warp per key turns the counts into scatter offsets, the
-// key's range and its work items, and a stable scatter (one contiguous run per
-// warp, ranked with warp match masks) writes the sorted lists -- four launches
-// and one pass over the entries.  Larger key spaces take the general stable LSD
-// radix sort and a range pass.
+// entries per key, and its last block forms each key's base, range and work
+// items; one warp per key turns the per-(key, block) counts into scatter
+// offsets; a stable scatter (one contiguous run per warp, ranked with warp match
+// masks) writes the sorted lists -- three launches after the projection, one pass
+// over the entries.  Larger key spaces take the general stable LSD radix sort and
+// a range pass.
 #pragma once
 
 #include "r2g_internal.cuh"
@@ -24,11 +28,31 @@
 namespace r2g {
 
 constexpr int kFusedKeys = 1024;
-constexpr int kFusedBlocks = 148;  // emit / scatter blocks of the fused path
-static_assert(kScanBlocks <= 1024 && kFusedBlocks <= 1024, "the last count block scans <= 1024 chunk sums");
-static_assert((size_t)kFusedKeys * kFusedBlocks <= (size_t)kRadix * kSortBlocksMax,
-              "fused histograms fit the sort scratch");
+constexpr int kMaxListBlocks = kScanBlocks;  // the block-offset array holds kScanBlocks entries
+static_assert((size_t)kFusedKeys * kMaxListBlocks <= (size_t)kRadix * kSortBlocksMax,
+              "fused per-(key, block) counts fit the sort scratch");
 static_assert(kFusedKeys <= kRadix * 4, "fused key totals fit the sort scratch");
+
+// List blocking of n_rec records: per_thread records per thread, blocks blocks.
+struct ListBlocking {
+    int per_thread;
+    int blocks;
+};
+inline ListBlocking list_blocking(long long n_rec) {
+    const long long per_block = 256ll * kMaxListBlocks;
+    const int L = (int)((n_rec + per_block - 1) / per_block);
+    const int per = L < 1 ? 1 : L;
+    return ListBlocking{per, (int)((n_rec + 256ll * per - 1) / (256ll * per))};
+}
+
+// What the projection kernels need to count their blocks' entries.
+struct ListCount {
+    unsigned long long* partials;  // per-block entry counts -> exclusive offsets (nullptr: no count)
+    WsStatus* st;                  // arrival counter, total, verdict (cleared before the launch)
+    unsigned long long capacity;
+    uint32_t* key_totals;          // fused path: cleared by the last block for the emission
+    int n_keys;
+};
 
 // Block-wide exclusive scan of a 64-bit value for a 256-thread block.
 __device__ __forceinline__ unsigned long long block_excl_scan_u64_256(unsigned long long v, unsigned long long* smem,
@@ -54,71 +78,83 @@ __device__ __forceinline__ unsigned long long block_excl_scan_u64_256(unsigned l
     return before + x - v;
 }
 
-// Each block sums the entry counts of its contiguous chunk of records.  The last
-// block to finish (arrival counter in the status block, cleared by the caller)
-// turns the gridDim.x <= 1024 chunk sums into exclusive offsets, writes the total
-// and the capacity verdict, and clears key_totals (fused path) for the emission.
-template <class Op>
-__global__ void __launch_bounds__(256) k_count_chunks(Op op, long long n_rec, unsigned long long* partials,
-                                                      WsStatus* st, unsigned long long capacity,
-                                                      uint32_t* key_totals, int n_keys) {
+// Called by every thread of a 256-thread projection block with its entry count:
+// the block's sum goes to partials[block]; the last block to finish turns all
+// gridDim.x sums into exclusive offsets, writes the total and the capacity
+// verdict, and clears key_totals.
+__device__ __forceinline__ void list_count_tail(const ListCount& lc, unsigned long long mine) {
     __shared__ unsigned long long sm[8];
     __shared__ int s_last;
-    const long long chunk = (n_rec + gridDim.x - 1) / gridDim.x;
-    const long long begin = min(n_rec, (long long)blockIdx.x * chunk);
-    const long long end = min(n_rec, begin + chunk);
-    unsigned long long s = 0;
-    for (long long r = begin + threadIdx.x; r < end; r += 256) s += op.count(r);
-    s = block_sum_u64_256(s, sm);
+    const unsigned long long s = block_sum_u64_256(mine, sm);
     if (threadIdx.x == 0) {
-        partials[blockIdx.x] = s;
+        lc.partials[blockIdx.x] = s;
         __threadfence();
-        s_last = atomicAdd(&st->blocks_done, 1ull) == (unsigned long long)(gridDim.x - 1);
+        s_last = atomicAdd(&lc.st->blocks_done, 1ull) == (unsigned long long)(gridDim.x - 1);
     }
     __syncthreads();
     if (!s_last) return;
     __threadfence();
     const int nb = (int)gridDim.x, t = threadIdx.x;
-    unsigned long long v[4], mine = 0;
+    unsigned long long carry = 0;
+    for (int c0 = 0; c0 < nb; c0 += 1024) {  // uniform trip count: the scan syncs the block
+        unsigned long long v[4], sum = 0;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int i = 4 * t + q;
-        v[q] = i < nb ? __ldcg(partials + i) : 0ull;
-        mine += v[q];
-    }
-    unsigned long long total;
-    unsigned long long run = block_excl_scan_u64_256(mine, sm, &total);
+        for (int q = 0; q < 4; ++q) {
+            const int i = c0 + 4 * t + q;
+            v[q] = i < nb ? __ldcg(lc.partials + i) : 0ull;
+            sum += v[q];
+        }
+        unsigned long long total;
+        unsigned long long run = carry + block_excl_scan_u64_256(sum, sm, &total);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int i = 4 * t + q;
-        if (i < nb) partials[i] = run;
-        run += v[q];
+        for (int q = 0; q < 4; ++q) {
+            const int i = c0 + 4 * t + q;
+            if (i < nb) lc.partials[i] = run;
+            run += v[q];
+        }
+        carry += total;
     }
-    if (key_totals)
-        for (int k = t; k < n_keys; k += 256) key_totals[k] = 0;
+    if (lc.key_totals)
+        for (int k = t; k < lc.n_keys; k += 256) lc.key_totals[k] = 0;
     if (t == 0) {
-        st->needed = total;
-        st->n_keys = total < capacity ? total : capacity;
-        if (total > capacity) st->status = R2G_E_CAPACITY;
+        lc.st->needed = carry;
+        lc.st->n_keys = carry < lc.capacity ? carry : lc.capacity;
+        if (carry > lc.capacity) lc.st->status = R2G_E_CAPACITY;
     }
 }
 
-// HIST (fused path): also count the block's written entries per key, then store
-// the counts as hist[key * gridDim.x + block] and add them to key_totals.
+// Where the fused path's last emission block leaves each key's list.
+struct FusedKeys {
+    uint32_t chunk;           // entries per work item
+    uint2* ranges;            // [start, end) per key ([0, 0) when empty)
+    uint32_t* key_done;       // chunk arrival counters of the forward, cleared
+    uint32_t* item_off;       // first work item of each key
+    uint64_t* items;          // (key << 32) | chunk; every empty key gets one item
+    unsigned long long items_cap;
+    WsStatus* item_st;        // n_keys = item count
+};
+
+// Each block walks its records (blockIdx.x * per_block .. + per_block) in rounds of
+// 256 and writes every record's entries at its offset.  HIST (fused path): also
+// count the block's written entries per key into hist[key * gridDim.x + block]
+// and key_totals; the last block to finish (the status block's arrival counter,
+// which the count pass left at gridDim.x) turns key_totals into each key's first
+// entry (written back into key_totals), range, first item and items.
 template <class Op, bool HIST>
-__global__ void __launch_bounds__(256) k_emit_chunks(Op op, long long n_rec, const unsigned long long* partials,
-                                                     uint64_t* out, unsigned long long capacity,
-                                                     uint32_t* __restrict__ hist, uint32_t* __restrict__ key_totals,
-                                                     int n_keys) {
+__global__ void __launch_bounds__(256) k_emit_chunks(Op op, long long n_rec, long long per_block,
+                                                     const unsigned long long* partials, uint64_t* out,
+                                                     unsigned long long capacity, uint32_t* __restrict__ hist,
+                                                     uint32_t* __restrict__ key_totals, int n_keys, WsStatus* st,
+                                                     FusedKeys fk) {
     __shared__ uint32_t sm[8];
     __shared__ uint32_t h[HIST ? kFusedKeys : 1];
+    __shared__ int s_last;
     if (HIST) {
         for (int k = threadIdx.x; k < n_keys; k += 256) h[k] = 0;
         __syncthreads();
     }
-    const long long chunk = (n_rec + gridDim.x - 1) / gridDim.x;
-    const long long begin = min(n_rec, (long long)blockIdx.x * chunk);
-    const long long end = min(n_rec, begin + chunk);
+    const long long begin = min(n_rec, (long long)blockIdx.x * per_block);
+    const long long end = min(n_rec, begin + per_block);
     unsigned long long running = partials[blockIdx.x];
     for (long long base = begin; base < end; base += 256) {
         const long long r = base + threadIdx.x;
@@ -137,67 +173,80 @@ __global__ void __launch_bounds__(256) k_emit_chunks(Op op, long long n_rec, con
         }
         running += tot;
     }
-    if (HIST) {
-        __syncthreads();
-        for (int k = threadIdx.x; k < n_keys; k += 256) {
-            const uint32_t cnt = h[k];
-            hist[(size_t)k * gridDim.x + blockIdx.x] = cnt;
-            if (cnt) atomicAdd(&key_totals[k], cnt);
-        }
+    if (!HIST) return;
+    __syncthreads();
+    for (int k = threadIdx.x; k < n_keys; k += 256) {
+        const uint32_t cnt = h[k];
+        hist[(size_t)k * gridDim.x + blockIdx.x] = cnt;
+        if (cnt) atomicAdd(&key_totals[k], cnt);
     }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&st->blocks_done, 1ull) == 2ull * gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    // key bases and item bases: exclusive scans over the keys (<= 1024, 4 per thread)
+    const int t = threadIdx.x;
+    uint32_t tk[4], nc[4], sum = 0, isum = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int k = 4 * t + q;
+        tk[q] = k < n_keys ? __ldcg(key_totals + k) : 0u;
+        nc[q] = k < n_keys ? (tk[q] ? (tk[q] + fk.chunk - 1) / fk.chunk : 1u) : 0u;
+        sum += tk[q];
+        isum += nc[q];
+    }
+    uint32_t tot, itot;
+    uint32_t base = block_exclusive_scan_256(sum, sm, &tot);
+    uint32_t ibase = block_exclusive_scan_256(isum, sm, &itot);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int k = 4 * t + q;
+        if (k < n_keys) {
+            key_totals[k] = base;  // the key's first entry, for the offsets pass
+            fk.ranges[k] = tk[q] ? make_uint2(base, base + tk[q]) : make_uint2(0u, 0u);
+            fk.key_done[k] = 0;
+            fk.item_off[k] = ibase;
+            for (uint32_t c = 0; c < nc[q]; ++c)
+                if (ibase + c < fk.items_cap) fk.items[ibase + c] = ((uint64_t)(uint32_t)k << 32) | c;
+        }
+        base += tk[q];
+        ibase += nc[q];
+    }
+    if (t == 0) fk.item_st->n_keys = itot;
 }
 
-// One warp per key k: the scatter offset of (k, emit block b) = entries of
-// smaller keys + entries of key k in earlier blocks (hist rewritten in place),
-// the key's range [start, end) ([0, 0) when empty), its first work item and its
-// max(1, ceil(n / chunk)) items (an empty key's one item writes its zero output),
-// a cleared chunk arrival counter; the last key's warp writes the item count.
+// One warp per key k: the scatter offset of (k, emit block b) = the key's first
+// entry + entries of key k in earlier blocks (hist rewritten in place).
+constexpr int kMaxRowChunks = (kMaxListBlocks + 31) / 32;
 static __global__ void __launch_bounds__(256) k_fused_offsets(uint32_t* __restrict__ hist,
-                                                              const uint32_t* __restrict__ key_totals, int nb,
-                                                              int n_keys, uint32_t chunk, uint2* __restrict__ ranges,
-                                                              uint32_t* __restrict__ key_done,
-                                                              uint32_t* __restrict__ item_off,
-                                                              uint64_t* __restrict__ items,
-                                                              unsigned long long items_cap,
-                                                              WsStatus* __restrict__ item_st) {
+                                                              const uint32_t* __restrict__ key_first, int nb,
+                                                              int n_keys) {
     const int lane = threadIdx.x & 31;
     const int k = blockIdx.x * 8 + (threadIdx.x >> 5);
     if (k >= n_keys) return;
-    uint32_t base = 0, ibase = 0;
-    for (int q = lane; q < k; q += 32) {
-        const uint32_t t = key_totals[q];
-        base += t;
-        ibase += t ? (t + chunk - 1) / chunk : 1u;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        base += __shfl_xor_sync(0xffffffffu, base, o);
-        ibase += __shfl_xor_sync(0xffffffffu, ibase, o);
-    }
-    uint32_t running = base;
     uint32_t* row = hist + (size_t)k * nb;
-    for (int c = 0; c < nb; c += 32) {
-        const int idx = c + lane;
-        const uint32_t v = idx < nb ? row[idx] : 0u;
-        uint32_t x = v;
+    uint32_t v[kMaxRowChunks];
+#pragma unroll
+    for (int c = 0; c < kMaxRowChunks; ++c) {
+        const int idx = c * 32 + lane;
+        v[c] = idx < nb ? row[idx] : 0u;
+    }
+    uint32_t running = key_first[k];
+#pragma unroll
+    for (int c = 0; c < kMaxRowChunks; ++c) {
+        if (c * 32 >= nb) break;
+        uint32_t x = v[c];
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
             if (lane >= o) x += y;
         }
-        if (idx < nb) row[idx] = running + x - v;
+        const int idx = c * 32 + lane;
+        if (idx < nb) row[idx] = running + x - v[c];
         running += __shfl_sync(0xffffffffu, x, 31);
     }
-    const uint32_t total = key_totals[k];
-    const uint32_t nch = total ? (total + chunk - 1) / chunk : 1u;
-    if (lane == 0) {
-        ranges[k] = total ? make_uint2(base, base + total) : make_uint2(0u, 0u);
-        key_done[k] = 0;
-        item_off[k] = ibase;
-        if (k == n_keys - 1) item_st->n_keys = (unsigned long long)ibase + nch;
-    }
-    for (uint32_t c = lane; c < nch; c += 32)
-        if (ibase + c < items_cap) items[ibase + c] = ((uint64_t)(uint32_t)k << 32) | c;
 }
 
 // One block per emit block: its entries [start_b, start_{b+1}) (clipped to the
@@ -255,39 +304,49 @@ inline int list_sort_passes(long long n_slots) {
     return fused_lists(n_slots) ? 1 : (bits_for(n_slots) + kRadixBits - 1) / kRadixBits;
 }
 
-// Emit, sort and range the lists of n_slots keys; returns the buffer (a or b)
-// holding the sorted entries and adds the kernel launches to *launches.  The
-// status block must have been cleared by the caller.  key_done (one chunk
-// arrival counter per key) must lie between the ranges and the item status
-// block, so that the general path's clear of that span zeroes it; the fused path
-// zeroes it and gives every empty key one work item, the general path gives
-// empty keys none (their outputs must be cleared by the caller).
+// The count the projection kernel of a list build must make (see list_count_tail).
+inline ListCount list_count(long long n_slots, unsigned long long* partials, WsStatus* st, long long cap,
+                            uint32_t* scratch) {
+    return ListCount{partials, st, (unsigned long long)cap,
+                     fused_lists(n_slots) ? scratch + (size_t)kRadix * kSortBlocksMax : nullptr, (int)n_slots};
+}
+
+// After the projection kernel (launched with list_blocking(n_rec) and
+// list_count(...) on a cleared status block): emit, sort and range the lists of
+// n_slots keys; returns the buffer (a or b) holding the sorted entries and adds
+// the kernel launches to *launches.  key_done (one chunk arrival counter per key)
+// must lie between the ranges and the item status block, so that the general
+// path's clear of that span zeroes it; the fused path zeroes it and gives every
+// empty key one work item, the general path gives empty keys none (their outputs
+// must be cleared by the caller).
 template <class Op>
 uint64_t* build_lists(const Op& op, long long n_rec, long long n_slots, unsigned long long* partials, WsStatus* st,
                       uint64_t* a, uint64_t* b, uint32_t* scratch, long long cap, uint2* ranges, uint32_t* key_done,
                       WsStatus* item_st, uint32_t* item_off, uint64_t* items, long long items_cap, int chunk,
                       ListProf prof, cudaStream_t s, int* launches) {
     const unsigned long long ucap = (unsigned long long)cap;
+    const ListBlocking lb = list_blocking(n_rec);
+    const long long per_block = 256ll * lb.per_thread;
     if (fused_lists(n_slots)) {
         uint32_t* hist = scratch;
         uint32_t* totals = scratch + (size_t)kRadix * kSortBlocksMax;
         const int nk = (int)n_slots;
+        const FusedKeys fk{(uint32_t)chunk, ranges, key_done, item_off, items, (unsigned long long)items_cap,
+                           item_st};
         prof_begin(prof.emit, s);
-        k_count_chunks<Op><<<kFusedBlocks, 256, 0, s>>>(op, n_rec, partials, st, ucap, totals, nk);
-        k_emit_chunks<Op, true><<<kFusedBlocks, 256, 0, s>>>(op, n_rec, partials, a, ucap, hist, totals, nk);
+        k_emit_chunks<Op, true><<<lb.blocks, 256, 0, s>>>(op, n_rec, per_block, partials, a, ucap, hist, totals, nk,
+                                                          st, fk);
         prof_end(prof.emit, s);
         prof_begin(prof.sort, s);
-        k_fused_offsets<<<(nk + 7) / 8, 256, 0, s>>>(hist, totals, kFusedBlocks, nk, (uint32_t)chunk, ranges,
-                                                      key_done, item_off, items, (unsigned long long)items_cap,
-                                                      item_st);
-        k_fused_scatter<<<kFusedBlocks, 256, 0, s>>>(a, b, hist, partials, st, nk);
+        k_fused_offsets<<<(nk + 7) / 8, 256, 0, s>>>(hist, totals, lb.blocks, nk);
+        k_fused_scatter<<<lb.blocks, 256, 0, s>>>(a, b, hist, partials, st, nk);
         prof_end(prof.sort, s);
-        *launches += 4;
+        *launches += 3;
         return b;
     }
     prof_begin(prof.emit, s);
-    k_count_chunks<Op><<<kScanBlocks, 256, 0, s>>>(op, n_rec, partials, st, ucap, nullptr, 0);
-    k_emit_chunks<Op, false><<<kScanBlocks, 256, 0, s>>>(op, n_rec, partials, a, ucap, nullptr, nullptr, 0);
+    k_emit_chunks<Op, false><<<lb.blocks, 256, 0, s>>>(op, n_rec, per_block, partials, a, ucap, nullptr, nullptr, 0,
+                                                       st, FusedKeys{});
     prof_end(prof.emit, s);
     prof_begin(prof.sort, s);
     uint64_t* sorted = radix_sort_u64(a, b, scratch, st, bits_for(n_slots), sort_blocks_for(cap), s);
@@ -295,7 +354,7 @@ uint64_t* build_lists(const Op& op, long long n_rec, long long n_slots, unsigned
     prof_begin(prof.ranges, s);
     build_ranges_items(sorted, st, ranges, n_slots, item_st, item_off, items, items_cap, chunk, s);
     prof_end(prof.ranges, s);
-    *launches += 2 + 3 * list_sort_passes(n_slots) + 1;
+    *launches += 1 + 3 * list_sort_passes(n_slots) + 1;
     return sorted;
 }
 

@@ -345,7 +345,9 @@ r2g_status r2g::projection_loss_impl(int32_t V, int32_t H, int32_t W, const floa
     cudaGetDevice(&dev);
     if (dev < 0 || dev >= 64 || !smem_set[dev]) {
         if (cudaFuncSetAttribute(k_ssim, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SsimSmem)) !=
-            cudaSuccess)
+                cudaSuccess ||
+            cudaFuncSetAttribute(k_ssim, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared) != cudaSuccess)
             return fail(R2G_E_CUDA, "r2g_projection_loss: shared memory attribute (%s)",
                         cudaGetErrorString(cudaGetLastError()));
         if (dev >= 0 && dev < 64) smem_set[dev] = true;

@@ -213,23 +213,13 @@ constexpr float kTwoPi = 6.283185307179586f;
 
 // ------------------------------------------------------------------ K1: project
 
-// view_sel (optional, device): view v of this call is views[view_sel[v]].
-__global__ void __launch_bounds__(256) k_project(Params G, const float* __restrict__ views,
-                                                 const int* __restrict__ view_sel, CamF cam, float Q, int TW, int TH,
-                                                 long long M, long long n_rec, float4* __restrict__ rec,
-                                                 uint2* __restrict__ rect, float* __restrict__ proj_out,
-                                                 int* __restrict__ rect_out, WsStatus* __restrict__ st_clear,
-                                                 float4* __restrict__ mom_clear) {
-    // st_clear / mom_clear (optional): this call's status block and every record's
-    // backward moment slot start at zero
-    if (st_clear && blockIdx.x == 0 && threadIdx.x < sizeof(WsStatus) / 8)
-        reinterpret_cast<unsigned long long*>(st_clear)[threadIdx.x] = 0ull;
-    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n_rec) return;
-    if (mom_clear) {
-        mom_clear[2 * r] = make_float4(0.f, 0.f, 0.f, 0.f);
-        mom_clear[2 * r + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
+// One record of k_project: the stated FP32 projection, the splat record and the
+// tile rectangle (or the debug outputs); returns the record's tile count.
+__device__ __forceinline__ uint32_t project_one(const Params& G, const float* __restrict__ views,
+                                                const int* __restrict__ view_sel, const CamF& cam, float Q, int TW,
+                                                int TH, long long M, long long r, float4* __restrict__ rec,
+                                                uint2* __restrict__ rect, float* __restrict__ proj_out,
+                                                int* __restrict__ rect_out) {
     const long long v = r / M, i = r - v * M;
     const float* view = views + 12 * (view_sel ? (long long)view_sel[v] : v);
     float p[3], s[3], q[4];
@@ -284,6 +274,31 @@ __global__ void __launch_bounds__(256) k_project(Params G, const float* __restri
         o2[2] = b.ok ? b.r0 : 0;
         o2[3] = b.ok ? b.r1 : 0;
     }
+    return b.ok ? (uint32_t)((b.c1 / TW - b.c0 / TW + 1) * (b.r1 / TH - b.r0 / TH + 1)) : 0u;
+}
+
+// view_sel (optional, device): view v of this call is views[view_sel[v]].  Each
+// thread projects per_thread records, r = ((block * per_thread) + l) * 256 + thread,
+// so that a block covers the records of one list block.  mom_clear (optional):
+// every record's backward moment slot starts at zero.  lc.partials (optional):
+// count the blocks' tile entries for the list build (list_count_tail).
+__global__ void __launch_bounds__(256) k_project(Params G, const float* __restrict__ views,
+                                                 const int* __restrict__ view_sel, CamF cam, float Q, int TW, int TH,
+                                                 long long M, long long n_rec, int per_thread,
+                                                 float4* __restrict__ rec, uint2* __restrict__ rect,
+                                                 float* __restrict__ proj_out, int* __restrict__ rect_out,
+                                                 float4* __restrict__ mom_clear, ListCount lc) {
+    unsigned long long cnt = 0;
+    for (int l = 0; l < per_thread; ++l) {
+        const long long r = ((long long)blockIdx.x * per_thread + l) * 256 + threadIdx.x;
+        if (r >= n_rec) continue;
+        if (mom_clear) {
+            mom_clear[2 * r] = make_float4(0.f, 0.f, 0.f, 0.f);
+            mom_clear[2 * r + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        cnt += project_one(G, views, view_sel, cam, Q, TW, TH, M, r, rec, rect, proj_out, rect_out);
+    }
+    if (lc.partials) list_count_tail(lc, cnt);
 }
 
 // ------------------------------------------------------------------ K2: tile keys
@@ -953,8 +968,8 @@ R2G_API r2g_status r2g_project(int64_t M, const float* mean, const float* scale,
     const long long n = (long long)M * V;
     Params G{mean, scale, quat, rho};
     k_project<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(G, views, nullptr, camf(cam), opts->Q, opts->tile_w,
-                                                                opts->tile_h, M, n, nullptr, nullptr, proj, rect,
-                                                                nullptr, nullptr);
+                                                                opts->tile_h, M, n, 1, nullptr, nullptr, proj, rect,
+                                                                nullptr, ListCount{});
     note_launches(1);
     return check_launch("r2g_project");
 }
@@ -987,14 +1002,18 @@ r2g_status r2g::rasterize_impl(int64_t M, const float* mean, const float* scale,
     uint32_t* key_done = reinterpret_cast<uint32_t*>(base + L.key_done);
     uint64_t* items = reinterpret_cast<uint64_t*>(base + T.items);
     float* partial = reinterpret_cast<float*>(base + T.partial);
+    // the status block (with the arrival counters of the list passes) starts cleared
+    cudaMemsetAsync(st, 0, sizeof(WsStatus), stream);
     // the general list path gives empty tiles no work item: their pixels stay zero
     if (!fused_lists(L.n_tiles)) cudaMemsetAsync(image, 0, sizeof(float) * (size_t)V * cam->H * cam->W, stream);
     Params G{mean, scale, quat, rho};
     const CamF cf = camf(cam);
     prof_begin(P_PROJECT, stream);
-    k_project<<<(unsigned)((L.n_rec + 255) / 256), 256, 0, stream>>>(
-        G, views, view_sel, cf, opts->Q, opts->tile_w, opts->tile_h, M, L.n_rec, rec, rect, nullptr, nullptr, st,
-        reinterpret_cast<float4*>(base + L.mom));
+    const ListBlocking lb = list_blocking(L.n_rec);
+    k_project<<<(unsigned)lb.blocks, 256, 0, stream>>>(G, views, view_sel, cf, opts->Q, opts->tile_w, opts->tile_h, M,
+                                                        L.n_rec, lb.per_thread, rec, rect, nullptr, nullptr,
+                                                        reinterpret_cast<float4*>(base + L.mom),
+                                                        list_count(L.n_tiles, partials, st, cap, scratch));
     prof_end(P_PROJECT, stream);
     TileOp op{rect, M, L.tiles_x, L.tiles_per_view};
     int launches = 0;

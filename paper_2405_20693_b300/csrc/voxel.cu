@@ -110,17 +110,11 @@ __device__ __forceinline__ void precision(const float R[3][3], const float s[3],
 // ------------------------------------------------------------------ records + brick bound
 
 // origin_dev (optional, device): grid g's origin is origin_dev[3g .. 3g+2].
-__global__ void __launch_bounds__(256) k_vox_project(Params G, const __grid_constant__ Grids grids,
-                                                     const float* __restrict__ origin_dev, float Q3, long long M,
-                                                     float4* __restrict__ rec, uint4* __restrict__ rect,
-                                                     WsStatus* __restrict__ st_clear, float4* __restrict__ mom_clear) {
-    // this call's status block and every record's backward moment slot start at zero
-    if (blockIdx.x == 0 && threadIdx.x < sizeof(WsStatus) / 8)
-        reinterpret_cast<unsigned long long*>(st_clear)[threadIdx.x] = 0ull;
-    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= M * grids.G) return;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) mom_clear[3 * r + k] = make_float4(0.f, 0.f, 0.f, 0.f);
+// One (grid, Gaussian) record: returns its brick count.
+__device__ __forceinline__ uint32_t vox_project_one(const Params& G, const Grids& grids,
+                                                    const float* __restrict__ origin_dev, float Q3, long long M,
+                                                    long long r, float4* __restrict__ rec,
+                                                    uint4* __restrict__ rect) {
     const int g = (int)(r / M);
     const long long i = r - (long long)g * M;
     const GridF& gf = grids.g[g];
@@ -167,6 +161,30 @@ __global__ void __launch_bounds__(256) k_vox_project(Params G, const __grid_cons
     }
     rc.w = 0;
     rect[r] = rc;
+    return ok ? (uint32_t)((hi[0] / kB - lo[0] / kB + 1) * (hi[1] / kB - lo[1] / kB + 1) *
+                           (hi[2] / kB - lo[2] / kB + 1))
+              : 0u;
+}
+
+// Each thread projects per_thread records, r = ((block * per_thread) + l) * 256 +
+// thread, so that a block covers the records of one list block; every record's
+// backward moment slot starts at zero; the blocks' brick entries are counted for
+// the list build (list_count_tail).
+__global__ void __launch_bounds__(256) k_vox_project(Params G, const __grid_constant__ Grids grids,
+                                                     const float* __restrict__ origin_dev, float Q3, long long M,
+                                                     int per_thread, float4* __restrict__ rec,
+                                                     uint4* __restrict__ rect, float4* __restrict__ mom_clear,
+                                                     ListCount lc) {
+    unsigned long long cnt = 0;
+    const long long n_rec = M * grids.G;
+    for (int l = 0; l < per_thread; ++l) {
+        const long long r = ((long long)blockIdx.x * per_thread + l) * 256 + threadIdx.x;
+        if (r >= n_rec) continue;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) mom_clear[3 * r + k] = make_float4(0.f, 0.f, 0.f, 0.f);
+        cnt += vox_project_one(G, grids, origin_dev, Q3, M, r, rec, rect);
+    }
+    list_count_tail(lc, cnt);
 }
 
 // The emit needs per-grid brick numbering; it gets the table by value.
@@ -707,12 +725,16 @@ r2g_status voxelize_impl(int64_t M, const float* mean, const float* scale, const
     uint32_t* key_done = reinterpret_cast<uint32_t*>(base + L.key_done);
     uint64_t* items = reinterpret_cast<uint64_t*>(base + T.items);
     float* partial = reinterpret_cast<float*>(base + T.partial);
+    // the status block (with the arrival counters of the list passes) starts cleared
+    cudaMemsetAsync(st, 0, sizeof(WsStatus), stream);
     // the general list path gives empty bricks no work item: their voxels stay zero
     if (!fused_lists(L.n_bricks)) cudaMemsetAsync(vol, 0, sizeof(float) * (size_t)L.n_vox, stream);
     Params P{mean, scale, quat, rho};
     prof_begin(P_VOX_PROJECT, stream);
-    k_vox_project<<<(unsigned)((L.n_rec + 255) / 256), 256, 0, stream>>>(
-        P, gr, origin_dev, Q3, M, rec, rect, st, reinterpret_cast<float4*>(base + L.mom));
+    const ListBlocking lb = list_blocking(L.n_rec);
+    k_vox_project<<<(unsigned)lb.blocks, 256, 0, stream>>>(P, gr, origin_dev, Q3, M, lb.per_thread, rec, rect,
+                                                            reinterpret_cast<float4*>(base + L.mom),
+                                                            list_count(L.n_bricks, partials, st, cap, scratch));
     prof_end(P_VOX_PROJECT, stream);
     BrickEmitOp op;
     op.rect = rect;
