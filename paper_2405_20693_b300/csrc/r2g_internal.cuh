@@ -116,17 +116,24 @@ inline int bits_for(int64_t n_slots) {
 r2g_status rasterize_impl(int64_t M, const float* mean, const float* scale, const float* quat, const float* rho,
                           int32_t V, const float* views, const int* view_sel, const r2g_camera* cam,
                           const r2g_raster_opts* opts, float* image, void* ws, size_t ws_bytes, cudaStream_t stream);
+// The raster backward in two parts: the per-record moments and the chain rule
+// (added to dmean .. drho; with `adam` set, added to adam->grad and the Adam step
+// of every Gaussian taken in the same kernel instead, dmean .. drho unused).
+struct AdamState;
+constexpr int kRasterBwdMoments = 1, kRasterBwdChain = 2;
 r2g_status rasterize_backward_impl(int64_t M, const float* mean, const float* scale, const float* quat,
                                    const float* rho, int32_t V, const float* views, const int* view_sel,
                                    const r2g_camera* cam, const r2g_raster_opts* opts, const float* dimage,
                                    float* dmean, float* dscale, float* dquat, float* drho, void* ws, size_t ws_bytes,
-                                   cudaStream_t stream);
+                                   cudaStream_t stream, int parts = kRasterBwdMoments | kRasterBwdChain,
+                                   const AdamState* adam = nullptr);
 r2g_status voxelize_impl(int64_t M, const float* mean, const float* scale, const float* quat, const float* rho,
                          int32_t G, const r2g_grid* grids, const float* origin_dev, float Q3, float* vol, void* ws,
                          size_t ws_bytes, cudaStream_t stream, bool count);
 // The voxel backward in two parts: the per-record moments (dvol -> moments, in the
-// workspace) and the chain rule (moments -> gradients, added to dmean .. drho).
-constexpr int kVoxBwdMoments = 1, kVoxBwdChain = 2;
+// workspace) and the chain rule (moments -> gradients, added to dmean .. drho, or
+// with kVoxBwdAssign written over them).
+constexpr int kVoxBwdMoments = 1, kVoxBwdChain = 2, kVoxBwdAssign = 4;
 r2g_status voxelize_backward_impl(int64_t M, const float* mean, const float* scale, const float* quat,
                                   const float* rho, int32_t G, const r2g_grid* grids, float Q3, const float* dvol,
                                   float* dmean, float* dscale, float* dquat, float* drho, void* ws, size_t ws_bytes,

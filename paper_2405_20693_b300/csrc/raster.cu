@@ -28,6 +28,7 @@
 //                  projection to d mean, d scale, d quat, d rho.
 #include <math.h>
 
+#include "adam_math.cuh"
 #include "emit.cuh"
 #include "r2g_internal.cuh"
 
@@ -655,12 +656,16 @@ __device__ __forceinline__ void quat_grad(const float qn[4], float qnorm, const 
     dq[3] = (dz - z * dot) / qnorm;
 }
 
+// ADAM: instead of adding the gradients to dmean .. drho, add them to the
+// gradient already in adam.grad and take the Adam step of the Gaussian's eleven
+// parameters (every Gaussian, with or without moments).
+template <bool ADAM>
 __global__ void __launch_bounds__(128) k_project_bwd(Params G, const float* __restrict__ views,
                                                      const int* __restrict__ view_sel, CamF cam, float Q,
                                                      long long M, int V, const float4* __restrict__ rec,
                                                      float4* __restrict__ mom, float* __restrict__ dmean,
                                                      float* __restrict__ dscale, float* __restrict__ dquat,
-                                                     float* __restrict__ drho) {
+                                                     float* __restrict__ drho, AdamState adam) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= M) return;
     float p[3], s[3], q[4];
@@ -779,9 +784,13 @@ __global__ void __launch_bounds__(128) k_project_bwd(Params G, const float* __re
 #pragma unroll
         for (int k = 0; k < 3; ++k) gp[k] += view[k] * du[0] + view[3 + k] * du[1] + view[6 + k] * du[2];
     }
+    float gq[4] = {0.f, 0.f, 0.f, 0.f};
+    if (have_rot) quat_grad(P.qn, P.qnorm, gR, gq);
+    if (ADAM) {
+        adam_gaussian(adam, i, gq, gp, gs, grho);
+        return;
+    }
     if (!have_rot) return;
-    float gq[4];
-    quat_grad(P.qn, P.qnorm, gR, gq);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         dmean[3 * i + k] += gp[k];
@@ -1043,11 +1052,11 @@ r2g_status r2g::rasterize_backward_impl(int64_t M, const float* mean, const floa
                                         const float* rho, int32_t V, const float* views, const int* view_sel,
                                         const r2g_camera* cam, const r2g_raster_opts* opts, const float* dimage,
                                         float* dmean, float* dscale, float* dquat, float* drho, void* ws,
-                                        size_t ws_bytes, cudaStream_t stream) {
+                                        size_t ws_bytes, cudaStream_t stream, int parts, const AdamState* adam) {
     r2g_status e = check_args(M, V, cam, opts);
     if (e) return e;
-    if (!mean || !scale || !quat || !rho || !views || !dimage || !dmean || !dscale || !dquat || !drho || !ws)
-        return fail(R2G_E_INVAL, "NULL pointer");
+    if (!mean || !scale || !quat || !rho || !views || !dimage || !ws) return fail(R2G_E_INVAL, "NULL pointer");
+    if (!adam && (!dmean || !dscale || !dquat || !drho)) return fail(R2G_E_INVAL, "NULL gradient pointer");
     if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(R2G_E_INVAL, "workspace must be 256-byte aligned");
     if (reinterpret_cast<uintptr_t>(quat) % 16) return fail(R2G_E_INVAL, "quat must be 16-byte aligned");
     const RasterLayout L = raster_layout(M, V, cam, opts);
@@ -1063,16 +1072,26 @@ r2g_status r2g::rasterize_backward_impl(int64_t M, const float* mean, const floa
     const uint64_t* items = reinterpret_cast<const uint64_t*>(base + T.items);
     const WsStatus* item_st = reinterpret_cast<const WsStatus*>(base + L.item_status);
     const float Tq = -0.5f * kLog2e * opts->Q;
-    prof_begin(P_SPLAT_BWD, stream);
-    launch_bwd(opts->tile_w, opts->tile_h, rec, ranges, sorted, items, item_st, T.icap, M, L, cam->H, cam->W, Tq,
-               dimage, mom, stream);
-    prof_end(P_SPLAT_BWD, stream);
-    Params G{mean, scale, quat, rho};
-    prof_begin(P_PROJECT_BWD, stream);
-    k_project_bwd<<<(unsigned)((M + 127) / 128), 128, 0, stream>>>(G, views, view_sel, camf(cam), opts->Q, M, V,
-                                                                    rec, mom, dmean, dscale, dquat, drho);
-    prof_end(P_PROJECT_BWD, stream);
-    note_launches(2);
+    if (parts & kRasterBwdMoments) {
+        prof_begin(P_SPLAT_BWD, stream);
+        launch_bwd(opts->tile_w, opts->tile_h, rec, ranges, sorted, items, item_st, T.icap, M, L, cam->H, cam->W,
+                   Tq, dimage, mom, stream);
+        prof_end(P_SPLAT_BWD, stream);
+        note_launches(1);
+    }
+    if (parts & kRasterBwdChain) {
+        Params G{mean, scale, quat, rho};
+        const unsigned grid = (unsigned)((M + 127) / 128);
+        prof_begin(P_PROJECT_BWD, stream);
+        if (adam)
+            k_project_bwd<true><<<grid, 128, 0, stream>>>(G, views, view_sel, camf(cam), opts->Q, M, V, rec, mom,
+                                                          nullptr, nullptr, nullptr, nullptr, *adam);
+        else
+            k_project_bwd<false><<<grid, 128, 0, stream>>>(G, views, view_sel, camf(cam), opts->Q, M, V, rec, mom,
+                                                           dmean, dscale, dquat, drho, AdamState{});
+        prof_end(P_PROJECT_BWD, stream);
+        note_launches(1);
+    }
     return check_launch("r2g_rasterize_backward");
 }
 

@@ -4,17 +4,20 @@
 // replayed: rasterize the selected view, L1 + D-SSIM against its measurement,
 // voxelize the TV patch at the selected origin, TV, both backward passes, Adam.
 //
-// The projection branch (rasterize, loss, raster backward) and the TV branch
-// (voxelize, TV, voxel moments) share nothing until their chain rules add into
-// the same gradient arrays, so the TV branch runs on a side stream forked from
-// the caller's stream and joined before the voxel chain rule; the two branches'
-// latency-bound kernels then overlap.  Each caller stream gets its own side
+// The projection branch (rasterize, loss, raster moments) and the TV branch
+// (voxelize, TV, voxel moments and chain rule) share nothing until the gradients
+// are summed, so the TV branch runs on a side stream forked from the caller's
+// stream; it writes its gradient (assigning, so nothing needs clearing) and is
+// joined before the raster chain rule, which adds its own gradient in registers
+// and takes the Adam step of each Gaussian in the same kernel.  The two
+// branches' latency-bound kernels overlap.  Each caller stream gets its own side
 // stream and event pair (created on first use, kept for the process), so calls
 // on different streams -- the branches of a batched round -- stay independent.
 #include <map>
 #include <mutex>
 #include <utility>
 
+#include "adam_math.cuh"
 #include "r2g_internal.cuh"
 
 using namespace r2g;
@@ -87,7 +90,8 @@ R2G_API r2g_status r2g_train_step(const r2g_job* job, const r2g_round_entry* ent
     if (!e_tv) e_tv = r2g_tv3d(1, J.D, J.vol, J.lambda_tv, J.loss + 1, J.dvol, J.tv_ws, J.tv_ws_bytes, tv);
     if (!e_tv)
         e_tv = voxelize_backward_impl(M, mean, scale, quat, rho, 1, &grid, J.Q3, J.dvol, dmean, dscale, dquat, drho,
-                                      J.voxel_ws, J.voxel_ws_bytes, tv, kVoxBwdMoments);
+                                      J.voxel_ws, J.voxel_ws_bytes, tv,
+                                      kVoxBwdMoments | kVoxBwdChain | kVoxBwdAssign);
     r2g_status e_px = rasterize_impl(M, mean, scale, quat, rho, 1, J.views, view_sel, &J.cam, &J.ropts, J.image,
                                      J.raster_ws, J.raster_ws_bytes, stream);
     if (!e_px)
@@ -95,16 +99,19 @@ R2G_API r2g_status r2g_train_step(const r2g_job* job, const r2g_round_entry* ent
                                     J.loss_ws, J.loss_ws_bytes, stream);
     if (!e_px)
         e_px = rasterize_backward_impl(M, mean, scale, quat, rho, 1, J.views, view_sel, &J.cam, &J.ropts, J.dimage,
-                                       dmean, dscale, dquat, drho, J.raster_ws, J.raster_ws_bytes, stream);
+                                       dmean, dscale, dquat, drho, J.raster_ws, J.raster_ws_bytes, stream,
+                                       kRasterBwdMoments);
     // join (also on error, so that no captured branch is left open)
     if (cudaEventRecord(side->join, tv) != cudaSuccess || cudaStreamWaitEvent(stream, side->join, 0) != cudaSuccess)
         return fail(R2G_E_CUDA, "r2g_train_step: join failed (%s)", cudaGetErrorString(cudaGetLastError()));
     if (e_tv) return e_tv;
     if (e_px) return e_px;
-    if ((e = voxelize_backward_impl(M, mean, scale, quat, rho, 1, &grid, J.Q3, J.dvol, dmean, dscale, dquat, drho,
-                                    J.voxel_ws, J.voxel_ws_bytes, stream, kVoxBwdChain)))
-        return e;
-    return adam_impl(M, J.raw, J.act, J.grad, J.adam_m, J.adam_v, 0, &entry->it, &J.adam, stream);
+    if (J.adam.total_iters < 1 || !(J.adam.final_factor > 0.f))
+        return fail(R2G_E_INVAL, "r2g_train_step: bad Adam options");
+    const AdamState adam{J.raw, J.act, J.adam_m, J.adam_v, J.grad, adam_args(M, &J.adam, 0, &entry->it)};
+    return rasterize_backward_impl(M, mean, scale, quat, rho, 1, J.views, view_sel, &J.cam, &J.ropts, J.dimage,
+                                   dmean, dscale, dquat, drho, J.raster_ws, J.raster_ws_bytes, stream,
+                                   kRasterBwdChain, &adam);
 }
 
 R2G_API r2g_status r2g_upload_round(r2g_round_entry* dst, const r2g_round_entry* src, int32_t n, r2g_stream stream) {

@@ -518,6 +518,9 @@ __device__ __forceinline__ void quat_grad(const float qn[4], float qnorm, const 
     dq[3] = (dz - z * dot) / qnorm;
 }
 
+// ASSIGN: write the gradients (zeros where the Gaussian has no moments) instead
+// of adding to them.
+template <bool ASSIGN>
 __global__ void __launch_bounds__(128) k_vox_chain(Params G, const __grid_constant__ Grids grids, long long M,
                                                    float4* __restrict__ mom, float* __restrict__ dmean,
                                                    float* __restrict__ dscale, float* __restrict__ dquat,
@@ -560,7 +563,16 @@ __global__ void __launch_bounds__(128) k_vox_chain(Params G, const __grid_consta
 #pragma unroll
             for (int k = 0; k < 3; ++k) dP[j][k] += -0.5f * rho * S2[j][k] * v[j] * v[k];
     }
-    if (!any) return;
+    if (!any) {
+        if (ASSIGN) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) dmean[3 * i + k] = dscale[3 * i + k] = 0.f;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) dquat[4 * i + k] = 0.f;
+            drho[i] = 0.f;
+        }
+        return;
+    }
     // P = N N^T, N = R diag(1/s): dN = (dP + dP^T) N
     float gR[3][3], gs[3] = {0.f, 0.f, 0.f};
 #pragma unroll
@@ -577,12 +589,12 @@ __global__ void __launch_bounds__(128) k_vox_chain(Params G, const __grid_consta
     quat_grad(qn, qnorm, gR, gq);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        dmean[3 * i + k] += gp[k];
-        dscale[3 * i + k] += gs[k];
+        dmean[3 * i + k] = ASSIGN ? gp[k] : dmean[3 * i + k] + gp[k];
+        dscale[3 * i + k] = ASSIGN ? gs[k] : dscale[3 * i + k] + gs[k];
     }
 #pragma unroll
-    for (int k = 0; k < 4; ++k) dquat[4 * i + k] += gq[k];
-    drho[i] += grho;
+    for (int k = 0; k < 4; ++k) dquat[4 * i + k] = ASSIGN ? gq[k] : dquat[4 * i + k] + gq[k];
+    drho[i] = ASSIGN ? grho : drho[i] + grho;
 }
 
 // ------------------------------------------------------------------ host side
@@ -808,7 +820,12 @@ r2g_status voxelize_backward_impl(int64_t M, const float* mean, const float* sca
     if (parts & kVoxBwdChain) {
         Params P{mean, scale, quat, rho};
         prof_begin(P_VOX_CHAIN, stream);
-        k_vox_chain<<<(unsigned)((M + 127) / 128), 128, 0, stream>>>(P, gr, M, mom, dmean, dscale, dquat, drho);
+        if (parts & kVoxBwdAssign)
+            k_vox_chain<true><<<(unsigned)((M + 127) / 128), 128, 0, stream>>>(P, gr, M, mom, dmean, dscale, dquat,
+                                                                              drho);
+        else
+            k_vox_chain<false><<<(unsigned)((M + 127) / 128), 128, 0, stream>>>(P, gr, M, mom, dmean, dscale, dquat,
+                                                                               drho);
         prof_end(P_VOX_CHAIN, stream);
         note_launches(1);
     }
