@@ -180,9 +180,12 @@ __global__ void __launch_bounds__(256) k_emit_chunks(Op op, long long n_rec, lon
         hist[(size_t)k * gridDim.x + blockIdx.x] = cnt;
         if (cnt) atomicAdd(&key_totals[k], cnt);
     }
-    __threadfence();
+    // the barrier orders every thread's stores before thread 0's release fence
     __syncthreads();
-    if (threadIdx.x == 0) s_last = atomicAdd(&st->blocks_done, 1ull) == 2ull * gridDim.x - 1;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(&st->blocks_done, 1ull) == 2ull * gridDim.x - 1;
+    }
     __syncthreads();
     if (!s_last) return;
     __threadfence();

@@ -443,9 +443,12 @@ __global__ void __launch_bounds__(FwdShape<TW, TH>::NT) k_splat_fwd(const float4
         float* p = partial + it * (size_t)(TW * TH) + ly * TW + lx;
 #pragma unroll
         for (int k = 0; k < PX; ++k) p[k] = acc[k];
-        __threadfence();
+        // the barrier orders every thread's stores before thread 0's release fence
         __syncthreads();
-        if (threadIdx.x == 0) s_last = atomicAdd(&key_done[tile], 1u) == nch - 1;
+        if (threadIdx.x == 0) {
+            __threadfence();
+            s_last = atomicAdd(&key_done[tile], 1u) == nch - 1;
+        }
         __syncthreads();
         if (!s_last) return;
         __threadfence();
@@ -499,11 +502,12 @@ __device__ __forceinline__ uint32_t cta_excl_scan_128(uint32_t v, uint32_t* s_w,
 constexpr int kBwdUnitW = 4, kBwdUnitH = 2;
 
 // One CTA per work item (<= 128 records of one tile).  Each record's pixel box
-// inside the tile, w x h pixels, is cut into ceil(h / UH) rows of ceil(w / UW)
-// units of UW x UH pixels.  A unit may reach past the box: those pixels lie
-// outside the box, where the gate t >= Tq rejects them exactly as the forward
-// does, or past the tile edge, where the staged dL/dI is padded with UW zero
-// columns and UH - 1 zero rows.  The units of the CTA's records are split into
+// inside the tile, columns c0..c1 and h rows, is cut into ceil(h / UH) rows of
+// units of UW x UH pixels whose columns start at multiples of UW (tile-local), so
+// that a unit row is one aligned vector load of the staged dL/dI.  A unit may
+// reach past the box: those pixels lie outside the box, where the gate t >= Tq
+// rejects them exactly as the forward does, or past the tile's last row, where
+// the staged dL/dI is padded with UH - 1 zero rows.  The units of the CTA's records are split into
 // 128 equal contiguous ranges, one per lane, so every lane evaluates the same
 // number of units whatever the record sizes.  A lane derives each unit's row and
 // column from its index inside the record (no per-row state, so lanes never
@@ -520,11 +524,11 @@ __global__ void __launch_bounds__(kBwdThreads) k_splat_bwd(const float4* __restr
                                                            const float* __restrict__ dimage,
                                                            float4* __restrict__ mom) {
     static_assert(kChunk == kBwdThreads, "one record per thread");
-    static_assert(TW <= 32 && TH <= 16 && UW >= 1 && UW <= 4 && UH >= 1 && UH <= 2,
-                  "unit decode is exact for these sizes");
-    constexpr int TWP = TW + UW;          // staged row stride: UW zero columns past the tile edge
+    static_assert(TW <= 32 && TH <= 16 && UW == 4 && UH >= 1 && UH <= 2 && TW % UW == 0,
+                  "unit decode is exact for these sizes; a unit row is one float4");
+    constexpr int TWP = TW + 4;           // staged row stride (16-byte multiple; spreads rows over banks)
     constexpr int THP = TH + UH - 1;      // staged rows: UH - 1 zero rows past the tile edge
-    __shared__ float s_g[THP * TWP];      // dL/dI of the tile
+    __shared__ __align__(16) float s_g[THP * TWP];  // dL/dI of the tile
     __shared__ float4 s_k1[kChunk];        // A, B, C of the conic; dx of the box's first pixel
     __shared__ float4 s_k2[kChunk];        // dy of the first row; s_g index of the first pixel; 1/uw; uw
     __shared__ uint32_t s_gid[kChunk];     // Gaussian id
@@ -558,10 +562,11 @@ __global__ void __launch_bounds__(kBwdThreads) k_splat_bwd(const float4* __restr
         const int r0 = max(0, (int)ceilf(a.y - b.w) - Y0), r1 = min(TH - 1, (int)floorf(a.y + b.w) - Y0);
         const int w = c1 - c0 + 1, h = r1 - r0 + 1;
         if (w > 0 && h > 0) {
-            const int uw = (w + UW - 1) / UW;
+            const int ca = c0 & ~(UW - 1);  // first unit column, aligned
+            const int uw = (c1 - ca) / UW + 1;
             n = (uint32_t)(uw * ((h + UH - 1) / UH));
-            s_k1[j] = make_float4(a.z, a.w, b.x, (float)(X0 + c0) - a.x);
-            s_k2[j] = make_float4((float)(Y0 + r0) - a.y, (float)(r0 * TWP + c0), 1.0f / (float)uw, (float)uw);
+            s_k1[j] = make_float4(a.z, a.w, b.x, (float)(X0 + ca) - a.x);
+            s_k2[j] = make_float4((float)(Y0 + r0) - a.y, (float)(r0 * TWP + ca), 1.0f / (float)uw, (float)uw);
             s_gid[j] = gid;
         }
     }
@@ -597,13 +602,15 @@ __global__ void __launch_bounds__(kBwdThreads) k_splat_bwd(const float4* __restr
         for (int qy = 0; qy < UH; ++qy) {
             const float dy = dy0 + (float)qy;
             const float bdy = k1.y * dy, cdy2 = k1.z * dy * dy;
+            const float4 g4 = *reinterpret_cast<const float4*>(&s_g[gi + qy * TWP]);
+            const float gq4[4] = {g4.x, g4.y, g4.z, g4.w};
             float Wu = 0.f, Xu = 0.f;
 #pragma unroll
             for (int q = 0; q < UW; ++q) {
                 const float dxq = dx + (float)q;
                 const float t = fmaf(fmaf(k1.x, dxq, bdy), dxq, cdy2);
                 const float ev = ex2_approx(t);
-                const float wq = (t >= Tq) ? s_g[gi + qy * TWP + q] * ev : 0.0f;
+                const float wq = (t >= Tq) ? gq4[q] * ev : 0.0f;
                 const float aq = wq * dxq;
                 Wu += wq;
                 Xu += aq;

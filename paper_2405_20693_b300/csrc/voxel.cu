@@ -301,9 +301,12 @@ __global__ void __launch_bounds__(kVoxThreads) k_vox_fwd(const float4* __restric
         // the brick's chunk volumes in chunk order
         float4* p = reinterpret_cast<float4*>(partial + it * (size_t)(kB * kB * kB)) + t;
         *p = make_float4(acc[0], acc[1], acc[2], acc[3]);
-        __threadfence();
+        // the barrier orders every thread's stores before thread 0's release fence
         __syncthreads();
-        if (t == 0) s_last = atomicAdd(&key_done[brick], 1u) == nch - 1;
+        if (t == 0) {
+            __threadfence();
+            s_last = atomicAdd(&key_done[brick], 1u) == nch - 1;
+        }
         __syncthreads();
         if (!s_last) return;
         __threadfence();
