@@ -103,11 +103,18 @@ class Server:
         mse = float(torch.mean((cls.volume(sc, vox) - gt) ** 2))
         return 10.0 * np.log10(1.0 / max(mse, 1e-30))
 
+    def warm(self):
+        """Load the device code of the server's own evaluation (the PSNR reduction)
+        before requests are timed: the first use of a kernel loads its module."""
+        a = torch.zeros(256, dtype=torch.float32, device=self.device)
+        float(torch.mean((a - a) ** 2))
+
     def run(self, requests):
         pending = sorted(requests, key=lambda r: r.arrival)
         queue, active, results = [], {}, []
         used = 0
         trainer, dirty = None, True
+        self.warm()
         t0 = time.perf_counter()
         while pending or queue or active:
             now = time.perf_counter() - t0
