@@ -10,8 +10,10 @@
 // the total and the capacity verdict into the status block.  The emission then
 // re-walks each block's records in rounds of 256 and writes every record's
 // entries at its offset, in record order (an Op supplies, for record r, its entry
-// count and entries(r, f), calling f(key, id) once per entry).  Entries beyond
-// the capacity are not written.
+// count, per-record decode data info(r) and key(info, li), the key of its li-th
+// entry).  Each round's entries are spread evenly over the block's threads (an
+// entry finds its record by binary search over the round's entry offsets), so the
+// writes are balanced and contiguous.  Entries beyond the capacity are not written.
 //
 // Key spaces of at most kFusedKeys keys (one 512^2 view in 16 x 16 tiles, the
 // bricks of a TV patch) take a fused path: the emission also counts its block's
@@ -153,24 +155,41 @@ __global__ void __launch_bounds__(256) k_emit_chunks(Op op, long long n_rec, lon
         for (int k = threadIdx.x; k < n_keys; k += 256) h[k] = 0;
         __syncthreads();
     }
+    __shared__ uint4 s_info[256];
+    __shared__ uint32_t s_ex[256];
     const long long begin = min(n_rec, (long long)blockIdx.x * per_block);
     const long long end = min(n_rec, begin + per_block);
     unsigned long long running = partials[blockIdx.x];
     for (long long base = begin; base < end; base += 256) {
         const long long r = base + threadIdx.x;
-        const uint32_t c = r < end ? op.count(r) : 0u;
+        uint32_t c = 0;
+        uint4 inf = make_uint4(0u, 0u, 0u, 0u);
+        if (r < end) {
+            c = op.count(r);
+            inf = op.info(r);
+        }
         uint32_t tot;
         const uint32_t ex = block_exclusive_scan_256(c, sm, &tot);
-        if (c) {
-            unsigned long long off = running + ex;
-            op.entries(r, [&](uint32_t key, uint32_t id) {
-                if (off < capacity) {
-                    out[off] = ((uint64_t)key << 32) | (uint64_t)id;
-                    if (HIST) atomicAdd(&h[key], 1u);
-                }
-                ++off;
-            });
+        s_info[threadIdx.x] = inf;
+        s_ex[threadIdx.x] = ex;
+        __syncthreads();
+        // the round's entries, flattened: thread t writes entries t, t + 256, ...
+        for (uint32_t e = threadIdx.x; e < tot; e += 256) {
+            int lo = 0, hi = 255;  // the record holding entry e: the last k with ex_k <= e
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_ex[mid] <= e) lo = mid;
+                else hi = mid - 1;
+            }
+            const uint4 ri = s_info[lo];
+            const uint32_t key = op.key(ri, e - s_ex[lo]);
+            const unsigned long long off = running + e;
+            if (off < capacity) {
+                out[off] = ((uint64_t)key << 32) | (uint64_t)ri.w;
+                if (HIST) atomicAdd(&h[key], 1u);
+            }
         }
+        __syncthreads();
         running += tot;
     }
     if (!HIST) return;
@@ -273,7 +292,18 @@ static __global__ void __launch_bounds__(256) k_fused_scatter(const uint64_t* __
 #pragma unroll
         for (int w = 0; w < 8; ++w) s_h[w][k] = 0;
     __syncthreads();
-    for (unsigned long long i = wlo + lane; i < whi; i += 32) atomicAdd(&s_h[warp][(uint32_t)(in[i] >> 32)], 1u);
+    constexpr int R = 8;  // entries per lane loaded at once
+    for (unsigned long long b0 = wlo; b0 < whi; b0 += 32 * R) {
+        uint32_t k[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const unsigned long long i = b0 + q * 32 + lane;
+            k[q] = i < whi ? (uint32_t)(in[i] >> 32) : 0xffffffffu;
+        }
+#pragma unroll
+        for (int q = 0; q < R; ++q)
+            if (k[q] != 0xffffffffu) atomicAdd(&s_h[warp][k[q]], 1u);
+    }
     __syncthreads();
     for (int k = tid; k < n_keys; k += 256) {
         uint32_t run = offs[(size_t)k * nb + b];
@@ -286,18 +316,25 @@ static __global__ void __launch_bounds__(256) k_fused_scatter(const uint64_t* __
     }
     __syncthreads();
     const uint32_t lt = (1u << lane) - 1u;
-    for (unsigned long long base = wlo; base < whi; base += 32) {
-        const unsigned long long i = base + lane;
-        const bool valid = i < whi;
-        const uint64_t x = valid ? in[i] : 0ull;
-        const uint32_t k = valid ? (uint32_t)(x >> 32) : 0xffffffffu;
-        const uint32_t peers = __match_any_sync(0xffffffffu, k);
-        const uint32_t rank = __popc(peers & lt);
-        const uint32_t pos = valid ? s_h[warp][k] + rank : 0u;
-        __syncwarp();
-        if (valid && rank == 0) s_h[warp][k] += __popc(peers);
-        __syncwarp();
-        if (valid) out[pos] = x;
+    for (unsigned long long b0 = wlo; b0 < whi; b0 += 32 * R) {
+        uint64_t x[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const unsigned long long i = b0 + q * 32 + lane;
+            x[q] = i < whi ? in[i] : ~0ull;
+        }
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const bool valid = b0 + q * 32 + lane < whi;
+            const uint32_t k = valid ? (uint32_t)(x[q] >> 32) : 0xffffffffu;
+            const uint32_t peers = __match_any_sync(0xffffffffu, k);
+            const uint32_t rank = __popc(peers & lt);
+            const uint32_t pos = valid ? s_h[warp][k] + rank : 0u;
+            __syncwarp();
+            if (valid && rank == 0) s_h[warp][k] += __popc(peers);
+            __syncwarp();
+            if (valid) out[pos] = x[q];
+        }
     }
 }
 

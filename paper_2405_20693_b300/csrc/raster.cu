@@ -314,14 +314,19 @@ struct TileOp {
         const int x0 = rc.x & 0xffff, x1 = rc.x >> 16, y0 = rc.y & 0xffff, y1 = rc.y >> 16;
         return (x1 >= x0 && y1 >= y0) ? (uint32_t)((x1 - x0 + 1) * (y1 - y0 + 1)) : 0u;
     }
-    template <class F>
-    __device__ __forceinline__ void entries(long long r, F&& f) const {
+    // Per-record decode data: x0 | w << 16, y0, key base of the record's view, Gaussian id.
+    __device__ __forceinline__ uint4 info(long long r) const {
         const uint2 rc = rect[r];
-        const int x0 = rc.x & 0xffff, x1 = rc.x >> 16, y0 = rc.y & 0xffff, y1 = rc.y >> 16;
-        const long long v = r / M, i = r - v * M;
-        const uint32_t base = (uint32_t)(v * tiles_per_view);
-        for (int ty = y0; ty <= y1; ++ty)
-            for (int tx = x0; tx <= x1; ++tx) f(base + (uint32_t)(ty * tiles_x + tx), (uint32_t)i);
+        const uint32_t x0 = rc.x & 0xffff, x1 = rc.x >> 16;
+        const long long v = r / M;
+        return make_uint4(x0 | ((x1 - x0 + 1) << 16), rc.y & 0xffff, (uint32_t)(v * tiles_per_view),
+                          (uint32_t)(r - v * M));
+    }
+    // Key of the record's li-th entry (tiles in row-major order of its rectangle).
+    __device__ __forceinline__ uint32_t key(const uint4& inf, uint32_t li) const {
+        const uint32_t w = inf.x >> 16;
+        const uint32_t ty = li / w, tx = li - ty * w;
+        return inf.z + (inf.y + ty) * (uint32_t)tiles_x + (inf.x & 0xffff) + tx;
     }
 };
 

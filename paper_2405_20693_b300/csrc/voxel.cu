@@ -200,19 +200,21 @@ struct BrickEmitOp {
         const int z0 = rc.z & 0xffff, z1 = rc.z >> 16;
         return (x1 >= x0 && y1 >= y0 && z1 >= z0) ? (uint32_t)((x1 - x0 + 1) * (y1 - y0 + 1) * (z1 - z0 + 1)) : 0u;
     }
-    template <class F>
-    __device__ __forceinline__ void entries(long long r, F&& f) const {
+    // Per-record decode data: x0 | w << 16, y0 | h << 16, z0 | grid << 16, Gaussian id.
+    __device__ __forceinline__ uint4 info(long long r) const {
         const uint4 rc = rect[r];
-        const int x0 = rc.x & 0xffff, x1 = rc.x >> 16, y0 = rc.y & 0xffff, y1 = rc.y >> 16;
-        const int z0 = rc.z & 0xffff, z1 = rc.z >> 16;
+        const uint32_t x0 = rc.x & 0xffff, x1 = rc.x >> 16, y0 = rc.y & 0xffff, y1 = rc.y >> 16;
         const int g = (int)(r / M);
-        const long long i = r - (long long)g * M;
-        const long long bb = brick_base[g];
-        const int nx = nbx[g], ny = nby[g];
-        for (int bz = z0; bz <= z1; ++bz)
-            for (int by = y0; by <= y1; ++by)
-                for (int bx = x0; bx <= x1; ++bx)
-                    f((uint32_t)(bb + ((long long)bz * ny + by) * nx + bx), (uint32_t)i);
+        return make_uint4(x0 | ((x1 - x0 + 1) << 16), y0 | ((y1 - y0 + 1) << 16), (rc.z & 0xffff) | ((uint32_t)g << 16),
+                          (uint32_t)(r - (long long)g * M));
+    }
+    // Key of the record's li-th entry (bricks in x-fastest order of its box).
+    __device__ __forceinline__ uint32_t key(const uint4& inf, uint32_t li) const {
+        const uint32_t w = inf.x >> 16, h = inf.y >> 16, g = inf.z >> 16;
+        const uint32_t q = li / w, bx = li - q * w;
+        const uint32_t bz = q / h, by = q - bz * h;
+        return (uint32_t)(brick_base[g] + ((long long)((inf.z & 0xffff) + bz) * nby[g] + (inf.y & 0xffff) + by) *
+                                              nbx[g] + (inf.x & 0xffff) + bx);
     }
 };
 
