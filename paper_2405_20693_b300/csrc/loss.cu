@@ -79,89 +79,162 @@ __global__ void __launch_bounds__(kSsimThreads) k_ssim(const float* __restrict__
         S.sy[r][c] = in ? yv[(size_t)gy * W + gx] : 0.f;
     }
     __syncthreads();
-    for (int k = tid; k < kS * kM; k += kSsimThreads) {
-        const int r = k / kM, c = k - r * kM;
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f;
+    // Each pass is register-blocked along its filter direction: a thread computes a
+    // run of outputs from one sliding set of inputs (every input loaded once), and
+    // the lanes of a warp take consecutive rows (horizontal passes) or columns
+    // (vertical passes), so shared-memory accesses are free of bank conflicts.
+    // Horizontal pass of x, y, xx, yy, xy: rows 0..kS-1, output columns 0..kM-1.
+    {
+        constexpr int RB = 6, NSEG = kM / RB;  // 7 runs of 6 columns per row
+        static_assert(kM % RB == 0 && NSEG * kS <= kSsimThreads, "one pass");
+        if (tid < NSEG * kS) {
+            const int r = tid % kS, c0 = (tid / kS) * RB;
+            float acc[RB][5];
 #pragma unroll
-        for (int j = 0; j < 11; ++j) {
-            const float w = win.w[j];
-            const float xa = S.sx[r][c + j], ya = S.sy[r][c + j];
-            a0 = fmaf(w, xa, a0);
-            a1 = fmaf(w, ya, a1);
-            a2 = fmaf(w, xa * xa, a2);
-            a3 = fmaf(w, ya * ya, a3);
-            a4 = fmaf(w, xa * ya, a4);
+            for (int o = 0; o < RB; ++o)
+#pragma unroll
+                for (int q = 0; q < 5; ++q) acc[o][q] = 0.f;
+#pragma unroll
+            for (int i = 0; i < RB + 10; ++i) {
+                const float xa = S.sx[r][c0 + i], ya = S.sy[r][c0 + i];
+                const float f[5] = {xa, ya, xa * xa, ya * ya, xa * ya};
+#pragma unroll
+                for (int o = 0; o < RB; ++o) {
+                    const int j = i - o;
+                    if (j >= 0 && j <= 10) {
+#pragma unroll
+                        for (int q = 0; q < 5; ++q) acc[o][q] = fmaf(win.w[j], f[q], acc[o][q]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int o = 0; o < RB; ++o)
+#pragma unroll
+                for (int q = 0; q < 5; ++q) S.u.h[q][r][c0 + o] = acc[o][q];
         }
-        S.u.h[0][r][c] = a0;
-        S.u.h[1][r][c] = a1;
-        S.u.h[2][r][c] = a2;
-        S.u.h[3][r][c] = a3;
-        S.u.h[4][r][c] = a4;
     }
     __syncthreads();
+    // Vertical pass -> moments, SSIM term and its derivatives on the tile plus halo.
     float sS = 0.f, sL1 = 0.f;
-    for (int k = tid; k < kM * kM; k += kSsimThreads) {
-        const int r = k / kM, c = k - r * kM;
-        const int gy = TY - kR + r, gx = TX - kR + c;
-        float dm = 0.f, dxx = 0.f, dxy = 0.f;
-        if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
-            float m[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    {
+        constexpr int RB = 4, NSEG = (kM + RB - 1) / RB;  // 11 runs of (up to) 4 rows per column
+        static_assert(NSEG * kM <= kSsimThreads, "one pass");
+        if (tid < NSEG * kM) {
+            const int c = tid % kM, r0 = (tid / kM) * RB;
+            float m[RB][5];
 #pragma unroll
-            for (int j = 0; j < 11; ++j) {
-                const float w = win.w[j];
+            for (int o = 0; o < RB; ++o)
 #pragma unroll
-                for (int q = 0; q < 5; ++q) m[q] = fmaf(w, S.u.h[q][r + j][c], m[q]);
+                for (int q = 0; q < 5; ++q) m[o][q] = 0.f;
+#pragma unroll
+            for (int i = 0; i < RB + 10; ++i) {
+                if (r0 + i < kS) {
+                    float hq[5];
+#pragma unroll
+                    for (int q = 0; q < 5; ++q) hq[q] = S.u.h[q][r0 + i][c];
+#pragma unroll
+                    for (int o = 0; o < RB; ++o) {
+                        const int j = i - o;
+                        if (j >= 0 && j <= 10) {
+#pragma unroll
+                            for (int q = 0; q < 5; ++q) m[o][q] = fmaf(win.w[j], hq[q], m[o][q]);
+                        }
+                    }
+                }
             }
-            const float mx = m[0], my = m[1];
-            const float sxx = m[2] - mx * mx, syy = m[3] - my * my, sxy = m[4] - mx * my;
-            const float A1 = 2.f * mx * my + kC1, A2 = 2.f * sxy + kC2;
-            const float B1 = mx * mx + my * my + kC1, B2 = sxx + syy + kC2;
-            const float iB = 1.f / (B1 * B2);
-            const float Sv = A1 * A2 * iB;
-            dm = (2.f * my * (A2 - A1) - 2.f * mx * Sv * (B2 - B1)) * iB;
-            dxx = -Sv / B2;
-            dxy = 2.f * A1 * iB;
-            if (r >= kR && r < kR + kT && c >= kR && c < kR + kT) {  // this tile's own pixels
-                sS += Sv;
-                sL1 += fabsf(S.sx[r + kR][c + kR] - S.sy[r + kR][c + kR]);
+#pragma unroll
+            for (int o = 0; o < RB; ++o) {
+                const int r = r0 + o;
+                if (r >= kM) break;
+                const int gy = TY - kR + r, gx = TX - kR + c;
+                float dm = 0.f, dxx = 0.f, dxy = 0.f;
+                if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
+                    const float mx = m[o][0], my = m[o][1];
+                    const float sxx = m[o][2] - mx * mx, syy = m[o][3] - my * my, sxy = m[o][4] - mx * my;
+                    const float A1 = 2.f * mx * my + kC1, A2 = 2.f * sxy + kC2;
+                    const float B1 = mx * mx + my * my + kC1, B2 = sxx + syy + kC2;
+                    const float iB = 1.f / (B1 * B2);
+                    const float Sv = A1 * A2 * iB;
+                    dm = (2.f * my * (A2 - A1) - 2.f * mx * Sv * (B2 - B1)) * iB;
+                    dxx = -Sv / B2;
+                    dxy = 2.f * A1 * iB;
+                    if (r >= kR && r < kR + kT && c >= kR && c < kR + kT) {  // this tile's own pixels
+                        sS += Sv;
+                        sL1 += fabsf(S.sx[r + kR][c + kR] - S.sy[r + kR][c + kR]);
+                    }
+                }
+                S.d[0][r][c] = dm;
+                S.d[1][r][c] = dxx;
+                S.d[2][r][c] = dxy;
             }
         }
-        S.d[0][r][c] = dm;
-        S.d[1][r][c] = dxx;
-        S.d[2][r][c] = dxy;
     }
     __syncthreads();
-    for (int k = tid; k < kM * kT; k += kSsimThreads) {
-        const int r = k / kT, c = k - r * kT;
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+    // Horizontal pass of the derivative maps: rows 0..kM-1, output columns 0..kT-1.
+    {
+        constexpr int RB = 8, NSEG = kT / RB;  // 4 runs of 8 columns per row
+        static_assert(kT % RB == 0 && NSEG * kM <= kSsimThreads, "one pass");
+        if (tid < NSEG * kM) {
+            const int r = tid % kM, c0 = (tid / kM) * RB;
+            float acc[RB][3];
 #pragma unroll
-        for (int j = 0; j < 11; ++j) {
-            const float w = win.w[j];
-            a0 = fmaf(w, S.d[0][r][c + j], a0);
-            a1 = fmaf(w, S.d[1][r][c + j], a1);
-            a2 = fmaf(w, S.d[2][r][c + j], a2);
+            for (int o = 0; o < RB; ++o)
+#pragma unroll
+                for (int q = 0; q < 3; ++q) acc[o][q] = 0.f;
+#pragma unroll
+            for (int i = 0; i < RB + 10; ++i) {
+                const float f[3] = {S.d[0][r][c0 + i], S.d[1][r][c0 + i], S.d[2][r][c0 + i]};
+#pragma unroll
+                for (int o = 0; o < RB; ++o) {
+                    const int j = i - o;
+                    if (j >= 0 && j <= 10) {
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) acc[o][q] = fmaf(win.w[j], f[q], acc[o][q]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int o = 0; o < RB; ++o)
+#pragma unroll
+                for (int q = 0; q < 3; ++q) S.u.g[q][r][c0 + o] = acc[o][q];
         }
-        S.u.g[0][r][c] = a0;
-        S.u.g[1][r][c] = a1;
-        S.u.g[2][r][c] = a2;
     }
     __syncthreads();
-    for (int k = tid; k < kT * kT; k += kSsimThreads) {
-        const int r = k / kT, c = k - r * kT;
-        const int gy = TY + r, gx = TX + c;
-        if (gy >= H || gx >= W) continue;
-        float b0 = 0.f, b1 = 0.f, b2 = 0.f;
+    // Vertical pass -> d loss / d render on the tile's own pixels.
+    {
+        constexpr int RB = 4, NSEG = kT / RB;  // 8 runs of 4 rows per column
+        static_assert(kT % RB == 0 && NSEG * kT <= kSsimThreads, "one pass");
+        if (tid < NSEG * kT) {
+            const int c = tid % kT, r0 = (tid / kT) * RB;
+            float b[RB][3];
 #pragma unroll
-        for (int j = 0; j < 11; ++j) {
-            const float w = win.w[j];
-            b0 = fmaf(w, S.u.g[0][r + j][c], b0);
-            b1 = fmaf(w, S.u.g[1][r + j][c], b1);
-            b2 = fmaf(w, S.u.g[2][r + j][c], b2);
+            for (int o = 0; o < RB; ++o)
+#pragma unroll
+                for (int q = 0; q < 3; ++q) b[o][q] = 0.f;
+#pragma unroll
+            for (int i = 0; i < RB + 10; ++i) {
+                const float f[3] = {S.u.g[0][r0 + i][c], S.u.g[1][r0 + i][c], S.u.g[2][r0 + i][c]};
+#pragma unroll
+                for (int o = 0; o < RB; ++o) {
+                    const int j = i - o;
+                    if (j >= 0 && j <= 10) {
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) b[o][q] = fmaf(win.w[j], f[q], b[o][q]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int o = 0; o < RB; ++o) {
+                const int r = r0 + o;
+                const int gy = TY + r, gx = TX + c;
+                if (gy >= H || gx >= W) continue;
+                const float xp = S.sx[r + 2 * kR][c + 2 * kR], yp = S.sy[r + 2 * kR][c + 2 * kR];
+                const float dd = xp - yp;
+                const float sgn = (dd > 0.f) ? 1.f : ((dd < 0.f) ? -1.f : 0.f);
+                grad[((size_t)v * H + gy) * W + gx] =
+                    l1_scale * sgn - ssim_scale * (b[o][0] + 2.f * xp * b[o][1] + yp * b[o][2]);
+            }
         }
-        const float xp = S.sx[r + 2 * kR][c + 2 * kR], yp = S.sy[r + 2 * kR][c + 2 * kR];
-        const float dd = xp - yp;
-        const float sgn = (dd > 0.f) ? 1.f : ((dd < 0.f) ? -1.f : 0.f);
-        grad[((size_t)v * H + gy) * W + gx] = l1_scale * sgn - ssim_scale * (b0 + 2.f * xp * b1 + yp * b2);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
