@@ -494,7 +494,7 @@ def run_ours(args, rank, world, local_rank):
                        "pixel_pairs_per_step": per_step_pix, "voxel_pairs_per_step": per_step_vox,
                        "step_cycle": f"{N_DISTINCT} seeded (view, patch) pairs, repeated",
                        "l2": "flushed (256 MB write) before every timed step", "parallelism": f"replicas x{world}",
-                       "tile": "16x16", "bricks": "8^3"},
+                       "tile": "32x32", "bricks": "8^3"},
             "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": 4 * cam.H * cam.W,
                     "d2h_bytes_per_step": 8},
             "gpu_launches": int(launches),

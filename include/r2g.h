@@ -66,7 +66,7 @@ typedef struct {
 /* Rasterizer options. */
 typedef struct {
     float Q;             /* pixel gate: a Gaussian adds to a pixel when q = d^T Sigma^^{-1} d <= Q (9 = 3 sigma) */
-    int32_t tile_w;      /* tile shape: 16x16 (default), 8x8 or 32x8 */
+    int32_t tile_w;      /* tile shape: 16x16 (default), 8x8, 32x8 or 32x32 */
     int32_t tile_h;
     int32_t count_pairs; /* 1: also count the gated pairs (bookkeeping runs only; slower) */
 } r2g_raster_opts;

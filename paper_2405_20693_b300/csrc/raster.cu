@@ -357,7 +357,9 @@ __global__ void __launch_bounds__(FwdShape<TW, TH>::NT) k_splat_fwd(const float4
     constexpr int BW = 4 * PX;                // warp block: 8 rows x BW columns
     constexpr int WPR = TW / BW;              // warp blocks per tile row
     constexpr int NW = NT / 32;               // warps = warp blocks per tile
-    static_assert(TW % BW == 0 && TH % 8 == 0 && kChunk % NT == 0 && NT % 32 == 0 && NW <= 32, "tile shape");
+    static_assert(TW % BW == 0 && TH % 8 == 0 && (kChunk % NT == 0 || NT % kChunk == 0) && NT % 32 == 0 &&
+                      NW <= 32 && NT <= 256,
+                  "tile shape");
     __shared__ float4 s_a[NT];
     __shared__ float4 s_b[NT];
     __shared__ uint32_t s_mask[NT];           // bit w: the record's box meets warp w's block
@@ -529,8 +531,8 @@ __global__ void __launch_bounds__(kBwdThreads) k_splat_bwd(const float4* __restr
                                                            const float* __restrict__ dimage,
                                                            float4* __restrict__ mom) {
     static_assert(kChunk == kBwdThreads, "one record per thread");
-    static_assert(TW <= 32 && TH <= 16 && UW == 4 && UH >= 1 && UH <= 2 && TW % UW == 0,
-                  "unit decode is exact for these sizes; a unit row is one float4");
+    static_assert(TW <= 32 && TH <= 32 && UW == 4 && UH >= 1 && UH <= 2 && TW % UW == 0,
+                  "unit decode is exact for these sizes (units per record <= 2^10); a unit row is one float4");
     constexpr int TWP = TW + 4;           // staged row stride (16-byte multiple; spreads rows over banks)
     constexpr int THP = TH + UH - 1;      // staged rows: UH - 1 zero rows past the tile edge
     __shared__ __align__(16) float s_g[THP * TWP];  // dL/dI of the tile
@@ -821,7 +823,9 @@ struct RasterLayout {
     long long n_tiles, n_rec;
 };
 
-bool valid_tile(int tw, int th) { return (tw == 16 && th == 16) || (tw == 8 && th == 8) || (tw == 32 && th == 8); }
+bool valid_tile(int tw, int th) {
+    return (tw == 16 && th == 16) || (tw == 8 && th == 8) || (tw == 32 && th == 8) || (tw == 32 && th == 32);
+}
 
 r2g_status check_args(int64_t M, int32_t V, const r2g_camera* cam, const r2g_raster_opts* opts) {
     if (!cam || !opts) return fail(R2G_E_INVAL, "camera and options must not be NULL");
@@ -834,7 +838,7 @@ r2g_status check_args(int64_t M, int32_t V, const r2g_camera* cam, const r2g_ras
     if (!(cam->pitch_u > 0.f) || !(cam->pitch_v > 0.f)) return fail(R2G_E_INVAL, "pitches must be > 0");
     if (cam->beam == 1 && !(cam->L_SD > 0.f)) return fail(R2G_E_INVAL, "cone beam needs L_SD > 0");
     if (!valid_tile(opts->tile_w, opts->tile_h))
-        return fail(R2G_E_INVAL, "tile %dx%d not one of 16x16, 8x8, 32x8", opts->tile_w, opts->tile_h);
+        return fail(R2G_E_INVAL, "tile %dx%d not one of 16x16, 8x8, 32x8, 32x32", opts->tile_w, opts->tile_h);
     if (!(opts->Q > 0.f)) return fail(R2G_E_INVAL, "Q must be > 0");
     const long long tx = (cam->W + opts->tile_w - 1) / opts->tile_w, ty = (cam->H + opts->tile_h - 1) / opts->tile_h;
     if ((long long)V * tx * ty >= (1ll << 31)) return fail(R2G_E_INVAL, "too many tiles");
@@ -936,6 +940,8 @@ void launch_fwd(int tw, int th, const FwdArgs& f, long long M, const RasterLayou
         fwd_shape<16, 16, COUNT>(f, M, L, icap, H, W, Tq, image, st, s);
     else if (tw == 8 && th == 8)
         fwd_shape<8, 8, COUNT>(f, M, L, icap, H, W, Tq, image, st, s);
+    else if (tw == 32 && th == 32)
+        fwd_shape<32, 32, COUNT>(f, M, L, icap, H, W, Tq, image, st, s);
     else
         fwd_shape<32, 8, COUNT>(f, M, L, icap, H, W, Tq, image, st, s);
 }
@@ -952,6 +958,10 @@ void launch_bwd(int tw, int th, const float4* rec, const uint2* ranges, const ui
         k_splat_bwd<8, 8, kBwdUnitW, kBwdUnitH><<<grid, kBwdThreads, 0, s>>>(rec, ranges, sorted, items, item_st,
                                                                                    M, L.tiles_x,
                                                        L.tiles_per_view, H, W, Tq, dimage, mom);
+    else if (tw == 32 && th == 32)
+        k_splat_bwd<32, 32, kBwdUnitW, kBwdUnitH><<<grid, kBwdThreads, 0, s>>>(rec, ranges, sorted, items, item_st,
+                                                                                    M, L.tiles_x, L.tiles_per_view,
+                                                                                    H, W, Tq, dimage, mom);
     else
         k_splat_bwd<32, 8, kBwdUnitW, kBwdUnitH><<<grid, kBwdThreads, 0, s>>>(rec, ranges, sorted, items, item_st,
                                                                                    M, L.tiles_x,

@@ -17,6 +17,7 @@ Q_PIXEL = 9.0        # 3-sigma pixel gate
 Q_VOXEL = 11.345     # chi^2_3 0.99 quantile: the paper's "99% confidence" brick culling
 LAMBDA_SSIM = 0.25   # Sec. 5.1
 LAMBDA_TV = 0.05     # Sec. 5.1
+SCAN_TILE = (32, 32)  # tile shape of the training step's rasterizer (fewest list entries at 512^2)
 
 
 def _bytes(n: int, device) -> torch.Tensor:
@@ -196,14 +197,14 @@ class TrainStep:
     """One iteration of Eq. 8 on one projection view and one D^3 TV patch."""
 
     def __init__(self, state: TrainState, views: torch.Tensor, meas: torch.Tensor, cam, D=32, n_out=256,
-                 tile=(16, 16), total_iters=30000, device="cuda"):
+                 tile=None, total_iters=30000, device="cuda"):
         self.s = state
         self.views = views            # [V, 12] device
         self.meas = meas              # [V, H, W] device
         self.cam = cam
         self.D = D
         self.n_out = n_out
-        self.rast = Rasterizer(state.M, 1, cam, tile=tile, device=device)
+        self.rast = Rasterizer(state.M, 1, cam, tile=tile or SCAN_TILE, device=device)
         from .inputs import patch_grid
         self._patch = patch_grid
         self.vox = Voxelizer(state.M, patch_grid((0, 0, 0), D, n_out), device=device)
@@ -241,7 +242,7 @@ class Scan:
     views, measured projections, step buffers and workspaces, and the C job
     descriptor for r2g_train_step."""
 
-    def __init__(self, G, views_np, meas_np, cam, n_out=256, D=32, tile=(16, 16), total_iters=30000,
+    def __init__(self, G, views_np, meas_np, cam, n_out=256, D=32, tile=None, total_iters=30000,
                  device="cuda", headroom=1.5, seed=0):
         self.state = TrainState(G, device=device)
         self.rng = np.random.Generator(np.random.PCG64(seed + 2))  # this scan's view / patch choices
@@ -258,7 +259,7 @@ class Scan:
         self.vol = torch.empty(D ** 3, dtype=torch.float32, device=device)
         self.dvol = torch.empty_like(self.vol)
         self.loss = torch.zeros(2, dtype=torch.float32, device=device)
-        self.rast = Rasterizer(self.M, 1, cam, tile=tile, device=device)
+        self.rast = Rasterizer(self.M, 1, cam, tile=tile or SCAN_TILE, device=device)
         from .inputs import patch_grid
 
         self.vox = Voxelizer(self.M, patch_grid((0, 0, 0), D, n_out), device=device)

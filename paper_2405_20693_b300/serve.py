@@ -66,7 +66,7 @@ def footprint_estimate(spec: I.ScanSpec, D: int = 32, capacity_factor: float = 6
     Adam state (5 x 11 floats per Gaussian), measured projections, step buffers, and
     the workspaces at the library's own size for capacity_factor x M list entries."""
     cam = r2g.camera(I.cone_camera(spec.det, spec.det, pitch=I.CONE_PITCH * 512 / spec.det))
-    ro = r2g.raster_opts()
+    ro = r2g.raster_opts(tile=engine.SCAN_TILE)
     raster = r2g.r2g_raster_workspace_size(spec.M, 1, cam, ro, int(capacity_factor * spec.M) + 4096)
     grid = r2g.grids(I.patch_grid((0, 0, 0), D, spec.n_out))
     voxel = r2g.r2g_voxel_workspace_size(spec.M, grid, int(capacity_factor * spec.M) + 4096)

@@ -71,7 +71,7 @@ def _lists_gpu(rast, M, V):
 
 
 @pytest.mark.parametrize("case,tile", [("parallel", (16, 16)), ("cone", (16, 16)), ("cone", (8, 8)),
-                                       ("parallel", (32, 8)), ("cone25", (16, 16))])
+                                       ("parallel", (32, 8)), ("cone", (32, 32)), ("cone25", (16, 16))])
 def test_tile_lists_bit_exact(case, tile):
     G, cam, views = _case(case)
     rast = engine.Rasterizer(G.M, views.shape[0], cam, tile=tile, capacity=1024)  # forces a regrow
@@ -102,10 +102,10 @@ def test_rasterize_matches_oracle(case):
 def test_tile_shape_does_not_change_the_image():
     G, cam, views = cone_small()
     imgs = []
-    for tile in ((16, 16), (8, 8), (32, 8)):
+    for tile in ((16, 16), (8, 8), (32, 8), (32, 32)):
         rast = engine.Rasterizer(G.M, views.shape[0], cam, tile=tile)
         imgs.append(host(rast.forward(*dev_set(G), dev(views))))
-    for k in (1, 2):
+    for k in (1, 2, 3):
         assert np.abs(imgs[k] - imgs[0]).max() <= 1e-6 * np.abs(imgs[0]).max()
 
 
