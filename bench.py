@@ -205,17 +205,27 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel sources; else None."""
+def _ncu_summary():
     try:
         with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
             t = json.load(f)
-        if t.get("source_hash") != source_hash():
-            return None
-        return t["kernels"].get(kernel)
+        return t if t.get("source_hash") == source_hash() else None
     except Exception:
         return None
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel sources; else None."""
+    t = _ncu_summary()
+    return t["kernels"].get(kernel) if t else None
+
+
+def ncu_pipes(kernel: str):
+    """FMA and XU (MUFU) pipe utilisation (% of peak sustained) of the kernel from the
+    committed ncu summary, if it was taken on the current kernel sources; else None."""
+    t = _ncu_summary()
+    return t.get("pipes", {}).get(kernel) if t else None
 
 
 def measure_batched(dev, rounds=20, n_scans=16, seed=5):
@@ -313,6 +323,29 @@ def measure_serving(dev, n_requests=16, mean_interarrival_s=0.25, max_iters=500,
     return out
 
 
+def voxel_box_counter(sc):
+    """Voxels of each Gaussian's box (|x_k - p_k| <= sqrt(Q3 Sigma_kk), voxel centres)
+    inside a D^3 TV patch at a given offset, summed over Gaussians: FP64 on the host
+    from the parameters at the start of the timed region."""
+    mean, scale, quat, rho = (t.detach().double().cpu().numpy() for t in sc.state.params())
+    q = quat / np.linalg.norm(quat, axis=1, keepdims=True)
+    w, x, y, z = q.T
+    R = np.stack([1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y),
+                  2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x),
+                  2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)], 1).reshape(-1, 3, 3)
+    sig_kk = np.einsum('nkj,nkj->nk', R * scale[:, None, :], R * scale[:, None, :])
+    vs = 2.0 / N_OUT
+    ext = np.sqrt(11.345 * sig_kk) / vs
+
+    def count(off):
+        c = (mean - (-1.0 + np.asarray(off) * vs)) / vs - 0.5
+        lo = np.maximum(0, np.ceil(c - ext))
+        hi = np.minimum(D_TV - 1, np.floor(c + ext))
+        n = np.clip(hi - lo + 1, 0, None)
+        return int(np.prod(n, axis=1).sum())
+    return count
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -374,6 +407,11 @@ def run_ours(args, rank, world, local_rank):
     from paper_2405_20693_b300 import inputs as I
 
     mean, scale, quat, rho = sc.state.params()
+    # the superset the kernels walk: each Gaussian's pixel box (the projection's
+    # stated FP32 bounds) and voxel box inside the patch
+    proj = torch.empty((1, sc.M, 8), dtype=torch.float32, device=dev)
+    prect = torch.empty((1, sc.M, 4), dtype=torch.int32, device=dev)
+    vox_box = voxel_box_counter(sc)
     counted = {}
     for k in range(t0_steps, t0_steps + args.steps):
         v, off = seq[k]
@@ -383,10 +421,15 @@ def run_ours(args, rank, world, local_rank):
         pp = sc.rast.pair_count()
         sc.vox.set_grids(I.patch_grid(off, D_TV, N_OUT))
         sc.vox.forward(mean, scale, quat, rho, sc.vol, check=True, count=True)
-        counted[(v, off)] = (pp, sc.vox.pair_count())
+        r2g.r2g_project(mean, scale, quat, rho, sc.views[v:v + 1], sc.rast.cam, sc.rast.opts, proj, prect)
+        rc = prect[0].long()
+        ok = proj[0, :, 7] == 1.0
+        box_p = int(((rc[:, 1] - rc[:, 0] + 1) * (rc[:, 3] - rc[:, 2] + 1))[ok].sum())
+        counted[(v, off)] = (pp, sc.vox.pair_count(), box_p, vox_box(off))
     sc.job = sc._make_job()  # a checked run that had to regrow a workspace moved it
     pix_pairs = [counted[seq[k]][0] for k in range(t0_steps, t0_steps + args.steps)]
     vox_pairs = [counted[seq[k]][1] for k in range(t0_steps, t0_steps + args.steps)]
+    box_pairs = [counted[seq[k]][2] + counted[seq[k]][3] for k in range(t0_steps, t0_steps + args.steps)]
     total_pairs = float(sum(pix_pairs) + sum(vox_pairs))
 
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -466,7 +509,7 @@ def run_ours(args, rank, world, local_rank):
             avg_s = t_dom / n_dom * 1e-3
             ach = units / avg_s / 1e9
             roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak, "unit": "Gpair/s",
-                    "frac": ach / peak, "traffic": ncu_traffic(dom),
+                    "frac": ach / peak, "traffic": ncu_traffic(dom), "pipes_pct_of_peak": ncu_pipes(dom),
                     "peak_note": f"min(MUFU ex2 {MUFU_PER_CLK}/clk/SM, FP32 {FP32_PER_CLK}/clk/SM / {ops} ops) "
                                  f"x {SM_COUNT} SMs x {pk['sm_max_mhz']:.0f} MHz"}
         elif dom is not None:
@@ -492,6 +535,8 @@ def run_ours(args, rank, world, local_rank):
                                    "L_SO 1000 mm, L_SD 1500 mm, 50 views x 512^2 at 0.8 mm; per step 1 view "
                                    "(L1+0.25 D-SSIM) + one 32^3 TV patch (0.05), full backward, Adam",
                        "pixel_pairs_per_step": per_step_pix, "voxel_pairs_per_step": per_step_vox,
+                       "box_pairs_per_step": sum(box_pairs) / args.steps,
+                       "gated_over_box": total_pairs / max(1.0, float(sum(box_pairs))),
                        "step_cycle": f"{N_DISTINCT} seeded (view, patch) pairs, repeated",
                        "l2": "flushed (256 MB write) before every timed step", "parallelism": f"replicas x{world}",
                        "tile": "32x32", "bricks": "8^3"},
