@@ -69,6 +69,8 @@ typedef struct {
     int32_t tile_w;      /* tile shape: 16x16 (default), 8x8, 32x8 or 32x32 */
     int32_t tile_h;
     int32_t count_pairs; /* 1: also count the gated pairs (bookkeeping runs only; slower) */
+    int32_t biased;      /* 1: the un-rectified amplitude rho_hat = rho of the 3DGS-style X-ray splatting that
+                          * Sec. 4.2.1 corrects (mu = 1, view-dependent projected mass); 0 (default): Eq. 7 */
 } r2g_raster_opts;
 
 /* One voxel grid: the centre of voxel (x, y, z) is origin + (index + 1/2) * voxel;
@@ -137,6 +139,18 @@ r2g_status r2g_rasterize_backward(int64_t M, const float* mean, const float* sca
 r2g_status r2g_project(int64_t M, const float* mean, const float* scale, const float* quat, const float* rho,
                        int32_t V, const float* views, const r2g_camera* cam, const r2g_raster_opts* opts,
                        float* proj, int32_t* rect, r2g_stream stream);
+
+/* Eq. 7's factor averaged over views, for the X-3DGS variant (Sec. 4.2.1).
+ * mu_mean[M] (device, may be NULL) = the mean over the V views of
+ * mu = sqrt(2 pi / (omega^T Sigma^-1 omega)) of each Gaussian, omega the unit ray
+ * through its mean (views that drop it by the near plane are left out; 0 if every
+ * view drops it).  rho_vol[M] (device, may be NULL; needs rho) = rho / mu_mean, 0
+ * where mu_mean is 0: a model trained with `biased` = 1 learns per-view amplitudes
+ * mu rho, and rho_vol is the density that variant hands to the voxelizer.  At
+ * least one output must be given.  No workspace; M = 0 is a no-op. */
+r2g_status r2g_mean_mu(int64_t M, const float* mean, const float* scale, const float* quat, const float* rho,
+                       int32_t V, const float* views, const r2g_camera* cam, float* mu_mean, float* rho_vol,
+                       r2g_stream stream);
 
 /* The per-tile lists of the last r2g_rasterize on `ws`.  Synchronises `stream`.
  * ranges[n_tiles][2] (device uint32, [start, end) into ids) with n_tiles =

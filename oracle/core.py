@@ -57,6 +57,8 @@ def lib():
             L.orc_voxelize_backward.restype = None
             L.orc_voxelize_backward.argtypes = [i64, _D, _D, _D, _D, _D, i32, dbl, _D, _D, _D, _D, _D, _D, _D, _D,
                                                 _D]
+            L.orc_mean_mu.restype = None
+            L.orc_mean_mu.argtypes = [i64, _D, _D, _D, _D, i32, _D, _D]
             L.orc_render_exact.restype = None
             L.orc_render_exact.argtypes = [i64, _D, _D, _D, _D, _D, i32, _D, _D]
             L.orc_ray_pair.restype = None
@@ -71,10 +73,11 @@ def lib():
     return _lib
 
 
-def _camv(cam, jmode: int = 0) -> np.ndarray:
+def _camv(cam, jmode: int = 0, biased: bool = False) -> np.ndarray:
     """Camera vector for the C entry points; jmode 1 plants the depth-row Jacobian
-    (used only by the test that pins the EWA reading)."""
-    return np.concatenate([np.asarray(cam.as_vector(), dtype=np.float64), [float(jmode)]])
+    (used only by the test that pins the EWA reading); biased selects the X-3DGS
+    amplitude rho_hat = rho in place of Eq. 7's mu rho."""
+    return np.concatenate([np.asarray(cam.as_vector(), dtype=np.float64), [float(jmode), float(bool(biased))]])
 
 
 def _d(a) -> np.ndarray:
@@ -103,12 +106,12 @@ class _G:
 # ----------------------------------------------------------------------------- O1 rasterizer
 
 
-def render(G, views, cam, Q=9.0, brute=False, want_band=False, jmode=0):
+def render(G, views, cam, Q=9.0, brute=False, want_band=False, jmode=0, biased=False):
     """O1 image [V, H, W] (float64), the number of gated (pixel, Gaussian) pairs and,
     if asked, the per-pixel gate-band magnitude."""
     g = _G(G)
     views = _d(views)
-    cv = _camv(cam, jmode)
+    cv = _camv(cam, jmode, biased)
     V = views.shape[0]
     img = np.zeros((V, cam.H, cam.W))
     band = np.zeros((V, cam.H, cam.W)) if want_band else None
@@ -117,23 +120,23 @@ def render(G, views, cam, Q=9.0, brute=False, want_band=False, jmode=0):
     return (img, int(pairs), band) if want_band else (img, int(pairs))
 
 
-def project(G, views, cam, jmode=0):
+def project(G, views, cam, jmode=0, biased=False):
     """FP64 per-(view, Gaussian) quantities [V, M, 12]: valid, p^(2), Sigma^(alpha, beta,
     gamma), |Sigma~|, |Sigma^|, mu, rho_hat, u2, |u|."""
     g = _G(G)
     views = _d(views)
-    cv = _camv(cam, jmode)
+    cv = _camv(cam, jmode, biased)
     out = np.zeros((views.shape[0], g.M, 12))
     lib().orc_project(g.M, *g.ptrs(), _p(views), views.shape[0], _p(cv), _p(out))
     return out
 
 
-def render_cs(G, views, cam, Q, kind, i, comp, h=1e-20):
+def render_cs(G, views, cam, Q, kind, i, comp, h=1e-20, biased=False):
     """Complex-step derivative of the image wrt one parameter (kind 0 mean, 1 scale,
     2 quat, 3 rho)."""
     g = _G(G)
     views = _d(views)
-    cv = _camv(cam)
+    cv = _camv(cam, 0, biased)
     out = np.zeros((views.shape[0], cam.H, cam.W))
     lib().orc_render_cs(g.M, *g.ptrs(), _p(views), views.shape[0], _p(cv), float(Q), kind, i, comp, h, _p(out))
     return out
@@ -143,18 +146,29 @@ def _grad_arrays(M):
     return np.zeros((M, 3)), np.zeros((M, 3)), np.zeros((M, 4)), np.zeros(M)
 
 
-def render_backward(G, views, cam, dimg, Q=9.0, want_band=False):
+def render_backward(G, views, cam, dimg, Q=9.0, want_band=False, biased=False):
     """Hand adjoint: (dmean, dscale, dquat, drho) in float64; with want_band also the
     per-parameter gate-band bound (summed |contribution| of pairs with |q - Q| <= 1e-4 Q)."""
     g = _G(G)
     views = _d(views)
-    cv = _camv(cam)
+    cv = _camv(cam, 0, biased)
     dimg = _d(dimg)
     out = _grad_arrays(g.M)
     band = _grad_arrays(g.M) if want_band else (None,) * 4
     lib().orc_render_backward(g.M, *g.ptrs(), _p(views), views.shape[0], _p(cv), float(Q), _p(dimg),
                               *(_p(a) for a in out), *((_p(a) if a is not None else None) for a in band))
     return (out, band) if want_band else out
+
+
+def mean_mu(G, views, cam):
+    """Eq. 7's factor mu of each Gaussian averaged over the views in which it
+    projects (0 where it projects in none): [M] float64."""
+    g = _G(G)
+    views = _d(views)
+    cv = _camv(cam)
+    out = np.zeros(g.M)
+    lib().orc_mean_mu(g.M, _p(g.mean), _p(g.scale), _p(g.quat), _p(views), views.shape[0], _p(cv), _p(out))
+    return out
 
 
 def render_exact(G, views, cam):

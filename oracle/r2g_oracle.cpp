@@ -54,6 +54,8 @@ struct Cam {
     double near_plane;  // cone: drop Gaussians with u2 <= near_plane
     int jmode;          // third Jacobian row: 0 = u/|u| (EWA, used everywhere);
                         // 1 = (0, 0, 1), a planted mistake for the reading test only
+    int biased;         // 1 = the X-3DGS amplitude rho_hat = rho (no integration bias
+                        // correction, Sec. 4.2.1); 0 = the rectified rho_hat = mu rho (Eq. 7)
 };
 
 template <class T> struct M3 { T a[3][3]; };
@@ -184,7 +186,7 @@ Proj<T> project_one(const T* p, const M3<T>& Sigma, T rho, const double* view, c
     P.d2 = P.sh[0] * P.sh[2] - P.sh[1] * P.sh[1];
     if (!(re(P.d2) > 0.0)) { P.valid = false; return P; }
     P.mu = std::sqrt(2.0 * M_PI * P.d3 / P.d2);
-    P.rhohat = P.mu * rho;
+    P.rhohat = cam.biased ? rho : P.mu * rho;
     P.conic[0] = P.sh[2] / P.d2;
     P.conic[1] = -P.sh[1] / P.d2;
     P.conic[2] = P.sh[0] / P.d2;
@@ -333,9 +335,9 @@ void chain_record(const Proj<double>& P, const M3<double>& Sigma, const M3<doubl
                   const double drec[6], Grad g, int64_t oi) {
     const double d_rhohat = drec[0], d_ph0 = drec[1], d_ph1 = drec[2], da = drec[3], db = drec[4], dc = drec[5];
     const double a = P.conic[0], b = P.conic[1], c = P.conic[2];
-    // rho_hat = mu rho
-    g.rho[oi] += d_rhohat * P.mu;
-    const double dmu = d_rhohat * G.rho[i];
+    // rho_hat = mu rho (rectified, Eq. 7) or rho_hat = rho (X-3DGS, no mu term)
+    g.rho[oi] += cam.biased ? d_rhohat : d_rhohat * P.mu;
+    const double dmu = cam.biased ? 0.0 : d_rhohat * G.rho[i];
     // mu = sqrt(2 pi d3 / d2)
     const double dd3 = dmu * P.mu / (2.0 * P.d3);
     const double dd2 = -dmu * P.mu / (2.0 * P.d2);
@@ -722,6 +724,7 @@ Cam make_cam(const double* c) {
     cam.off_v = c[7];
     cam.near_plane = c[8];
     cam.jmode = (int)c[9];
+    cam.biased = (int)c[10];
     return cam;
 }
 
@@ -874,7 +877,7 @@ int brick_bound_f32(const float* p, const float* s, const float* q, const float*
 
 extern "C" {
 
-// cam: [beam, H, W, L_SD, pitch_u, pitch_v, off_u, off_v, near_plane, jmode]
+// cam: [beam, H, W, L_SD, pitch_u, pitch_v, off_u, off_v, near_plane, jmode, biased]
 int64_t orc_render(int64_t M, const double* mean, const double* scale, const double* quat, const double* rho,
                    const double* views, int V, const double* camv, double Q, int brute, double* img, double* band) {
     const Params P{M, mean, scale, quat, rho};
@@ -902,6 +905,28 @@ void orc_project(int64_t M, const double* mean, const double* scale, const doubl
             o[10] = P.u[2];
             o[11] = std::sqrt(P.u[0] * P.u[0] + P.u[1] * P.u[1] + P.u[2] * P.u[2]);
         }
+}
+
+// Mean over the views of the integration-bias factor mu = sqrt(2 pi |Sigma~| / |Sigma^|)
+// of each Gaussian (Eq. 7), counting only the views in which it projects (cone beam:
+// u2 > near plane); 0 where it projects in none.  mu_mean[i] for Gaussian i.
+void orc_mean_mu(int64_t M, const double* mean, const double* scale, const double* quat, const double* views,
+                 int V, const double* camv, double* mu_mean) {
+    const Cam cam = make_cam(camv);
+    for (int64_t i = 0; i < M; ++i) {
+        M3<double> Sigma, R;
+        double qn[4], qnorm;
+        covariance(&scale[3 * i], &quat[4 * i], Sigma, R, qn, qnorm);
+        double sum = 0.0;
+        int n = 0;
+        for (int v = 0; v < V; ++v) {
+            Proj<double> P = project_one(&mean[3 * i], Sigma, 1.0, views + 12 * v, cam);
+            if (!P.valid) continue;
+            sum += P.mu;
+            ++n;
+        }
+        mu_mean[i] = n ? sum / n : 0.0;
+    }
 }
 
 // Complex-step derivative of the whole image with respect to one parameter:

@@ -38,6 +38,7 @@ namespace {
 struct CamF {
     int beam, H, W;
     float L_SD, pu, pv, ou, ov, near_plane;
+    int biased;  // 1: rho_hat = rho (no Eq. 7 factor)
 };
 
 struct Params {
@@ -230,9 +231,13 @@ __device__ __forceinline__ uint32_t project_one(const Params& G, const float* __
     const Bound b = pixel_bound(P, cam, Q);
     float rhohat = 0.0f;
     if (b.ok) {
-        float om[3], vv[3];
-        const float kap = kappa_of(P, s, view, cam, om, vv);
-        rhohat = sqrtf(kTwoPi / kap) * G.rho[i];
+        if (cam.biased) {
+            rhohat = G.rho[i];
+        } else {
+            float om[3], vv[3];
+            const float kap = kappa_of(P, s, view, cam, om, vv);
+            rhohat = sqrtf(kTwoPi / kap) * G.rho[i];
+        }
     }
     if (rec) {
         float4 a, c;
@@ -741,25 +746,29 @@ __global__ void __launch_bounds__(128) k_project_bwd(Params G, const float* __re
                 gR[j][k] += dM[j][k] * s[k];
                 gs[k] += dM[j][k] * P.R[j][k];
             }
-        // --- rho_hat = mu rho, mu = sqrt(2 pi / kappa)
-        float om[3], vv[3];
-        const float kap = kappa_of(P, s, view, cam, om, vv);
-        const float mu = sqrtf(kTwoPi / kap);
-        grho += d_rhohat * mu;
-        const float d_kap = -0.5f * d_rhohat * rho * mu / kap;
-        float dv[3];
+        // --- rho_hat = mu rho, mu = sqrt(2 pi / kappa) (biased: rho_hat = rho)
+        float dom[3] = {0.f, 0.f, 0.f};
+        if (cam.biased) {
+            grho += d_rhohat;
+        } else {
+            float om[3], vv[3];
+            const float kap = kappa_of(P, s, view, cam, om, vv);
+            const float mu = sqrtf(kTwoPi / kap);
+            grho += d_rhohat * mu;
+            const float d_kap = -0.5f * d_rhohat * rho * mu / kap;
+            float dv[3];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const float is2 = 1.0f / (s[k] * s[k]);
-            dv[k] = 2.f * d_kap * vv[k] * is2;
-            gs[k] += -2.f * d_kap * vv[k] * vv[k] * is2 / s[k];
-        }
-        float dom[3];
+            for (int k = 0; k < 3; ++k) {
+                const float is2 = 1.0f / (s[k] * s[k]);
+                dv[k] = 2.f * d_kap * vv[k] * is2;
+                gs[k] += -2.f * d_kap * vv[k] * vv[k] * is2 / s[k];
+            }
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
+            for (int j = 0; j < 3; ++j) {
 #pragma unroll
-            for (int k = 0; k < 3; ++k) gR[j][k] += om[j] * dv[k];
-            dom[j] = P.R[j][0] * dv[0] + P.R[j][1] * dv[1] + P.R[j][2] * dv[2];
+                for (int k = 0; k < 3; ++k) gR[j][k] += om[j] * dv[k];
+                dom[j] = P.R[j][0] * dv[0] + P.R[j][1] * dv[1] + P.R[j][2] * dv[2];
+            }
         }
         // --- scanner-space mean
         float du[3] = {0.f, 0.f, 0.f};
@@ -813,6 +822,30 @@ __global__ void __launch_bounds__(128) k_project_bwd(Params G, const float* __re
 #pragma unroll
     for (int k = 0; k < 4; ++k) dquat[4 * i + k] += gq[k];
     drho[i] += grho;
+}
+
+// Eq. 7's factor mu averaged over the views in front of the near plane; with
+// rho_vol, also rho / mean mu (0 where no view keeps the Gaussian).
+__global__ void __launch_bounds__(256) k_mean_mu(Params G, const float* __restrict__ views, CamF cam, long long M,
+                                                 int V, float* __restrict__ mu_mean, float* __restrict__ rho_vol) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    float p[3], s[3], q[4];
+    load_gaussian(G, i, p, s, q);
+    float sum = 0.f;
+    int n = 0;
+    for (int v = 0; v < V; ++v) {
+        const float* view = views + 12 * (size_t)v;
+        Proj P;
+        project_stated(p, s, q, view, cam, P);
+        if (cam.beam == 1 && !(P.u[2] > cam.near_plane)) continue;
+        float om[3], vv[3];
+        sum += sqrtf(kTwoPi / kappa_of(P, s, view, cam, om, vv));
+        ++n;
+    }
+    const float mm = n ? sum / (float)n : 0.f;
+    if (mu_mean) mu_mean[i] = mm;
+    if (rho_vol) rho_vol[i] = n ? G.rho[i] / mm : 0.f;
 }
 
 // ------------------------------------------------------------------ host side
@@ -900,8 +933,9 @@ long long capacity_of(const RasterLayout& L, size_t ws_bytes, int tile_px) {
     return cap;
 }
 
-CamF camf(const r2g_camera* c) {
+CamF camf(const r2g_camera* c, const r2g_raster_opts* o) {
     CamF f;
+    f.biased = o->biased != 0;
     f.beam = c->beam;
     f.H = c->H;
     f.W = c->W;
@@ -998,11 +1032,30 @@ R2G_API r2g_status r2g_project(int64_t M, const float* mean, const float* scale,
     if (reinterpret_cast<uintptr_t>(quat) % 16) return fail(R2G_E_INVAL, "quat must be 16-byte aligned");
     const long long n = (long long)M * V;
     Params G{mean, scale, quat, rho};
-    k_project<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(G, views, nullptr, camf(cam), opts->Q, opts->tile_w,
+    k_project<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(G, views, nullptr, camf(cam, opts), opts->Q, opts->tile_w,
                                                                 opts->tile_h, M, n, 1, nullptr, nullptr, proj, rect,
                                                                 nullptr, ListCount{});
     note_launches(1);
     return check_launch("r2g_project");
+}
+
+R2G_API r2g_status r2g_mean_mu(int64_t M, const float* mean, const float* scale, const float* quat,
+                               const float* rho, int32_t V, const float* views, const r2g_camera* cam,
+                               float* mu_mean, float* rho_vol, r2g_stream stream) {
+    r2g_raster_opts o{};
+    o.Q = 9.f;
+    o.tile_w = o.tile_h = 16;
+    r2g_status e = check_args(M, V, cam, &o);
+    if (e) return e;
+    if (!mean || !scale || !quat || !views) return fail(R2G_E_INVAL, "NULL device pointer");
+    if (!mu_mean && !rho_vol) return fail(R2G_E_INVAL, "mu_mean and rho_vol are both NULL");
+    if (rho_vol && !rho) return fail(R2G_E_INVAL, "rho_vol needs rho");
+    if (reinterpret_cast<uintptr_t>(quat) % 16) return fail(R2G_E_INVAL, "quat must be 16-byte aligned");
+    if (M == 0) return R2G_OK;
+    Params G{mean, scale, quat, rho};
+    k_mean_mu<<<(unsigned)((M + 255) / 256), 256, 0, stream>>>(G, views, camf(cam, &o), M, V, mu_mean, rho_vol);
+    note_launches(1);
+    return check_launch("r2g_mean_mu");
 }
 
 r2g_status r2g::rasterize_impl(int64_t M, const float* mean, const float* scale, const float* quat,
@@ -1038,7 +1091,7 @@ r2g_status r2g::rasterize_impl(int64_t M, const float* mean, const float* scale,
     // the general list path gives empty tiles no work item: their pixels stay zero
     if (!fused_lists(L.n_tiles)) cudaMemsetAsync(image, 0, sizeof(float) * (size_t)V * cam->H * cam->W, stream);
     Params G{mean, scale, quat, rho};
-    const CamF cf = camf(cam);
+    const CamF cf = camf(cam, opts);
     prof_begin(P_PROJECT, stream);
     const ListBlocking lb = list_blocking(L.n_rec);
     k_project<<<(unsigned)lb.blocks, 256, 0, stream>>>(G, views, view_sel, cf, opts->Q, opts->tile_w, opts->tile_h, M,
@@ -1106,10 +1159,10 @@ r2g_status r2g::rasterize_backward_impl(int64_t M, const float* mean, const floa
         const unsigned grid = (unsigned)((M + 127) / 128);
         prof_begin(P_PROJECT_BWD, stream);
         if (adam)
-            k_project_bwd<true><<<grid, 128, 0, stream>>>(G, views, view_sel, camf(cam), opts->Q, M, V, rec, mom,
+            k_project_bwd<true><<<grid, 128, 0, stream>>>(G, views, view_sel, camf(cam, opts), opts->Q, M, V, rec, mom,
                                                           nullptr, nullptr, nullptr, nullptr, *adam);
         else
-            k_project_bwd<false><<<grid, 128, 0, stream>>>(G, views, view_sel, camf(cam), opts->Q, M, V, rec, mom,
+            k_project_bwd<false><<<grid, 128, 0, stream>>>(G, views, view_sel, camf(cam, opts), opts->Q, M, V, rec, mom,
                                                            dmean, dscale, dquat, drho, AdamState{});
         prof_end(P_PROJECT_BWD, stream);
         note_launches(1);

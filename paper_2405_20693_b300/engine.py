@@ -27,11 +27,11 @@ def _bytes(n: int, device) -> torch.Tensor:
 class Rasterizer:
     """Owns the workspace of one (M, V, camera, tile) configuration."""
 
-    def __init__(self, M: int, V: int, cam, Q=Q_PIXEL, tile=(16, 16), device="cuda", capacity=None):
+    def __init__(self, M: int, V: int, cam, Q=Q_PIXEL, tile=(16, 16), device="cuda", capacity=None, biased=False):
         self.M, self.V = int(M), int(V)
         self.cam = r2g.camera(cam)
-        self.opts = r2g.raster_opts(Q, tile)
-        self.copts = r2g.raster_opts(Q, tile, count_pairs=True)
+        self.opts = r2g.raster_opts(Q, tile, biased=biased)
+        self.copts = r2g.raster_opts(Q, tile, count_pairs=True, biased=biased)
         self.device = device
         self.capacity = int(capacity or max(1 << 16, 4 * self.M * self.V))
         self.ws = None
@@ -243,8 +243,9 @@ class Scan:
     descriptor for r2g_train_step."""
 
     def __init__(self, G, views_np, meas_np, cam, n_out=256, D=32, tile=None, total_iters=30000,
-                 device="cuda", headroom=1.5, seed=0):
+                 device="cuda", headroom=1.5, seed=0, biased=False):
         self.state = TrainState(G, device=device)
+        self.biased = bool(biased)
         self.rng = np.random.Generator(np.random.PCG64(seed + 2))  # this scan's view / patch choices
         self.it = 0
         self.M = G.M
@@ -259,7 +260,7 @@ class Scan:
         self.vol = torch.empty(D ** 3, dtype=torch.float32, device=device)
         self.dvol = torch.empty_like(self.vol)
         self.loss = torch.zeros(2, dtype=torch.float32, device=device)
-        self.rast = Rasterizer(self.M, 1, cam, tile=tile or SCAN_TILE, device=device)
+        self.rast = Rasterizer(self.M, 1, cam, tile=tile or SCAN_TILE, device=device, biased=biased)
         from .inputs import patch_grid
 
         self.vox = Voxelizer(self.M, patch_grid((0, 0, 0), D, n_out), device=device)
@@ -268,6 +269,18 @@ class Scan:
         self.adam = r2g.adam_opts(total_iters=total_iters)
         self._size_workspaces(headroom)
         self.job = self._make_job()
+
+    def volume_params(self):
+        """(mean, scale, quat, rho) for the voxelizer.  The rectified model's densities
+        are the 3D densities; the X-3DGS variant (biased=True) learned mu rho per view,
+        so each density is divided by its Gaussian's mean mu over the training views
+        (Sec. 4.2.1) -- in the r2g_mean_mu kernel."""
+        mean, scale, quat, rho = self.state.params()
+        if not self.biased:
+            return mean, scale, quat, rho
+        rv = torch.empty_like(rho)
+        r2g.r2g_mean_mu(mean, scale, quat, self.views, self.rast.cam, rho=rho, rho_vol=rv)
+        return mean, scale, quat, rv
 
     def _size_workspaces(self, headroom):
         """Size the list workspaces on a spread of views and patch positions with

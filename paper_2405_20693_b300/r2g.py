@@ -35,7 +35,7 @@ class Camera(ctypes.Structure):
 
 class RasterOpts(ctypes.Structure):
     _fields_ = [("Q", ctypes.c_float), ("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32),
-                ("count_pairs", ctypes.c_int32)]
+                ("count_pairs", ctypes.c_int32), ("biased", ctypes.c_int32)]
 
 
 class Grid(ctypes.Structure):
@@ -71,8 +71,8 @@ def camera(cam) -> Camera:
                   float(cam.off_u), float(cam.off_v), float(cam.near_plane))
 
 
-def raster_opts(Q=9.0, tile=(16, 16), count_pairs=False) -> RasterOpts:
-    return RasterOpts(float(Q), int(tile[0]), int(tile[1]), int(bool(count_pairs)))
+def raster_opts(Q=9.0, tile=(16, 16), count_pairs=False, biased=False) -> RasterOpts:
+    return RasterOpts(float(Q), int(tile[0]), int(tile[1]), int(bool(count_pairs)), int(bool(biased)))
 
 
 def grids(gdescs) -> ctypes.Array:
@@ -116,6 +116,7 @@ def lib():
             "r2g_rasterize_backward": (_I32, [_I64, _P, _P, _P, _P, _I32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _SZ,
                                               _P]),
             "r2g_project": (_I32, [_I64, _P, _P, _P, _P, _I32, _P, _P, _P, _P, _P, _P]),
+            "r2g_mean_mu": (_I32, [_I64, _P, _P, _P, _P, _I32, _P, _P, _P, _P, _P]),
             "r2g_raster_lists": (_I32, [_I64, _I32, _P, _P, _P, _SZ, _P, _P, _I64, _P, _P]),
             "r2g_pair_count": (_I32, [_P, _SZ, _P, _P]),
             "r2g_voxel_workspace_size": (_SZ, [_I64, _I32, _P, _I64]),
@@ -218,6 +219,13 @@ def r2g_project(mean, scale, quat, rho, views, cam: Camera, opts: RasterOpts, pr
     M, V = mean.shape[0], views.shape[0]
     _check(lib().r2g_project(M, _ptr(mean), _ptr(scale), _ptr(quat), _ptr(rho), V, _ptr(views), ctypes.byref(cam),
                              ctypes.byref(opts), _ptr(proj), _ptr(rect), _stream(stream)))
+
+
+def r2g_mean_mu(mean, scale, quat, views, cam: Camera, mu_mean=None, rho=None, rho_vol=None, stream=None):
+    _f32(mean, scale, quat, views, mu_mean, rho, rho_vol)
+    M, V = mean.shape[0], views.shape[0]
+    _check(lib().r2g_mean_mu(M, _ptr(mean), _ptr(scale), _ptr(quat), _ptr(rho), V, _ptr(views), ctypes.byref(cam),
+                             _ptr(mu_mean), _ptr(rho_vol), _stream(stream)))
 
 
 def r2g_raster_lists(M: int, V: int, cam: Camera, opts: RasterOpts, ws, ranges, ids, stream=None) -> int:

@@ -1,4 +1,5 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle."""
+import dataclasses
 import math
 
 import numpy as np
@@ -315,3 +316,82 @@ def test_capacity_overflow_is_reported_and_recovered():
     assert rast.capacity >= needed
     ref, _, band = core.render(G, views, cam, Q=Q9, want_band=True)
     assert_values_close(host(out), ref, band, "after regrow")
+
+
+# ----------------------------------------------------------------------------- X-3DGS amplitude (Sec. 4.2.1)
+
+
+@pytest.mark.parametrize("case", ["config1", "cone"])
+def test_rasterize_biased_matches_oracle(case):
+    """rho_hat = rho (no Eq. 7 factor): image, projection record and adjoint."""
+    G, cam, views = _case(case)
+    V = views.shape[0]
+    rast = engine.Rasterizer(G.M, V, cam, biased=True)
+    mean, scale, quat, rho = dev_set(G)
+    vv = dev(views)
+    img = rast.forward(mean, scale, quat, rho, vv)
+    torch.cuda.synchronize()
+    ref, _, band = core.render(G, views, cam, Q=Q9, want_band=True, biased=True)
+    assert_values_close(host(img), ref, band, f"{case} biased")
+    # the projection record carries rho itself
+    proj = torch.empty((V, G.M, 8), dtype=torch.float32, device="cuda")
+    rect = torch.empty((V, G.M, 4), dtype=torch.int32, device="cuda")
+    r2g.r2g_project(mean, scale, quat, rho, vv, rast.cam, rast.opts, proj, rect)
+    p = proj.cpu().numpy()
+    valid = p[..., 7] == 1.0
+    assert np.array_equal(p[..., 6][valid], np.broadcast_to(G.rho.astype(np.float32), p[..., 6].shape)[valid])
+    dimg = I.rng(8).standard_normal((V, cam.H, cam.W)).astype(np.float32)
+    g = [torch.zeros_like(t) for t in (mean, scale, quat, rho)]
+    rast.backward(mean, scale, quat, rho, vv, dev(dimg), *g)
+    torch.cuda.synchronize()
+    refg, bandg = core.render_backward(G, views, cam, dimg, Q=Q9, want_band=True, biased=True)
+    for name, a, b, bd in zip(("mean", "scale", "quat", "rho"), g, refg, bandg):
+        assert_grads_close(host(a), b, f"{case} biased d{name}", band=bd)
+
+
+def test_mean_mu_matches_oracle():
+    """r2g_mean_mu against the oracle, cone beam with a near plane that drops the
+    Gaussians on the source's side in some views, and parallel beam."""
+    G, cam, views = cone_small(M=2000, V=5)
+    cam_np = dataclasses.replace(cam, near_plane=I.CONE_L_SO)
+    # Gaussians within 1e-4 of the near plane in some view may fall on either side in FP32
+    u2 = np.einsum("vj,mj->vm", views[:, 6:9].astype(np.float64), G.mean.astype(np.float64)) + views[:, 11:12]
+    sure = (np.abs(u2 - I.CONE_L_SO) > 1e-4).all(axis=0)
+    for c in (cam, cam_np, I.parallel_camera(64, 64, 2.0 / 64)):
+        mean, scale, quat, rho = dev_set(G)
+        out = torch.empty(G.M, dtype=torch.float32, device="cuda")
+        rv = torch.empty(G.M, dtype=torch.float32, device="cuda")
+        r2g.r2g_mean_mu(mean, scale, quat, dev(views), r2g.camera(c), out, rho=rho, rho_vol=rv)
+        full = core.mean_mu(G, views, c)
+        ref, got = full[sure], host(out)[sure]
+        assert np.array_equal(got == 0, ref == 0)
+        assert np.abs(got - ref).max() <= 2e-5 * np.abs(ref).max()
+        # rho / mean mu where some view keeps the Gaussian, else 0
+        keep = full > 0
+        want = np.where(keep, G.rho / np.where(keep, full, 1.0), 0.0)[sure]
+        assert np.abs(host(rv)[sure] - want).max() <= 2e-5 * np.abs(want).max()
+    assert (core.mean_mu(G, views, cam_np) == 0).sum() < G.M  # some views dropped, not all
+
+
+def test_biased_per_view_fit_recovers_mu_rho():
+    """The view-consistency argument of Sec. 4.2.1 on the CUDA path: each view's
+    measured projection is the oracle's rectified render of one anisotropic Gaussian;
+    the least-squares amplitude of the GPU's biased splat is mu_v rho (it changes
+    with the view), that of the GPU's rectified splat is rho in every view."""
+    g = I.rng(45)
+    mean = np.zeros((1, 3))
+    scale = np.array([[0.03, 0.12, 0.07]])
+    quat = I.random_quats(g, 1)
+    G = I.GaussianSet(mean, scale, quat, np.array([0.8])).astype(np.float32)
+    cam = I.parallel_camera(64, 64, 2.0 / 64)
+    views = I.view_table(np.deg2rad([0.0, 40.0, 85.0, 130.0, 170.0]), I.CONE_L_SO)
+    meas, _ = core.render(G, views, cam, Q=Q9)
+    unit = I.GaussianSet(G.mean, G.scale, G.quat, np.ones(1, np.float32))
+    mu = core.project(unit, views, cam)[:, 0, 8]
+    for biased, expect in ((False, np.full(5, 0.8)), (True, 0.8 * mu)):
+        rast = engine.Rasterizer(1, 5, cam, biased=biased)
+        b = host(rast.forward(*dev_set(unit), dev(views)))
+        fit = (b * meas).sum(axis=(1, 2)) / (b * b).sum(axis=(1, 2))
+        # one pixel whose q sits on the gate in FP32 moves a fit by ~1e-4 at most
+        assert np.abs(fit / expect - 1).max() <= 2e-4, (biased, fit, expect)
+    assert mu.max() / mu.min() > 1.3

@@ -315,6 +315,144 @@ def test_voxelize_adjoint_matches_complex_step():
                 assert abs(cs - arr[i, c]) <= 1e-10 * max(abs(cs), 1e-8), (kind, i, c, cs, arr[i, c])
 
 
+# ----------------------------------------------------------------------------- X-3DGS amplitude (Sec. 4.2.1)
+
+
+def _cov(scale, quat):
+    """Sigma = R S S^T R^T with scipy's rotation of the (w, x, y, z) quaternion."""
+    w, x, y, z = quat
+    R = Rotation.from_quat([x, y, z, w]).as_matrix()
+    return R @ np.diag(np.asarray(scale) ** 2) @ R.T
+
+
+def _aniso(M=5, seed=41):
+    """Strongly anisotropic Gaussians (axis ratio up to 5) so mu varies with the view."""
+    g = I.rng(seed)
+    mean = g.uniform(-0.2, 0.2, (M, 3))
+    scale = np.stack([g.uniform(0.02, 0.03, M), g.uniform(0.08, 0.1, M), g.uniform(0.04, 0.1, M)], axis=1)
+    return I.GaussianSet(mean, scale, I.random_quats(g, M), g.uniform(0.3, 1.0, M))
+
+
+def test_biased_projected_mass_is_the_2d_gaussian_mass():
+    """Parallel beam, no gate: with rho_hat = rho the splat of Gaussian i is an
+    unnormalised 2D Gaussian of covariance Sigma^_v (top-left 2x2 of W Sigma W^T), so
+    its detector mass is rho 2 pi sqrt|Sigma^_v| -- view-dependent, unlike the 3D
+    mass rho (2 pi)^{3/2} sqrt|Sigma| that the rectified splat keeps in every view."""
+    G = _aniso()
+    pitch = 2.0 / 96
+    cam = I.parallel_camera(96, 96, pitch)
+    ang = np.deg2rad([0.0, 37.0, 90.0, 151.0])
+    views = I.view_table(ang, 4.0, dtype=np.float64)
+    masses = []
+    for i in range(G.M):
+        Gi = G.subset([i])
+        img, _ = core.render(Gi, views, cam, Q=math.inf, biased=True)
+        S = _cov(G.scale[i], G.quat[i])
+        for v in range(len(ang)):
+            Wm = views[v, :9].reshape(3, 3)
+            Sh = (Wm @ S @ Wm.T)[:2, :2]
+            expect = G.rho[i] * 2 * np.pi * np.sqrt(np.linalg.det(Sh))
+            got = img[v].sum() * pitch * pitch
+            assert abs(got - expect) <= 1e-9 * expect, (i, v, got, expect)
+            masses.append(got)
+    # the anisotropy makes the biased mass move by more than 10% across views
+    m = np.array(masses).reshape(G.M, len(ang))
+    assert np.all(m.max(axis=1) / m.min(axis=1) > 1.1)
+
+
+def test_biased_splat_is_rectified_over_mu():
+    """Gaussian by Gaussian the two amplitudes differ by exactly mu_v (Eq. 7): the
+    rectified image equals mu_v times the biased one, cone and parallel beam, gated."""
+    G = _aniso(4, 43)
+    views = I.view_table(np.deg2rad([12.0, 100.0, 222.0]), 4.0, dtype=np.float64)
+    cone = I.Camera(beam=1, H=40, W=44, L_SD=6.0, pitch_u=2.5 / 44, pitch_v=2.5 / 40, near_plane=0.04)
+    par = I.parallel_camera(40, 44, 2.0 / 44)
+    for cam in (cone, par):
+        for i in range(G.M):
+            Gi = G.subset([i])
+            rect, pr = core.render(Gi, views, cam, Q=Q9)
+            bias, pb = core.render(Gi, views, cam, Q=Q9, biased=True)
+            assert pr == pb
+            mu = core.project(Gi, views, cam)[:, 0, 8]
+            for v in range(views.shape[0]):
+                assert np.abs(rect[v] - mu[v] * bias[v]).max() <= 1e-13 * np.abs(rect[v]).max()
+
+
+def test_mean_mu_matches_direct_ray_formula():
+    """mean_mu = the average over the views that keep the Gaussian of
+    sqrt(2 pi / (omega^T Sigma^-1 omega)), omega the unit ray through the mean (the
+    view direction for parallel beam, source -> mean for cone beam); a near plane at
+    the source distance drops the views in which the Gaussian lies on the source's side."""
+    G = _aniso(6, 44)
+    ang = np.deg2rad([0.0, 61.0, 133.0, 250.0, 300.0])
+    views = I.view_table(ang, 4.0, dtype=np.float64)
+    cone = I.Camera(beam=1, H=8, W=8, L_SD=6.0, pitch_u=0.4, pitch_v=0.4, near_plane=4.0)
+    par = I.parallel_camera(8, 8, 0.25)
+    for cam in (cone, par):
+        got = core.mean_mu(G, views, cam)
+        n_dropped = 0
+        for i in range(G.M):
+            Si = np.linalg.inv(_cov(G.scale[i], G.quat[i]))
+            vals = []
+            for v in range(len(ang)):
+                Wm, t = views[v, :9].reshape(3, 3), views[v, 9:]
+                if cam.beam == 1:
+                    if (Wm @ G.mean[i] + t)[2] <= cam.near_plane:
+                        n_dropped += 1
+                        continue
+                    om = G.mean[i] + Wm.T @ t
+                else:
+                    om = Wm[2].copy()
+                om /= np.linalg.norm(om)
+                vals.append(np.sqrt(2 * np.pi / (om @ Si @ om)))
+            expect = np.mean(vals) if vals else 0.0
+            assert abs(got[i] - expect) <= 1e-11 * expect, (cam.beam, i, got[i], expect)
+        if cam.beam == 1:
+            assert 0 < n_dropped < G.M * len(ang)
+
+
+def test_biased_fit_is_view_inconsistent():
+    """Sec. 4.2.1's argument on one anisotropic Gaussian: fit the amplitude of each
+    view's splat to that view's exact projection by least squares.  Rectified splats
+    recover the true density in every view; biased splats recover mu_v rho, which
+    changes with the view.  One biased amplitude fitted to all views together is rho
+    times the harmonic mean of mu_v (each view's splat energy is proportional to
+    sqrt|Sigma^_v|, i.e. to 1 / mu_v), so no single density fits every view."""
+    G = _aniso(1, 45)
+    pitch = 2.0 / 64
+    cam = I.parallel_camera(64, 64, pitch)
+    views = I.view_table(np.deg2rad([0.0, 40.0, 85.0, 130.0, 170.0]), 4.0, dtype=np.float64)
+    meas = core.render_exact(G, views, cam)
+    unit = I.GaussianSet(G.mean, G.scale, G.quat, np.ones(1))
+    basis_r, _ = core.render(unit, views, cam, Q=math.inf)
+    basis_b, _ = core.render(unit, views, cam, Q=math.inf, biased=True)
+    mu = core.project(unit, views, cam)[:, 0, 8]
+    rho = G.rho[0]
+    fit_r = (basis_r * meas).sum(axis=(1, 2)) / (basis_r ** 2).sum(axis=(1, 2))
+    fit_b = (basis_b * meas).sum(axis=(1, 2)) / (basis_b ** 2).sum(axis=(1, 2))
+    assert np.abs(fit_r / rho - 1).max() <= 1e-10
+    assert np.abs(fit_b / (mu * rho) - 1).max() <= 1e-10
+    assert fit_b.max() / fit_b.min() > 1.2
+    joint = (basis_b * meas).sum() / (basis_b ** 2).sum()
+    assert abs(joint / (rho * len(mu) / (1.0 / mu).sum()) - 1) <= 1e-10
+
+
+def test_biased_adjoint_matches_complex_step():
+    """The biased chain rule (rho_hat = rho: no mu branch) against complex steps."""
+    G = small_set(4, 3)
+    views = I.view_table(np.deg2rad([10, 37, 100]), 4.0)
+    cam = I.Camera(beam=1, H=24, W=28, L_SD=6.0, pitch_u=3.0 / 28, pitch_v=3.0 / 24, off_u=0.05, near_plane=0.04)
+    g = np.random.default_rng(4).standard_normal((3, cam.H, cam.W))
+    dm, ds, dq, dr = core.render_backward(G, views, cam, g, Q=Q9, biased=True)
+    dm_r = core.render_backward(G, views, cam, g, Q=Q9)[0]
+    assert np.abs(dm - dm_r).max() > 1e-3 * np.abs(dm_r).max()   # the variants differ
+    for kind, arr, nc in ((0, dm, 3), (1, ds, 3), (2, dq, 4), (3, dr[:, None], 1)):
+        for i in range(G.M):
+            for c in range(nc):
+                cs = (core.render_cs(G, views, cam, Q9, kind, i, c, biased=True) * g).sum()
+                assert abs(cs - arr[i, c]) <= 1e-10 * max(abs(cs), 1e-8), (kind, i, c, cs, arr[i, c])
+
+
 # ----------------------------------------------------------------------------- losses
 
 
