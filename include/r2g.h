@@ -324,6 +324,51 @@ r2g_status r2g_train_step(const r2g_job* job, const r2g_round_entry* entry, r2g_
  * each time the graph runs, so the host rewrites it between replays). */
 r2g_status r2g_upload_round(r2g_round_entry* dst, const r2g_round_entry* src, int32_t n, r2g_stream stream);
 
+/* ---------------------------------------------------------------- FDK initialisation (Sec. 4.1)
+ *
+ * The preliminary reconstruction that the Gaussians start from: Feldkamp-Davis-
+ * Kress filtered back-projection for a circular orbit and a flat detector (cone
+ * beam), or plain filtered back-projection (parallel beam), then M positions drawn
+ * among the voxels above a density threshold.  Projections are the log
+ * projections of Eq. 1 on the camera's detector, [V][H][W] row-major. */
+
+/* Pre-weighting and ramp filtering of every detector row: filt[v][r][c] =
+ * (1 / pitch_u) sum_n c_(c-n) R'[v][r][n], R' = proj * L_SD / sqrt(L_SD^2 + xi^2 +
+ * eta^2) (cone; parallel: R' = proj), c_0 = 1/8, c_m = -1/(2 pi^2 m^2) for odd m
+ * and 0 for even m != 0 -- the band-limited (Ram-Lak) ramp at the detector
+ * spacing with the factor 1/2 of a full-circle scan; the row is zero outside the
+ * detector.  proj, filt: device [V][H][W], not aliased.  W <= 8192. */
+r2g_status r2g_fdk_filter(int32_t V, const r2g_camera* cam, const float* proj, float* filt, r2g_stream stream);
+
+/* Back-projection of filtered projections onto one grid: vol[z][y][x] (device,
+ * written) = dbeta * sum_v w_v F_v(xi, eta) at the voxel centre p, u = W_v p + t_v;
+ * cone: (xi, eta) = L_SD (u0, u1) / u2, w_v = t_v[2] L_SD / u2^2 (views with u2 <=
+ * near_plane skip the voxel); parallel: (xi, eta) = (u0, u1), w_v = 1.  F_v is
+ * read by bilinear interpolation between pixel centres; samples outside the
+ * detector count as zero.  dbeta = angular step of the views (2 pi / V for V
+ * evenly spaced views on a full circle).  views: device [V][12] as for the
+ * rasterizer; filt: device [V][H][W]. */
+r2g_status r2g_fdk_backproject(int32_t V, const float* views, const r2g_camera* cam, const float* filt,
+                               const r2g_grid* grid, float dbeta, float* vol, r2g_stream stream);
+
+/* Workspace bytes of r2g_init_gaussians for this grid and M (0 for bad arguments). */
+size_t r2g_init_workspace_size(const r2g_grid* grid, int64_t M);
+
+/* Sec. 4.1's initialisation from a volume vol[z][y][x] (device) on `grid`:
+ * candidates are the voxels with vol > tau (FP32 comparison); candidate j (flat
+ * index) gets the key SplitMix64(seed + (j + 1) * 0x9E3779B97F4A7C15) (Steele, Lea
+ * & Flood 2014), and the M candidates with the smallest (key, j) are chosen (all
+ * of them when there are at most M).  The chosen voxels, in increasing index
+ * order, become Gaussians: mean = voxel centre, quat = (1, 0, 0, 0), rho = k *
+ * vol, and an isotropic scale = the mean distance to the three nearest other
+ * chosen centres (fewer when fewer exist; the smallest voxel edge for a lone one).
+ * mean[M][3], scale[M][3], quat[M][4] (16-byte aligned), rho[M]: device, the
+ * first *n_out rows written; n_out: device int64 (number chosen).  ws: device,
+ * r2g_init_workspace_size bytes.  The grid has fewer than 2^31 voxels. */
+r2g_status r2g_init_gaussians(const float* vol, const r2g_grid* grid, float tau, int64_t M, uint64_t seed, float k,
+                              float* mean, float* scale, float* quat, float* rho, int64_t* n_out, void* ws,
+                              size_t ws_bytes, r2g_stream stream);
+
 /* ---------------------------------------------------------------- measurement
  *
  * Optional timing of the library's own kernels: when enabled, every call records
@@ -331,7 +376,9 @@ r2g_status r2g_upload_round(r2g_round_entry* dst, const r2g_round_entry* src, in
  * 0 project, 1 emit (tile entries: count + emit), 2 sort (tile lists: offsets +
  * scatter, or the radix passes), 3 ranges (radix path only), 4 splat_fwd,
  * 5 splat_bwd, 6 project_bwd, 7 vox_project, 8 vox_fwd, 9 vox_bwd, 10 vox_chain,
- * 11 loss, 12 tv, 13 adam, 14-16 the same three list stages for the brick lists.
+ * 11 loss, 12 tv, 13 adam, 14-16 the same three list stages for the brick lists,
+ * 17 fdk_filter, 18 fdk_bp, 19 init_select (the selection passes and the writes
+ * of r2g_init_gaussians), 20 init_knn.
  * Not for use inside stream capture.
  * max_spans bounds the recorded pairs (events are created once, here). */
 r2g_status r2g_profile_enable(int32_t on, int32_t max_spans);

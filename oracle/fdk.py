@@ -69,10 +69,11 @@ def detector_coords(cam):
     return xi, eta
 
 
-def fdk_filter(proj, cam) -> np.ndarray:
+def fdk_filter(proj, cam, rows=None) -> np.ndarray:
     """Weighted, ramp-filtered projections F [V, H, W] (float64) from log projections
     [V, H, W]: pre-weighting (cone beam), then each detector row convolved with the
-    taps c_n over the whole row (no wrap-around), divided by pitch_u."""
+    taps c_n over the whole row (no wrap-around), divided by pitch_u.  rows: an
+    optional boolean mask [V, H] of the rows to compute (the others are NaN)."""
     proj = np.asarray(proj, dtype=np.float64)
     V, H, W = proj.shape
     if cam.beam == 1:
@@ -80,9 +81,11 @@ def fdk_filter(proj, cam) -> np.ndarray:
         XI, ETA = np.meshgrid(xi, eta)
         proj = proj * (cam.L_SD / np.sqrt(cam.L_SD ** 2 + XI ** 2 + ETA ** 2))
     c = ramp_taps(W - 1)
-    out = np.empty_like(proj)
+    out = np.full_like(proj, np.nan)
     for v in range(V):
         for r in range(H):
+            if rows is not None and not rows[v, r]:
+                continue
             # full convolution has length 2W-1 + W-1; the outputs at the pixel
             # centres are the middle W samples
             out[v, r] = np.convolve(proj[v, r], c)[W - 1:2 * W - 1]
@@ -175,9 +178,10 @@ def splitmix64_stream(seed: int, n: int) -> np.ndarray:
 def sample_candidates(vol, tau: float, M: int, seed: int) -> np.ndarray:
     """Flat voxel indices of the M candidates (vol > tau) with the smallest keys
     SplitMix64(seed + (j + 1) * golden), in increasing index order; all candidates
-    if there are at most M."""
+    if there are at most M.  The threshold comparison is made in the volume's own
+    precision (tau rounded to it), as the kernel makes it."""
     v = np.asarray(vol).ravel()
-    cand = np.flatnonzero(v > tau)
+    cand = np.flatnonzero(v > v.dtype.type(tau))
     if cand.size <= M:
         return cand
     with np.errstate(over="ignore"):
@@ -186,28 +190,35 @@ def sample_candidates(vol, tau: float, M: int, seed: int) -> np.ndarray:
     return np.sort(cand[pick])
 
 
-def knn3_mean_distance(points, chunk: int = 2048) -> np.ndarray:
-    """Mean Euclidean distance from each point to its three nearest other points,
-    by brute force (needs at least four points)."""
+def knn3_mean_distance(points, chunk: int = 2048, lone: float = np.nan, which=None) -> np.ndarray:
+    """Mean Euclidean distance from each point to its three nearest other points, by
+    brute force; with fewer than four points, to all the others; a single point
+    gets `lone`.  which: optional indices of the points to compute (default all)."""
     P = np.asarray(points, dtype=np.float64)
     n = P.shape[0]
-    out = np.empty(n)
-    for a in range(0, n, chunk):
-        b = min(n, a + chunk)
-        d2 = ((P[a:b, None, :] - P[None, :, :]) ** 2).sum(-1)
-        d2[np.arange(b - a), np.arange(a, b)] = np.inf
-        part = np.partition(d2, 3, axis=1)[:, :3]
+    q = np.arange(n) if which is None else np.asarray(which, dtype=np.int64)
+    out = np.empty(q.size)
+    kk = min(3, n - 1)
+    if kk <= 0:
+        out[:] = lone
+        return out
+    for a in range(0, q.size, chunk):
+        b = min(q.size, a + chunk)
+        d2 = ((P[q[a:b], None, :] - P[None, :, :]) ** 2).sum(-1)
+        d2[np.arange(b - a), q[a:b]] = np.inf
+        part = np.sort(d2, axis=1)[:, :kk] if n <= 4 else np.partition(d2, kk, axis=1)[:, :kk]
         out[a:b] = np.sqrt(part).mean(axis=1)
     return out
 
 
 def init_gaussians(vol, gdesc, tau: float, M: int, seed: int, k: float):
     """Sec. 4.1: positions at the chosen voxel centres, isotropic scales = the mean
-    3-NN distance, identity rotations, rho = k * vol.  Returns
-    (mean [n, 3], scale [n, 3], quat [n, 4] (w, x, y, z), rho [n]) in float64."""
+    3-NN distance (a lone position: the smallest voxel edge), identity rotations,
+    rho = k * vol.  Returns (mean [n, 3], scale [n, 3], quat [n, 4] (w, x, y, z),
+    rho [n]) in float64."""
     idx = sample_candidates(vol, tau, M, seed)
     mean = voxel_centres(gdesc)[idx]
-    s = knn3_mean_distance(mean)
+    s = knn3_mean_distance(mean, lone=float(np.min(np.asarray(gdesc, dtype=np.float64)[3:6])))
     scale = np.repeat(s[:, None], 3, axis=1)
     quat = np.zeros((idx.size, 4))
     quat[:, 0] = 1.0

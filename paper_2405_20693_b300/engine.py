@@ -153,6 +153,55 @@ def voxelize(mean, scale, quat, rho, vox: Voxelizer):
     return _VoxelizeFn.apply(mean, scale, quat, rho, vox)
 
 
+# ----------------------------------------------------------------------------- FDK initialisation
+
+
+INIT_TAU = 0.05   # Sec. 5.1: density threshold of the candidate voxels
+INIT_K = 0.15     # Sec. 5.1: scale-down of the queried densities
+INIT_M = 50_000   # Sec. 5.1: Gaussians at initialisation
+
+
+def fdk_volume(views, meas, cam, gdesc, dbeta=None, device="cuda"):
+    """FDK reconstruction (Sec. 4.1) of one grid from the measured log projections:
+    views [V, 12] and meas [V, H, W] float32 device tensors; returns the volume
+    [Z, Y, X] on the device.  dbeta defaults to 2 pi / V (a full circle)."""
+    V = int(views.shape[0])
+    c = r2g.camera(cam)
+    filt = torch.empty_like(meas)
+    r2g.r2g_fdk_filter(meas, c, filt)
+    g = r2g.grids(gdesc)[0]
+    vol = torch.empty((g.dims[2], g.dims[1], g.dims[0]), dtype=torch.float32, device=device)
+    r2g.r2g_fdk_backproject(views, c, filt, g, 2 * np.pi / V if dbeta is None else dbeta, vol)
+    return vol
+
+
+def init_gaussians(vol, gdesc, M=INIT_M, tau=INIT_TAU, k=INIT_K, seed=0, device="cuda"):
+    """Sec. 4.1's Gaussians from a device volume on grid gdesc: returns device
+    tensors (mean [n, 3], scale [n, 3], quat [n, 4], rho [n]), n <= M."""
+    g = r2g.grids(gdesc)[0]
+    mean = torch.empty((M, 3), dtype=torch.float32, device=device)
+    scale = torch.empty_like(mean)
+    quat = torch.empty((M, 4), dtype=torch.float32, device=device)
+    rho = torch.empty(M, dtype=torch.float32, device=device)
+    n_out = torch.zeros(1, dtype=torch.int64, device=device)
+    ws = _bytes(r2g.r2g_init_workspace_size(g, M), device)
+    r2g.r2g_init_gaussians(vol, g, tau, M, seed, k, mean, scale, quat, rho, n_out, ws)
+    n = int(n_out.item())
+    return mean[:n], scale[:n], quat[:n], rho[:n]
+
+
+def fdk_init(views, meas, cam, n_out: int, M=INIT_M, tau=INIT_TAU, k=INIT_K, seed=0, device="cuda"):
+    """FDK volume on the n_out^3 output grid over [-1, 1]^3, then the initial
+    Gaussians; returns (GaussianSet on the host, volume on the device)."""
+    from .inputs import GaussianSet, cube_grid
+
+    gd = cube_grid(n_out)
+    vol = fdk_volume(views, meas, cam, gd, device=device)
+    mean, scale, quat, rho = init_gaussians(vol, gd, M, tau, k, seed, device)
+    G = GaussianSet(*(t.cpu().numpy() for t in (mean, scale, quat, rho)))
+    return G, vol
+
+
 # ----------------------------------------------------------------------------- training state
 
 

@@ -117,6 +117,11 @@ def lib():
                                               _P]),
             "r2g_project": (_I32, [_I64, _P, _P, _P, _P, _I32, _P, _P, _P, _P, _P, _P]),
             "r2g_mean_mu": (_I32, [_I64, _P, _P, _P, _P, _I32, _P, _P, _P, _P, _P]),
+            "r2g_fdk_filter": (_I32, [_I32, _P, _P, _P, _P]),
+            "r2g_fdk_backproject": (_I32, [_I32, _P, _P, _P, _P, ctypes.c_float, _P, _P]),
+            "r2g_init_workspace_size": (_SZ, [_P, _I64]),
+            "r2g_init_gaussians": (_I32, [_P, _P, ctypes.c_float, _I64, ctypes.c_uint64, ctypes.c_float, _P, _P, _P,
+                                          _P, _P, _P, _SZ, _P]),
             "r2g_raster_lists": (_I32, [_I64, _I32, _P, _P, _P, _SZ, _P, _P, _I64, _P, _P]),
             "r2g_pair_count": (_I32, [_P, _SZ, _P, _P]),
             "r2g_voxel_workspace_size": (_SZ, [_I64, _I32, _P, _I64]),
@@ -228,6 +233,32 @@ def r2g_mean_mu(mean, scale, quat, views, cam: Camera, mu_mean=None, rho=None, r
                              _ptr(mu_mean), _ptr(rho_vol), _stream(stream)))
 
 
+def r2g_fdk_filter(proj, cam: Camera, filt, stream=None):
+    _f32(proj, filt)
+    _check(lib().r2g_fdk_filter(proj.shape[0], ctypes.byref(cam), _ptr(proj), _ptr(filt), _stream(stream)))
+
+
+def r2g_fdk_backproject(views, cam: Camera, filt, grid, dbeta: float, vol, stream=None):
+    """grid: one Grid struct (see grids())."""
+    _f32(views, filt, vol)
+    _check(lib().r2g_fdk_backproject(views.shape[0], _ptr(views), ctypes.byref(cam), _ptr(filt), ctypes.byref(grid),
+                                     float(dbeta), _ptr(vol), _stream(stream)))
+
+
+def r2g_init_workspace_size(grid, M: int) -> int:
+    return lib().r2g_init_workspace_size(ctypes.byref(grid), int(M))
+
+
+def r2g_init_gaussians(vol, grid, tau: float, M: int, seed: int, k: float, mean, scale, quat, rho, n_out, ws,
+                       stream=None):
+    _f32(vol, mean, scale, quat, rho)
+    if n_out.dtype != torch.int64:
+        raise ValueError("n_out must be an int64 tensor")
+    _check(lib().r2g_init_gaussians(_ptr(vol), ctypes.byref(grid), float(tau), int(M), int(seed) & (2 ** 64 - 1),
+                                    float(k), _ptr(mean), _ptr(scale), _ptr(quat), _ptr(rho), _ptr(n_out), _ptr(ws),
+                                    ws.numel(), _stream(stream)))
+
+
 def r2g_raster_lists(M: int, V: int, cam: Camera, opts: RasterOpts, ws, ranges, ids, stream=None) -> int:
     n = ctypes.c_int64(0)
     _check(lib().r2g_raster_lists(M, V, ctypes.byref(cam), ctypes.byref(opts), _ptr(ws), ws.numel(), _ptr(ranges),
@@ -321,7 +352,8 @@ def r2g_adam_step(raw, act, grad, m, v, it: int, opts: AdamOpts, stream=None):
 
 
 PROFILE_KERNELS = ("project", "emit", "sort", "ranges", "splat_fwd", "splat_bwd", "project_bwd", "vox_project",
-                   "vox_fwd", "vox_bwd", "vox_chain", "loss", "tv", "adam", "vox_emit", "vox_sort", "vox_ranges")
+                   "vox_fwd", "vox_bwd", "vox_chain", "loss", "tv", "adam", "vox_emit", "vox_sort", "vox_ranges",
+                   "fdk_filter", "fdk_bp", "init_select", "init_knn")
 
 
 def r2g_profile_enable(on: bool, max_spans: int = 4096):
