@@ -8,18 +8,20 @@
 // xi^2 + eta^2) (cone beam); F(xi_n) = (1 / pitch_u) sum_m c_m R'(xi_{n-m}) with
 // the Ram-Lak ramp in units of 1/tau^2 times the full-circle factor 1/2:
 // c_0 = 1/8, c_m = -1/(2 pi^2 m^2) for odd m, 0 for even m.  The row sits in
-// shared memory between zero margins; each thread produces 8 adjacent outputs
-// and walks the odd taps eight at a time, reusing two sliding register windows
-// (44 shared loads per 128 floating-point operations).
+// shared memory between zero margins (one skew word per 16 positions, so the
+// lanes' windows fall in distinct banks); each thread produces 16 adjacent
+// outputs and walks the odd taps eight at a time, reusing two sliding register
+// windows (60 shared loads per 256 floating-point operations).
 //
-// Back-projection (one thread per (x, y) column and 8 consecutive z voxels).
+// Back-projection (one thread per (x, y) column and 16 consecutive z voxels).
 // f(p) = dbeta sum_v w_v F_v(xi, eta), (xi, eta) = L_SD (u0, u1) / u2 and w_v =
 // D_v L_SD / u2^2 (cone; D_v = t_v[2] is the source-to-isocentre depth), or
 // (u0, u1) and 1 (parallel), u = W p + t; F is read by bilinear interpolation
 // between pixel centres, samples outside the detector counting as zero.  The
 // views' transforms are staged in shared memory 64 at a time.  When the view's
 // rotation leaves u0 and u2 independent of z (rotation about the z axis, W's
-// third column = (0, w12, 0)), the column's 8 voxels share xi and the weight.
+// third column = (0, w12, 0)), the column's 16 voxels share xi, the column half
+// of the bilinear weights and the distance weight.
 //
 // Selection.  Candidate voxel j (flat [z][y][x] index, vol[j] > tau) has the key
 // SplitMix64(seed + (j + 1) * 0x9E3779B97F4A7C15); the M candidates with the
@@ -32,8 +34,10 @@
 // mean = voxel centre, identity rotation, rho = k * vol[j]; their cells are marked
 // in an occupancy bit mask of the grid.
 //
-// Scales.  Each chosen position searches the occupancy mask in cubic shells of
-// growing Chebyshev radius r and keeps its three nearest other positions; once
+// Scales.  Each chosen position (one warp; the lanes share the (z, y) rows of a
+// shell and read the occupancy mask a word at a time) searches the occupancy
+// mask in cubic shells of growing Chebyshev radius r and keeps its three nearest
+// other positions; once
 // three are held and the third is no farther than (r + 1) * (smallest voxel
 // edge), no unvisited cell can be nearer and the search stops.  The scale is the
 // mean of the (up to) three distances; a position with no other position gets the
@@ -45,9 +49,9 @@
 namespace r2g {
 namespace {
 
-constexpr int kFiltJ = 8;     // outputs per thread
+constexpr int kFiltJ = 16;    // outputs per thread (a power of two: see skew())
 constexpr int kFiltS = 8;     // odd taps per window step
-constexpr int kBpZ = 8;       // voxels per back-projection thread (along z)
+constexpr int kBpZ = 16;      // voxels per back-projection thread (along z)
 constexpr int kBpViews = 64;  // views staged in shared memory at a time
 constexpr int kSelDigits = 16;
 constexpr int kSelBins = 1 << kSelDigits;
@@ -63,27 +67,33 @@ __device__ __forceinline__ unsigned long long splitmix64(unsigned long long z) {
 
 // ------------------------------------------------------------------ filtering
 
+// Shared-memory slot of padded row position k: one skew word per kFiltJ, so that
+// lanes whose windows start kFiltJ positions apart are kFiltJ + 1 (odd) slots
+// apart and hit distinct banks.
+__device__ __forceinline__ int skew(int k) { return k + k / kFiltJ; }
+
 __global__ void __launch_bounds__(256) k_fdk_filter(const float* __restrict__ proj, float* __restrict__ filt, int H,
                                                     int W, int cone, float L_SD, float pu, float pv, float ou,
                                                     float ov, float inv_pu) {
     extern __shared__ float sm[];
-    const int P = W + 32;          // zero margin on each side
-    float* row = sm + P;           // row[-P .. W + P)
-    float* tap = sm + W + 2 * P;   // tap[m], m = 0 .. W + 2*kFiltS (0 beyond W - 1)
+    const int P = W + 32;                  // zero margin on each side of the row
+    const int n_row = W + 2 * P;           // padded row positions
+    float* tap = sm + skew(n_row) + 8;     // tap[m], m = 0 .. W + 2 kFiltS + 1 (0 beyond W - 1)
     const long long r = blockIdx.x;
     const int rr = (int)(r % H);
     const float* src = proj + r * W;
     const float eta = ((float)rr + 0.5f - 0.5f * (float)H) * pv + ov;
-    for (int k = threadIdx.x - P; k < W + P; k += blockDim.x) {
+    for (int k = threadIdx.x; k < n_row; k += blockDim.x) {
+        const int c = k - P;
         float x = 0.f;
-        if (k >= 0 && k < W) {
-            x = src[k];
+        if (c >= 0 && c < W) {
+            x = src[c];
             if (cone) {
-                const float xi = ((float)k + 0.5f - 0.5f * (float)W) * pu + ou;
+                const float xi = ((float)c + 0.5f - 0.5f * (float)W) * pu + ou;
                 x *= L_SD * __frsqrt_rn(L_SD * L_SD + xi * xi + eta * eta);
             }
         }
-        row[k] = x;
+        sm[skew(k)] = x;
     }
     const float kInv2Pi2 = 0.05066059182116889f;  // 1 / (2 pi^2)
     for (int m = threadIdx.x; m < W + 2 * kFiltS + 2; m += blockDim.x)
@@ -91,9 +101,12 @@ __global__ void __launch_bounds__(256) k_fdk_filter(const float* __restrict__ pr
     __syncthreads();
     const int n0 = threadIdx.x * kFiltJ;
     if (n0 >= W) return;
+    // padded position of output n0 + i is P + n0 + i; with n0 a multiple of kFiltJ
+    // its slot is skew(P + n0 + i) = (kFiltJ + 1) n0 / kFiltJ + skew(P + i)
+    const float* base = sm + (kFiltJ + 1) * (n0 / kFiltJ);
     float acc[kFiltJ];
 #pragma unroll
-    for (int j = 0; j < kFiltJ; ++j) acc[j] = 0.125f * row[n0 + j];
+    for (int j = 0; j < kFiltJ; ++j) acc[j] = 0.125f * base[skew(P + j)];
     // taps m0, m0 + 2, ..., m0 + 2(S-1):
     //   left  R[n0 + j - m0 - 2s] = L[j - 2s + 2(S-1)],  L[i] = R[n0 - m0 - 2(S-1) + i]
     //   right R[n0 + j + m0 + 2s] = Rw[j + 2s],            Rw[i] = R[n0 + m0 + i]
@@ -102,15 +115,16 @@ __global__ void __launch_bounds__(256) k_fdk_filter(const float* __restrict__ pr
         float L[NW], Rw[NW], c[kFiltS];
 #pragma unroll
         for (int i = 0; i < NW; ++i) {
-            L[i] = row[n0 - m0 - 2 * (kFiltS - 1) + i];
-            Rw[i] = row[n0 + m0 + i];
+            L[i] = base[skew(P - m0 - 2 * (kFiltS - 1) + i)];
+            Rw[i] = base[skew(P + m0 + i)];
         }
 #pragma unroll
-        for (int s = 0; s < kFiltS; ++s) c[s] = tap[m0 + 2 * s];
+        for (int s2 = 0; s2 < kFiltS; ++s2) c[s2] = tap[m0 + 2 * s2];
 #pragma unroll
-        for (int s = 0; s < kFiltS; ++s)
+        for (int s2 = 0; s2 < kFiltS; ++s2)
 #pragma unroll
-            for (int j = 0; j < kFiltJ; ++j) acc[j] = fmaf(c[s], L[j - 2 * s + 2 * (kFiltS - 1)] + Rw[j + 2 * s], acc[j]);
+            for (int j = 0; j < kFiltJ; ++j)
+                acc[j] = fmaf(c[s2], L[j - 2 * s2 + 2 * (kFiltS - 1)] + Rw[j + 2 * s2], acc[j]);
     }
     float* dst = filt + r * W;
 #pragma unroll
@@ -140,6 +154,41 @@ __device__ __forceinline__ float bilerp(const float* __restrict__ img, int H, in
     const float v11 = (yb && xb) ? __ldg(p + W + 1) : 0.f;
     const float top = fmaf(ax, v01 - v00, v00);
     const float bot = fmaf(ax, v11 - v10, v10);
+    return fmaf(ay, bot - top, top);
+}
+
+// Column half of the bilinear read, shared by the voxels of a column whose
+// detector column does not change along z.
+struct ColW {
+    int x0;
+    float ax;
+    bool xa, xb;
+};
+
+__device__ __forceinline__ ColW col_weights(float xc, int W) {
+    xc = fminf(fmaxf(xc, -2.f), (float)W + 1.f);
+    const float fx = floorf(xc);
+    ColW c;
+    c.x0 = (int)fx;
+    c.ax = xc - fx;
+    c.xa = c.x0 >= 0 && c.x0 < W;
+    c.xb = c.x0 >= -1 && c.x0 < W - 1;
+    return c;
+}
+
+__device__ __forceinline__ float bilerp_col(const float* __restrict__ img, int H, int W, const ColW& c, float yc) {
+    yc = fminf(fmaxf(yc, -2.f), (float)H + 1.f);
+    const float fy = floorf(yc);
+    const int y0 = (int)fy;
+    const float ay = yc - fy;
+    const bool ya = y0 >= 0 && y0 < H, yb = y0 >= -1 && y0 < H - 1;
+    const float* p = img + (long long)y0 * W + c.x0;
+    const float v00 = (ya && c.xa) ? __ldg(p) : 0.f;
+    const float v01 = (ya && c.xb) ? __ldg(p + 1) : 0.f;
+    const float v10 = (yb && c.xa) ? __ldg(p + W) : 0.f;
+    const float v11 = (yb && c.xb) ? __ldg(p + W + 1) : 0.f;
+    const float top = fmaf(c.ax, v01 - v00, v00);
+    const float bot = fmaf(c.ax, v11 - v10, v10);
     return fmaf(ay, bot - top, top);
 }
 
@@ -178,13 +227,13 @@ __global__ void __launch_bounds__(256) k_fdk_bp(const float* __restrict__ filt, 
                     // u0, u2 constant along the column: one reciprocal, one weight
                     if (u2 > cam.near_plane) {
                         const float inv = 1.0f / u2;
-                        const float xc = fmaf(cam.L_SD * u0 * inv, cam.inv_pu, cam.cu);
+                        const ColW cw = col_weights(fmaf(cam.L_SD * u0 * inv, cam.inv_pu, cam.cu), cam.W);
                         const float wt = DL * inv * inv;
                         const float ys = cam.L_SD * inv * cam.inv_pv;
 #pragma unroll
                         for (int j = 0; j < kBpZ; ++j) {
                             const float yc = fmaf(u1 + (float)j * d1, ys, cam.cv);
-                            acc[j] = fmaf(wt, bilerp(img, cam.H, cam.W, xc, yc), acc[j]);
+                            acc[j] = fmaf(wt, bilerp_col(img, cam.H, cam.W, cw, yc), acc[j]);
                         }
                     }
                 } else {
@@ -201,6 +250,11 @@ __global__ void __launch_bounds__(256) k_fdk_bp(const float* __restrict__ filt, 
                         u2 += d2;
                     }
                 }
+            } else if (w[2] == 0.f) {
+                const ColW cw = col_weights(fmaf(u0, cam.inv_pu, cam.cu), cam.W);
+#pragma unroll
+                for (int j = 0; j < kBpZ; ++j)
+                    acc[j] += bilerp_col(img, cam.H, cam.W, cw, fmaf(u1 + (float)j * d1, cam.inv_pv, cam.cv));
             } else {
 #pragma unroll
                 for (int j = 0; j < kBpZ; ++j) {
@@ -431,10 +485,6 @@ __global__ void __launch_bounds__(256) k_sel_write(SelArgs a, const SelState* __
     }
 }
 
-__device__ __forceinline__ bool occupied(const unsigned int* __restrict__ occ, long long j) {
-    return (__ldg(&occ[j >> 5]) >> (j & 31)) & 1u;
-}
-
 // The three smallest squared distances so far, ascending (+inf while fewer).
 __device__ __forceinline__ void keep3(float d2, float& b0, float& b1, float& b2) {
     if (d2 < b2) {
@@ -452,57 +502,85 @@ __device__ __forceinline__ void keep3(float d2, float& b0, float& b1, float& b2)
     }
 }
 
-__global__ void __launch_bounds__(128) k_knn3(const unsigned int* __restrict__ sel_idx, const SelState* __restrict__ st,
-                                              const unsigned int* __restrict__ occ, GridF g, float vmin,
-                                              float* __restrict__ scale) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= (long long)st->n_sel) return;
+// Occupied cells among flat bit indices [lo, hi] of one grid row (rowj = flat
+// index of the row's x = 0 cell), folded into the three nearest.
+__device__ __forceinline__ void scan_row(const unsigned int* __restrict__ occ, long long lo, long long hi,
+                                         long long rowj, int cx, float vx, float eyz2, float& b0, float& b1,
+                                         float& b2) {
+    for (long long w = lo >> 5; w <= (hi >> 5); ++w) {
+        unsigned int bits = __ldg(&occ[w]);
+        const long long wb = w << 5;
+        if (wb < lo) bits &= ~0u << (int)(lo - wb);
+        if (hi - wb < 31) bits &= (2u << (int)(hi - wb)) - 1u;
+        while (bits) {
+            const int t = __ffs(bits) - 1;
+            bits &= bits - 1u;
+            const float ex = (float)((int)(wb + t - rowj) - cx) * vx;
+            keep3(fmaf(ex, ex, eyz2), b0, b1, b2);
+        }
+    }
+}
+
+// The three smallest of the warp's per-lane lists (every lane gets them).
+__device__ __forceinline__ void warp_top3(float b0, float b1, float b2, float out[3]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        float m = b0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        out[k] = m;
+        const unsigned int owner = __ballot_sync(0xffffffffu, b0 == m);
+        if (lane == __ffs(owner) - 1) {
+            b0 = b1;
+            b1 = b2;
+            b2 = INFINITY;
+        }
+    }
+}
+
+// One warp per chosen position; the lanes share each shell's (z, y) rows.
+__global__ void __launch_bounds__(256) k_knn3(const unsigned int* __restrict__ sel_idx,
+                                              const SelState* __restrict__ st, const unsigned int* __restrict__ occ,
+                                              GridF g, float vmin, float* __restrict__ scale) {
+    const long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= (long long)st->n_sel) return;  // whole warps
     const long long j = sel_idx[i];
     const long long XY = (long long)g.X * g.Y;
     const int cz = (int)(j / XY), cy = (int)((j / g.X) % g.Y), cx = (int)(j % g.X);
     float b0 = INFINITY, b1 = INFINITY, b2 = INFINITY;
+    float top[3];
     const int rmax = min(kKnnMaxR, max(g.X, max(g.Y, g.Z)));
     for (int r = 1; r <= rmax; ++r) {
-        const int z_lo = max(cz - r, 0), z_hi = min(cz + r, g.Z - 1);
-        const int y_lo = max(cy - r, 0), y_hi = min(cy + r, g.Y - 1);
-        for (int z = z_lo; z <= z_hi; ++z) {
-            const int dz = z - cz;
-            const float ez = (float)dz * g.vz;
-            for (int y = y_lo; y <= y_hi; ++y) {
-                const int dy = y - cy;
-                const float ey = (float)dy * g.vy;
-                const bool face = dz == -r || dz == r || dy == -r || dy == r;
-                const long long rowj = ((long long)z * g.Y + y) * g.X;
-                if (face) {
-                    const int x_lo = max(cx - r, 0), x_hi = min(cx + r, g.X - 1);
-                    for (int x = x_lo; x <= x_hi; ++x)
-                        if (occupied(occ, rowj + x)) {
-                            const float ex = (float)(x - cx) * g.vx;
-                            keep3(ex * ex + ey * ey + ez * ez, b0, b1, b2);
-                        }
-                } else {
-#pragma unroll
-                    for (int sgn = -1; sgn <= 1; sgn += 2) {
-                        const int x = cx + sgn * r;
-                        if (x >= 0 && x < g.X && occupied(occ, rowj + x)) {
-                            const float ex = (float)(sgn * r) * g.vx;
-                            keep3(ex * ex + ey * ey + ez * ez, b0, b1, b2);
-                        }
-                    }
-                }
+        const int side = 2 * r + 1;
+        for (int q = lane; q < side * side; q += 32) {
+            const int dz = q / side - r, dy = q % side - r;
+            const int z = cz + dz, y = cy + dy;
+            if (z < 0 || z >= g.Z || y < 0 || y >= g.Y) continue;
+            const float ez = (float)dz * g.vz, ey = (float)dy * g.vy;
+            const float eyz2 = fmaf(ey, ey, ez * ez);
+            const long long rowj = ((long long)z * g.Y + y) * g.X;
+            if (dz == -r || dz == r || dy == -r || dy == r) {
+                scan_row(occ, rowj + max(cx - r, 0), rowj + min(cx + r, g.X - 1), rowj, cx, g.vx, eyz2, b0, b1, b2);
+            } else {
+                if (cx - r >= 0) scan_row(occ, rowj + cx - r, rowj + cx - r, rowj, cx, g.vx, eyz2, b0, b1, b2);
+                if (cx + r < g.X) scan_row(occ, rowj + cx + r, rowj + cx + r, rowj, cx, g.vx, eyz2, b0, b1, b2);
             }
         }
+        warp_top3(b0, b1, b2, top);
         const float reach = (float)(r + 1) * vmin;
-        if (b2 <= reach * reach) break;
-        if (r >= g.X && r >= g.Y && r >= g.Z) break;  // the whole grid has been visited
+        if (top[2] <= reach * reach) break;                     // no unvisited cell is nearer
+        if (r >= g.X && r >= g.Y && r >= g.Z) break;             // the whole grid has been visited
     }
+    if (lane != 0) return;
     float s = vmin;
-    if (b2 < INFINITY)
-        s = (sqrtf(b0) + sqrtf(b1) + sqrtf(b2)) / 3.f;
-    else if (b1 < INFINITY)
-        s = 0.5f * (sqrtf(b0) + sqrtf(b1));
-    else if (b0 < INFINITY)
-        s = sqrtf(b0);
+    if (top[2] < INFINITY)
+        s = (sqrtf(top[0]) + sqrtf(top[1]) + sqrtf(top[2])) / 3.f;
+    else if (top[1] < INFINITY)
+        s = 0.5f * (sqrtf(top[0]) + sqrtf(top[1]));
+    else if (top[0] < INFINITY)
+        s = sqrtf(top[0]);
     scale[3 * i + 0] = s;
     scale[3 * i + 1] = s;
     scale[3 * i + 2] = s;
@@ -565,7 +643,8 @@ R2G_API r2g_status r2g_fdk_filter(int32_t V, const r2g_camera* cam, const float*
     if (proj == filt) return fail(R2G_E_INVAL, "proj and filt must not alias");
     const int W = cam->W;
     const int threads = ((W + kFiltJ - 1) / kFiltJ + 31) / 32 * 32;
-    const size_t smem = sizeof(float) * (size_t)(3 * W + 64 + W + 2 * kFiltS + 2);
+    const int n_row = 3 * W + 64;
+    const size_t smem = sizeof(float) * (size_t)(n_row + n_row / kFiltJ + 8 + W + 2 * kFiltS + 2);
     static thread_local bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_fdk_filter, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
@@ -649,7 +728,7 @@ R2G_API r2g_status r2g_init_gaussians(const float* vol, const r2g_grid* grid, fl
     prof_end(P_INIT_SELECT, stream);
     const float vmin = fminf(g.vx, fminf(g.vy, g.vz));
     prof_begin(P_INIT_KNN, stream);
-    k_knn3<<<(unsigned)((M + 127) / 128), 128, 0, stream>>>(sel, st, occ, g, vmin, scale);
+    k_knn3<<<(unsigned)((M * 32 + 255) / 256), 256, 0, stream>>>(sel, st, occ, g, vmin, scale);
     prof_end(P_INIT_KNN, stream);
     note_launches(16);
     return check_launch("r2g_init_gaussians");
