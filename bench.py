@@ -196,10 +196,20 @@ def _has_cuda():
 # ----------------------------------------------------------------------------- our arm
 
 
-def source_hash():
+# the source file of each profiled kernel (with every shared .cuh header)
+KERNEL_SOURCES = {"splat_bwd": "raster.cu", "splat_fwd": "raster.cu", "project_bwd": "raster.cu", "sort": "raster.cu",
+                  "loss": "loss.cu", "fdk_bp": "fdk.cu", "fdk_filter": "fdk.cu", "init_knn": "fdk.cu",
+                  "init_select_hist": "fdk.cu"}
+
+
+def source_hash(kernel: str | None = None):
+    """Hash of the sources a kernel is built from: its .cu file and every .cuh
+    header (all of csrc when kernel is None)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2405_20693_b300", "csrc")
     for f in sorted(os.listdir(csrc)):
+        if kernel is not None and not (f.endswith(".cuh") or f == KERNEL_SOURCES[kernel]):
+            continue
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -208,24 +218,27 @@ def source_hash():
 def _ncu_summary():
     try:
         with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
-            t = json.load(f)
-        return t if t.get("source_hash") == source_hash() else None
+            return json.load(f)
     except Exception:
         return None
 
 
+def _current(t, kernel: str) -> bool:
+    return bool(t) and kernel in KERNEL_SOURCES and t.get("source_hashes", {}).get(kernel) == source_hash(kernel)
+
+
 def ncu_traffic(kernel: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel sources; else None."""
+    the kernel's current sources; else None."""
     t = _ncu_summary()
-    return t["kernels"].get(kernel) if t else None
+    return t["kernels"].get(kernel) if _current(t, kernel) else None
 
 
 def ncu_pipes(kernel: str):
     """FMA and XU (MUFU) pipe utilisation (% of peak sustained) of the kernel from the
-    committed ncu summary, if it was taken on the current kernel sources; else None."""
+    committed ncu summary, if it was taken on the kernel's current sources; else None."""
     t = _ncu_summary()
-    return t.get("pipes", {}).get(kernel) if t else None
+    return t.get("pipes", {}).get(kernel) if _current(t, kernel) else None
 
 
 def measure_batched(dev, rounds=20, n_scans=16, seed=5):
@@ -323,6 +336,83 @@ def measure_serving(dev, n_requests=16, mean_interarrival_s=0.25, max_iters=500,
     return out
 
 
+LSU_PER_CLK = 32   # load/store lanes per SM per clock
+BP_LOADS = 4       # detector reads per (voxel, view): one bilinear interpolation
+
+
+def measure_fdk_init(dev, views_np, meas_np, cam, reps=10, cpu=True):
+    """Sec. 4.1 initialisation of the workload's scan on the device: FDK of the 50
+    measured views onto the 256^3 output grid, then the draw of 50k Gaussians (tau
+    0.05, k 0.15) with their 3-NN scales.  Device time per kernel (event pairs over
+    `reps` runs after 3 warm-up runs), the whole initialisation's device time, and the
+    back-projection's roofline: (voxel, view) updates per second against the issue
+    rate of its 4 detector reads per update on the SMs' load/store lanes.  With cpu,
+    the FP64 oracle back-projects one z slice of the same grid on the host."""
+    import torch
+
+    from oracle import fdk as ofdk
+    from paper_2405_20693_b300 import engine, r2g
+    from paper_2405_20693_b300 import inputs as I
+
+    vd = torch.as_tensor(np.ascontiguousarray(views_np, np.float32), device=dev)
+    md = torch.as_tensor(np.ascontiguousarray(meas_np, np.float32), device=dev)
+    gd = I.cube_grid(N_OUT)
+
+    def once():
+        vol = engine.fdk_volume(vd, md, cam, gd, device=dev)
+        return vol, engine.init_gaussians(vol, gd, M_GAUSS, device=dev)
+
+    for _ in range(3):
+        once()
+    torch.cuda.synchronize()
+    ids = [r2g.PROFILE_KERNELS.index(n) for n in ("fdk_filter", "fdk_bp", "init_select", "init_knn")]
+    r2g.r2g_profile_enable(True, 16 * reps + 16)
+    r2g.r2g_profile_select(sum(1 << k for k in ids))
+    r2g.r2g_profile_reset()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        vol, G = once()
+    e1.record()
+    torch.cuda.synchronize()
+    ks = {}
+    for k in ids:
+        n, t = r2g.r2g_profile_read(k)
+        ks[r2g.PROFILE_KERNELS[k]] = t / max(n, 1)
+    r2g.r2g_profile_enable(False)
+    total_ms = e0.elapsed_time(e1) / reps
+    updates = float(N_OUT) ** 3 * views_np.shape[0]
+    pk = peaks()
+    lsu_peak = SM_COUNT * LSU_PER_CLK * pk["sm_max_mhz"] * 1e6 / BP_LOADS
+    ach = updates / (ks["fdk_bp"] * 1e-3)
+    out = {"ms_per_init": total_ms, "kernels_ms": ks, "gaussians": int(G[0].shape[0]),
+           "grid": f"{N_OUT}^3", "views": int(views_np.shape[0]),
+           "roofline": {"kernel": "fdk_bp", "bound": "lsu", "achieved": ach / 1e9, "peak": lsu_peak / 1e9,
+                        "unit": "G voxel-view updates/s", "frac": ach / lsu_peak, "traffic": ncu_traffic("fdk_bp"),
+                        "peak_note": f"{LSU_PER_CLK} load lanes/clk/SM / {BP_LOADS} reads per update x {SM_COUNT} "
+                                     f"SMs x {pk['sm_max_mhz']:.0f} MHz"},
+           "note": "ms_per_init: device time of the whole initialisation (FDK filter + back-projection + draw + "
+                   "3-NN) incl. the host's read of the drawn count"}
+    if cpu:
+        t0 = time.perf_counter()
+        filt = ofdk.fdk_filter(meas_np[:2], cam)
+        t_filt = (time.perf_counter() - t0) / 2
+        sl = np.asarray(gd, np.float64).copy()
+        sl[2] = -1.0 + (N_OUT // 2) * (2.0 / N_OUT)
+        sl[8] = 1
+        F = np.repeat(filt[:1], views_np.shape[0], axis=0)
+        t0 = time.perf_counter()
+        ofdk.fdk_backproject(F, views_np, cam, sl, 2 * np.pi / views_np.shape[0])
+        t_bp = time.perf_counter() - t0
+        upd = float(N_OUT) ** 2 * views_np.shape[0]
+        out["cpu_baseline"] = {"value": upd / t_bp / 1e9, "unit": "G voxel-view updates/s", "cores": 1,
+                               "kind": "oracle",
+                               "sample": f"FP64 oracle back-projection of one {N_OUT}^2 z slice from "
+                                         f"{views_np.shape[0]} views ({t_bp:.2f} s); filter "
+                                         f"{t_filt * 1e3:.0f} ms per 512^2 view"}
+    return out
+
+
 def voxel_box_counter(sc):
     """Voxels of each Gaussian's box (|x_k - p_k| <= sqrt(Q3 Sigma_kk), voxel centres)
     inside a D^3 TV patch at a given offset, summed over Gaussians: FP64 on the host
@@ -361,6 +451,11 @@ def run_ours(args, rank, world, local_rank):
         dist.init_process_group("nccl", device_id=dev)
     seed = rank * 1000
     G, cam, views_np, meas_np = make_workload(seed, dev)
+    if args.fdk_only:
+        if rank == 0:
+            print(json.dumps({"fdk_init": measure_fdk_init(dev, views_np, meas_np, cam, reps=args.steps,
+                                                           cpu=not args.no_cpu_baseline)}), flush=True)
+        return
     # the scan's parameters, Adam state, views, measured projections, step buffers and
     # workspaces stay resident; one step = one r2g_train_step call reading its view,
     # iteration and TV patch origin from a device table holding every step's entry
@@ -517,9 +612,11 @@ def run_ours(args, rank, world, local_rank):
                     "frac": None, "traffic": ncu_traffic(dom)}
         batched = None
         serving = None
+        fdk_init = None
         if world == 1 and not args.no_batched:
             batched = measure_batched(dev)
             serving = measure_serving(dev)
+            fdk_init = measure_fdk_init(dev, views_np, meas_np, cam, cpu=not args.no_cpu_baseline)
         cpu = None
         # CPU baseline: the oracle on two full steps of the same workload
         if world == 1 and not args.no_cpu_baseline:
@@ -551,6 +648,7 @@ def run_ours(args, rank, world, local_rank):
             "cpu_baseline": cpu,
             "batched": batched,
             "serving": serving,
+            "fdk_init": fdk_init,
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
@@ -567,7 +665,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true",
-                    help="skip the multi-scan scans/hour and serving measurements")
+                    help="skip the multi-scan scans/hour, serving and FDK-initialisation measurements")
+    ap.add_argument("--fdk-only", action="store_true",
+                    help="time only the FDK initialisation of the workload's scan (--steps runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

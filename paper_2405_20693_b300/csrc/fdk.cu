@@ -76,7 +76,10 @@ __global__ void __launch_bounds__(256) k_fdk_filter(const float* __restrict__ pr
                                                     int W, int cone, float L_SD, float pu, float pv, float ou,
                                                     float ov, float inv_pu) {
     extern __shared__ float sm[];
-    const int P = W + 32;                  // zero margin on each side of the row
+    // zero margin on each side of the row, P = 15 (mod 16): with outputs n0 a
+    // multiple of kFiltJ = 16 and taps m0 = 1 (mod 16), both windows below start at
+    // multiples of 16, so slot(start + i) = slot(start) + i + i / 16
+    const int P = ((W + 32 + 15) / 16) * 16 + 15;
     const int n_row = W + 2 * P;           // padded row positions
     float* tap = sm + skew(n_row) + 8;     // tap[m], m = 0 .. W + 2 kFiltS + 1 (0 beyond W - 1)
     const long long r = blockIdx.x;
@@ -101,22 +104,23 @@ __global__ void __launch_bounds__(256) k_fdk_filter(const float* __restrict__ pr
     __syncthreads();
     const int n0 = threadIdx.x * kFiltJ;
     if (n0 >= W) return;
-    // padded position of output n0 + i is P + n0 + i; with n0 a multiple of kFiltJ
-    // its slot is skew(P + n0 + i) = (kFiltJ + 1) n0 / kFiltJ + skew(P + i)
-    const float* base = sm + (kFiltJ + 1) * (n0 / kFiltJ);
     float acc[kFiltJ];
 #pragma unroll
-    for (int j = 0; j < kFiltJ; ++j) acc[j] = 0.125f * base[skew(P + j)];
+    for (int j = 0; j < kFiltJ; ++j) acc[j] = 0.125f * sm[skew(P + n0 + j)];
     // taps m0, m0 + 2, ..., m0 + 2(S-1):
     //   left  R[n0 + j - m0 - 2s] = L[j - 2s + 2(S-1)],  L[i] = R[n0 - m0 - 2(S-1) + i]
     //   right R[n0 + j + m0 + 2s] = Rw[j + 2s],            Rw[i] = R[n0 + m0 + i]
+    // padded starts: P + n0 - m0 - 14 and P + n0 + m0, both multiples of 16
     constexpr int NW = kFiltJ + 2 * (kFiltS - 1);
-    for (int m0 = 1; m0 < W; m0 += 2 * kFiltS) {
+    static_assert(kFiltJ == 16 && kFiltS == 8, "window alignment assumes 16 outputs and 8 taps per step");
+    const float* lp = sm + skew(P + n0 - 15);   // left window start for m0 = 1
+    const float* rp = sm + skew(P + n0 + 1);    // right window start for m0 = 1
+    for (int m0 = 1; m0 < W; m0 += 2 * kFiltS, lp -= kFiltJ + 1, rp += kFiltJ + 1) {
         float L[NW], Rw[NW], c[kFiltS];
 #pragma unroll
         for (int i = 0; i < NW; ++i) {
-            L[i] = base[skew(P - m0 - 2 * (kFiltS - 1) + i)];
-            Rw[i] = base[skew(P + m0 + i)];
+            L[i] = lp[i + i / 16];
+            Rw[i] = rp[i + i / 16];
         }
 #pragma unroll
         for (int s2 = 0; s2 < kFiltS; ++s2) c[s2] = tap[m0 + 2 * s2];
@@ -325,64 +329,67 @@ __global__ void __launch_bounds__(256) k_sel_hist(SelArgs a, int pass, const Sel
 
 // One CTA of 1024 threads: the bin of the wanted rank; the prefix grows by that
 // digit and the rank becomes the rank inside the bin.  Clears the histogram.
+// Warp w owns bins [w * 2048, (w + 1) * 2048), read 32 at a time (coalesced).
 __global__ void __launch_bounds__(1024) k_sel_find(int pass, long long M, SelState* __restrict__ st,
                                                    unsigned int* __restrict__ hist) {
     __shared__ unsigned long long wsum[32];
     __shared__ unsigned long long total_s;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    constexpr int per = kSelBins / 1024;
+    constexpr int kPerWarp = kSelBins / 32;
+    const unsigned int* h = hist + warp * kPerWarp;
     unsigned long long mine = 0;
-    for (int i = 0; i < per; ++i) mine += hist[t * per + i];
-    unsigned long long x = mine;
+    for (int c = lane; c < kPerWarp; c += 32) mine += h[c];
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) wsum[warp] = x;
+    for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+    if (lane == 0) wsum[warp] = mine;
     __syncthreads();
     if (warp == 0) {
-        unsigned long long s = wsum[lane];
+        const unsigned long long s = wsum[lane];
         unsigned long long incl = s;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= o) incl += y;
         }
-        wsum[lane] = incl - s;
+        wsum[lane] = incl - s;  // candidates in the warps before
         if (lane == 31) total_s = incl;
     }
     __syncthreads();
     const unsigned long long total = total_s;
-    const unsigned long long before = wsum[warp] + x - mine;  // candidates in bins below this thread's
-    if (pass == 0) {
-        if (t == 0) {
-            st->n_cand = total;
-            st->take_all = total <= (unsigned long long)M ? 1u : 0u;
-            st->need = (unsigned long long)M;
-        }
-        __syncthreads();
-    }
-    const unsigned long long need = (pass == 0) ? (unsigned long long)M : st->need;
-    const bool take_all = (pass == 0) ? (total <= (unsigned long long)M) : false;
+    const bool take_all = pass == 0 && total <= (unsigned long long)M;
+    const unsigned long long need = pass == 0 ? (unsigned long long)M : st->need;
     __syncthreads();
+    if (pass == 0 && t == 0) {  // st->need is written only by the warp that finds the bin
+        st->n_cand = total;
+        st->take_all = take_all ? 1u : 0u;
+    }
+    const unsigned long long before = wsum[warp];
     if (!take_all && need > before && need <= before + mine) {
-        unsigned long long c = before;
-        for (int i = 0; i < per; ++i) {
-            const unsigned int hi = hist[t * per + i];
-            if (need > c && need <= c + hi) {
-                const unsigned int digit = (unsigned int)(t * per + i);
-                st->need = need - c;
+        // this warp holds the bin: walk its chunks of 32 bins in order
+        unsigned long long c0 = before;
+        for (int c = 0; c < kPerWarp; c += 32) {
+            const unsigned int v = h[c + lane];
+            unsigned long long incl = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const unsigned long long lo = c0 + incl - v;
+            if (need > lo && need <= lo + v) {
+                const unsigned int digit = (unsigned int)(warp * kPerWarp + c + lane);
+                st->need = need - lo;
                 if (pass < 4)
                     st->kprefix = (st->kprefix << 16) | digit;
                 else
                     st->iprefix = pass == 4 ? digit : ((st->iprefix << 16) | digit);
             }
-            c += hi;
+            c0 += __shfl_sync(0xffffffffu, incl, 31);
+            if (c0 >= need) break;
         }
     }
     __syncthreads();
-    for (int i = 0; i < per; ++i) hist[t * per + i] = 0u;
+    for (int i = t; i < kSelBins; i += 1024) hist[i] = 0u;
 }
 
 __device__ __forceinline__ bool selected(const SelArgs& a, const SelState& st, long long j) {
@@ -643,7 +650,8 @@ R2G_API r2g_status r2g_fdk_filter(int32_t V, const r2g_camera* cam, const float*
     if (proj == filt) return fail(R2G_E_INVAL, "proj and filt must not alias");
     const int W = cam->W;
     const int threads = ((W + kFiltJ - 1) / kFiltJ + 31) / 32 * 32;
-    const int n_row = 3 * W + 64;
+    const int P = ((W + 32 + 15) / 16) * 16 + 15;  // as in the kernel
+    const int n_row = W + 2 * P;
     const size_t smem = sizeof(float) * (size_t)(n_row + n_row / kFiltJ + 8 + W + 2 * kFiltS + 2);
     static thread_local bool attr = false;
     if (!attr) {
