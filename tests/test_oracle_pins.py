@@ -635,3 +635,43 @@ def test_fp32_tile_bound_covers_the_gate(beam):
             assert oi[v, i, 0] == 1
             c0, c1, r0, r1 = oi[v, i, 1:5]
             assert cc.min() >= c0 and cc.max() <= c1 and rr.min() >= r0 and rr.max() <= r1
+
+
+# ----------------------------------------------------------------------------- volume metrics (Sec. 5.1)
+
+
+def test_volume_metrics_closed_forms():
+    """3D SSIM = 1 for identical volumes; a volume constant along z has every axial
+    slice equal to one image, so its axial SSIM is that image's 2D SSIM; the PSNR of
+    a uniform offset e is -20 log10(e)."""
+    from oracle import metrics
+
+    g = I.rng(12)
+    a = g.uniform(0, 1, (6, 9, 11))
+    assert metrics.ssim3d(a, a)["ssim"] == pytest.approx(1.0, abs=1e-12)
+    img_a, img_b = g.uniform(0, 1, (9, 11)), g.uniform(0, 1, (9, 11))
+    sa = np.repeat(img_a[None], 6, axis=0)
+    sb = np.repeat(img_b[None], 6, axis=0)
+    assert metrics.ssim3d(sa, sb)["axial"] == pytest.approx(losses.ssim(img_a, img_b), abs=1e-14)
+    mse, p = metrics.psnr3d(a, a + 0.01)
+    assert mse == pytest.approx(1e-4, rel=1e-9) and p == pytest.approx(40.0, rel=1e-9)
+
+
+def test_volume_ssim_orientations_permute_with_the_axes():
+    """Transposing the volume's axes permutes the three orientation means: swapping
+    x and y exchanges coronal and sagittal (an image's SSIM is transpose-invariant);
+    swapping z and y exchanges axial and coronal."""
+    from oracle import metrics
+
+    g = I.rng(13)
+    a = g.uniform(0, 1, (7, 8, 10))
+    b = np.clip(a + g.normal(0, 0.2, a.shape), 0, 1)
+    m = metrics.ssim3d(a, b)
+    mxy = metrics.ssim3d(a.transpose(0, 2, 1), b.transpose(0, 2, 1))
+    myz = metrics.ssim3d(a.transpose(1, 0, 2), b.transpose(1, 0, 2))
+    assert mxy["axial"] == pytest.approx(m["axial"], abs=1e-14)
+    assert mxy["coronal"] == pytest.approx(m["sagittal"], abs=1e-14)
+    assert mxy["sagittal"] == pytest.approx(m["coronal"], abs=1e-14)
+    assert myz["axial"] == pytest.approx(m["coronal"], abs=1e-14)
+    assert myz["coronal"] == pytest.approx(m["axial"], abs=1e-14)
+    assert len({round(m[o], 6) for o in ("axial", "coronal", "sagittal")}) == 3
