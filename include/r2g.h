@@ -369,6 +369,23 @@ r2g_status r2g_init_gaussians(const float* vol, const r2g_grid* grid, float tau,
                               float* mean, float* scale, float* quat, float* rho, int64_t* n_out, void* ws,
                               size_t ws_bytes, r2g_stream stream);
 
+/* ---------------------------------------------------------------- volume metrics (Sec. 5.1)
+ *
+ * The scores the paper reports for a reconstruction: PSNR over the whole volume and
+ * SSIM averaged over the 2D slices in the axial, coronal and sagittal directions.
+ * For vol[Z][Y][X] (z the rotation axis): axial slices are z = const (rows y,
+ * columns x), coronal y = const (rows z, columns x), sagittal x = const (rows z,
+ * columns y).  Slice SSIM: Wang et al. 2004 with an 11 x 11 Gaussian window (sigma
+ * 1.5), zero-padded "same" filtering, C1 = 1e-4, C2 = 9e-4 (data range 1), the mean
+ * of the SSIM map over the slice; per orientation the mean over its slices; SSIM =
+ * the mean of the three.  PSNR = 10 log10(1 / MSE) (data range 1). */
+size_t r2g_metrics_workspace_size(int32_t X, int32_t Y, int32_t Z);
+/* vol, ref: device [Z][Y][X]; out: device double[6] = {MSE, PSNR, SSIM, axial,
+ * coronal, sagittal}, written; ws: device, 256-byte aligned,
+ * r2g_metrics_workspace_size bytes.  Deterministic (fixed summation order). */
+r2g_status r2g_volume_metrics(int32_t X, int32_t Y, int32_t Z, const float* vol, const float* ref, double* out,
+                              void* ws, size_t ws_bytes, r2g_stream stream);
+
 /* ---------------------------------------------------------------- measurement
  *
  * Optional timing of the library's own kernels: when enabled, every call records
@@ -378,7 +395,7 @@ r2g_status r2g_init_gaussians(const float* vol, const r2g_grid* grid, float tau,
  * 5 splat_bwd, 6 project_bwd, 7 vox_project, 8 vox_fwd, 9 vox_bwd, 10 vox_chain,
  * 11 loss, 12 tv, 13 adam, 14-16 the same three list stages for the brick lists,
  * 17 fdk_filter, 18 fdk_bp, 19 init_select (the selection passes and the writes
- * of r2g_init_gaussians), 20 init_knn.
+ * of r2g_init_gaussians), 20 init_knn, 21 metrics (r2g_volume_metrics).
  * Not for use inside stream capture.
  * max_spans bounds the recorded pairs (events are created once, here). */
 r2g_status r2g_profile_enable(int32_t on, int32_t max_spans);

@@ -1,0 +1,258 @@
+// metrics.cu -- the reconstruction metrics of Sec. 5.1 on the GPU: PSNR over the
+// whole volume and SSIM averaged over the 2D slices of the three orientations.
+//
+// For a [Z][Y][X] volume (z the rotation axis) the axial slices are the z = const
+// images (rows y, columns x), the coronal ones y = const (rows z, columns x) and
+// the sagittal ones x = const (rows z, columns y).  Slice SSIM is Wang et al.'s
+// with an 11 x 11 Gaussian window (sigma 1.5), zero-padded "same" filtering,
+// C1 = (0.01 L)^2, C2 = (0.03 L)^2 and L = 1, averaged over the slice's pixels;
+// each orientation's value is the mean over its slices, and the 3D SSIM the mean
+// of the three.  PSNR = 10 log10(1 / MSE).
+//
+//   k_slice_ssim  one CTA per 32 x 32 output tile of one slice of one orientation:
+//                 both volumes' tiles staged with a 5-voxel halo (zeros outside
+//                 the slice), the window applied separably to a, b, a^2, b^2, ab,
+//                 the SSIM term summed over the tile's in-slice pixels (double)
+//                 into a per-tile partial;
+//   k_sq_err      per-CTA partial sums of (a - b)^2 (double), grid-stride;
+//   k_metrics_fin one CTA sums the partials in a fixed order (deterministic).
+#include <math.h>
+
+#include "r2g_internal.cuh"
+
+namespace r2g {
+namespace {
+
+constexpr int kMT = 32;              // output tile edge
+constexpr int kMR = 5;               // window radius
+constexpr int kMS = kMT + 2 * kMR;   // staged edge
+constexpr int kMetThreads = 256;
+constexpr int kSqBlocks = 148 * 4;
+constexpr float kMC1 = 1e-4f, kMC2 = 9e-4f;
+
+struct MWin {
+    float w[11];
+};
+
+struct Orient {
+    long long ss, sr, sc;  // element strides of slice, row, column
+    int n, H, W;           // slices, rows, columns
+    int tiles_x, tiles;    // tiles per row of tiles, tiles per slice
+    long long first;       // first CTA of this orientation
+};
+
+struct Orients {
+    Orient o[3];
+};
+
+__global__ void __launch_bounds__(kMetThreads) k_slice_ssim(const float* __restrict__ a, const float* __restrict__ b,
+                                                            Orients os, MWin win, double* __restrict__ partials) {
+    __shared__ float sa[kMS][kMS + 1], sb[kMS][kMS + 1];
+    __shared__ float h[5][kMS][kMT + 1];
+    __shared__ double red[kMetThreads / 32];
+    const long long cta = blockIdx.x;
+    const int oi = cta >= os.o[2].first ? 2 : (cta >= os.o[1].first ? 1 : 0);
+    const Orient o = os.o[oi];
+    const long long local = cta - o.first;
+    const int s = (int)(local / o.tiles);
+    const int tile = (int)(local - (long long)s * o.tiles);
+    const int r0 = (tile / o.tiles_x) * kMT, c0 = (tile % o.tiles_x) * kMT;
+    const float* pa = a + (long long)s * o.ss;
+    const float* pb = b + (long long)s * o.ss;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < kMS * kMS; i += kMetThreads) {
+        const int r = i / kMS, c = i - r * kMS;
+        const int gr = r0 + r - kMR, gc = c0 + c - kMR;
+        float va = 0.f, vb = 0.f;
+        if (gr >= 0 && gr < o.H && gc >= 0 && gc < o.W) {
+            const long long off = (long long)gr * o.sr + (long long)gc * o.sc;
+            va = pa[off];
+            vb = pb[off];
+        }
+        sa[r][c] = va;
+        sb[r][c] = vb;
+    }
+    __syncthreads();
+    // horizontal pass: h[m][r][c] = sum_k w_k P_m(r, c + k), c over the 32 output columns
+    for (int i = tid; i < kMS * kMT; i += kMetThreads) {
+        const int r = i / kMT, c = i - r * kMT;
+        float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f, m4 = 0.f;
+#pragma unroll
+        for (int k = 0; k < 11; ++k) {
+            const float x = sa[r][c + k], y = sb[r][c + k], w = win.w[k];
+            m0 = fmaf(w, x, m0);
+            m1 = fmaf(w, y, m1);
+            m2 = fmaf(w, x * x, m2);
+            m3 = fmaf(w, y * y, m3);
+            m4 = fmaf(w, x * y, m4);
+        }
+        h[0][r][c] = m0;
+        h[1][r][c] = m1;
+        h[2][r][c] = m2;
+        h[3][r][c] = m3;
+        h[4][r][c] = m4;
+    }
+    __syncthreads();
+    float part = 0.f;
+    for (int i = tid; i < kMT * kMT; i += kMetThreads) {
+        const int r = i / kMT, c = i - r * kMT;
+        if (r0 + r >= o.H || c0 + c >= o.W) continue;
+        float mx = 0.f, my = 0.f, exx = 0.f, eyy = 0.f, exy = 0.f;
+#pragma unroll
+        for (int k = 0; k < 11; ++k) {
+            const float w = win.w[k];
+            mx = fmaf(w, h[0][r + k][c], mx);
+            my = fmaf(w, h[1][r + k][c], my);
+            exx = fmaf(w, h[2][r + k][c], exx);
+            eyy = fmaf(w, h[3][r + k][c], eyy);
+            exy = fmaf(w, h[4][r + k][c], exy);
+        }
+        const float sxx = exx - mx * mx, syy = eyy - my * my, sxy = exy - mx * my;
+        const float num = (2.f * mx * my + kMC1) * (2.f * sxy + kMC2);
+        const float den = (mx * mx + my * my + kMC1) * (sxx + syy + kMC2);
+        part += num / den;
+    }
+    double v = part;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    if ((tid & 31) == 0) red[tid >> 5] = v;
+    __syncthreads();
+    if (tid == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kMetThreads / 32; ++w) t += red[w];
+        partials[cta] = t;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_sq_err(const float* __restrict__ a, const float* __restrict__ b, long long n,
+                                                double* __restrict__ partials) {
+    __shared__ double red[8];
+    double acc = 0.0;
+    for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < n; i += (long long)gridDim.x * 256) {
+        const float d = a[i] - b[i];
+        acc += (double)d * (double)d;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < 8; ++w) t += red[w];
+        partials[blockIdx.x] = t;
+    }
+}
+
+// out = {MSE, PSNR, SSIM (mean of the three), axial, coronal, sagittal}
+__global__ void __launch_bounds__(256) k_metrics_fin(const double* __restrict__ tile_partials, Orients os,
+                                                     const double* __restrict__ sq_partials, long long n,
+                                                     double* __restrict__ out) {
+    __shared__ double red[8];
+    __shared__ double res[4];
+    for (int q = 0; q < 4; ++q) {
+        long long lo, hi;
+        if (q < 3) {
+            lo = os.o[q].first;
+            hi = lo + (long long)os.o[q].n * os.o[q].tiles;
+        }
+        const double* src = q < 3 ? tile_partials : sq_partials;
+        if (q == 3) {
+            lo = 0;
+            hi = kSqBlocks;
+        }
+        double acc = 0.0;
+        for (long long i = lo + threadIdx.x; i < hi; i += 256) acc += src[i];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < 8; ++w) t += red[w];
+            res[q] = t;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double ss[3];
+        for (int q = 0; q < 3; ++q) ss[q] = res[q] / ((double)os.o[q].n * os.o[q].H * os.o[q].W);
+        const double mse = res[3] / (double)n;
+        out[0] = mse;
+        out[1] = mse > 0.0 ? 10.0 * log10(1.0 / mse) : INFINITY;
+        out[2] = (ss[0] + ss[1] + ss[2]) / 3.0;
+        out[3] = ss[0];
+        out[4] = ss[1];
+        out[5] = ss[2];
+    }
+}
+
+Orients orients(int X, int Y, int Z) {
+    const long long XY = (long long)X * Y;
+    Orients os;
+    os.o[0] = Orient{XY, X, 1, Z, Y, X, 0, 0, 0};   // axial: z = const, rows y, columns x
+    os.o[1] = Orient{X, XY, 1, Y, Z, X, 0, 0, 0};   // coronal: y = const, rows z, columns x
+    os.o[2] = Orient{1, XY, X, X, Z, Y, 0, 0, 0};   // sagittal: x = const, rows z, columns y
+    long long first = 0;
+    for (int q = 0; q < 3; ++q) {
+        Orient& o = os.o[q];
+        o.tiles_x = (o.W + kMT - 1) / kMT;
+        o.tiles = o.tiles_x * ((o.H + kMT - 1) / kMT);
+        o.first = first;
+        first += (long long)o.n * o.tiles;
+    }
+    return os;
+}
+
+long long total_tiles(const Orients& os) { return os.o[2].first + (long long)os.o[2].n * os.o[2].tiles; }
+
+MWin metric_window() {
+    double g[11], s = 0;
+    for (int k = 0; k < 11; ++k) {
+        const double d = k - 5.0;
+        g[k] = exp(-d * d / (2 * 1.5 * 1.5));
+        s += g[k];
+    }
+    MWin w;
+    for (int k = 0; k < 11; ++k) w.w[k] = (float)(g[k] / s);
+    return w;
+}
+
+bool bad_dims(int X, int Y, int Z) { return X < 1 || Y < 1 || Z < 1 || X > 4096 || Y > 4096 || Z > 4096; }
+
+}  // namespace
+}  // namespace r2g
+
+using namespace r2g;
+
+R2G_API size_t r2g_metrics_workspace_size(int32_t X, int32_t Y, int32_t Z) {
+    if (bad_dims(X, Y, Z)) return 0;
+    Layout L;
+    L.take(sizeof(double) * (size_t)total_tiles(orients(X, Y, Z)));
+    L.take(sizeof(double) * kSqBlocks);
+    return L.off;
+}
+
+R2G_API r2g_status r2g_volume_metrics(int32_t X, int32_t Y, int32_t Z, const float* vol, const float* ref, double* out,
+                                      void* ws, size_t ws_bytes, r2g_stream stream) {
+    if (bad_dims(X, Y, Z)) return fail(R2G_E_INVAL, "volume dims must be 1..4096");
+    if (!vol || !ref || !out || !ws) return fail(R2G_E_INVAL, "NULL device pointer");
+    if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(R2G_E_INVAL, "workspace must be 256-byte aligned");
+    const Orients os = orients(X, Y, Z);
+    const long long nt = total_tiles(os);
+    Layout L;
+    const size_t o_tiles = L.take(sizeof(double) * (size_t)nt);
+    const size_t o_sq = L.take(sizeof(double) * kSqBlocks);
+    if (ws_bytes < L.off) return fail(R2G_E_INVAL, "metrics workspace needs %zu bytes", L.off);
+    if (nt >= (1ll << 31)) return fail(R2G_E_INVAL, "volume too large");
+    char* base = static_cast<char*>(ws);
+    double* tp = reinterpret_cast<double*>(base + o_tiles);
+    double* sq = reinterpret_cast<double*>(base + o_sq);
+    const long long n = (long long)X * Y * Z;
+    prof_begin(P_METRICS, stream);
+    k_slice_ssim<<<(unsigned)nt, kMetThreads, 0, stream>>>(vol, ref, os, metric_window(), tp);
+    k_sq_err<<<kSqBlocks, 256, 0, stream>>>(vol, ref, n, sq);
+    k_metrics_fin<<<1, 256, 0, stream>>>(tp, os, sq, n, out);
+    prof_end(P_METRICS, stream);
+    note_launches(3);
+    return check_launch("r2g_volume_metrics");
+}

@@ -202,6 +202,23 @@ def fdk_init(views, meas, cam, n_out: int, M=INIT_M, tau=INIT_TAU, k=INIT_K, see
     return G, vol
 
 
+# ----------------------------------------------------------------------------- volume metrics
+
+
+METRIC_KEYS = ("mse", "psnr", "ssim", "ssim_axial", "ssim_coronal", "ssim_sagittal")
+
+
+def volume_metrics(vol, ref, device="cuda") -> dict:
+    """Sec. 5.1's scores of a [Z, Y, X] device volume against a reference (float32
+    device tensors): MSE, PSNR (data range 1) and SSIM averaged over the axial,
+    coronal and sagittal slices (and each orientation's mean)."""
+    Z, Y, X = vol.shape
+    out = torch.empty(6, dtype=torch.float64, device=device)
+    ws = _bytes(r2g.r2g_metrics_workspace_size(X, Y, Z), device)
+    r2g.r2g_volume_metrics(vol.contiguous(), ref.contiguous(), out, ws)
+    return dict(zip(METRIC_KEYS, out.cpu().tolist()))
+
+
 # ----------------------------------------------------------------------------- training state
 
 

@@ -119,6 +119,12 @@ def even_angles(V: int, span_deg: float = 360.0) -> np.ndarray:
     return np.deg2rad(np.arange(V) * (span_deg / V))
 
 
+def limited_angles(V: int, span_deg: float) -> np.ndarray:
+    """Limited-angle scan (App. E): V projection angles evenly
+    spaced over [0, span_deg], both ends included."""
+    return np.deg2rad(np.linspace(0.0, span_deg, V))
+
+
 def grid_desc(origin, voxel, dims) -> np.ndarray:
     """One voxel grid: origin (3), voxel size (3), dims (X, Y, Z); centre of voxel
     (i, j, k) is origin + (index + 1/2) * voxel."""
@@ -357,6 +363,7 @@ class ScanSpec:
     V: int
     det: int      # detector edge in pixels (the detector always spans 409.6 mm)
     n_out: int    # output volume edge in voxels (TV patch spacing 2 / n_out)
+    span: float = 360.0  # scanned arc in degrees; < 360 = limited-angle (ends included)
 
 
 def batched_specs(n_scans: int = 16, seed: int = 5):
@@ -380,7 +387,8 @@ def make_scan(spec: ScanSpec, device=None):
     (gaussians, camera, views, measured projections, phantom volume)."""
     ph, vol = normalised_phantom(spec.seed, spec.n_out)
     cam = cone_camera(spec.det, spec.det, pitch=CONE_PITCH * 512 / spec.det)
-    views = view_table(even_angles(spec.V), CONE_L_SO)
+    ang = even_angles(spec.V) if spec.span >= 360.0 else limited_angles(spec.V, spec.span)
+    views = view_table(ang, CONE_L_SO)
     meas = phantom_projections(ph, views, cam, device=device).astype(np.float32)
     G = random_init(spec.M, spec.seed)
     return G, cam, views, meas, vol

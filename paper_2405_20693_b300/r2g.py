@@ -120,6 +120,8 @@ def lib():
             "r2g_fdk_filter": (_I32, [_I32, _P, _P, _P, _P]),
             "r2g_fdk_backproject": (_I32, [_I32, _P, _P, _P, _P, ctypes.c_float, _P, _P]),
             "r2g_init_workspace_size": (_SZ, [_P, _I64]),
+            "r2g_metrics_workspace_size": (_SZ, [_I32, _I32, _I32]),
+            "r2g_volume_metrics": (_I32, [_I32, _I32, _I32, _P, _P, _P, _P, _SZ, _P]),
             "r2g_init_gaussians": (_I32, [_P, _P, ctypes.c_float, _I64, ctypes.c_uint64, ctypes.c_float, _P, _P, _P,
                                           _P, _P, _P, _SZ, _P]),
             "r2g_raster_lists": (_I32, [_I64, _I32, _P, _P, _P, _SZ, _P, _P, _I64, _P, _P]),
@@ -259,6 +261,19 @@ def r2g_init_gaussians(vol, grid, tau: float, M: int, seed: int, k: float, mean,
                                     ws.numel(), _stream(stream)))
 
 
+def r2g_metrics_workspace_size(X: int, Y: int, Z: int) -> int:
+    return lib().r2g_metrics_workspace_size(int(X), int(Y), int(Z))
+
+
+def r2g_volume_metrics(vol, ref, out, ws, stream=None):
+    """vol, ref: float32 [Z, Y, X]; out: float64 [6] = MSE, PSNR, SSIM, axial, coronal, sagittal."""
+    _f32(vol, ref)
+    if out.dtype != torch.float64:
+        raise ValueError("out must be a float64 tensor")
+    Z, Y, X = vol.shape
+    _check(lib().r2g_volume_metrics(X, Y, Z, _ptr(vol), _ptr(ref), _ptr(out), _ptr(ws), ws.numel(), _stream(stream)))
+
+
 def r2g_raster_lists(M: int, V: int, cam: Camera, opts: RasterOpts, ws, ranges, ids, stream=None) -> int:
     n = ctypes.c_int64(0)
     _check(lib().r2g_raster_lists(M, V, ctypes.byref(cam), ctypes.byref(opts), _ptr(ws), ws.numel(), _ptr(ranges),
@@ -353,7 +368,7 @@ def r2g_adam_step(raw, act, grad, m, v, it: int, opts: AdamOpts, stream=None):
 
 PROFILE_KERNELS = ("project", "emit", "sort", "ranges", "splat_fwd", "splat_bwd", "project_bwd", "vox_project",
                    "vox_fwd", "vox_bwd", "vox_chain", "loss", "tv", "adam", "vox_emit", "vox_sort", "vox_ranges",
-                   "fdk_filter", "fdk_bp", "init_select", "init_knn")
+                   "fdk_filter", "fdk_bp", "init_select", "init_knn", "metrics")
 
 
 def r2g_profile_enable(on: bool, max_spans: int = 4096):
