@@ -57,6 +57,8 @@ def lib():
             L.orc_voxelize_backward.restype = None
             L.orc_voxelize_backward.argtypes = [i64, _D, _D, _D, _D, _D, i32, dbl, _D, _D, _D, _D, _D, _D, _D, _D,
                                                 _D]
+            L.orc_record_grads.restype = None
+            L.orc_record_grads.argtypes = [i64, _D, _D, _D, _D, _D, i32, _D, dbl, _D, _D]
             L.orc_mean_mu.restype = None
             L.orc_mean_mu.argtypes = [i64, _D, _D, _D, _D, i32, _D, _D]
             L.orc_render_exact.restype = None
@@ -158,6 +160,18 @@ def render_backward(G, views, cam, dimg, Q=9.0, want_band=False, biased=False):
     lib().orc_render_backward(g.M, *g.ptrs(), _p(views), views.shape[0], _p(cv), float(Q), _p(dimg),
                               *(_p(a) for a in out), *((_p(a) if a is not None else None) for a in band))
     return (out, band) if want_band else out
+
+
+def record_grads(G, views, cam, dimg, Q=9.0, biased=False):
+    """Per (view, Gaussian) record gradient d(rho_hat, p^x, p^y, a, b, c) of the gated
+    image for dL/dI = dimg, [V, M, 6] float64 (p^ in detector units)."""
+    g = _G(G)
+    views = _d(views)
+    cv = _camv(cam, 0, biased)
+    dimg = _d(dimg)
+    out = np.zeros((views.shape[0], g.M, 6))
+    lib().orc_record_grads(g.M, *g.ptrs(), _p(views), views.shape[0], _p(cv), float(Q), _p(dimg), _p(out))
+    return out
 
 
 def mean_mu(G, views, cam):

@@ -468,6 +468,43 @@ void render_backward(const Params& Pm, const double* views, int V, const Cam& ca
     }
 }
 
+// Per (view, Gaussian) record gradient d(rho_hat, p^x, p^y, a, b, c) of the gated
+// image sum for dL/dI = dimg (detector units), out[v][i][6]; zeros for records
+// that are dropped or touch no gated pixel.
+void record_grads(const Params& Pm, const double* views, int V, const Cam& cam, double Q, const double* dimg,
+                  double* out) {
+    const int H = cam.H, Wd = cam.W;
+    const ParamsT<double> G = widen<double>(Pm);
+    for (int v = 0; v < V; ++v) {
+        const double* view = views + 12 * v;
+        const double* dIv = dimg + (int64_t)v * H * Wd;
+        for (int64_t i = 0; i < Pm.M; ++i) {
+            double* drec = out + ((int64_t)v * Pm.M + i) * 6;
+            for (int k = 0; k < 6; ++k) drec[k] = 0.0;
+            M3<double> Sigma, R;
+            double qn[4], qnorm;
+            covariance(&G.scale[3 * i], &G.quat[4 * i], Sigma, R, qn, qnorm);
+            Proj<double> P = project_one(&G.mean[3 * i], Sigma, G.rho[i], view, cam);
+            if (!P.valid) continue;
+            int c0, c1, r0, r1;
+            centre_range(P.ph[0], std::sqrt(Q * P.sh[0]), cam.pitch_u, cam.off_u, Wd, c0, c1);
+            centre_range(P.ph[1], std::sqrt(Q * P.sh[2]), cam.pitch_v, cam.off_v, H, r0, r1);
+            const double a = P.conic[0], b = P.conic[1], c = P.conic[2];
+            for (int r = r0; r <= r1; ++r) {
+                const double dy = pix_eta(r, cam) - P.ph[1];
+                for (int cc = c0; cc <= c1; ++cc) {
+                    const double dx = pix_xi(cc, cam) - P.ph[0];
+                    const double q = a * dx * dx + 2 * b * dx * dy + c * dy * dy;
+                    if (!(q <= Q)) continue;
+                    double pr[6];
+                    pair_record_grad(P, dx, dy, q, dIv[(int64_t)r * Wd + cc], pr);
+                    for (int k = 0; k < 6; ++k) drec[k] += pr[k];
+                }
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // O1 voxelizer (Eq. 4): V[x] = sum_i rho_i exp(-1/2 (x-p_i)^T Sigma_i^{-1} (x-p_i)) [q <= Q3]
 // at voxel centres x = origin + (idx + 1/2) * voxel.  Grid layout [Z][Y][X].
@@ -927,6 +964,11 @@ void orc_mean_mu(int64_t M, const double* mean, const double* scale, const doubl
         }
         mu_mean[i] = n ? sum / n : 0.0;
     }
+}
+
+void orc_record_grads(int64_t M, const double* mean, const double* scale, const double* quat, const double* rho,
+                      const double* views, int V, const double* camv, double Q, const double* dimg, double* out) {
+    record_grads(Params{M, mean, scale, quat, rho}, views, V, make_cam(camv), Q, dimg, out);
 }
 
 // Complex-step derivative of the whole image with respect to one parameter:
