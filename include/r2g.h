@@ -315,6 +315,12 @@ typedef struct {
     size_t loss_ws_bytes;
     void* tv_ws;
     size_t tv_ws_bytes;
+    /* adaptive-control statistics (optional, device [M] each, or NULL): every step adds,
+     * per Gaussian whose projection received a gradient, |dL/dp^| in normalised device
+     * coordinates (the pixel-space gradient of its projected mean times (W/2, H/2)) to
+     * dens_grad and 1 to dens_count; r2g_densify reads them. */
+    float* dens_grad;
+    float* dens_count;
 } r2g_job;
 
 r2g_status r2g_train_step(const r2g_job* job, const r2g_round_entry* entry, r2g_stream stream);
@@ -369,6 +375,39 @@ r2g_status r2g_init_gaussians(const float* vol, const r2g_grid* grid, float tau,
                               float* mean, float* scale, float* quat, float* rho, int64_t* n_out, void* ws,
                               size_t ws_bytes, r2g_stream stream);
 
+/* ---------------------------------------------------------------- adaptive density control (Sec. 4.2.3)
+ *
+ * Between training steps (Sec. 5.1: every 100 iterations from 500 to 15k), empty
+ * Gaussians are removed and those whose projected means received large gradients
+ * are cloned or split, the density of the original and of every copy halved. */
+typedef struct {
+    float grad_threshold;  /* densify where the mean |dL/dp^| (NDC, see r2g_job.dens_grad) >= this (5e-5) */
+    float min_density;     /* remove where rho < this; no size-based removal */
+    float split_scale;     /* a densified Gaussian whose largest scale exceeds this is split, else cloned */
+    float split_factor;    /* a split's two children have scales / split_factor (1.6) */
+    uint64_t seed;         /* counter for the children's offsets (see below) */
+} r2g_densify_opts;
+
+size_t r2g_densify_workspace_size(void);
+/* In: the training state of M Gaussians (device raw, act, m, v in the flat layout
+ * [quat 4M | mean 3M | scale 3M | rho M]) and the accumulated statistics dens_grad[M],
+ * dens_count[M].  Out: the new state in raw_out, act_out, m_out, v_out (device, each
+ * holding 11 * max_gaussians floats, not aliasing the inputs), flat layout with the
+ * new count M' = *m_new (device int64): the survivors in index order (Adam moments
+ * kept; a clone's original with rho / 2), then the copies in the order of their
+ * originals with zero moments -- a clone's copy (rho / 2), a split's two children
+ * (means p + R(q)(s * z), scales s / split_factor, rho / 2; the split original is
+ * removed).  z: child c of Gaussian i, component k, uses u_j, u_(j+1) with j =
+ * ((2 i + c) 3 + k) 2, u_j = ((SplitMix64(seed + (j + 1) 0x9E3779B97F4A7C15) >> 40)
+ * + 1/2) / 2^24, z = sqrt(-2 ln u_j) cos(2 pi u_(j+1)) (Box-Muller).  Densify
+ * candidates beyond max_gaussians (>= M) are left as they are, in index order.
+ * The activated values of the copies are written and the raw ones derived from them
+ * (scale: log, rho: inverse softplus). */
+r2g_status r2g_densify(int64_t M, const float* raw, const float* act, const float* m, const float* v,
+                       const float* dens_grad, const float* dens_count, const r2g_densify_opts* opts,
+                       int64_t max_gaussians, float* raw_out, float* act_out, float* m_out, float* v_out,
+                       int64_t* m_new, void* ws, size_t ws_bytes, r2g_stream stream);
+
 /* ---------------------------------------------------------------- volume metrics (Sec. 5.1)
  *
  * The scores the paper reports for a reconstruction: PSNR over the whole volume and
@@ -395,7 +434,7 @@ r2g_status r2g_volume_metrics(int32_t X, int32_t Y, int32_t Z, const float* vol,
  * 5 splat_bwd, 6 project_bwd, 7 vox_project, 8 vox_fwd, 9 vox_bwd, 10 vox_chain,
  * 11 loss, 12 tv, 13 adam, 14-16 the same three list stages for the brick lists,
  * 17 fdk_filter, 18 fdk_bp, 19 init_select (the selection passes and the writes
- * of r2g_init_gaussians), 20 init_knn, 21 metrics (r2g_volume_metrics).
+ * of r2g_init_gaussians), 20 init_knn, 21 metrics (r2g_volume_metrics), 22 densify.
  * Not for use inside stream capture.
  * max_spans bounds the recorded pairs (events are created once, here). */
 r2g_status r2g_profile_enable(int32_t on, int32_t max_spans);

@@ -40,7 +40,7 @@ const char* const kProfNames[P_COUNT] = {"project",    "emit",       "sort",    
                                          "splat_bwd",  "project_bwd", "vox_project", "vox_fwd", "vox_bwd",
                                          "vox_chain",  "loss",       "tv",        "adam",    "vox_emit",
                                          "vox_sort",   "vox_ranges", "fdk_filter", "fdk_bp",  "init_select",
-                                         "init_knn",   "metrics"};
+                                         "init_knn",   "metrics",    "densify"};
 std::atomic<long long> g_launches{0};
 std::mutex g_prof_mu;
 bool g_prof_on = false;

@@ -84,6 +84,10 @@ struct AdamState {
     float* v;
     const float* grad;  // gradient already accumulated by other kernels (added to this kernel's own)
     AdamArgs a;
+    // adaptive-control statistics (optional): per Gaussian, the sum over its records
+    // with a gradient of |dL/dp^| in normalised device coordinates, and their count
+    float* dens_grad;
+    float* dens_count;
 };
 
 // Device: one parameter at flat index e of group grp with this kernel's own

@@ -27,7 +27,7 @@ r2g_status check_launch(const char* what);
 enum ProfKernel : int {
     P_PROJECT = 0, P_EMIT, P_SORT, P_RANGES, P_SPLAT_FWD, P_SPLAT_BWD, P_PROJECT_BWD,
     P_VOX_PROJECT, P_VOX_FWD, P_VOX_BWD, P_VOX_CHAIN, P_LOSS, P_TV, P_ADAM, P_VOX_EMIT, P_VOX_SORT,
-    P_VOX_RANGES, P_FDK_FILTER, P_FDK_BP, P_INIT_SELECT, P_INIT_KNN, P_METRICS, P_COUNT
+    P_VOX_RANGES, P_FDK_FILTER, P_FDK_BP, P_INIT_SELECT, P_INIT_KNN, P_METRICS, P_DENSIFY, P_COUNT
 };
 // The profile ids of one list build's three stages (emission, sorting, ranges).
 struct ListProf {

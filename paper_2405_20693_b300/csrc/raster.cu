@@ -691,6 +691,7 @@ __global__ void __launch_bounds__(128) k_project_bwd(Params G, const float* __re
     load_gaussian(G, i, p, s, q);
     const float rho = G.rho[i];
     float gp[3] = {0.f, 0.f, 0.f}, gs[3] = {0.f, 0.f, 0.f}, gR[3][3] = {{0.f}}, grho = 0.f;
+    float dens_g = 0.f, dens_n = 0.f;  // adaptive-control statistics of this call
     Proj P;
     bool have_rot = false;
     for (int v = 0; v < V; ++v) {
@@ -713,6 +714,10 @@ __global__ void __launch_bounds__(128) k_project_bwd(Params G, const float* __re
         const float d_cx = rhohat * (pa * Sx + pb * Sy);
         const float d_cy = rhohat * (pb * Sx + pc * Sy);
         const float d_pa = -0.5f * rhohat * Sxx, d_pb = -rhohat * Sxy, d_pc = -0.5f * rhohat * Syy;
+        if (ADAM) {  // |dL/dp^| in normalised device coordinates (pixel gradient x (W/2, H/2))
+            dens_g += hypotf(d_cx * (0.5f * (float)cam.W), d_cy * (0.5f * (float)cam.H));
+            dens_n += 1.f;
+        }
         // --- to detector units
         const float d_phx = d_cx / cam.pu, d_phy = d_cy / cam.pv;
         const float d_a = d_pa * cam.pu * cam.pu, d_b = d_pb * cam.pu * cam.pv, d_c = d_pc * cam.pv * cam.pv;
@@ -811,6 +816,10 @@ __global__ void __launch_bounds__(128) k_project_bwd(Params G, const float* __re
     if (have_rot) quat_grad(P.qn, P.qnorm, gR, gq);
     if (ADAM) {
         adam_gaussian(adam, i, gq, gp, gs, grho);
+        if (adam.dens_grad && dens_n > 0.f) {
+            adam.dens_grad[i] += dens_g;
+            adam.dens_count[i] += dens_n;
+        }
         return;
     }
     if (!have_rot) return;

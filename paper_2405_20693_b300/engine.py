@@ -245,6 +245,12 @@ class TrainState:
         self.m = torch.zeros_like(self.act)
         self.v = torch.zeros_like(self.act)
 
+    def adopt(self, raw, act, m, v, M: int):
+        """Take over a state of M Gaussians (flat layout, arrays of at least 11 M floats)."""
+        self.M = int(M)
+        self.raw, self.act, self.m, self.v = raw, act, m, v
+        self.grad = torch.zeros_like(act)
+
     def views_of(self, t):
         M = self.M
         return t[0:4 * M].view(M, 4), t[4 * M:7 * M].view(M, 3), t[7 * M:10 * M].view(M, 3), t[10 * M:11 * M]
@@ -312,6 +318,10 @@ class Scan:
                  device="cuda", headroom=1.5, seed=0, biased=False):
         self.state = TrainState(G, device=device)
         self.biased = bool(biased)
+        self.version = 0              # bumped whenever the C job changes (densification)
+        self.dens_grad = self.dens_count = None
+        self.dens_schedule = None
+        self.dens_seed = seed
         self.rng = np.random.Generator(np.random.PCG64(seed + 2))  # this scan's view / patch choices
         self.it = 0
         self.M = G.M
@@ -333,8 +343,51 @@ class Scan:
         self.loss_ws = _bytes(r2g.r2g_loss_workspace_size(1, cam.H, cam.W), device)
         self.tv_ws = _bytes(r2g.r2g_tv_workspace_size(1, D), device)
         self.adam = r2g.adam_opts(total_iters=total_iters)
+        self.device = device
+        self.headroom = headroom
         self._size_workspaces(headroom)
         self.job = self._make_job()
+
+    def enable_adaptive(self, max_gaussians: int, opts=None, start=500, stop=15000, every=100):
+        """Adaptive density control (Sec. 4.2.3, schedule of Sec. 5.1): from then on each
+        step accumulates the position-gradient statistics, and `densify()` runs after
+        the steps whose iteration count is a multiple of `every` in [start, stop]."""
+        self.max_gaussians = int(max_gaussians)
+        self.dens_opts = opts or r2g.densify_opts()
+        self.dens_schedule = (int(start), int(stop), int(every))
+        self.dens_ws = _bytes(r2g.r2g_densify_workspace_size(), self.device)
+        self.dens_grad = torch.zeros(self.max_gaussians, dtype=torch.float32, device=self.device)
+        self.dens_count = torch.zeros_like(self.dens_grad)
+        self.job = self._make_job()
+
+    def densify_due(self) -> bool:
+        if getattr(self, "dens_schedule", None) is None:
+            return False
+        a, b, e = self.dens_schedule
+        return a <= self.it <= b and self.it % e == 0
+
+    def densify(self):
+        """One prune/clone/split step (r2g_densify) into a new state; the statistics
+        restart, the workspaces are re-sized for the new count, and the C job is
+        rebuilt (a captured round graph must be recaptured: `version` changes)."""
+        s, cap = self.state, self.max_gaussians
+        out = [torch.empty(11 * cap, dtype=torch.float32, device=self.device) for _ in range(4)]
+        m_new = torch.zeros(1, dtype=torch.int64, device=self.device)
+        opts = self.dens_opts
+        opts.seed = (int(self.dens_seed) * 1_000_003 + self.it) & (2 ** 64 - 1)
+        r2g.r2g_densify(s.M, s.raw, s.act, s.m, s.v, self.dens_grad, self.dens_count, opts, cap, *out, m_new,
+                        self.dens_ws)
+        M2 = int(m_new.item())
+        s.adopt(*out, M2)
+        self.M = M2
+        self.dens_grad.zero_()
+        self.dens_count.zero_()
+        self.rast.M = M2
+        self.vox.M = M2
+        self._size_workspaces(self.headroom, probes=2)
+        self.job = self._make_job()
+        self.version += 1
+        return M2
 
     def volume_params(self):
         """(mean, scale, quat, rho) for the voxelizer.  The rectified model's densities
@@ -348,14 +401,14 @@ class Scan:
         r2g.r2g_mean_mu(mean, scale, quat, self.views, self.rast.cam, rho=rho, rho_vol=rv)
         return mean, scale, quat, rv
 
-    def _size_workspaces(self, headroom):
+    def _size_workspaces(self, headroom, probes=6):
         """Size the list workspaces on a spread of views and patch positions with
         checked runs, then add headroom: the captured graph cannot regrow them."""
         from .inputs import patch_grid
 
         mean, scale, quat, rho = self.state.params()
         need_r, need_v = 0, 0
-        for v in np.linspace(0, self.V - 1, min(self.V, 6)).astype(int):
+        for v in np.linspace(0, self.V - 1, min(self.V, probes)).astype(int):
             self.rast.forward(mean, scale, quat, rho, self.views[v:v + 1], self.image, check=True)
             need_r = max(need_r, r2g.r2g_poll(self.rast.ws)[1])
         for off in ((0, 0, 0), ((self.n_out - self.D) // 2,) * 3, (self.n_out - self.D,) * 3):
@@ -388,6 +441,8 @@ class Scan:
         J.voxel_ws, J.voxel_ws_bytes = self.vox.ws.data_ptr(), self.vox.ws.numel()
         J.loss_ws, J.loss_ws_bytes = self.loss_ws.data_ptr(), self.loss_ws.numel()
         J.tv_ws, J.tv_ws_bytes = self.tv_ws.data_ptr(), self.tv_ws.numel()
+        if self.dens_grad is not None:
+            J.dens_grad, J.dens_count = self.dens_grad.data_ptr(), self.dens_count.data_ptr()
         return J
 
     def next_entry(self):
@@ -431,6 +486,7 @@ class BatchTrainer:
         self.streams = [torch.cuda.Stream(device=device) for _ in range(max(1, n_streams))]
         self.graph = None
         self.use_graph = graph
+        self._versions = [sc.version for sc in self.scans]
         self.elem = ctypes_sizeof_entry()
 
     def _fill(self):
@@ -461,9 +517,23 @@ class BatchTrainer:
     def round(self):
         """One iteration of every scan.  The host table is rewritten only after the
         previous round has finished.  With graph=True the first round runs eagerly
-        (which also loads every kernel) and is then captured; later rounds replay."""
+        (which also loads every kernel) and is then captured; later rounds replay.
+        Scans with adaptive control densify after the round when due, and the graph
+        is recaptured at the next round."""
         torch.cuda.current_stream().synchronize()
+        versions = [sc.version for sc in self.scans]
+        if versions != self._versions:
+            self.graph = None
+            self._versions = versions
         self._fill()
+        self._round()
+        due = [sc for sc in self.scans if sc.densify_due()]
+        if due:
+            torch.cuda.current_stream().synchronize()
+            for sc in due:
+                sc.densify()
+
+    def _round(self):
         if not self.use_graph:
             self._issue()
             return

@@ -38,6 +38,16 @@ class RasterOpts(ctypes.Structure):
                 ("count_pairs", ctypes.c_int32), ("biased", ctypes.c_int32)]
 
 
+class DensifyOpts(ctypes.Structure):
+    _fields_ = [("grad_threshold", ctypes.c_float), ("min_density", ctypes.c_float), ("split_scale", ctypes.c_float),
+                ("split_factor", ctypes.c_float), ("seed", ctypes.c_uint64)]
+
+
+def densify_opts(grad_threshold=5e-5, min_density=1e-5, split_scale=0.02, split_factor=1.6, seed=0) -> DensifyOpts:
+    return DensifyOpts(float(grad_threshold), float(min_density), float(split_scale), float(split_factor),
+                       int(seed) & (2 ** 64 - 1))
+
+
 class Grid(ctypes.Structure):
     _fields_ = [("origin", ctypes.c_float * 3), ("voxel", ctypes.c_float * 3), ("dims", ctypes.c_int32 * 3)]
 
@@ -62,7 +72,8 @@ class Job(ctypes.Structure):
                 ("dvol", ctypes.c_void_p), ("loss", ctypes.c_void_p), ("raster_ws", ctypes.c_void_p),
                 ("raster_ws_bytes", ctypes.c_size_t), ("voxel_ws", ctypes.c_void_p),
                 ("voxel_ws_bytes", ctypes.c_size_t), ("loss_ws", ctypes.c_void_p),
-                ("loss_ws_bytes", ctypes.c_size_t), ("tv_ws", ctypes.c_void_p), ("tv_ws_bytes", ctypes.c_size_t)]
+                ("loss_ws_bytes", ctypes.c_size_t), ("tv_ws", ctypes.c_void_p), ("tv_ws_bytes", ctypes.c_size_t),
+                ("dens_grad", ctypes.c_void_p), ("dens_count", ctypes.c_void_p)]
 
 
 def camera(cam) -> Camera:
@@ -121,6 +132,8 @@ def lib():
             "r2g_fdk_backproject": (_I32, [_I32, _P, _P, _P, _P, ctypes.c_float, _P, _P]),
             "r2g_init_workspace_size": (_SZ, [_P, _I64]),
             "r2g_metrics_workspace_size": (_SZ, [_I32, _I32, _I32]),
+            "r2g_densify_workspace_size": (_SZ, []),
+            "r2g_densify": (_I32, [_I64, _P, _P, _P, _P, _P, _P, _P, _I64, _P, _P, _P, _P, _P, _P, _SZ, _P]),
             "r2g_volume_metrics": (_I32, [_I32, _I32, _I32, _P, _P, _P, _P, _SZ, _P]),
             "r2g_init_gaussians": (_I32, [_P, _P, ctypes.c_float, _I64, ctypes.c_uint64, ctypes.c_float, _P, _P, _P,
                                           _P, _P, _P, _SZ, _P]),
@@ -261,6 +274,20 @@ def r2g_init_gaussians(vol, grid, tau: float, M: int, seed: int, k: float, mean,
                                     ws.numel(), _stream(stream)))
 
 
+def r2g_densify_workspace_size() -> int:
+    return lib().r2g_densify_workspace_size()
+
+
+def r2g_densify(M: int, raw, act, m, v, dens_grad, dens_count, opts: DensifyOpts, max_gaussians: int, raw_out,
+                act_out, m_out, v_out, m_new, ws, stream=None):
+    _f32(raw, act, m, v, dens_grad, dens_count, raw_out, act_out, m_out, v_out)
+    if m_new.dtype != torch.int64:
+        raise ValueError("m_new must be an int64 tensor")
+    _check(lib().r2g_densify(int(M), _ptr(raw), _ptr(act), _ptr(m), _ptr(v), _ptr(dens_grad), _ptr(dens_count),
+                             ctypes.byref(opts), int(max_gaussians), _ptr(raw_out), _ptr(act_out), _ptr(m_out),
+                             _ptr(v_out), _ptr(m_new), _ptr(ws), ws.numel(), _stream(stream)))
+
+
 def r2g_metrics_workspace_size(X: int, Y: int, Z: int) -> int:
     return lib().r2g_metrics_workspace_size(int(X), int(Y), int(Z))
 
@@ -368,7 +395,7 @@ def r2g_adam_step(raw, act, grad, m, v, it: int, opts: AdamOpts, stream=None):
 
 PROFILE_KERNELS = ("project", "emit", "sort", "ranges", "splat_fwd", "splat_bwd", "project_bwd", "vox_project",
                    "vox_fwd", "vox_bwd", "vox_chain", "loss", "tv", "adam", "vox_emit", "vox_sort", "vox_ranges",
-                   "fdk_filter", "fdk_bp", "init_select", "init_knn", "metrics")
+                   "fdk_filter", "fdk_bp", "init_select", "init_knn", "metrics", "densify")
 
 
 def r2g_profile_enable(on: bool, max_spans: int = 4096):
