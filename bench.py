@@ -475,6 +475,58 @@ def measure_limited_angle(dev, iters=3000):
     return {"iterations": iters, "views": 100, "results": out}
 
 
+def measure_adaptive(dev, iters=3000):
+    """Adaptive density control (Sec. 4.2.3) on one scan of the uneven workload's kind
+    (seed 242: 20k Gaussians from the random initialisation, 50 views of 256^2, 128^3
+    volume), trained with and without it for `iters` fused iterations (one batched
+    round each), densifying every 100 iterations from 500 to iters / 2 (the paper's
+    500..15k of 30k, compressed): Gaussian counts, the volumes' PSNR / 3D SSIM, and the
+    device time of r2g_densify with its HBM roofline (algorithmic bytes: the four
+    11-float state arrays read for every input Gaussian and written for every output
+    one, plus the two statistics arrays)."""
+    import torch
+
+    from paper_2405_20693_b300 import engine, r2g
+    from paper_2405_20693_b300 import inputs as I
+
+    spec = I.ScanSpec(242, 20000, 50, 256, 128)
+    G, cam, views, meas, vol = I.make_scan(spec, device=dev)
+    gt = torch.as_tensor(vol.astype(np.float32), device=dev)
+    plain = engine.Scan(G, views, meas, cam, n_out=128, D=32, total_iters=iters, seed=1, device=dev)
+    ac = engine.Scan(G, views, meas, cam, n_out=128, D=32, total_iters=iters, seed=1, device=dev)
+    ac.enable_adaptive(10 * G.M, start=500, stop=iters // 2, every=100)
+    bt = engine.BatchTrainer([plain, ac], graph=True, device=dev)
+    kid = r2g.PROFILE_KERNELS.index("densify")
+    r2g.r2g_profile_enable(True, 4096)
+    r2g.r2g_profile_select(1 << kid)
+    r2g.r2g_profile_reset()
+    counts, ins = [], []
+    for _ in range(iters):
+        m_before = ac.M
+        bt.round()
+        if ac.M != m_before or (ac.it % 100 == 0 and 500 <= ac.it <= iters // 2):
+            counts.append((ac.it, ac.M))
+            ins.append((m_before, ac.M))
+    torch.cuda.synchronize()
+    n, t = r2g.r2g_profile_read(kid)
+    r2g.r2g_profile_enable(False)
+    out = {"iterations": iters, "densify_every": 100, "densify_from_to": [500, iters // 2],
+           "gaussians": {"start": G.M, "end": ac.M, "trajectory": counts}}
+    for name, sc in (("without", plain), ("with", ac)):
+        vox = engine.Voxelizer(sc.M, I.cube_grid(128), device=dev)
+        m = engine.volume_metrics(vox.forward(*sc.state.params()).view(128, 128, 128), gt, device=dev)
+        out[name] = {"psnr": m["psnr"], "ssim": m["ssim"], "gaussians": sc.M}
+    if n:
+        ms = t / n
+        algo = sum(4 * 11 * 4 * (a + b) + 8 * a for a, b in ins) / max(1, len(ins))
+        pk = peaks()
+        out["densify_kernel"] = {"calls": n, "ms_per_call": ms,
+                                 "roofline": {"bound": "hbm", "achieved": algo / (ms * 1e-3) / 1e9,
+                                              "peak": pk["hbm_gbs"], "unit": "GB/s",
+                                              "frac": algo / (ms * 1e-3) / 1e9 / pk["hbm_gbs"], "traffic": None}}
+    return out
+
+
 def voxel_box_counter(sc):
     """Voxels of each Gaussian's box (|x_k - p_k| <= sqrt(Q3 Sigma_kk), voxel centres)
     inside a D^3 TV patch at a given offset, summed over Gaussians: FP64 on the host
@@ -513,6 +565,11 @@ def run_ours(args, rank, world, local_rank):
         dist.init_process_group("nccl", device_id=dev)
     seed = rank * 1000
     G, cam, views_np, meas_np = make_workload(seed, dev)
+    if args.extras_only:
+        if rank == 0:
+            print(json.dumps({"volume_metrics": measure_metrics(dev), "limited_angle": measure_limited_angle(dev),
+                              "adaptive_control": measure_adaptive(dev)}), flush=True)
+        return
     if args.fdk_only:
         if rank == 0:
             print(json.dumps({"fdk_init": measure_fdk_init(dev, views_np, meas_np, cam, reps=args.steps,
@@ -674,13 +731,14 @@ def run_ours(args, rank, world, local_rank):
                     "frac": None, "traffic": ncu_traffic(dom)}
         batched = None
         serving = None
-        fdk_init = metrics = limited = None
+        fdk_init = metrics = limited = adaptive = None
         if world == 1 and not args.no_batched:
             batched = measure_batched(dev)
             serving = measure_serving(dev)
             fdk_init = measure_fdk_init(dev, views_np, meas_np, cam, cpu=not args.no_cpu_baseline)
             metrics = measure_metrics(dev)
             limited = measure_limited_angle(dev)
+            adaptive = measure_adaptive(dev)
         cpu = None
         # CPU baseline: the oracle on two full steps of the same workload
         if world == 1 and not args.no_cpu_baseline:
@@ -715,6 +773,7 @@ def run_ours(args, rank, world, local_rank):
             "fdk_init": fdk_init,
             "volume_metrics": metrics,
             "limited_angle": limited,
+            "adaptive_control": adaptive,
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
@@ -734,6 +793,8 @@ def main():
                     help="skip the multi-scan scans/hour, serving and FDK-initialisation measurements")
     ap.add_argument("--fdk-only", action="store_true",
                     help="time only the FDK initialisation of the workload's scan (--steps runs)")
+    ap.add_argument("--extras-only", action="store_true",
+                    help="run only the volume-metrics, limited-angle and adaptive-control legs")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
