@@ -421,7 +421,8 @@ r2g_status r2g_densify(int64_t M, const float* raw, const float* act, const floa
 size_t r2g_metrics_workspace_size(int32_t X, int32_t Y, int32_t Z);
 /* vol, ref: device [Z][Y][X]; out: device double[6] = {MSE, PSNR, SSIM, axial,
  * coronal, sagittal}, written; ws: device, 256-byte aligned,
- * r2g_metrics_workspace_size bytes.  Deterministic (fixed summation order). */
+ * r2g_metrics_workspace_size bytes (it holds transposed copies of both volumes).
+ * Deterministic (fixed summation order). */
 r2g_status r2g_volume_metrics(int32_t X, int32_t Y, int32_t Z, const float* vol, const float* ref, double* out,
                               void* ws, size_t ws_bytes, r2g_stream stream);
 

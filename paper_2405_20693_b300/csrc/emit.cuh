@@ -136,27 +136,21 @@ struct FusedKeys {
     WsStatus* item_st;        // n_keys = item count
 };
 
-// Each block walks its records (blockIdx.x * per_block .. + per_block) in rounds of
-// 256 and writes every record's entries at its offset.  HIST (fused path): also
-// count the block's written entries per key into hist[key * gridDim.x + block]
-// and key_totals; the last block to finish (the status block's arrival counter,
-// which the count pass left at gridDim.x) turns key_totals into each key's first
-// entry (written back into key_totals), range, first item and items.
+// Emission of one block's records (blockIdx.x * per_block .. + per_block), in
+// rounds of 256: every record's entries are written at its offset.  HIST (fused
+// path): also count the block's written entries per key into hist[key * gridDim.x +
+// block] and add them to key_totals.  h: shared [kFusedKeys] (HIST), s_info: shared
+// uint4 [256], s_ex: shared [256], sm8: shared [8].
 template <class Op, bool HIST>
-__global__ void __launch_bounds__(256) k_emit_chunks(Op op, long long n_rec, long long per_block,
-                                                     const unsigned long long* partials, uint64_t* out,
-                                                     unsigned long long capacity, uint32_t* __restrict__ hist,
-                                                     uint32_t* __restrict__ key_totals, int n_keys, WsStatus* st,
-                                                     FusedKeys fk) {
-    __shared__ uint32_t sm[8];
-    __shared__ uint32_t h[HIST ? kFusedKeys : 1];
-    __shared__ int s_last;
+__device__ __forceinline__ void emit_block(const Op& op, long long n_rec, long long per_block,
+                                           const unsigned long long* partials, uint64_t* out,
+                                           unsigned long long capacity, uint32_t* __restrict__ hist,
+                                           uint32_t* __restrict__ key_totals, int n_keys, uint32_t* h, uint4* s_info,
+                                           uint32_t* s_ex, uint32_t* sm8) {
     if (HIST) {
         for (int k = threadIdx.x; k < n_keys; k += 256) h[k] = 0;
         __syncthreads();
     }
-    __shared__ uint4 s_info[256];
-    __shared__ uint32_t s_ex[256];
     const long long begin = min(n_rec, (long long)blockIdx.x * per_block);
     const long long end = min(n_rec, begin + per_block);
     unsigned long long running = partials[blockIdx.x];
@@ -169,7 +163,7 @@ __global__ void __launch_bounds__(256) k_emit_chunks(Op op, long long n_rec, lon
             inf = op.info(r);
         }
         uint32_t tot;
-        const uint32_t ex = block_exclusive_scan_256(c, sm, &tot);
+        const uint32_t ex = block_exclusive_scan_256(c, sm8, &tot);
         s_info[threadIdx.x] = inf;
         s_ex[threadIdx.x] = ex;
         __syncthreads();
@@ -199,16 +193,16 @@ __global__ void __launch_bounds__(256) k_emit_chunks(Op op, long long n_rec, lon
         hist[(size_t)k * gridDim.x + blockIdx.x] = cnt;
         if (cnt) atomicAdd(&key_totals[k], cnt);
     }
-    // the barrier orders every thread's stores before thread 0's release fence
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        s_last = atomicAdd(&st->blocks_done, 1ull) == 2ull * gridDim.x - 1;
-    }
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    // key bases and item bases: exclusive scans over the keys (<= 1024, 4 per thread)
+}
+
+// Key bases and item bases (one 256-thread block): exclusive scans over the key
+// totals (<= 1024 keys, 4 per thread).  Each key's first entry goes to s_base
+// (shared) and/or key_first (global; may be key_totals itself: every thread reads
+// its keys' totals before the scans' barriers); with write_items, also every key's
+// range, a cleared chunk arrival counter, its first work item and its items, and
+// the item count.
+__device__ __forceinline__ void key_scan(const uint32_t* key_totals, int n_keys, const FusedKeys& fk,
+                                         bool write_items, uint32_t* s_base, uint32_t* key_first, uint32_t* sm8) {
     const int t = threadIdx.x;
     uint32_t tk[4], nc[4], sum = 0, isum = 0;
 #pragma unroll
@@ -220,42 +214,72 @@ __global__ void __launch_bounds__(256) k_emit_chunks(Op op, long long n_rec, lon
         isum += nc[q];
     }
     uint32_t tot, itot;
-    uint32_t base = block_exclusive_scan_256(sum, sm, &tot);
-    uint32_t ibase = block_exclusive_scan_256(isum, sm, &itot);
+    uint32_t base = block_exclusive_scan_256(sum, sm8, &tot);
+    uint32_t ibase = block_exclusive_scan_256(isum, sm8, &itot);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const int k = 4 * t + q;
         if (k < n_keys) {
-            key_totals[k] = base;  // the key's first entry, for the offsets pass
-            fk.ranges[k] = tk[q] ? make_uint2(base, base + tk[q]) : make_uint2(0u, 0u);
-            fk.key_done[k] = 0;
-            fk.item_off[k] = ibase;
-            for (uint32_t c = 0; c < nc[q]; ++c)
-                if (ibase + c < fk.items_cap) fk.items[ibase + c] = ((uint64_t)(uint32_t)k << 32) | c;
+            if (s_base) s_base[k] = base;
+            if (key_first) key_first[k] = base;
+            if (write_items) {
+                fk.ranges[k] = tk[q] ? make_uint2(base, base + tk[q]) : make_uint2(0u, 0u);
+                fk.key_done[k] = 0;
+                fk.item_off[k] = ibase;
+                for (uint32_t c = 0; c < nc[q]; ++c)
+                    if (ibase + c < fk.items_cap) fk.items[ibase + c] = ((uint64_t)(uint32_t)k << 32) | c;
+            }
         }
         base += tk[q];
         ibase += nc[q];
     }
-    if (t == 0) fk.item_st->n_keys = itot;
+    if (write_items && t == 0) fk.item_st->n_keys = itot;
 }
 
-// One warp per key k: the scatter offset of (k, emit block b) = the key's first
-// entry + entries of key k in earlier blocks (hist rewritten in place).
+// Each block walks its records in rounds of 256 and writes every record's entries
+// at its offset (emit_block).  HIST (fused path): the last block to finish (the
+// status block's arrival counter, which the count pass left at gridDim.x) turns
+// key_totals into each key's first entry (written back into key_totals), range,
+// first item and items.
+template <class Op, bool HIST>
+__global__ void __launch_bounds__(256) k_emit_chunks(Op op, long long n_rec, long long per_block,
+                                                     const unsigned long long* partials, uint64_t* out,
+                                                     unsigned long long capacity, uint32_t* __restrict__ hist,
+                                                     uint32_t* __restrict__ key_totals, int n_keys, WsStatus* st,
+                                                     FusedKeys fk) {
+    __shared__ uint32_t sm[8];
+    __shared__ uint32_t h[HIST ? kFusedKeys : 1];
+    __shared__ uint4 s_info[256];
+    __shared__ uint32_t s_ex[256];
+    __shared__ int s_last;
+    emit_block<Op, HIST>(op, n_rec, per_block, partials, out, capacity, hist, key_totals, n_keys, h, s_info, s_ex,
+                         sm);
+    if (!HIST) return;
+    // the barrier orders every thread's stores before thread 0's release fence
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(&st->blocks_done, 1ull) == 2ull * gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    key_scan(key_totals, n_keys, fk, true, nullptr, key_totals, sm);
+}
+
+// The scatter offsets of key k (one warp): offset of (k, emit block b) = the key's
+// first entry + entries of key k in earlier blocks (hist row rewritten in place).
 constexpr int kMaxRowChunks = (kMaxListBlocks + 31) / 32;
-static __global__ void __launch_bounds__(256) k_fused_offsets(uint32_t* __restrict__ hist,
-                                                              const uint32_t* __restrict__ key_first, int nb,
-                                                              int n_keys) {
-    const int lane = threadIdx.x & 31;
-    const int k = blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (k >= n_keys) return;
+__device__ __forceinline__ void key_offsets(uint32_t* __restrict__ hist, uint32_t key_first, int nb, int k,
+                                            int lane) {
     uint32_t* row = hist + (size_t)k * nb;
     uint32_t v[kMaxRowChunks];
 #pragma unroll
     for (int c = 0; c < kMaxRowChunks; ++c) {
         const int idx = c * 32 + lane;
-        v[c] = idx < nb ? row[idx] : 0u;
+        v[c] = idx < nb ? __ldcg(row + idx) : 0u;
     }
-    uint32_t running = key_first[k];
+    uint32_t running = key_first;
 #pragma unroll
     for (int c = 0; c < kMaxRowChunks; ++c) {
         if (c * 32 >= nb) break;
@@ -271,17 +295,25 @@ static __global__ void __launch_bounds__(256) k_fused_offsets(uint32_t* __restri
     }
 }
 
-// One block per emit block: its entries [start_b, start_{b+1}) (clipped to the
-// written count) go to their sorted positions.  Each warp takes one contiguous
-// run; per-(warp, key) counts and the block's offsets give each warp its base
-// per key; inside a warp, lanes with equal keys are ranked by lane (match mask),
-// so equal keys keep their input order.
-static __global__ void __launch_bounds__(256) k_fused_scatter(const uint64_t* __restrict__ in,
-                                                              uint64_t* __restrict__ out,
-                                                              const uint32_t* __restrict__ offs,
-                                                              const unsigned long long* __restrict__ starts,
-                                                              const WsStatus* __restrict__ st, int n_keys) {
-    __shared__ uint32_t s_h[8][kFusedKeys];
+// One warp per key k (see key_offsets).
+static __global__ void __launch_bounds__(256) k_fused_offsets(uint32_t* __restrict__ hist,
+                                                              const uint32_t* __restrict__ key_first, int nb,
+                                                              int n_keys) {
+    const int k = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (k >= n_keys) return;
+    key_offsets(hist, key_first[k], nb, k, threadIdx.x & 31);
+}
+
+// Block b's entries [start_b, start_{b+1}) (clipped to the written count) go to their
+// sorted positions.  Each warp takes one contiguous run; per-(warp, key) counts and
+// the block's offsets give each warp its base per key; inside a warp, lanes with
+// equal keys are ranked by lane (match mask), so equal keys keep their input order.
+// s_h: shared [8][kFusedKeys].
+__device__ __forceinline__ void scatter_block(const uint64_t* __restrict__ in, uint64_t* __restrict__ out,
+                                              const uint32_t* __restrict__ offs,
+                                              const unsigned long long* __restrict__ starts,
+                                              const WsStatus* __restrict__ st, int n_keys,
+                                              uint32_t (*s_h)[kFusedKeys]) {
     const int b = blockIdx.x, nb = gridDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned long long n_written = st->n_keys;
     const unsigned long long lo = min(starts[b], n_written);
@@ -306,7 +338,7 @@ static __global__ void __launch_bounds__(256) k_fused_scatter(const uint64_t* __
     }
     __syncthreads();
     for (int k = tid; k < n_keys; k += 256) {
-        uint32_t run = offs[(size_t)k * nb + b];
+        uint32_t run = __ldcg(offs + (size_t)k * nb + b);
 #pragma unroll
         for (int w = 0; w < 8; ++w) {
             const uint32_t c = s_h[w][k];
@@ -336,6 +368,101 @@ static __global__ void __launch_bounds__(256) k_fused_scatter(const uint64_t* __
             if (valid) out[pos] = x[q];
         }
     }
+}
+
+// One block per emit block (see scatter_block).
+static __global__ void __launch_bounds__(256) k_fused_scatter(const uint64_t* __restrict__ in,
+                                                              uint64_t* __restrict__ out,
+                                                              const uint32_t* __restrict__ offs,
+                                                              const unsigned long long* __restrict__ starts,
+                                                              const WsStatus* __restrict__ st, int n_keys) {
+    __shared__ uint32_t s_h[8][kFusedKeys];
+    scatter_block(in, out, offs, starts, st, n_keys, s_h);
+}
+
+// Grid barrier of a cooperative launch (all blocks resident): thread 0 of each
+// block arrives on the status block's counter and waits, with a bounded spin, until
+// `epoch` x gridDim.x blocks have arrived; a wait that gives up sets R2G_E_TIMEOUT
+// (the results are then not valid) instead of hanging.
+constexpr unsigned long long kGridSyncSpins = 1ull << 22;
+__device__ __forceinline__ void grid_barrier(WsStatus* st, unsigned int epoch) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned long long target = (unsigned long long)epoch * gridDim.x;
+        atomicAdd(&st->grid_sync, 1ull);
+        unsigned long long spins = 0;
+        while (atomicAdd(&st->grid_sync, 0ull) < target) {
+            if (++spins > kGridSyncSpins) {
+                atomicExch(&st->status, (int32_t)R2G_E_TIMEOUT);
+                break;
+            }
+            __nanosleep(64);
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+// The fused list build in one cooperative launch (grid = the emit blocks): emission
+// with per-block key counts; barrier; every block scans the key totals into the
+// keys' first entries (block 0 also writes ranges and work items) and the grid's
+// warps turn the per-key rows of counts into scatter offsets; barrier; each block
+// scatters its entries.  Equal to k_emit_chunks<Op, true> + k_fused_offsets +
+// k_fused_scatter, without their launches and the emission's last-block tail.
+template <class Op>
+__global__ void __launch_bounds__(256) k_lists_coop(Op op, long long n_rec, long long per_block,
+                                                    const unsigned long long* __restrict__ partials,
+                                                    uint64_t* __restrict__ a, uint64_t* __restrict__ b,
+                                                    unsigned long long capacity, uint32_t* __restrict__ hist,
+                                                    uint32_t* __restrict__ key_totals, int n_keys, WsStatus* st,
+                                                    FusedKeys fk) {
+    __shared__ __align__(16) uint32_t pool[8 * kFusedKeys];  // reused by the three phases
+    __shared__ uint32_t sm8[8];
+    emit_block<Op, true>(op, n_rec, per_block, partials, a, capacity, hist, key_totals, n_keys, pool,
+                         reinterpret_cast<uint4*>(pool + kFusedKeys), pool + 2 * kFusedKeys, sm8);
+    grid_barrier(st, 1);
+    uint32_t* s_base = pool;
+    key_scan(key_totals, n_keys, fk, blockIdx.x == 0, s_base, nullptr, sm8);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    for (int k = blockIdx.x * 8 + (threadIdx.x >> 5); k < n_keys; k += gridDim.x * 8)
+        key_offsets(hist, s_base[k], (int)gridDim.x, k, lane);
+    grid_barrier(st, 2);
+    scatter_block(a, b, hist, partials, st, n_keys, reinterpret_cast<uint32_t(*)[kFusedKeys]>(pool));
+}
+
+// Launches k_lists_coop if `blocks` blocks can all be resident on this device;
+// false (nothing launched) otherwise.
+template <class Op>
+bool launch_lists_coop(const Op& op, long long n_rec, long long per_block, const unsigned long long* partials,
+                       uint64_t* a, uint64_t* b, unsigned long long capacity, uint32_t* hist, uint32_t* key_totals,
+                       int n_keys, WsStatus* st, const FusedKeys& fk, int blocks, cudaStream_t s) {
+    static int resident[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
+    if (resident[dev] == 0) {
+        int per_sm = 0, sms = 0, coop = 0;
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lists_coop<Op>, 256, 0) != cudaSuccess)
+            per_sm = 0;
+        resident[dev] = coop ? per_sm * sms : 0;
+        if (resident[dev] <= 0) resident[dev] = -1;
+    }
+    if (blocks > resident[dev]) return false;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)blocks);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_lists_coop<Op>, op, n_rec, per_block, partials, a, b, capacity, hist,
+                              key_totals, n_keys, st, fk) == cudaSuccess;
 }
 
 // Whether a key space takes the fused path, and where the sorted lists end up.
@@ -374,6 +501,11 @@ uint64_t* build_lists(const Op& op, long long n_rec, long long n_slots, unsigned
         const FusedKeys fk{(uint32_t)chunk, ranges, key_done, item_off, items, (unsigned long long)items_cap,
                            item_st};
         prof_begin(prof.emit, s);
+        if (launch_lists_coop(op, n_rec, per_block, partials, a, b, ucap, hist, totals, nk, st, fk, lb.blocks, s)) {
+            prof_end(prof.emit, s);
+            *launches += 1;
+            return b;
+        }
         k_emit_chunks<Op, true><<<lb.blocks, 256, 0, s>>>(op, n_rec, per_block, partials, a, ucap, hist, totals, nk,
                                                           st, fk);
         prof_end(prof.emit, s);

@@ -9,6 +9,8 @@
 // each orientation's value is the mean over its slices, and the 3D SSIM the mean
 // of the three.  PSNR = 10 log10(1 / MSE).
 //
+//   k_transpose_zyx  copies of both volumes in [x][z][y] order, so that sagittal
+//                 slices are read like the others (rows contiguous);
 //   k_slice_ssim  one CTA per 32 x 32 output tile of one slice of one orientation:
 //                 both volumes' tiles staged with a 5-voxel halo (zeros outside
 //                 the slice), the window applied separably to a, b, a^2, b^2, ab,
@@ -46,7 +48,9 @@ struct Orients {
 };
 
 __global__ void __launch_bounds__(kMetThreads) k_slice_ssim(const float* __restrict__ a, const float* __restrict__ b,
-                                                            Orients os, MWin win, double* __restrict__ partials) {
+                                                            const float* __restrict__ ta,
+                                                            const float* __restrict__ tb, Orients os, MWin win,
+                                                            double* __restrict__ partials) {
     __shared__ float sa[kMS][kMS + 1], sb[kMS][kMS + 1];
     __shared__ float h[5][kMS][kMT + 1];
     __shared__ double red[kMetThreads / 32];
@@ -57,8 +61,8 @@ __global__ void __launch_bounds__(kMetThreads) k_slice_ssim(const float* __restr
     const int s = (int)(local / o.tiles);
     const int tile = (int)(local - (long long)s * o.tiles);
     const int r0 = (tile / o.tiles_x) * kMT, c0 = (tile % o.tiles_x) * kMT;
-    const float* pa = a + (long long)s * o.ss;
-    const float* pb = b + (long long)s * o.ss;
+    const float* pa = (oi == 2 ? ta : a) + (long long)s * o.ss;
+    const float* pb = (oi == 2 ? tb : b) + (long long)s * o.ss;
     const int tid = threadIdx.x;
     for (int i = tid; i < kMS * kMS; i += kMetThreads) {
         const int r = i / kMS, c = i - r * kMS;
@@ -121,6 +125,35 @@ __global__ void __launch_bounds__(kMetThreads) k_slice_ssim(const float* __restr
         double t = 0.0;
         for (int w = 0; w < kMetThreads / 32; ++w) t += red[w];
         partials[cta] = t;
+    }
+}
+
+// T[x][z][y] = A[z][y][x] for both volumes (so that sagittal slices x = const are
+// contiguous images with rows z and columns y); 32 x 32 (y, x) tiles through shared
+// memory, reads and writes coalesced.
+__global__ void __launch_bounds__(256) k_transpose_zyx(const float* __restrict__ a, const float* __restrict__ b,
+                                                       int X, int Y, int Z, float* __restrict__ ta,
+                                                       float* __restrict__ tb) {
+    __shared__ float sa[32][33], sb[32][33];
+    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32, z = blockIdx.z;
+    const long long plane = (long long)z * Y * X;
+#pragma unroll
+    for (int k = 0; k < 32; k += 8) {
+        const int y = y0 + threadIdx.y + k, x = x0 + threadIdx.x;
+        if (y < Y && x < X) {
+            sa[threadIdx.y + k][threadIdx.x] = a[plane + (long long)y * X + x];
+            sb[threadIdx.y + k][threadIdx.x] = b[plane + (long long)y * X + x];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 32; k += 8) {
+        const int x = x0 + threadIdx.y + k, y = y0 + threadIdx.x;
+        if (y < Y && x < X) {
+            const long long o = ((long long)x * Z + z) * Y + y;
+            ta[o] = sa[threadIdx.x][threadIdx.y + k];
+            tb[o] = sb[threadIdx.x][threadIdx.y + k];
+        }
     }
 }
 
@@ -191,7 +224,8 @@ Orients orients(int X, int Y, int Z) {
     Orients os;
     os.o[0] = Orient{XY, X, 1, Z, Y, X, 0, 0, 0};   // axial: z = const, rows y, columns x
     os.o[1] = Orient{X, XY, 1, Y, Z, X, 0, 0, 0};   // coronal: y = const, rows z, columns x
-    os.o[2] = Orient{1, XY, X, X, Z, Y, 0, 0, 0};   // sagittal: x = const, rows z, columns y
+    // sagittal: x = const, rows z, columns y -- read from the transposed copies [x][z][y]
+    os.o[2] = Orient{(long long)Z * Y, Y, 1, X, Z, Y, 0, 0, 0};
     long long first = 0;
     for (int q = 0; q < 3; ++q) {
         Orient& o = os.o[q];
@@ -229,6 +263,8 @@ R2G_API size_t r2g_metrics_workspace_size(int32_t X, int32_t Y, int32_t Z) {
     Layout L;
     L.take(sizeof(double) * (size_t)total_tiles(orients(X, Y, Z)));
     L.take(sizeof(double) * kSqBlocks);
+    L.take(sizeof(float) * (size_t)X * Y * Z);
+    L.take(sizeof(float) * (size_t)X * Y * Z);
     return L.off;
 }
 
@@ -242,6 +278,8 @@ R2G_API r2g_status r2g_volume_metrics(int32_t X, int32_t Y, int32_t Z, const flo
     Layout L;
     const size_t o_tiles = L.take(sizeof(double) * (size_t)nt);
     const size_t o_sq = L.take(sizeof(double) * kSqBlocks);
+    const size_t o_ta = L.take(sizeof(float) * (size_t)X * Y * Z);
+    const size_t o_tb = L.take(sizeof(float) * (size_t)X * Y * Z);
     if (ws_bytes < L.off) return fail(R2G_E_INVAL, "metrics workspace needs %zu bytes", L.off);
     if (nt >= (1ll << 31)) return fail(R2G_E_INVAL, "volume too large");
     char* base = static_cast<char*>(ws);
@@ -249,10 +287,14 @@ R2G_API r2g_status r2g_volume_metrics(int32_t X, int32_t Y, int32_t Z, const flo
     double* sq = reinterpret_cast<double*>(base + o_sq);
     const long long n = (long long)X * Y * Z;
     prof_begin(P_METRICS, stream);
-    k_slice_ssim<<<(unsigned)nt, kMetThreads, 0, stream>>>(vol, ref, os, metric_window(), tp);
+    float* ta = reinterpret_cast<float*>(base + o_ta);
+    float* tb = reinterpret_cast<float*>(base + o_tb);
+    k_transpose_zyx<<<dim3((unsigned)((X + 31) / 32), (unsigned)((Y + 31) / 32), (unsigned)Z), dim3(32, 8), 0,
+                      stream>>>(vol, ref, X, Y, Z, ta, tb);
+    k_slice_ssim<<<(unsigned)nt, kMetThreads, 0, stream>>>(vol, ref, ta, tb, os, metric_window(), tp);
     k_sq_err<<<kSqBlocks, 256, 0, stream>>>(vol, ref, n, sq);
     k_metrics_fin<<<1, 256, 0, stream>>>(tp, os, sq, n, out);
     prof_end(P_METRICS, stream);
-    note_launches(3);
+    note_launches(4);
     return check_launch("r2g_volume_metrics");
 }

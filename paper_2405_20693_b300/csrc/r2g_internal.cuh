@@ -47,7 +47,8 @@ struct WsStatus {
     unsigned long long n_keys;  // entries actually emitted = min(needed, capacity)
     unsigned long long pairs;   // gated pairs (counting runs only)
     unsigned long long blocks_done;  // arrival counter of the entry count pass
-    unsigned long long reserved[27];
+    unsigned long long grid_sync;    // arrivals at the cooperative list build's grid barriers
+    unsigned long long reserved[26];
 };
 static_assert(sizeof(WsStatus) == 256, "status block is 256 bytes");
 
