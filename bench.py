@@ -686,52 +686,56 @@ def run_ours(args, rank, world, local_rank):
 
     # end to end through the public API: every step's inputs -- its measured view
     # (H x W floats), the view's geometry row and its round entry -- go host -> device
-    # from pinned memory into one of two staging slots on a copy stream, the fused
-    # step (a C job whose view table and measurements are the two slots) runs on the
-    # compute stream once its slot has arrived, and its loss comes back to pinned host
-    # memory; the copy of step k + 1 overlaps step k, and the host reads step k's
-    # loss after queueing step k + 1
+    # from pinned memory into one of NS staging slots on a copy stream, the fused step
+    # (a C job whose view table and measurements are the slots) runs on the compute
+    # stream once its slot has arrived, and its loss comes back to pinned host memory;
+    # copies overlap the steps before them, and the host reads step k's loss after
+    # queueing step k + NS - 1
+    NS = 3
     H, W = cam.H, cam.W
     meas_host = torch.from_numpy(np.ascontiguousarray(meas_np, np.float32)).pin_memory()
     views_host = torch.from_numpy(np.ascontiguousarray(views_np, np.float32)).pin_memory()
     ent_host = torch.from_numpy(tab.copy()).pin_memory()
-    meas_stage = torch.empty((2, H, W), dtype=torch.float32, device=dev)
-    views_stage = torch.empty((2, 12), dtype=torch.float32, device=dev)
-    ent_stage = torch.empty((2, 8), dtype=torch.int32, device=dev)
+    meas_stage = torch.empty((NS, H, W), dtype=torch.float32, device=dev)
+    views_stage = torch.empty((NS, 12), dtype=torch.float32, device=dev)
+    ent_stage = torch.empty((NS, 8), dtype=torch.int32, device=dev)
     job2 = r2g.Job.from_buffer_copy(sc.job)
-    job2.V, job2.views, job2.meas = 2, views_stage.data_ptr(), meas_stage.data_ptr()
+    job2.V, job2.views, job2.meas = NS, views_stage.data_ptr(), meas_stage.data_ptr()
     copy_stream = torch.cuda.Stream(device=dev)
-    ev_in = [torch.cuda.Event(), torch.cuda.Event()]
-    ev_done = [torch.cuda.Event(), torch.cuda.Event()]
-    loss_host = [torch.empty(2, dtype=torch.float32).pin_memory() for _ in range(2)]
-    loss_sum = 0.0
+    ev_in = [torch.cuda.Event() for _ in range(NS)]
+    ev_done = [torch.cuda.Event() for _ in range(NS)]
+    loss_host = [torch.empty(2, dtype=torch.float32).pin_memory() for _ in range(NS)]
+    loss_sum, n_read = 0.0, 0
     for k in range(t0_steps, t0_steps + args.steps):
-        ent_host[k, 0] = (k - t0_steps) % 2       # the step's view is its staging slot
+        ent_host[k, 0] = (k - t0_steps) % NS      # the step's view is its staging slot
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     t0 = time.perf_counter()
     for j in range(args.steps):
         k = t0_steps + j
-        v, slot = seq[k][0], j % 2
+        v, slot = seq[k][0], j % NS
+        if j >= NS:                                # step j - NS: done, loss read below already
+            ev_done[slot].synchronize()
         with torch.cuda.stream(copy_stream):
-            if j >= 2:
-                copy_stream.wait_event(ev_done[slot])  # step j - 2 has finished with this slot
             meas_stage[slot].copy_(meas_host[v], non_blocking=True)
             views_stage[slot].copy_(views_host[v], non_blocking=True)
             ent_stage[slot].copy_(ent_host[k], non_blocking=True)
             ev_in[slot].record(copy_stream)
         stream.wait_event(ev_in[slot])
         r2g.r2g_train_step(job2, ent_stage[slot].data_ptr(), stream)
-        if j >= 2:
-            ev_done[slot].synchronize()            # step j - 2's loss was read already
         loss_host[slot].copy_(sc.loss, non_blocking=True)
         ev_done[slot].record(stream)
-        if j >= 1:
-            ev_done[(j - 1) % 2].synchronize()
-            loss_sum += float(loss_host[(j - 1) % 2][0])
-    ev_done[(args.steps - 1) % 2].synchronize()
-    loss_sum += float(loss_host[(args.steps - 1) % 2][0])
+        if j >= NS - 1:
+            r = j - (NS - 1)
+            ev_done[r % NS].synchronize()
+            loss_sum += float(loss_host[r % NS][0])
+            n_read += 1
+    for r in range(max(0, args.steps - (NS - 1)), args.steps):
+        ev_done[r % NS].synchronize()
+        loss_sum += float(loss_host[r % NS][0])
+        n_read += 1
+    assert n_read == args.steps
     e2e_s = time.perf_counter() - t0
     assert np.isfinite(loss_sum)
     if dist:
@@ -795,8 +799,8 @@ def run_ours(args, rank, world, local_rank):
             "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": 4 * cam.H * cam.W + 48 + 32,
                     "d2h_bytes_per_step": 8,
                     "note": "per step: the measured view, its geometry row and its round entry copied from pinned "
-                            "host memory into one of two device slots on a copy stream (overlapping the previous "
-                            "step), the fused step through r2g_train_step, the loss read back to the host"},
+                            "host memory into one of three device slots on a copy stream (overlapping the steps "
+                            "before it), the fused step through r2g_train_step, the loss read back to the host"},
             "gpu_launches": int(launches),
             "roofline": roof,
             "kernels_ms_per_step": breakdown,

@@ -62,3 +62,38 @@ def test_host_side_argument_errors(lib):
     assert lib.r2g_tv_workspace_size(1, 1) == 0
     st = lib.r2g_tv3d(1, 1, None, 0.05, None, None, None, 0, None)
     assert st == r2g.R2G_E_INVAL
+
+
+def test_host_side_argument_errors_of_the_other_entry_points(lib):
+    """FDK initialisation, volume metrics, adaptive control and the mean-mu query
+    reject bad arguments on the host (R2G_E_INVAL, or a zero workspace size)."""
+    cam = r2g.Camera(1, 64, 64, 11.7, 0.05, 0.05, 0.0, 0.0, 0.078)
+    fake = ctypes.c_void_p(0x1000)  # never dereferenced: every call below fails its host checks
+    assert lib.r2g_fdk_filter(0, ctypes.byref(cam), fake, fake, None) == r2g.R2G_E_INVAL
+    assert lib.r2g_fdk_filter(1, ctypes.byref(cam), None, fake, None) == r2g.R2G_E_INVAL
+    assert lib.r2g_fdk_filter(1, ctypes.byref(cam), fake, fake, None) == r2g.R2G_E_INVAL  # aliased
+    wide = r2g.Camera(1, 4, 9000, 11.7, 0.05, 0.05, 0.0, 0.0, 0.078)
+    assert lib.r2g_fdk_filter(1, ctypes.byref(wide), fake, ctypes.c_void_p(0x2000), None) == r2g.R2G_E_INVAL
+    bad = r2g.grids([[-1, -1, -1, 0.1, 0.1, 0.1, 0, 20, 20]])[0]
+    good = r2g.grids([[-1, -1, -1, 0.1, 0.1, 0.1, 20, 20, 20]])[0]
+    assert lib.r2g_fdk_backproject(1, fake, ctypes.byref(cam), fake, ctypes.byref(bad), 0.1, fake, None) == \
+        r2g.R2G_E_INVAL
+    assert lib.r2g_init_workspace_size(ctypes.byref(bad), 10) == 0
+    assert lib.r2g_init_workspace_size(ctypes.byref(good), 0) == 0
+    ws_n = lib.r2g_init_workspace_size(ctypes.byref(good), 10)
+    assert ws_n > 0
+    assert lib.r2g_init_gaussians(fake, ctypes.byref(good), 0.05, 10, 1, 0.15, fake, fake, fake, fake, fake, fake,
+                                  ws_n - 1, None) == r2g.R2G_E_INVAL
+    assert lib.r2g_init_gaussians(fake, ctypes.byref(good), 0.05, 10, 1, 0.15, fake, fake, ctypes.c_void_p(0x1004),
+                                  fake, fake, fake, ws_n, None) == r2g.R2G_E_INVAL  # quat not 16-byte aligned
+    assert lib.r2g_metrics_workspace_size(0, 4, 4) == 0
+    assert lib.r2g_volume_metrics(4, 4, 5000, fake, fake, fake, fake, 1 << 20, None) == r2g.R2G_E_INVAL
+    opts = r2g.densify_opts()
+    assert lib.r2g_densify(100, fake, fake, fake, fake, fake, fake, ctypes.byref(opts), 99, fake, fake, fake, fake,
+                           fake, fake, 4096, None) == r2g.R2G_E_INVAL  # max_gaussians < M
+    assert lib.r2g_densify(100, fake, fake, fake, fake, fake, None, ctypes.byref(opts), 200, fake, fake, fake, fake,
+                           fake, fake, 4096, None) == r2g.R2G_E_INVAL
+    assert lib.r2g_densify(100, fake, fake, fake, fake, fake, fake, ctypes.byref(opts), 200, fake, fake, fake, fake,
+                           fake, fake, 0, None) == r2g.R2G_E_INVAL  # workspace too small
+    assert lib.r2g_mean_mu(10, fake, fake, fake, None, 1, fake, ctypes.byref(cam), None, None, None) == \
+        r2g.R2G_E_INVAL
