@@ -143,7 +143,7 @@ struct FusedKeys {
 // uint4 [256], s_ex: shared [256], sm8: shared [8].
 template <class Op, bool HIST>
 __device__ __forceinline__ void emit_block(const Op& op, long long n_rec, long long per_block,
-                                           const unsigned long long* partials, uint64_t* out,
+                                           unsigned long long running, uint64_t* out,
                                            unsigned long long capacity, uint32_t* __restrict__ hist,
                                            uint32_t* __restrict__ key_totals, int n_keys, uint32_t* h, uint4* s_info,
                                            uint32_t* s_ex, uint32_t* sm8) {
@@ -153,7 +153,6 @@ __device__ __forceinline__ void emit_block(const Op& op, long long n_rec, long l
     }
     const long long begin = min(n_rec, (long long)blockIdx.x * per_block);
     const long long end = min(n_rec, begin + per_block);
-    unsigned long long running = partials[blockIdx.x];
     for (long long base = begin; base < end; base += 256) {
         const long long r = base + threadIdx.x;
         uint32_t c = 0;
@@ -252,8 +251,8 @@ __global__ void __launch_bounds__(256) k_emit_chunks(Op op, long long n_rec, lon
     __shared__ uint4 s_info[256];
     __shared__ uint32_t s_ex[256];
     __shared__ int s_last;
-    emit_block<Op, HIST>(op, n_rec, per_block, partials, out, capacity, hist, key_totals, n_keys, h, s_info, s_ex,
-                         sm);
+    emit_block<Op, HIST>(op, n_rec, per_block, partials[blockIdx.x], out, capacity, hist, key_totals, n_keys, h,
+                         s_info, s_ex, sm);
     if (!HIST) return;
     // the barrier orders every thread's stores before thread 0's release fence
     __syncthreads();
@@ -310,14 +309,9 @@ static __global__ void __launch_bounds__(256) k_fused_offsets(uint32_t* __restri
 // equal keys are ranked by lane (match mask), so equal keys keep their input order.
 // s_h: shared [8][kFusedKeys].
 __device__ __forceinline__ void scatter_block(const uint64_t* __restrict__ in, uint64_t* __restrict__ out,
-                                              const uint32_t* __restrict__ offs,
-                                              const unsigned long long* __restrict__ starts,
-                                              const WsStatus* __restrict__ st, int n_keys,
-                                              uint32_t (*s_h)[kFusedKeys]) {
+                                              const uint32_t* __restrict__ offs, unsigned long long lo,
+                                              unsigned long long hi, int n_keys, uint32_t (*s_h)[kFusedKeys]) {
     const int b = blockIdx.x, nb = gridDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const unsigned long long n_written = st->n_keys;
-    const unsigned long long lo = min(starts[b], n_written);
-    const unsigned long long hi = (b + 1 < nb) ? min(starts[b + 1], n_written) : n_written;
     const unsigned long long per = (hi - lo + 7) / 8;
     const unsigned long long wlo = min(hi, lo + warp * per), whi = min(hi, wlo + per);
     for (int k = tid; k < n_keys; k += 256)
@@ -377,7 +371,11 @@ static __global__ void __launch_bounds__(256) k_fused_scatter(const uint64_t* __
                                                               const unsigned long long* __restrict__ starts,
                                                               const WsStatus* __restrict__ st, int n_keys) {
     __shared__ uint32_t s_h[8][kFusedKeys];
-    scatter_block(in, out, offs, starts, st, n_keys, s_h);
+    const int b = blockIdx.x;
+    const unsigned long long n_written = st->n_keys;
+    const unsigned long long lo = min(starts[b], n_written);
+    const unsigned long long hi = (b + 1 < (int)gridDim.x) ? min(starts[b + 1], n_written) : n_written;
+    scatter_block(in, out, offs, lo, hi, n_keys, s_h);
 }
 
 // Grid barrier of a cooperative launch (all blocks resident): thread 0 of each
@@ -419,7 +417,7 @@ __global__ void __launch_bounds__(256) k_lists_coop(Op op, long long n_rec, long
                                                     FusedKeys fk) {
     __shared__ __align__(16) uint32_t pool[8 * kFusedKeys];  // reused by the three phases
     __shared__ uint32_t sm8[8];
-    emit_block<Op, true>(op, n_rec, per_block, partials, a, capacity, hist, key_totals, n_keys, pool,
+    emit_block<Op, true>(op, n_rec, per_block, partials[blockIdx.x], a, capacity, hist, key_totals, n_keys, pool,
                          reinterpret_cast<uint4*>(pool + kFusedKeys), pool + 2 * kFusedKeys, sm8);
     grid_barrier(st, 1);
     uint32_t* s_base = pool;
@@ -429,7 +427,81 @@ __global__ void __launch_bounds__(256) k_lists_coop(Op op, long long n_rec, long
     for (int k = blockIdx.x * 8 + (threadIdx.x >> 5); k < n_keys; k += gridDim.x * 8)
         key_offsets(hist, s_base[k], (int)gridDim.x, k, lane);
     grid_barrier(st, 2);
-    scatter_block(a, b, hist, partials, st, n_keys, reinterpret_cast<uint32_t(*)[kFusedKeys]>(pool));
+    const unsigned long long n_written = st->n_keys;
+    const unsigned long long lo = min(partials[blockIdx.x], n_written);
+    const unsigned long long hi =
+        (blockIdx.x + 1 < gridDim.x) ? min(partials[blockIdx.x + 1], n_written) : n_written;
+    scatter_block(a, b, hist, lo, hi, n_keys, reinterpret_cast<uint32_t(*)[kFusedKeys]>(pool));
+}
+
+// The projection and the fused list build in one cooperative launch: each block
+// projects its records (proj(r): writes record r, returns its entry count; 0 past
+// n_rec) and counts their entries; barrier; every block forms its exclusive entry
+// offset and the total from the block counts (block 0 writes the total and the
+// capacity verdict into the status block), then emits; barrier; key scan and
+// offsets; barrier; scatter.  counts: [gridDim.x] block entry counts (written).
+template <class Proj, class Op>
+__global__ void __launch_bounds__(256) k_plists_coop(Proj proj, Op op, long long n_rec, int per_thread,
+                                                     unsigned long long* __restrict__ counts,
+                                                     uint64_t* __restrict__ a, uint64_t* __restrict__ b,
+                                                     unsigned long long capacity, uint32_t* __restrict__ hist,
+                                                     uint32_t* __restrict__ key_totals, int n_keys, WsStatus* st,
+                                                     FusedKeys fk) {
+    __shared__ __align__(16) uint32_t pool[8 * kFusedKeys];  // reused by the phases
+    __shared__ uint32_t sm8[8];
+    __shared__ unsigned long long smu[8];
+    unsigned long long cnt = 0;
+    for (int l = 0; l < per_thread; ++l) cnt += proj(((long long)blockIdx.x * per_thread + l) * 256 + threadIdx.x);
+    const unsigned long long mine = block_sum_u64_256(cnt, smu);
+    if (threadIdx.x == 0) counts[blockIdx.x] = mine;
+    if (blockIdx.x == 0)
+        for (int k = threadIdx.x; k < n_keys; k += 256) key_totals[k] = 0;
+    grid_barrier(st, 1);
+    unsigned long long before = 0, total = 0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += 256) {
+        const unsigned long long c = __ldcg(counts + i);
+        total += c;
+        before += i < (int)blockIdx.x ? c : 0ull;
+    }
+    before = block_sum_u64_256(before, smu);
+    total = block_sum_u64_256(total, smu);
+    const unsigned long long written = total < capacity ? total : capacity;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->needed = total;
+        st->n_keys = written;
+        if (total > capacity) atomicExch(&st->status, (int32_t)R2G_E_CAPACITY);
+    }
+    const long long per_block = 256ll * per_thread;
+    emit_block<Op, true>(op, n_rec, per_block, before, a, capacity, hist, key_totals, n_keys, pool,
+                         reinterpret_cast<uint4*>(pool + kFusedKeys), pool + 2 * kFusedKeys, sm8);
+    grid_barrier(st, 2);
+    uint32_t* s_base = pool;
+    key_scan(key_totals, n_keys, fk, blockIdx.x == 0, s_base, nullptr, sm8);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    for (int k = blockIdx.x * 8 + (threadIdx.x >> 5); k < n_keys; k += gridDim.x * 8)
+        key_offsets(hist, s_base[k], (int)gridDim.x, k, lane);
+    grid_barrier(st, 3);
+    const unsigned long long lo = before < written ? before : written;
+    const unsigned long long hi = before + mine < written ? before + mine : written;
+    scatter_block(a, b, hist, lo, hi, n_keys, reinterpret_cast<uint32_t(*)[kFusedKeys]>(pool));
+}
+
+// Largest co-resident grid of a kernel of 256-thread blocks on this device (0: no
+// cooperative launch); computed once per kernel and device.
+template <class K>
+int coop_resident(K kern) {
+    static int resident[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    if (resident[dev] == 0) {
+        int per_sm = 0, sms = 0, coop = 0;
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0) != cudaSuccess) per_sm = 0;
+        resident[dev] = coop && per_sm > 0 ? per_sm * sms : -1;
+    }
+    return resident[dev] > 0 ? resident[dev] : 0;
 }
 
 // Launches k_lists_coop if `blocks` blocks can all be resident on this device;
@@ -438,19 +510,7 @@ template <class Op>
 bool launch_lists_coop(const Op& op, long long n_rec, long long per_block, const unsigned long long* partials,
                        uint64_t* a, uint64_t* b, unsigned long long capacity, uint32_t* hist, uint32_t* key_totals,
                        int n_keys, WsStatus* st, const FusedKeys& fk, int blocks, cudaStream_t s) {
-    static int resident[64] = {0};
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
-    if (resident[dev] == 0) {
-        int per_sm = 0, sms = 0, coop = 0;
-        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lists_coop<Op>, 256, 0) != cudaSuccess)
-            per_sm = 0;
-        resident[dev] = coop ? per_sm * sms : 0;
-        if (resident[dev] <= 0) resident[dev] = -1;
-    }
-    if (blocks > resident[dev]) return false;
+    if (blocks > coop_resident(k_lists_coop<Op>)) return false;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)blocks);
     cfg.blockDim = dim3(256);
@@ -469,6 +529,39 @@ bool launch_lists_coop(const Op& op, long long n_rec, long long per_block, const
 inline bool fused_lists(long long n_slots) { return n_slots <= kFusedKeys; }
 inline int list_sort_passes(long long n_slots) {
     return fused_lists(n_slots) ? 1 : (bits_for(n_slots) + kRadixBits - 1) / kRadixBits;
+}
+
+// Projection + fused list build in one cooperative launch, with as many records per
+// thread as it takes for the grid to be co-resident (at most kMaxListBlocks blocks).
+// False (nothing launched) if the key space is not fused or the grid cannot be
+// resident; the caller then launches the projection and build_lists.
+template <class Proj, class Op>
+bool launch_plists_coop(const Proj& proj, const Op& op, long long n_rec, long long n_slots,
+                        unsigned long long* counts, uint64_t* a, uint64_t* b, long long cap, uint32_t* scratch,
+                        WsStatus* st, uint2* ranges, uint32_t* key_done, WsStatus* item_st, uint32_t* item_off,
+                        uint64_t* items, long long items_cap, int chunk, cudaStream_t s) {
+    if (!fused_lists(n_slots)) return false;
+    const int res = coop_resident(k_plists_coop<Proj, Op>);
+    const int max_blocks = res < kMaxListBlocks ? res : kMaxListBlocks;
+    if (max_blocks <= 0) return false;
+    const long long per_thread = (n_rec + 256ll * max_blocks - 1) / (256ll * max_blocks);
+    const int per = per_thread < 1 ? 1 : (int)per_thread;
+    const int blocks = (int)((n_rec + 256ll * per - 1) / (256ll * per));
+    if (blocks < 1 || blocks > max_blocks) return false;
+    uint32_t* hist = scratch;
+    uint32_t* totals = scratch + (size_t)kRadix * kSortBlocksMax;
+    const FusedKeys fk{(uint32_t)chunk, ranges, key_done, item_off, items, (unsigned long long)items_cap, item_st};
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)blocks);
+    cfg.blockDim = dim3(256);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_plists_coop<Proj, Op>, proj, op, n_rec, per, counts, a, b,
+                              (unsigned long long)cap, hist, totals, (int)n_slots, st, fk) == cudaSuccess;
 }
 
 // The count the projection kernel of a list build must make (see list_count_tail).

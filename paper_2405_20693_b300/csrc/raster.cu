@@ -307,6 +307,27 @@ __global__ void __launch_bounds__(256) k_project(Params G, const float* __restri
     if (lc.partials) list_count_tail(lc, cnt);
 }
 
+// Record r's projection for the cooperative list build (0 entries past n_rec).
+struct TileProj {
+    Params G;
+    const float* views;
+    const int* view_sel;
+    CamF cam;
+    float Q;
+    int TW, TH;
+    long long M, n_rec;
+    float4* rec;
+    uint2* rect;
+    float4* mom_clear;
+
+    __device__ __forceinline__ uint32_t operator()(long long r) const {
+        if (r >= n_rec) return 0u;
+        mom_clear[2 * r] = make_float4(0.f, 0.f, 0.f, 0.f);
+        mom_clear[2 * r + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        return project_one(G, views, view_sel, cam, Q, TW, TH, M, r, rec, rect, nullptr, nullptr);
+    }
+};
+
 // ------------------------------------------------------------------ K2: tile keys
 
 struct TileOp {
@@ -1101,18 +1122,30 @@ r2g_status r2g::rasterize_impl(int64_t M, const float* mean, const float* scale,
     if (!fused_lists(L.n_tiles)) cudaMemsetAsync(image, 0, sizeof(float) * (size_t)V * cam->H * cam->W, stream);
     Params G{mean, scale, quat, rho};
     const CamF cf = camf(cam, opts);
-    prof_begin(P_PROJECT, stream);
-    const ListBlocking lb = list_blocking(L.n_rec);
-    k_project<<<(unsigned)lb.blocks, 256, 0, stream>>>(G, views, view_sel, cf, opts->Q, opts->tile_w, opts->tile_h, M,
-                                                        L.n_rec, lb.per_thread, rec, rect, nullptr, nullptr,
-                                                        reinterpret_cast<float4*>(base + L.mom),
-                                                        list_count(L.n_tiles, partials, st, cap, scratch));
-    prof_end(P_PROJECT, stream);
+    float4* mom = reinterpret_cast<float4*>(base + L.mom);
     TileOp op{rect, M, L.tiles_x, L.tiles_per_view};
     int launches = 0;
-    uint64_t* sorted = build_lists(op, L.n_rec, L.n_tiles, partials, st, a, b, scratch, cap, ranges, key_done,
-                                   item_st, item_off, items, T.icap, kChunk, ListProf{P_EMIT, P_SORT, P_RANGES},
-                                   stream, &launches);
+    uint64_t* sorted = nullptr;
+    // fused key spaces: projection and lists in one cooperative launch when the grid fits
+    const TileProj tp{G, views, view_sel, cf, opts->Q, opts->tile_w, opts->tile_h, M, L.n_rec, rec, rect, mom};
+    prof_begin(P_PROJECT, stream);
+    if (launch_plists_coop(tp, op, L.n_rec, L.n_tiles, partials, a, b, cap, scratch, st, ranges, key_done, item_st,
+                           item_off, items, T.icap, kChunk, stream)) {
+        prof_end(P_PROJECT, stream);
+        sorted = b;
+        launches = 1;
+    } else {
+        const ListBlocking lb = list_blocking(L.n_rec);
+        k_project<<<(unsigned)lb.blocks, 256, 0, stream>>>(G, views, view_sel, cf, opts->Q, opts->tile_w,
+                                                            opts->tile_h, M, L.n_rec, lb.per_thread, rec, rect,
+                                                            nullptr, nullptr, mom,
+                                                            list_count(L.n_tiles, partials, st, cap, scratch));
+        prof_end(P_PROJECT, stream);
+        sorted = build_lists(op, L.n_rec, L.n_tiles, partials, st, a, b, scratch, cap, ranges, key_done, item_st,
+                             item_off, items, T.icap, kChunk, ListProf{P_EMIT, P_SORT, P_RANGES}, stream,
+                             &launches);
+        launches += 1;
+    }
     const float Tq = -0.5f * kLog2e * opts->Q;
     prof_begin(P_SPLAT_FWD, stream);
     const FwdArgs fa{rec, ranges, sorted, items, item_st, partial, item_off, key_done};
@@ -1121,7 +1154,7 @@ r2g_status r2g::rasterize_impl(int64_t M, const float* mean, const float* scale,
     else
         launch_fwd<false>(opts->tile_w, opts->tile_h, fa, M, L, T.icap, cam->H, cam->W, Tq, image, st, stream);
     prof_end(P_SPLAT_FWD, stream);
-    note_launches(1 + launches + 1);
+    note_launches(launches + 1);
     return check_launch("r2g_rasterize");
 }
 
