@@ -118,4 +118,49 @@ __device__ __forceinline__ void adam_gaussian(const AdamState& st, long long i, 
     adam_param(st, lr, bc1, bc2, 3, 10 * M + i, grho);
 }
 
+// The Adam state of one Gaussian's eleven parameters, loaded ahead of the
+// arithmetic that produces its gradient (so the loads' latency overlaps it), in
+// the order quat (4), mean (3), scale (3), rho.
+struct AdamPre {
+    float raw[11], m[11], v[11], g[11];
+};
+
+__device__ __forceinline__ long long adam_index(long long M, long long i, int e) {
+    return e < 4 ? 4 * i + e : (e < 7 ? 4 * M + 3 * i + (e - 4) : (e < 10 ? 7 * M + 3 * i + (e - 7) : 10 * M + i));
+}
+
+__device__ __forceinline__ void adam_prefetch(const AdamState& st, long long i, AdamPre& p) {
+    const long long M = st.a.M;
+#pragma unroll
+    for (int e = 0; e < 11; ++e) {
+        const long long x = adam_index(M, i, e);
+        p.raw[e] = st.raw[x];
+        p.m[e] = st.m[x];
+        p.v[e] = st.v[x];
+        p.g[e] = st.grad[x];
+    }
+}
+
+// adam_gaussian with the state prefetched; act: the activated values (the
+// Gaussian's parameters as the kernel loaded them), same order.
+__device__ __forceinline__ void adam_gaussian_pre(const AdamState& st, long long i, const AdamPre& p,
+                                                  const float act[11], const float gq[4], const float gp[3],
+                                                  const float gs[3], float grho) {
+    const long long M = st.a.M;
+    float lr[4], bc1, bc2;
+    adam_schedule(st.a, lr, bc1, bc2);
+    const float own[11] = {gq[0], gq[1], gq[2], gq[3], gp[0], gp[1], gp[2], gs[0], gs[1], gs[2], grho};
+#pragma unroll
+    for (int e = 0; e < 11; ++e) {
+        const int grp = e < 4 ? 2 : (e < 7 ? 0 : (e < 10 ? 1 : 3));
+        float mk = p.m[e], vk = p.v[e], rn, out;
+        adam_elem(st.a, grp, lr[grp], bc1, bc2, p.raw[e], p.g[e] + own[e], act[e], mk, vk, rn, out);
+        const long long x = adam_index(M, i, e);
+        st.m[x] = mk;
+        st.v[x] = vk;
+        st.raw[x] = rn;
+        st.act[x] = out;
+    }
+}
+
 }  // namespace r2g

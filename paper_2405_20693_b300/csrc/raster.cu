@@ -711,6 +711,8 @@ __global__ void __launch_bounds__(128) k_project_bwd(Params G, const float* __re
     float p[3], s[3], q[4];
     load_gaussian(G, i, p, s, q);
     const float rho = G.rho[i];
+    AdamPre pre;
+    if (ADAM) adam_prefetch(adam, i, pre);
     float gp[3] = {0.f, 0.f, 0.f}, gs[3] = {0.f, 0.f, 0.f}, gR[3][3] = {{0.f}}, grho = 0.f;
     float dens_g = 0.f, dens_n = 0.f;  // adaptive-control statistics of this call
     Proj P;
@@ -836,7 +838,8 @@ __global__ void __launch_bounds__(128) k_project_bwd(Params G, const float* __re
     float gq[4] = {0.f, 0.f, 0.f, 0.f};
     if (have_rot) quat_grad(P.qn, P.qnorm, gR, gq);
     if (ADAM) {
-        adam_gaussian(adam, i, gq, gp, gs, grho);
+        const float act[11] = {q[0], q[1], q[2], q[3], p[0], p[1], p[2], s[0], s[1], s[2], rho};
+        adam_gaussian_pre(adam, i, pre, act, gq, gp, gs, grho);
         if (adam.dens_grad && dens_n > 0.f) {
             adam.dens_grad[i] += dens_g;
             adam.dens_count[i] += dens_n;
