@@ -620,10 +620,12 @@ __global__ void __launch_bounds__(kBwdThreads) k_splat_bwd(const float4* __restr
     }
     int k = lo;
     float4 k1 = s_k1[k], k2 = s_k2[k];
+    float A2 = 2.f * k1.x, A4 = 4.f * k1.x, A9 = 9.f * k1.x;
     uint32_t gid = s_gid[k];
     uint32_t rec_end = s_excl[k + 1];
     float uf = (float)(p0 - s_excl[k]);  // unit index inside the record
     float S0 = 0.f, Sx = 0.f, Sy = 0.f, Sxx = 0.f, Sxy = 0.f, Syy = 0.f;
+    static_assert(UW == 4, "the per-row sums below are written for 4-pixel unit rows");
     for (uint32_t p = p0; p < p1; ++p) {
         // unit row = floor((u + 1/2) / uw), exact for u < 2^10 and uw <= 16
         const float rowf = floorf(fmaf(uf, k2.z, 0.5f * k2.z));
@@ -636,24 +638,27 @@ __global__ void __launch_bounds__(kBwdThreads) k_splat_bwd(const float4* __restr
             const float dy = dy0 + (float)qy;
             const float bdy = k1.y * dy, cdy2 = k1.z * dy * dy;
             const float4 g4 = *reinterpret_cast<const float4*>(&s_g[gi + qy * TWP]);
-            const float gq4[4] = {g4.x, g4.y, g4.z, g4.w};
-            float Wu = 0.f, Xu = 0.f;
-#pragma unroll
-            for (int q = 0; q < UW; ++q) {
-                const float dxq = dx + (float)q;
-                const float t = fmaf(fmaf(k1.x, dxq, bdy), dxq, cdy2);
-                const float ev = ex2_approx(t);
-                const float wq = (t >= Tq) ? gq4[q] * ev : 0.0f;
-                const float aq = wq * dxq;
-                Wu += wq;
-                Xu += aq;
-                Sxx = fmaf(aq, dxq, Sxx);
-            }
-            S0 += Wu;
-            Sx += Xu;
-            Sy = fmaf(Wu, dy, Sy);
-            Sxy = fmaf(Xu, dy, Sxy);
-            Syy = fmaf(Wu * dy, dy, Syy);
+            // t(dx + q) = t0 + q gl + A q^2, gl = 2 A dx + B dy
+            const float t0 = fmaf(fmaf(k1.x, dx, bdy), dx, cdy2);
+            const float gl = fmaf(A2, dx, bdy);
+            const float t1 = (t0 + k1.x) + gl;
+            const float t2 = fmaf(2.f, gl, t0 + A4);
+            const float t3 = fmaf(3.f, gl, t0 + A9);
+            const float w0 = (t0 >= Tq) ? g4.x * ex2_approx(t0) : 0.0f;
+            const float w1 = (t1 >= Tq) ? g4.y * ex2_approx(t1) : 0.0f;
+            const float w2 = (t2 >= Tq) ? g4.z * ex2_approx(t2) : 0.0f;
+            const float w3 = (t3 >= Tq) ? g4.w * ex2_approx(t3) : 0.0f;
+            // the row's sums of w, q w and q^2 w give its moments at dx + q
+            const float Wr = (w0 + w1) + (w2 + w3);
+            const float Q1 = fmaf(3.f, w3, fmaf(2.f, w2, w1));
+            const float Q2 = fmaf(9.f, w3, fmaf(4.f, w2, w1));
+            const float Xr = fmaf(Wr, dx, Q1);             // sum w (dx + q)
+            S0 += Wr;
+            Sx += Xr;
+            Sxx += fmaf(dx, Xr + Q1, Q2);                    // sum w (dx + q)^2
+            Sy = fmaf(Wr, dy, Sy);
+            Sxy = fmaf(Xr, dy, Sxy);
+            Syy = fmaf(Wr * dy, dy, Syy);
         }
         uf += 1.0f;
         if (p + 1 == rec_end && p + 1 < p1) {  // next record
@@ -665,6 +670,9 @@ __global__ void __launch_bounds__(kBwdThreads) k_splat_bwd(const float4* __restr
             } while (s_excl[k + 1] == s_excl[k]);
             k1 = s_k1[k];
             k2 = s_k2[k];
+            A2 = 2.f * k1.x;
+            A4 = 4.f * k1.x;
+            A9 = 9.f * k1.x;
             gid = s_gid[k];
             rec_end = s_excl[k + 1];
             uf = 0.0f;
