@@ -71,6 +71,10 @@ typedef struct {
     int32_t count_pairs; /* 1: also count the gated pairs (bookkeeping runs only; slower) */
     int32_t biased;      /* 1: the un-rectified amplitude rho_hat = rho of the 3DGS-style X-ray splatting that
                           * Sec. 4.2.1 corrects (mu = 1, view-dependent projected mass); 0 (default): Eq. 7 */
+    int32_t separate_lists; /* 1: build the per-tile lists in separate launches; 0 (default): one cooperative
+                             * launch when the grid can be resident (fewer launches; it holds its SMs until
+                             * the whole grid runs, which limits overlap with other streams' kernels).  The
+                             * lists are the same either way.  r2g_train_step applies it to both branches. */
 } r2g_raster_opts;
 
 /* One voxel grid: the centre of voxel (x, y, z) is origin + (index + 1/2) * voxel;

@@ -583,7 +583,7 @@ template <class Op>
 uint64_t* build_lists(const Op& op, long long n_rec, long long n_slots, unsigned long long* partials, WsStatus* st,
                       uint64_t* a, uint64_t* b, uint32_t* scratch, long long cap, uint2* ranges, uint32_t* key_done,
                       WsStatus* item_st, uint32_t* item_off, uint64_t* items, long long items_cap, int chunk,
-                      ListProf prof, cudaStream_t s, int* launches) {
+                      ListProf prof, cudaStream_t s, int* launches, bool allow_coop = true) {
     const unsigned long long ucap = (unsigned long long)cap;
     const ListBlocking lb = list_blocking(n_rec);
     const long long per_block = 256ll * lb.per_thread;
@@ -594,7 +594,8 @@ uint64_t* build_lists(const Op& op, long long n_rec, long long n_slots, unsigned
         const FusedKeys fk{(uint32_t)chunk, ranges, key_done, item_off, items, (unsigned long long)items_cap,
                            item_st};
         prof_begin(prof.emit, s);
-        if (launch_lists_coop(op, n_rec, per_block, partials, a, b, ucap, hist, totals, nk, st, fk, lb.blocks, s)) {
+        if (allow_coop &&
+            launch_lists_coop(op, n_rec, per_block, partials, a, b, ucap, hist, totals, nk, st, fk, lb.blocks, s)) {
             prof_end(prof.emit, s);
             *launches += 1;
             return b;

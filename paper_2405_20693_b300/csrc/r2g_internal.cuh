@@ -130,7 +130,7 @@ r2g_status rasterize_backward_impl(int64_t M, const float* mean, const float* sc
                                    const AdamState* adam = nullptr);
 r2g_status voxelize_impl(int64_t M, const float* mean, const float* scale, const float* quat, const float* rho,
                          int32_t G, const r2g_grid* grids, const float* origin_dev, float Q3, float* vol, void* ws,
-                         size_t ws_bytes, cudaStream_t stream, bool count);
+                         size_t ws_bytes, cudaStream_t stream, bool count, bool separate_lists = false);
 // The voxel backward in two parts: the per-record moments (dvol -> moments, in the
 // workspace) and the chain rule (moments -> gradients, added to dmean .. drho, or
 // with kVoxBwdAssign written over them).

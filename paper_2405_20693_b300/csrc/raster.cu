@@ -1140,7 +1140,8 @@ r2g_status r2g::rasterize_impl(int64_t M, const float* mean, const float* scale,
     // fused key spaces: projection and lists in one cooperative launch when the grid fits
     const TileProj tp{G, views, view_sel, cf, opts->Q, opts->tile_w, opts->tile_h, M, L.n_rec, rec, rect, mom};
     prof_begin(P_PROJECT, stream);
-    if (launch_plists_coop(tp, op, L.n_rec, L.n_tiles, partials, a, b, cap, scratch, st, ranges, key_done, item_st,
+    if (!opts->separate_lists &&
+        launch_plists_coop(tp, op, L.n_rec, L.n_tiles, partials, a, b, cap, scratch, st, ranges, key_done, item_st,
                            item_off, items, T.icap, kChunk, stream)) {
         prof_end(P_PROJECT, stream);
         sorted = b;
@@ -1154,7 +1155,7 @@ r2g_status r2g::rasterize_impl(int64_t M, const float* mean, const float* scale,
         prof_end(P_PROJECT, stream);
         sorted = build_lists(op, L.n_rec, L.n_tiles, partials, st, a, b, scratch, cap, ranges, key_done, item_st,
                              item_off, items, T.icap, kChunk, ListProf{P_EMIT, P_SORT, P_RANGES}, stream,
-                             &launches);
+                             &launches, !opts->separate_lists);
         launches += 1;
     }
     const float Tq = -0.5f * kLog2e * opts->Q;

@@ -86,7 +86,7 @@ R2G_API r2g_status r2g_train_step(const r2g_job* job, const r2g_round_entry* ent
     if (cudaEventRecord(side->fork, stream) != cudaSuccess || cudaStreamWaitEvent(tv, side->fork, 0) != cudaSuccess)
         return fail(R2G_E_CUDA, "r2g_train_step: fork failed (%s)", cudaGetErrorString(cudaGetLastError()));
     r2g_status e_tv = voxelize_impl(M, mean, scale, quat, rho, 1, &grid, entry->origin, J.Q3, J.vol, J.voxel_ws,
-                                    J.voxel_ws_bytes, tv, false);
+                                    J.voxel_ws_bytes, tv, false, J.ropts.separate_lists != 0);
     if (!e_tv) e_tv = r2g_tv3d(1, J.D, J.vol, J.lambda_tv, J.loss + 1, J.dvol, J.tv_ws, J.tv_ws_bytes, tv);
     if (!e_tv)
         e_tv = voxelize_backward_impl(M, mean, scale, quat, rho, 1, &grid, J.Q3, J.dvol, dmean, dscale, dquat, drho,

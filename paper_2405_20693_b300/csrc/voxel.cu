@@ -715,7 +715,7 @@ R2G_API size_t r2g_voxel_workspace_size(int64_t M, int32_t G, const r2g_grid* gr
 namespace r2g {
 r2g_status voxelize_impl(int64_t M, const float* mean, const float* scale, const float* quat, const float* rho,
                          int32_t G, const r2g_grid* grids, const float* origin_dev, float Q3, float* vol, void* ws,
-                         size_t ws_bytes, cudaStream_t stream, bool count) {
+                         size_t ws_bytes, cudaStream_t stream, bool count, bool separate_lists) {
     r2g_status e = check_params(M, mean, scale, quat, rho);
     if (e) return e;
     Grids gr;
@@ -764,7 +764,7 @@ r2g_status voxelize_impl(int64_t M, const float* mean, const float* scale, const
     int launches = 0;
     uint64_t* sorted = build_lists(op, L.n_rec, L.n_bricks, partials, st, a, b, scratch, cap, ranges, key_done,
                                    item_st, item_off, items, T.icap, kVoxChunk,
-                                   ListProf{P_VOX_EMIT, P_VOX_SORT, P_VOX_RANGES}, stream, &launches);
+                                   ListProf{P_VOX_EMIT, P_VOX_SORT, P_VOX_RANGES}, stream, &launches, !separate_lists);
     const float Tq = -0.5f * kLog2e * Q3;
     note_launches(1 + launches + 1);
     prof_begin(P_VOX_FWD, stream);

@@ -476,9 +476,18 @@ class BatchTrainer:
     CUDA graph and replayed; with graph=False the same calls are issued eagerly on
     the same streams."""
 
-    def __init__(self, scans, n_streams=None, graph=True, seed=0, device="cuda"):
+    def __init__(self, scans, n_streams=None, graph=True, seed=0, device="cuda", separate_lists=None):
         self.scans = list(scans)
         self.J = len(self.scans)
+        # with several scans in flight the list builds run as separate launches: a
+        # cooperative launch holds its SMs until its whole grid runs, which limits the
+        # overlap between the scans' branches (measured: 1.55 vs 1.86 ms per 16-scan round)
+        sep = self.J > 1 if separate_lists is None else bool(separate_lists)
+        for sc in self.scans:
+            if bool(sc.rast.opts.separate_lists) != sep:
+                sc.rast.opts.separate_lists = int(sep)
+                sc.job = sc._make_job()
+                sc.version += 1
         self.device = device
         self.table_host = torch.zeros((self.J, 8), dtype=torch.int32).pin_memory()
         self.table_dev = torch.zeros((self.J, 8), dtype=torch.int32, device=device)

@@ -100,6 +100,23 @@ def test_rasterize_matches_oracle(case):
     assert abs(got - pairs) <= max(10, 1e-4 * pairs), (got, pairs)
 
 
+@pytest.mark.parametrize("case,tile", [("config1", (16, 16)), ("cone", (32, 32))])
+def test_cooperative_and_separate_list_builds_agree(case, tile):
+    """The one-launch (cooperative) list build and the separate launches give the same
+    lists, bit for bit, and the same image."""
+    G, cam, views = _case(case)
+    out = []
+    for sep in (False, True):
+        rast = engine.Rasterizer(G.M, views.shape[0], cam, tile=tile)
+        rast.opts.separate_lists = int(sep)
+        img = host(rast.forward(*dev_set(G), dev(views)))
+        ranges, ids, n = _lists_gpu(rast, G.M, views.shape[0])
+        out.append((img, ranges, ids, n))
+    assert out[0][3] == out[1][3]
+    assert np.array_equal(out[0][1], out[1][1]) and np.array_equal(out[0][2], out[1][2])
+    assert np.array_equal(out[0][0], out[1][0])
+
+
 def test_tile_shape_does_not_change_the_image():
     G, cam, views = cone_small()
     imgs = []
