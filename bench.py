@@ -197,9 +197,9 @@ def _has_cuda():
 
 
 # the source file of each profiled kernel (with every shared .cuh header)
-KERNEL_SOURCES = {"splat_bwd": "raster.cu", "splat_fwd": "raster.cu", "project_bwd": "raster.cu", "sort": "raster.cu",
+KERNEL_SOURCES = {"splat_bwd": "raster.cu", "splat_fwd": "raster.cu", "project_bwd": "raster.cu", "project": "raster.cu",
                   "loss": "loss.cu", "fdk_bp": "fdk.cu", "fdk_filter": "fdk.cu", "init_knn": "fdk.cu",
-                  "init_select_hist": "fdk.cu"}
+                  "init_select_hist": "fdk.cu", "metrics": "metrics.cu", "densify": "densify.cu"}
 
 
 def source_hash(kernel: str | None = None):

@@ -389,13 +389,15 @@ __device__ __forceinline__ void grid_barrier(WsStatus* st, unsigned int epoch) {
         __threadfence();
         const unsigned long long target = (unsigned long long)epoch * gridDim.x;
         atomicAdd(&st->grid_sync, 1ull);
-        unsigned long long spins = 0;
-        while (atomicAdd(&st->grid_sync, 0ull) < target) {
+        unsigned long long spins = 0, seen;
+        for (;;) {
+            asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(seen) : "l"(&st->grid_sync) : "memory");
+            if (seen >= target) break;
             if (++spins > kGridSyncSpins) {
                 atomicExch(&st->status, (int32_t)R2G_E_TIMEOUT);
                 break;
             }
-            __nanosleep(64);
+            __nanosleep(20);
         }
         __threadfence();
     }
