@@ -134,6 +134,7 @@ struct FusedKeys {
     uint64_t* items;          // (key << 32) | chunk; every empty key gets one item
     unsigned long long items_cap;
     WsStatus* item_st;        // n_keys = item count
+    int kd_per_key;           // arrival counters per key (consecutive; 0 taken as 1)
 };
 
 // Emission of one block's records (blockIdx.x * per_block .. + per_block), in
@@ -223,7 +224,8 @@ __device__ __forceinline__ void key_scan(const uint32_t* key_totals, int n_keys,
             if (key_first) key_first[k] = base;
             if (write_items) {
                 fk.ranges[k] = tk[q] ? make_uint2(base, base + tk[q]) : make_uint2(0u, 0u);
-                fk.key_done[k] = 0;
+                const int kd = fk.kd_per_key > 0 ? fk.kd_per_key : 1;
+                for (int w = 0; w < kd; ++w) fk.key_done[(size_t)k * kd + w] = 0;
                 fk.item_off[k] = ibase;
                 for (uint32_t c = 0; c < nc[q]; ++c)
                     if (ibase + c < fk.items_cap) fk.items[ibase + c] = ((uint64_t)(uint32_t)k << 32) | c;
@@ -541,7 +543,7 @@ template <class Proj, class Op>
 bool launch_plists_coop(const Proj& proj, const Op& op, long long n_rec, long long n_slots,
                         unsigned long long* counts, uint64_t* a, uint64_t* b, long long cap, uint32_t* scratch,
                         WsStatus* st, uint2* ranges, uint32_t* key_done, WsStatus* item_st, uint32_t* item_off,
-                        uint64_t* items, long long items_cap, int chunk, cudaStream_t s) {
+                        uint64_t* items, long long items_cap, int chunk, cudaStream_t s, int kd_per_key = 1) {
     if (!fused_lists(n_slots)) return false;
     const int res = coop_resident(k_plists_coop<Proj, Op>);
     const int max_blocks = res < kMaxListBlocks ? res : kMaxListBlocks;
@@ -552,7 +554,8 @@ bool launch_plists_coop(const Proj& proj, const Op& op, long long n_rec, long lo
     if (blocks < 1 || blocks > max_blocks) return false;
     uint32_t* hist = scratch;
     uint32_t* totals = scratch + (size_t)kRadix * kSortBlocksMax;
-    const FusedKeys fk{(uint32_t)chunk, ranges, key_done, item_off, items, (unsigned long long)items_cap, item_st};
+    const FusedKeys fk{(uint32_t)chunk, ranges,  key_done, item_off, items, (unsigned long long)items_cap,
+                       item_st,         kd_per_key};
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)blocks);
     cfg.blockDim = dim3(256);
@@ -585,7 +588,7 @@ template <class Op>
 uint64_t* build_lists(const Op& op, long long n_rec, long long n_slots, unsigned long long* partials, WsStatus* st,
                       uint64_t* a, uint64_t* b, uint32_t* scratch, long long cap, uint2* ranges, uint32_t* key_done,
                       WsStatus* item_st, uint32_t* item_off, uint64_t* items, long long items_cap, int chunk,
-                      ListProf prof, cudaStream_t s, int* launches, bool allow_coop = true) {
+                      ListProf prof, cudaStream_t s, int* launches, bool allow_coop = true, int kd_per_key = 1) {
     const unsigned long long ucap = (unsigned long long)cap;
     const ListBlocking lb = list_blocking(n_rec);
     const long long per_block = 256ll * lb.per_thread;
@@ -593,8 +596,8 @@ uint64_t* build_lists(const Op& op, long long n_rec, long long n_slots, unsigned
         uint32_t* hist = scratch;
         uint32_t* totals = scratch + (size_t)kRadix * kSortBlocksMax;
         const int nk = (int)n_slots;
-        const FusedKeys fk{(uint32_t)chunk, ranges, key_done, item_off, items, (unsigned long long)items_cap,
-                           item_st};
+        const FusedKeys fk{(uint32_t)chunk, ranges,  key_done, item_off, items, (unsigned long long)items_cap,
+                           item_st,         kd_per_key};
         prof_begin(prof.emit, s);
         if (allow_coop &&
             launch_lists_coop(op, n_rec, per_block, partials, a, b, ucap, hist, totals, nk, st, fk, lb.blocks, s)) {

@@ -359,110 +359,121 @@ struct TileOp {
 // ------------------------------------------------------------------ K3: splat forward
 
 // Pixels per lane of the forward splat for a tile shape (a warp owns an 8-row block
-// 4 * PX pixels wide).
+// 4 * PX pixels wide), and the warp blocks per tile.
 template <int TW, int TH>
 struct FwdShape {
     static constexpr int PX = (TW * TH >= 256) ? 4 : 2;
-    static constexpr int NT = TW * TH / PX;
+    static constexpr int BW = 4 * PX;
+    static constexpr int NW = TW * TH / (8 * BW);
 };
+constexpr int kFwdMaxBlocks = 8;   // warp blocks per tile at most (32 x 32 tiles)
+constexpr int kFwdWarps = 4;       // independent warps per CTA
 
+// One warp per (work item, warp block): the item's <= 128 records of one tile are
+// read by the warp's lanes (four each), the records whose box meets the warp's
+// 8 x BW pixel block are compacted (ballot) into the warp's shared-memory list, and
+// each lane accumulates its PX pixels over that list -- the quadratic is one FMA per
+// pixel (t0 + k (g + A k)).  The warps of a CTA share nothing (no block barrier).
+// A tile with several chunks: each chunk's warp writes its block of the chunk image;
+// the last chunk of a block to finish (per-(tile, block) arrival counter) sums the
+// block's chunk images in chunk order (deterministic).
 template <int TW, int TH, bool COUNT>
-__global__ void __launch_bounds__(FwdShape<TW, TH>::NT) k_splat_fwd(const float4* __restrict__ rec,
-                                                                    const uint2* __restrict__ ranges,
-                                                                    const uint64_t* __restrict__ sorted,
-                                                                    const uint64_t* __restrict__ items,
-                                                                    const WsStatus* __restrict__ item_st,
-                                                                    float* __restrict__ partial,
-                                                                    const uint32_t* __restrict__ item_off,
-                                                                    uint32_t* __restrict__ key_done, long long M,
-                                                                    int tiles_x, int tiles_per_view, int H, int W,
-                                                                    float Tq, float* __restrict__ image,
-                                                                    WsStatus* st) {
+__global__ void __launch_bounds__(32 * kFwdWarps) k_splat_fwd(const float4* __restrict__ rec,
+                                                              const uint2* __restrict__ ranges,
+                                                              const uint64_t* __restrict__ sorted,
+                                                              const uint64_t* __restrict__ items,
+                                                              const WsStatus* __restrict__ item_st,
+                                                              float* __restrict__ partial,
+                                                              const uint32_t* __restrict__ item_off,
+                                                              uint32_t* __restrict__ key_done, long long M,
+                                                              int tiles_x, int tiles_per_view, int H, int W,
+                                                              float Tq, float* __restrict__ image, WsStatus* st) {
     constexpr int PX = FwdShape<TW, TH>::PX;  // pixels per lane, along x
-    constexpr int NT = FwdShape<TW, TH>::NT;  // threads
-    constexpr int BW = 4 * PX;                // warp block: 8 rows x BW columns
+    constexpr int BW = FwdShape<TW, TH>::BW;  // warp block: 8 rows x BW columns
+    constexpr int NW = FwdShape<TW, TH>::NW;  // warp blocks per tile
     constexpr int WPR = TW / BW;              // warp blocks per tile row
-    constexpr int NW = NT / 32;               // warps = warp blocks per tile
-    static_assert(TW % BW == 0 && TH % 8 == 0 && (kChunk % NT == 0 || NT % kChunk == 0) && NT % 32 == 0 &&
-                      NW <= 32 && NT <= 256,
-                  "tile shape");
-    __shared__ float4 s_a[NT];
-    __shared__ float4 s_b[NT];
-    __shared__ uint32_t s_mask[NT];           // bit w: the record's box meets warp w's block
-    __shared__ uint8_t s_list[NW][NT];        // per warp: the batch's records that meet its block
-    __shared__ int s_last;
-    const unsigned long long it = blockIdx.x;
-    if (it >= item_st->n_keys) return;
+    static_assert(TW % BW == 0 && TH % 8 == 0 && NW <= kFwdMaxBlocks && kChunk == 128, "tile shape");
+    __shared__ float4 s_a[kFwdWarps][kChunk];
+    __shared__ float4 s_b[kFwdWarps][kChunk];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned long long gw = (unsigned long long)blockIdx.x * kFwdWarps + warp;
+    const unsigned long long it = gw / NW;
+    const int wb = (int)(gw - it * NW);
+    if (it >= item_st->n_keys) return;  // whole warps
     const uint64_t item = items[it];
     const int tile = (int)(item >> 32);
     const uint32_t chunk = (uint32_t)item;
     const int v = tile / tiles_per_view;
     const int lt = tile - v * tiles_per_view;
     const int ty = lt / tiles_x, tx = lt - ty * tiles_x;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int bx = (warp % WPR) * BW, by = (warp / WPR) * 8;
+    const int bx = (wb % WPR) * BW, by = (wb / WPR) * 8;
     const int lx = bx + (lane & 3) * PX, ly = by + (lane >> 2);
     const int px = tx * TW + lx, py = ty * TH + ly;
     const float fx = (float)px, fy = (float)py;
     const float4* vrec = rec + 2 * (size_t)v * (size_t)M;
-    float acc[PX];
-#pragma unroll
-    for (int k = 0; k < PX; ++k) acc[k] = 0.0f;
-    unsigned int cnt = 0;
     const uint2 rg = ranges[tile];
     const uint32_t start = rg.x + chunk * kChunk;
     const uint32_t end = min(start + (uint32_t)kChunk, rg.y);
     const uint32_t nch = (rg.y - rg.x + kChunk - 1) / kChunk;
-    for (uint32_t base = start; base < end; base += NT) {
-        const int n = min((uint32_t)NT, end - base);
-        __syncthreads();
-        if ((int)threadIdx.x < n) {
-            const uint32_t gid = (uint32_t)sorted[base + threadIdx.x];
-            const float4 a = vrec[2 * (size_t)gid];      // cx, cy, A, B
-            const float4 b = vrec[2 * (size_t)gid + 1];  // C, rho_hat, rx, ry
-            s_a[threadIdx.x] = a;
-            s_b[threadIdx.x] = b;
-            // the record's pixel box inside the tile, and the warp blocks it meets
-            const int c0 = (int)ceilf(a.x - b.z) - tx * TW, c1 = (int)floorf(a.x + b.z) - tx * TW;
-            const int r0 = (int)ceilf(a.y - b.w) - ty * TH, r1 = (int)floorf(a.y + b.w) - ty * TH;
-            uint32_t mask = 0;
+    const int n = (int)(end > start ? end - start : 0u);
+    // the item's records (lane j holds records j, j + 32, ...), loads issued together
+    uint32_t gid[kChunk / 32];
 #pragma unroll
-            for (int w = 0; w < NW; ++w) {
-                const int wbx = (w % WPR) * BW, wby = (w / WPR) * 8;
-                if (c1 >= wbx && c0 <= wbx + BW - 1 && r1 >= wby && r0 <= wby + 7) mask |= 1u << w;
-            }
-            s_mask[threadIdx.x] = mask;
+    for (int c = 0; c < kChunk / 32; ++c) {
+        const int j = c * 32 + lane;
+        gid[c] = j < n ? (uint32_t)sorted[start + j] : 0u;
+    }
+    float4 ra[kChunk / 32], rb[kChunk / 32];
+#pragma unroll
+    for (int c = 0; c < kChunk / 32; ++c) {
+        const int j = c * 32 + lane;
+        if (j < n) {
+            ra[c] = vrec[2 * (size_t)gid[c]];      // cx, cy, A, B
+            rb[c] = vrec[2 * (size_t)gid[c] + 1];  // C, rho_hat, rx, ry
         }
-        __syncthreads();
-        // this warp's records of the batch, in batch order
-        int m = 0;
+    }
+    // compact the records whose pixel box meets this warp's block, in item order
+    const int gx0 = tx * TW + bx, gy0 = ty * TH + by;
+    int m = 0;
 #pragma unroll
-        for (int c = 0; c < NT / 32; ++c) {
-            const int j = c * 32 + lane;
-            const bool mine = j < n && ((s_mask[j] >> warp) & 1u);
-            const uint32_t bal = __ballot_sync(0xffffffffu, mine);
-            if (mine) s_list[warp][m + __popc(bal & ((1u << lane) - 1u))] = (uint8_t)j;
-            m += __popc(bal);
+    for (int c = 0; c < kChunk / 32; ++c) {
+        const int j = c * 32 + lane;
+        bool mine = false;
+        if (j < n) {
+            const float4 a = ra[c], b = rb[c];
+            const int c0 = (int)ceilf(a.x - b.z), c1 = (int)floorf(a.x + b.z);
+            const int r0 = (int)ceilf(a.y - b.w), r1 = (int)floorf(a.y + b.w);
+            mine = c1 >= gx0 && c0 <= gx0 + BW - 1 && r1 >= gy0 && r0 <= gy0 + 7;
         }
-        __syncwarp();
-        for (int q = 0; q < m; ++q) {
-            const int j = s_list[warp][q];
-            const float4 a = s_a[j];
-            const float4 b = s_b[j];
-            const float dy = fy - a.y;
-            const float bdy = a.w * dy;
-            const float cdy2 = b.x * dy * dy;
-            const float dx0 = fx - a.x;
-            // t(dx0 + k) = t0 + k (g + A k), g = dt/ddx at dx0
-            const float t0 = fmaf(fmaf(a.z, dx0, bdy), dx0, cdy2);
-            const float g = fmaf(2.0f * a.z, dx0, bdy);
+        const uint32_t bal = __ballot_sync(0xffffffffu, mine);
+        if (mine) {
+            const int pos = m + __popc(bal & ((1u << lane) - 1u));
+            s_a[warp][pos] = ra[c];
+            s_b[warp][pos] = rb[c];
+        }
+        m += __popc(bal);
+    }
+    __syncwarp();
+    float acc[PX];
 #pragma unroll
-            for (int k = 0; k < PX; ++k) {
-                const float t = k == 0 ? t0 : fmaf((float)k, fmaf(a.z, (float)k, g), t0);
-                const float e = ex2_approx(t);
-                acc[k] = (t >= Tq) ? fmaf(b.y, e, acc[k]) : acc[k];
-                if (COUNT) cnt += (t >= Tq && px + k < W && py < H);
-            }
+    for (int k = 0; k < PX; ++k) acc[k] = 0.0f;
+    unsigned int cnt = 0;
+    for (int q = 0; q < m; ++q) {
+        const float4 a = s_a[warp][q];
+        const float4 b = s_b[warp][q];
+        const float dy = fy - a.y;
+        const float bdy = a.w * dy;
+        const float cdy2 = b.x * dy * dy;
+        const float dx0 = fx - a.x;
+        // t(dx0 + k) = t0 + k (g + A k), g = dt/ddx at dx0
+        const float t0 = fmaf(fmaf(a.z, dx0, bdy), dx0, cdy2);
+        const float g = fmaf(2.0f * a.z, dx0, bdy);
+#pragma unroll
+        for (int k = 0; k < PX; ++k) {
+            const float t = k == 0 ? t0 : fmaf((float)k, fmaf(a.z, (float)k, g), t0);
+            const float e = ex2_approx(t);
+            acc[k] = (t >= Tq) ? fmaf(b.y, e, acc[k]) : acc[k];
+            if (COUNT) cnt += (t >= Tq && px + k < W && py < H);
         }
     }
     if (COUNT) {
@@ -471,26 +482,24 @@ __global__ void __launch_bounds__(FwdShape<TW, TH>::NT) k_splat_fwd(const float4
         if (lane == 0 && cnt) atomicAdd(&st->pairs, (unsigned long long)cnt);
     }
     if (nch > 1) {
-        // several chunks: store this chunk's image; the last chunk to finish sums
-        // the tile's chunk images in chunk order
+        // several chunks: store this chunk's block; the last chunk of the block to
+        // finish sums the block's chunk images in chunk order
         float* p = partial + it * (size_t)(TW * TH) + ly * TW + lx;
 #pragma unroll
         for (int k = 0; k < PX; ++k) p[k] = acc[k];
-        // the barrier orders every thread's stores before thread 0's release fence
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            __threadfence();
-            s_last = atomicAdd(&key_done[tile], 1u) == nch - 1;
-        }
-        __syncthreads();
-        if (!s_last) return;
+        __threadfence();  // every lane's stores before lane 0's arrival
+        __syncwarp();
+        uint32_t last = 0;
+        if (lane == 0) last = atomicAdd(&key_done[(size_t)tile * kFwdMaxBlocks + wb], 1u) == nch - 1;
+        last = __shfl_sync(0xffffffffu, last, 0);
+        if (!last) return;
         __threadfence();
-        const float* q = partial + (size_t)item_off[tile] * (TW * TH) + ly * TW + lx;
+        const float* qp = partial + (size_t)item_off[tile] * (TW * TH) + ly * TW + lx;
 #pragma unroll
         for (int k = 0; k < PX; ++k) acc[k] = 0.0f;
         for (uint32_t c = 0; c < nch; ++c)
 #pragma unroll
-            for (int k = 0; k < PX; ++k) acc[k] += __ldcg(q + (size_t)c * (TW * TH) + k);
+            for (int k = 0; k < PX; ++k) acc[k] += __ldcg(qp + (size_t)c * (TW * TH) + k);
     }
     if (py < H) {  // one chunk (or none: an empty tile's item writes zeros), or the sum
         float* row = image + ((size_t)v * H + py) * W;
@@ -932,7 +941,7 @@ RasterLayout raster_layout(int64_t M, int32_t V, const r2g_camera* cam, const r2
     L.rect = lay.take(8 * (size_t)L.n_rec);
     L.partials = lay.take(8 * (size_t)kScanBlocks);
     L.ranges = lay.take(8 * (size_t)L.n_tiles);
-    L.key_done = lay.take(4 * (size_t)L.n_tiles);  // chunk arrival counters of the forward
+    L.key_done = lay.take(4 * (size_t)L.n_tiles * kFwdMaxBlocks);  // chunk arrivals per (tile, warp block)
     L.item_status = lay.take(sizeof(WsStatus));     // ranges .. item status are cleared together
     L.mom = lay.take(32 * (size_t)L.n_rec);
     L.scratch = lay.take(sort_scratch_bytes());
@@ -1003,7 +1012,8 @@ struct FwdArgs {
 template <int TW, int TH, bool COUNT>
 void fwd_shape(const FwdArgs& f, long long M, const RasterLayout& L, long long icap, int H, int W, float Tq,
                float* image, WsStatus* st, cudaStream_t s) {
-    k_splat_fwd<TW, TH, COUNT><<<(unsigned)icap, FwdShape<TW, TH>::NT, 0, s>>>(
+    const unsigned long long warps = (unsigned long long)icap * FwdShape<TW, TH>::NW;
+    k_splat_fwd<TW, TH, COUNT><<<(unsigned)((warps + kFwdWarps - 1) / kFwdWarps), 32 * kFwdWarps, 0, s>>>(
         f.rec, f.ranges, f.sorted, f.items, f.item_st, f.partial, f.item_off, f.key_done, M, L.tiles_x,
         L.tiles_per_view, H, W, Tq, image, st);
 }
@@ -1142,7 +1152,7 @@ r2g_status r2g::rasterize_impl(int64_t M, const float* mean, const float* scale,
     prof_begin(P_PROJECT, stream);
     if (!opts->separate_lists &&
         launch_plists_coop(tp, op, L.n_rec, L.n_tiles, partials, a, b, cap, scratch, st, ranges, key_done, item_st,
-                           item_off, items, T.icap, kChunk, stream)) {
+                           item_off, items, T.icap, kChunk, stream, kFwdMaxBlocks)) {
         prof_end(P_PROJECT, stream);
         sorted = b;
         launches = 1;
@@ -1155,7 +1165,7 @@ r2g_status r2g::rasterize_impl(int64_t M, const float* mean, const float* scale,
         prof_end(P_PROJECT, stream);
         sorted = build_lists(op, L.n_rec, L.n_tiles, partials, st, a, b, scratch, cap, ranges, key_done, item_st,
                              item_off, items, T.icap, kChunk, ListProf{P_EMIT, P_SORT, P_RANGES}, stream,
-                             &launches, !opts->separate_lists);
+                             &launches, !opts->separate_lists, kFwdMaxBlocks);
         launches += 1;
     }
     const float Tq = -0.5f * kLog2e * opts->Q;
