@@ -310,9 +310,11 @@ static __global__ void __launch_bounds__(256) k_fused_offsets(uint32_t* __restri
 // the block's offsets give each warp its base per key; inside a warp, lanes with
 // equal keys are ranked by lane (match mask), so equal keys keep their input order.
 // s_h: shared [8][kFusedKeys].
-__device__ __forceinline__ void scatter_block(const uint64_t* __restrict__ in, uint64_t* __restrict__ out,
-                                              const uint32_t* __restrict__ offs, unsigned long long lo,
-                                              unsigned long long hi, int n_keys, uint32_t (*s_h)[kFusedKeys]) {
+template <class Op>
+__device__ __forceinline__ void scatter_block(const Op& op, const uint64_t* __restrict__ in,
+                                              uint64_t* __restrict__ out, const uint32_t* __restrict__ offs,
+                                              unsigned long long lo, unsigned long long hi, int n_keys,
+                                              uint32_t (*s_h)[kFusedKeys]) {
     const int b = blockIdx.x, nb = gridDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned long long per = (hi - lo + 7) / 8;
     const unsigned long long wlo = min(hi, lo + warp * per), whi = min(hi, wlo + per);
@@ -361,23 +363,26 @@ __device__ __forceinline__ void scatter_block(const uint64_t* __restrict__ in, u
             __syncwarp();
             if (valid && rank == 0) s_h[warp][k] += __popc(peers);
             __syncwarp();
-            if (valid) out[pos] = x[q];
+            if (valid) {
+                out[pos] = x[q];
+                op.copy_rec(x[q], pos);  // the entry's record next to it (Op's choice)
+            }
         }
     }
 }
 
 // One block per emit block (see scatter_block).
-static __global__ void __launch_bounds__(256) k_fused_scatter(const uint64_t* __restrict__ in,
-                                                              uint64_t* __restrict__ out,
-                                                              const uint32_t* __restrict__ offs,
-                                                              const unsigned long long* __restrict__ starts,
-                                                              const WsStatus* __restrict__ st, int n_keys) {
+template <class Op>
+__global__ void __launch_bounds__(256) k_fused_scatter(Op op, const uint64_t* __restrict__ in,
+                                                       uint64_t* __restrict__ out, const uint32_t* __restrict__ offs,
+                                                       const unsigned long long* __restrict__ starts,
+                                                       const WsStatus* __restrict__ st, int n_keys) {
     __shared__ uint32_t s_h[8][kFusedKeys];
     const int b = blockIdx.x;
     const unsigned long long n_written = st->n_keys;
     const unsigned long long lo = min(starts[b], n_written);
     const unsigned long long hi = (b + 1 < (int)gridDim.x) ? min(starts[b + 1], n_written) : n_written;
-    scatter_block(in, out, offs, lo, hi, n_keys, s_h);
+    scatter_block(op, in, out, offs, lo, hi, n_keys, s_h);
 }
 
 // Grid barrier of a cooperative launch (all blocks resident): thread 0 of each
@@ -435,7 +440,7 @@ __global__ void __launch_bounds__(256) k_lists_coop(Op op, long long n_rec, long
     const unsigned long long lo = min(partials[blockIdx.x], n_written);
     const unsigned long long hi =
         (blockIdx.x + 1 < gridDim.x) ? min(partials[blockIdx.x + 1], n_written) : n_written;
-    scatter_block(a, b, hist, lo, hi, n_keys, reinterpret_cast<uint32_t(*)[kFusedKeys]>(pool));
+    scatter_block(op, a, b, hist, lo, hi, n_keys, reinterpret_cast<uint32_t(*)[kFusedKeys]>(pool));
 }
 
 // The projection and the fused list build in one cooperative launch: each block
@@ -488,7 +493,7 @@ __global__ void __launch_bounds__(256) k_plists_coop(Proj proj, Op op, long long
     grid_barrier(st, 3);
     const unsigned long long lo = before < written ? before : written;
     const unsigned long long hi = before + mine < written ? before + mine : written;
-    scatter_block(a, b, hist, lo, hi, n_keys, reinterpret_cast<uint32_t(*)[kFusedKeys]>(pool));
+    scatter_block(op, a, b, hist, lo, hi, n_keys, reinterpret_cast<uint32_t(*)[kFusedKeys]>(pool));
 }
 
 // Largest co-resident grid of a kernel of 256-thread blocks on this device (0: no
@@ -610,7 +615,7 @@ uint64_t* build_lists(const Op& op, long long n_rec, long long n_slots, unsigned
         prof_end(prof.emit, s);
         prof_begin(prof.sort, s);
         k_fused_offsets<<<(nk + 7) / 8, 256, 0, s>>>(hist, totals, lb.blocks, nk);
-        k_fused_scatter<<<lb.blocks, 256, 0, s>>>(a, b, hist, partials, st, nk);
+        k_fused_scatter<Op><<<lb.blocks, 256, 0, s>>>(op, a, b, hist, partials, st, nk);
         prof_end(prof.sort, s);
         *launches += 3;
         return b;

@@ -334,6 +334,17 @@ struct TileOp {
     const uint2* rect;
     long long M;
     int tiles_x, tiles_per_view;
+    const float4* rec;  // with srec: each sorted entry's splat record is copied next to it
+    float4* srec;
+
+    __device__ __forceinline__ void copy_rec(uint64_t x, unsigned long long pos) const {
+        if (!srec) return;
+        const uint32_t key = (uint32_t)(x >> 32);
+        const long long v = key / (uint32_t)tiles_per_view;
+        const float4* r = rec + 2 * (size_t)(v * M + (uint32_t)x);
+        srec[2 * pos] = r[0];
+        srec[2 * pos + 1] = r[1];
+    }
 
     __device__ __forceinline__ uint32_t count(long long r) const {
         const uint2 rc = rect[r];
@@ -379,6 +390,7 @@ constexpr int kFwdWarps = 4;       // independent warps per CTA
 // block's chunk images in chunk order (deterministic).
 template <int TW, int TH, bool COUNT>
 __global__ void __launch_bounds__(32 * kFwdWarps) k_splat_fwd(const float4* __restrict__ rec,
+                                                              const float4* __restrict__ srec,
                                                               const uint2* __restrict__ ranges,
                                                               const uint64_t* __restrict__ sorted,
                                                               const uint64_t* __restrict__ items,
@@ -416,20 +428,32 @@ __global__ void __launch_bounds__(32 * kFwdWarps) k_splat_fwd(const float4* __re
     const uint32_t end = min(start + (uint32_t)kChunk, rg.y);
     const uint32_t nch = (rg.y - rg.x + kChunk - 1) / kChunk;
     const int n = (int)(end > start ? end - start : 0u);
-    // the item's records (lane j holds records j, j + 32, ...), loads issued together
-    uint32_t gid[kChunk / 32];
-#pragma unroll
-    for (int c = 0; c < kChunk / 32; ++c) {
-        const int j = c * 32 + lane;
-        gid[c] = j < n ? (uint32_t)sorted[start + j] : 0u;
-    }
+    // the item's records (lane j holds records j, j + 32, ...), loads issued together:
+    // next to the sorted entries (srec), else gathered by Gaussian id
     float4 ra[kChunk / 32], rb[kChunk / 32];
+    if (srec) {
 #pragma unroll
-    for (int c = 0; c < kChunk / 32; ++c) {
-        const int j = c * 32 + lane;
-        if (j < n) {
-            ra[c] = vrec[2 * (size_t)gid[c]];      // cx, cy, A, B
-            rb[c] = vrec[2 * (size_t)gid[c] + 1];  // C, rho_hat, rx, ry
+        for (int c = 0; c < kChunk / 32; ++c) {
+            const int j = c * 32 + lane;
+            if (j < n) {
+                ra[c] = srec[2 * (size_t)(start + j)];      // cx, cy, A, B
+                rb[c] = srec[2 * (size_t)(start + j) + 1];  // C, rho_hat, rx, ry
+            }
+        }
+    } else {
+        uint32_t gid[kChunk / 32];
+#pragma unroll
+        for (int c = 0; c < kChunk / 32; ++c) {
+            const int j = c * 32 + lane;
+            gid[c] = j < n ? (uint32_t)sorted[start + j] : 0u;
+        }
+#pragma unroll
+        for (int c = 0; c < kChunk / 32; ++c) {
+            const int j = c * 32 + lane;
+            if (j < n) {
+                ra[c] = vrec[2 * (size_t)gid[c]];
+                rb[c] = vrec[2 * (size_t)gid[c] + 1];
+            }
         }
     }
     // compact the records whose pixel box meets this warp's block, in item order
@@ -558,6 +582,7 @@ constexpr int kBwdUnitW = 4, kBwdUnitH = 2;
 // leaves the record or its range ends.
 template <int TW, int TH, int UW, int UH>
 __global__ void __launch_bounds__(kBwdThreads) k_splat_bwd(const float4* __restrict__ rec,
+                                                           const float4* __restrict__ srec,
                                                            const uint2* __restrict__ ranges,
                                                            const uint64_t* __restrict__ sorted,
                                                            const uint64_t* __restrict__ items,
@@ -598,8 +623,9 @@ __global__ void __launch_bounds__(kBwdThreads) k_splat_bwd(const float4* __restr
     uint32_t n = 0;
     if (e < rg.y) {
         const uint32_t gid = (uint32_t)sorted[e];
-        const float4 a = vrec[2 * (size_t)gid];
-        const float4 b = vrec[2 * (size_t)gid + 1];
+        // the record next to the sorted entry (srec: independent of the id load), else gathered
+        const float4 a = srec ? srec[2 * (size_t)e] : vrec[2 * (size_t)gid];
+        const float4 b = srec ? srec[2 * (size_t)e + 1] : vrec[2 * (size_t)gid + 1];
         const int c0 = max(0, (int)ceilf(a.x - b.z) - X0), c1 = min(TW - 1, (int)floorf(a.x + b.z) - X0);
         const int r0 = max(0, (int)ceilf(a.y - b.w) - Y0), r1 = min(TH - 1, (int)floorf(a.y + b.w) - Y0);
         const int w = c1 - c0 + 1, h = r1 - r0 + 1;
@@ -953,10 +979,12 @@ RasterLayout raster_layout(int64_t M, int32_t V, const r2g_camera* cam, const r2
 // Capacity-dependent tail: two entry buffers, the work items and the per-item
 // chunk images of the forward pass.
 struct Tail {
-    size_t a, b, items, partial, end;
+    size_t a, b, srec, items, partial, end;
     long long icap;
 };
 
+// Fused key spaces also keep each sorted entry's 32-byte splat record next to it
+// (srec), so that the splat kernels read records contiguously.
 Tail raster_tail(const RasterLayout& L, long long cap, int tile_px) {
     Tail t;
     t.icap = items_capacity(L.n_tiles, cap, kChunk);
@@ -964,6 +992,7 @@ Tail raster_tail(const RasterLayout& L, long long cap, int tile_px) {
     lay.off = L.fixed;
     t.a = lay.take(8 * (size_t)cap);
     t.b = lay.take(8 * (size_t)cap);
+    t.srec = fused_lists(L.n_tiles) ? lay.take(32 * (size_t)cap) : 0;
     t.items = lay.take(8 * (size_t)t.icap);
     t.partial = lay.take(4 * (size_t)tile_px * (size_t)t.icap);
     t.end = lay.off;
@@ -973,7 +1002,7 @@ Tail raster_tail(const RasterLayout& L, long long cap, int tile_px) {
 // Largest key capacity (a multiple of 32) whose tail fits in ws_bytes.
 long long capacity_of(const RasterLayout& L, size_t ws_bytes, int tile_px) {
     if (ws_bytes <= L.fixed) return 0;
-    const double per = 16.0 + (8.0 + 4.0 * tile_px) / kChunk;
+    const double per = (fused_lists(L.n_tiles) ? 48.0 : 16.0) + (8.0 + 4.0 * tile_px) / kChunk;
     const double fixed_tail = (double)L.n_tiles * (8.0 + 4.0 * tile_px) + 4096.0;
     double est = ((double)(ws_bytes - L.fixed) - fixed_tail) / per;
     long long cap = est > 0 ? ((long long)est / 32) * 32 : 0;
@@ -1000,6 +1029,7 @@ CamF camf(const r2g_camera* c, const r2g_raster_opts* o) {
 
 struct FwdArgs {
     const float4* rec;
+    const float4* srec;  // the sorted entries' records (fused key spaces), or null
     const uint2* ranges;
     const uint64_t* sorted;
     const uint64_t* items;
@@ -1014,7 +1044,7 @@ void fwd_shape(const FwdArgs& f, long long M, const RasterLayout& L, long long i
                float* image, WsStatus* st, cudaStream_t s) {
     const unsigned long long warps = (unsigned long long)icap * FwdShape<TW, TH>::NW;
     k_splat_fwd<TW, TH, COUNT><<<(unsigned)((warps + kFwdWarps - 1) / kFwdWarps), 32 * kFwdWarps, 0, s>>>(
-        f.rec, f.ranges, f.sorted, f.items, f.item_st, f.partial, f.item_off, f.key_done, M, L.tiles_x,
+        f.rec, f.srec, f.ranges, f.sorted, f.items, f.item_st, f.partial, f.item_off, f.key_done, M, L.tiles_x,
         L.tiles_per_view, H, W, Tq, image, st);
 }
 
@@ -1031,26 +1061,23 @@ void launch_fwd(int tw, int th, const FwdArgs& f, long long M, const RasterLayou
         fwd_shape<32, 8, COUNT>(f, M, L, icap, H, W, Tq, image, st, s);
 }
 
-void launch_bwd(int tw, int th, const float4* rec, const uint2* ranges, const uint64_t* sorted,
+void launch_bwd(int tw, int th, const float4* rec, const float4* srec, const uint2* ranges, const uint64_t* sorted,
                 const uint64_t* items, const WsStatus* item_st, long long icap, long long M, const RasterLayout& L,
                 int H, int W, float Tq, const float* dimage, float4* mom, cudaStream_t s) {
     const unsigned grid = (unsigned)icap;
+#define R2G_BWD(TW, TH)                                                                                       \
+    k_splat_bwd<TW, TH, kBwdUnitW, kBwdUnitH><<<grid, kBwdThreads, 0, s>>>(rec, srec, ranges, sorted, items,   \
+                                                                           item_st, M, L.tiles_x,               \
+                                                                           L.tiles_per_view, H, W, Tq, dimage, mom)
     if (tw == 16 && th == 16)
-        k_splat_bwd<16, 16, kBwdUnitW, kBwdUnitH><<<grid, kBwdThreads, 0, s>>>(rec, ranges, sorted, items, item_st,
-                                                                                   M, L.tiles_x,
-                                                         L.tiles_per_view, H, W, Tq, dimage, mom);
+        R2G_BWD(16, 16);
     else if (tw == 8 && th == 8)
-        k_splat_bwd<8, 8, kBwdUnitW, kBwdUnitH><<<grid, kBwdThreads, 0, s>>>(rec, ranges, sorted, items, item_st,
-                                                                                   M, L.tiles_x,
-                                                       L.tiles_per_view, H, W, Tq, dimage, mom);
+        R2G_BWD(8, 8);
     else if (tw == 32 && th == 32)
-        k_splat_bwd<32, 32, kBwdUnitW, kBwdUnitH><<<grid, kBwdThreads, 0, s>>>(rec, ranges, sorted, items, item_st,
-                                                                                    M, L.tiles_x, L.tiles_per_view,
-                                                                                    H, W, Tq, dimage, mom);
+        R2G_BWD(32, 32);
     else
-        k_splat_bwd<32, 8, kBwdUnitW, kBwdUnitH><<<grid, kBwdThreads, 0, s>>>(rec, ranges, sorted, items, item_st,
-                                                                                   M, L.tiles_x,
-                                                        L.tiles_per_view, H, W, Tq, dimage, mom);
+        R2G_BWD(32, 8);
+#undef R2G_BWD
 }
 
 uint64_t* sorted_buffer(char* base, const RasterLayout& L, const Tail& t) {
@@ -1144,7 +1171,8 @@ r2g_status r2g::rasterize_impl(int64_t M, const float* mean, const float* scale,
     Params G{mean, scale, quat, rho};
     const CamF cf = camf(cam, opts);
     float4* mom = reinterpret_cast<float4*>(base + L.mom);
-    TileOp op{rect, M, L.tiles_x, L.tiles_per_view};
+    float4* srec = fused_lists(L.n_tiles) ? reinterpret_cast<float4*>(base + T.srec) : nullptr;
+    TileOp op{rect, M, L.tiles_x, L.tiles_per_view, rec, srec};
     int launches = 0;
     uint64_t* sorted = nullptr;
     // fused key spaces: projection and lists in one cooperative launch when the grid fits
@@ -1170,7 +1198,7 @@ r2g_status r2g::rasterize_impl(int64_t M, const float* mean, const float* scale,
     }
     const float Tq = -0.5f * kLog2e * opts->Q;
     prof_begin(P_SPLAT_FWD, stream);
-    const FwdArgs fa{rec, ranges, sorted, items, item_st, partial, item_off, key_done};
+    const FwdArgs fa{rec, srec, ranges, sorted, items, item_st, partial, item_off, key_done};
     if (opts->count_pairs)
         launch_fwd<true>(opts->tile_w, opts->tile_h, fa, M, L, T.icap, cam->H, cam->W, Tq, image, st, stream);
     else
@@ -1213,7 +1241,8 @@ r2g_status r2g::rasterize_backward_impl(int64_t M, const float* mean, const floa
     const float Tq = -0.5f * kLog2e * opts->Q;
     if (parts & kRasterBwdMoments) {
         prof_begin(P_SPLAT_BWD, stream);
-        launch_bwd(opts->tile_w, opts->tile_h, rec, ranges, sorted, items, item_st, T.icap, M, L, cam->H, cam->W,
+        const float4* srec = fused_lists(L.n_tiles) ? reinterpret_cast<const float4*>(base + T.srec) : nullptr;
+        launch_bwd(opts->tile_w, opts->tile_h, rec, srec, ranges, sorted, items, item_st, T.icap, M, L, cam->H, cam->W,
                    Tq, dimage, mom, stream);
         prof_end(P_SPLAT_BWD, stream);
         note_launches(1);

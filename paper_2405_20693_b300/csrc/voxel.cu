@@ -191,6 +191,8 @@ __global__ void __launch_bounds__(256) k_vox_project(Params G, const __grid_cons
 struct BrickEmitOp {
     const uint4* rect;
     long long M;
+
+    __device__ __forceinline__ void copy_rec(uint64_t, unsigned long long) const {}
     long long brick_base[kMaxGrids];
     int nbx[kMaxGrids], nby[kMaxGrids];
 
