@@ -550,6 +550,32 @@ def voxel_box_counter(sc):
     return count
 
 
+def job_totals(dist, ms: float, pairs: float, device):
+    """Whole-job (device ms, pairs) of a timed region across ranks: the slowest rank's
+    time and every rank's pairs (independent replicas; one process per GPU).  dist =
+    torch.distributed with an initialised process group, or None for one process."""
+    if dist is None:
+        return ms, pairs
+    import torch
+
+    tt = torch.tensor([ms, pairs], dtype=torch.float64, device=device)
+    mx = tt.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(tt, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(tt[1])
+
+
+def slowest(dist, seconds: float, device) -> float:
+    """The largest of a per-rank wall time over ranks (dist None: as is)."""
+    if dist is None:
+        return seconds
+    import torch
+
+    tt = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt[0])
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -674,14 +700,7 @@ def run_ours(args, rank, world, local_rank):
     r2g.r2g_profile_enable(False)
     r2g.r2g_profile_select(0xFFFFFFFF)
 
-    if dist:
-        tt = torch.tensor([ms, total_pairs], dtype=torch.float64, device=dev)
-        mx = tt.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
-        ms_job, pairs_job = float(mx[0]), float(tt[1])
-    else:
-        ms_job, pairs_job = ms, total_pairs
+    ms_job, pairs_job = job_totals(dist, ms, total_pairs, dev)
     value = pairs_job / (ms_job * 1e-3)
 
     # end to end through the public API: every step's inputs -- its measured view
@@ -738,10 +757,7 @@ def run_ours(args, rank, world, local_rank):
     assert n_read == args.steps
     e2e_s = time.perf_counter() - t0
     assert np.isfinite(loss_sum)
-    if dist:
-        tt = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt[0])
+    e2e_s = slowest(dist, e2e_s, dev)
     e2e_value = pairs_job / e2e_s
 
     if rank == 0:
