@@ -256,6 +256,9 @@ def measure_batched(dev, rounds=20, n_scans=16, seed=5):
     for sp in specs:
         G, cam, views, meas, _ = I.make_scan(sp, device=dev)
         scans.append(engine.Scan(G, views, meas, cam, n_out=sp.n_out, D=D_TV, device=dev, seed=sp.seed))
+    # each scan's tile shape by measurement (its fused step alone, state restored); both
+    # legs below use the chosen shapes
+    tuned = [sc.autotune_tile() for sc in scans]
     # one scan at a time: each scan's steps back to back on one stream, their entries
     # preloaded in a device table so the host only issues the calls
     stream = torch.cuda.current_stream()
@@ -301,6 +304,9 @@ def measure_batched(dev, rounds=20, n_scans=16, seed=5):
     return {"workload": f"{n_scans} uneven cone-beam scans (seed {seed}): M log-U[5k, 300k], 25/50/75 views, "
                         "256^2/512^2 detectors, 128^3/256^3 volumes, random init; one training iteration each per round",
             "gaussians": [sp.M for sp in specs],
+            "tiles": ["%dx%d" % min(t, key=t.get) for t in tuned],
+            "tile_note": "per scan, the tile shape with the shortest fused step among 8x8, 16x16, 32x8, 32x32 "
+                         "(4 timed steps each on a restored copy of the state)",
             "plain_ms_per_iteration_of_all_scans": plain_ms, "batched_ms_per_round": batched_ms,
             "scans_per_hour_plain": n_scans * 3600.0 / (iters * plain_ms * 1e-3),
             "scans_per_hour_batched": n_scans * 3600.0 / (iters * batched_ms * 1e-3),

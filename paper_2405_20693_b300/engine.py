@@ -445,6 +445,50 @@ class Scan:
             J.dens_grad, J.dens_count = self.dens_grad.data_ptr(), self.dens_count.data_ptr()
         return J
 
+    def autotune_tile(self, tiles=((8, 8), (16, 16), (32, 8), (32, 32)), steps=4):
+        """Pick the rasterizer tile shape with the shortest fused training step for this
+        scan: each candidate is timed over `steps` steps (CUDA events, after one warm-up
+        step) on a copy of the state, which is restored afterwards, so the scan's
+        trajectory does not change.  Returns {tile: ms per step} and keeps the fastest."""
+        import ctypes
+
+        s = self.state
+        saved = [t.clone() for t in (s.raw, s.act, s.m, s.v)]
+        stream = torch.cuda.current_stream()
+        t = np.zeros((steps + 1, 8), np.int32)
+        f = t.view(np.float32)
+        g = np.random.Generator(np.random.PCG64(12345))
+        for k in range(steps + 1):
+            off = g.integers(0, self.n_out - self.D + 1, 3)
+            t[k, 0], t[k, 1] = int(g.integers(0, self.V)), self.it
+            f[k, 2:5] = -1.0 + off * (2.0 / self.n_out)
+        table = torch.as_tensor(t, device=self.device)
+        elem = ctypes.sizeof(r2g.RoundEntry)
+        sep = int(self.rast.opts.separate_lists)
+        times = {}
+        for tile in tiles:
+            self.rast = Rasterizer(self.M, 1, self.cam, tile=tile, device=self.device, biased=self.biased)
+            self.rast.opts.separate_lists = sep
+            self._size_workspaces(self.headroom, probes=2)
+            self.job = self._make_job()
+            r2g.r2g_train_step(self.job, table.data_ptr(), stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for k in range(1, steps + 1):
+                r2g.r2g_train_step(self.job, table.data_ptr() + k * elem, stream)
+            e1.record(stream)
+            e1.synchronize()
+            times[tuple(tile)] = e0.elapsed_time(e1) / steps
+            for dst, src in zip((s.raw, s.act, s.m, s.v), saved):
+                dst.copy_(src)
+        best = min(times, key=times.get)
+        self.rast = Rasterizer(self.M, 1, self.cam, tile=best, device=self.device, biased=self.biased)
+        self.rast.opts.separate_lists = sep
+        self._size_workspaces(self.headroom, probes=2)
+        self.job = self._make_job()
+        self.version += 1
+        return times
+
     def next_entry(self):
         """(view, iteration, TV patch origin) of this scan's next iteration."""
         v = int(self.rng.integers(0, self.V))
@@ -476,7 +520,8 @@ class BatchTrainer:
     CUDA graph and replayed; with graph=False the same calls are issued eagerly on
     the same streams."""
 
-    def __init__(self, scans, n_streams=None, graph=True, seed=0, device="cuda", separate_lists=None):
+    def __init__(self, scans, n_streams=None, graph=True, seed=0, device="cuda", separate_lists=None,
+                 autotune=False):
         self.scans = list(scans)
         self.J = len(self.scans)
         # with several scans in flight the list builds run as separate launches: a
@@ -488,6 +533,8 @@ class BatchTrainer:
                 sc.rast.opts.separate_lists = int(sep)
                 sc.job = sc._make_job()
                 sc.version += 1
+        # per-scan tile shape by measurement (each scan alone, state restored)
+        self.tiles = [sc.autotune_tile() if autotune else None for sc in self.scans]
         self.device = device
         self.table_host = torch.zeros((self.J, 8), dtype=torch.int32).pin_memory()
         self.table_dev = torch.zeros((self.J, 8), dtype=torch.int32, device=device)

@@ -161,3 +161,18 @@ def test_x3dgs_variant_trails_rectified_in_3d():
         per_view.append(psnr(host(vox.forward(mean, scale, quat, rv)), gt))
     assert max(per_view) < p3[0] - 2.0, (per_view, p3)
     assert max(per_view) - min(per_view) > 0.1, per_view
+
+
+def test_autotune_tile_restores_the_state():
+    """The tile autotuner times each shape on a copy of the state: afterwards the
+    parameters and Adam moments are exactly as before, the iteration count is unchanged,
+    and the scan runs with the fastest shape."""
+    G, cam, views, meas = small_scan(250, 3000, 128)
+    sc = engine.Scan(G, views, meas, cam, n_out=64, D=16)
+    before = [host(t) for t in (sc.state.raw, sc.state.act, sc.state.m, sc.state.v)]
+    it0 = sc.it
+    times = sc.autotune_tile()
+    after = [host(t) for t in (sc.state.raw, sc.state.act, sc.state.m, sc.state.v)]
+    assert all(np.array_equal(a, b) for a, b in zip(before, after)) and sc.it == it0
+    best = min(times, key=times.get)
+    assert (sc.rast.opts.tile_w, sc.rast.opts.tile_h) == best and len(times) == 4
