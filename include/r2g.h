@@ -232,6 +232,16 @@ size_t r2g_tv_workspace_size(int32_t G, int32_t D);
 r2g_status r2g_tv3d(int32_t G, int32_t D, const float* vol, float lambda_tv, float* loss, float* dvol, void* ws,
                     size_t ws_bytes, r2g_stream stream);
 
+/* lambda_tv x isotropic 3D total variation, an alternative to the anisotropic form
+ * of r2g_tv3d (Sec. 4.2.3 names 3D TV without fixing the norm): per volume, the
+ * mean over its D^3 voxels of sqrt(sum over the 3 axes of the squared forward
+ * difference + eps), a difference being 0 where the forward neighbour lies outside
+ * the volume; summed over the G volumes.  eps > 0 keeps the gradient finite in
+ * flat regions.  Same layouts, workspace (r2g_tv_workspace_size) and errors as
+ * r2g_tv3d; eps <= 0 returns R2G_E_INVAL. */
+r2g_status r2g_tv3d_iso(int32_t G, int32_t D, const float* vol, float lambda_tv, float eps, float* loss, float* dvol,
+                        void* ws, size_t ws_bytes, r2g_stream stream);
+
 /* The same TV loss and gradient as r2g_tv3d, for callers that cannot allocate
  * device memory where they call it (a host that fixes the device budget up front,
  * a real-time loop that must not stall on an allocation, a plugin that only
@@ -325,6 +335,9 @@ typedef struct {
      * dens_grad and 1 to dens_count; r2g_densify reads them. */
     float* dens_grad;
     float* dens_count;
+    /* TV form of the step: <= 0 the anisotropic TV of r2g_tv3d (the default), > 0 the
+     * isotropic TV of r2g_tv3d_iso with this eps */
+    float tv_eps;
 } r2g_job;
 
 r2g_status r2g_train_step(const r2g_job* job, const r2g_round_entry* entry, r2g_stream stream);

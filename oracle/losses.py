@@ -9,7 +9,9 @@ losses without formulas; the readings used here:
     "same" filtering, C1 = (0.01 L)^2, C2 = (0.03 L)^2 with L = 1, mean of the
     SSIM map over all pixels; D-SSIM = 1 - SSIM;
   * TV   = anisotropic L1: for each of the three axes, the mean of |forward
-    difference| over all valid differences, summed over the axes;
+    difference| over all valid differences, summed over the axes (the isotropic
+    form sqrt(sum of squared forward differences + eps), averaged over voxels, is
+    the option tv3d_iso);
   * Adam (Kingma & Ba) with the paper's per-group learning rates, decayed
     exponentially to 0.1x over the run (Sec. 5.1).
 Each function that returns a gradient derives it by hand; the tests pin those
@@ -112,6 +114,36 @@ def tv3d(vol: np.ndarray, lam_tv: float = LAMBDA_TV):
         g[tuple(hi)] += sg
         g[tuple(lo)] -= sg
     return lam_tv * loss, lam_tv * g
+
+
+def tv3d_iso(vol: np.ndarray, lam_tv: float = LAMBDA_TV, eps: float = 1e-6):
+    """lambda_tv * isotropic TV of a [Z, Y, X] volume: the mean over all voxels of
+    sqrt(sum_k d_k^2 + eps), d_k the forward difference along axis k (0 where the
+    neighbour lies outside); returns (loss, gradient).  With n(x) that root,
+    dn(x)/dV(x) = -sum_k d_k(x) / n(x) and dn(x)/dV(x + e_k) = d_k(x) / n(x)."""
+    vol = np.asarray(vol)
+    N = vol.size
+    d = []
+    for ax in range(3):
+        dk = np.zeros_like(vol)
+        lo = [slice(None)] * 3
+        hi = [slice(None)] * 3
+        lo[ax] = slice(0, -1)
+        hi[ax] = slice(1, None)
+        dk[tuple(lo)] = vol[tuple(hi)] - vol[tuple(lo)]
+        d.append(dk)
+    n = np.sqrt(d[0] ** 2 + d[1] ** 2 + d[2] ** 2 + eps)
+    loss = n.mean()
+    g = np.zeros_like(vol)
+    for ax in range(3):
+        r = d[ax] / n
+        g -= r
+        lo = [slice(None)] * 3
+        hi = [slice(None)] * 3
+        lo[ax] = slice(0, -1)
+        hi[ax] = slice(1, None)
+        g[tuple(hi)] += r[tuple(lo)]
+    return lam_tv * loss, lam_tv * g / N
 
 
 # ----------------------------------------------------------------------------- optimizer

@@ -653,10 +653,17 @@ R2G_API r2g_status r2g_fdk_filter(int32_t V, const r2g_camera* cam, const float*
     const int P = ((W + 32 + 15) / 16) * 16 + 15;  // as in the kernel
     const int n_row = W + 2 * P;
     const size_t smem = sizeof(float) * (size_t)(n_row + n_row / kFiltJ + 8 + W + 2 * kFiltS + 2);
-    static thread_local bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_fdk_filter, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-        attr = true;
+    // the row's shared memory may exceed the 48 KB default: opt in once per device
+    // (idempotent, so racing first calls are harmless)
+    static bool attr_set[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+        if (cudaFuncSetAttribute(k_fdk_filter, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
+            cudaSuccess)
+            return fail(R2G_E_CUDA, "r2g_fdk_filter: shared memory attribute (%s)",
+                        cudaGetErrorString(cudaGetLastError()));
+        if (dev >= 0 && dev < 64) attr_set[dev] = true;
     }
     prof_begin(P_FDK_FILTER, stream);
     k_fdk_filter<<<(unsigned)((long long)V * cam->H), threads, smem, stream>>>(

@@ -358,6 +358,64 @@ __global__ void __launch_bounds__(256) k_tv3d(const float* __restrict__ vol, int
     }
 }
 
+// Isotropic TV: n(x) = sqrt(sum_k d_k(x)^2 + eps) with d_k(x) = V(x + e_k) - V(x)
+// (0 on the far face).  V(x) enters its own n with d(n)/dV(x) = -sum_k d_k(x) / n(x)
+// and the n of each backward neighbour x - e_k with d_k(x - e_k) / n(x - e_k), so a
+// thread reads its voxel, its 3 forward and 3 backward neighbours and the 6
+// diagonal ones that the backward neighbours' differences need (L1-resident).
+__device__ __forceinline__ float tv_fwd_diff(const float* vg, long long l, long long st, int co, int D, float c) {
+    return (co + 1 < D) ? vg[l + st] - c : 0.f;
+}
+
+__global__ void __launch_bounds__(256) k_tv3d_iso(const float* __restrict__ vol, int D, long long n, float inv_cnt,
+                                                  float lam, float eps, float* __restrict__ grad,
+                                                  float* __restrict__ partials) {
+    __shared__ float red[8];
+    const long long idx = (long long)blockIdx.x * 256 + threadIdx.x;
+    float part = 0.f;
+    if (idx < n) {
+        const long long D3 = (long long)D * D * D;
+        const long long g = idx / D3;
+        const long long l = idx - g * D3;
+        const int z = (int)(l / ((long long)D * D)), y = (int)((l / D) % D), x = (int)(l % D);
+        const float* vg = vol + g * D3;
+        const float c = vg[l];
+        const long long st[3] = {1, D, (long long)D * D};
+        const int co[3] = {x, y, z};
+        float d[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) d[a] = tv_fwd_diff(vg, l, st[a], co[a], D, c);
+        const float nrm = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2] + eps);
+        part = nrm;
+        float gr = -(d[0] + d[1] + d[2]) / nrm;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (co[a] == 0) continue;
+            const long long lb = l - st[a];
+            const float cb = vg[lb];
+            const float da = c - cb;
+            float s = da * da + eps;
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                if (b == a) continue;
+                const float db = tv_fwd_diff(vg, lb, st[b], co[b], D, cb);
+                s += db * db;
+            }
+            gr += da / sqrtf(s);
+        }
+        grad[idx] = lam * inv_cnt * gr;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float s = 0.f;
+        for (int w = 0; w < 8; ++w) s += red[w];
+        partials[blockIdx.x] = s;
+    }
+}
+
 Win gaussian_window() {
     double g[11], s = 0;
     for (int k = 0; k < 11; ++k) {
@@ -466,4 +524,24 @@ R2G_API r2g_status r2g_tv3d(int32_t G, int32_t D, const float* vol, float lambda
     prof_end(P_TV, stream);
     note_launches(2);
     return check_launch("r2g_tv3d");
+}
+
+R2G_API r2g_status r2g_tv3d_iso(int32_t G, int32_t D, const float* vol, float lambda_tv, float eps, float* loss,
+                                float* dvol, void* ws, size_t ws_bytes, r2g_stream stream) {
+    if (G < 1 || D < 2 || D > 1024) return fail(R2G_E_INVAL, "bad TV volume shape G=%d D=%d", G, D);
+    if (!vol || !loss || !dvol || !ws) return fail(R2G_E_INVAL, "NULL pointer");
+    if (!(eps > 0.f)) return fail(R2G_E_INVAL, "r2g_tv3d_iso: eps must be > 0 (got %g)", (double)eps);
+    const long long n = (long long)G * D * D * D;
+    const long long blocks = (n + 255) / 256;
+    if (blocks >= (1ll << 31)) return fail(R2G_E_INVAL, "TV volume too large");
+    if (ws_bytes < 4 * (size_t)blocks) return fail(R2G_E_INVAL, "TV workspace needs %zu bytes", 4 * (size_t)blocks);
+    float* partials = static_cast<float*>(ws);
+    // the mean over the D^3 voxels of each volume
+    const float inv_cnt = (float)(1.0 / ((double)D * D * D));
+    prof_begin(P_TV, stream);
+    k_tv3d_iso<<<(unsigned)blocks, 256, 0, stream>>>(vol, D, n, inv_cnt, lambda_tv, eps, dvol, partials);
+    k_finalize<<<1, 256, 0, stream>>>(partials, (int)blocks, 1, lambda_tv * inv_cnt, 0.f, 0.f, loss);
+    prof_end(P_TV, stream);
+    note_launches(2);
+    return check_launch("r2g_tv3d_iso");
 }

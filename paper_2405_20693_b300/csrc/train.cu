@@ -87,7 +87,10 @@ R2G_API r2g_status r2g_train_step(const r2g_job* job, const r2g_round_entry* ent
         return fail(R2G_E_CUDA, "r2g_train_step: fork failed (%s)", cudaGetErrorString(cudaGetLastError()));
     r2g_status e_tv = voxelize_impl(M, mean, scale, quat, rho, 1, &grid, entry->origin, J.Q3, J.vol, J.voxel_ws,
                                     J.voxel_ws_bytes, tv, false, J.ropts.separate_lists != 0);
-    if (!e_tv) e_tv = r2g_tv3d(1, J.D, J.vol, J.lambda_tv, J.loss + 1, J.dvol, J.tv_ws, J.tv_ws_bytes, tv);
+    if (!e_tv)
+        e_tv = J.tv_eps > 0.f
+                   ? r2g_tv3d_iso(1, J.D, J.vol, J.lambda_tv, J.tv_eps, J.loss + 1, J.dvol, J.tv_ws, J.tv_ws_bytes, tv)
+                   : r2g_tv3d(1, J.D, J.vol, J.lambda_tv, J.loss + 1, J.dvol, J.tv_ws, J.tv_ws_bytes, tv);
     if (!e_tv)
         e_tv = voxelize_backward_impl(M, mean, scale, quat, rho, 1, &grid, J.Q3, J.dvol, dmean, dscale, dquat, drho,
                                       J.voxel_ws, J.voxel_ws_bytes, tv,

@@ -315,9 +315,10 @@ class Scan:
     descriptor for r2g_train_step."""
 
     def __init__(self, G, views_np, meas_np, cam, n_out=256, D=32, tile=None, total_iters=30000,
-                 device="cuda", headroom=1.5, seed=0, biased=False):
+                 device="cuda", headroom=1.5, seed=0, biased=False, tv_eps=0.0):
         self.state = TrainState(G, device=device)
         self.biased = bool(biased)
+        self.tv_eps = float(tv_eps)   # > 0: isotropic TV with this eps; 0: anisotropic (default)
         self.version = 0              # bumped whenever the C job changes (densification)
         self.dens_grad = self.dens_count = None
         self.dens_schedule = None
@@ -441,6 +442,7 @@ class Scan:
         J.voxel_ws, J.voxel_ws_bytes = self.vox.ws.data_ptr(), self.vox.ws.numel()
         J.loss_ws, J.loss_ws_bytes = self.loss_ws.data_ptr(), self.loss_ws.numel()
         J.tv_ws, J.tv_ws_bytes = self.tv_ws.data_ptr(), self.tv_ws.numel()
+        J.tv_eps = self.tv_eps
         if self.dens_grad is not None:
             J.dens_grad, J.dens_count = self.dens_grad.data_ptr(), self.dens_count.data_ptr()
         return J

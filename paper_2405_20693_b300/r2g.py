@@ -73,7 +73,7 @@ class Job(ctypes.Structure):
                 ("raster_ws_bytes", ctypes.c_size_t), ("voxel_ws", ctypes.c_void_p),
                 ("voxel_ws_bytes", ctypes.c_size_t), ("loss_ws", ctypes.c_void_p),
                 ("loss_ws_bytes", ctypes.c_size_t), ("tv_ws", ctypes.c_void_p), ("tv_ws_bytes", ctypes.c_size_t),
-                ("dens_grad", ctypes.c_void_p), ("dens_count", ctypes.c_void_p)]
+                ("dens_grad", ctypes.c_void_p), ("dens_count", ctypes.c_void_p), ("tv_eps", ctypes.c_float)]
 
 
 def camera(cam) -> Camera:
@@ -150,6 +150,7 @@ def lib():
             "r2g_tv_workspace_size": (_SZ, [_I32, _I32]),
             "r2g_tv3d": (_I32, [_I32, _I32, _P, _F, _P, _P, _P, _SZ, _P]),
             "r2g_tv3d_noalloc": (_I32, [_I32, _I32, _P, _F, _P, _P, _P]),
+            "r2g_tv3d_iso": (_I32, [_I32, _I32, _P, _F, _F, _P, _P, _P, _SZ, _P]),
             "r2g_adam_step": (_I32, [_I64, _P, _P, _P, _P, _P, _I32, _P, _P]),
             "r2g_poll": (_I32, [_P, _SZ, _P, _P]),
             "r2g_train_step": (_I32, [_P, _P, _P]),
@@ -379,6 +380,13 @@ def r2g_tv3d(vol, lambda_tv, loss, dvol, ws, stream=None):
     G, D = vol.shape[0], vol.shape[1]
     _check(lib().r2g_tv3d(G, D, _ptr(vol), float(lambda_tv), _ptr(loss), _ptr(dvol), _ptr(ws), ws.numel(),
                           _stream(stream)))
+
+
+def r2g_tv3d_iso(vol, lambda_tv, eps, loss, dvol, ws, stream=None):
+    _f32(vol, loss, dvol)
+    G, D = vol.shape[0], vol.shape[1]
+    _check(lib().r2g_tv3d_iso(G, D, _ptr(vol), float(lambda_tv), float(eps), _ptr(loss), _ptr(dvol), _ptr(ws),
+                              ws.numel(), _stream(stream)))
 
 
 def r2g_tv3d_noalloc(vol, lambda_tv, loss, dvol, stream=None):

@@ -62,6 +62,9 @@ def test_host_side_argument_errors(lib):
     assert lib.r2g_tv_workspace_size(1, 1) == 0
     st = lib.r2g_tv3d(1, 1, None, 0.05, None, None, None, 0, None)
     assert st == r2g.R2G_E_INVAL
+    fake = ctypes.c_void_p(0x1000)  # never dereferenced: the eps check fails first
+    st = lib.r2g_tv3d_iso(1, 4, fake, 0.05, 0.0, fake, fake, fake, 4096, None)
+    assert st == r2g.R2G_E_INVAL
 
 
 def test_host_side_argument_errors_of_the_other_entry_points(lib):

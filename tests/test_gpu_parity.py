@@ -292,6 +292,29 @@ def test_tv_matches_oracle():
     assert np.abs(host(grad) - G).max() <= 1e-6 * np.abs(G).max()
 
 
+def test_isotropic_tv_matches_oracle():
+    """Isotropic TV over 3 volumes of a ragged edge (13: the last block is partial),
+    plus the flat volume (all differences 0: loss sqrt(eps) per volume, gradient 0)."""
+    eps = 1e-6
+    v = I.rng(19).standard_normal((3, 13, 13, 13)).astype(np.float32)
+    vd = dev(v)
+    loss = torch.zeros(1, device="cuda")
+    grad = torch.empty_like(vd)
+    ws = torch.empty(r2g.r2g_tv_workspace_size(3, 13), dtype=torch.uint8, device="cuda")
+    r2g.r2g_tv3d_iso(vd, 0.05, eps, loss, grad, ws)
+    ref = [losses.tv3d_iso(v[k].astype(np.float64), 0.05, eps) for k in range(3)]
+    L = sum(r[0] for r in ref)
+    G = np.stack([r[1] for r in ref])
+    assert abs(float(loss) - L) <= 1e-5 * abs(L)
+    assert np.abs(host(grad) - G).max() <= 1e-5 * np.abs(G).max()
+    flat = torch.full((1, 6, 6, 6), 0.3, device="cuda")
+    g2 = torch.empty_like(flat)
+    ws2 = torch.empty(r2g.r2g_tv_workspace_size(1, 6), dtype=torch.uint8, device="cuda")
+    r2g.r2g_tv3d_iso(flat, 0.05, eps, loss, g2, ws2)
+    assert float(loss) == pytest.approx(0.05 * np.sqrt(eps), rel=1e-5)
+    assert float(g2.abs().max()) == 0.0
+
+
 def test_adam_matches_oracle():
     G = I.uniform_gaussians(333, 10)
     st = engine.TrainState(G)

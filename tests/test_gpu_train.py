@@ -176,3 +176,20 @@ def test_autotune_tile_restores_the_state():
     assert all(np.array_equal(a, b) for a, b in zip(before, after)) and sc.it == it0
     best = min(times, key=times.get)
     assert (sc.rast.opts.tile_w, sc.rast.opts.tile_h) == best and len(times) == 4
+
+
+def test_train_step_isotropic_tv_option():
+    """With tv_eps > 0 the fused step takes the isotropic TV of the voxelized patch:
+    its TV loss matches the oracle's isotropic TV of the oracle's patch."""
+    G, cam, views, meas = small_scan(200, 3000, 128)
+    sc = engine.Scan(G, views, meas, cam, n_out=64, D=16, tv_eps=1e-6)
+    act = [host(t) for t in sc.state.views_of(sc.state.act)]
+    origin = (0.0, -0.25, -0.5)
+    table = entry_table([(1, 0, origin)])
+    r2g.r2g_train_step(sc.job, table.data_ptr(), torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    Ga = I.GaussianSet(act[1], act[2], act[0], act[3])
+    gd = np.asarray(I.grid_desc(origin, (2 / 64,) * 3, (16, 16, 16)), np.float32).astype(np.float64)
+    vol, _ = core.voxelize(Ga, gd, engine.Q_VOXEL)
+    Ltv, _ = losses.tv3d_iso(vol.reshape(16, 16, 16), engine.LAMBDA_TV, 1e-6)
+    assert abs(host(sc.loss)[1] - Ltv) <= 1e-4 * abs(Ltv) + 1e-7

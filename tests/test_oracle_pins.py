@@ -675,3 +675,26 @@ def test_volume_ssim_orientations_permute_with_the_axes():
     assert myz["axial"] == pytest.approx(m["coronal"], abs=1e-14)
     assert myz["coronal"] == pytest.approx(m["axial"], abs=1e-14)
     assert len({round(m[o], 6) for o in ("axial", "coronal", "sagittal")}) == 3
+
+
+def test_isotropic_tv_closed_form_and_gradient():
+    """A linear ramp v = a x + b y + c z: interior voxels have sqrt(a^2 + b^2 + c^2 + eps),
+    voxels on the far faces lose that axis' term; a constant volume gives sqrt(eps);
+    the hand gradient equals the complex-step derivative (the square root is analytic
+    for eps > 0)."""
+    D = 5
+    a, b, c, eps = 0.3, -0.2, 0.1, 1e-6
+    z, y, x = np.meshgrid(np.arange(D), np.arange(D), np.arange(D), indexing="ij")
+    vol = a * x + b * y + c * z
+    ex = np.where(x < D - 1, a * a, 0) + np.where(y < D - 1, b * b, 0) + np.where(z < D - 1, c * c, 0)
+    loss, _ = losses.tv3d_iso(vol, 1.0, eps)
+    assert loss == pytest.approx(np.sqrt(ex + eps).mean(), rel=1e-13)
+    assert losses.tv3d_iso(np.full((3, 4, 5), 0.7), 1.0, eps)[0] == pytest.approx(np.sqrt(eps), rel=1e-12)
+    g = np.random.default_rng(5).uniform(0, 1, (4, 5, 6))
+    _, grad = losses.tv3d_iso(g, 0.05, eps)
+    h = 1e-30
+    for idx in [(0, 0, 0), (1, 2, 3), (3, 4, 5), (2, 0, 5)]:
+        gc = g.astype(np.complex128)
+        gc[idx] += 1j * h
+        cs = losses.tv3d_iso(gc, 0.05, eps)[0].imag / h
+        assert abs(cs - grad[idx]) <= 1e-12 * max(1.0, abs(cs)), (idx, cs, grad[idx])
