@@ -677,6 +677,10 @@ def run_ours(args, rank, world, local_rank):
     vox_pairs = [counted[seq[k]][1] for k in range(t0_steps, t0_steps + args.steps)]
     box_pairs = [counted[seq[k]][2] + counted[seq[k]][3] for k in range(t0_steps, t0_steps + args.steps)]
     total_pairs = float(sum(pix_pairs) + sum(vox_pairs))
+    # the state at the start of the timed region: the end-to-end leg restarts from it,
+    # so that both legs run the same steps on the same parameters (the same pairs)
+    st = sc.state
+    start_state = [t.clone() for t in (st.raw, st.act, st.m, st.v)]
 
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     r2g.r2g_profile_enable(True, 2 * args.steps + 64)
@@ -709,56 +713,36 @@ def run_ours(args, rank, world, local_rank):
     ms_job, pairs_job = job_totals(dist, ms, total_pairs, dev)
     value = pairs_job / (ms_job * 1e-3)
 
-    # end to end through the public API: every step's inputs -- its measured view
-    # (H x W floats), the view's geometry row and its round entry -- go host -> device
-    # from pinned memory into one of NS staging slots on a copy stream, the fused step
-    # (a C job whose view table and measurements are the slots) runs on the compute
-    # stream once its slot has arrived, and its loss comes back to pinned host memory;
-    # copies overlap the steps before them, and the host reads step k's loss after
-    # queueing step k + NS - 1
+    # end to end through the public API (engine.HostFeed over r2g_train_step_host):
+    # every step's inputs -- its measured view (H x W floats), the view's geometry
+    # row and its round entry -- go host -> device from pinned memory into one of NS
+    # staging slots on a copy stream, the fused step runs once its slot has arrived,
+    # and its losses come back to pinned host memory; copies overlap the steps
+    # before them, and the host reads step k's losses after queueing step k + NS - 1
     NS = 3
-    H, W = cam.H, cam.W
     meas_host = torch.from_numpy(np.ascontiguousarray(meas_np, np.float32)).pin_memory()
     views_host = torch.from_numpy(np.ascontiguousarray(views_np, np.float32)).pin_memory()
     ent_host = torch.from_numpy(tab.copy()).pin_memory()
-    meas_stage = torch.empty((NS, H, W), dtype=torch.float32, device=dev)
-    views_stage = torch.empty((NS, 12), dtype=torch.float32, device=dev)
-    ent_stage = torch.empty((NS, 8), dtype=torch.int32, device=dev)
-    job2 = r2g.Job.from_buffer_copy(sc.job)
-    job2.V, job2.views, job2.meas = NS, views_stage.data_ptr(), meas_stage.data_ptr()
-    copy_stream = torch.cuda.Stream(device=dev)
-    ev_in = [torch.cuda.Event() for _ in range(NS)]
-    ev_done = [torch.cuda.Event() for _ in range(NS)]
-    loss_host = [torch.empty(2, dtype=torch.float32).pin_memory() for _ in range(NS)]
+    ent0 = ent_host.data_ptr()
+    feed = engine.HostFeed(sc, meas_host, views_host, n_slots=NS, stream=stream)
+    for j in range(NS):                            # creates the copy stream and events
+        feed.step(seq[j][0], ent0 + 32 * j)
+    feed.finish()
+    for t, saved in zip((st.raw, st.act, st.m, st.v), start_state):
+        t.copy_(saved)
     loss_sum, n_read = 0.0, 0
-    for k in range(t0_steps, t0_steps + args.steps):
-        ent_host[k, 0] = (k - t0_steps) % NS      # the step's view is its staging slot
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     t0 = time.perf_counter()
     for j in range(args.steps):
         k = t0_steps + j
-        v, slot = seq[k][0], j % NS
-        if j >= NS:                                # step j - NS: done, loss read below already
-            ev_done[slot].synchronize()
-        with torch.cuda.stream(copy_stream):
-            meas_stage[slot].copy_(meas_host[v], non_blocking=True)
-            views_stage[slot].copy_(views_host[v], non_blocking=True)
-            ent_stage[slot].copy_(ent_host[k], non_blocking=True)
-            ev_in[slot].record(copy_stream)
-        stream.wait_event(ev_in[slot])
-        r2g.r2g_train_step(job2, ent_stage[slot].data_ptr(), stream)
-        loss_host[slot].copy_(sc.loss, non_blocking=True)
-        ev_done[slot].record(stream)
-        if j >= NS - 1:
-            r = j - (NS - 1)
-            ev_done[r % NS].synchronize()
-            loss_sum += float(loss_host[r % NS][0])
+        out = feed.step(seq[k][0], ent0 + 32 * k)
+        if out is not None:
+            loss_sum += out[0]
             n_read += 1
-    for r in range(max(0, args.steps - (NS - 1)), args.steps):
-        ev_done[r % NS].synchronize()
-        loss_sum += float(loss_host[r % NS][0])
+    for out in feed.finish():
+        loss_sum += out[0]
         n_read += 1
     assert n_read == args.steps
     e2e_s = time.perf_counter() - t0
@@ -820,9 +804,11 @@ def run_ours(args, rank, world, local_rank):
                        "tile": "32x32", "bricks": "8^3"},
             "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": 4 * cam.H * cam.W + 48 + 32,
                     "d2h_bytes_per_step": 8,
-                    "note": "per step: the measured view, its geometry row and its round entry copied from pinned "
-                            "host memory into one of three device slots on a copy stream (overlapping the steps "
-                            "before it), the fused step through r2g_train_step, the loss read back to the host"},
+                    "note": "per step, one r2g_train_step_host call (engine.HostFeed): the measured view, its "
+                            "geometry row and its round entry copied from pinned host memory into one of three "
+                            "device slots on a copy stream (overlapping the steps before it), the fused step, the "
+                            "two losses read back to pinned host memory and read by the host; the same steps as the "
+                            "device-timed leg, from the same starting state"},
             "gpu_launches": int(launches),
             "roofline": roof,
             "kernels_ms_per_step": breakdown,

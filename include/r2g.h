@@ -342,6 +342,36 @@ typedef struct {
 
 r2g_status r2g_train_step(const r2g_job* job, const r2g_round_entry* entry, r2g_stream stream);
 
+/* Staging slots of r2g_train_step_host (all caller-owned): n_slots in 1..16. */
+typedef struct {
+    int32_t n_slots;
+    float* meas;                      /* device [n_slots][H][W] */
+    float* views;                     /* device [n_slots][12] */
+    r2g_round_entry* entries;         /* device [n_slots] */
+    r2g_round_entry* entries_host;    /* pinned host [n_slots]; written by the call */
+    float* loss;                      /* device [n_slots][2]: the step's losses (instead of job->loss) */
+} r2g_staging;
+
+/* One training iteration fed from HOST memory: the step's measured projection
+ * meas_host[H][W], its geometry row view_host[12] and its round entry (host
+ * memory, read during the call; its view field is ignored) are copied into staging slot step % n_slots on a copy stream
+ * owned by the library (one per caller stream, created by the first call), the
+ * iteration of r2g_train_step runs on `stream` once they have arrived (with the
+ * job's view table, measurements and loss buffer replaced by the slot's), and its
+ * two losses are copied to loss_host[2] on a second library stream, so that no copy
+ * sits between two steps on `stream`.  meas_host, view_host and loss_host should be pinned for
+ * the copies to overlap; step counts the caller's calls from 0.  Before rewriting
+ * a slot the call BLOCKS until the step that used it last (step - n_slots) has
+ * finished, so at most n_slots steps are in flight.  loss_host of a step is valid
+ * once r2g_train_step_host_wait(stg, step, stream) has returned; the caller must not
+ * reuse it for another step before then.  Not capturable (host waits). */
+r2g_status r2g_train_step_host(const r2g_job* job, const r2g_staging* stg, int64_t step, const float* meas_host,
+                               const float* view_host, const r2g_round_entry* entry_host, float* loss_host,
+                               r2g_stream stream);
+/* Blocks until step `step` of r2g_train_step_host on `stream` has finished (its
+ * loss_host filled); returns at once for a slot that never ran. */
+r2g_status r2g_train_step_host_wait(const r2g_staging* stg, int64_t step, r2g_stream stream);
+
 /* Copy n round entries from PAGE-LOCKED host memory `src` to device `dst` on
  * `stream` (an asynchronous copy; inside a captured graph the copy reads `src`
  * each time the graph runs, so the host rewrites it between replays). */

@@ -32,6 +32,40 @@ struct SideStream {
 std::mutex g_side_mu;
 std::map<std::pair<int, cudaStream_t>, SideStream> g_side;
 
+// Copy stream and per-slot events of r2g_train_step_host, per (device, caller stream).
+constexpr int kMaxSlots = 16;
+// `in` carries the host -> device copies, `out` the loss read-back (kept off the
+// caller's stream, where a copy between two steps would hold the next step back).
+struct HostStage {
+    cudaStream_t in_s, out_s;
+    cudaEvent_t in[kMaxSlots], step[kMaxSlots], done[kMaxSlots];
+};
+
+std::map<std::pair<int, cudaStream_t>, HostStage> g_stage;
+
+r2g_status host_stage_for(cudaStream_t caller, HostStage** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return fail(R2G_E_CUDA, "r2g_train_step_host: no current device");
+    std::lock_guard<std::mutex> lk(g_side_mu);
+    const auto key = std::make_pair(dev, caller);
+    auto it = g_stage.find(key);
+    if (it == g_stage.end()) {
+        HostStage hs{};
+        bool ok = cudaStreamCreateWithFlags(&hs.in_s, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaStreamCreateWithFlags(&hs.out_s, cudaStreamNonBlocking) == cudaSuccess;
+        for (int k = 0; ok && k < kMaxSlots; ++k)
+            ok = cudaEventCreateWithFlags(&hs.in[k], cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&hs.step[k], cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&hs.done[k], cudaEventDisableTiming) == cudaSuccess;
+        if (!ok)
+            return fail(R2G_E_CUDA, "r2g_train_step_host: creating the copy stream failed (%s)",
+                        cudaGetErrorString(cudaGetLastError()));
+        it = g_stage.emplace(key, hs).first;
+    }
+    *out = &it->second;
+    return R2G_OK;
+}
+
 r2g_status side_stream_for(cudaStream_t caller, SideStream** out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return fail(R2G_E_CUDA, "r2g_train_step: no current device");
@@ -116,6 +150,64 @@ R2G_API r2g_status r2g_train_step(const r2g_job* job, const r2g_round_entry* ent
     return rasterize_backward_impl(M, mean, scale, quat, rho, 1, J.views, view_sel, &J.cam, &J.ropts, J.dimage,
                                    dmean, dscale, dquat, drho, J.raster_ws, J.raster_ws_bytes, stream,
                                    kRasterBwdChain, &adam);
+}
+
+R2G_API r2g_status r2g_train_step_host(const r2g_job* job, const r2g_staging* stg, int64_t step,
+                                       const float* meas_host, const float* view_host,
+                                       const r2g_round_entry* entry_host, float* loss_host, r2g_stream stream) {
+    if (!job || !stg || !meas_host || !view_host || !entry_host || !loss_host)
+        return fail(R2G_E_INVAL, "r2g_train_step_host: NULL argument");
+    if (stg->n_slots < 1 || stg->n_slots > kMaxSlots || !stg->meas || !stg->views || !stg->entries ||
+        !stg->entries_host || !stg->loss || step < 0)
+        return fail(R2G_E_INVAL, "r2g_train_step_host: bad staging (n_slots %d, step %lld)", stg->n_slots,
+                    (long long)step);
+    if (job->cam.H < 1 || job->cam.W < 1 || !job->loss) return fail(R2G_E_INVAL, "r2g_train_step_host: bad job");
+    HostStage* hs = nullptr;
+    r2g_status e = host_stage_for(stream, &hs);
+    if (e) return e;
+    const int slot = (int)(step % stg->n_slots);
+    const size_t img = (size_t)job->cam.H * (size_t)job->cam.W;
+    // the step that used this slot last (step - n_slots) must be done, its losses
+    // read back, before the slot's pinned entry, device inputs and losses are
+    // rewritten (no wait if it never ran)
+    if (cudaEventSynchronize(hs->done[slot]) != cudaSuccess)
+        return fail(R2G_E_CUDA, "r2g_train_step_host: waiting for slot %d (%s)", slot,
+                    cudaGetErrorString(cudaGetLastError()));
+    stg->entries_host[slot] = *entry_host;
+    stg->entries_host[slot].view = slot;  // the slot holds the step's view and measurement
+    if (cudaMemcpyAsync(stg->meas + slot * img, meas_host, img * sizeof(float), cudaMemcpyHostToDevice, hs->in_s) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(stg->views + 12 * (size_t)slot, view_host, 12 * sizeof(float), cudaMemcpyHostToDevice,
+                        hs->in_s) != cudaSuccess ||
+        cudaMemcpyAsync(stg->entries + slot, stg->entries_host + slot, sizeof(r2g_round_entry),
+                        cudaMemcpyHostToDevice, hs->in_s) != cudaSuccess ||
+        cudaEventRecord(hs->in[slot], hs->in_s) != cudaSuccess || cudaStreamWaitEvent(stream, hs->in[slot], 0) != cudaSuccess)
+        return fail(R2G_E_CUDA, "r2g_train_step_host: staging copy failed (%s)", cudaGetErrorString(cudaGetLastError()));
+    r2g_job J = *job;
+    J.V = stg->n_slots;
+    J.views = stg->views;
+    J.meas = stg->meas;
+    J.loss = stg->loss + 2 * (size_t)slot;
+    e = r2g_train_step(&J, stg->entries + slot, stream);
+    if (e) return e;
+    if (cudaEventRecord(hs->step[slot], stream) != cudaSuccess ||
+        cudaStreamWaitEvent(hs->out_s, hs->step[slot], 0) != cudaSuccess ||
+        cudaMemcpyAsync(loss_host, J.loss, 2 * sizeof(float), cudaMemcpyDeviceToHost, hs->out_s) != cudaSuccess ||
+        cudaEventRecord(hs->done[slot], hs->out_s) != cudaSuccess)
+        return fail(R2G_E_CUDA, "r2g_train_step_host: loss read-back failed (%s)",
+                    cudaGetErrorString(cudaGetLastError()));
+    return R2G_OK;
+}
+
+R2G_API r2g_status r2g_train_step_host_wait(const r2g_staging* stg, int64_t step, r2g_stream stream) {
+    if (!stg || stg->n_slots < 1 || stg->n_slots > kMaxSlots || step < 0)
+        return fail(R2G_E_INVAL, "r2g_train_step_host_wait: bad arguments");
+    HostStage* hs = nullptr;
+    r2g_status e = host_stage_for(stream, &hs);
+    if (e) return e;
+    if (cudaEventSynchronize(hs->done[step % stg->n_slots]) != cudaSuccess)
+        return fail(R2G_E_CUDA, "r2g_train_step_host_wait: %s", cudaGetErrorString(cudaGetLastError()));
+    return R2G_OK;
 }
 
 R2G_API r2g_status r2g_upload_round(r2g_round_entry* dst, const r2g_round_entry* src, int32_t n, r2g_stream stream) {

@@ -511,6 +511,60 @@ class Scan:
         return r2g.r2g_poll(self.rast.ws)[0] != r2g.R2G_OK or r2g.r2g_poll(self.vox.ws)[0] != r2g.R2G_OK
 
 
+class HostFeed:
+    """Training one scan from host memory (r2g_train_step_host): its measured
+    projections [V][H][W] and view table [V][12] stay in pinned host memory; each
+    step's measurement, geometry row and round entry go into one of n_slots device
+    staging slots on a copy stream while the steps before it run, and its losses
+    come back to pinned host memory.  step() returns the losses of the step
+    n_slots - 1 calls earlier (None for the first n_slots - 1 calls); finish()
+    returns those still in flight."""
+
+    def __init__(self, scan: "Scan", meas_host: torch.Tensor, views_host: torch.Tensor, n_slots=3, stream=None):
+        if not (meas_host.is_pinned() and views_host.is_pinned()):
+            raise ValueError("HostFeed needs pinned host tensors")
+        H, W = scan.cam.H, scan.cam.W
+        if tuple(meas_host.shape[1:]) != (H, W) or views_host.shape[1] != 12:
+            raise ValueError("measurements must be [V][H][W] and views [V][12]")
+        dev = scan.device
+        self.scan, self.n = scan, int(n_slots)
+        self.meas_host, self.views_host = meas_host.contiguous(), views_host.contiguous()
+        self.meas_stage = torch.empty((self.n, H, W), dtype=torch.float32, device=dev)
+        self.views_stage = torch.empty((self.n, 12), dtype=torch.float32, device=dev)
+        self.ent_stage = torch.zeros((self.n, 8), dtype=torch.int32, device=dev)
+        self.ent_host = torch.zeros((self.n, 8), dtype=torch.int32).pin_memory()
+        self.loss_dev = torch.zeros((self.n, 2), dtype=torch.float32, device=dev)
+        self.loss_host = torch.zeros((self.n, 2), dtype=torch.float32).pin_memory()
+        self.loss_np = self.loss_host.numpy()
+        self.stg = r2g.Staging(self.n, self.meas_stage.data_ptr(), self.views_stage.data_ptr(),
+                               self.ent_stage.data_ptr(), self.ent_host.data_ptr(), self.loss_dev.data_ptr())
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._meas0, self._img = self.meas_host.data_ptr(), 4 * H * W
+        self._views0, self._loss0 = self.views_host.data_ptr(), self.loss_host.data_ptr()
+        self.k = 0   # steps queued
+        self.r = 0   # first step whose losses have not been returned
+
+    def _take(self):
+        r = self.r
+        r2g.r2g_train_step_host_wait(self.stg, r, self.stream)
+        self.r = r + 1
+        return float(self.loss_np[r % self.n, 0]), float(self.loss_np[r % self.n, 1])
+
+    def step(self, view: int, entry_ptr: int):
+        """Queue one iteration on the measurement and geometry of `view` with the
+        round entry at host address entry_ptr (read during the call)."""
+        k, n = self.k, self.n
+        r2g.r2g_train_step_host(self.scan.job, self.stg, k, self._meas0 + view * self._img, self._views0 + 48 * view,
+                                entry_ptr, self._loss0 + 8 * (k % n), self.stream)
+        self.k = k + 1
+        # step k + 1 reuses the loss buffer of step k + 1 - n: return that step's first
+        return self._take() if self.k - self.r >= n else None
+
+    def finish(self):
+        """Wait for every queued step; their losses, in step order."""
+        return [self._take() for _ in range(self.k - self.r)]
+
+
 class BatchTrainer:
     """Runs one training iteration of every resident scan per round.
 

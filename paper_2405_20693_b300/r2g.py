@@ -76,6 +76,11 @@ class Job(ctypes.Structure):
                 ("dens_grad", ctypes.c_void_p), ("dens_count", ctypes.c_void_p), ("tv_eps", ctypes.c_float)]
 
 
+class Staging(ctypes.Structure):
+    _fields_ = [("n_slots", ctypes.c_int32), ("meas", ctypes.c_void_p), ("views", ctypes.c_void_p),
+                ("entries", ctypes.c_void_p), ("entries_host", ctypes.c_void_p), ("loss", ctypes.c_void_p)]
+
+
 def camera(cam) -> Camera:
     """Camera struct from an ``inputs.Camera``-like object."""
     return Camera(int(cam.beam), int(cam.H), int(cam.W), float(cam.L_SD), float(cam.pitch_u), float(cam.pitch_v),
@@ -154,6 +159,8 @@ def lib():
             "r2g_adam_step": (_I32, [_I64, _P, _P, _P, _P, _P, _I32, _P, _P]),
             "r2g_poll": (_I32, [_P, _SZ, _P, _P]),
             "r2g_train_step": (_I32, [_P, _P, _P]),
+            "r2g_train_step_host": (_I32, [_P, _P, _I64, _P, _P, _P, _P, _P]),
+            "r2g_train_step_host_wait": (_I32, [_P, _I64, _P]),
             "r2g_upload_round": (_I32, [_P, _P, _I32, _P]),
             "r2g_profile_enable": (_I32, [_I32, _I32]),
             "r2g_profile_select": (_I32, [ctypes.c_uint32]),
@@ -438,6 +445,18 @@ def r2g_train_step(job: Job, entry_ptr: int, stream=None):
     """One training iteration of one scan; entry_ptr is the device address of its
     round entry (r2g_round_entry)."""
     _check(lib().r2g_train_step(ctypes.byref(job), ctypes.c_void_p(int(entry_ptr)), _stream(stream)))
+
+
+def r2g_train_step_host(job: Job, stg: Staging, step: int, meas_ptr: int, view_ptr: int, entry_ptr: int,
+                        loss_ptr: int, stream=None):
+    """One training iteration fed from host memory (addresses of the step's pinned
+    measured projection, geometry row, round entry and 2-float loss buffer)."""
+    _check(lib().r2g_train_step_host(ctypes.byref(job), ctypes.byref(stg), int(step), meas_ptr, view_ptr, entry_ptr,
+                                     loss_ptr, _stream(stream)))
+
+
+def r2g_train_step_host_wait(stg: Staging, step: int, stream=None):
+    _check(lib().r2g_train_step_host_wait(ctypes.byref(stg), int(step), _stream(stream)))
 
 
 def r2g_upload_round(dst_dev, src_pinned, n: int, stream=None):

@@ -62,7 +62,12 @@ def test_host_side_argument_errors(lib):
     assert lib.r2g_tv_workspace_size(1, 1) == 0
     st = lib.r2g_tv3d(1, 1, None, 0.05, None, None, None, 0, None)
     assert st == r2g.R2G_E_INVAL
-    fake = ctypes.c_void_p(0x1000)  # never dereferenced: the eps check fails first
+    stg = r2g.Staging(0, 0x1000, 0x1000, 0x1000, 0x1000, 0x1000)  # n_slots 0: rejected before any CUDA call
+    job = r2g.Job()
+    fake = ctypes.c_void_p(0x1000)  # never dereferenced: the argument checks fail first
+    assert lib.r2g_train_step_host(ctypes.byref(job), ctypes.byref(stg), 0, fake, fake, fake, fake,
+                                   None) == r2g.R2G_E_INVAL
+    assert lib.r2g_train_step_host_wait(ctypes.byref(stg), 0, None) == r2g.R2G_E_INVAL
     st = lib.r2g_tv3d_iso(1, 4, fake, 0.05, 0.0, fake, fake, fake, 4096, None)
     assert st == r2g.R2G_E_INVAL
 

@@ -193,3 +193,34 @@ def test_train_step_isotropic_tv_option():
     vol, _ = core.voxelize(Ga, gd, engine.Q_VOXEL)
     Ltv, _ = losses.tv3d_iso(vol.reshape(16, 16, 16), engine.LAMBDA_TV, 1e-6)
     assert abs(host(sc.loss)[1] - Ltv) <= 1e-4 * abs(Ltv) + 1e-7
+
+
+def test_host_feed_equals_device_resident_steps():
+    """Ten iterations fed from pinned host memory (r2g_train_step_host through
+    engine.HostFeed, 3 staging slots) return the losses of the same iterations run
+    on device-resident tables: the first step's exactly (same state, deterministic
+    forward), the later ones within 1e-4 (the gradient moments are summed with float
+    atomics, so the states drift apart in their last bits)."""
+    G, cam, views, meas = small_scan(201, 3000, 128)
+    rows = [(v % 8, it, ((-1) ** it * 0.25, -0.25, 0.125 * (it % 3))) for it, v in enumerate([3, 1, 6, 0, 7, 2, 5, 4, 1, 3])]
+    a = engine.Scan(G, views, meas, cam, n_out=64, D=16)
+    b = engine.Scan(G, views, meas, cam, n_out=64, D=16)
+    tab = entry_table(rows)
+    losses_a = []
+    for j in range(len(rows)):
+        r2g.r2g_train_step(a.job, tab[j].data_ptr(), torch.cuda.current_stream())
+        losses_a.append(host(a.loss).copy())
+    ent_host = tab.cpu().pin_memory()
+    feed = engine.HostFeed(b, torch.from_numpy(np.ascontiguousarray(meas, np.float32)).pin_memory(),
+                           torch.from_numpy(np.ascontiguousarray(views, np.float32)).pin_memory(), n_slots=3)
+    got = []
+    for j, (v, _, _) in enumerate(rows):
+        out = feed.step(v, ent_host.data_ptr() + 32 * j)
+        if out is not None:
+            got.append(out)
+    got += feed.finish()
+    torch.cuda.synchronize()
+    assert len(got) == len(rows)
+    assert (np.float32(got[0][0]), np.float32(got[0][1])) == (np.float32(losses_a[0][0]), np.float32(losses_a[0][1]))
+    for j, ((l0, l1), want) in enumerate(zip(got, losses_a)):
+        assert abs(l0 - want[0]) <= 1e-4 * abs(want[0]) and abs(l1 - want[1]) <= 1e-4 * abs(want[1]), (j, l0, l1, want)
