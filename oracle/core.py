@@ -75,11 +75,14 @@ def lib():
     return _lib
 
 
-def _camv(cam, jmode: int = 0, biased: bool = False) -> np.ndarray:
+def _camv(cam, jmode: int = 0, biased: bool = False, dilation: float = 0.0) -> np.ndarray:
     """Camera vector for the C entry points; jmode 1 plants the depth-row Jacobian
     (used only by the test that pins the EWA reading); biased selects the X-3DGS
-    amplitude rho_hat = rho in place of Eq. 7's mu rho."""
-    return np.concatenate([np.asarray(cam.as_vector(), dtype=np.float64), [float(jmode), float(bool(biased))]])
+    amplitude rho_hat = rho in place of Eq. 7's mu rho; dilation (pixels^2, 0 = none)
+    adds dilation * pitch^2 to the diagonal of the footprint evaluated at the pixels
+    (3DGS's low-pass filter), leaving mu on the undilated Sigma^."""
+    return np.concatenate([np.asarray(cam.as_vector(), dtype=np.float64),
+                           [float(jmode), float(bool(biased)), float(dilation)]])
 
 
 def _d(a) -> np.ndarray:
@@ -108,12 +111,12 @@ class _G:
 # ----------------------------------------------------------------------------- O1 rasterizer
 
 
-def render(G, views, cam, Q=9.0, brute=False, want_band=False, jmode=0, biased=False):
+def render(G, views, cam, Q=9.0, brute=False, want_band=False, jmode=0, biased=False, dilation=0.0):
     """O1 image [V, H, W] (float64), the number of gated (pixel, Gaussian) pairs and,
     if asked, the per-pixel gate-band magnitude."""
     g = _G(G)
     views = _d(views)
-    cv = _camv(cam, jmode, biased)
+    cv = _camv(cam, jmode, biased, dilation)
     V = views.shape[0]
     img = np.zeros((V, cam.H, cam.W))
     band = np.zeros((V, cam.H, cam.W)) if want_band else None
@@ -133,12 +136,12 @@ def project(G, views, cam, jmode=0, biased=False):
     return out
 
 
-def render_cs(G, views, cam, Q, kind, i, comp, h=1e-20, biased=False):
+def render_cs(G, views, cam, Q, kind, i, comp, h=1e-20, biased=False, dilation=0.0):
     """Complex-step derivative of the image wrt one parameter (kind 0 mean, 1 scale,
     2 quat, 3 rho)."""
     g = _G(G)
     views = _d(views)
-    cv = _camv(cam, 0, biased)
+    cv = _camv(cam, 0, biased, dilation)
     out = np.zeros((views.shape[0], cam.H, cam.W))
     lib().orc_render_cs(g.M, *g.ptrs(), _p(views), views.shape[0], _p(cv), float(Q), kind, i, comp, h, _p(out))
     return out
@@ -148,12 +151,12 @@ def _grad_arrays(M):
     return np.zeros((M, 3)), np.zeros((M, 3)), np.zeros((M, 4)), np.zeros(M)
 
 
-def render_backward(G, views, cam, dimg, Q=9.0, want_band=False, biased=False):
+def render_backward(G, views, cam, dimg, Q=9.0, want_band=False, biased=False, dilation=0.0):
     """Hand adjoint: (dmean, dscale, dquat, drho) in float64; with want_band also the
     per-parameter gate-band bound (summed |contribution| of pairs with |q - Q| <= 1e-4 Q)."""
     g = _G(G)
     views = _d(views)
-    cv = _camv(cam, 0, biased)
+    cv = _camv(cam, 0, biased, dilation)
     dimg = _d(dimg)
     out = _grad_arrays(g.M)
     band = _grad_arrays(g.M) if want_band else (None,) * 4
@@ -162,12 +165,12 @@ def render_backward(G, views, cam, dimg, Q=9.0, want_band=False, biased=False):
     return (out, band) if want_band else out
 
 
-def record_grads(G, views, cam, dimg, Q=9.0, biased=False):
+def record_grads(G, views, cam, dimg, Q=9.0, biased=False, dilation=0.0):
     """Per (view, Gaussian) record gradient d(rho_hat, p^x, p^y, a, b, c) of the gated
     image for dL/dI = dimg, [V, M, 6] float64 (p^ in detector units)."""
     g = _G(G)
     views = _d(views)
-    cv = _camv(cam, 0, biased)
+    cv = _camv(cam, 0, biased, dilation)
     dimg = _d(dimg)
     out = np.zeros((views.shape[0], g.M, 6))
     lib().orc_record_grads(g.M, *g.ptrs(), _p(views), views.shape[0], _p(cv), float(Q), _p(dimg), _p(out))
@@ -253,14 +256,14 @@ def voxelize_backward(G, gdescs, dvol, Q3=11.345, want_band=False):
 # ----------------------------------------------------------------------------- R32 replica
 
 
-def project_f32(G, views, cam, Q=9.0, tile=(16, 16)):
+def project_f32(G, views, cam, Q=9.0, tile=(16, 16), dilation=0.0):
     """FP32 replica of the stated projection and tile-bound sequence.
     Returns (f [V, M, 6] = p^x, p^y, alpha, beta, gamma, det;
              i [V, M, 9] = valid, pixel c_lo, c_hi, r_lo, r_hi, tile x_lo, x_hi, y_lo, y_hi)."""
     M = int(np.asarray(G.mean).shape[0])
     mean, scale, quat = _f(G.mean), _f(G.scale), _f(G.quat)
     views = _f(views)
-    cf = _f(cam.as_vector())
+    cf = _f(np.concatenate([np.asarray(cam.as_vector(), np.float64), [float(dilation)]]))
     V = views.shape[0]
     out_f = np.zeros((V, M, 6), dtype=np.float32)
     out_i = np.zeros((V, M, 9), dtype=np.int32)
@@ -269,10 +272,10 @@ def project_f32(G, views, cam, Q=9.0, tile=(16, 16)):
     return out_f, out_i
 
 
-def tile_lists_f32(G, views, cam, Q=9.0, tile=(16, 16)):
+def tile_lists_f32(G, views, cam, Q=9.0, tile=(16, 16), dilation=0.0):
     """Per-tile Gaussian lists from the R32 bounds: dict tile_key -> sorted array of
     Gaussian ids, tile_key = (v * tiles_y + ty) * tiles_x + tx."""
-    _, oi = project_f32(G, views, cam, Q, tile)
+    _, oi = project_f32(G, views, cam, Q, tile, dilation)
     TW, TH = tile
     tx_n = (cam.W + TW - 1) // TW
     ty_n = (cam.H + TH - 1) // TH

@@ -56,6 +56,9 @@ struct Cam {
                         // 1 = (0, 0, 1), a planted mistake for the reading test only
     int biased;         // 1 = the X-3DGS amplitude rho_hat = rho (no integration bias
                         // correction, Sec. 4.2.1); 0 = the rectified rho_hat = mu rho (Eq. 7)
+    double dilation;    // low-pass dilation in pixels^2 (0 = none): the footprint evaluated at
+                        // the pixels is Sigma^ + dilation diag(pitch_u^2, pitch_v^2), as 3DGS
+                        // does for anti-aliasing; mu (Eq. 7) keeps the undilated Sigma^
 };
 
 template <class T> struct M3 { T a[3][3]; };
@@ -141,6 +144,7 @@ template <class T> struct Proj {
     M3<T> St;        // Sigma~ = J W Sigma W^T J^T
     T sh[3];         // Sigma^ = top-left 2x2 of Sigma~: (alpha, beta, gamma)
     T d3, d2;        // |Sigma~|, |Sigma^|
+    T shd[3];        // the evaluated footprint: Sigma^ plus the dilation (= sh without one)
     T mu, rhohat;    // mu = sqrt(2 pi d3 / d2), rho_hat = mu rho
     T ph[2];         // p^ = first two coordinates of phi(u)
     T conic[3];      // Sigma^^{-1} = [[a, b], [b, c]]
@@ -187,9 +191,15 @@ Proj<T> project_one(const T* p, const M3<T>& Sigma, T rho, const double* view, c
     if (!(re(P.d2) > 0.0)) { P.valid = false; return P; }
     P.mu = std::sqrt(2.0 * M_PI * P.d3 / P.d2);
     P.rhohat = cam.biased ? rho : P.mu * rho;
-    P.conic[0] = P.sh[2] / P.d2;
-    P.conic[1] = -P.sh[1] / P.d2;
-    P.conic[2] = P.sh[0] / P.d2;
+    // the footprint evaluated at the pixels (optional low-pass dilation; a constant
+    // added to Sigma^, so d footprint / d Sigma^ is the identity)
+    P.shd[0] = P.sh[0] + cam.dilation * cam.pitch_u * cam.pitch_u;
+    P.shd[1] = P.sh[1];
+    P.shd[2] = P.sh[2] + cam.dilation * cam.pitch_v * cam.pitch_v;
+    const T dd = P.shd[0] * P.shd[2] - P.shd[1] * P.shd[1];
+    P.conic[0] = P.shd[2] / dd;
+    P.conic[1] = -P.shd[1] / dd;
+    P.conic[2] = P.shd[0] / dd;
     return P;
 }
 
@@ -251,8 +261,8 @@ int64_t render(const ParamsT<T>& G, int64_t M, const double* views, int V, const
             if (!P.valid) continue;
             int c0 = 0, c1 = Wd - 1, r0 = 0, r1 = H - 1;
             if (!brute) {
-                centre_range(re(P.ph[0]), std::sqrt(Q * re(P.sh[0])), cam.pitch_u, cam.off_u, Wd, c0, c1);
-                centre_range(re(P.ph[1]), std::sqrt(Q * re(P.sh[2])), cam.pitch_v, cam.off_v, H, r0, r1);
+                centre_range(re(P.ph[0]), std::sqrt(Q * re(P.shd[0])), cam.pitch_u, cam.off_u, Wd, c0, c1);
+                centre_range(re(P.ph[1]), std::sqrt(Q * re(P.shd[2])), cam.pitch_v, cam.off_v, H, r0, r1);
             }
             for (int r = r0; r <= r1; ++r) {
                 const T dy = pix_eta(r, cam) - P.ph[1];
@@ -341,8 +351,8 @@ void chain_record(const Proj<double>& P, const M3<double>& Sigma, const M3<doubl
     // mu = sqrt(2 pi d3 / d2)
     const double dd3 = dmu * P.mu / (2.0 * P.d3);
     const double dd2 = -dmu * P.mu / (2.0 * P.d2);
-    // conic = Sigma^^{-1}: full-matrix gradient Gc = [[da, db/2], [db/2, dc]];
-    // dL/dSigma^ = -C Gc C with C the conic.
+    // conic = (Sigma^ + dilation)^{-1}: full-matrix gradient Gc = [[da, db/2], [db/2, dc]];
+    // dL/dSigma^ = -C Gc C with C the conic (the dilation is a constant).
     const double C2[2][2] = {{a, b}, {b, c}};
     const double Gc[2][2] = {{da, 0.5 * db}, {0.5 * db, dc}};
     double T1[2][2], dSh[2][2];
@@ -432,8 +442,8 @@ void render_backward(const Params& Pm, const double* views, int V, const Cam& ca
             Proj<double> P = project_one(&G.mean[3 * i], Sigma, G.rho[i], view, cam);
             if (!P.valid) continue;
             int c0, c1, r0, r1;
-            centre_range(P.ph[0], std::sqrt(Q * P.sh[0]), cam.pitch_u, cam.off_u, Wd, c0, c1);
-            centre_range(P.ph[1], std::sqrt(Q * P.sh[2]), cam.pitch_v, cam.off_v, H, r0, r1);
+            centre_range(P.ph[0], std::sqrt(Q * P.shd[0]), cam.pitch_u, cam.off_u, Wd, c0, c1);
+            centre_range(P.ph[1], std::sqrt(Q * P.shd[2]), cam.pitch_v, cam.off_v, H, r0, r1);
             const double a = P.conic[0], b = P.conic[1], c = P.conic[2];
             double drec[6] = {0, 0, 0, 0, 0, 0};
             for (int r = r0; r <= r1; ++r) {
@@ -487,8 +497,8 @@ void record_grads(const Params& Pm, const double* views, int V, const Cam& cam, 
             Proj<double> P = project_one(&G.mean[3 * i], Sigma, G.rho[i], view, cam);
             if (!P.valid) continue;
             int c0, c1, r0, r1;
-            centre_range(P.ph[0], std::sqrt(Q * P.sh[0]), cam.pitch_u, cam.off_u, Wd, c0, c1);
-            centre_range(P.ph[1], std::sqrt(Q * P.sh[2]), cam.pitch_v, cam.off_v, H, r0, r1);
+            centre_range(P.ph[0], std::sqrt(Q * P.shd[0]), cam.pitch_u, cam.off_u, Wd, c0, c1);
+            centre_range(P.ph[1], std::sqrt(Q * P.shd[2]), cam.pitch_v, cam.off_v, H, r0, r1);
             const double a = P.conic[0], b = P.conic[1], c = P.conic[2];
             for (int r = r0; r <= r1; ++r) {
                 const double dy = pix_eta(r, cam) - P.ph[1];
@@ -762,6 +772,7 @@ Cam make_cam(const double* c) {
     cam.near_plane = c[8];
     cam.jmode = (int)c[9];
     cam.biased = (int)c[10];
+    cam.dilation = c[11];
     return cam;
 }
 
@@ -791,7 +802,7 @@ static inline float f_floor_clamped(float x, int n) {
 
 F32Out project_f32(const float* p, const float* s, const float* q, const float* view, int beam, float L_SD,
                    int H, int Wd, float pitch_u, float pitch_v, float off_u, float off_v, float near_plane,
-                   float Q, int TW, int TH) {
+                   float Q, int TW, int TH, float dilation) {
     F32Out o{};
     o.valid = 0;
     const float w0 = q[0], x0 = q[1], y0 = q[2], z0 = q[3];
@@ -851,8 +862,16 @@ F32Out project_f32(const float* p, const float* s, const float* q, const float* 
     o.sh[1] = be;
     o.sh[2] = ga;
     o.det = (m01 * m01 + m02 * m02) + m12 * m12;
+    if (dilation > 0.0f) {
+        // footprint Sigma^ + diag(dx, dy), dx = dilation pitch_u^2, dy = dilation pitch_v^2;
+        // its determinant expanded as |Sigma^| + (dy alpha + dx gamma) + dx dy
+        const float dx = (dilation * pitch_u) * pitch_u, dy = (dilation * pitch_v) * pitch_v;
+        o.det = (o.det + (dy * al + dx * ga)) + dx * dy;
+        o.sh[0] = al + dx;
+        o.sh[2] = ga + dy;
+    }
     if (!(o.det > 0.0f)) return o;
-    const float ex = std::sqrt(Q * al), ey = std::sqrt(Q * ga);
+    const float ex = std::sqrt(Q * o.sh[0]), ey = std::sqrt(Q * o.sh[2]);
     const float hw = 0.5f * (float)Wd - 0.5f, hh = 0.5f * (float)H - 0.5f;
     const float cx = (o.ph[0] - off_u) / pitch_u + hw;
     const float cy = (o.ph[1] - off_v) / pitch_v + hh;
@@ -914,7 +933,7 @@ int brick_bound_f32(const float* p, const float* s, const float* q, const float*
 
 extern "C" {
 
-// cam: [beam, H, W, L_SD, pitch_u, pitch_v, off_u, off_v, near_plane, jmode, biased]
+// cam: [beam, H, W, L_SD, pitch_u, pitch_v, off_u, off_v, near_plane, jmode, biased, dilation]
 int64_t orc_render(int64_t M, const double* mean, const double* scale, const double* quat, const double* rho,
                    const double* views, int V, const double* camv, double Q, int brute, double* img, double* band) {
     const Params P{M, mean, scale, quat, rho};
@@ -1091,7 +1110,7 @@ void orc_pixel_ray(const double* view, const double* camv, int r, int c, double*
 }
 
 // R32 projection + tile bounds for all (view, Gaussian) records, record index v*M + i.
-// camf: [beam, H, W, L_SD, pitch_u, pitch_v, off_u, off_v, near_plane] as float.
+// camf: [beam, H, W, L_SD, pitch_u, pitch_v, off_u, off_v, near_plane, dilation] as float.
 // out_f[rec][6] = p^x, p^y, alpha, beta, gamma, det ; out_i[rec][9] = valid, pix(4), tile(4)
 void orc_project_f32(int64_t M, const float* mean, const float* scale, const float* quat, const float* views,
                      int V, const float* camf, float Q, int TW, int TH, float* out_f, int32_t* out_i) {
@@ -1099,7 +1118,7 @@ void orc_project_f32(int64_t M, const float* mean, const float* scale, const flo
         for (int64_t i = 0; i < M; ++i) {
             F32Out o = project_f32(&mean[3 * i], &scale[3 * i], &quat[4 * i], views + 12 * v, (int)camf[0], camf[3],
                                    (int)camf[1], (int)camf[2], camf[4], camf[5], camf[6], camf[7], camf[8], Q, TW,
-                                   TH);
+                                   TH, camf[9]);
             const int64_t rec = (int64_t)v * M + i;
             float* f = out_f + rec * 6;
             f[0] = o.ph[0]; f[1] = o.ph[1]; f[2] = o.sh[0]; f[3] = o.sh[1]; f[4] = o.sh[2]; f[5] = o.det;

@@ -698,3 +698,86 @@ def test_isotropic_tv_closed_form_and_gradient():
         gc[idx] += 1j * h
         cs = losses.tv3d_iso(gc, 0.05, eps)[0].imag / h
         assert abs(cs - grad[idx]) <= 1e-12 * max(1.0, abs(cs)), (idx, cs, grad[idx])
+
+
+# ----------------------------------------------------------------------------- low-pass dilation (option)
+
+
+def test_dilation_widens_the_footprint_by_pitch_squared():
+    """Parallel beam, untruncated, one isotropic Gaussian of scale s: with dilation d
+    (pixels^2) the image is the 2D Gaussian of variance s^2 + d pitch^2 with the
+    undilated peak mu rho = sqrt(2 pi) s rho, so the projected mass grows by
+    (s^2 + d pitch^2) / s^2 (the dilation breaks Eq. 7's mass invariant)."""
+    s, rho, d = 0.06, 0.7, 0.3
+    pitch = 2.0 / 80
+    cam = I.parallel_camera(80, 80, pitch)
+    G = I.GaussianSet(np.array([[0.013, -0.021, 0.0]]), np.full((1, 3), s), np.array([[1.0, 0, 0, 0]]), np.array([rho]))
+    views = I.view_table(np.deg2rad([0.0]), 4.0, dtype=np.float64)
+    img, _ = core.render(G, views, cam, Q=math.inf, dilation=d)
+    pr = core.project(G, views, cam)
+    xi = (np.arange(cam.W) + 0.5 - cam.W / 2) * pitch
+    XI, ETA = np.meshgrid(xi, xi)
+    var = s * s + d * pitch * pitch
+    want = math.sqrt(2 * math.pi) * s * rho * np.exp(-((XI - pr[0, 0, 1]) ** 2 + (ETA - pr[0, 0, 2]) ** 2) / (2 * var))
+    assert np.abs(img[0] - want).max() <= 1e-12 * want.max()
+    mass0 = math.sqrt(2 * math.pi) * s * rho * 2 * math.pi * s * s
+    assert abs(img[0].sum() * pitch * pitch / mass0 - var / (s * s)) <= 1e-9
+    assert np.array_equal(core.render(G, views, cam, Q=math.inf, dilation=0.0)[0],
+                          core.render(G, views, cam, Q=math.inf)[0])
+
+
+@pytest.mark.parametrize("beam", [0, 1])
+def test_dilated_adjoint_matches_complex_step(beam):
+    """With a dilation the hand adjoint still equals complex-step derivatives."""
+    G = small_set(3, 7)
+    views = I.view_table(np.deg2rad([15, 80]), 4.0)
+    if beam == 0:
+        cam = I.parallel_camera(24, 28, 2.0 / 28)
+    else:
+        cam = I.Camera(beam=1, H=24, W=28, L_SD=6.0, pitch_u=3.0 / 28, pitch_v=3.0 / 24, off_u=0.05, near_plane=0.04)
+    g = np.random.default_rng(9).standard_normal((2, cam.H, cam.W))
+    dm, ds, dq, dr = core.render_backward(G, views, cam, g, Q=Q9, dilation=0.3)
+    assert np.abs(dm - core.render_backward(G, views, cam, g, Q=Q9)[0]).max() > 1e-4 * np.abs(dm).max()
+    for kind, arr, nc in ((0, dm, 3), (1, ds, 3), (2, dq, 4), (3, dr[:, None], 1)):
+        for i in range(G.M):
+            for c in range(nc):
+                cs = (core.render_cs(G, views, cam, Q9, kind, i, c, dilation=0.3) * g).sum()
+                assert abs(cs - arr[i, c]) <= 1e-10 * max(abs(cs), 1e-8), (kind, i, c, cs, arr[i, c])
+
+
+def test_dilated_fp32_tile_bound_covers_the_dilated_gate():
+    """The FP32 replica's dilated pixel box holds every pixel the dilated FP64 gate
+    admits (away from the gate band), and contains the undilated box."""
+    d = 0.3
+    G = I.uniform_gaussians(150, 17, 0.01, 0.05)
+    views = I.view_table(np.deg2rad([0, 60, 120]), I.CONE_L_SO)
+    cam = I.cone_camera(64, 64, pitch=I.CONE_PITCH * 8)
+    _, oi = core.project_f32(G, views, cam, dilation=d)
+    _, oi0 = core.project_f32(G, views, cam)
+    pr = core.project(G, views, cam)
+    xi = (np.arange(cam.W) + 0.5 - cam.W / 2) * cam.pitch_u + cam.off_u
+    eta = (np.arange(cam.H) + 0.5 - cam.H / 2) * cam.pitch_v + cam.off_v
+    XI, ETA = np.meshgrid(xi, eta)
+    checked = 0
+    for v in range(3):
+        for i in range(G.M):
+            if pr[v, i, 0] != 1:
+                continue
+            if oi0[v, i, 0]:
+                assert oi[v, i, 0] == 1
+                assert oi[v, i, 1] <= oi0[v, i, 1] and oi[v, i, 2] >= oi0[v, i, 2]
+                assert oi[v, i, 3] <= oi0[v, i, 3] and oi[v, i, 4] >= oi0[v, i, 4]
+            al = pr[v, i, 3] + d * cam.pitch_u ** 2
+            be = pr[v, i, 4]
+            ga = pr[v, i, 5] + d * cam.pitch_v ** 2
+            det = al * ga - be * be
+            dx, dy = XI - pr[v, i, 1], ETA - pr[v, i, 2]
+            q = (ga * dx * dx - 2 * be * dx * dy + al * dy * dy) / det
+            rr, cc = np.nonzero(q <= Q9 * (1 - 1e-4))
+            if rr.size == 0:
+                continue
+            checked += 1
+            assert oi[v, i, 0] == 1
+            c0, c1, r0, r1 = oi[v, i, 1:5]
+            assert cc.min() >= c0 and cc.max() <= c1 and rr.min() >= r0 and rr.max() <= r1
+    assert checked > 100
