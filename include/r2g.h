@@ -75,6 +75,11 @@ typedef struct {
                              * launch when the grid can be resident (fewer launches; it holds its SMs until
                              * the whole grid runs, which limits overlap with other streams' kernels).  The
                              * lists are the same either way.  r2g_train_step applies it to both branches. */
+    float dilation;      /* low-pass dilation in pixels^2, 0 (default) = none.  > 0: the footprint evaluated at
+                          * the pixels (and its pixel box) is Sigma^ + diag(dilation pitch_u^2, dilation
+                          * pitch_v^2), as 3DGS adds 0.3 px^2 for anti-aliasing; rho_hat keeps Eq. 7's mu of the
+                          * undilated Sigma^, so the projected mass is no longer the Gaussian's (the paper uses
+                          * none).  Negative or non-finite: R2G_E_INVAL. */
 } r2g_raster_opts;
 
 /* One voxel grid: the centre of voxel (x, y, z) is origin + (index + 1/2) * voxel;

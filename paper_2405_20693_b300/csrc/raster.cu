@@ -39,6 +39,7 @@ struct CamF {
     int beam, H, W;
     float L_SD, pu, pv, ou, ov, near_plane;
     int biased;  // 1: rho_hat = rho (no Eq. 7 factor)
+    float dil, dil_x, dil_y;  // low-pass dilation (pixels^2) and its detector-unit terms d pu^2, d pv^2
 };
 
 struct Params {
@@ -140,6 +141,14 @@ __device__ __forceinline__ void project_stated(const float p[3], const float s[3
     const float m02 = fs(fm(P.N[0][0], P.N[1][2]), fm(P.N[0][2], P.N[1][0]));
     const float m12 = fs(fm(P.N[0][1], P.N[1][2]), fm(P.N[0][2], P.N[1][1]));
     P.det = fa(fa(fm(m01, m01), fm(m02, m02)), fm(m12, m12));
+    if (cam.dil > 0.0f) {
+        // optional low-pass dilation: the footprint evaluated at the pixels is
+        // Sigma^ + diag(dx, dy); its determinant |Sigma^| + (dy alpha + dx gamma) + dx dy.
+        // A constant shift, so the adjoint through (alpha, beta, gamma) is unchanged.
+        P.det = fa(fa(P.det, fa(fm(cam.dil_y, P.al), fm(cam.dil_x, P.ga))), fm(cam.dil_x, cam.dil_y));
+        P.al = fa(P.al, cam.dil_x);
+        P.ga = fa(P.ga, cam.dil_y);
+    }
     P.valid = P.det > 0.0f;
 }
 
@@ -949,6 +958,8 @@ r2g_status check_args(int64_t M, int32_t V, const r2g_camera* cam, const r2g_ras
     if (!valid_tile(opts->tile_w, opts->tile_h))
         return fail(R2G_E_INVAL, "tile %dx%d not one of 16x16, 8x8, 32x8, 32x32", opts->tile_w, opts->tile_h);
     if (!(opts->Q > 0.f)) return fail(R2G_E_INVAL, "Q must be > 0");
+    if (!(opts->dilation >= 0.f) || !(opts->dilation < 1e6f))
+        return fail(R2G_E_INVAL, "dilation must be finite and >= 0 (got %g)", (double)opts->dilation);
     const long long tx = (cam->W + opts->tile_w - 1) / opts->tile_w, ty = (cam->H + opts->tile_h - 1) / opts->tile_h;
     if ((long long)V * tx * ty >= (1ll << 31)) return fail(R2G_E_INVAL, "too many tiles");
     return R2G_OK;
@@ -1024,6 +1035,10 @@ CamF camf(const r2g_camera* c, const r2g_raster_opts* o) {
     f.ou = c->off_u;
     f.ov = c->off_v;
     f.near_plane = c->near_plane;
+    f.dil = o->dilation > 0.f ? o->dilation : 0.f;
+    const float du = f.dil * f.pu, dv = f.dil * f.pv;  // IEEE single products, in this order
+    f.dil_x = du * f.pu;
+    f.dil_y = dv * f.pv;
     return f;
 }
 

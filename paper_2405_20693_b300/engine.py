@@ -27,11 +27,12 @@ def _bytes(n: int, device) -> torch.Tensor:
 class Rasterizer:
     """Owns the workspace of one (M, V, camera, tile) configuration."""
 
-    def __init__(self, M: int, V: int, cam, Q=Q_PIXEL, tile=(16, 16), device="cuda", capacity=None, biased=False):
+    def __init__(self, M: int, V: int, cam, Q=Q_PIXEL, tile=(16, 16), device="cuda", capacity=None, biased=False,
+                 dilation=0.0):
         self.M, self.V = int(M), int(V)
         self.cam = r2g.camera(cam)
-        self.opts = r2g.raster_opts(Q, tile, biased=biased)
-        self.copts = r2g.raster_opts(Q, tile, count_pairs=True, biased=biased)
+        self.opts = r2g.raster_opts(Q, tile, biased=biased, dilation=dilation)
+        self.copts = r2g.raster_opts(Q, tile, count_pairs=True, biased=biased, dilation=dilation)
         self.device = device
         self.capacity = int(capacity or max(1 << 16, 4 * self.M * self.V))
         self.ws = None
@@ -315,9 +316,10 @@ class Scan:
     descriptor for r2g_train_step."""
 
     def __init__(self, G, views_np, meas_np, cam, n_out=256, D=32, tile=None, total_iters=30000,
-                 device="cuda", headroom=1.5, seed=0, biased=False, tv_eps=0.0):
+                 device="cuda", headroom=1.5, seed=0, biased=False, tv_eps=0.0, dilation=0.0):
         self.state = TrainState(G, device=device)
         self.biased = bool(biased)
+        self.dilation = float(dilation)  # low-pass dilation of the footprint, pixels^2 (0: none, the paper's)
         self.tv_eps = float(tv_eps)   # > 0: isotropic TV with this eps; 0: anisotropic (default)
         self.version = 0              # bumped whenever the C job changes (densification)
         self.dens_grad = self.dens_count = None
@@ -337,7 +339,8 @@ class Scan:
         self.vol = torch.empty(D ** 3, dtype=torch.float32, device=device)
         self.dvol = torch.empty_like(self.vol)
         self.loss = torch.zeros(2, dtype=torch.float32, device=device)
-        self.rast = Rasterizer(self.M, 1, cam, tile=tile or SCAN_TILE, device=device, biased=biased)
+        self.rast = Rasterizer(self.M, 1, cam, tile=tile or SCAN_TILE, device=device, biased=biased,
+                               dilation=self.dilation)
         from .inputs import patch_grid
 
         self.vox = Voxelizer(self.M, patch_grid((0, 0, 0), D, n_out), device=device)
@@ -469,7 +472,8 @@ class Scan:
         sep = int(self.rast.opts.separate_lists)
         times = {}
         for tile in tiles:
-            self.rast = Rasterizer(self.M, 1, self.cam, tile=tile, device=self.device, biased=self.biased)
+            self.rast = Rasterizer(self.M, 1, self.cam, tile=tile, device=self.device, biased=self.biased,
+                                   dilation=self.dilation)
             self.rast.opts.separate_lists = sep
             self._size_workspaces(self.headroom, probes=2)
             self.job = self._make_job()
@@ -484,7 +488,8 @@ class Scan:
             for dst, src in zip((s.raw, s.act, s.m, s.v), saved):
                 dst.copy_(src)
         best = min(times, key=times.get)
-        self.rast = Rasterizer(self.M, 1, self.cam, tile=best, device=self.device, biased=self.biased)
+        self.rast = Rasterizer(self.M, 1, self.cam, tile=best, device=self.device, biased=self.biased,
+                               dilation=self.dilation)
         self.rast.opts.separate_lists = sep
         self._size_workspaces(self.headroom, probes=2)
         self.job = self._make_job()

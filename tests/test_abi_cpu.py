@@ -53,6 +53,12 @@ def test_host_side_argument_errors(lib):
     ok = r2g.raster_opts(9.0, (16, 16))
     n = lib.r2g_raster_workspace_size(1000, 1, ctypes.byref(cam), ctypes.byref(ok), 4096)
     assert n > 2 * 8 * 4096
+    for bad in (-0.1, float("nan"), float("inf")):  # dilation must be finite and >= 0
+        o = r2g.raster_opts(9.0, (16, 16), dilation=bad)
+        assert lib.r2g_raster_workspace_size(1000, 1, ctypes.byref(cam), ctypes.byref(o), 4096) == 0
+        assert "dilation" in lib.r2g_last_error().decode()
+    assert lib.r2g_raster_workspace_size(1000, 1, ctypes.byref(cam),
+                                         ctypes.byref(r2g.raster_opts(9.0, (16, 16), dilation=0.3)), 4096) == n
     # NULL pointers are rejected on the host with R2G_E_INVAL, nothing launched
     st = lib.r2g_rasterize(1000, None, None, None, None, 1, None, ctypes.byref(cam), ctypes.byref(ok), None, None,
                            0, None)

@@ -435,3 +435,44 @@ def test_biased_per_view_fit_recovers_mu_rho():
         # one pixel whose q sits on the gate in FP32 moves a fit by ~1e-4 at most
         assert np.abs(fit / expect - 1).max() <= 2e-4, (biased, fit, expect)
     assert mu.max() / mu.min() > 1.3
+
+
+@pytest.mark.parametrize("dil", [0.3, 2.0])
+def test_dilated_rasterizer_matches_oracle(dil):
+    """Low-pass dilation (an option, off by default): the dilated FP32 projection and
+    pixel boxes are bit-identical to the oracle's replica, the tile lists equal its
+    lists, and the image and adjoint match the FP64 oracle with the same dilation."""
+    G, cam, views = cone_small()
+    V = views.shape[0]
+    rast = engine.Rasterizer(G.M, V, cam, dilation=dil)
+    mean, scale, quat, rho = dev_set(G)
+    vv = dev(views)
+    proj = torch.empty((V, G.M, 8), dtype=torch.float32, device="cuda")
+    rect = torch.empty((V, G.M, 4), dtype=torch.int32, device="cuda")
+    r2g.r2g_project(mean, scale, quat, rho, vv, rast.cam, rast.opts, proj, rect)
+    p, rc = proj.cpu().numpy(), rect.cpu().numpy()
+    of, oi = core.project_f32(G, views, cam, Q9, (16, 16), dilation=dil)
+    valid = oi[..., 0] == 1
+    assert np.array_equal(p[..., 7] == 1.0, valid)
+    for k in range(6):
+        assert np.array_equal(p[..., k][valid].view(np.uint32), of[..., k][valid].view(np.uint32)), k
+    assert np.array_equal(rc[valid], oi[..., 1:5][valid])
+    img = rast.forward(mean, scale, quat, rho, vv)
+    ranges, ids, n = _lists_gpu(rast, G.M, V)
+    ref_lists = core.tile_lists_f32(G, views, cam, Q9, (16, 16), dilation=dil)
+    assert n == sum(len(v) for v in ref_lists.values())
+    for t in range(ranges.shape[0]):
+        a, b = ranges[t]
+        assert np.array_equal(ids[a:b].astype(np.int64), ref_lists.get(t, np.zeros(0, np.int64))), t
+    torch.cuda.synchronize()
+    ref, _, band = core.render(G, views, cam, Q=Q9, want_band=True, dilation=dil)
+    ref0, _ = core.render(G, views, cam, Q=Q9)
+    assert np.abs(ref - ref0).max() > 1e-3 * np.abs(ref0).max()   # the option changes the image
+    assert_values_close(host(img), ref, band, f"dilation {dil}")
+    dimg = I.rng(12).standard_normal((V, cam.H, cam.W)).astype(np.float32)
+    g = [torch.zeros_like(t) for t in (mean, scale, quat, rho)]
+    rast.backward(mean, scale, quat, rho, vv, dev(dimg), *g)
+    torch.cuda.synchronize()
+    refg, bandg = core.render_backward(G, views, cam, dimg, Q=Q9, want_band=True, dilation=dil)
+    for name, a, b, bd in zip(("mean", "scale", "quat", "rho"), g, refg, bandg):
+        assert_grads_close(host(a), b, f"dilation {dil} d{name}", band=bd)
