@@ -42,9 +42,15 @@ struct SsimSmem {
         float g[3][kM][kT + 1];            // horizontally filtered derivative maps
     } u;
     float d[3][kM][kM + 1];                // dS/dmu_x, dS/dE_xx, dS/dE_xy (zero outside the image)
-    double red[2][kSsimThreads / 32];
+    float red[2][kSsimThreads / 32];
     int last;
 };
+
+// The thread that publishes the CTA's partial sums: one of the threads that write
+// no d loss / d render (the last pass uses threads 0 .. kT * kT / 4 - 1), so its
+// release fence does not wait for gradient stores.
+constexpr int kArriveThread = kSsimThreads - 1;
+static_assert(kArriveThread >= kT * kT / 4, "the arriving thread writes no gradient");
 
 // One CTA per 32 x 32 output tile of one view.  x and y are staged with a
 // 10-pixel halo; the windowed moments and each pixel's SSIM term S and its
@@ -52,16 +58,20 @@ struct SsimSmem {
 // 5-pixel halo (zero outside the image, whose pixels the mean leaves out); those
 // derivative maps are filtered again with the window (the adjoint of a
 // zero-padded symmetric filter is itself) and combined with x, y and the L1 sign
-// into d loss / d render.  Per-tile sums of S and |x - y| go to `partials`; the
-// last CTA to finish (arrival counter cleared before the launch) sums them in
-// tile order into the loss.  meas_sel (optional, device): view v of the batch is
-// compared with measurement meas_sel[v] of y.
+// into d loss / d render.  Per-tile sums of 1 - S and |x - y| go to `partials`;
+// the last CTA to finish (arrival counter cleared before the launch) sums them in
+// tile order into the loss (FP32 trees in a fixed order; 1 - S is summed rather
+// than S so that no cancellation is left when SSIM nears 1).  meas_sel (optional,
+// device): view v of the batch is compared with measurement meas_sel[v] of y.
+// vec4: W % 4 == 0 and both images 16-byte aligned -- the staging then reads
+// aligned float4 groups (columns TX - 12 .. TX + 43, the outer two on each side
+// dropped).
 __global__ void __launch_bounds__(kSsimThreads) k_ssim(const float* __restrict__ x, const float* __restrict__ y,
                                                        const int* __restrict__ meas_sel, int H, int W, int tiles_x,
                                                        int tiles_per_view, int n_tiles, const Win win,
                                                        float l1_scale, float ssim_scale, float* __restrict__ grad,
                                                        float* __restrict__ partials, unsigned int* __restrict__ arrive,
-                                                       float lam, double inv_n, float* __restrict__ loss) {
+                                                       float lam, float inv_n, int vec4, float* __restrict__ loss) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SsimSmem& S = *reinterpret_cast<SsimSmem*>(smem_raw);
     const int tid = threadIdx.x;
@@ -71,12 +81,45 @@ __global__ void __launch_bounds__(kSsimThreads) k_ssim(const float* __restrict__
     const int TY = ty * kT, TX = tx * kT;
     const float* xv = x + (size_t)v * H * W;
     const float* yv = y + (size_t)(meas_sel ? meas_sel[v] : v) * H * W;
-    for (int k = tid; k < kS * kS; k += kSsimThreads) {
-        const int r = k / kS, c = k - r * kS;
-        const int gy = TY - 2 * kR + r, gx = TX - 2 * kR + c;
-        const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
-        S.sx[r][c] = in ? xv[(size_t)gy * W + gx] : 0.f;
-        S.sy[r][c] = in ? yv[(size_t)gy * W + gx] : 0.f;
+    if (vec4) {
+        constexpr int G = (kS + 4 + 3) / 4;          // float4 groups per staged row (14)
+        constexpr int N = 2 * kS * G;                // both images
+        constexpr int IT = (N + kSsimThreads - 1) / kSsimThreads;
+        float4 val[IT];
+#pragma unroll
+        for (int t = 0; t < IT; ++t) {               // every load issued before any store
+            const int k = tid + t * kSsimThreads;
+            val[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (k < N) {
+                const int im = k / (kS * G), kk = k - im * (kS * G);
+                const int r = kk / G, g = kk - r * G;
+                const int gy = TY - 2 * kR + r, gx = TX - 2 * kR - 2 + 4 * g;  // gx % 4 == 0
+                if (gy >= 0 && gy < H && gx >= 0 && gx < W)
+                    val[t] = __ldg(reinterpret_cast<const float4*>((im ? yv : xv) + (size_t)gy * W + gx));
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < IT; ++t) {
+            const int k = tid + t * kSsimThreads;
+            if (k < N) {
+                const int im = k / (kS * G), kk = k - im * (kS * G);
+                const int r = kk / G, g = kk - r * G;
+                float* row = im ? S.sy[r] : S.sx[r];
+                const int c = 4 * g - 2;             // staged column of the group's first element
+                const float e[4] = {val[t].x, val[t].y, val[t].z, val[t].w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (c + q >= 0 && c + q < kS) row[c + q] = e[q];
+            }
+        }
+    } else {
+        for (int k = tid; k < kS * kS; k += kSsimThreads) {
+            const int r = k / kS, c = k - r * kS;
+            const int gy = TY - 2 * kR + r, gx = TX - 2 * kR + c;
+            const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
+            S.sx[r][c] = in ? xv[(size_t)gy * W + gx] : 0.f;
+            S.sy[r][c] = in ? yv[(size_t)gy * W + gx] : 0.f;
+        }
     }
     __syncthreads();
     // Each pass is register-blocked along its filter direction: a thread computes a
@@ -153,13 +196,13 @@ __global__ void __launch_bounds__(kSsimThreads) k_ssim(const float* __restrict__
                     const float sxx = m[o][2] - mx * mx, syy = m[o][3] - my * my, sxy = m[o][4] - mx * my;
                     const float A1 = 2.f * mx * my + kC1, A2 = 2.f * sxy + kC2;
                     const float B1 = mx * mx + my * my + kC1, B2 = sxx + syy + kC2;
-                    const float iB = 1.f / (B1 * B2);
+                    const float iB = __frcp_rn(B1 * B2);
                     const float Sv = A1 * A2 * iB;
                     dm = (2.f * my * (A2 - A1) - 2.f * mx * Sv * (B2 - B1)) * iB;
-                    dxx = -Sv / B2;
+                    dxx = -Sv * (B1 * iB);                   // -S / B2
                     dxy = 2.f * A1 * iB;
                     if (r >= kR && r < kR + kT && c >= kR && c < kR + kT) {  // this tile's own pixels
-                        sS += Sv;
+                        sS += 1.f - Sv;
                         sL1 += fabsf(S.sx[r + kR][c + kR] - S.sy[r + kR][c + kR]);
                     }
                 }
@@ -246,21 +289,23 @@ __global__ void __launch_bounds__(kSsimThreads) k_ssim(const float* __restrict__
         S.red[1][tid >> 5] = sL1;
     }
     __syncthreads();
-    if (tid == 0) {
-        double a = 0.0, b = 0.0;
+    if (tid == kArriveThread) {
+        float a = 0.f, b = 0.f;
+#pragma unroll
         for (int w = 0; w < kSsimThreads / 32; ++w) {
             a += S.red[0][w];
             b += S.red[1][w];
         }
-        partials[2 * tile] = (float)a;
-        partials[2 * tile + 1] = (float)b;
+        partials[2 * tile] = a;
+        partials[2 * tile + 1] = b;
         __threadfence();
         S.last = atomicAdd(arrive, 1u) == (unsigned)(n_tiles - 1);
     }
     __syncthreads();
     if (!S.last) return;
     __threadfence();
-    double a = 0.0, b = 0.0;
+    // the tiles' partials in a fixed order: a strided sum per thread, then warp and CTA trees
+    float a = 0.f, b = 0.f;
     for (int k = tid; k < n_tiles; k += kSsimThreads) {
         a += __ldcg(partials + 2 * k);
         b += __ldcg(partials + 2 * k + 1);
@@ -277,12 +322,13 @@ __global__ void __launch_bounds__(kSsimThreads) k_ssim(const float* __restrict__
     }
     __syncthreads();
     if (tid == 0) {
-        double sa = 0.0, sb = 0.0;
+        float sa = 0.f, sb = 0.f;
+#pragma unroll
         for (int w = 0; w < kSsimThreads / 32; ++w) {
             sa += S.red[0][w];
             sb += S.red[1][w];
         }
-        *loss = (float)(inv_n * sb + lam * (1.0 - inv_n * sa));
+        *loss = inv_n * sb + lam * (inv_n * sa);
     }
 }
 
@@ -485,11 +531,13 @@ r2g_status r2g::projection_loss_impl(int32_t V, int32_t H, int32_t W, const floa
     }
     const int tpv = L.tiles_x * L.tiles_y;
     const double N = (double)V * H * W;
+    const int vec4 = (W % 4 == 0) && reinterpret_cast<uintptr_t>(render) % 16 == 0 &&
+                     reinterpret_cast<uintptr_t>(meas) % 16 == 0;
     prof_begin(P_LOSS, stream);
     cudaMemsetAsync(arrive, 0, sizeof(unsigned int), stream);
     k_ssim<<<(unsigned)L.n_tiles, kSsimThreads, sizeof(SsimSmem), stream>>>(
         render, meas, meas_sel, H, W, L.tiles_x, tpv, (int)L.n_tiles, win, (float)(1.0 / N), (float)(lambda_ssim / N),
-        drender, partials, arrive, lambda_ssim, 1.0 / N, loss);
+        drender, partials, arrive, lambda_ssim, (float)(1.0 / N), vec4, loss);
     prof_end(P_LOSS, stream);
     note_launches(1);
     return check_launch("r2g_projection_loss");
