@@ -296,6 +296,56 @@ __device__ __forceinline__ void key_offsets(uint32_t* __restrict__ hist, uint32_
     }
 }
 
+// Key bases in shared memory (one 256-thread block, <= 1024 keys, 4 per thread):
+// s_base[k] = first entry of key k, s_ibase[k] = its first work item (every key
+// gets ceil(entries / chunk) items, an empty key one); [n_keys] hold the totals.
+__device__ __forceinline__ void key_bases(const uint32_t* key_totals, int n_keys, uint32_t chunk, uint32_t* s_base,
+                                          uint32_t* s_ibase, uint32_t* sm8) {
+    const int t = threadIdx.x;
+    uint32_t tk[4], nc[4], sum = 0, isum = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int k = 4 * t + q;
+        tk[q] = k < n_keys ? __ldcg(key_totals + k) : 0u;
+        nc[q] = k < n_keys ? (tk[q] ? (tk[q] + chunk - 1) / chunk : 1u) : 0u;
+        sum += tk[q];
+        isum += nc[q];
+    }
+    uint32_t tot, itot;
+    uint32_t base = block_exclusive_scan_256(sum, sm8, &tot);
+    uint32_t ibase = block_exclusive_scan_256(isum, sm8, &itot);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int k = 4 * t + q;
+        if (k < n_keys) {
+            s_base[k] = base;
+            s_ibase[k] = ibase;
+        }
+        base += tk[q];
+        ibase += nc[q];
+    }
+    if (t == 0) {
+        s_base[n_keys] = tot;
+        s_ibase[n_keys] = itot;
+    }
+}
+
+// What the forward and backward read of key k (one warp): its range, cleared chunk
+// arrival counters, its first work item and its items (lanes in parallel).
+__device__ __forceinline__ void key_publish(const FusedKeys& fk, int k, const uint32_t* s_base,
+                                            const uint32_t* s_ibase, int lane) {
+    const uint32_t base = s_base[k], tk = s_base[k + 1] - base;
+    const uint32_t ibase = s_ibase[k], nc = s_ibase[k + 1] - ibase;
+    if (lane == 0) {
+        fk.ranges[k] = tk ? make_uint2(base, base + tk) : make_uint2(0u, 0u);
+        fk.item_off[k] = ibase;
+    }
+    const int kd = fk.kd_per_key > 0 ? fk.kd_per_key : 1;
+    for (int w = lane; w < kd; w += 32) fk.key_done[(size_t)k * kd + w] = 0;
+    for (uint32_t c = lane; c < nc; c += 32)
+        if (ibase + c < fk.items_cap) fk.items[ibase + c] = ((uint64_t)(uint32_t)k << 32) | c;
+}
+
 // One warp per key k (see key_offsets).
 static __global__ void __launch_bounds__(256) k_fused_offsets(uint32_t* __restrict__ hist,
                                                               const uint32_t* __restrict__ key_first, int nb,
@@ -411,6 +461,26 @@ __device__ __forceinline__ void grid_barrier(WsStatus* st, unsigned int epoch) {
     __syncthreads();
 }
 
+// The key phase of the cooperative builds: the blocks that own keys (warp w of
+// block b owns keys b * 8 + w + i * 8 * gridDim.x) form the key bases in shared
+// memory; each owning warp turns its key's row of per-block counts into scatter
+// offsets and publishes the key's range, arrival counters and work items.  Blocks
+// without keys skip the scan.  pool: shared [>= 2 * (n_keys + 1)].
+__device__ __forceinline__ void keys_phase(uint32_t* __restrict__ hist, const uint32_t* key_totals, int n_keys,
+                                           const FusedKeys& fk, uint32_t* pool, uint32_t* sm8) {
+    if ((int)blockIdx.x * 8 >= n_keys) return;  // block-uniform
+    uint32_t* s_base = pool;
+    uint32_t* s_ibase = pool + kFusedKeys + 1;
+    key_bases(key_totals, n_keys, fk.chunk, s_base, s_ibase, sm8);
+    __syncthreads();
+    if (blockIdx.x == 0 && threadIdx.x == 0) fk.item_st->n_keys = s_ibase[n_keys];
+    const int lane = threadIdx.x & 31;
+    for (int k = blockIdx.x * 8 + (threadIdx.x >> 5); k < n_keys; k += gridDim.x * 8) {
+        key_offsets(hist, s_base[k], (int)gridDim.x, k, lane);
+        key_publish(fk, k, s_base, s_ibase, lane);
+    }
+}
+
 // The fused list build in one cooperative launch (grid = the emit blocks): emission
 // with per-block key counts; barrier; every block scans the key totals into the
 // keys' first entries (block 0 also writes ranges and work items) and the grid's
@@ -429,12 +499,7 @@ __global__ void __launch_bounds__(256) k_lists_coop(Op op, long long n_rec, long
     emit_block<Op, true>(op, n_rec, per_block, partials[blockIdx.x], a, capacity, hist, key_totals, n_keys, pool,
                          reinterpret_cast<uint4*>(pool + kFusedKeys), pool + 2 * kFusedKeys, sm8);
     grid_barrier(st, 1);
-    uint32_t* s_base = pool;
-    key_scan(key_totals, n_keys, fk, blockIdx.x == 0, s_base, nullptr, sm8);
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    for (int k = blockIdx.x * 8 + (threadIdx.x >> 5); k < n_keys; k += gridDim.x * 8)
-        key_offsets(hist, s_base[k], (int)gridDim.x, k, lane);
+    keys_phase(hist, key_totals, n_keys, fk, pool, sm8);
     grid_barrier(st, 2);
     const unsigned long long n_written = st->n_keys;
     const unsigned long long lo = min(partials[blockIdx.x], n_written);
@@ -484,12 +549,7 @@ __global__ void __launch_bounds__(256) k_plists_coop(Proj proj, Op op, long long
     emit_block<Op, true>(op, n_rec, per_block, before, a, capacity, hist, key_totals, n_keys, pool,
                          reinterpret_cast<uint4*>(pool + kFusedKeys), pool + 2 * kFusedKeys, sm8);
     grid_barrier(st, 2);
-    uint32_t* s_base = pool;
-    key_scan(key_totals, n_keys, fk, blockIdx.x == 0, s_base, nullptr, sm8);
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    for (int k = blockIdx.x * 8 + (threadIdx.x >> 5); k < n_keys; k += gridDim.x * 8)
-        key_offsets(hist, s_base[k], (int)gridDim.x, k, lane);
+    keys_phase(hist, key_totals, n_keys, fk, pool, sm8);
     grid_barrier(st, 3);
     const unsigned long long lo = before < written ? before : written;
     const unsigned long long hi = before + mine < written ? before + mine : written;
