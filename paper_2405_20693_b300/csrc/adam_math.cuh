@@ -129,7 +129,7 @@ __device__ __forceinline__ long long adam_index(long long M, long long i, int e)
     return e < 4 ? 4 * i + e : (e < 7 ? 4 * M + 3 * i + (e - 4) : (e < 10 ? 7 * M + 3 * i + (e - 7) : 10 * M + i));
 }
 
-__device__ __forceinline__ void adam_prefetch(const AdamState& st, long long i, AdamPre& p) {
+__device__ __forceinline__ void adam_prefetch_state(const AdamState& st, long long i, AdamPre& p) {
     const long long M = st.a.M;
 #pragma unroll
     for (int e = 0; e < 11; ++e) {
@@ -137,8 +137,12 @@ __device__ __forceinline__ void adam_prefetch(const AdamState& st, long long i, 
         p.raw[e] = st.raw[x];
         p.m[e] = st.m[x];
         p.v[e] = st.v[x];
-        p.g[e] = st.grad[x];
     }
+}
+__device__ __forceinline__ void adam_prefetch_grad(const AdamState& st, long long i, AdamPre& p) {
+    const long long M = st.a.M;
+#pragma unroll
+    for (int e = 0; e < 11; ++e) p.g[e] = st.grad[adam_index(M, i, e)];
 }
 
 // adam_gaussian with the state prefetched; act: the activated values (the

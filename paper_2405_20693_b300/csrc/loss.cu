@@ -52,6 +52,48 @@ struct SsimSmem {
 constexpr int kArriveThread = kSsimThreads - 1;
 static_assert(kArriveThread >= kT * kT / 4, "the arriving thread writes no gradient");
 
+// Stage one image's tile plus its 10-pixel halo into dst (zeros outside the image).
+// vec4: aligned float4 groups of columns TX - 12 .. TX + 43, the outer two on each
+// side dropped, every load issued before any store; else one float per thread.
+__device__ __forceinline__ void stage_tile(float (*dst)[kS + 1], const float* __restrict__ img, int TY, int TX,
+                                           int H, int W, int tid, int vec4) {
+    if (vec4) {
+        constexpr int G = (kS + 4 + 3) / 4;          // float4 groups per staged row (14)
+        constexpr int N = kS * G;
+        constexpr int IT = (N + kSsimThreads - 1) / kSsimThreads;
+        float4 val[IT];
+#pragma unroll
+        for (int t = 0; t < IT; ++t) {
+            const int k = tid + t * kSsimThreads;
+            val[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (k < N) {
+                const int r = k / G, g = k - r * G;
+                const int gy = TY - 2 * kR + r, gx = TX - 2 * kR - 2 + 4 * g;  // gx % 4 == 0
+                if (gy >= 0 && gy < H && gx >= 0 && gx < W)
+                    val[t] = __ldg(reinterpret_cast<const float4*>(img + (size_t)gy * W + gx));
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < IT; ++t) {
+            const int k = tid + t * kSsimThreads;
+            if (k < N) {
+                const int r = k / G, g = k - r * G;
+                const int c = 4 * g - 2;             // staged column of the group's first element
+                const float e[4] = {val[t].x, val[t].y, val[t].z, val[t].w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (c + q >= 0 && c + q < kS) dst[r][c + q] = e[q];
+            }
+        }
+    } else {
+        for (int k = tid; k < kS * kS; k += kSsimThreads) {
+            const int r = k / kS, c = k - r * kS;
+            const int gy = TY - 2 * kR + r, gx = TX - 2 * kR + c;
+            dst[r][c] = (gy >= 0 && gy < H && gx >= 0 && gx < W) ? img[(size_t)gy * W + gx] : 0.f;
+        }
+    }
+}
+
 // One CTA per 32 x 32 output tile of one view.  x and y are staged with a
 // 10-pixel halo; the windowed moments and each pixel's SSIM term S and its
 // derivatives with respect to mu_x, E_xx and E_xy are formed on the tile plus a
@@ -81,46 +123,12 @@ __global__ void __launch_bounds__(kSsimThreads) k_ssim(const float* __restrict__
     const int TY = ty * kT, TX = tx * kT;
     const float* xv = x + (size_t)v * H * W;
     const float* yv = y + (size_t)(meas_sel ? meas_sel[v] : v) * H * W;
-    if (vec4) {
-        constexpr int G = (kS + 4 + 3) / 4;          // float4 groups per staged row (14)
-        constexpr int N = 2 * kS * G;                // both images
-        constexpr int IT = (N + kSsimThreads - 1) / kSsimThreads;
-        float4 val[IT];
-#pragma unroll
-        for (int t = 0; t < IT; ++t) {               // every load issued before any store
-            const int k = tid + t * kSsimThreads;
-            val[t] = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (k < N) {
-                const int im = k / (kS * G), kk = k - im * (kS * G);
-                const int r = kk / G, g = kk - r * G;
-                const int gy = TY - 2 * kR + r, gx = TX - 2 * kR - 2 + 4 * g;  // gx % 4 == 0
-                if (gy >= 0 && gy < H && gx >= 0 && gx < W)
-                    val[t] = __ldg(reinterpret_cast<const float4*>((im ? yv : xv) + (size_t)gy * W + gx));
-            }
-        }
-#pragma unroll
-        for (int t = 0; t < IT; ++t) {
-            const int k = tid + t * kSsimThreads;
-            if (k < N) {
-                const int im = k / (kS * G), kk = k - im * (kS * G);
-                const int r = kk / G, g = kk - r * G;
-                float* row = im ? S.sy[r] : S.sx[r];
-                const int c = 4 * g - 2;             // staged column of the group's first element
-                const float e[4] = {val[t].x, val[t].y, val[t].z, val[t].w};
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (c + q >= 0 && c + q < kS) row[c + q] = e[q];
-            }
-        }
-    } else {
-        for (int k = tid; k < kS * kS; k += kSsimThreads) {
-            const int r = k / kS, c = k - r * kS;
-            const int gy = TY - 2 * kR + r, gx = TX - 2 * kR + c;
-            const bool in = gy >= 0 && gy < H && gx >= 0 && gx < W;
-            S.sx[r][c] = in ? xv[(size_t)gy * W + gx] : 0.f;
-            S.sy[r][c] = in ? yv[(size_t)gy * W + gx] : 0.f;
-        }
-    }
+    pdl_trigger();
+    // the measurement first (no earlier kernel writes it), then, once the kernel
+    // that renders x has finished, the render
+    stage_tile(S.sy, yv, TY, TX, H, W, tid, vec4);
+    pdl_wait();
+    stage_tile(S.sx, xv, TY, TX, H, W, tid, vec4);
     __syncthreads();
     // Each pass is register-blocked along its filter direction: a thread computes a
     // run of outputs from one sliding set of inputs (every input loaded once), and
@@ -502,9 +510,19 @@ R2G_API size_t r2g_loss_workspace_size(int32_t V, int32_t H, int32_t W) {
     return loss_layout(V, H, W).fixed;
 }
 
+r2g_status r2g::projection_loss_clear(int32_t V, int32_t H, int32_t W, void* ws, size_t ws_bytes,
+                                      cudaStream_t stream) {
+    if (V < 1 || H < 1 || W < 1 || !ws) return fail(R2G_E_INVAL, "bad loss workspace");
+    const LossLayout L = loss_layout(V, H, W);
+    if (ws_bytes < L.fixed) return fail(R2G_E_INVAL, "loss workspace needs %zu bytes", L.fixed);
+    if (cudaMemsetAsync(static_cast<char*>(ws) + L.arrive, 0, sizeof(unsigned int), stream) != cudaSuccess)
+        return fail(R2G_E_CUDA, "clearing the loss arrival counter: %s", cudaGetErrorString(cudaGetLastError()));
+    return R2G_OK;
+}
+
 r2g_status r2g::projection_loss_impl(int32_t V, int32_t H, int32_t W, const float* render, const float* meas,
                                      const int* meas_sel, float lambda_ssim, float* loss, float* drender, void* ws,
-                                     size_t ws_bytes, cudaStream_t stream) {
+                                     size_t ws_bytes, cudaStream_t stream, bool clear_arrival) {
     if (V < 1 || H < 1 || W < 1 || H > 32768 || W > 32768) return fail(R2G_E_INVAL, "bad image shape");
     if (!render || !meas || !loss || !drender || !ws) return fail(R2G_E_INVAL, "NULL pointer");
     if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(R2G_E_INVAL, "workspace must be 256-byte aligned");
@@ -534,10 +552,10 @@ r2g_status r2g::projection_loss_impl(int32_t V, int32_t H, int32_t W, const floa
     const int vec4 = (W % 4 == 0) && reinterpret_cast<uintptr_t>(render) % 16 == 0 &&
                      reinterpret_cast<uintptr_t>(meas) % 16 == 0;
     prof_begin(P_LOSS, stream);
-    cudaMemsetAsync(arrive, 0, sizeof(unsigned int), stream);
-    k_ssim<<<(unsigned)L.n_tiles, kSsimThreads, sizeof(SsimSmem), stream>>>(
-        render, meas, meas_sel, H, W, L.tiles_x, tpv, (int)L.n_tiles, win, (float)(1.0 / N), (float)(lambda_ssim / N),
-        drender, partials, arrive, lambda_ssim, (float)(1.0 / N), vec4, loss);
+    if (clear_arrival) cudaMemsetAsync(arrive, 0, sizeof(unsigned int), stream);
+    launch_pdl(k_ssim, dim3((unsigned)L.n_tiles), dim3(kSsimThreads), sizeof(SsimSmem), stream, render, meas, meas_sel,
+               H, W, L.tiles_x, tpv, (int)L.n_tiles, win, (float)(1.0 / N), (float)(lambda_ssim / N), drender,
+               partials, arrive, lambda_ssim, (float)(1.0 / N), vec4, loss);
     prof_end(P_LOSS, stream);
     note_launches(1);
     return check_launch("r2g_projection_loss");

@@ -139,13 +139,43 @@ r2g_status voxelize_backward_impl(int64_t M, const float* mean, const float* sca
                                   const float* rho, int32_t G, const r2g_grid* grids, float Q3, const float* dvol,
                                   float* dmean, float* dscale, float* dquat, float* drho, void* ws, size_t ws_bytes,
                                   cudaStream_t stream, int parts);
+// clear_arrival false: the caller has cleared the arrival counter earlier on the
+// stream (projection_loss_clear), so that the SSIM kernel follows the previous
+// kernel directly and can take a programmatic dependent launch.
 r2g_status projection_loss_impl(int32_t V, int32_t H, int32_t W, const float* render, const float* meas,
                                 const int* meas_sel, float lambda_ssim, float* loss, float* drender, void* ws,
-                                size_t ws_bytes, cudaStream_t stream);
+                                size_t ws_bytes, cudaStream_t stream, bool clear_arrival = true);
+r2g_status projection_loss_clear(int32_t V, int32_t H, int32_t W, void* ws, size_t ws_bytes, cudaStream_t stream);
 r2g_status adam_impl(int64_t M, float* raw, float* act, float* grad, float* m, float* v, int32_t it,
                      const int* it_dev, const r2g_adam_opts* opts, cudaStream_t stream);
 
 // ---------------------------------------------------------------- device helpers
+
+// Programmatic dependent launch.  A kernel launched by launch_pdl may become
+// resident while the kernel before it on the stream is still running; it calls
+// pdl_wait() before its first access to anything earlier kernels wrote (the wait
+// returns once they have completed and their writes are visible; without the
+// launch attribute it returns at once).  pdl_trigger() lets the next kernel
+// launch once every CTA of this one has called it (called at CTA start: the
+// dependents then only take resources this grid no longer needs to start).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args&&>(args)...);
+}
 
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;

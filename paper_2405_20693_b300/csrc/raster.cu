@@ -416,6 +416,8 @@ __global__ void __launch_bounds__(32 * kFwdWarps) k_splat_fwd(const float4* __re
     static_assert(TW % BW == 0 && TH % 8 == 0 && NW <= kFwdMaxBlocks && kChunk == 128, "tile shape");
     __shared__ float4 s_a[kFwdWarps][kChunk];
     __shared__ float4 s_b[kFwdWarps][kChunk];
+    pdl_trigger();
+    pdl_wait();  // the lists and records of the build before
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned long long gw = (unsigned long long)blockIdx.x * kFwdWarps + warp;
     const unsigned long long it = gw / NW;
@@ -610,6 +612,8 @@ __global__ void __launch_bounds__(kBwdThreads) k_splat_bwd(const float4* __restr
     __shared__ uint32_t s_gid[kChunk];     // Gaussian id
     __shared__ uint32_t s_excl[kChunk + 1];  // exclusive prefix of the unit counts; [kChunk] = total
     __shared__ uint32_t s_w[kBwdThreads / 32];
+    pdl_trigger();
+    pdl_wait();  // dL/dI of the loss before
     const unsigned long long it = blockIdx.x;
     if (it >= item_st->n_keys) return;
     const uint64_t item = items[it];
@@ -760,11 +764,14 @@ __global__ void __launch_bounds__(128) k_project_bwd(Params G, const float* __re
                                                      float* __restrict__ drho, AdamState adam) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= M) return;
+    // parameters and Adam moments: written before this step's kernels began
     float p[3], s[3], q[4];
     load_gaussian(G, i, p, s, q);
     const float rho = G.rho[i];
     AdamPre pre;
-    if (ADAM) adam_prefetch(adam, i, pre);
+    if (ADAM) adam_prefetch_state(adam, i, pre);
+    pdl_wait();  // the backward moments, and the gradient already in adam.grad
+    if (ADAM) adam_prefetch_grad(adam, i, pre);
     float gp[3] = {0.f, 0.f, 0.f}, gs[3] = {0.f, 0.f, 0.f}, gR[3][3] = {{0.f}}, grho = 0.f;
     float dens_g = 0.f, dens_n = 0.f;  // adaptive-control statistics of this call
     Proj P;
@@ -1058,9 +1065,9 @@ template <int TW, int TH, bool COUNT>
 void fwd_shape(const FwdArgs& f, long long M, const RasterLayout& L, long long icap, int H, int W, float Tq,
                float* image, WsStatus* st, cudaStream_t s) {
     const unsigned long long warps = (unsigned long long)icap * FwdShape<TW, TH>::NW;
-    k_splat_fwd<TW, TH, COUNT><<<(unsigned)((warps + kFwdWarps - 1) / kFwdWarps), 32 * kFwdWarps, 0, s>>>(
-        f.rec, f.srec, f.ranges, f.sorted, f.items, f.item_st, f.partial, f.item_off, f.key_done, M, L.tiles_x,
-        L.tiles_per_view, H, W, Tq, image, st);
+    launch_pdl(k_splat_fwd<TW, TH, COUNT>, dim3((unsigned)((warps + kFwdWarps - 1) / kFwdWarps)),
+               dim3(32 * kFwdWarps), 0, s, f.rec, f.srec, f.ranges, f.sorted, f.items, f.item_st, f.partial,
+               f.item_off, f.key_done, M, L.tiles_x, L.tiles_per_view, H, W, Tq, image, st);
 }
 
 template <bool COUNT>
@@ -1081,9 +1088,8 @@ void launch_bwd(int tw, int th, const float4* rec, const float4* srec, const uin
                 int H, int W, float Tq, const float* dimage, float4* mom, cudaStream_t s) {
     const unsigned grid = (unsigned)icap;
 #define R2G_BWD(TW, TH)                                                                                       \
-    k_splat_bwd<TW, TH, kBwdUnitW, kBwdUnitH><<<grid, kBwdThreads, 0, s>>>(rec, srec, ranges, sorted, items,   \
-                                                                           item_st, M, L.tiles_x,               \
-                                                                           L.tiles_per_view, H, W, Tq, dimage, mom)
+    launch_pdl(k_splat_bwd<TW, TH, kBwdUnitW, kBwdUnitH>, dim3(grid), dim3(kBwdThreads), 0, s, rec, srec, ranges, \
+               sorted, items, item_st, M, L.tiles_x, L.tiles_per_view, H, W, Tq, dimage, mom)
     if (tw == 16 && th == 16)
         R2G_BWD(16, 16);
     else if (tw == 8 && th == 8)
@@ -1267,11 +1273,12 @@ r2g_status r2g::rasterize_backward_impl(int64_t M, const float* mean, const floa
         const unsigned grid = (unsigned)((M + 127) / 128);
         prof_begin(P_PROJECT_BWD, stream);
         if (adam)
-            k_project_bwd<true><<<grid, 128, 0, stream>>>(G, views, view_sel, camf(cam, opts), opts->Q, M, V, rec, mom,
-                                                          nullptr, nullptr, nullptr, nullptr, *adam);
+            launch_pdl(k_project_bwd<true>, dim3(grid), dim3(128), 0, stream, G, views, view_sel, camf(cam, opts),
+                       opts->Q, M, V, rec, mom, (float*)nullptr, (float*)nullptr, (float*)nullptr, (float*)nullptr,
+                       *adam);
         else
-            k_project_bwd<false><<<grid, 128, 0, stream>>>(G, views, view_sel, camf(cam, opts), opts->Q, M, V, rec, mom,
-                                                           dmean, dscale, dquat, drho, AdamState{});
+            launch_pdl(k_project_bwd<false>, dim3(grid), dim3(128), 0, stream, G, views, view_sel, camf(cam, opts),
+                       opts->Q, M, V, rec, mom, dmean, dscale, dquat, drho, AdamState{});
         prof_end(P_PROJECT_BWD, stream);
         note_launches(1);
     }

@@ -129,11 +129,15 @@ R2G_API r2g_status r2g_train_step(const r2g_job* job, const r2g_round_entry* ent
         e_tv = voxelize_backward_impl(M, mean, scale, quat, rho, 1, &grid, J.Q3, J.dvol, dmean, dscale, dquat, drho,
                                       J.voxel_ws, J.voxel_ws_bytes, tv,
                                       kVoxBwdMoments | kVoxBwdChain | kVoxBwdAssign);
-    r2g_status e_px = rasterize_impl(M, mean, scale, quat, rho, 1, J.views, view_sel, &J.cam, &J.ropts, J.image,
-                                     J.raster_ws, J.raster_ws_bytes, stream);
+    // the loss's arrival counter is cleared first, so that no copy sits between the
+    // rasterizer and the loss kernel (which then takes a programmatic dependent launch)
+    r2g_status e_px = projection_loss_clear(1, J.cam.H, J.cam.W, J.loss_ws, J.loss_ws_bytes, stream);
+    if (!e_px)
+        e_px = rasterize_impl(M, mean, scale, quat, rho, 1, J.views, view_sel, &J.cam, &J.ropts, J.image,
+                              J.raster_ws, J.raster_ws_bytes, stream);
     if (!e_px)
         e_px = projection_loss_impl(1, J.cam.H, J.cam.W, J.image, J.meas, view_sel, J.lambda_ssim, J.loss, J.dimage,
-                                    J.loss_ws, J.loss_ws_bytes, stream);
+                                    J.loss_ws, J.loss_ws_bytes, stream, false);
     if (!e_px)
         e_px = rasterize_backward_impl(M, mean, scale, quat, rho, 1, J.views, view_sel, &J.cam, &J.ropts, J.dimage,
                                        dmean, dscale, dquat, drho, J.raster_ws, J.raster_ws_bytes, stream,
