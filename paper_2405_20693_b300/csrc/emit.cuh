@@ -551,6 +551,7 @@ __global__ void __launch_bounds__(256) k_plists_coop(Proj proj, Op op, long long
     grid_barrier(st, 2);
     keys_phase(hist, key_totals, n_keys, fk, pool, sm8);
     grid_barrier(st, 3);
+    pdl_trigger();  // the forward splat may become resident during the scatter
     const unsigned long long lo = before < written ? before : written;
     const unsigned long long hi = before + mine < written ? before + mine : written;
     scatter_block(op, a, b, hist, lo, hi, n_keys, reinterpret_cast<uint32_t(*)[kFusedKeys]>(pool));
