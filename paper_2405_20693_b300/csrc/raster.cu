@@ -71,11 +71,41 @@ __device__ __forceinline__ float fm(float a, float b) { return __fmul_rn(a, b); 
 __device__ __forceinline__ float fa(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ float fs(float a, float b) { return __fsub_rn(a, b); }
 
+// Hardware approximations for the recompute in the backward, where no result has to
+// match the stated sequence bit for bit (1-2 ulp; divisors and roots far from 0 and
+// 2^126): the approximate square root and reciprocal instructions.
+__device__ __forceinline__ float sqrt_fast(float x) {
+    float y;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_fast(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// The operations of the projection: EXACT = the stated sequence (one correctly
+// rounded IEEE operation per step, no contraction), else the fast forms.
+template <bool EXACT>
+struct POps {
+    static __device__ __forceinline__ float mul(float a, float b) { return EXACT ? __fmul_rn(a, b) : a * b; }
+    static __device__ __forceinline__ float add(float a, float b) { return EXACT ? __fadd_rn(a, b) : a + b; }
+    static __device__ __forceinline__ float sub(float a, float b) { return EXACT ? __fsub_rn(a, b) : a - b; }
+    static __device__ __forceinline__ float div(float a, float b) { return EXACT ? __fdiv_rn(a, b) : a * rcp_fast(b); }
+    static __device__ __forceinline__ float sqrt(float x) { return EXACT ? __fsqrt_rn(x) : sqrt_fast(x); }
+};
+
+template <bool EXACT>
 __device__ __forceinline__ void rotation(const float q[4], Proj& P) {
+    using O = POps<EXACT>;
+    const auto fm = O::mul;
+    const auto fa = O::add;
+    const auto fs = O::sub;
     const float n2 = fa(fa(fa(fm(q[0], q[0]), fm(q[1], q[1])), fm(q[2], q[2])), fm(q[3], q[3]));
-    const float n = __fsqrt_rn(n2);
+    const float n = O::sqrt(n2);
     P.qnorm = n;
-    const float w = __fdiv_rn(q[0], n), x = __fdiv_rn(q[1], n), y = __fdiv_rn(q[2], n), z = __fdiv_rn(q[3], n);
+    const float w = O::div(q[0], n), x = O::div(q[1], n), y = O::div(q[2], n), z = O::div(q[3], n);
     P.qn[0] = w;
     P.qn[1] = x;
     P.qn[2] = y;
@@ -93,9 +123,14 @@ __device__ __forceinline__ void rotation(const float q[4], Proj& P) {
     P.R[2][2] = fs(1.0f, fm(2.0f, fa(xx, yy)));
 }
 
+template <bool EXACT = true>
 __device__ __forceinline__ void project_stated(const float p[3], const float s[3], const float q[4],
                                                const float* __restrict__ view, const CamF& cam, Proj& P) {
-    rotation(q, P);
+    using O = POps<EXACT>;
+    const auto fm = O::mul;
+    const auto fa = O::add;
+    const auto fs = O::sub;
+    rotation<EXACT>(q, P);
     P.phx = P.phy = P.al = P.be = P.ga = P.det = 0.0f;
 #pragma unroll
     for (int j = 0; j < 3; ++j)
@@ -107,9 +142,9 @@ __device__ __forceinline__ void project_stated(const float p[3], const float s[3
     P.valid = false;
     if (cam.beam == 1) {
         if (!(P.u[2] > cam.near_plane)) return;
-        P.f = __fdiv_rn(cam.L_SD, P.u[2]);
-        P.j02 = -__fdiv_rn(fm(P.f, P.u[0]), P.u[2]);
-        P.j12 = -__fdiv_rn(fm(P.f, P.u[1]), P.u[2]);
+        P.f = O::div(cam.L_SD, P.u[2]);
+        P.j02 = -O::div(fm(P.f, P.u[0]), P.u[2]);
+        P.j12 = -O::div(fm(P.f, P.u[1]), P.u[2]);
         P.phx = fm(P.f, P.u[0]);
         P.phy = fm(P.f, P.u[1]);
 #pragma unroll
@@ -190,8 +225,8 @@ __device__ __forceinline__ Bound pixel_bound(const Proj& P, const CamF& cam, flo
 __device__ __forceinline__ float kappa_of(const Proj& P, const float s[3], const float* __restrict__ view,
                                           const CamF& cam, float om[3], float v[3]) {
     if (cam.beam == 1) {
-        const float l = sqrtf(P.u[0] * P.u[0] + P.u[1] * P.u[1] + P.u[2] * P.u[2]);
-        const float n0 = P.u[0] / l, n1 = P.u[1] / l, n2 = P.u[2] / l;
+        const float il = rsqrtf(P.u[0] * P.u[0] + P.u[1] * P.u[1] + P.u[2] * P.u[2]);
+        const float n0 = P.u[0] * il, n1 = P.u[1] * il, n2 = P.u[2] * il;
 #pragma unroll
         for (int k = 0; k < 3; ++k) om[k] = view[k] * n0 + view[3 + k] * n1 + view[6 + k] * n2;
     } else {
@@ -202,7 +237,7 @@ __device__ __forceinline__ float kappa_of(const Proj& P, const float s[3], const
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         v[k] = P.R[0][k] * om[0] + P.R[1][k] * om[1] + P.R[2][k] * om[2];
-        kap += v[k] * v[k] / (s[k] * s[k]);
+        kap += v[k] * v[k] * rcp_fast(s[k] * s[k]);
     }
     return kap;
 }
@@ -245,13 +280,13 @@ __device__ __forceinline__ uint32_t project_one(const Params& G, const float* __
         } else {
             float om[3], vv[3];
             const float kap = kappa_of(P, s, view, cam, om, vv);
-            rhohat = sqrtf(kTwoPi / kap) * G.rho[i];
+            rhohat = sqrt_fast(kTwoPi * rcp_fast(kap)) * G.rho[i];
         }
     }
     if (rec) {
         float4 a, c;
         if (b.ok) {
-            const float id = 1.0f / P.det;
+            const float id = rcp_fast(P.det);  // the bound above is the stated one; the record need not be
             const float ca = P.ga * id * cam.pu * cam.pu;      // conic in pixel units
             const float cb = -P.be * id * cam.pu * cam.pv;
             const float cc = P.al * id * cam.pv * cam.pv;
@@ -746,10 +781,11 @@ __device__ __forceinline__ void quat_grad(const float qn[4], float qnorm, const 
     dy += 2.f * z * g[2][1]; dz += 2.f * y * g[2][1]; dw += 2.f * x * g[2][1]; dx += 2.f * w * g[2][1];
     dx -= 4.f * x * g[2][2]; dy -= 4.f * y * g[2][2];
     const float dot = w * dw + x * dx + y * dy + z * dz;
-    dq[0] = (dw - w * dot) / qnorm;
-    dq[1] = (dx - x * dot) / qnorm;
-    dq[2] = (dy - y * dot) / qnorm;
-    dq[3] = (dz - z * dot) / qnorm;
+    const float iq = rcp_fast(qnorm);
+    dq[0] = (dw - w * dot) * iq;
+    dq[1] = (dx - x * dot) * iq;
+    dq[2] = (dy - y * dot) * iq;
+    dq[3] = (dz - z * dot) * iq;
 }
 
 // ADAM: instead of adding the gradients to dmean .. drho, add them to the
@@ -785,10 +821,10 @@ __global__ void __launch_bounds__(128) k_project_bwd(Params G, const float* __re
         mom[2 * r + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
         const float rhohat = rec[2 * r + 1].y;
         const float* view = views + 12 * (view_sel ? view_sel[v] : v);
-        project_stated(p, s, q, view, cam, P);
+        project_stated<false>(p, s, q, view, cam, P);  // values only: no bound is formed here
         have_rot = true;
         // --- moments -> gradients of the pixel-unit record
-        const float D = P.det, id = 1.0f / D;
+        const float D = P.det, id = rcp_fast(D);
         const float ca = P.ga * id, cb = -P.be * id, cc = P.al * id;  // conic, detector units
         const float pa = ca * cam.pu * cam.pu, pb = cb * cam.pu * cam.pv, pc = cc * cam.pv * cam.pv;
         const float S0 = m0.x, Sx = m0.y, Sy = m0.z, Sxx = m0.w, Sxy = m1.x, Syy = m1.y;
@@ -801,7 +837,7 @@ __global__ void __launch_bounds__(128) k_project_bwd(Params G, const float* __re
             dens_n += 1.f;
         }
         // --- to detector units
-        const float d_phx = d_cx / cam.pu, d_phy = d_cy / cam.pv;
+        const float d_phx = d_cx * rcp_fast(cam.pu), d_phy = d_cy * rcp_fast(cam.pv);
         const float d_a = d_pa * cam.pu * cam.pu, d_b = d_pb * cam.pu * cam.pv, d_c = d_pc * cam.pv * cam.pv;
         // --- conic (a, b, c) = (gamma, -beta, alpha) / D  ->  Sigma^ (alpha, beta, gamma)
         const float al = P.al, be = P.be, ga = P.ga, iD2 = id * id;
@@ -840,15 +876,16 @@ __global__ void __launch_bounds__(128) k_project_bwd(Params G, const float* __re
         } else {
             float om[3], vv[3];
             const float kap = kappa_of(P, s, view, cam, om, vv);
-            const float mu = sqrtf(kTwoPi / kap);
+            const float ikap = rcp_fast(kap);
+            const float mu = sqrt_fast(kTwoPi * ikap);
             grho += d_rhohat * mu;
-            const float d_kap = -0.5f * d_rhohat * rho * mu / kap;
+            const float d_kap = -0.5f * d_rhohat * rho * mu * ikap;
             float dv[3];
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                const float is2 = 1.0f / (s[k] * s[k]);
+                const float is = rcp_fast(s[k]), is2 = is * is;
                 dv[k] = 2.f * d_kap * vv[k] * is2;
-                gs[k] += -2.f * d_kap * vv[k] * vv[k] * is2 / s[k];
+                gs[k] += -2.f * d_kap * vv[k] * vv[k] * is2 * is;
             }
 #pragma unroll
             for (int j = 0; j < 3; ++j) {
@@ -861,7 +898,7 @@ __global__ void __launch_bounds__(128) k_project_bwd(Params G, const float* __re
         float du[3] = {0.f, 0.f, 0.f};
         if (cam.beam == 1) {
             const float L = cam.L_SD, u0 = P.u[0], u1 = P.u[1], u2 = P.u[2];
-            const float iu2 = 1.0f / u2;
+            const float iu2 = rcp_fast(u2);
             // T rows: f W0 + j02 W2, f W1 + j12 W2
             float d_f = 0.f, d_j02 = 0.f, d_j12 = 0.f;
 #pragma unroll
@@ -878,7 +915,7 @@ __global__ void __launch_bounds__(128) k_project_bwd(Params G, const float* __re
                      (d_phx * u0 + d_phy * u1) * f * iu2;
             (void)L;
             // omega = W^T u/|u|
-            const float l = sqrtf(u0 * u0 + u1 * u1 + u2 * u2), il = 1.0f / l;
+            const float il = rsqrtf(u0 * u0 + u1 * u1 + u2 * u2);
             const float n[3] = {u0 * il, u1 * il, u2 * il};
             float dn[3];
 #pragma unroll
