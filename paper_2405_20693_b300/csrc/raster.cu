@@ -71,20 +71,6 @@ __device__ __forceinline__ float fm(float a, float b) { return __fmul_rn(a, b); 
 __device__ __forceinline__ float fa(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ float fs(float a, float b) { return __fsub_rn(a, b); }
 
-// Hardware approximations for the recompute in the backward, where no result has to
-// match the stated sequence bit for bit (1-2 ulp; divisors and roots far from 0 and
-// 2^126): the approximate square root and reciprocal instructions.
-__device__ __forceinline__ float sqrt_fast(float x) {
-    float y;
-    asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ float rcp_fast(float x) {
-    float y;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
 // The operations of the projection: EXACT = the stated sequence (one correctly
 // rounded IEEE operation per step, no contraction), else the fast forms.
 template <bool EXACT>
