@@ -443,9 +443,10 @@ constexpr unsigned long long kGridSyncSpins = 1ull << 22;
 __device__ __forceinline__ void grid_barrier(WsStatus* st, unsigned int epoch) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
         const unsigned long long target = (unsigned long long)epoch * gridDim.x;
-        atomicAdd(&st->grid_sync, 1ull);
+        // release: the block's writes (ordered before this thread by the block
+        // barrier) are visible to any block that observes the arrival
+        asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(&st->grid_sync), "l"(1ull) : "memory");
         unsigned long long spins = 0, seen;
         for (;;) {
             asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(seen) : "l"(&st->grid_sync) : "memory");
@@ -456,7 +457,8 @@ __device__ __forceinline__ void grid_barrier(WsStatus* st, unsigned int epoch) {
             }
             __nanosleep(20);
         }
-        __threadfence();
+        // the acquire load that saw the last arrival orders the block's later reads
+        // (through the block barrier) after every block's writes
     }
     __syncthreads();
 }
