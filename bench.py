@@ -202,14 +202,28 @@ KERNEL_SOURCES = {"splat_bwd": "raster.cu", "splat_fwd": "raster.cu", "project_b
                   "init_select_hist": "fdk.cu", "metrics": "metrics.cu", "densify": "densify.cu"}
 
 
+def _included(csrc: str, name: str, seen: set):
+    """name and the local headers it includes (#include "..."), transitively."""
+    if name in seen or not os.path.exists(os.path.join(csrc, name)):
+        return
+    seen.add(name)
+    with open(os.path.join(csrc, name)) as fh:
+        for line in fh:
+            line = line.strip()
+            if line.startswith('#include "'):
+                _included(csrc, os.path.basename(line.split('"')[1]), seen)
+
+
 def source_hash(kernel: str | None = None):
-    """Hash of the sources a kernel is built from: its .cu file and every .cuh
-    header (all of csrc when kernel is None)."""
+    """Hash of the sources a kernel is built from: its .cu file and the local headers
+    it includes (all of csrc when kernel is None)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2405_20693_b300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if kernel is not None and not (f.endswith(".cuh") or f == KERNEL_SOURCES[kernel]):
-            continue
+    files = set(os.listdir(csrc))
+    if kernel is not None:
+        files = set()
+        _included(csrc, KERNEL_SOURCES[kernel], files)
+    for f in sorted(files):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
