@@ -543,13 +543,19 @@ __global__ void __launch_bounds__(32 * kFwdWarps) k_splat_fwd(const float4* __re
         float* p = partial + it * (size_t)(TW * TH) + ly * TW + lx;
 #pragma unroll
         for (int k = 0; k < PX; ++k) p[k] = acc[k];
-        __threadfence();  // every lane's stores before lane 0's arrival
-        __syncwarp();
+        __syncwarp();  // every lane's stores ordered before lane 0's release
         uint32_t last = 0;
-        if (lane == 0) last = atomicAdd(&key_done[(size_t)tile * kFwdMaxBlocks + wb], 1u) == nch - 1;
+        if (lane == 0) {
+            uint32_t before;
+            asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;"
+                         : "=r"(before)
+                         : "l"(&key_done[(size_t)tile * kFwdMaxBlocks + wb])
+                         : "memory");
+            last = before == nch - 1;
+        }
         last = __shfl_sync(0xffffffffu, last, 0);
         if (!last) return;
-        __threadfence();
+        __syncwarp();  // lane 0's acquire orders the warp's reads of the other chunks' images
         const float* qp = partial + (size_t)item_off[tile] * (TW * TH) + ly * TW + lx;
 #pragma unroll
         for (int k = 0; k < PX; ++k) acc[k] = 0.0f;
