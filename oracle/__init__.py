@@ -18,8 +18,9 @@ itself:
   * SSIM(x, x) = 1 with zero gradient; phantom chords == quadrature of the indicator.
   * the FP32 tile-bound replica is pinned to the FP64 projection (same p^, Sigma^
     to FP32 rounding) and to the gate: every pixel with q <= Q lies in its box.
-Parity unpinned: the Adam step (its formula is restated, not derived; it is
-checked only against a direct transcription of Kingma & Ba's update).
+  * the Adam step: a constant gradient moves every raw parameter by exactly
+    -lr g / (|g| + eps), and two steps with different gradients match the unrolled
+    closed form of the moment recursions (which fixes both decay rates).
 """
 from . import core, losses  # noqa: F401
 from .core import build  # noqa: F401

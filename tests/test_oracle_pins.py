@@ -551,6 +551,35 @@ def test_adam_constant_gradient_closed_form():
     assert abs(losses.lr_at("mean", 30000) - 2e-5) < 1e-18
 
 
+def test_adam_two_step_closed_form():
+    """Two steps with different gradients g1, g2 (groups whose activation is the
+    identity): unrolling the moment recursions gives the bias-corrected moments
+    m^ = (b1 g1 + g2) / (1 + b1) and v^ = (b2 g1^2 + g2^2) / (1 + b2) after step 2,
+    which pins both decay rates and the bias correction (a constant gradient does
+    not: its corrected moments are g and g^2 for any rates)."""
+    b1, b2, eps = 0.9, 0.999, 1e-15
+    g = np.random.default_rng(13)
+    M = 7
+    raw = {"mean": g.standard_normal((M, 3)), "scale": np.zeros((M, 3)), "quat": g.standard_normal((M, 4)),
+           "rho": np.zeros(M)}
+    m = {k: np.zeros_like(v) for k, v in raw.items()}
+    vv = {k: np.zeros_like(v) for k, v in raw.items()}
+    g1 = {k: g.standard_normal(raw[k].shape) for k in raw}
+    g2 = {k: g.standard_normal(raw[k].shape) for k in raw}
+    start = {k: v.copy() for k, v in raw.items()}
+    losses.adam_step(raw, g1, m, vv, 0)
+    after1 = {k: v.copy() for k, v in raw.items()}
+    losses.adam_step(raw, g2, m, vv, 1)
+    for k in ("mean", "quat"):
+        step1 = -losses.lr_at(k, 0) * g1[k] / (np.abs(g1[k]) + eps)
+        mh = (b1 * g1[k] + g2[k]) / (1 + b1)
+        vh = (b2 * g1[k] ** 2 + g2[k] ** 2) / (1 + b2)
+        step2 = -losses.lr_at(k, 1) * mh / (np.sqrt(vh) + eps)
+        assert np.abs((after1[k] - start[k]) - step1).max() <= 1e-12 * losses.LR0[k]
+        assert np.abs((raw[k] - after1[k]) - step2).max() <= 1e-12 * losses.LR0[k]
+    assert losses.lr_at("mean", 1) == pytest.approx(2e-4 * 0.1 ** (1 / 30000), rel=1e-14)
+
+
 # ----------------------------------------------------------------------------- phantom + noise
 
 
