@@ -470,10 +470,28 @@ def test_ssim_identities():
     assert np.abs(losses.ssim_grad(x, x)).max() < 1e-13
     y = g.uniform(0, 1, (20, 24))
     assert abs(losses.ssim(x, y) - losses.ssim(y, x)) < 1e-14
-    # constant images: interior SSIM = (2ab + C1) / (a^2 + b^2 + C1)
+    # constant images: interior SSIM = (2ab + C1) / (a^2 + b^2 + C1), C1 = (0.01 L)^2 with L = 1
     a, b = 0.7, 0.2
     S = losses.ssim_parts(np.full((30, 30), a), np.full((30, 30), b), losses.gaussian_window())[-1]
-    assert abs(S[15, 15] - (2 * a * b + losses.C1) / (a * a + b * b + losses.C1)) < 1e-12
+    assert abs(S[15, 15] - (2 * a * b + 1e-4) / (a * a + b * b + 1e-4)) < 1e-12
+
+
+def test_ssim_of_column_ramps_closed_form():
+    """x = a + s c, y = b + t c along the columns c: away from the zero-padded border the
+    window's means are a + s c and b + t c (the window is symmetric) and its variances
+    and covariance s^2 V, t^2 V, s t V, V the window's second moment; so SSIM has a
+    closed form that fixes C1 = (0.01)^2, C2 = (0.03)^2 and the 11-tap, sigma 1.5
+    Gaussian window."""
+    k = np.arange(11) - 5.0
+    w = np.exp(-k * k / (2 * 1.5 ** 2))
+    w /= w.sum()
+    V = float((w * k * k).sum())
+    c = np.arange(40, dtype=np.float64)[None, :].repeat(40, axis=0)
+    a, s_, b, t = 0.3, 0.02, 0.5, -0.015
+    S = losses.ssim_parts(a + s_ * c, b + t * c, losses.gaussian_window())[-1]
+    mx, my = a + s_ * c, b + t * c
+    want = ((2 * mx * my + 1e-4) * (2 * s_ * t * V + 9e-4)) / ((mx * mx + my * my + 1e-4) * ((s_ * s_ + t * t) * V + 9e-4))
+    assert np.abs(S[10:30, 10:30] - want[10:30, 10:30]).max() < 1e-12
 
 
 def test_ssim_gradient_matches_complex_step():
