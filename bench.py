@@ -1,20 +1,25 @@
 #!/usr/bin/env python
 """Benchmark of the R^2-Gaussian hot path on B300: fwd+bwd Gaussian-pixel evals/s.
 
-One step = one training iteration of the one-scan cone-beam workload (50,000
-Gaussians initialised from a seeded 40-ellipsoid 256^3 phantom; source-to-origin
-1000 mm, source-to-detector 1500 mm, 50 views over 360 deg, 512^2 detector at
-0.8 mm): rasterize one view, L1 + 0.25 D-SSIM, voxelize a random 32^3 TV patch
-with weight 0.05, full backward through both, fused Adam -- all in libr2g.so.
-The metric counts the (pixel, Gaussian) and (voxel, Gaussian) pairs that pass
-the gates in that step, once, over the device time of the whole step.
+Headline step (differentiation at scale): 500,000 anisotropic, rotated Gaussians
+sampled from a seeded 40-ellipsoid 256^3 phantom (per-axis scales log-uniform in
+[0.002, 0.05]); cone beam with source-to-origin 1000 mm and source-to-detector
+1500 mm; all 75 views of 512^2 at 0.8 mm rasterized in one launch against
+projections with Poisson noise (1e5 photons per ray); L1 + 0.25 D-SSIM over the
+75 views; 8 random 32^3 TV patches (weight 0.05) voxelized, with their TV; the
+full 256^3 volume voxelized (forward); the full backward through the rasterizer
+and the patches, and the fused Adam step -- one r2g_train_step call, all in
+libr2g.so.  The metric counts the (pixel, Gaussian) and (voxel, Gaussian) pairs
+that pass the gates in that step, once, over the device time of the whole step.
+The one-scan step (50,000 Gaussians, one view and one TV patch per iteration) is
+reported beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 N > 1 runs under torchrun as independent replicas (one scan per rank, no data
 exchange: the path has nothing to reduce across scans); value = all ranks'
 pairs / the slowest rank's time.  --impl reference times the FP64 CPU oracle on
-the same workload (a bounded number of full steps) on the host cores.
+the host cores on bounded samples of the same workload.
 """
 from __future__ import annotations
 
@@ -35,10 +40,17 @@ sys.path.insert(0, ROOT)
 
 METRIC = "fwd+bwd Gaussian-pixel evals/s"
 N_VIEWS, M_GAUSS, D_TV, N_OUT = 50, 50_000, 32, 256
+SCALE_M, SCALE_V, SCALE_NP = 500_000, 75, 8     # the headline (differentiation-at-scale) workload
+SCALE_TILES = ((16, 16), (32, 32), (8, 8), (32, 8))
 SM_COUNT = 148
 MUFU_PER_CLK = 16          # ex2 per SM per clock
 FP32_PER_CLK = 128         # FP32 lanes per SM per clock
-OPS_FWD, OPS_BWD = 6, 14   # algorithmic FP32 ops per gated pair (forward, backward)
+# FP32 operations charged per gated pair (the scope table's count of the work a pair
+# needs: forward ~10 -- 2 FADD, 5 FMUL/FFMA for q, a compare, the -1/2 log2(e) fold,
+# the accumulate; backward ~20 -- the recomputed forward and ~10 FFMA for the six
+# moments); the kernels' own reduced counts (incremental quadratics) beside them
+OPS_FWD, OPS_BWD = 10, 20
+OWN_OPS_FWD, OWN_OPS_BWD = 6, 14
 
 
 def peaks():
@@ -84,56 +96,80 @@ def step_sequence(seed: int, n: int):
 
 
 class ClockSampler:
-    """nvidia-smi samples every 100 ms while the timed region runs."""
+    """SM clock, its maximum, power and the clock-event (throttle) reasons, sampled
+    every 200 ms through NVML (read-only queries; nothing is set) while the timed
+    region runs.  Falls back to one nvidia-smi query per sample if NVML is missing.
+    (A long-running `nvidia-smi -lms` whose stdout is a pipe buffers its lines and
+    loses them when it is terminated, which left no samples.)"""
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
-         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-         "clocks_event_reasons.sw_power_cap")
+    REASONS = (("hw_slowdown", 0x8), ("hw_thermal_slowdown", 0x40), ("sw_thermal_slowdown", 0x20),
+               ("sw_power_cap", 0x4), ("hw_power_brake_slowdown", 0x80))
 
-    def __init__(self, gpu_id: str):
-        self.idx = gpu_id
-        self.proc = None
-        self.lines = []
+    def __init__(self, gpu_uuid: str | None, index: int = 0, period_s: float = 0.2):
+        self.uuid, self.index, self.period = gpu_uuid, index, period_s
+        self.samples = []   # (sm_mhz, sm_max_mhz, power_w, reasons bitmask)
+        self._stop = threading.Event()
+        self._t = None
+        self._nvml = None
+        self._h = None
+        self.source = None
+
+    def _open(self):
+        try:
+            import pynvml
+
+            pynvml.nvmlInit()
+            h = None
+            if self.uuid:
+                try:
+                    h = pynvml.nvmlDeviceGetHandleByUUID(self.uuid)
+                except Exception:
+                    h = None
+            if h is None:
+                h = pynvml.nvmlDeviceGetHandleByIndex(self.index)
+            self._nvml, self._h, self.source = pynvml, h, "nvml"
+        except Exception:
+            self._nvml, self.source = None, "nvidia-smi"
+
+    def _one(self):
+        if self._nvml is not None:
+            n, h = self._nvml, self._h
+            sm = n.nvmlDeviceGetClockInfo(h, n.NVML_CLOCK_SM)
+            smax = n.nvmlDeviceGetMaxClockInfo(h, n.NVML_CLOCK_SM)
+            pw = n.nvmlDeviceGetPowerUsage(h) / 1000.0
+            rs = n.nvmlDeviceGetCurrentClocksEventReasons(h)
+            return float(sm), float(smax), float(pw), int(rs)
+        q = "clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active"
+        target = self.uuid or str(self.index)
+        out = subprocess.run(["nvidia-smi", f"--id={target}", f"--query-gpu={q}", "--format=csv,noheader,nounits"],
+                             capture_output=True, text=True, timeout=5).stdout.strip().split(",")
+        return float(out[0]), float(out[1]), float(out[2]), int(out[3].strip(), 16)
+
+    def _run(self):
+        while not self._stop.is_set():
+            try:
+                self.samples.append(self._one())
+            except Exception:
+                pass
+            self._stop.wait(self.period)
 
     def start(self):
-        try:
-            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
-                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.t = threading.Thread(target=self._read, daemon=True)
-            self.t.start()
-        except Exception:
-            self.proc = None
-
-    def _read(self):
-        for line in self.proc.stdout:
-            self.lines.append(line.strip())
+        self._open()
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
 
     def stop(self):
-        if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except Exception:
-            self.proc.kill()
-        self.t.join(timeout=2)
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            f = [x.strip() for x in ln.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                sm.append(float(f[1]))
-                smax.append(float(f[2]))
-            except ValueError:
-                continue
-            for name, val in zip(names, f[5:9]):
-                if val.lower().startswith("active"):
-                    reasons.add(name)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "samples": len(sm), "reasons": sorted(reasons)}
+        self._stop.set()
+        if self._t is not None:
+            self._t.join(timeout=10)
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "samples": 0, "source": self.source,
+                    "reasons": ["no clock samples"]}
+        sm = [x[0] for x in self.samples]
+        reasons = sorted({name for name, bit in self.REASONS for x in self.samples if x[3] & bit})
+        return {"sm_mhz": statistics.median(sm), "sm_min_mhz": min(sm), "sm_max_mhz": max(x[1] for x in self.samples),
+                "power_w_max": max(x[2] for x in self.samples), "samples": len(sm), "source": self.source,
+                "period_ms": int(1000 * self.period), "reasons": reasons}
 
 
 # ----------------------------------------------------------------------------- reference arm / CPU baseline
@@ -162,26 +198,189 @@ def oracle_steps(G, cam, views, meas, seq, n_steps, budget_s=None):
     return pairs, time.perf_counter() - t0, done
 
 
+def make_scale_workload(seed: int, device):
+    """The headline workload: 500k Gaussians sampled from the phantom's support
+    (per-axis scales log-U[0.002, 0.05], uniform random rotations, rho = 0.15 V(p)),
+    75 cone-beam views of 512^2, and (with a device for the chord evaluation) the
+    measured projections with Poisson noise at 1e5 photons per ray."""
+    from paper_2405_20693_b300 import inputs as I
+
+    ph, vol = I.normalised_phantom(seed, N_OUT)
+    G = I.init_from_volume(vol, I.cube_grid(N_OUT), SCALE_M, seed + 3, scale_override=(0.002, 0.05), random_rot=True)
+    cam = I.cone_camera(512, 512)
+    views = I.view_table(I.even_angles(SCALE_V), I.CONE_L_SO)
+    meas = None
+    if device is not None:
+        clean = I.phantom_projections(ph, views, cam, device=device)
+        meas = I.poisson_noise(clean, seed + 3, 1e5).astype(np.float32)
+    return G, cam, views, meas
+
+
+def scale_patch_origins(seed: int, n_steps: int) -> np.ndarray:
+    """Origins of the 8 TV patches of each step, [n_steps, 8, 3] float32: offsets
+    U{0..224}^3 voxels of the 256^3 grid over [-1, 1]^3 (seeded)."""
+    g = np.random.Generator(np.random.PCG64(seed + 4))
+    offs = g.integers(0, N_OUT - D_TV + 1, (n_steps, SCALE_NP, 3))
+    return (-1.0 + offs * (2.0 / N_OUT)).astype(np.float32)
+
+
+def host_cpu():
+    """(threads this process may use, CPU model)."""
+    try:
+        n = len(os.sched_getaffinity(0))
+    except Exception:
+        n = os.cpu_count() or 1
+    model = "unknown"
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except Exception:
+        pass
+    return n, model
+
+
+# worker side of the oracle sample: the upstream gradients are drawn once per process
+_SAMPLE_CACHE = {}
+
+
+def _oracle_sample_shard(task):
+    """One shard of the oracle sample: forward and backward of the sampled Gaussians
+    over all views (render, render_backward with a seeded dL/dI), and the voxelizer
+    forward of the patches and the full volume with the patches' backward (seeded
+    dL/dV).  Returns (pairs, seconds)."""
+    from oracle import core
+    from paper_2405_20693_b300 import inputs as I
+
+    G, views, cam, patch_gd, full_gd = task
+    key = (views.shape[0], cam.H, cam.W, patch_gd.shape[0])
+    if key not in _SAMPLE_CACHE:
+        g = np.random.default_rng(11)
+        _SAMPLE_CACHE[key] = (g.standard_normal((views.shape[0], cam.H, cam.W)) * 1e-6,
+                              g.standard_normal(patch_gd.shape[0] * D_TV ** 3) * 1e-4)
+    dimg, dvol = _SAMPLE_CACHE[key]
+    t0 = time.perf_counter()
+    _, pp = core.render(G, views, cam, Q=9.0)
+    core.render_backward(G, views, cam, dimg, Q=9.0)
+    _, vp = core.voxelize(G, patch_gd, 11.345)
+    core.voxelize_backward(G, patch_gd, dvol, 11.345)
+    _, fp = core.voxelize(G, full_gd, 11.345)
+    return pp + vp + fp, time.perf_counter() - t0
+
+
+class OracleSampler:
+    """Times the FP64 oracle on bounded samples of the headline workload on the host
+    cores: each sample is a seeded subset of the Gaussians, split over a spawned
+    process pool (one shard per worker) or run in this process (cores = 1).  The
+    oracle runs as it stands; only the Gaussians are partitioned across processes.
+    The projection loss (a fixed per-pixel cost, small next to the pairs at this
+    size) is not part of the sample."""
+
+    def __init__(self, G, views, cam, workers: int):
+        from paper_2405_20693_b300 import inputs as I
+
+        self.G, self.views, self.cam = G, views, cam
+        self.full_gd = np.asarray(I.cube_grid(N_OUT), np.float64)
+        self.workers = max(1, int(workers))
+        self.pool = None
+        if self.workers > 1:
+            import multiprocessing as mp
+
+            self.pool = mp.get_context("spawn").Pool(self.workers)
+
+    def patch_grids(self, origins):
+        from paper_2405_20693_b300 import inputs as I
+
+        return np.stack([np.asarray(I.grid_desc(o, (2.0 / N_OUT,) * 3, (D_TV,) * 3), np.float64) for o in origins])
+
+    def run(self, n_gauss: int, seed: int, origins):
+        """(pairs, wall seconds) of one sample of n_gauss Gaussians."""
+        idx = np.sort(np.random.default_rng(seed).choice(self.G.M, size=n_gauss, replace=False))
+        sub = self.G.subset(idx).astype(np.float64)
+        gd = self.patch_grids(origins)
+        if self.pool is None:
+            p, _ = _oracle_sample_shard((sub, self.views, self.cam, gd, self.full_gd))
+            return p, None
+        shards = np.array_split(np.arange(n_gauss), self.workers)
+        tasks = [(sub.subset(s), self.views, self.cam, gd, self.full_gd) for s in shards if len(s)]
+        t0 = time.perf_counter()
+        res = self.pool.map(_oracle_sample_shard, tasks)
+        return sum(r[0] for r in res), time.perf_counter() - t0
+
+    def timed(self, n_gauss: int, seed: int, origins):
+        t0 = time.perf_counter()
+        p, wall = self.run(n_gauss, seed, origins)
+        return p, (wall if wall is not None else time.perf_counter() - t0)
+
+    def close(self):
+        if self.pool is not None:
+            self.pool.close()
+            self.pool.join()
+
+
+def cpu_baseline_scale(G, views, cam, n_gauss=6000):
+    """The oracle's pairs/s on one bounded sample of the headline workload, on all the
+    host's cores and on one core (same sample)."""
+    cores, model = host_cpu()
+    origins = scale_patch_origins(0, 1)[0]
+    out = {"unit": "pairs/s", "kind": "oracle", "cpu_model": model, "nproc": cores}
+    one = OracleSampler(G, views, cam, 1)
+    one.timed(200, 1, origins)  # loads the library
+    p1, s1 = one.timed(n_gauss, 2, origins)
+    out["single_core"] = {"value": p1 / s1, "cores": 1, "seconds": s1, "pairs": p1}
+    if cores > 1:
+        w = min(cores, 32)
+        allc = OracleSampler(G, views, cam, w)
+        allc.timed(w * 4, 1, origins)  # spawns and warms the workers
+        pa, sa = allc.timed(n_gauss, 2, origins)
+        allc.close()
+        out["all_cores"] = {"value": pa / sa, "cores": w, "seconds": sa, "pairs": pa}
+    best = out.get("all_cores", out["single_core"])
+    out.update(value=best["value"], cores=best["cores"],
+               sample=f"{n_gauss} seeded Gaussians of the 500k set (the same subset on 1 core and on "
+                      f"{best['cores']} processes, Gaussians split evenly): FP64 oracle render + adjoint over all "
+                      f"75 views of 512^2 with a seeded dL/dI, voxelize + adjoint of 8 32^3 patches, voxelize of "
+                      f"the 256^3 volume; the projection loss is not in the sample")
+    return out
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    G, cam, views, meas = make_workload(0, None if not _has_cuda() else "cuda")
-    seq = step_sequence(0, args.warmup + args.steps)
-    # each oracle step is a full training step (~5 s single-threaded); the run is
-    # bounded by time: one warm-up step, then timed steps until K or 120 s
-    oracle_steps(G, cam, views, meas, seq, 1)
-    pairs, secs, done = oracle_steps(G, cam, views, meas, seq[args.warmup:], args.steps, budget_s=120.0)
+    G, cam, views, _ = make_scale_workload(0, None)
+    cores, model = host_cpu()
+    w = min(cores, 32)
+    smp = OracleSampler(G, views, cam, w)
+    n_step = 400 * w  # about a second of oracle work per step on each worker
+    origins = scale_patch_origins(0, args.warmup + args.steps)
+    for k in range(args.warmup):
+        smp.timed(n_step, 1000 + k, origins[k])
+    pairs, secs = 0, 0.0
+    for k in range(args.steps):
+        p, t = smp.timed(n_step, 2000 + k, origins[args.warmup + k])
+        pairs += p
+        secs += t
+    smp.close()
     value = pairs / secs
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": args.gpus,
-            "steps": done, "warmup": 1, "ms_per_step": 1e3 * secs / done,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "one cone-beam scan, 50k Gaussians, 512^2 x 50 views, 1 view + 32^3 TV patch "
-                                   "per step", "oracle": "FP64 C++ scatter form + numpy losses, single thread"},
-            "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{done} full training steps of the same workload (time-bounded at 120 s "
-                                       f"of the {args.steps} asked)"},
+            "config": {"workload": SCALE_WORKLOAD, "oracle": "FP64 C++ scatter form, one process per core"},
+            "cpu_baseline": {"value": value, "unit": "pairs/s", "cores": w, "kind": "oracle", "nproc": cores,
+                             "cpu_model": model,
+                             "sample": f"each step {n_step} seeded Gaussians of the 500k set split over {w} "
+                                       "processes: render + adjoint over all 75 views, voxelize + adjoint of the "
+                                       "step's 8 TV patches, voxelize of the 256^3 volume (no projection loss)"},
             "e2e": {"value": value, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+SCALE_WORKLOAD = ("differentiation at scale: 500k Gaussians (per-axis scales log-U[0.002, 0.05], random rotations) "
+                  "from a seeded 40-ellipsoid 256^3 phantom; cone beam L_SO 1000 mm, L_SD 1500 mm; all 75 views x "
+                  "512^2 at 0.8 mm in one launch against Poisson-noised projections (1e5 photons/ray), L1 + 0.25 "
+                  "D-SSIM; 8 random 32^3 TV patches (0.05) and the full 256^3 volume voxelized; full backward; Adam")
 
 
 def _has_cuda():
@@ -596,34 +795,223 @@ def slowest(dist, seconds: float, device) -> float:
     return float(tt[0])
 
 
-def run_ours(args, rank, world, local_rank):
+def splat_roofline(name: str, units: float, avg_ms: float, pk: dict) -> dict:
+    """ALU roofline of a splat kernel: units (gated pairs per launch) / mean launch
+    time, against min(MUFU ex2 rate, FP32 rate / ops per pair) at the maximum SM
+    clock, charging the scope table's ops per pair (forward 10, backward 20); the
+    fraction on the kernel's own reduced count is reported beside it."""
+    f = pk["sm_max_mhz"] * 1e6
+    mufu = SM_COUNT * MUFU_PER_CLK * f
+    fp32 = SM_COUNT * FP32_PER_CLK * f
+    fwd = name.endswith("fwd")
+    ops, own = (OPS_FWD, OWN_OPS_FWD) if fwd else (OPS_BWD, OWN_OPS_BWD)
+    peak = min(mufu, fp32 / ops) / 1e9
+    peak_own = min(mufu, fp32 / own) / 1e9
+    ach = units / (avg_ms * 1e-3) / 1e9
+    return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "Gpair/s", "frac": ach / peak,
+            "ops_per_pair": ops, "frac_own_ops": ach / peak_own, "own_ops_per_pair": own,
+            "ms_per_launch": avg_ms, "units_per_launch": units,
+            "traffic": ncu_traffic(name), "pipes_pct_of_peak": ncu_pipes(name),
+            "peak_note": f"min(MUFU ex2 {MUFU_PER_CLK}/clk/SM, FP32 {FP32_PER_CLK}/clk/SM / {ops} ops) x {SM_COUNT} "
+                         f"SMs x {pk['sm_max_mhz']:.0f} MHz (of measured sm_max_mhz; no FP32 peak is measured)"}
+
+
+def _profile_breakdown(step, ks, n_brk):
+    """Event pairs around every kernel group over the steps ks (untimed)."""
     import torch
 
-    from paper_2405_20693_b300 import build, engine, r2g
+    from paper_2405_20693_b300 import r2g
 
-    build.build()
-    dev = torch.device("cuda", local_rank)
-    torch.cuda.set_device(dev)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
+    r2g.r2g_profile_enable(True, 64 * n_brk + 64)
+    r2g.r2g_profile_select(0xFFFFFFFF)
+    r2g.r2g_profile_reset()
+    for k in ks:
+        step(k)
+    torch.cuda.synchronize()
+    out = {}
+    for kid, name in enumerate(r2g.PROFILE_KERNELS):
+        n, t = r2g.r2g_profile_read(kid)
+        if n:
+            out[name] = t / len(ks)
+    r2g.r2g_profile_enable(False)
+    return out
 
-        dist.init_process_group("nccl", device_id=dev)
-    seed = rank * 1000
+
+def measure_scale(args, dev, dist, seed, world):
+    """The headline: the batch form of r2g_train_step on the differentiation-at-scale
+    workload (see the module docstring).  Per step: all 75 views, the step's 8 TV
+    patches (seeded origins), the full volume.  Returns the fields of the JSON line."""
+    import torch
+
+    from paper_2405_20693_b300 import engine, r2g
+
+    G, cam, views_np, meas_np = make_scale_workload(seed, dev)
+    n_brk = min(args.steps, 5)
+    n_all = args.warmup + n_brk + args.steps
+    origins = torch.as_tensor(scale_patch_origins(seed, n_all), device=dev)
+    tab = np.zeros((n_all, 8), np.int32)
+    tab[:, 1] = np.arange(n_all)
+    table = torch.as_tensor(tab, device=dev)
+    sc = engine.Scan(G, views_np, meas_np, cam, n_out=N_OUT, D=D_TV, device=dev, headroom=1.25, all_views=True,
+                     n_patches=SCALE_NP, full_volume=True, tile=(16, 16))
+    # tile shape by measurement (the fused step per shape, on a restored copy of the state)
+    tiles = sc.autotune_tile(tiles=SCALE_TILES, steps=2)
+    elem = engine.ctypes_sizeof_entry()
+    stream = torch.cuda.current_stream()
+    org0, org_row = origins.data_ptr(), 4 * 3 * SCALE_NP
+
+    def step(k):
+        sc.job.patch_origins = org0 + k * org_row
+        r2g.r2g_train_step(sc.job, table.data_ptr() + k * elem, stream)
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize()
+    assert not sc.overflowed(), "list capacity overflow in the warm-up"
+    breakdown = _profile_breakdown(step, range(args.warmup, args.warmup + n_brk), n_brk)
+    dom = max(breakdown, key=breakdown.get)
+    t0_steps = args.warmup + n_brk
+    # algorithmic pairs (counting runs, untimed, on the parameters at the start of the
+    # timed region): all views, each step's 8 patches, the full volume
+    from paper_2405_20693_b300 import inputs as I
+
+    mean, scale, quat, rho = sc.state.params()
+    sc.rast.forward(mean, scale, quat, rho, sc.views, sc.image, check=True, count=True)
+    pix = sc.rast.pair_count()
+    org_np = origins.cpu().numpy()
+    vox = []
+    for k in range(t0_steps, t0_steps + args.steps):
+        sc.vox.set_grids([I.grid_desc(o, (2.0 / N_OUT,) * 3, (D_TV,) * 3) for o in org_np[k]])
+        sc.vox.forward(mean, scale, quat, rho, sc.vol, check=True, count=True)
+        vox.append(sc.vox.pair_count())
+    sc.full_vox.forward(mean, scale, quat, rho, sc.full_vol.view(-1), check=True, count=True)
+    full = sc.full_vox.pair_count()
+    # the superset the raster kernels walk: every record's pixel box (stated FP32 bounds)
+    proj = torch.empty((SCALE_V, sc.M, 8), dtype=torch.float32, device=dev)
+    prect = torch.empty((SCALE_V, sc.M, 4), dtype=torch.int32, device=dev)
+    r2g.r2g_project(mean, scale, quat, rho, sc.views, sc.rast.cam, sc.rast.opts, proj, prect)
+    rc = prect.long()
+    box_pix = int(((rc[..., 1] - rc[..., 0] + 1) * (rc[..., 3] - rc[..., 2] + 1))[proj[..., 7] == 1.0].sum())
+    del proj, prect, rc
+    sc.job = sc._make_job()  # a checked run that had to regrow a workspace moved it
+    total_pairs = float(args.steps * pix + sum(vox) + args.steps * full)
+    st = sc.state
+    start_state = [t.clone() for t in (st.raw, st.act, st.m, st.v)]
+
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    kf, kb = r2g.PROFILE_KERNELS.index("splat_fwd"), r2g.PROFILE_KERNELS.index("splat_bwd")
+    kd = r2g.PROFILE_KERNELS.index(dom)
+    r2g.r2g_profile_enable(True, 8 * args.steps + 64)
+    r2g.r2g_profile_select((1 << kf) | (1 << kb) | (1 << kd))
+    r2g.r2g_profile_reset()
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        gpu_id = None
+    clock = ClockSampler(gpu_id, dev.index or 0)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clock.start()
+    launches0 = r2g.r2g_launch_count()
+    for j in range(args.steps):
+        evs[j][0].record(stream)
+        step(t0_steps + j)
+        evs[j][1].record(stream)
+    torch.cuda.synchronize()
+    launches = r2g.r2g_launch_count() - launches0
+    clocks = clock.stop()
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    assert not sc.overflowed(), "list capacity overflow inside the timed region"
+    prof = {}
+    for name, kid in (("splat_fwd", kf), ("splat_bwd", kb), (dom, kd)):
+        n, t = r2g.r2g_profile_read(kid)
+        prof[name] = (n, t)
+    r2g.r2g_profile_enable(False)
+    r2g.r2g_profile_select(0xFFFFFFFF)
+    ms_job, pairs_job = job_totals(dist, ms, total_pairs, dev)
+    value = pairs_job / (ms_job * 1e-3)
+
+    # end to end through the public API: every step's 75 measured views, their geometry
+    # rows, the 8 patch origins and the round entry go host -> device from pinned memory
+    # (one r2g_train_step_host_batch call, staged on a copy stream), the losses come back
+    NS = 2
+    meas_host = torch.from_numpy(np.ascontiguousarray(meas_np, np.float32)).pin_memory()
+    views_host = torch.from_numpy(np.ascontiguousarray(views_np, np.float32)).pin_memory()
+    ent_host = torch.from_numpy(tab.copy()).pin_memory()
+    org_host = torch.from_numpy(org_np.copy()).pin_memory()
+    feed = engine.HostFeed(sc, meas_host, views_host, n_slots=NS, stream=stream)
+    for j in range(NS):                            # creates the copy stream and events
+        feed.step(0, ent_host.data_ptr() + 32 * j, org_host.data_ptr() + org_row * j)
+    feed.finish()
+    for t, saved in zip((st.raw, st.act, st.m, st.v), start_state):
+        t.copy_(saved)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    loss_sum, n_read = 0.0, 0
+    t0 = time.perf_counter()
+    for j in range(args.steps):
+        k = t0_steps + j
+        out = feed.step(0, ent_host.data_ptr() + 32 * k, org_host.data_ptr() + org_row * k)
+        if out is not None:
+            loss_sum += out[0]
+            n_read += 1
+    for out in feed.finish():
+        loss_sum += out[0]
+        n_read += 1
+    e2e_s = time.perf_counter() - t0
+    assert n_read == args.steps and np.isfinite(loss_sum)
+    e2e_s = slowest(dist, e2e_s, dev)
+    pk = peaks()
+    roofs = {}
+    for name in ("splat_fwd", "splat_bwd"):
+        n, t = prof[name]
+        if n:
+            roofs[name] = splat_roofline(name, float(pix), t / n, pk)
+    if dom in roofs:
+        roof = roofs[dom]
+    else:
+        n, t = prof[dom]
+        roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": None, "traffic": ncu_traffic(dom), "ms_per_launch": t / max(n, 1)}
+    return {
+        "value": value, "ms_per_step": ms_job / args.steps, "pairs_per_step": total_pairs / args.steps,
+        "e2e": {"value": pairs_job / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": feed.bytes_in,
+                "d2h_bytes_per_step": 8,
+                "note": "per step, one r2g_train_step_host_batch call (engine.HostFeed): the 75 measured views "
+                        "(78.6 MB), their geometry rows, the 8 patch origins and the round entry copied from "
+                        "pinned host memory into one of two device slots on a copy stream (overlapping the step "
+                        "before it), the fused step, the two losses read back to pinned host memory and read by "
+                        "the host; the same steps as the device-timed leg, from the same starting state"},
+        "gpu_launches": int(launches), "roofline": roof, "splat_rooflines": roofs, "kernels_ms_per_step": breakdown,
+        "clocks": clocks,
+        "config": {"workload": SCALE_WORKLOAD, "gaussians": int(sc.M), "views_per_step": SCALE_V,
+                   "detector": "512x512", "tv_patches_per_step": SCALE_NP, "full_volume": f"{N_OUT}^3",
+                   "pixel_pairs_per_step": pix, "voxel_pairs_per_step_patches": sum(vox) / args.steps,
+                   "voxel_pairs_per_step_full_volume": full, "box_pixel_pairs_per_step": box_pix,
+                   "gated_over_box_pixels": pix / max(1, box_pix),
+                   "tile": "%dx%d" % (sc.rast.opts.tile_w, sc.rast.opts.tile_h),
+                   "tile_autotune_ms_per_step": {"%dx%d" % t: v for t, v in tiles.items()},
+                   "bricks": "8^3", "l2": "not flushed: each step's working set (records 1.2 GB, lists, 79 MB of "
+                                         "images) is far larger than the 126 MB L2",
+                   "parallelism": f"replicas x{world}",
+                   "kernels_note": f"breakdown: event pairs around every kernel group over {n_brk} untimed steps; "
+                                   "timed region: events around the two splat kernels (and the dominant kernel)"},
+        "_sc": sc, "_G": G, "_views": views_np, "_cam": cam,
+    }
+
+
+def measure_one_scan(args, dev, dist, seed):
+    """The one-scan step (one view and one 32^3 TV patch per iteration, 50k Gaussians):
+    device-timed value with an L2 flush before every step, end to end through
+    r2g_train_step_host, the per-kernel breakdown and the splat rooflines."""
+    import torch
+
+    from paper_2405_20693_b300 import engine, r2g
+    from paper_2405_20693_b300 import inputs as I
+
     G, cam, views_np, meas_np = make_workload(seed, dev)
-    if args.extras_only:
-        if rank == 0:
-            print(json.dumps({"volume_metrics": measure_metrics(dev), "limited_angle": measure_limited_angle(dev),
-                              "adaptive_control": measure_adaptive(dev)}), flush=True)
-        return
-    if args.fdk_only:
-        if rank == 0:
-            print(json.dumps({"fdk_init": measure_fdk_init(dev, views_np, meas_np, cam, reps=args.steps,
-                                                           cpu=not args.no_cpu_baseline)}), flush=True)
-        return
-    # the scan's parameters, Adam state, views, measured projections, step buffers and
-    # workspaces stay resident; one step = one r2g_train_step call reading its view,
-    # iteration and TV patch origin from a device table holding every step's entry
     sc = engine.Scan(G, views_np, meas_np, cam, n_out=N_OUT, D=D_TV, device=dev)
     n_brk = min(args.steps, 200)
     n_all = args.warmup + n_brk + args.steps
@@ -640,38 +1028,17 @@ def run_ours(args, rank, world, local_rank):
     def step(k):
         r2g.r2g_train_step(sc.job, table.data_ptr() + k * elem, stream)
 
+    def flushed_step(k):
+        flush.zero_()
+        step(k)
+
     for k in range(args.warmup):
         step(k)
     torch.cuda.synchronize()
     assert not sc.overflowed(), "list capacity overflow in the warm-up"
-
-    # per-kernel breakdown, untimed: event pairs around every kernel group of n_brk
-    # steps; it names the dominant kernel, the only one bracketed in the timed region
-    r2g.r2g_profile_enable(True, 64 * n_brk + 64)
-    r2g.r2g_profile_select(0xFFFFFFFF)
-    r2g.r2g_profile_reset()
-    for k in range(args.warmup, args.warmup + n_brk):
-        flush.zero_()
-        step(k)
-    torch.cuda.synchronize()
-    breakdown = {}
-    for kid, name in enumerate(r2g.PROFILE_KERNELS):
-        n, t = r2g.r2g_profile_read(kid)
-        if n:
-            breakdown[name] = t / n_brk
-    dom = max(breakdown, key=breakdown.get)
+    breakdown = _profile_breakdown(flushed_step, range(args.warmup, args.warmup + n_brk), n_brk)
     t0_steps = args.warmup + n_brk
-
-    # algorithmic pairs of every distinct (view, patch) of the timed steps (counting
-    # runs, untimed, on the parameters at the start of the timed region)
-    from paper_2405_20693_b300 import inputs as I
-
     mean, scale, quat, rho = sc.state.params()
-    # the superset the kernels walk: each Gaussian's pixel box (the projection's
-    # stated FP32 bounds) and voxel box inside the patch
-    proj = torch.empty((1, sc.M, 8), dtype=torch.float32, device=dev)
-    prect = torch.empty((1, sc.M, 4), dtype=torch.int32, device=dev)
-    vox_box = voxel_box_counter(sc)
     counted = {}
     for k in range(t0_steps, t0_steps + args.steps):
         v, off = seq[k]
@@ -681,73 +1048,48 @@ def run_ours(args, rank, world, local_rank):
         pp = sc.rast.pair_count()
         sc.vox.set_grids(I.patch_grid(off, D_TV, N_OUT))
         sc.vox.forward(mean, scale, quat, rho, sc.vol, check=True, count=True)
-        r2g.r2g_project(mean, scale, quat, rho, sc.views[v:v + 1], sc.rast.cam, sc.rast.opts, proj, prect)
-        rc = prect[0].long()
-        ok = proj[0, :, 7] == 1.0
-        box_p = int(((rc[:, 1] - rc[:, 0] + 1) * (rc[:, 3] - rc[:, 2] + 1))[ok].sum())
-        counted[(v, off)] = (pp, sc.vox.pair_count(), box_p, vox_box(off))
-    sc.job = sc._make_job()  # a checked run that had to regrow a workspace moved it
-    pix_pairs = [counted[seq[k]][0] for k in range(t0_steps, t0_steps + args.steps)]
-    vox_pairs = [counted[seq[k]][1] for k in range(t0_steps, t0_steps + args.steps)]
-    box_pairs = [counted[seq[k]][2] + counted[seq[k]][3] for k in range(t0_steps, t0_steps + args.steps)]
-    total_pairs = float(sum(pix_pairs) + sum(vox_pairs))
-    # the state at the start of the timed region: the end-to-end leg restarts from it,
-    # so that both legs run the same steps on the same parameters (the same pairs)
+        counted[(v, off)] = (pp, sc.vox.pair_count())
+    sc.job = sc._make_job()
+    pix = [counted[seq[k]][0] for k in range(t0_steps, t0_steps + args.steps)]
+    voxp = [counted[seq[k]][1] for k in range(t0_steps, t0_steps + args.steps)]
+    total_pairs = float(sum(pix) + sum(voxp))
     st = sc.state
     start_state = [t.clone() for t in (st.raw, st.act, st.m, st.v)]
-
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    r2g.r2g_profile_enable(True, 2 * args.steps + 64)
-    r2g.r2g_profile_select(1 << r2g.PROFILE_KERNELS.index(dom))
+    kf, kb = r2g.PROFILE_KERNELS.index("splat_fwd"), r2g.PROFILE_KERNELS.index("splat_bwd")
+    r2g.r2g_profile_enable(True, 4 * args.steps + 64)
+    r2g.r2g_profile_select((1 << kf) | (1 << kb))
     r2g.r2g_profile_reset()
-    try:
-        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
-    except Exception:
-        gpu_id = str(local_rank)
-    clock = ClockSampler(gpu_id)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    clock.start()
-    launches0 = r2g.r2g_launch_count()
     for j in range(args.steps):
         flush.zero_()
         evs[j][0].record(stream)
         step(t0_steps + j)
         evs[j][1].record(stream)
     torch.cuda.synchronize()
-    launches = r2g.r2g_launch_count() - launches0
-    clocks = clock.stop()
     ms = sum(a.elapsed_time(b) for a, b in evs)
     assert not sc.overflowed(), "list capacity overflow inside the timed region"
-    n_dom, t_dom = r2g.r2g_profile_read(r2g.PROFILE_KERNELS.index(dom))
+    prof = {name: r2g.r2g_profile_read(kid) for name, kid in (("splat_fwd", kf), ("splat_bwd", kb))}
     r2g.r2g_profile_enable(False)
     r2g.r2g_profile_select(0xFFFFFFFF)
-
     ms_job, pairs_job = job_totals(dist, ms, total_pairs, dev)
-    value = pairs_job / (ms_job * 1e-3)
-
-    # end to end through the public API (engine.HostFeed over r2g_train_step_host):
-    # every step's inputs -- its measured view (H x W floats), the view's geometry
-    # row and its round entry -- go host -> device from pinned memory into one of NS
-    # staging slots on a copy stream, the fused step runs once its slot has arrived,
-    # and its losses come back to pinned host memory; copies overlap the steps
-    # before them, and the host reads step k's losses after queueing step k + NS - 1
     NS = 3
     meas_host = torch.from_numpy(np.ascontiguousarray(meas_np, np.float32)).pin_memory()
     views_host = torch.from_numpy(np.ascontiguousarray(views_np, np.float32)).pin_memory()
     ent_host = torch.from_numpy(tab.copy()).pin_memory()
     ent0 = ent_host.data_ptr()
     feed = engine.HostFeed(sc, meas_host, views_host, n_slots=NS, stream=stream)
-    for j in range(NS):                            # creates the copy stream and events
+    for j in range(NS):
         feed.step(seq[j][0], ent0 + 32 * j)
     feed.finish()
     for t, saved in zip((st.raw, st.act, st.m, st.v), start_state):
         t.copy_(saved)
-    loss_sum, n_read = 0.0, 0
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
+    loss_sum, n_read = 0.0, 0
     t0 = time.perf_counter()
     for j in range(args.steps):
         k = t0_steps + j
@@ -758,85 +1100,86 @@ def run_ours(args, rank, world, local_rank):
     for out in feed.finish():
         loss_sum += out[0]
         n_read += 1
-    assert n_read == args.steps
-    e2e_s = time.perf_counter() - t0
-    assert np.isfinite(loss_sum)
-    e2e_s = slowest(dist, e2e_s, dev)
-    e2e_value = pairs_job / e2e_s
+    e2e_s = slowest(dist, time.perf_counter() - t0, dev)
+    assert n_read == args.steps and np.isfinite(loss_sum)
+    pk = peaks()
+    per_step_pix = sum(pix) / args.steps
+    roofs = {name: splat_roofline(name, per_step_pix, t / n, pk) for name, (n, t) in prof.items() if n}
+    return {"value": pairs_job / (ms_job * 1e-3), "unit": "pairs/s", "ms_per_step": ms_job / args.steps,
+            "e2e": {"value": pairs_job / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": feed.bytes_in,
+                    "d2h_bytes_per_step": 8},
+            "workload": "one cone-beam scan: 50k Gaussians from a seeded 40-ellipsoid 256^3 phantom, L_SO 1000 mm, "
+                        "L_SD 1500 mm, 50 views x 512^2 at 0.8 mm; per step 1 view (L1+0.25 D-SSIM) + one 32^3 TV "
+                        "patch (0.05), full backward, Adam",
+            "pixel_pairs_per_step": per_step_pix, "voxel_pairs_per_step": sum(voxp) / args.steps,
+            "splat_rooflines": roofs, "kernels_ms_per_step": breakdown, "tile": "32x32",
+            "l2": "flushed (256 MB write) before every timed step",
+            "step_cycle": f"{N_DISTINCT} seeded (view, patch) pairs, repeated",
+            "_G": G, "_cam": cam, "_views": views_np, "_meas": meas_np, "_seq": seq[t0_steps:]}
 
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    from paper_2405_20693_b300 import build
+
+    build.build()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    seed = rank * 1000
+    if args.extras_only:
+        if rank == 0:
+            print(json.dumps({"volume_metrics": measure_metrics(dev), "limited_angle": measure_limited_angle(dev),
+                              "adaptive_control": measure_adaptive(dev)}), flush=True)
+        return
+    if args.fdk_only:
+        if rank == 0:
+            G, cam, views_np, meas_np = make_workload(seed, dev)
+            print(json.dumps({"fdk_init": measure_fdk_init(dev, views_np, meas_np, cam, reps=args.steps,
+                                                           cpu=not args.no_cpu_baseline)}), flush=True)
+        return
+    head = measure_scale(args, dev, dist, seed, world)
+    sc = head.pop("_sc")
+    Gs, views_s, cam_s = head.pop("_G"), head.pop("_views"), head.pop("_cam")
+    del sc
+    torch.cuda.empty_cache()
+    one = None
+    if not args.no_one_scan:
+        one = measure_one_scan(args, dev, dist, seed)
     if rank == 0:
-        pk = peaks()
-        f = pk["sm_max_mhz"] * 1e6
-        mufu_peak = SM_COUNT * MUFU_PER_CLK * f
-        fp32_peak = SM_COUNT * FP32_PER_CLK * f
-        per_step_pix = sum(pix_pairs) / args.steps
-        per_step_vox = sum(vox_pairs) / args.steps
-        # roofline of the kernel with the largest device time (timed live, alone)
-        roof = None
-        if dom in ("splat_fwd", "splat_bwd", "vox_fwd", "vox_bwd"):
-            units = per_step_pix if dom.startswith("splat") else per_step_vox
-            ops = OPS_FWD if dom.endswith("fwd") else OPS_BWD
-            peak = min(mufu_peak, fp32_peak / ops) / 1e9
-            avg_s = t_dom / n_dom * 1e-3
-            ach = units / avg_s / 1e9
-            roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": peak, "unit": "Gpair/s",
-                    "frac": ach / peak, "traffic": ncu_traffic(dom), "pipes_pct_of_peak": ncu_pipes(dom),
-                    "peak_note": f"min(MUFU ex2 {MUFU_PER_CLK}/clk/SM, FP32 {FP32_PER_CLK}/clk/SM / {ops} ops) "
-                                 f"x {SM_COUNT} SMs x {pk['sm_max_mhz']:.0f} MHz"}
-        elif dom is not None:
-            roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                    "frac": None, "traffic": ncu_traffic(dom)}
-        batched = None
-        serving = None
-        fdk_init = metrics = limited = adaptive = None
+        extras = {}
         if world == 1 and not args.no_batched:
-            batched = measure_batched(dev)
-            serving = measure_serving(dev)
-            fdk_init = measure_fdk_init(dev, views_np, meas_np, cam, cpu=not args.no_cpu_baseline)
-            metrics = measure_metrics(dev)
-            limited = measure_limited_angle(dev)
-            adaptive = measure_adaptive(dev)
+            G2, cam2, views2, meas2 = one["_G"], one["_cam"], one["_views"], one["_meas"]
+            extras = {"batched": measure_batched(dev), "serving": measure_serving(dev),
+                      "fdk_init": measure_fdk_init(dev, views2, meas2, cam2, cpu=not args.no_cpu_baseline),
+                      "volume_metrics": measure_metrics(dev), "limited_angle": measure_limited_angle(dev),
+                      "adaptive_control": measure_adaptive(dev)}
         cpu = None
-        # CPU baseline: the oracle on two full steps of the same workload
         if world == 1 and not args.no_cpu_baseline:
-            p, s, _ = oracle_steps(G, cam, views_np, meas_np, seq[t0_steps:], 2)
-            cpu = {"value": p / s, "unit": "pairs/s", "cores": 1, "kind": "oracle",
-                   "sample": "2 full training steps of the same workload (FP64 oracle, single thread, "
-                             "initial parameters)"}
+            cpu = cpu_baseline_scale(Gs, views_s, cam_s)
+            if one is not None:
+                p, s_, _ = oracle_steps(one["_G"], one["_cam"], one["_views"], one["_meas"], one["_seq"], 2)
+                one["cpu_baseline"] = {"value": p / s_, "unit": "pairs/s", "cores": 1, "kind": "oracle",
+                                       "sample": "2 full training steps of the one-scan workload (FP64 oracle, "
+                                                 "single thread)"}
+        if one is not None:
+            for k in ("_G", "_cam", "_views", "_meas", "_seq"):
+                one.pop(k, None)
         line = {
-            "metric": METRIC, "value": value, "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_job / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "one cone-beam scan: 50k Gaussians from a seeded 40-ellipsoid 256^3 phantom, "
-                                   "L_SO 1000 mm, L_SD 1500 mm, 50 views x 512^2 at 0.8 mm; per step 1 view "
-                                   "(L1+0.25 D-SSIM) + one 32^3 TV patch (0.05), full backward, Adam",
-                       "pixel_pairs_per_step": per_step_pix, "voxel_pairs_per_step": per_step_vox,
-                       "box_pairs_per_step": sum(box_pairs) / args.steps,
-                       "gated_over_box": total_pairs / max(1.0, float(sum(box_pairs))),
-                       "step_cycle": f"{N_DISTINCT} seeded (view, patch) pairs, repeated",
-                       "l2": "flushed (256 MB write) before every timed step", "parallelism": f"replicas x{world}",
-                       "tile": "32x32", "bricks": "8^3"},
-            "e2e": {"value": e2e_value, "unit": "pairs/s", "h2d_bytes_per_step": 4 * cam.H * cam.W + 48 + 32,
-                    "d2h_bytes_per_step": 8,
-                    "note": "per step, one r2g_train_step_host call (engine.HostFeed): the measured view, its "
-                            "geometry row and its round entry copied from pinned host memory into one of three "
-                            "device slots on a copy stream (overlapping the steps before it), the fused step, the "
-                            "two losses read back to pinned host memory and read by the host; the same steps as the "
-                            "device-timed leg, from the same starting state"},
-            "gpu_launches": int(launches),
-            "roofline": roof,
-            "kernels_ms_per_step": breakdown,
-            "kernels_note": f"breakdown: event pairs around every kernel group over {n_brk} untimed steps; "
-                            f"timed region: events around {dom} only",
-            "step_call": "r2g_train_step (one C call per step; entries from a device table)",
-            "cpu_baseline": cpu,
-            "batched": batched,
-            "serving": serving,
-            "fdk_init": fdk_init,
-            "volume_metrics": metrics,
-            "limited_angle": limited,
-            "adaptive_control": adaptive,
-            "clocks": clocks,
+            "metric": METRIC, "value": head["value"], "unit": "pairs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": head["config"],
+            "e2e": head["e2e"], "gpu_launches": head["gpu_launches"], "roofline": head["roofline"],
+            "splat_rooflines": head["splat_rooflines"], "kernels_ms_per_step": head["kernels_ms_per_step"],
+            "pairs_per_step": head["pairs_per_step"],
+            "step_call": "r2g_train_step, batch form (one C call per step; all views, 8 patch origins and the "
+                         "full volume from the job, iteration from a device table)",
+            "cpu_baseline": cpu, "one_scan": one, **extras, "clocks": head["clocks"],
         }
         print(json.dumps(line), flush=True)
     if dist:
@@ -851,6 +1194,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-one-scan", action="store_true", help="skip the one-scan (50k Gaussians, 1 view) leg")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the multi-scan scans/hour, serving and FDK-initialisation measurements")
     ap.add_argument("--fdk-only", action="store_true",

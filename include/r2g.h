@@ -293,7 +293,9 @@ r2g_status r2g_poll(const void* ws, size_t ws_bytes, r2g_stream stream, int64_t*
  *
  * One iteration of Eq. 8 for one scan (rasterize one view, L1 + lambda_ssim
  * D-SSIM against its measurement, voxelize one D^3 TV patch, lambda_tv TV, both
- * backward passes, Adam), launched on `stream` with no host synchronisation.
+ * backward passes, Adam), launched on `stream` with no host synchronisation.  The
+ * batch form (r2g_job.views_per_step, n_patches, full_vol) rasterizes every view of
+ * the scan in one launch, takes several TV patches and voxelizes the full volume.
  * Every per-iteration choice comes from a DEVICE round entry, read when the
  * kernels run, so a sequence of r2g_train_step calls over many scans can be
  * captured once in a CUDA graph and replayed each round after rewriting the
@@ -343,18 +345,41 @@ typedef struct {
     /* TV form of the step: <= 0 the anisotropic TV of r2g_tv3d (the default), > 0 the
      * isotropic TV of r2g_tv3d_iso with this eps */
     float tv_eps;
+    /* ---- batch form of the step (all zero / NULL: the one-view, one-patch step above).
+     * views_per_step: 0 or 1 = the round entry's view; V = every view of the scan in one
+     *   rasterizer launch (entry->view ignored): image and dimage are [V][H][W], the
+     *   projection loss is Eq. 8's over the V views (L1 over all their pixels, SSIM
+     *   averaged over the views), raster_ws and loss_ws are sized for V views.
+     * n_patches: TV patches per step, 0 or 1 = one at entry->origin; 2..64 = patches
+     *   whose origins are read from patch_origins (device [n_patches][3]) when the step
+     *   runs; vol and dvol hold n_patches D^3 volumes, voxel_ws and tv_ws are sized for
+     *   n_patches grids; the TV loss is the sum over the patches.
+     * full_vol (optional, device [Z][Y][X] of full_grid): the forward voxelization (Eq. 4)
+     *   of full_grid with the step's parameters before its update, on the TV branch,
+     *   through its own workspace full_ws of full_ws_bytes (r2g_voxel_workspace_size for
+     *   1 grid); it takes no part in the loss. */
+    int32_t views_per_step;
+    int32_t n_patches;
+    const float* patch_origins;
+    float* full_vol;
+    r2g_grid full_grid;
+    void* full_ws;
+    size_t full_ws_bytes;
 } r2g_job;
 
 r2g_status r2g_train_step(const r2g_job* job, const r2g_round_entry* entry, r2g_stream stream);
 
-/* Staging slots of r2g_train_step_host (all caller-owned): n_slots in 1..16. */
+/* Staging slots of r2g_train_step_host (all caller-owned): n_slots in 1..16.  Vs =
+ * the views a step rasterizes (1, or V with job->views_per_step = V), NP = the job's
+ * TV patches per step. */
 typedef struct {
     int32_t n_slots;
-    float* meas;                      /* device [n_slots][H][W] */
-    float* views;                     /* device [n_slots][12] */
+    float* meas;                      /* device [n_slots][Vs][H][W] */
+    float* views;                     /* device [n_slots][Vs][12] */
     r2g_round_entry* entries;         /* device [n_slots] */
     r2g_round_entry* entries_host;    /* pinned host [n_slots]; written by the call */
     float* loss;                      /* device [n_slots][2]: the step's losses (instead of job->loss) */
+    float* patch_origins;             /* device [n_slots][NP][3] when NP > 1 (else unused) */
 } r2g_staging;
 
 /* One training iteration fed from HOST memory: the step's measured projection
@@ -373,6 +398,16 @@ typedef struct {
 r2g_status r2g_train_step_host(const r2g_job* job, const r2g_staging* stg, int64_t step, const float* meas_host,
                                const float* view_host, const r2g_round_entry* entry_host, float* loss_host,
                                r2g_stream stream);
+/* r2g_train_step_host for the batch form of the step: meas_host [Vs][H][W] and
+ * views_host [Vs][12] are the step's measured projections and their geometry rows (Vs
+ * = 1, or V when job->views_per_step = V), patch_origins_host [NP][3] the origins of
+ * its TV patches when the job has NP = n_patches > 1 (else NULL; the entry's origin
+ * is used); all host memory, read during the call.  Everything else as
+ * r2g_train_step_host, which is this call with patch_origins_host = NULL. */
+r2g_status r2g_train_step_host_batch(const r2g_job* job, const r2g_staging* stg, int64_t step, const float* meas_host,
+                                     const float* views_host, const float* patch_origins_host,
+                                     const r2g_round_entry* entry_host, float* loss_host, r2g_stream stream);
+
 /* Blocks until step `step` of r2g_train_step_host on `stream` has finished (its
  * loss_host filled); returns at once for a slot that never ran. */
 r2g_status r2g_train_step_host_wait(const r2g_staging* stg, int64_t step, r2g_stream stream);

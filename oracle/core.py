@@ -43,6 +43,10 @@ def lib():
             i64, i32, dbl, flt = ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_float
             L.orc_render.restype = i64
             L.orc_render.argtypes = [i64, _D, _D, _D, _D, _D, i32, _D, dbl, i32, _D, _D]
+            L.orc_render_gated.restype = i64
+            L.orc_render_gated.argtypes = [i64, _D, _D, _D, _D, _D, _D, _D, _D, _D, i32, _D, dbl, _D]
+            L.orc_voxelize_gated.restype = i64
+            L.orc_voxelize_gated.argtypes = [i64, _D, _D, _D, _D, _D, _D, _D, _D, _D, i32, dbl, _D]
             L.orc_project.restype = None
             L.orc_project.argtypes = [i64, _D, _D, _D, _D, _D, i32, _D, _D]
             L.orc_render_cs.restype = None
@@ -123,6 +127,30 @@ def render(G, views, cam, Q=9.0, brute=False, want_band=False, jmode=0, biased=F
     pairs = lib().orc_render(g.M, *g.ptrs(), _p(views), V, _p(cv), float(Q), int(brute), _p(img),
                              _p(band) if band is not None else None)
     return (img, int(pairs), band) if want_band else (img, int(pairs))
+
+
+def render_gated(G, Ggate, views, cam, Q=9.0):
+    """O1 image [V, H, W] of G with every Gaussian's gate (box and q <= Q) taken from
+    the same Gaussian of Ggate; equals render(G) when Ggate is G.  Central
+    differences of it hold the gate membership fixed."""
+    g, gg = _G(G), _G(Ggate)
+    assert g.M == gg.M
+    views = _d(views)
+    cv = _camv(cam)
+    img = np.zeros((views.shape[0], cam.H, cam.W))
+    lib().orc_render_gated(g.M, *g.ptrs(), *gg.ptrs(), _p(views), views.shape[0], _p(cv), float(Q), _p(img))
+    return img
+
+
+def voxelize_gated(G, Ggate, gdescs, Q3=11.345):
+    """O1 volumes (grids concatenated) of G with every Gaussian's gate taken from the
+    same Gaussian of Ggate; equals voxelize(G) when Ggate is G."""
+    g, gg = _G(G), _G(Ggate)
+    assert g.M == gg.M
+    gd, G_, n = _grids(gdescs)
+    vol = np.zeros(n)
+    lib().orc_voxelize_gated(g.M, *g.ptrs(), *gg.ptrs(), _p(gd), G_, float(Q3), _p(vol))
+    return vol
 
 
 def project(G, views, cam, jmode=0, biased=False):

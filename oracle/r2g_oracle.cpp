@@ -283,6 +283,49 @@ int64_t render(const ParamsT<T>& G, int64_t M, const double* views, int V, const
     return pairs;
 }
 
+// O1 rasterizer with the gate of every Gaussian held at a second parameter set Gg:
+// the box and the pixels with q <= Q come from Gaussian i of Gg, the value
+// rho_hat e^{-q/2} at those pixels from Gaussian i of G.  With G == Gg this is
+// render().  A central difference in G is then the derivative with the gate
+// membership fixed -- the quantity an adjoint of the gated sum computes (the gate's
+// moving boundary adds jumps of e^{-Q/2} rho_hat that no derivative sees).
+int64_t render_gated(const ParamsT<double>& G, const ParamsT<double>& Gg, int64_t M, const double* views, int V,
+                     const Cam& cam, double Q, double* img) {
+    const int H = cam.H, Wd = cam.W;
+    for (int64_t k = 0; k < (int64_t)V * H * Wd; ++k) img[k] = 0.0;
+    int64_t pairs = 0;
+    for (int v = 0; v < V; ++v) {
+        const double* view = views + 12 * v;
+        double* Iv = img + (int64_t)v * H * Wd;
+        for (int64_t i = 0; i < M; ++i) {
+            M3<double> Sg, Rg, S, R;
+            double qg[4], ng, qn[4], nn;
+            covariance(&Gg.scale[3 * i], &Gg.quat[4 * i], Sg, Rg, qg, ng);
+            covariance(&G.scale[3 * i], &G.quat[4 * i], S, R, qn, nn);
+            const Proj<double> Pg = project_one(&Gg.mean[3 * i], Sg, Gg.rho[i], view, cam);
+            const Proj<double> P = project_one(&G.mean[3 * i], S, G.rho[i], view, cam);
+            if (!Pg.valid || !P.valid) continue;
+            int c0, c1, r0, r1;
+            centre_range(Pg.ph[0], std::sqrt(Q * Pg.shd[0]), cam.pitch_u, cam.off_u, Wd, c0, c1);
+            centre_range(Pg.ph[1], std::sqrt(Q * Pg.shd[2]), cam.pitch_v, cam.off_v, H, r0, r1);
+            for (int r = r0; r <= r1; ++r) {
+                const double eta = pix_eta(r, cam);
+                for (int c = c0; c <= c1; ++c) {
+                    const double xi = pix_xi(c, cam);
+                    const double gx = xi - Pg.ph[0], gy = eta - Pg.ph[1];
+                    const double qgate = Pg.conic[0] * gx * gx + 2.0 * Pg.conic[1] * gx * gy + Pg.conic[2] * gy * gy;
+                    if (!(qgate <= Q)) continue;
+                    const double dx = xi - P.ph[0], dy = eta - P.ph[1];
+                    const double q = P.conic[0] * dx * dx + 2.0 * P.conic[1] * dx * dy + P.conic[2] * dy * dy;
+                    Iv[(int64_t)r * Wd + c] += P.rhohat * std::exp(-0.5 * q);
+                    ++pairs;
+                }
+            }
+        }
+    }
+    return pairs;
+}
+
 // ---------------------------------------------------------------------------
 // Hand-derived adjoint of the O1 rasterizer.  Gradients are accumulated (+=).
 // Matrix gradients are taken entry-wise on full (not symmetrised) matrices.
@@ -585,6 +628,59 @@ int64_t voxelize(const ParamsT<T>& Gp, int64_t M, const std::vector<GridSpec>& g
                             Bg[idx] += std::fabs(re(Gp.rho[i])) * std::exp(-0.5 * qr);
                         if (!(qr <= Q3)) continue;
                         Vg[idx] += Gp.rho[i] * std::exp(-0.5 * q);
+                        ++pairs;
+                    }
+        }
+        off += (int64_t)X * Y * Z;
+    }
+    return pairs;
+}
+
+// O1 voxelizer with each Gaussian's gate held at a second parameter set Gg (see
+// render_gated): the voxels with q <= Q3 for Gaussian i of Gg receive
+// rho_i exp(-q/2) of Gaussian i of G.
+int64_t voxelize_gated(const ParamsT<double>& Gp, const ParamsT<double>& Gg, int64_t M,
+                       const std::vector<GridSpec>& grids, double Q3, double* vol) {
+    int64_t off = 0, pairs = 0;
+    for (const GridSpec& gs : grids) {
+        const int X = gs.dims[0], Y = gs.dims[1], Z = gs.dims[2];
+        double* Vg = vol + off;
+        for (int64_t k = 0; k < (int64_t)X * Y * Z; ++k) Vg[k] = 0.0;
+        for (int64_t i = 0; i < M; ++i) {
+            M3<double> Sg, Rg, S, R;
+            double qg[4], ng, qn[4], nn;
+            covariance(&Gg.scale[3 * i], &Gg.quat[4 * i], Sg, Rg, qg, ng);
+            covariance(&Gp.scale[3 * i], &Gp.quat[4 * i], S, R, qn, nn);
+            const M3<double> Pg = inverse(Sg), P = inverse(S);
+            const double* pg = &Gg.mean[3 * i];
+            const double* p = &Gp.mean[3 * i];
+            int lo[3], hi[3];
+            for (int k = 0; k < 3; ++k) {
+                const double e = std::sqrt(Q3 * Sg.a[k][k]);
+                const double a = (pg[k] - e - gs.origin[k]) / gs.voxel[k] - 0.5;
+                const double b = (pg[k] + e - gs.origin[k]) / gs.voxel[k] - 0.5;
+                lo[k] = std::max(0, (int)std::max(-1.0, std::min((double)gs.dims[k], std::ceil(a) - 1.0)));
+                hi[k] = std::min(gs.dims[k] - 1, (int)std::max(-1.0, std::min((double)gs.dims[k], std::floor(b) + 1.0)));
+            }
+            for (int z = lo[2]; z <= hi[2]; ++z)
+                for (int y = lo[1]; y <= hi[1]; ++y)
+                    for (int x = lo[0]; x <= hi[0]; ++x) {
+                        const double xc[3] = {gs.origin[0] + (x + 0.5) * gs.voxel[0],
+                                              gs.origin[1] + (y + 0.5) * gs.voxel[1],
+                                              gs.origin[2] + (z + 0.5) * gs.voxel[2]};
+                        double dg[3], d[3];
+                        for (int k = 0; k < 3; ++k) {
+                            dg[k] = xc[k] - pg[k];
+                            d[k] = xc[k] - p[k];
+                        }
+                        double qgate = 0.0, q = 0.0;
+                        for (int j = 0; j < 3; ++j)
+                            for (int k = 0; k < 3; ++k) {
+                                qgate += dg[j] * Pg.a[j][k] * dg[k];
+                                q += d[j] * P.a[j][k] * d[k];
+                            }
+                        if (!(qgate <= Q3)) continue;
+                        Vg[((int64_t)z * Y + y) * X + x] += Gp.rho[i] * std::exp(-0.5 * q);
                         ++pairs;
                     }
         }
@@ -940,6 +1036,26 @@ int64_t orc_render(int64_t M, const double* mean, const double* scale, const dou
     const Cam cam = make_cam(camv);
     ParamsT<double> G = widen<double>(P);
     return render<double>(G, M, views, V, cam, Q, img, band, brute != 0);
+}
+
+// render_gated: values from (mean, scale, quat, rho), gates from the g* set.
+int64_t orc_render_gated(int64_t M, const double* mean, const double* scale, const double* quat, const double* rho,
+                         const double* gmean, const double* gscale, const double* gquat, const double* grho,
+                         const double* views, int V, const double* camv, double Q, double* img) {
+    const ParamsT<double> G = widen<double>(Params{M, mean, scale, quat, rho});
+    const ParamsT<double> Gg = widen<double>(Params{M, gmean, gscale, gquat, grho});
+    return render_gated(G, Gg, M, views, V, make_cam(camv), Q, img);
+}
+
+// voxelize_gated: values from (mean, scale, quat, rho), gates from the g* set.
+int64_t orc_voxelize_gated(int64_t M, const double* mean, const double* scale, const double* quat, const double* rho,
+                           const double* gmean, const double* gscale, const double* gquat, const double* grho,
+                           const double* gdesc, int G, double Q3, double* vol) {
+    std::vector<GridSpec> grids;
+    grids_from(gdesc, G, grids);
+    const ParamsT<double> Gp = widen<double>(Params{M, mean, scale, quat, rho});
+    const ParamsT<double> Gg = widen<double>(Params{M, gmean, gscale, gquat, grho});
+    return voxelize_gated(Gp, Gg, M, grids, Q3, vol);
 }
 
 // Per (Gaussian, view) projection quantities in FP64: out[v][i][12] =

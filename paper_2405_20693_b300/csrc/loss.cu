@@ -97,7 +97,8 @@ __device__ __forceinline__ void stage_tile(float (*dst)[kS + 1], const float* __
 // One CTA per 32 x 32 output tile of one view.  x and y are staged with a
 // 10-pixel halo; the windowed moments and each pixel's SSIM term S and its
 // derivatives with respect to mu_x, E_xx and E_xy are formed on the tile plus a
-// 5-pixel halo (zero outside the image, whose pixels the mean leaves out); those
+// 5-pixel halo (zero outside the image, whose pixels the mean leaves out), from the
+// moments of both images shifted by one constant per CTA; those
 // derivative maps are filtered again with the window (the adjoint of a
 // zero-padded symmetric filter is itself) and combined with x, y and the L1 sign
 // into d loss / d render.  Per-tile sums of 1 - S and |x - y| go to `partials`;
@@ -130,6 +131,12 @@ __global__ void __launch_bounds__(kSsimThreads) k_ssim(const float* __restrict__
     pdl_wait();
     stage_tile(S.sx, xv, TY, TX, H, W, tid, vec4);
     __syncthreads();
+    // The moments are taken of x - cs and y - cs (cs: the mean of both images at the
+    // staged region's centre; pixels outside the image, x = y = 0, become -cs), so that
+    // the (co)variances E[x'y'] - mu_x' mu_y' do not cancel the squared means of
+    // bright, smooth regions; they equal those of x and y because the window sums to
+    // one.  mu_x = mu_x' + cs enters the luminance term.
+    const float cs = 0.5f * (S.sx[kS / 2][kS / 2] + S.sy[kS / 2][kS / 2]);
     // Each pass is register-blocked along its filter direction: a thread computes a
     // run of outputs from one sliding set of inputs (every input loaded once), and
     // the lanes of a warp take consecutive rows (horizontal passes) or columns
@@ -147,7 +154,7 @@ __global__ void __launch_bounds__(kSsimThreads) k_ssim(const float* __restrict__
                 for (int q = 0; q < 5; ++q) acc[o][q] = 0.f;
 #pragma unroll
             for (int i = 0; i < RB + 10; ++i) {
-                const float xa = S.sx[r][c0 + i], ya = S.sy[r][c0 + i];
+                const float xa = S.sx[r][c0 + i] - cs, ya = S.sy[r][c0 + i] - cs;
                 const float f[5] = {xa, ya, xa * xa, ya * ya, xa * ya};
 #pragma unroll
                 for (int o = 0; o < RB; ++o) {
@@ -200,13 +207,16 @@ __global__ void __launch_bounds__(kSsimThreads) k_ssim(const float* __restrict__
                 const int gy = TY - kR + r, gx = TX - kR + c;
                 float dm = 0.f, dxx = 0.f, dxy = 0.f;
                 if (gy >= 0 && gy < H && gx >= 0 && gx < W) {
-                    const float mx = m[o][0], my = m[o][1];
-                    const float sxx = m[o][2] - mx * mx, syy = m[o][3] - my * my, sxy = m[o][4] - mx * my;
+                    const float mxs = m[o][0], mys = m[o][1];       // means of the shifted images
+                    const float mx = mxs + cs, my = mys + cs;
+                    const float sxx = m[o][2] - mxs * mxs, syy = m[o][3] - mys * mys, sxy = m[o][4] - mxs * mys;
                     const float A1 = 2.f * mx * my + kC1, A2 = 2.f * sxy + kC2;
                     const float B1 = mx * mx + my * my + kC1, B2 = sxx + syy + kC2;
                     const float iB = __frcp_rn(B1 * B2);
                     const float Sv = A1 * A2 * iB;
-                    dm = (2.f * my * (A2 - A1) - 2.f * mx * Sv * (B2 - B1)) * iB;
+                    // dS/dmu_x' with E_x'x', E_x'y' held: A1, B1 move with mu_x = mu_x' + cs,
+                    // A2, B2 with -mu_x'^2 and -mu_x' mu_y'
+                    dm = (2.f * (my * A2 - mys * A1) - 2.f * Sv * (mx * B2 - mxs * B1)) * iB;
                     dxx = -Sv * (B1 * iB);                   // -S / B2
                     dxy = 2.f * A1 * iB;
                     if (r >= kR && r < kR + kT && c >= kR && c < kR + kT) {  // this tile's own pixels
@@ -283,7 +293,7 @@ __global__ void __launch_bounds__(kSsimThreads) k_ssim(const float* __restrict__
                 const float dd = xp - yp;
                 const float sgn = (dd > 0.f) ? 1.f : ((dd < 0.f) ? -1.f : 0.f);
                 grad[((size_t)v * H + gy) * W + gx] =
-                    l1_scale * sgn - ssim_scale * (b[o][0] + 2.f * xp * b[o][1] + yp * b[o][2]);
+                    l1_scale * sgn - ssim_scale * (b[o][0] + 2.f * (xp - cs) * b[o][1] + (yp - cs) * b[o][2]);
             }
         }
     }

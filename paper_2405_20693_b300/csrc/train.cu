@@ -3,6 +3,9 @@
 // so that a round over many scans can be captured once as a CUDA graph and
 // replayed: rasterize the selected view, L1 + D-SSIM against its measurement,
 // voxelize the TV patch at the selected origin, TV, both backward passes, Adam.
+// The batch form of the same call rasterizes every view of the scan in one launch
+// (the loss over all of them), takes several TV patches whose origins are read on
+// the device, and can voxelize the full output volume alongside (forward only).
 //
 // The projection branch (rasterize, loss, raster moments) and the TV branch
 // (voxelize, TV, voxel moments and chain rule) share nothing until the gradients
@@ -94,6 +97,14 @@ R2G_API r2g_status r2g_train_step(const r2g_job* job, const r2g_round_entry* ent
         !J.dimage || !J.vol || !J.dvol || !J.loss || !J.raster_ws || !J.voxel_ws || !J.loss_ws || !J.tv_ws)
         return fail(R2G_E_INVAL, "r2g_train_step: NULL pointer in the job");
     if (J.D < 2 || !(J.voxel > 0.f)) return fail(R2G_E_INVAL, "r2g_train_step: bad TV patch");
+    // batch form: every view per step, several TV patches, the full volume
+    if (J.views_per_step < 0 || (J.views_per_step > 1 && J.views_per_step != J.V))
+        return fail(R2G_E_INVAL, "r2g_train_step: views_per_step %d must be 0, 1 or V = %d", J.views_per_step, J.V);
+    const int Vs = J.views_per_step > 1 ? J.V : 1;
+    const int NP = J.n_patches > 1 ? J.n_patches : 1;
+    if (J.n_patches < 0 || NP > 64) return fail(R2G_E_INVAL, "r2g_train_step: n_patches %d out of range", J.n_patches);
+    if (NP > 1 && !J.patch_origins) return fail(R2G_E_INVAL, "r2g_train_step: n_patches > 1 needs patch_origins");
+    if (J.full_vol && !J.full_ws) return fail(R2G_E_INVAL, "r2g_train_step: full_vol needs full_ws");
     const int64_t M = J.M;
     // activated parameters [quat 4M | mean 3M | scale 3M | rho M]
     const float* quat = J.act;
@@ -104,13 +115,16 @@ R2G_API r2g_status r2g_train_step(const r2g_job* job, const r2g_round_entry* ent
     float* dmean = J.grad + 4 * M;
     float* dscale = J.grad + 7 * M;
     float* drho = J.grad + 10 * M;
-    const int* view_sel = &entry->view;
-    r2g_grid grid;
-    for (int k = 0; k < 3; ++k) {
-        grid.origin[k] = 0.f;  // replaced on the device by entry->origin
-        grid.voxel[k] = J.voxel;
-        grid.dims[k] = J.D;
-    }
+    // one view picked by the entry (on the device), or all V views in order
+    const int* view_sel = Vs == 1 ? &entry->view : nullptr;
+    const float* origin_dev = NP > 1 ? J.patch_origins : entry->origin;
+    r2g_grid grids[64];
+    for (int g = 0; g < NP; ++g)
+        for (int k = 0; k < 3; ++k) {
+            grids[g].origin[k] = 0.f;  // replaced on the device by the patch origins
+            grids[g].voxel[k] = J.voxel;
+            grids[g].dims[k] = J.D;
+        }
     SideStream* side = nullptr;
     r2g_status e = side_stream_for(stream, &side);
     if (e) return e;
@@ -119,27 +133,31 @@ R2G_API r2g_status r2g_train_step(const r2g_job* job, const r2g_round_entry* ent
     // stream (the previous iteration's Adam step)
     if (cudaEventRecord(side->fork, stream) != cudaSuccess || cudaStreamWaitEvent(tv, side->fork, 0) != cudaSuccess)
         return fail(R2G_E_CUDA, "r2g_train_step: fork failed (%s)", cudaGetErrorString(cudaGetLastError()));
-    r2g_status e_tv = voxelize_impl(M, mean, scale, quat, rho, 1, &grid, entry->origin, J.Q3, J.vol, J.voxel_ws,
+    r2g_status e_tv = voxelize_impl(M, mean, scale, quat, rho, NP, grids, origin_dev, J.Q3, J.vol, J.voxel_ws,
                                     J.voxel_ws_bytes, tv, false, J.ropts.separate_lists != 0);
     if (!e_tv)
         e_tv = J.tv_eps > 0.f
-                   ? r2g_tv3d_iso(1, J.D, J.vol, J.lambda_tv, J.tv_eps, J.loss + 1, J.dvol, J.tv_ws, J.tv_ws_bytes, tv)
-                   : r2g_tv3d(1, J.D, J.vol, J.lambda_tv, J.loss + 1, J.dvol, J.tv_ws, J.tv_ws_bytes, tv);
+                   ? r2g_tv3d_iso(NP, J.D, J.vol, J.lambda_tv, J.tv_eps, J.loss + 1, J.dvol, J.tv_ws, J.tv_ws_bytes, tv)
+                   : r2g_tv3d(NP, J.D, J.vol, J.lambda_tv, J.loss + 1, J.dvol, J.tv_ws, J.tv_ws_bytes, tv);
     if (!e_tv)
-        e_tv = voxelize_backward_impl(M, mean, scale, quat, rho, 1, &grid, J.Q3, J.dvol, dmean, dscale, dquat, drho,
+        e_tv = voxelize_backward_impl(M, mean, scale, quat, rho, NP, grids, J.Q3, J.dvol, dmean, dscale, dquat, drho,
                                       J.voxel_ws, J.voxel_ws_bytes, tv,
                                       kVoxBwdMoments | kVoxBwdChain | kVoxBwdAssign);
+    // the full volume: forward only, with the parameters this step started from
+    if (!e_tv && J.full_vol)
+        e_tv = voxelize_impl(M, mean, scale, quat, rho, 1, &J.full_grid, nullptr, J.Q3, J.full_vol, J.full_ws,
+                             J.full_ws_bytes, tv, false, J.ropts.separate_lists != 0);
     // the loss's arrival counter is cleared first, so that no copy sits between the
     // rasterizer and the loss kernel (which then takes a programmatic dependent launch)
-    r2g_status e_px = projection_loss_clear(1, J.cam.H, J.cam.W, J.loss_ws, J.loss_ws_bytes, stream);
+    r2g_status e_px = projection_loss_clear(Vs, J.cam.H, J.cam.W, J.loss_ws, J.loss_ws_bytes, stream);
     if (!e_px)
-        e_px = rasterize_impl(M, mean, scale, quat, rho, 1, J.views, view_sel, &J.cam, &J.ropts, J.image,
+        e_px = rasterize_impl(M, mean, scale, quat, rho, Vs, J.views, view_sel, &J.cam, &J.ropts, J.image,
                               J.raster_ws, J.raster_ws_bytes, stream);
     if (!e_px)
-        e_px = projection_loss_impl(1, J.cam.H, J.cam.W, J.image, J.meas, view_sel, J.lambda_ssim, J.loss, J.dimage,
+        e_px = projection_loss_impl(Vs, J.cam.H, J.cam.W, J.image, J.meas, view_sel, J.lambda_ssim, J.loss, J.dimage,
                                     J.loss_ws, J.loss_ws_bytes, stream, false);
     if (!e_px)
-        e_px = rasterize_backward_impl(M, mean, scale, quat, rho, 1, J.views, view_sel, &J.cam, &J.ropts, J.dimage,
+        e_px = rasterize_backward_impl(M, mean, scale, quat, rho, Vs, J.views, view_sel, &J.cam, &J.ropts, J.dimage,
                                        dmean, dscale, dquat, drho, J.raster_ws, J.raster_ws_bytes, stream,
                                        kRasterBwdMoments);
     // join (also on error, so that no captured branch is left open)
@@ -151,26 +169,31 @@ R2G_API r2g_status r2g_train_step(const r2g_job* job, const r2g_round_entry* ent
         return fail(R2G_E_INVAL, "r2g_train_step: bad Adam options");
     const AdamState adam{J.raw,  J.act, J.adam_m, J.adam_v, J.grad, adam_args(M, &J.adam, 0, &entry->it),
                          J.dens_grad, J.dens_count};
-    return rasterize_backward_impl(M, mean, scale, quat, rho, 1, J.views, view_sel, &J.cam, &J.ropts, J.dimage,
+    return rasterize_backward_impl(M, mean, scale, quat, rho, Vs, J.views, view_sel, &J.cam, &J.ropts, J.dimage,
                                    dmean, dscale, dquat, drho, J.raster_ws, J.raster_ws_bytes, stream,
                                    kRasterBwdChain, &adam);
 }
 
-R2G_API r2g_status r2g_train_step_host(const r2g_job* job, const r2g_staging* stg, int64_t step,
-                                       const float* meas_host, const float* view_host,
-                                       const r2g_round_entry* entry_host, float* loss_host, r2g_stream stream) {
-    if (!job || !stg || !meas_host || !view_host || !entry_host || !loss_host)
+R2G_API r2g_status r2g_train_step_host_batch(const r2g_job* job, const r2g_staging* stg, int64_t step,
+                                             const float* meas_host, const float* views_host,
+                                             const float* patch_origins_host, const r2g_round_entry* entry_host,
+                                             float* loss_host, r2g_stream stream) {
+    if (!job || !stg || !meas_host || !views_host || !entry_host || !loss_host)
         return fail(R2G_E_INVAL, "r2g_train_step_host: NULL argument");
     if (stg->n_slots < 1 || stg->n_slots > kMaxSlots || !stg->meas || !stg->views || !stg->entries ||
         !stg->entries_host || !stg->loss || step < 0)
         return fail(R2G_E_INVAL, "r2g_train_step_host: bad staging (n_slots %d, step %lld)", stg->n_slots,
                     (long long)step);
     if (job->cam.H < 1 || job->cam.W < 1 || !job->loss) return fail(R2G_E_INVAL, "r2g_train_step_host: bad job");
+    const int Vs = job->views_per_step > 1 ? job->V : 1;
+    const int NP = job->n_patches > 1 ? job->n_patches : 1;
+    if (NP > 1 && (!patch_origins_host || !stg->patch_origins))
+        return fail(R2G_E_INVAL, "r2g_train_step_host: the job's %d TV patches need their origins", NP);
     HostStage* hs = nullptr;
     r2g_status e = host_stage_for(stream, &hs);
     if (e) return e;
     const int slot = (int)(step % stg->n_slots);
-    const size_t img = (size_t)job->cam.H * (size_t)job->cam.W;
+    const size_t img = (size_t)Vs * (size_t)job->cam.H * (size_t)job->cam.W;
     // the step that used this slot last (step - n_slots) must be done, its losses
     // read back, before the slot's pinned entry, device inputs and losses are
     // rewritten (no wait if it never ran)
@@ -178,19 +201,28 @@ R2G_API r2g_status r2g_train_step_host(const r2g_job* job, const r2g_staging* st
         return fail(R2G_E_CUDA, "r2g_train_step_host: waiting for slot %d (%s)", slot,
                     cudaGetErrorString(cudaGetLastError()));
     stg->entries_host[slot] = *entry_host;
-    stg->entries_host[slot].view = slot;  // the slot holds the step's view and measurement
+    stg->entries_host[slot].view = Vs == 1 ? slot : 0;  // the slot holds the step's views and measurements
+    float* pdev = NP > 1 ? stg->patch_origins + (size_t)slot * 3 * NP : nullptr;
     if (cudaMemcpyAsync(stg->meas + slot * img, meas_host, img * sizeof(float), cudaMemcpyHostToDevice, hs->in_s) !=
             cudaSuccess ||
-        cudaMemcpyAsync(stg->views + 12 * (size_t)slot, view_host, 12 * sizeof(float), cudaMemcpyHostToDevice,
-                        hs->in_s) != cudaSuccess ||
+        cudaMemcpyAsync(stg->views + 12 * (size_t)Vs * slot, views_host, 12 * sizeof(float) * Vs,
+                        cudaMemcpyHostToDevice, hs->in_s) != cudaSuccess ||
+        (pdev && cudaMemcpyAsync(pdev, patch_origins_host, 3 * sizeof(float) * NP, cudaMemcpyHostToDevice,
+                                 hs->in_s) != cudaSuccess) ||
         cudaMemcpyAsync(stg->entries + slot, stg->entries_host + slot, sizeof(r2g_round_entry),
                         cudaMemcpyHostToDevice, hs->in_s) != cudaSuccess ||
         cudaEventRecord(hs->in[slot], hs->in_s) != cudaSuccess || cudaStreamWaitEvent(stream, hs->in[slot], 0) != cudaSuccess)
         return fail(R2G_E_CUDA, "r2g_train_step_host: staging copy failed (%s)", cudaGetErrorString(cudaGetLastError()));
     r2g_job J = *job;
-    J.V = stg->n_slots;
-    J.views = stg->views;
-    J.meas = stg->meas;
+    if (Vs == 1) {
+        J.V = stg->n_slots;  // the slots' views, picked by the entry
+        J.views = stg->views;
+        J.meas = stg->meas;
+    } else {
+        J.views = stg->views + 12 * (size_t)Vs * slot;
+        J.meas = stg->meas + slot * img;
+    }
+    if (pdev) J.patch_origins = pdev;
     J.loss = stg->loss + 2 * (size_t)slot;
     e = r2g_train_step(&J, stg->entries + slot, stream);
     if (e) return e;
@@ -201,6 +233,12 @@ R2G_API r2g_status r2g_train_step_host(const r2g_job* job, const r2g_staging* st
         return fail(R2G_E_CUDA, "r2g_train_step_host: loss read-back failed (%s)",
                     cudaGetErrorString(cudaGetLastError()));
     return R2G_OK;
+}
+
+R2G_API r2g_status r2g_train_step_host(const r2g_job* job, const r2g_staging* stg, int64_t step,
+                                       const float* meas_host, const float* view_host,
+                                       const r2g_round_entry* entry_host, float* loss_host, r2g_stream stream) {
+    return r2g_train_step_host_batch(job, stg, step, meas_host, view_host, nullptr, entry_host, loss_host, stream);
 }
 
 R2G_API r2g_status r2g_train_step_host_wait(const r2g_staging* stg, int64_t step, r2g_stream stream) {

@@ -144,6 +144,53 @@ class _VoxelizeFn(torch.autograd.Function):
         return (*g, None)
 
 
+class _ProjectionLossFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, render, meas, lam, ws):
+        loss = torch.empty(1, dtype=torch.float32, device=render.device)
+        drender = torch.empty_like(render)
+        r2g.r2g_projection_loss(render.detach().contiguous(), meas, lam, loss, drender, ws)
+        ctx.save_for_backward(drender)
+        return loss[0]
+
+    @staticmethod
+    def backward(ctx, g):
+        (drender,) = ctx.saved_tensors
+        return drender * g, None, None, None
+
+
+class _TVFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, vol, G, D, lam, ws):
+        loss = torch.empty(1, dtype=torch.float32, device=vol.device)
+        dvol = torch.empty_like(vol)
+        r2g.r2g_tv3d(vol.detach().contiguous().view(G, D, D, D), lam, loss, dvol.view(G, D, D, D), ws)
+        ctx.save_for_backward(dvol)
+        return loss[0]
+
+    @staticmethod
+    def backward(ctx, g):
+        (dvol,) = ctx.saved_tensors
+        return dvol * g, None, None, None, None
+
+
+def projection_loss(render, meas, lam=LAMBDA_SSIM, ws=None):
+    """Eq. 8's projection term L1 + lam (1 - SSIM) of a [V, H, W] render against the
+    measured [V, H, W] projections, differentiable in the render (r2g_projection_loss)."""
+    V, H, W = render.shape
+    if ws is None:
+        ws = _bytes(r2g.r2g_loss_workspace_size(V, H, W), render.device)
+    return _ProjectionLossFn.apply(render, meas.contiguous(), float(lam), ws)
+
+
+def tv3d(vol, G: int, D: int, lam=LAMBDA_TV, ws=None):
+    """lam x the anisotropic 3D TV summed over G concatenated D^3 volumes (Eq. 8,
+    r2g_tv3d), differentiable in the volumes."""
+    if ws is None:
+        ws = _bytes(r2g.r2g_tv_workspace_size(G, D), vol.device)
+    return _TVFn.apply(vol, int(G), int(D), float(lam), ws)
+
+
 def rasterize(mean, scale, quat, rho, views, rast: Rasterizer):
     """Differentiable X-ray projection (Eq. 5, Eq. 7): [V, H, W]."""
     return _RasterizeFn.apply(mean, scale, quat, rho, views, rast)
@@ -316,8 +363,17 @@ class Scan:
     descriptor for r2g_train_step."""
 
     def __init__(self, G, views_np, meas_np, cam, n_out=256, D=32, tile=None, total_iters=30000,
-                 device="cuda", headroom=1.5, seed=0, biased=False, tv_eps=0.0, dilation=0.0):
+                 device="cuda", headroom=1.5, seed=0, biased=False, tv_eps=0.0, dilation=0.0, all_views=False,
+                 n_patches=1, full_volume=False):
+        """all_views: every step rasterizes all V views in one launch (the batch form of
+        r2g_train_step) instead of one view picked per step; n_patches: TV patches per
+        step (> 1: their origins come from `patch_origins`, a device [n_patches, 3]
+        tensor the caller fills before each step); full_volume: every step also
+        voxelizes the whole n_out^3 output volume into `full_vol` (forward only)."""
         self.state = TrainState(G, device=device)
+        self.all_views = bool(all_views)
+        self.n_patches = max(1, int(n_patches))
+        self.full_volume = bool(full_volume)
         self.biased = bool(biased)
         self.dilation = float(dilation)  # low-pass dilation of the footprint, pixels^2 (0: none, the paper's)
         self.tv_eps = float(tv_eps)   # > 0: isotropic TV with this eps; 0: anisotropic (default)
@@ -334,18 +390,24 @@ class Scan:
         self.views = torch.as_tensor(np.ascontiguousarray(views_np, np.float32), device=device)
         self.meas = torch.as_tensor(np.ascontiguousarray(meas_np, np.float32), device=device)
         self.V = int(self.views.shape[0])
-        self.image = torch.empty((1, cam.H, cam.W), dtype=torch.float32, device=device)
+        self.Vs = self.V if self.all_views else 1   # views rasterized per step
+        NP = self.n_patches
+        self.image = torch.empty((self.Vs, cam.H, cam.W), dtype=torch.float32, device=device)
         self.dimage = torch.empty_like(self.image)
-        self.vol = torch.empty(D ** 3, dtype=torch.float32, device=device)
+        self.vol = torch.empty(NP * D ** 3, dtype=torch.float32, device=device)
         self.dvol = torch.empty_like(self.vol)
         self.loss = torch.zeros(2, dtype=torch.float32, device=device)
-        self.rast = Rasterizer(self.M, 1, cam, tile=tile or SCAN_TILE, device=device, biased=biased,
+        self.patch_origins = torch.zeros((NP, 3), dtype=torch.float32, device=device)
+        self.rast = Rasterizer(self.M, self.Vs, cam, tile=tile or SCAN_TILE, device=device, biased=biased,
                                dilation=self.dilation)
-        from .inputs import patch_grid
+        from .inputs import cube_grid, patch_grid
 
-        self.vox = Voxelizer(self.M, patch_grid((0, 0, 0), D, n_out), device=device)
-        self.loss_ws = _bytes(r2g.r2g_loss_workspace_size(1, cam.H, cam.W), device)
-        self.tv_ws = _bytes(r2g.r2g_tv_workspace_size(1, D), device)
+        self.vox = Voxelizer(self.M, [patch_grid((0, 0, 0), D, n_out)] * NP, device=device)
+        self.full_vox = Voxelizer(self.M, cube_grid(n_out), device=device) if self.full_volume else None
+        self.full_vol = (torch.empty((n_out, n_out, n_out), dtype=torch.float32, device=device)
+                         if self.full_volume else None)
+        self.loss_ws = _bytes(r2g.r2g_loss_workspace_size(self.Vs, cam.H, cam.W), device)
+        self.tv_ws = _bytes(r2g.r2g_tv_workspace_size(NP, D), device)
         self.adam = r2g.adam_opts(total_iters=total_iters)
         self.device = device
         self.headroom = headroom
@@ -412,17 +474,27 @@ class Scan:
 
         mean, scale, quat, rho = self.state.params()
         need_r, need_v = 0, 0
-        for v in np.linspace(0, self.V - 1, min(self.V, probes)).astype(int):
-            self.rast.forward(mean, scale, quat, rho, self.views[v:v + 1], self.image, check=True)
-            need_r = max(need_r, r2g.r2g_poll(self.rast.ws)[1])
+        if self.all_views:
+            self.rast.forward(mean, scale, quat, rho, self.views, self.image, check=True)
+            need_r = r2g.r2g_poll(self.rast.ws)[1]
+        else:
+            for v in np.linspace(0, self.V - 1, min(self.V, probes)).astype(int):
+                self.rast.forward(mean, scale, quat, rho, self.views[v:v + 1], self.image, check=True)
+                need_r = max(need_r, r2g.r2g_poll(self.rast.ws)[1])
+        NP = self.n_patches
         for off in ((0, 0, 0), ((self.n_out - self.D) // 2,) * 3, (self.n_out - self.D,) * 3):
-            self.vox.set_grids(patch_grid(off, self.D, self.n_out))
+            # every patch of the step at the densest of the probed positions
+            self.vox.set_grids([patch_grid(off, self.D, self.n_out)] * NP)
             self.vox.forward(mean, scale, quat, rho, self.vol, check=True)
             need_v = max(need_v, r2g.r2g_poll(self.vox.ws)[1])
         self.rast.capacity = int(need_r * headroom) + 4096
         self.rast._alloc()
         self.vox.capacity = int(need_v * headroom) + 4096
         self.vox._alloc()
+        if self.full_vox is not None:
+            self.full_vox.forward(mean, scale, quat, rho, self.full_vol.view(-1), check=True)
+            self.full_vox.capacity = int(r2g.r2g_poll(self.full_vox.ws)[1] * headroom) + 4096
+            self.full_vox._alloc()
 
     def _make_job(self):
         s = self.state
@@ -446,6 +518,13 @@ class Scan:
         J.loss_ws, J.loss_ws_bytes = self.loss_ws.data_ptr(), self.loss_ws.numel()
         J.tv_ws, J.tv_ws_bytes = self.tv_ws.data_ptr(), self.tv_ws.numel()
         J.tv_eps = self.tv_eps
+        J.views_per_step = self.V if self.all_views else 0
+        J.n_patches = self.n_patches if self.n_patches > 1 else 0
+        J.patch_origins = self.patch_origins.data_ptr() if self.n_patches > 1 else None
+        if self.full_vox is not None:
+            J.full_vol = self.full_vol.data_ptr()
+            J.full_grid = self.full_vox.grids[0]
+            J.full_ws, J.full_ws_bytes = self.full_vox.ws.data_ptr(), self.full_vox.ws.numel()
         if self.dens_grad is not None:
             J.dens_grad, J.dens_count = self.dens_grad.data_ptr(), self.dens_count.data_ptr()
         return J
@@ -472,7 +551,7 @@ class Scan:
         sep = int(self.rast.opts.separate_lists)
         times = {}
         for tile in tiles:
-            self.rast = Rasterizer(self.M, 1, self.cam, tile=tile, device=self.device, biased=self.biased,
+            self.rast = Rasterizer(self.M, self.Vs, self.cam, tile=tile, device=self.device, biased=self.biased,
                                    dilation=self.dilation)
             self.rast.opts.separate_lists = sep
             self._size_workspaces(self.headroom, probes=2)
@@ -488,7 +567,7 @@ class Scan:
             for dst, src in zip((s.raw, s.act, s.m, s.v), saved):
                 dst.copy_(src)
         best = min(times, key=times.get)
-        self.rast = Rasterizer(self.M, 1, self.cam, tile=best, device=self.device, biased=self.biased,
+        self.rast = Rasterizer(self.M, self.Vs, self.cam, tile=best, device=self.device, biased=self.biased,
                                dilation=self.dilation)
         self.rast.opts.separate_lists = sep
         self._size_workspaces(self.headroom, probes=2)
@@ -510,20 +589,24 @@ class Scan:
         s = self.state
         n = sum(t.numel() * t.element_size() for t in (s.raw, s.act, s.grad, s.m, s.v, self.views, self.meas,
                                                          self.image, self.dimage, self.vol, self.dvol, self.loss))
+        if self.full_vox is not None:
+            n += self.full_vol.numel() * 4 + self.full_vox.ws.numel()
         return int(n + self.rast.ws.numel() + self.vox.ws.numel() + self.loss_ws.numel() + self.tv_ws.numel())
 
     def overflowed(self) -> bool:
-        return r2g.r2g_poll(self.rast.ws)[0] != r2g.R2G_OK or r2g.r2g_poll(self.vox.ws)[0] != r2g.R2G_OK
+        bad = r2g.r2g_poll(self.rast.ws)[0] != r2g.R2G_OK or r2g.r2g_poll(self.vox.ws)[0] != r2g.R2G_OK
+        return bad or (self.full_vox is not None and r2g.r2g_poll(self.full_vox.ws)[0] != r2g.R2G_OK)
 
 
 class HostFeed:
-    """Training one scan from host memory (r2g_train_step_host): its measured
+    """Training one scan from host memory (r2g_train_step_host_batch): its measured
     projections [V][H][W] and view table [V][12] stay in pinned host memory; each
-    step's measurement, geometry row and round entry go into one of n_slots device
-    staging slots on a copy stream while the steps before it run, and its losses
-    come back to pinned host memory.  step() returns the losses of the step
-    n_slots - 1 calls earlier (None for the first n_slots - 1 calls); finish()
-    returns those still in flight."""
+    step's measurements, geometry rows, TV patch origins and round entry go into
+    one of n_slots device staging slots on a copy stream while the steps before it
+    run, and its losses come back to pinned host memory.  A one-view scan stages the
+    step's view; an all-views scan (Scan(all_views=True)) stages all V views every
+    step.  step() returns the losses of the step n_slots - 1 calls earlier (None
+    for the first n_slots - 1 calls); finish() returns those still in flight."""
 
     def __init__(self, scan: "Scan", meas_host: torch.Tensor, views_host: torch.Tensor, n_slots=3, stream=None):
         if not (meas_host.is_pinned() and views_host.is_pinned()):
@@ -533,19 +616,23 @@ class HostFeed:
             raise ValueError("measurements must be [V][H][W] and views [V][12]")
         dev = scan.device
         self.scan, self.n = scan, int(n_slots)
+        Vs, NP = scan.Vs, scan.n_patches
         self.meas_host, self.views_host = meas_host.contiguous(), views_host.contiguous()
-        self.meas_stage = torch.empty((self.n, H, W), dtype=torch.float32, device=dev)
-        self.views_stage = torch.empty((self.n, 12), dtype=torch.float32, device=dev)
+        self.meas_stage = torch.empty((self.n, Vs, H, W), dtype=torch.float32, device=dev)
+        self.views_stage = torch.empty((self.n, Vs, 12), dtype=torch.float32, device=dev)
         self.ent_stage = torch.zeros((self.n, 8), dtype=torch.int32, device=dev)
         self.ent_host = torch.zeros((self.n, 8), dtype=torch.int32).pin_memory()
+        self.org_stage = torch.zeros((self.n, NP, 3), dtype=torch.float32, device=dev)
         self.loss_dev = torch.zeros((self.n, 2), dtype=torch.float32, device=dev)
         self.loss_host = torch.zeros((self.n, 2), dtype=torch.float32).pin_memory()
         self.loss_np = self.loss_host.numpy()
         self.stg = r2g.Staging(self.n, self.meas_stage.data_ptr(), self.views_stage.data_ptr(),
-                               self.ent_stage.data_ptr(), self.ent_host.data_ptr(), self.loss_dev.data_ptr())
+                               self.ent_stage.data_ptr(), self.ent_host.data_ptr(), self.loss_dev.data_ptr(),
+                               self.org_stage.data_ptr())
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self._meas0, self._img = self.meas_host.data_ptr(), 4 * H * W
         self._views0, self._loss0 = self.views_host.data_ptr(), self.loss_host.data_ptr()
+        self.bytes_in = 4 * Vs * H * W + 48 * Vs + 32 + (12 * NP if NP > 1 else 0)  # per step, host -> device
         self.k = 0   # steps queued
         self.r = 0   # first step whose losses have not been returned
 
@@ -555,12 +642,16 @@ class HostFeed:
         self.r = r + 1
         return float(self.loss_np[r % self.n, 0]), float(self.loss_np[r % self.n, 1])
 
-    def step(self, view: int, entry_ptr: int):
-        """Queue one iteration on the measurement and geometry of `view` with the
-        round entry at host address entry_ptr (read during the call)."""
+    def step(self, view: int, entry_ptr: int, origins_ptr: int | None = None):
+        """Queue one iteration on the measurement and geometry of `view` (all views for
+        an all-views scan) with the round entry at host address entry_ptr and, for a
+        scan with several TV patches, their origins at host address origins_ptr
+        (pinned float32 [n_patches][3]; both read during the call)."""
         k, n = self.k, self.n
-        r2g.r2g_train_step_host(self.scan.job, self.stg, k, self._meas0 + view * self._img, self._views0 + 48 * view,
-                                entry_ptr, self._loss0 + 8 * (k % n), self.stream)
+        v0 = 0 if self.scan.all_views else view
+        r2g.r2g_train_step_host_batch(self.scan.job, self.stg, k, self._meas0 + v0 * self._img,
+                                      self._views0 + 48 * v0, origins_ptr, entry_ptr, self._loss0 + 8 * (k % n),
+                                      self.stream)
         self.k = k + 1
         # step k + 1 reuses the loss buffer of step k + 1 - n: return that step's first
         return self._take() if self.k - self.r >= n else None

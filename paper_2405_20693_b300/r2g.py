@@ -74,12 +74,16 @@ class Job(ctypes.Structure):
                 ("raster_ws_bytes", ctypes.c_size_t), ("voxel_ws", ctypes.c_void_p),
                 ("voxel_ws_bytes", ctypes.c_size_t), ("loss_ws", ctypes.c_void_p),
                 ("loss_ws_bytes", ctypes.c_size_t), ("tv_ws", ctypes.c_void_p), ("tv_ws_bytes", ctypes.c_size_t),
-                ("dens_grad", ctypes.c_void_p), ("dens_count", ctypes.c_void_p), ("tv_eps", ctypes.c_float)]
+                ("dens_grad", ctypes.c_void_p), ("dens_count", ctypes.c_void_p), ("tv_eps", ctypes.c_float),
+                ("views_per_step", ctypes.c_int32), ("n_patches", ctypes.c_int32), ("patch_origins", ctypes.c_void_p),
+                ("full_vol", ctypes.c_void_p), ("full_grid", Grid), ("full_ws", ctypes.c_void_p),
+                ("full_ws_bytes", ctypes.c_size_t)]
 
 
 class Staging(ctypes.Structure):
     _fields_ = [("n_slots", ctypes.c_int32), ("meas", ctypes.c_void_p), ("views", ctypes.c_void_p),
-                ("entries", ctypes.c_void_p), ("entries_host", ctypes.c_void_p), ("loss", ctypes.c_void_p)]
+                ("entries", ctypes.c_void_p), ("entries_host", ctypes.c_void_p), ("loss", ctypes.c_void_p),
+                ("patch_origins", ctypes.c_void_p)]
 
 
 def camera(cam) -> Camera:
@@ -162,6 +166,7 @@ def lib():
             "r2g_poll": (_I32, [_P, _SZ, _P, _P]),
             "r2g_train_step": (_I32, [_P, _P, _P]),
             "r2g_train_step_host": (_I32, [_P, _P, _I64, _P, _P, _P, _P, _P]),
+            "r2g_train_step_host_batch": (_I32, [_P, _P, _I64, _P, _P, _P, _P, _P, _P]),
             "r2g_train_step_host_wait": (_I32, [_P, _I64, _P]),
             "r2g_upload_round": (_I32, [_P, _P, _I32, _P]),
             "r2g_profile_enable": (_I32, [_I32, _I32]),
@@ -455,6 +460,15 @@ def r2g_train_step_host(job: Job, stg: Staging, step: int, meas_ptr: int, view_p
     measured projection, geometry row, round entry and 2-float loss buffer)."""
     _check(lib().r2g_train_step_host(ctypes.byref(job), ctypes.byref(stg), int(step), meas_ptr, view_ptr, entry_ptr,
                                      loss_ptr, _stream(stream)))
+
+
+def r2g_train_step_host_batch(job: Job, stg: Staging, step: int, meas_ptr: int, views_ptr: int, origins_ptr,
+                              entry_ptr: int, loss_ptr: int, stream=None):
+    """The batch form of r2g_train_step_host: host addresses of the step's pinned
+    measured projections [Vs][H][W], geometry rows [Vs][12], TV patch origins
+    [n_patches][3] (or None for one patch), round entry and 2-float loss buffer."""
+    _check(lib().r2g_train_step_host_batch(ctypes.byref(job), ctypes.byref(stg), int(step), meas_ptr, views_ptr,
+                                           origins_ptr, entry_ptr, loss_ptr, _stream(stream)))
 
 
 def r2g_train_step_host_wait(stg: Staging, step: int, stream=None):

@@ -333,6 +333,42 @@ def _aniso(M=5, seed=41):
     return I.GaussianSet(mean, scale, I.random_quats(g, M), g.uniform(0.3, 1.0, M))
 
 
+def _bump(G, kind, i, comp, h):
+    H = I.GaussianSet(*(np.array(a, np.float64) for a in (G.mean, G.scale, G.quat, G.rho)))  # copies
+    arr = (H.mean, H.scale, H.quat, H.rho)[kind]
+    if kind == 3:
+        arr[i] += h
+    else:
+        arr[i, comp] += h
+    return H
+
+
+@pytest.mark.parametrize("kind", [0, 1, 2, 3])
+def test_gated_forms_hold_the_gate_fixed(kind):
+    """render_gated / voxelize_gated with the gate set equal to the value set are
+    render / voxelize bit for bit, and their central differences in the value set
+    (gate fixed) equal the complex-step derivatives, whose gate uses the real part
+    and so is fixed by construction."""
+    G = small_set(M=8, seed=21, lo=0.05, hi=0.15)
+    cam = I.cone_camera(36, 40, pitch=I.CONE_PITCH * 14)
+    views = I.view_table(np.deg2rad([20.0, 140.0]), I.CONE_L_SO)
+    assert np.array_equal(core.render(G, views, cam)[0], core.render_gated(G, G, views, cam))
+    gd = np.asarray(I.grid_desc((-0.45, -0.4, -0.35), (0.05,) * 3, (18, 17, 16)), np.float64)
+    assert np.array_equal(core.voxelize(G, gd)[0], core.voxelize_gated(G, G, gd))
+    w = np.random.default_rng(22).standard_normal((2, 36, 40))
+    wv = np.random.default_rng(23).standard_normal(18 * 17 * 16)
+    for i, comp in ((1, 0), (5, kind % 3)):
+        h = 1e-5
+        fd = ((w * core.render_gated(_bump(G, kind, i, comp, h), G, views, cam)).sum()
+              - (w * core.render_gated(_bump(G, kind, i, comp, -h), G, views, cam)).sum()) / (2 * h)
+        cs = (w * core.render_cs(G, views, cam, 9.0, kind, i, comp)).sum()
+        assert abs(fd - cs) <= 1e-6 * max(abs(cs), 1e-3), (kind, i, fd, cs)
+        fv = ((wv * core.voxelize_gated(_bump(G, kind, i, comp, h), G, gd)).sum()
+              - (wv * core.voxelize_gated(_bump(G, kind, i, comp, -h), G, gd)).sum()) / (2 * h)
+        cv = (wv * core.voxelize_cs(G, gd, Q3, kind, i, comp)).sum()
+        assert abs(fv - cv) <= 1e-6 * max(abs(cv), 1e-3), (kind, i, fv, cv)
+
+
 def test_biased_projected_mass_is_the_2d_gaussian_mass():
     """Parallel beam, no gate: with rho_hat = rho the splat of Gaussian i is an
     unnormalised 2D Gaussian of covariance Sigma^_v (top-left 2x2 of W Sigma W^T), so
@@ -520,6 +556,45 @@ def test_projection_loss_gradient_matches_central_differences():
         xm[idx] -= h
         fd = (losses.projection_loss(xp, y)[0] - losses.projection_loss(xm, y)[0]) / (2 * h)
         assert abs(fd - G[idx]) <= 1e-6 * abs(G).max()
+
+
+def _window_mass_1d(n: int) -> np.ndarray:
+    """Share of the 11-tap, sigma 1.5 Gaussian window (normalised to 1) that falls
+    inside [0, n) when centred on each of the n positions: the zero padding drops the
+    rest."""
+    k = np.arange(11) - 5.0
+    w = np.exp(-k * k / (2 * 1.5 ** 2))
+    w /= w.sum()
+    return np.array([sum(w[j] for j in range(11) if 0 <= i + j - 5 < n) for i in range(n)])
+
+
+@pytest.mark.parametrize("lam", [0.0, 0.25, 1.0])
+def test_projection_loss_closed_form_constant_images(lam):
+    """Eq. 8's projection term on constant views: render a_v, measurement b_v on an
+    H x W detector.  L1 = the mean of |a_v - b_v| over every pixel of the batch (a sum
+    would be H W V times larger).  With zero padding the window keeps the share
+    m = m_r m_c of its mass at pixel (r, c), so the local means are m a, m b and the
+    (co)variances m (1 - m) a^2, m (1 - m) b^2, m (1 - m) a b; SSIM follows in closed
+    form, and L = L1 + lambda (1 - mean over views of the mean SSIM).  The gradient
+    at lambda = 0 is sign(a_v - b_v) / (V H W) at every pixel."""
+    H, W = 13, 18
+    a = np.array([0.7, 0.15])
+    b = np.array([0.2, 0.4])
+    render = np.stack([np.full((H, W), x) for x in a])
+    meas = np.stack([np.full((H, W), x) for x in b])
+    L, G = losses.projection_loss(render, meas, lam)
+    m = np.outer(_window_mass_1d(H), _window_mass_1d(W))
+    C1, C2 = 1e-4, 9e-4
+    s_mean = 0.0
+    for x, y in zip(a, b):
+        v = m * (1.0 - m)
+        S = ((2 * m * m * x * y + C1) * (2 * v * x * y + C2)) / ((m * m * (x * x + y * y) + C1) * (v * (x * x + y * y) + C2))
+        s_mean += S.mean() / len(a)
+    want = np.abs(a - b).mean() + lam * (1.0 - s_mean)
+    assert abs(L - want) < 1e-12
+    if lam == 0.0:
+        sg = np.sign(a - b)[:, None, None] * np.ones((2, H, W)) / render.size
+        assert np.abs(G - sg).max() < 1e-18
 
 
 def test_tv_closed_form_and_gradient():
