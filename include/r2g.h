@@ -47,8 +47,8 @@ typedef enum {
     R2G_E_INVAL = 1,    /* bad argument; nothing was launched */
     R2G_E_CAPACITY = 2, /* more tile/brick list entries than the workspace holds */
     R2G_E_CUDA = 3,     /* a CUDA call or launch failed */
-    R2G_E_TIMEOUT = 4,  /* reserved: a bounded device-side wait gave up */
-    R2G_E_NUMERIC = 5   /* reserved: non-finite values detected */
+    R2G_E_TIMEOUT = 4,  /* a bounded device-side wait gave up (see r2g_set_wait_limit) */
+    R2G_E_NUMERIC = 5   /* a training step met a non-finite loss and skipped its update */
 } r2g_status;
 
 /* Detector and beam of one scan (App. A).  Pixel (r, c) has its centre at
@@ -285,9 +285,21 @@ r2g_status r2g_adam_step(int64_t M, float* raw, float* act, float* grad, float* 
 /* ---------------------------------------------------------------- status */
 
 /* Waits for `stream`, then returns the device status of the last call on `ws`
- * (R2G_OK or R2G_E_CAPACITY) and, if needed_keys is not NULL, the number of list
+ * (R2G_OK, R2G_E_CAPACITY, R2G_E_TIMEOUT, or -- on a training step's raster
+ * workspace -- R2G_E_NUMERIC) and, if needed_keys is not NULL, the number of list
  * entries that call needed.  Clears nothing. */
 r2g_status r2g_poll(const void* ws, size_t ws_bytes, r2g_stream stream, int64_t* needed_keys);
+
+/* Bound of the library's device-side waits: the grid barriers of the cooperative
+ * list builds (one launch for projection + lists when the whole grid can be
+ * resident) give up after `polls` polls (about 20 ns apart) instead of waiting on;
+ * the call's workspace status then reads R2G_E_TIMEOUT (r2g_poll), the blocks leave
+ * the build, and the kernels that would read its lists (the splat and voxel kernels
+ * of that call and of the backward on the same workspace) skip their work, so the
+ * outputs of that call are not valid but every kernel ends.  0 restores the default
+ * (2^22 polls, about 0.1 s, far beyond any healthy barrier).  Process-wide; applies
+ * to launches issued after the call.  Always R2G_OK. */
+r2g_status r2g_set_wait_limit(uint64_t polls);
 
 /* ---------------------------------------------------------------- training step
  *
@@ -367,6 +379,10 @@ typedef struct {
     size_t full_ws_bytes;
 } r2g_job;
 
+/* Numeric guard: when either loss of the step is not finite (a NaN or an infinity in
+ * the measured projections, say), the step takes no update -- the parameters, both
+ * Adam moments and the adaptive-control statistics stay as they were -- and the raster
+ * workspace's status reads R2G_E_NUMERIC (r2g_poll) until the next step on it. */
 r2g_status r2g_train_step(const r2g_job* job, const r2g_round_entry* entry, r2g_stream stream);
 
 /* Staging slots of r2g_train_step_host (all caller-owned): n_slots in 1..16.  Vs =

@@ -33,6 +33,17 @@ r2g_status check_launch(const char* what) {
     return R2G_OK;
 }
 
+// ---------------------------------------------------------------- bounded waits
+
+namespace {
+std::atomic<unsigned long long> g_wait_polls{0};
+}
+
+unsigned long long wait_polls() {
+    const unsigned long long p = g_wait_polls.load(std::memory_order_relaxed);
+    return p ? p : kGridSyncSpins;
+}
+
 // ---------------------------------------------------------------- profiling
 
 namespace {
@@ -149,7 +160,16 @@ R2G_API r2g_status r2g_poll(const void* ws, size_t ws_bytes, r2g_stream stream, 
     if (needed_keys) *needed_keys = (int64_t)st.needed;
     if (st.status == R2G_E_CAPACITY)
         return fail(R2G_E_CAPACITY, "list entries needed: %llu, capacity: %llu", st.needed, st.n_keys);
+    if (st.status == R2G_E_TIMEOUT)
+        return fail(R2G_E_TIMEOUT, "a grid barrier of the list build gave up after %llu polls", wait_polls());
+    if (st.status == R2G_E_NUMERIC)
+        return fail(R2G_E_NUMERIC, "a non-finite loss: the step left the parameters and moments unchanged");
     return (r2g_status)st.status;
+}
+
+R2G_API r2g_status r2g_set_wait_limit(uint64_t polls) {
+    g_wait_polls.store(polls, std::memory_order_relaxed);
+    return R2G_OK;
 }
 
 R2G_API r2g_status r2g_pair_count(const void* ws, size_t ws_bytes, int64_t* pairs, r2g_stream stream) {

@@ -88,7 +88,18 @@ struct AdamState {
     // with a gradient of |dL/dp^| in normalised device coordinates, and their count
     float* dens_grad;
     float* dens_count;
+    // numeric guard (optional): when the step's losses loss_guard[0..1] are not both
+    // finite, the kernel takes no step at all (parameters, moments and statistics
+    // unchanged) and writes R2G_E_NUMERIC into *guard_status
+    const float* loss_guard;
+    WsStatus* guard_status;
 };
+
+// Device: whether the step's losses allow an update (true without a guard).
+__device__ __forceinline__ bool adam_loss_ok(const AdamState& st) {
+    if (!st.loss_guard) return true;
+    return isfinite(st.loss_guard[0]) && isfinite(st.loss_guard[1]);
+}
 
 // Device: one parameter at flat index e of group grp with this kernel's own
 // gradient contribution g_own (added to st.grad[e]).

@@ -135,6 +135,7 @@ struct FusedKeys {
     unsigned long long items_cap;
     WsStatus* item_st;        // n_keys = item count
     int kd_per_key;           // arrival counters per key (consecutive; 0 taken as 1)
+    unsigned long long wait_polls;  // grid-barrier polls before a wait gives up (cooperative builds)
 };
 
 // Emission of one block's records (blockIdx.x * per_block .. + per_block), in
@@ -437,10 +438,14 @@ __global__ void __launch_bounds__(256) k_fused_scatter(Op op, const uint64_t* __
 
 // Grid barrier of a cooperative launch (all blocks resident): thread 0 of each
 // block arrives on the status block's counter and waits, with a bounded spin, until
-// `epoch` x gridDim.x blocks have arrived; a wait that gives up sets R2G_E_TIMEOUT
-// (the results are then not valid) instead of hanging.
-constexpr unsigned long long kGridSyncSpins = 1ull << 22;
-__device__ __forceinline__ void grid_barrier(WsStatus* st, unsigned int epoch) {
+// `epoch` x gridDim.x blocks have arrived.  Returns true (in every thread of the
+// block) when they have; a wait that gives up after `polls` polls sets
+// R2G_E_TIMEOUT and returns false, and the caller's block then leaves the kernel:
+// it never arrives at a later barrier, so every other block's later wait gives up
+// too, and no block acts on phases that did not finish.  The kernels that consume
+// the lists skip their work when the status holds R2G_E_TIMEOUT.
+__device__ __forceinline__ bool grid_barrier(WsStatus* st, unsigned int epoch, unsigned long long polls) {
+    __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         const unsigned long long target = (unsigned long long)epoch * gridDim.x;
@@ -448,19 +453,23 @@ __device__ __forceinline__ void grid_barrier(WsStatus* st, unsigned int epoch) {
         // barrier) are visible to any block that observes the arrival
         asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(&st->grid_sync), "l"(1ull) : "memory");
         unsigned long long spins = 0, seen;
+        int ok = 1;
         for (;;) {
             asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(seen) : "l"(&st->grid_sync) : "memory");
             if (seen >= target) break;
-            if (++spins > kGridSyncSpins) {
+            if (++spins > polls) {
                 atomicExch(&st->status, (int32_t)R2G_E_TIMEOUT);
+                ok = 0;
                 break;
             }
             __nanosleep(20);
         }
+        s_ok = ok;
         // the acquire load that saw the last arrival orders the block's later reads
         // (through the block barrier) after every block's writes
     }
     __syncthreads();
+    return s_ok != 0;
 }
 
 // The key phase of the cooperative builds: the blocks that own keys (warp w of
@@ -500,9 +509,9 @@ __global__ void __launch_bounds__(256) k_lists_coop(Op op, long long n_rec, long
     __shared__ uint32_t sm8[8];
     emit_block<Op, true>(op, n_rec, per_block, partials[blockIdx.x], a, capacity, hist, key_totals, n_keys, pool,
                          reinterpret_cast<uint4*>(pool + kFusedKeys), pool + 2 * kFusedKeys, sm8);
-    grid_barrier(st, 1);
+    if (!grid_barrier(st, 1, fk.wait_polls)) return;
     keys_phase(hist, key_totals, n_keys, fk, pool, sm8);
-    grid_barrier(st, 2);
+    if (!grid_barrier(st, 2, fk.wait_polls)) return;
     const unsigned long long n_written = st->n_keys;
     const unsigned long long lo = min(partials[blockIdx.x], n_written);
     const unsigned long long hi =
@@ -532,7 +541,7 @@ __global__ void __launch_bounds__(256) k_plists_coop(Proj proj, Op op, long long
     if (threadIdx.x == 0) counts[blockIdx.x] = mine;
     if (blockIdx.x == 0)
         for (int k = threadIdx.x; k < n_keys; k += 256) key_totals[k] = 0;
-    grid_barrier(st, 1);
+    if (!grid_barrier(st, 1, fk.wait_polls)) return;
     unsigned long long before = 0, total = 0;
     for (int i = threadIdx.x; i < (int)gridDim.x; i += 256) {
         const unsigned long long c = __ldcg(counts + i);
@@ -550,9 +559,9 @@ __global__ void __launch_bounds__(256) k_plists_coop(Proj proj, Op op, long long
     const long long per_block = 256ll * per_thread;
     emit_block<Op, true>(op, n_rec, per_block, before, a, capacity, hist, key_totals, n_keys, pool,
                          reinterpret_cast<uint4*>(pool + kFusedKeys), pool + 2 * kFusedKeys, sm8);
-    grid_barrier(st, 2);
+    if (!grid_barrier(st, 2, fk.wait_polls)) return;
     keys_phase(hist, key_totals, n_keys, fk, pool, sm8);
-    grid_barrier(st, 3);
+    if (!grid_barrier(st, 3, fk.wait_polls)) return;
     pdl_trigger();  // the forward splat may become resident during the scatter
     const unsigned long long lo = before < written ? before : written;
     const unsigned long long hi = before + mine < written ? before + mine : written;
@@ -622,8 +631,8 @@ bool launch_plists_coop(const Proj& proj, const Op& op, long long n_rec, long lo
     if (blocks < 1 || blocks > max_blocks) return false;
     uint32_t* hist = scratch;
     uint32_t* totals = scratch + (size_t)kRadix * kSortBlocksMax;
-    const FusedKeys fk{(uint32_t)chunk, ranges,  key_done, item_off, items, (unsigned long long)items_cap,
-                       item_st,         kd_per_key};
+    const FusedKeys fk{(uint32_t)chunk, ranges,  key_done,  item_off,    items, (unsigned long long)items_cap,
+                       item_st,         kd_per_key, wait_polls()};
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)blocks);
     cfg.blockDim = dim3(256);
@@ -664,8 +673,8 @@ uint64_t* build_lists(const Op& op, long long n_rec, long long n_slots, unsigned
         uint32_t* hist = scratch;
         uint32_t* totals = scratch + (size_t)kRadix * kSortBlocksMax;
         const int nk = (int)n_slots;
-        const FusedKeys fk{(uint32_t)chunk, ranges,  key_done, item_off, items, (unsigned long long)items_cap,
-                           item_st,         kd_per_key};
+        const FusedKeys fk{(uint32_t)chunk, ranges,  key_done,  item_off,    items, (unsigned long long)items_cap,
+                           item_st,         kd_per_key, wait_polls()};
         prof_begin(prof.emit, s);
         if (allow_coop &&
             launch_lists_coop(op, n_rec, per_block, partials, a, b, ucap, hist, totals, nk, st, fk, lb.blocks, s)) {

@@ -37,6 +37,14 @@ void prof_begin(int k, cudaStream_t s);
 void prof_end(int k, cudaStream_t s);
 void note_launches(int n);
 
+// ---------------------------------------------------------------- bounded waits
+
+// Polls a device-side wait (the grid barriers of the cooperative list builds) makes
+// before it gives up and reports R2G_E_TIMEOUT: r2g_set_wait_limit's value, else
+// kGridSyncSpins (polls ~20 ns apart: about 0.1 s).  Read when a launch is issued.
+constexpr unsigned long long kGridSyncSpins = 1ull << 22;
+unsigned long long wait_polls();
+
 // ---------------------------------------------------------------- workspace
 
 // Status block at offset 0 of every workspace (256 bytes).

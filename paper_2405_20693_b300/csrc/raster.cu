@@ -443,7 +443,8 @@ __global__ void __launch_bounds__(32 * kFwdWarps) k_splat_fwd(const float4* __re
     const unsigned long long gw = (unsigned long long)blockIdx.x * kFwdWarps + warp;
     const unsigned long long it = gw / NW;
     const int wb = (int)(gw - it * NW);
-    if (it >= item_st->n_keys) return;  // whole warps
+    // whole warps: past the item count, or after a list build that gave up a wait
+    if (it >= item_st->n_keys || st->status == R2G_E_TIMEOUT) return;
     const uint64_t item = items[it];
     const int tile = (int)(item >> 32);
     const uint32_t chunk = (uint32_t)item;
@@ -627,7 +628,8 @@ __global__ void __launch_bounds__(kBwdThreads) k_splat_bwd(const float4* __restr
                                                            const WsStatus* __restrict__ item_st, long long M,
                                                            int tiles_x, int tiles_per_view, int H, int W, float Tq,
                                                            const float* __restrict__ dimage,
-                                                           float4* __restrict__ mom) {
+                                                           float4* __restrict__ mom,
+                                                           const WsStatus* __restrict__ st) {
     static_assert(kChunk == kBwdThreads, "one record per thread");
     static_assert(TW <= 32 && TH <= 32 && UW == 4 && UH >= 1 && UH <= 2 && TW % UW == 0,
                   "unit decode is exact for these sizes (units per record <= 2^10); a unit row is one float4");
@@ -642,7 +644,8 @@ __global__ void __launch_bounds__(kBwdThreads) k_splat_bwd(const float4* __restr
     pdl_trigger();
     pdl_wait();  // dL/dI of the loss before
     const unsigned long long it = blockIdx.x;
-    if (it >= item_st->n_keys) return;
+    // past the item count, or after a list build that gave up a wait
+    if (it >= item_st->n_keys || st->status == R2G_E_TIMEOUT) return;
     const uint64_t item = items[it];
     const int tile = (int)(item >> 32);
     const uint32_t chunk = (uint32_t)item;
@@ -799,7 +802,15 @@ __global__ void __launch_bounds__(128) k_project_bwd(Params G, const float* __re
     AdamPre pre;
     if (ADAM) adam_prefetch_state(adam, i, pre);
     pdl_wait();  // the backward moments, and the gradient already in adam.grad
-    if (ADAM) adam_prefetch_grad(adam, i, pre);
+    if (ADAM) {
+        // a non-finite loss: no update anywhere (every thread sees the same losses); the
+        // moments stay in their slots, and the next forward clears them
+        if (!adam_loss_ok(adam)) {
+            if (i == 0) atomicExch(&adam.guard_status->status, (int32_t)R2G_E_NUMERIC);
+            return;
+        }
+        adam_prefetch_grad(adam, i, pre);
+    }
     float gp[3] = {0.f, 0.f, 0.f}, gs[3] = {0.f, 0.f, 0.f}, gR[3][3] = {{0.f}}, grho = 0.f;
     float dens_g = 0.f, dens_n = 0.f;  // adaptive-control statistics of this call
     Proj P;
@@ -1114,11 +1125,11 @@ void launch_fwd(int tw, int th, const FwdArgs& f, long long M, const RasterLayou
 
 void launch_bwd(int tw, int th, const float4* rec, const float4* srec, const uint2* ranges, const uint64_t* sorted,
                 const uint64_t* items, const WsStatus* item_st, long long icap, long long M, const RasterLayout& L,
-                int H, int W, float Tq, const float* dimage, float4* mom, cudaStream_t s) {
+                int H, int W, float Tq, const float* dimage, float4* mom, const WsStatus* st, cudaStream_t s) {
     const unsigned grid = (unsigned)icap;
 #define R2G_BWD(TW, TH)                                                                                       \
     launch_pdl(k_splat_bwd<TW, TH, kBwdUnitW, kBwdUnitH>, dim3(grid), dim3(kBwdThreads), 0, s, rec, srec, ranges, \
-               sorted, items, item_st, M, L.tiles_x, L.tiles_per_view, H, W, Tq, dimage, mom)
+               sorted, items, item_st, M, L.tiles_x, L.tiles_per_view, H, W, Tq, dimage, mom, st)
     if (tw == 16 && th == 16)
         R2G_BWD(16, 16);
     else if (tw == 8 && th == 8)
@@ -1293,7 +1304,7 @@ r2g_status r2g::rasterize_backward_impl(int64_t M, const float* mean, const floa
         prof_begin(P_SPLAT_BWD, stream);
         const float4* srec = fused_lists(L.n_tiles) ? reinterpret_cast<const float4*>(base + T.srec) : nullptr;
         launch_bwd(opts->tile_w, opts->tile_h, rec, srec, ranges, sorted, items, item_st, T.icap, M, L, cam->H, cam->W,
-                   Tq, dimage, mom, stream);
+                   Tq, dimage, mom, reinterpret_cast<const WsStatus*>(base + L.status), stream);
         prof_end(P_SPLAT_BWD, stream);
         note_launches(1);
     }

@@ -167,8 +167,10 @@ R2G_API r2g_status r2g_train_step(const r2g_job* job, const r2g_round_entry* ent
     if (e_px) return e_px;
     if (J.adam.total_iters < 1 || !(J.adam.final_factor > 0.f))
         return fail(R2G_E_INVAL, "r2g_train_step: bad Adam options");
-    const AdamState adam{J.raw,  J.act, J.adam_m, J.adam_v, J.grad, adam_args(M, &J.adam, 0, &entry->it),
-                         J.dens_grad, J.dens_count};
+    // the update is skipped (and R2G_E_NUMERIC reported in the raster workspace's
+    // status) when the step's loss is not finite, so one bad step cannot poison the state
+    const AdamState adam{J.raw,       J.act,        J.adam_m, J.adam_v, J.grad, adam_args(M, &J.adam, 0, &entry->it),
+                         J.dens_grad, J.dens_count, J.loss,   reinterpret_cast<WsStatus*>(J.raster_ws)};
     return rasterize_backward_impl(M, mean, scale, quat, rho, Vs, J.views, view_sel, &J.cam, &J.ropts, J.dimage,
                                    dmean, dscale, dquat, drho, J.raster_ws, J.raster_ws_bytes, stream,
                                    kRasterBwdChain, &adam);

@@ -245,7 +245,8 @@ __global__ void __launch_bounds__(kVoxThreads) k_vox_fwd(const float4* __restric
     __shared__ float4 s_r[kVoxThreads][4];
     __shared__ int s_last;
     const unsigned long long it = blockIdx.x;
-    if (it >= item_st->n_keys) return;
+    // no work items past the count; none at all after a list build that gave up a wait
+    if (it >= item_st->n_keys || st->status == R2G_E_TIMEOUT) return;
     const uint64_t item = items[it];
     const long long brick = (long long)(item >> 32);
     const uint32_t chunk = (uint32_t)item;
@@ -370,7 +371,8 @@ __global__ void __launch_bounds__(kVoxThreads) k_vox_bwd(const float4* __restric
     __shared__ int s_slice[kVoxGroup];        // slice stride of the volume
     __shared__ uint32_t s_ridx[kVoxGroup];    // record index g M + gid
     __shared__ uint32_t s_excl[kVoxGroup + 1];
-    const unsigned long long n_keys = st->n_keys;
+    // no entries after a list build that gave up a wait (the lists are not valid)
+    const unsigned long long n_keys = st->status == R2G_E_TIMEOUT ? 0ull : st->n_keys;
     const unsigned long long n_groups = (n_keys + kVoxGroup - 1) / kVoxGroup;
     const int j = threadIdx.x;
     for (unsigned long long grp = blockIdx.x; grp < n_groups; grp += gridDim.x) {

@@ -55,6 +55,8 @@ class Rasterizer:
             st, needed = r2g.r2g_poll(self.ws)
             if st == r2g.R2G_OK:
                 return image
+            if st != r2g.R2G_E_CAPACITY:
+                raise r2g.R2GError(st, "rasterize: " + r2g.last_error())
             self.capacity = int(needed * 1.25) + 1024
             self._alloc()
 
@@ -100,6 +102,8 @@ class Voxelizer:
             st, needed = r2g.r2g_poll(self.ws)
             if st == r2g.R2G_OK:
                 return vol
+            if st != r2g.R2G_E_CAPACITY:
+                raise r2g.R2GError(st, "voxelize: " + r2g.last_error())
             self.capacity = int(needed * 1.25) + 1024
             self._alloc()
 

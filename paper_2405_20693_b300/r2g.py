@@ -164,6 +164,7 @@ def lib():
             "r2g_tv3d_iso": (_I32, [_I32, _I32, _P, _F, _F, _P, _P, _P, _SZ, _P]),
             "r2g_adam_step": (_I32, [_I64, _P, _P, _P, _P, _P, _I32, _P, _P]),
             "r2g_poll": (_I32, [_P, _SZ, _P, _P]),
+            "r2g_set_wait_limit": (_I32, [ctypes.c_uint64]),
             "r2g_train_step": (_I32, [_P, _P, _P]),
             "r2g_train_step_host": (_I32, [_P, _P, _I64, _P, _P, _P, _P, _P]),
             "r2g_train_step_host_batch": (_I32, [_P, _P, _I64, _P, _P, _P, _P, _P, _P]),
@@ -220,6 +221,11 @@ def _stream(stream=None) -> int:
 def _check(status: int):
     if status != R2G_OK:
         raise R2GError(status, lib().r2g_last_error().decode())
+
+
+def last_error() -> str:
+    """The library's message for the last failure on this thread."""
+    return lib().r2g_last_error().decode()
 
 
 # ----------------------------------------------------------------------------- rasterizer
@@ -331,12 +337,18 @@ def r2g_pair_count(ws, stream=None) -> int:
 
 
 def r2g_poll(ws, stream=None) -> tuple[int, int]:
-    """(status, needed entries); does not raise on R2G_E_CAPACITY."""
+    """(status, needed entries); the device statuses (R2G_E_CAPACITY, R2G_E_TIMEOUT,
+    R2G_E_NUMERIC) are returned, not raised."""
     n = ctypes.c_int64(0)
     st = lib().r2g_poll(_ptr(ws), ws.numel(), _stream(stream), ctypes.byref(n))
-    if st not in (R2G_OK, R2G_E_CAPACITY):
+    if st not in (R2G_OK, R2G_E_CAPACITY, R2G_E_TIMEOUT, R2G_E_NUMERIC):
         _check(st)
     return int(st), int(n.value)
+
+
+def r2g_set_wait_limit(polls: int):
+    """Polls before a device-side wait gives up (0: the default)."""
+    _check(lib().r2g_set_wait_limit(ctypes.c_uint64(int(polls))))
 
 
 # ----------------------------------------------------------------------------- voxelizer

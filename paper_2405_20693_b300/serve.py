@@ -10,6 +10,18 @@ PSNR of its voxelized volume against the phantom reaches the target; its memory
 is released and waiting requests are admitted at the next round boundary.  The
 graph is recaptured whenever the resident set changes.
 
+Faults are handled on the host, per request, without disturbing the others:
+  * a request whose footprint exceeds the whole HBM budget, or whose scan cannot be
+    built because the device runs out of memory, is refused ("refused");
+  * a cancellation (run(..., cancellations=[(time, rid)])) drops a queued request or
+    retires a resident one at the next round boundary ("cancelled");
+  * a scan whose training loss turns non-finite (a NaN or inf in its measured
+    projections, say) is quarantined ("numeric"): the library's step already left
+    its parameters untouched (R2G_E_NUMERIC), and the server retires it after the
+    round in which it happened.
+The other resident scans run on unchanged: each scan's choices come from its own
+seeded generator, so its result does not depend on the mix.
+
 Reported per request: arrival, admission and completion times (seconds on the
 run clock), iterations, final PSNR; overall: p50/p99 time-to-volume and
 scans/hour.
@@ -45,7 +57,7 @@ class Result:
     finished: float
     iters: int
     psnr: float
-    reason: str                   # "target" or "iterations"
+    reason: str                   # "target", "iterations", "cancelled", "refused" or "numeric"
 
     @property
     def time_to_volume(self) -> float:
@@ -109,31 +121,68 @@ class Server:
         a = torch.zeros(256, dtype=torch.float32, device=self.device)
         float(torch.mean((a - a) ** 2))
 
-    def run(self, requests):
+    def run(self, requests, cancellations=()):
+        """Serve the requests; cancellations: (time in seconds on the run clock,
+        request id) pairs, applied at the first round boundary at or after the time."""
         pending = sorted(requests, key=lambda r: r.arrival)
+        cancels = sorted(cancellations)
         queue, active, results = [], {}, []
         used = 0
         trainer, dirty = None, True
         self.warm()
         t0 = time.perf_counter()
+
+        def refuse(req, reason):
+            t = time.perf_counter() - t0
+            results.append(Result(req.rid, req.arrival, t, t, 0, float("nan"), reason))
+
         while pending or queue or active:
             now = time.perf_counter() - t0
             while pending and pending[0].arrival <= now:
                 queue.append(pending.pop(0))
+            # cancellations due: drop a queued request, retire a resident one
+            while cancels and cancels[0][0] <= now:
+                _, rid = cancels.pop(0)
+                for q in [q for q in queue if q.rid == rid]:
+                    queue.remove(q)
+                    refuse(q, "cancelled")
+                for q in [q for q in pending if q.rid == rid]:
+                    pending.remove(q)
+                    refuse(q, "cancelled")
+                if rid in active:
+                    a = active.pop(rid)
+                    t = time.perf_counter() - t0
+                    results.append(Result(rid, a["req"].arrival, a["admitted"], t, a["scan"].it, float("nan"),
+                                          "cancelled"))
+                    used -= a["bytes"]
+                    dirty = True
             # admission at a round boundary, first come first served, by HBM footprint
             while queue:
                 need = footprint_estimate(queue[0].spec, self.D)
-                if used + need > self.budget and active:
+                if need > self.budget:  # can never fit: refused at once, the queue moves on
+                    refuse(queue.pop(0), "refused")
+                    continue
+                if used + need > self.budget:
                     break
                 req = queue.pop(0)
-                sc, gt, vox = self._build(req)
+                try:
+                    sc, gt, vox = self._build(req)
+                except torch.cuda.OutOfMemoryError:
+                    torch.cuda.empty_cache()
+                    refuse(req, "refused")
+                    continue
                 active[req.rid] = dict(req=req, scan=sc, gt=gt, vox=vox, admitted=time.perf_counter() - t0,
                                        bytes=need)
                 used += need
                 dirty = True
             if not active:
                 if pending:
-                    time.sleep(max(0.0, pending[0].arrival - (time.perf_counter() - t0)))
+                    nxt = pending[0].arrival
+                    if cancels:
+                        nxt = min(nxt, cancels[0][0])
+                    time.sleep(max(0.0, nxt - (time.perf_counter() - t0)))
+                elif cancels and not queue:
+                    cancels = []
                 continue
             self.max_active = max(self.max_active, len(active))
             if dirty:
@@ -143,8 +192,16 @@ class Server:
             trainer.round()
             self.rounds += 1
             done = []
+            # quarantine: a scan whose step loss is not finite (its parameters were left as
+            # they were by the step) leaves after this round
+            losses = trainer.losses()
+            for j, (rid, a) in enumerate(active.items()):
+                if not np.all(np.isfinite(losses[j])):
+                    done.append((rid, "numeric"))
             for rid, a in active.items():
                 sc, req = a["scan"], a["req"]
+                if any(rid == d[0] for d in done):
+                    continue
                 if sc.it >= req.max_iters:
                     done.append((rid, "iterations"))
                 elif sc.it % req.check_every == 0:
@@ -156,7 +213,7 @@ class Server:
                 t = time.perf_counter() - t0
                 for rid, reason in done:
                     a = active.pop(rid)
-                    p = self.psnr(a["scan"], a["gt"], a["vox"])
+                    p = self.psnr(a["scan"], a["gt"], a["vox"]) if reason != "numeric" else float("nan")
                     results.append(Result(rid, a["req"].arrival, a["admitted"], t, a["scan"].it, p, reason))
                     if self.keep_volumes:
                         self.volumes[rid] = self.volume(a["scan"], a["vox"]).cpu().numpy()
@@ -167,8 +224,12 @@ class Server:
 
 
 def summarize(results, wall_s: float):
-    ttv = np.array([r.time_to_volume for r in results])
-    return {"requests": len(results), "p50_time_to_volume_s": float(np.percentile(ttv, 50)),
+    """p50/p99 time-to-volume and scans/hour over the requests that produced a volume
+    (retired at the target or the iteration cap); the other outcomes are counted."""
+    ok = [r for r in results if r.reason in ("target", "iterations")]
+    ttv = np.array([r.time_to_volume for r in ok]) if ok else np.zeros(1)
+    return {"requests": len(results), "completed": len(ok), "p50_time_to_volume_s": float(np.percentile(ttv, 50)),
             "p99_time_to_volume_s": float(np.percentile(ttv, 99)),
-            "scans_per_hour": len(results) * 3600.0 / wall_s, "wall_s": wall_s,
-            "reasons": {k: sum(r.reason == k for r in results) for k in ("target", "iterations")}}
+            "scans_per_hour": len(ok) * 3600.0 / wall_s, "wall_s": wall_s,
+            "reasons": {k: sum(r.reason == k for r in results)
+                        for k in ("target", "iterations", "cancelled", "refused", "numeric")}}

@@ -33,10 +33,24 @@ def entry_table(rows):
 def check_step_against_oracle(sc, act_before, raw_before, views, meas, cam, patch_gds, label):
     """The step just taken on sc (from a fresh state) against the oracle: projection
     loss of `views` vs `meas`, the summed TV of the patches, and Adam's first moment
-    against the oracle's adjoints chained through the activations."""
+    against the oracle's adjoints chained through the activations.
+
+    Gate band through the loss: a pixel where some Gaussian's q lies within 1e-4 Q of
+    the gate may hold that Gaussian's e^{-Q/2} rho_hat on the GPU and not in the oracle
+    (the image tolerance widens by exactly that), and the loss gradient dL/dI around
+    it -- through the 11 x 11 SSIM window and the L1 sign -- then differs for every
+    Gaussian that covers the window.  The oracle measures that effect by evaluating
+    dL/dI at its image plus and minus the band image and chaining both differences
+    through its adjoint; their magnitudes widen each element's tolerance beside the
+    pair's own band."""
     Ga = I.GaussianSet(act_before[1], act_before[2], act_before[0], act_before[3])
-    img, _ = core.render(Ga, views, cam, Q=engine.Q_PIXEL)
+    img, _, iband = core.render(Ga, views, cam, Q=engine.Q_PIXEL, want_band=True)
     L1, dimg = losses.projection_loss(img, meas, engine.LAMBDA_SSIM)
+    prop = [np.zeros_like(x) for x in (Ga.mean, Ga.scale, Ga.quat, Ga.rho)]
+    for sgn in (1.0, -1.0):
+        _, d2 = losses.projection_loss(img + sgn * iband, meas, engine.LAMBDA_SSIM)
+        for acc, gg in zip(prop, core.render_backward(Ga, views, cam, d2 - dimg, Q=engine.Q_PIXEL)):
+            acc += np.abs(gg)
     vols, _ = core.voxelize(Ga, patch_gds, engine.Q_VOXEL)
     D = int(patch_gds[0, 6])
     Ltv, dvol = 0.0, []
@@ -52,7 +66,8 @@ def check_step_against_oracle(sc, act_before, raw_before, views, meas, cam, patc
     sig = 1.0 / (1.0 + np.exp(-raw_before[3].astype(np.float64)))
     chain = {"quat": 1.0, "mean": 1.0, "scale": act_before[2], "rho": sig}
     ref = {"mean": gr[0] + gv[0], "scale": gr[1] + gv[1], "quat": gr[2] + gv[2], "rho": gr[3] + gv[3]}
-    band = {"mean": br[0] + bv[0], "scale": br[1] + bv[1], "quat": br[2] + bv[2], "rho": br[3] + bv[3]}
+    band = {"mean": br[0] + bv[0] + prop[0], "scale": br[1] + bv[1] + prop[1], "quat": br[2] + bv[2] + prop[2],
+            "rho": br[3] + bv[3] + prop[3]}
     mq, mm, ms, mr = (host(t) / 0.1 for t in sc.state.views_of(sc.state.m))
     for name, got in (("quat", mq), ("mean", mm), ("scale", ms), ("rho", mr)):
         want = ref[name] * chain[name]

@@ -74,8 +74,14 @@ def scale_fd():
     for j, k in enumerate(ks):
         kind = (3, 0, 1, 2)[j % 4]
         comp = 0 if kind == 3 else int(gs.integers(0, 4 if kind == 2 else 3))
-        s_min = float(Gd.scale[k].min())
-        eps = {3: EPS * float(Gd.rho[k]), 0: EPS * s_min, 1: EPS * float(Gd.scale[k, comp]), 2: EPS}[kind]
+        if kind == 3:
+            eps = EPS * float(Gd.rho[k])
+        elif kind == 0:
+            eps = EPS * float(Gd.scale[k].min())
+        elif kind == 1:
+            eps = EPS * float(Gd.scale[k, comp])
+        else:
+            eps = EPS
         params.append((k, kind, comp, eps))
     fd = OracleLossFD(Gd, views.astype(np.float64), cam, meas.astype(np.float64), patch_gds)
     ref = [fd.grad(k, kind, comp, eps) for (k, kind, comp, eps) in params]

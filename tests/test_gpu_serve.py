@@ -72,3 +72,84 @@ def test_admission_respects_the_hbm_budget():
     # first come first served: request 1 is admitted before request 2
     adm = {r.rid: r.admitted for r in res}
     assert adm[0] <= adm[1] <= adm[2] <= adm[3]
+
+
+def test_host_faults_leave_the_other_requests_alone():
+    """Faults injected on the host: request 1 is cancelled while resident, request 3
+    asks for more than the whole HBM budget and is refused at once, request 2's
+    measured projections carry a NaN (its first step's loss is not finite: the step
+    leaves its parameters as they were and the server quarantines it).  Requests 0
+    and 4 finish as they do with no fault at all (same iterations, volumes within the
+    tolerance of the alone-vs-mix check: the float-atomic gradients differ between
+    any two runs in their last bits)."""
+    sp = specs() + [I.ScanSpec(304, 2500, 5, 64, 64)]
+    big = I.ScanSpec(305, 4_000_000, 75, 512, 256)
+    budget = sum(serve.footprint_estimate(s, 16) for s in sp) + (1 << 20)
+    assert serve.footprint_estimate(big, 16) > budget
+
+    def run(faults):
+        reqs = []
+        for k, s in enumerate(sp):
+            spec = big if (faults and k == 3) else s
+            data = None
+            if faults and k == 2:
+                G, cam, views, meas, vol = I.make_scan(s, device="cuda")
+                meas = meas.copy()
+                meas[:, 5, 7] = np.nan  # a corrupt detector pixel in every view
+                data = (G, cam, views, meas, vol)
+            reqs.append(serve.Request(k, spec, arrival=0.0, max_iters=12, psnr_target=99.0, check_every=4, data=data))
+        srv = serve.Server(hbm_budget_bytes=budget, D=16, keep_volumes=True)
+        res = srv.run(reqs, cancellations=[(0.0, 1)] if faults else ())
+        return {r.rid: r for r in res}, srv
+
+    clean, srv_c = run(False)
+    faulty, srv_f = run(True)
+    assert faulty[1].reason == "cancelled" and faulty[3].reason == "refused" and faulty[3].iters == 0
+    assert faulty[2].reason == "numeric" and faulty[2].iters >= 1
+    for rid in (0, 4):
+        assert faulty[rid].reason == clean[rid].reason == "iterations" and faulty[rid].iters == clean[rid].iters
+        a, b = srv_c.volumes[rid], srv_f.volumes[rid]
+        assert np.abs(a - b).max() <= 1e-3 * np.abs(a).max(), rid
+    s = serve.summarize(list(faulty.values()), srv_f.wall)
+    assert s["reasons"]["cancelled"] == 1 and s["reasons"]["refused"] == 1 and s["reasons"]["numeric"] == 1
+    assert s["completed"] == 2
+
+
+def test_nonfinite_loss_leaves_the_state_and_reports_numeric():
+    """A training step whose projection loss is NaN (a NaN pixel in the measured view)
+    takes no update: parameters and both Adam moments stay bit for bit as they were,
+    and the raster workspace's status reads R2G_E_NUMERIC; the next step on a clean
+    view updates as usual and reports R2G_OK."""
+    G, cam, views, meas, _ = I.make_scan(specs()[0], device="cuda")
+    meas = meas.copy()
+    meas[2, 10, 11] = np.nan
+    sc = engine.Scan(G, views, meas, cam, n_out=64, D=16)
+    before = [t.clone() for t in (sc.state.raw, sc.state.act, sc.state.m, sc.state.v)]
+    t = np.zeros((2, 8), np.int32)
+    t[0, 0], t[1, 0], t[1, 1] = 2, 3, 1
+    tab = torch.as_tensor(t, device="cuda")
+    r2g.r2g_train_step(sc.job, tab[0].data_ptr(), torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    assert not np.isfinite(sc.loss.cpu().numpy()[0])
+    assert r2g.r2g_poll(sc.rast.ws)[0] == r2g.R2G_E_NUMERIC
+    assert all(torch.equal(a, b) for a, b in zip(before, (sc.state.raw, sc.state.act, sc.state.m, sc.state.v)))
+    r2g.r2g_train_step(sc.job, tab[1].data_ptr(), torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    assert np.all(np.isfinite(sc.loss.cpu().numpy()))
+    assert r2g.r2g_poll(sc.rast.ws)[0] == r2g.R2G_OK
+    assert not torch.equal(before[0], sc.state.raw)
+
+
+def test_footprint_estimate_covers_the_allocation():
+    """The admission estimate is at least what building a scan allocates on the device
+    (torch.cuda.memory_allocated before and after), and not more than twice it."""
+    for s in specs():
+        data = I.make_scan(s, device="cuda")
+        torch.cuda.synchronize()
+        a0 = torch.cuda.memory_allocated()
+        sc = engine.Scan(*data[:4], n_out=s.n_out, D=16, seed=s.seed)
+        torch.cuda.synchronize()
+        used = torch.cuda.memory_allocated() - a0
+        est = serve.footprint_estimate(s, 16)
+        assert used <= est <= 2 * used, (s, used, est)
+        del sc
