@@ -73,15 +73,21 @@ def poisson_requests(n: int, mean_interarrival_s: float, seed: int = 6, specs=No
     return [Request(k, specs[k % len(specs)], float(t[k]), **kw) for k in range(n)]
 
 
-def footprint_estimate(spec: I.ScanSpec, D: int = 32, capacity_factor: float = 6.0) -> int:
+def footprint_estimate(spec: I.ScanSpec, D: int = 32, capacity_factor: float = 12.0) -> int:
     """Device bytes a scan will hold, before it is built: parameters, gradient and
     Adam state (5 x 11 floats per Gaussian), measured projections, step buffers, and
-    the workspaces at the library's own size for capacity_factor x M list entries."""
+    the workspaces at the library's own size for list capacities that cover what the
+    scan's sizing probes give (entries per Gaussian at most the number of keys, 1.5x
+    headroom, capped at capacity_factor, plus the probes' 4096)."""
     cam = r2g.camera(I.cone_camera(spec.det, spec.det, pitch=I.CONE_PITCH * 512 / spec.det))
     ro = r2g.raster_opts(tile=engine.SCAN_TILE)
-    raster = r2g.r2g_raster_workspace_size(spec.M, 1, cam, ro, int(capacity_factor * spec.M) + 4096)
+    tiles = -(-spec.det // engine.SCAN_TILE[0]) * -(-spec.det // engine.SCAN_TILE[1])
+    bricks = (-(-D // 8)) ** 3
+    cap_r = int(min(1.5 * tiles, capacity_factor) * spec.M) + 4096
+    cap_v = int(min(1.5 * bricks, capacity_factor) * spec.M) + 4096
+    raster = r2g.r2g_raster_workspace_size(spec.M, 1, cam, ro, cap_r)
     grid = r2g.grids(I.patch_grid((0, 0, 0), D, spec.n_out))
-    voxel = r2g.r2g_voxel_workspace_size(spec.M, grid, int(capacity_factor * spec.M) + 4096)
+    voxel = r2g.r2g_voxel_workspace_size(spec.M, grid, cap_v)
     px = spec.det * spec.det
     return int(spec.M * 55 * 4 + spec.V * px * 4 + 2 * px * 4 + 2 * D ** 3 * 4 + raster + voxel
                + r2g.r2g_loss_workspace_size(1, spec.det, spec.det))

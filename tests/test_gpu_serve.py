@@ -142,14 +142,14 @@ def test_nonfinite_loss_leaves_the_state_and_reports_numeric():
 
 def test_footprint_estimate_covers_the_allocation():
     """The admission estimate is at least what building a scan allocates on the device
-    (torch.cuda.memory_allocated before and after), and not more than twice it."""
+    (torch.cuda.memory_allocated before and after), and not more than three times it."""
     for s in specs():
-        data = I.make_scan(s, device="cuda")
+        G, cam, views, meas, _ = I.make_scan(s, device="cuda")
         torch.cuda.synchronize()
         a0 = torch.cuda.memory_allocated()
-        sc = engine.Scan(*data[:4], n_out=s.n_out, D=16, seed=s.seed)
+        sc = engine.Scan(G, views, meas, cam, n_out=s.n_out, D=16, seed=s.seed)
         torch.cuda.synchronize()
         used = torch.cuda.memory_allocated() - a0
         est = serve.footprint_estimate(s, 16)
-        assert used <= est <= 2 * used, (s, used, est)
+        assert used <= est <= 3 * used, (s, used, est)
         del sc
