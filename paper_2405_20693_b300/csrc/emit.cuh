@@ -706,4 +706,338 @@ uint64_t* build_lists(const Op& op, long long n_rec, long long n_slots, unsigned
     return sorted;
 }
 
+// ---------------------------------------------------------------- view-segmented lists
+//
+// A key space of several views (key = view x kpv + key within the view, kpv <=
+// kFusedKeys) whose records are numbered view-major (r = v M + i): the emission, in
+// record order, leaves the entries grouped by view, so a stable order by key only
+// has to order each view's entries by their key within the view.  Each emission
+// block covers a contiguous range of records and so at most a few views: it counts
+// its entries per key of those views (its local keys, at most kSegLocalMax) into
+// its row of `hist`; one CTA scans the key totals into each key's first entry, its
+// range, its work items (every key gets at least one, an empty key's item writes
+// zeros) and cleared arrival counters; the offset of (key, block) is the key's first
+// entry plus the key's entries in the earlier blocks of its view (a handful); a
+// stable scatter (one contiguous run per warp, ranked with warp match masks) writes
+// the sorted entries -- one pass over them, where a radix sort of the full keys
+// takes two or three.
+
+constexpr int kSegLocalMax = 2 * kFusedKeys;  // local keys of one emission block
+constexpr int kSegKeysThreads = 1024;
+
+struct SegKeys {
+    long long M;          // records per view
+    long long per_block;  // records per emission block
+    int kpv;              // keys per view
+    int lmax;             // row length of hist / offs (>= every block's local keys)
+    int n_keys;           // keys in all
+};
+
+// First key and number of local keys of emission block b (0 keys past the records).
+__host__ __device__ __forceinline__ void seg_block_keys(const SegKeys& sk, long long n_rec, long long b, int& key_lo,
+                                                        int& nloc) {
+    const long long r0 = b * sk.per_block;
+    const long long r1 = (r0 + sk.per_block < n_rec ? r0 + sk.per_block : n_rec) - 1;
+    if (r0 > r1) {
+        key_lo = 0;
+        nloc = 0;
+        return;
+    }
+    const long long v0 = r0 / sk.M, v1 = r1 / sk.M;
+    key_lo = (int)(v0 * sk.kpv);
+    nloc = (int)((v1 - v0 + 1) * sk.kpv);
+}
+
+// Emission of block blockIdx.x (as emit_block) with the block's entries counted per
+// local key into hist_row and added to key_totals.
+template <class Op>
+__global__ void __launch_bounds__(256) k_emit_seg(Op op, long long n_rec, const unsigned long long* partials,
+                                                  uint64_t* __restrict__ out, unsigned long long capacity,
+                                                  uint32_t* __restrict__ hist, uint32_t* __restrict__ key_totals,
+                                                  SegKeys sk) {
+    __shared__ uint32_t h[kSegLocalMax];
+    __shared__ uint4 s_info[256];
+    __shared__ uint32_t s_ex[256];
+    __shared__ uint32_t sm8[8];
+    int key_lo, nloc;
+    seg_block_keys(sk, n_rec, blockIdx.x, key_lo, nloc);
+    for (int k = threadIdx.x; k < nloc; k += 256) h[k] = 0;
+    __syncthreads();
+    const long long begin = min(n_rec, (long long)blockIdx.x * sk.per_block);
+    const long long end = min(n_rec, begin + sk.per_block);
+    unsigned long long running = partials[blockIdx.x];
+    for (long long base = begin; base < end; base += 256) {
+        const long long r = base + threadIdx.x;
+        uint32_t c = 0;
+        uint4 inf = make_uint4(0u, 0u, 0u, 0u);
+        if (r < end) {
+            c = op.count(r);
+            inf = op.info(r);
+        }
+        uint32_t tot;
+        const uint32_t ex = block_exclusive_scan_256(c, sm8, &tot);
+        s_info[threadIdx.x] = inf;
+        s_ex[threadIdx.x] = ex;
+        __syncthreads();
+        for (uint32_t e = threadIdx.x; e < tot; e += 256) {
+            int lo = 0, hi = 255;  // the record holding entry e: the last k with ex_k <= e
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_ex[mid] <= e) lo = mid;
+                else hi = mid - 1;
+            }
+            const uint4 ri = s_info[lo];
+            const uint32_t key = op.key(ri, e - s_ex[lo]);
+            const unsigned long long off = running + e;
+            if (off < capacity) {
+                out[off] = ((uint64_t)key << 32) | (uint64_t)ri.w;
+                atomicAdd(&h[key - (uint32_t)key_lo], 1u);
+            }
+        }
+        __syncthreads();
+        running += tot;
+    }
+    uint32_t* row = hist + (size_t)blockIdx.x * sk.lmax;
+    for (int k = threadIdx.x; k < nloc; k += 256) {
+        const uint32_t cnt = h[k];
+        row[k] = cnt;
+        if (cnt) atomicAdd(&key_totals[key_lo + k], cnt);
+    }
+}
+
+// Block-wide exclusive scan of one uint32 per thread for a 1024-thread block.
+__device__ __forceinline__ uint32_t block_excl_scan_1024(uint32_t v, uint32_t* s32, uint32_t* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s32[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = s32[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        s32[lane] = w;  // inclusive over warps
+    }
+    __syncthreads();
+    *total = s32[31];
+    const uint32_t before = (warp > 0 ? s32[warp - 1] : 0u) + x - v;
+    __syncthreads();
+    return before;
+}
+
+// One CTA per view (kpv <= kSegKeysThreads keys, one per thread): the view's key
+// totals -> each key's first entry (key_first), range, first work item,
+// items, and cleared arrival counters.  The view's first entry and first item are the
+// sums over the earlier views' keys, which each CTA forms itself; the last view's CTA
+// writes the item count into item_st.
+static __global__ void __launch_bounds__(kSegKeysThreads) k_seg_keys(const uint32_t* __restrict__ key_totals,
+                                                                     uint32_t* __restrict__ key_first, int kpv,
+                                                                     FusedKeys fk) {
+    __shared__ uint32_t s32[32];
+    const int v = blockIdx.x, t = threadIdx.x;
+    const uint32_t chunk = fk.chunk;
+    uint32_t before = 0, ibefore = 0;  // this thread's share of the earlier views' entries and items
+    for (int u = 0; u < v; ++u)
+        if (t < kpv) {
+            const uint32_t x = __ldcg(key_totals + (size_t)u * kpv + t);
+            before += x;
+            ibefore += x ? (x + chunk - 1) / chunk : 1u;
+        }
+    uint32_t vb, vib;
+    block_excl_scan_1024(before, s32, &vb);
+    block_excl_scan_1024(ibefore, s32, &vib);
+    const int k = v * kpv + t;
+    const uint32_t tk = t < kpv ? __ldcg(key_totals + k) : 0u;
+    const uint32_t nc = t < kpv ? (tk ? (tk + chunk - 1) / chunk : 1u) : 0u;
+    uint32_t vt, vit;
+    const uint32_t base = vb + block_excl_scan_1024(tk, s32, &vt);
+    const uint32_t ibase = vib + block_excl_scan_1024(nc, s32, &vit);
+    if (t < kpv) {
+        key_first[k] = base;
+        fk.ranges[k] = tk ? make_uint2(base, base + tk) : make_uint2(0u, 0u);
+        fk.item_off[k] = ibase;
+        const int kd = fk.kd_per_key > 0 ? fk.kd_per_key : 1;
+        for (int w = 0; w < kd; ++w) fk.key_done[(size_t)k * kd + w] = 0;
+        for (uint32_t c = 0; c < nc; ++c)
+            if (ibase + c < fk.items_cap) fk.items[ibase + c] = ((uint64_t)(uint32_t)k << 32) | c;
+    }
+    if (v == (int)gridDim.x - 1 && t == 0) fk.item_st->n_keys = vib + vit;
+}
+
+// offs[b][j] = first entry of block b's local key j: the key's first entry plus its
+// entries in the earlier blocks of its view.
+static __global__ void __launch_bounds__(256) k_seg_offsets(const uint32_t* __restrict__ hist,
+                                                     const uint32_t* __restrict__ key_first,
+                                                     uint32_t* __restrict__ offs, long long n_rec, int nb,
+                                                     SegKeys sk) {
+    const long long t = (long long)blockIdx.x * 256 + threadIdx.x;
+    const long long b = t / sk.lmax;
+    const int j = (int)(t - b * sk.lmax);
+    if (b >= nb) return;
+    int key_lo, nloc;
+    seg_block_keys(sk, n_rec, b, key_lo, nloc);
+    if (j >= nloc) return;
+    const int k = key_lo + j;
+    const long long v = k / sk.kpv;
+    uint32_t run = key_first[k];
+    for (long long bb = (v * sk.M) / sk.per_block; bb < b; ++bb) {
+        int lo2, n2;
+        seg_block_keys(sk, n_rec, bb, lo2, n2);
+        run += hist[(size_t)bb * sk.lmax + (k - lo2)];
+    }
+    offs[(size_t)b * sk.lmax + j] = run;
+}
+
+// Block b's entries [start_b, start_{b+1}) (clipped to the written count) to their
+// sorted positions: as scatter_block, with the block's local keys.  Dynamic shared
+// memory: 8 x lmax words.
+template <class Op>
+__global__ void __launch_bounds__(256) k_seg_scatter(Op op, const uint64_t* __restrict__ in,
+                                                     uint64_t* __restrict__ out, const uint32_t* __restrict__ offs,
+                                                     const unsigned long long* __restrict__ starts,
+                                                     const WsStatus* __restrict__ st, long long n_rec, SegKeys sk) {
+    extern __shared__ uint32_t s_dyn[];
+    const int b = blockIdx.x, nb = gridDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int key_lo, nloc;
+    seg_block_keys(sk, n_rec, b, key_lo, nloc);
+    uint32_t* s_h = s_dyn;  // [8][lmax]
+    const unsigned long long n_written = st->n_keys;
+    const unsigned long long lo = min(starts[b], n_written);
+    const unsigned long long hi = (b + 1 < nb) ? min(starts[b + 1], n_written) : n_written;
+    const unsigned long long per = (hi - lo + 7) / 8;
+    const unsigned long long wlo = min(hi, lo + warp * per), whi = min(hi, wlo + per);
+    for (int k = tid; k < nloc; k += 256)
+#pragma unroll
+        for (int w = 0; w < 8; ++w) s_h[w * sk.lmax + k] = 0;
+    __syncthreads();
+    constexpr int R = 8;  // entries per lane loaded at once
+    for (unsigned long long b0 = wlo; b0 < whi; b0 += 32 * R) {
+        uint32_t k[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const unsigned long long i = b0 + q * 32 + lane;
+            k[q] = i < whi ? (uint32_t)(in[i] >> 32) - (uint32_t)key_lo : 0xffffffffu;
+        }
+#pragma unroll
+        for (int q = 0; q < R; ++q)
+            if (k[q] != 0xffffffffu) atomicAdd(&s_h[warp * sk.lmax + k[q]], 1u);
+    }
+    __syncthreads();
+    const uint32_t* orow = offs + (size_t)b * sk.lmax;
+    for (int k = tid; k < nloc; k += 256) {
+        uint32_t run = __ldg(orow + k);
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+            const uint32_t c = s_h[w * sk.lmax + k];
+            s_h[w * sk.lmax + k] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    const uint32_t lt = (1u << lane) - 1u;
+    for (unsigned long long b0 = wlo; b0 < whi; b0 += 32 * R) {
+        uint64_t x[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const unsigned long long i = b0 + q * 32 + lane;
+            x[q] = i < whi ? in[i] : ~0ull;
+        }
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const bool valid = b0 + q * 32 + lane < whi;
+            const uint32_t k = valid ? (uint32_t)(x[q] >> 32) - (uint32_t)key_lo : 0xffffffffu;
+            const uint32_t peers = __match_any_sync(0xffffffffu, k);
+            const uint32_t rank = __popc(peers & lt);
+            const uint32_t pos = valid ? s_h[warp * sk.lmax + k] + rank : 0u;
+            __syncwarp();
+            if (valid && rank == 0) s_h[warp * sk.lmax + k] += __popc(peers);
+            __syncwarp();
+            if (valid) {
+                out[pos] = x[q];
+                op.copy_rec(x[q], pos);  // the entry's record next to it (Op's choice)
+            }
+        }
+    }
+}
+
+// The segmented layout of n_rec records, M per view, kpv keys per view, for the
+// emission blocking of list_blocking(n_rec); lmax = 0 when it does not apply (the key
+// space is fused, or a block could span more than kSegLocalMax local keys).
+inline SegKeys seg_keys(long long n_slots, long long M, long long n_rec, int kpv) {
+    SegKeys sk{M, 0, kpv, 0, (int)n_slots};
+    if (fused_lists(n_slots) || kpv < 1 || kpv > kFusedKeys || M < 1 || n_rec % M != 0 ||
+        n_slots != (n_rec / M) * kpv)
+        return sk;
+    const ListBlocking lb = list_blocking(n_rec);
+    sk.per_block = 256ll * lb.per_thread;
+    long long span = (sk.per_block + M - 1) / M + 1;  // views one block can meet
+    if (span > n_rec / M) span = n_rec / M;
+    if (span * kpv > kSegLocalMax) return sk;
+    sk.lmax = (int)(span * kpv);
+    return sk;
+}
+inline bool seg_lists(const SegKeys& sk) { return sk.lmax > 0; }
+
+// Scratch words of the segmented build: hist and offs rows for every emission block,
+// the key totals and the keys' first entries.
+inline size_t seg_scratch_words(const SegKeys& sk) {
+    return seg_lists(sk) ? 2 * (size_t)kMaxListBlocks * sk.lmax + 2 * (size_t)sk.n_keys : 0;
+}
+inline uint32_t* seg_key_totals(uint32_t* seg_scratch, const SegKeys& sk) {
+    return seg_scratch + 2 * (size_t)kMaxListBlocks * sk.lmax;
+}
+
+// The count the projection kernel of a segmented build must make (it also clears the
+// key totals).
+inline ListCount seg_list_count(const SegKeys& sk, unsigned long long* partials, WsStatus* st, long long cap,
+                                uint32_t* seg_scratch) {
+    return ListCount{partials, st, (unsigned long long)cap, seg_key_totals(seg_scratch, sk), sk.n_keys};
+}
+
+// After the projection kernel (launched with list_blocking(n_rec) and seg_list_count):
+// emission with per-block local counts, key scan, offsets and stable scatter from a
+// into b (returned); every key gets a range, cleared arrival counters and at least one
+// work item.  Adds the launches to *launches.
+template <class Op>
+uint64_t* build_lists_seg(const Op& op, long long n_rec, const SegKeys& sk, const unsigned long long* partials,
+                          WsStatus* st, uint64_t* a, uint64_t* b, long long cap, uint32_t* seg_scratch, uint2* ranges,
+                          uint32_t* key_done, WsStatus* item_st, uint32_t* item_off, uint64_t* items,
+                          long long items_cap, int chunk, int kd_per_key, ListProf prof, cudaStream_t s,
+                          int* launches) {
+    const ListBlocking lb = list_blocking(n_rec);
+    uint32_t* hist = seg_scratch;
+    uint32_t* offs = seg_scratch + (size_t)kMaxListBlocks * sk.lmax;
+    uint32_t* totals = seg_key_totals(seg_scratch, sk);
+    prof_begin(prof.emit, s);
+    k_emit_seg<Op><<<lb.blocks, 256, 0, s>>>(op, n_rec, partials, a, (unsigned long long)cap, hist, totals, sk);
+    prof_end(prof.emit, s);
+    prof_begin(prof.sort, s);
+    const FusedKeys fk{(uint32_t)chunk, ranges,     key_done,    item_off, items, (unsigned long long)items_cap,
+                       item_st,         kd_per_key, wait_polls()};
+    uint32_t* first = totals + sk.n_keys;
+    k_seg_keys<<<(unsigned)(sk.n_keys / sk.kpv), kSegKeysThreads, 0, s>>>(totals, first, sk.kpv, fk);
+    const long long n_off = (long long)lb.blocks * sk.lmax;
+    k_seg_offsets<<<(unsigned)((n_off + 255) / 256), 256, 0, s>>>(hist, first, offs, n_rec, lb.blocks, sk);
+    const size_t smem = 8 * sizeof(uint32_t) * (size_t)sk.lmax;
+    static bool attr_set[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+        cudaFuncSetAttribute(k_seg_scatter<Op>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(8 * sizeof(uint32_t) * kSegLocalMax));
+        attr_set[dev] = true;
+    }
+    k_seg_scatter<Op><<<lb.blocks, 256, smem, s>>>(op, a, b, offs, partials, st, n_rec, sk);
+    prof_end(prof.sort, s);
+    *launches += 4;
+    return b;
+}
+
 }  // namespace r2g

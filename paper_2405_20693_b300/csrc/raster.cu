@@ -803,13 +803,13 @@ __global__ void __launch_bounds__(128) k_project_bwd(Params G, const float* __re
     if (ADAM) adam_prefetch_state(adam, i, pre);
     pdl_wait();  // the backward moments, and the gradient already in adam.grad
     if (ADAM) {
+        adam_prefetch_grad(adam, i, pre);  // issued first: its loads overlap the loss check's
         // a non-finite loss: no update anywhere (every thread sees the same losses); the
         // moments stay in their slots, and the next forward clears them
         if (!adam_loss_ok(adam)) {
             if (i == 0) atomicExch(&adam.guard_status->status, (int32_t)R2G_E_NUMERIC);
             return;
         }
-        adam_prefetch_grad(adam, i, pre);
     }
     float gp[3] = {0.f, 0.f, 0.f}, gs[3] = {0.f, 0.f, 0.f}, gR[3][3] = {{0.f}}, grho = 0.f;
     float dens_g = 0.f, dens_n = 0.f;  // adaptive-control statistics of this call
@@ -983,10 +983,17 @@ __global__ void __launch_bounds__(256) k_mean_mu(Params G, const float* __restri
 // ------------------------------------------------------------------ host side
 
 struct RasterLayout {
-    size_t status, rec, rect, partials, ranges, key_done, mom, scratch, item_status, item_off, fixed;
+    size_t status, rec, rect, partials, ranges, key_done, mom, scratch, item_status, item_off, seg, fixed;
     int tiles_x, tiles_y, tiles_per_view;
     long long n_tiles, n_rec;
+    SegKeys sk;  // the view-segmented list build, when it applies (several views, > kFusedKeys tiles)
 };
+
+// Whether the sorted entries carry their splat records (srec): the fused list build
+// copies them during its scatter.  (The view-segmented build does not: at 75 views x
+// 500k Gaussians the 32-byte gathers and scattered writes of the copy cost its scatter
+// 4 ms for 0.7 ms saved in the forward splat.)
+inline bool has_srec(const RasterLayout& L) { return fused_lists(L.n_tiles); }
 
 bool valid_tile(int tw, int th) {
     return (tw == 16 && th == 16) || (tw == 8 && th == 8) || (tw == 32 && th == 8) || (tw == 32 && th == 32);
@@ -1030,6 +1037,8 @@ RasterLayout raster_layout(int64_t M, int32_t V, const r2g_camera* cam, const r2
     L.mom = lay.take(32 * (size_t)L.n_rec);
     L.scratch = lay.take(sort_scratch_bytes());
     L.item_off = lay.take(4 * (size_t)L.n_tiles);
+    L.sk = seg_keys(L.n_tiles, M, L.n_rec, L.tiles_per_view);
+    L.seg = seg_lists(L.sk) ? lay.take(4 * seg_scratch_words(L.sk)) : 0;
     L.fixed = lay.off;
     return L;
 }
@@ -1050,7 +1059,7 @@ Tail raster_tail(const RasterLayout& L, long long cap, int tile_px) {
     lay.off = L.fixed;
     t.a = lay.take(8 * (size_t)cap);
     t.b = lay.take(8 * (size_t)cap);
-    t.srec = fused_lists(L.n_tiles) ? lay.take(32 * (size_t)cap) : 0;
+    t.srec = has_srec(L) ? lay.take(32 * (size_t)cap) : 0;
     t.items = lay.take(8 * (size_t)t.icap);
     t.partial = lay.take(4 * (size_t)tile_px * (size_t)t.icap);
     t.end = lay.off;
@@ -1060,7 +1069,7 @@ Tail raster_tail(const RasterLayout& L, long long cap, int tile_px) {
 // Largest key capacity (a multiple of 32) whose tail fits in ws_bytes.
 long long capacity_of(const RasterLayout& L, size_t ws_bytes, int tile_px) {
     if (ws_bytes <= L.fixed) return 0;
-    const double per = (fused_lists(L.n_tiles) ? 48.0 : 16.0) + (8.0 + 4.0 * tile_px) / kChunk;
+    const double per = (has_srec(L) ? 48.0 : 16.0) + (8.0 + 4.0 * tile_px) / kChunk;
     const double fixed_tail = (double)L.n_tiles * (8.0 + 4.0 * tile_px) + 4096.0;
     double est = ((double)(ws_bytes - L.fixed) - fixed_tail) / per;
     long long cap = est > 0 ? ((long long)est / 32) * 32 : 0;
@@ -1142,7 +1151,7 @@ void launch_bwd(int tw, int th, const float4* rec, const float4* srec, const uin
 }
 
 uint64_t* sorted_buffer(char* base, const RasterLayout& L, const Tail& t) {
-    return reinterpret_cast<uint64_t*>(base + ((list_sort_passes(L.n_tiles) & 1) ? t.b : t.a));
+    return reinterpret_cast<uint64_t*>(base + ((seg_lists(L.sk) || (list_sort_passes(L.n_tiles) & 1)) ? t.b : t.a));
 }
 
 }  // namespace
@@ -1228,11 +1237,12 @@ r2g_status r2g::rasterize_impl(int64_t M, const float* mean, const float* scale,
     // the status block (with the arrival counters of the list passes) starts cleared
     cudaMemsetAsync(st, 0, sizeof(WsStatus), stream);
     // the general list path gives empty tiles no work item: their pixels stay zero
-    if (!fused_lists(L.n_tiles)) cudaMemsetAsync(image, 0, sizeof(float) * (size_t)V * cam->H * cam->W, stream);
+    if (!fused_lists(L.n_tiles) && !seg_lists(L.sk))
+        cudaMemsetAsync(image, 0, sizeof(float) * (size_t)V * cam->H * cam->W, stream);
     Params G{mean, scale, quat, rho};
     const CamF cf = camf(cam, opts);
     float4* mom = reinterpret_cast<float4*>(base + L.mom);
-    float4* srec = fused_lists(L.n_tiles) ? reinterpret_cast<float4*>(base + T.srec) : nullptr;
+    float4* srec = has_srec(L) ? reinterpret_cast<float4*>(base + T.srec) : nullptr;
     TileOp op{rect, M, L.tiles_x, L.tiles_per_view, rec, srec};
     int launches = 0;
     uint64_t* sorted = nullptr;
@@ -1247,14 +1257,20 @@ r2g_status r2g::rasterize_impl(int64_t M, const float* mean, const float* scale,
         launches = 1;
     } else {
         const ListBlocking lb = list_blocking(L.n_rec);
-        k_project<<<(unsigned)lb.blocks, 256, 0, stream>>>(G, views, view_sel, cf, opts->Q, opts->tile_w,
-                                                            opts->tile_h, M, L.n_rec, lb.per_thread, rec, rect,
-                                                            nullptr, nullptr, mom,
-                                                            list_count(L.n_tiles, partials, st, cap, scratch));
+        uint32_t* seg = seg_lists(L.sk) ? reinterpret_cast<uint32_t*>(base + L.seg) : nullptr;
+        k_project<<<(unsigned)lb.blocks, 256, 0, stream>>>(
+            G, views, view_sel, cf, opts->Q, opts->tile_w, opts->tile_h, M, L.n_rec, lb.per_thread, rec, rect,
+            nullptr, nullptr, mom,
+            seg ? seg_list_count(L.sk, partials, st, cap, seg) : list_count(L.n_tiles, partials, st, cap, scratch));
         prof_end(P_PROJECT, stream);
-        sorted = build_lists(op, L.n_rec, L.n_tiles, partials, st, a, b, scratch, cap, ranges, key_done, item_st,
-                             item_off, items, T.icap, kChunk, ListProf{P_EMIT, P_SORT, P_RANGES}, stream,
-                             &launches, !opts->separate_lists, kFwdMaxBlocks);
+        if (seg)
+            sorted = build_lists_seg(op, L.n_rec, L.sk, partials, st, a, b, cap, seg, ranges, key_done, item_st,
+                                     item_off, items, T.icap, kChunk, kFwdMaxBlocks,
+                                     ListProf{P_EMIT, P_SORT, P_RANGES}, stream, &launches);
+        else
+            sorted = build_lists(op, L.n_rec, L.n_tiles, partials, st, a, b, scratch, cap, ranges, key_done,
+                                 item_st, item_off, items, T.icap, kChunk, ListProf{P_EMIT, P_SORT, P_RANGES},
+                                 stream, &launches, !opts->separate_lists, kFwdMaxBlocks);
         launches += 1;
     }
     const float Tq = -0.5f * kLog2e * opts->Q;
@@ -1302,7 +1318,7 @@ r2g_status r2g::rasterize_backward_impl(int64_t M, const float* mean, const floa
     const float Tq = -0.5f * kLog2e * opts->Q;
     if (parts & kRasterBwdMoments) {
         prof_begin(P_SPLAT_BWD, stream);
-        const float4* srec = fused_lists(L.n_tiles) ? reinterpret_cast<const float4*>(base + T.srec) : nullptr;
+        const float4* srec = has_srec(L) ? reinterpret_cast<const float4*>(base + T.srec) : nullptr;
         launch_bwd(opts->tile_w, opts->tile_h, rec, srec, ranges, sorted, items, item_st, T.icap, M, L, cam->H, cam->W,
                    Tq, dimage, mom, reinterpret_cast<const WsStatus*>(base + L.status), stream);
         prof_end(P_SPLAT_BWD, stream);

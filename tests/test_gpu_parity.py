@@ -27,11 +27,14 @@ def _lib():
 def _case(case):
     """config1 / parallel: 4 views x 16 tiles; cone: 3 views x 42 tiles -- both take
     the fused list path (<= 1024 keys); cone25: 25 views x 42 tiles = 1050 keys at
-    16 x 16, the general radix-sort path."""
+    16 x 16, the view-segmented path (several views, <= 1024 tiles per view); wide: 2
+    views of 264 x 264 pixels, 1089 tiles per view at 8 x 8, the radix-sort path."""
     if case in ("parallel", "config1"):
         return config1()
     if case == "cone25":
         return cone_small(M=1500, V=25)
+    if case == "wide":
+        return cone_small(M=2500, V=2, H=264, W=264)
     return cone_small()
 
 
@@ -72,7 +75,8 @@ def _lists_gpu(rast, M, V):
 
 
 @pytest.mark.parametrize("case,tile", [("parallel", (16, 16)), ("cone", (16, 16)), ("cone", (8, 8)),
-                                       ("parallel", (32, 8)), ("cone", (32, 32)), ("cone25", (16, 16))])
+                                       ("parallel", (32, 8)), ("cone", (32, 32)), ("cone25", (16, 16)),
+                                       ("cone25", (32, 8)), ("wide", (8, 8))])
 def test_tile_lists_bit_exact(case, tile):
     G, cam, views = _case(case)
     rast = engine.Rasterizer(G.M, views.shape[0], cam, tile=tile, capacity=1024)  # forces a regrow
@@ -87,7 +91,7 @@ def test_tile_lists_bit_exact(case, tile):
         assert np.array_equal(got, exp), t  # same ids, ascending (stable sort)
 
 
-@pytest.mark.parametrize("case", ["config1", "cone", "cone25"])
+@pytest.mark.parametrize("case", ["config1", "cone", "cone25", "wide"])
 def test_rasterize_matches_oracle(case):
     G, cam, views = _case(case)
     rast = engine.Rasterizer(G.M, views.shape[0], cam)
@@ -153,12 +157,15 @@ def test_rasterize_ragged_detector_and_empty_cases():
     assert float(rz.forward(*dev_set(Gz), dev(views)).abs().max()) == 0.0
 
 
-@pytest.mark.parametrize("case", ["config1", "cone", "cone25"])
-def test_rasterize_backward_matches_oracle_adjoint(case):
-    G, cam, views = config1() if case == "config1" else cone_small(M=1500, V=25 if case == "cone25" else 3)
+@pytest.mark.parametrize("case,tile", [("config1", (16, 16)), ("cone", (16, 16)), ("cone25", (16, 16)),
+                                       ("wide", (8, 8))])
+def test_rasterize_backward_matches_oracle_adjoint(case, tile):
+    """The adjoint through each list path: fused (config1, cone), view-segmented
+    (cone25) and radix-sorted with records gathered by id (wide at 8 x 8)."""
+    G, cam, views = _case(case)
     V = views.shape[0]
     dimg = I.rng(5).standard_normal((V, cam.H, cam.W)).astype(np.float32)
-    rast = engine.Rasterizer(G.M, V, cam)
+    rast = engine.Rasterizer(G.M, V, cam, tile=tile)
     mean, scale, quat, rho = dev_set(G)
     vv = dev(views)
     rast.forward(mean, scale, quat, rho, vv)
