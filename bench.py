@@ -963,6 +963,37 @@ def measure_scale(args, dev, dist, seed, world):
     e2e_s = time.perf_counter() - t0
     assert n_read == args.steps and np.isfinite(loss_sum)
     e2e_s = slowest(dist, e2e_s, dev)
+    # the memory-tight form of the same step: views 15 at a time through a workspace for
+    # one chunk, every chunk's lists but the last rebuilt in the backward (timed apart)
+    rc_out = None
+    if not args.no_recompute:
+        chunk = 15
+        tile = (sc.rast.opts.tile_w, sc.rast.opts.tile_h)
+        sc2 = engine.Scan(G, views_np, meas_np, cam, n_out=N_OUT, D=D_TV, device=dev, headroom=1.25,
+                          all_views=True, n_patches=SCALE_NP, full_volume=True, tile=tile, view_chunk=chunk)
+
+        def step2(k):
+            sc2.job.patch_origins = org0 + k * org_row
+            r2g.r2g_train_step(sc2.job, table.data_ptr() + k * elem, stream)
+
+        for k in range(args.warmup):
+            step2(k)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n2 = min(args.steps, 5)
+        e0.record(stream)
+        for j in range(n2):
+            step2(t0_steps + j)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        assert not sc2.overflowed()
+        rc_out = {"view_chunk": chunk, "ms_per_step": e0.elapsed_time(e1) / n2, "steps": n2,
+                  "raster_ws_bytes": int(sc2.rast.ws.numel()), "raster_ws_bytes_all_views": int(sc.rast.ws.numel()),
+                  "note": "the same step with r2g_raster_opts.view_chunk = 15: a workspace for 15 views, the backward "
+                          "rebuilding the records and lists of 4 of its 5 chunks; device time per step over the "
+                          "first steps of the timed sequence from the warmed-up state of that scan"}
+        del sc2
+        torch.cuda.empty_cache()
     pk = peaks()
     roofs = {}
     for name in ("splat_fwd", "splat_bwd"):
@@ -985,7 +1016,7 @@ def measure_scale(args, dev, dist, seed, world):
                         "before it), the fused step, the two losses read back to pinned host memory and read by "
                         "the host; the same steps as the device-timed leg, from the same starting state"},
         "gpu_launches": int(launches), "roofline": roof, "splat_rooflines": roofs, "kernels_ms_per_step": breakdown,
-        "clocks": clocks,
+        "clocks": clocks, "recompute_lists": rc_out,
         "config": {"workload": SCALE_WORKLOAD, "gaussians": int(sc.M), "views_per_step": SCALE_V,
                    "detector": "512x512", "tv_patches_per_step": SCALE_NP, "full_volume": f"{N_OUT}^3",
                    "pixel_pairs_per_step": pix, "voxel_pairs_per_step_patches": sum(vox) / args.steps,
@@ -1179,6 +1210,7 @@ def run_ours(args, rank, world, local_rank):
             "pairs_per_step": head["pairs_per_step"],
             "step_call": "r2g_train_step, batch form (one C call per step; all views, 8 patch origins and the "
                          "full volume from the job, iteration from a device table)",
+            "recompute_lists": head["recompute_lists"],
             "cpu_baseline": cpu, "one_scan": one, **extras, "clocks": head["clocks"],
         }
         print(json.dumps(line), flush=True)
@@ -1195,6 +1227,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-one-scan", action="store_true", help="skip the one-scan (50k Gaussians, 1 view) leg")
+    ap.add_argument("--no-recompute", action="store_true", help="skip the view-chunked (recomputed lists) timing")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the multi-scan scans/hour, serving and FDK-initialisation measurements")
     ap.add_argument("--fdk-only", action="store_true",

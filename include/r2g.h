@@ -80,6 +80,14 @@ typedef struct {
                           * pitch_v^2), as 3DGS adds 0.3 px^2 for anti-aliasing; rho_hat keeps Eq. 7's mu of the
                           * undilated Sigma^, so the projected mass is no longer the Gaussian's (the paper uses
                           * none).  Negative or non-finite: R2G_E_INVAL. */
+    int32_t view_chunk;  /* 0 (default): the workspace holds every view's records and lists, the forward
+                          * stores them and the backward reuses them.  k > 0 (and < V): views are processed k
+                          * at a time, the workspace holds one chunk of k views (its size is that of k views),
+                          * and the backward rebuilds each chunk's records and lists instead of reading them
+                          * stored -- the memory of a many-view launch for a second projection and list build
+                          * of all but the last chunk.  The image and the gradients are those of the stored
+                          * form (the forward bit for bit).  r2g_raster_lists then returns the last chunk's
+                          * lists.  Negative: R2G_E_INVAL. */
 } r2g_raster_opts;
 
 /* One voxel grid: the centre of voxel (x, y, z) is origin + (index + 1/2) * voxel;

@@ -119,7 +119,7 @@ __device__ __forceinline__ void list_count_tail(const ListCount& lc, unsigned lo
     if (lc.key_totals)
         for (int k = t; k < lc.n_keys; k += 256) lc.key_totals[k] = 0;
     if (t == 0) {
-        lc.st->needed = carry;
+        atomicMax(&lc.st->needed, carry);  // the largest of a call's view chunks
         lc.st->n_keys = carry < lc.capacity ? carry : lc.capacity;
         if (carry > lc.capacity) lc.st->status = R2G_E_CAPACITY;
     }
@@ -552,7 +552,7 @@ __global__ void __launch_bounds__(256) k_plists_coop(Proj proj, Op op, long long
     total = block_sum_u64_256(total, smu);
     const unsigned long long written = total < capacity ? total : capacity;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        st->needed = total;
+        atomicMax(&st->needed, total);  // the largest of a call's view chunks
         st->n_keys = written;
         if (total > capacity) atomicExch(&st->status, (int32_t)R2G_E_CAPACITY);
     }

@@ -49,9 +49,9 @@ unsigned long long wait_polls();
 
 // Status block at offset 0 of every workspace (256 bytes).
 struct WsStatus {
-    int32_t status;             // R2G_OK or R2G_E_CAPACITY
+    int32_t status;             // R2G_OK, R2G_E_CAPACITY, R2G_E_TIMEOUT or R2G_E_NUMERIC
     int32_t pad;
-    unsigned long long needed;  // list entries the last call needed
+    unsigned long long needed;  // list entries the last call needed (the most of its view chunks)
     unsigned long long n_keys;  // entries actually emitted = min(needed, capacity)
     unsigned long long pairs;   // gated pairs (counting runs only)
     unsigned long long blocks_done;  // arrival counter of the entry count pass

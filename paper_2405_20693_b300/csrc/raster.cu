@@ -835,7 +835,7 @@ __global__ void __launch_bounds__(128) k_project_bwd(Params G, const float* __re
         const float d_cx = rhohat * (pa * Sx + pb * Sy);
         const float d_cy = rhohat * (pb * Sx + pc * Sy);
         const float d_pa = -0.5f * rhohat * Sxx, d_pb = -rhohat * Sxy, d_pc = -0.5f * rhohat * Syy;
-        if (ADAM) {  // |dL/dp^| in normalised device coordinates (pixel gradient x (W/2, H/2))
+        if (adam.dens_grad) {  // |dL/dp^| in normalised device coordinates (pixel gradient x (W/2, H/2))
             dens_g += hypotf(d_cx * (0.5f * (float)cam.W), d_cy * (0.5f * (float)cam.H));
             dens_n += 1.f;
         }
@@ -945,6 +945,10 @@ __global__ void __launch_bounds__(128) k_project_bwd(Params G, const float* __re
         }
         return;
     }
+    if (adam.dens_grad && dens_n > 0.f) {  // an earlier view chunk of a fused step
+        adam.dens_grad[i] += dens_g;
+        adam.dens_count[i] += dens_n;
+    }
     if (!have_rot) return;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -1014,6 +1018,7 @@ r2g_status check_args(int64_t M, int32_t V, const r2g_camera* cam, const r2g_ras
     if (!(opts->Q > 0.f)) return fail(R2G_E_INVAL, "Q must be > 0");
     if (!(opts->dilation >= 0.f) || !(opts->dilation < 1e6f))
         return fail(R2G_E_INVAL, "dilation must be finite and >= 0 (got %g)", (double)opts->dilation);
+    if (opts->view_chunk < 0) return fail(R2G_E_INVAL, "view_chunk must be >= 0 (got %d)", opts->view_chunk);
     const long long tx = (cam->W + opts->tile_w - 1) / opts->tile_w, ty = (cam->H + opts->tile_h - 1) / opts->tile_h;
     if ((long long)V * tx * ty >= (1ll << 31)) return fail(R2G_E_INVAL, "too many tiles");
     return R2G_OK;
@@ -1154,6 +1159,93 @@ uint64_t* sorted_buffer(char* base, const RasterLayout& L, const Tail& t) {
     return reinterpret_cast<uint64_t*>(base + ((seg_lists(L.sk) || (list_sort_passes(L.n_tiles) & 1)) ? t.b : t.a));
 }
 
+// Views per chunk: all V, or opts->view_chunk when it is smaller (the workspace then
+// holds one chunk's records and lists).
+inline int chunk_views(int V, const r2g_raster_opts* o) { return o->view_chunk > 0 && o->view_chunk < V ? o->view_chunk : V; }
+
+// The workspace carved for a chunk of vc views.
+struct Chunk {
+    RasterLayout L;
+    Tail T;
+    long long cap;
+    char* base;
+    WsStatus* st;
+    WsStatus* item_st;
+    float4 *rec, *mom, *srec;
+    uint2 *rect, *ranges;
+    unsigned long long* partials;
+    uint32_t *scratch, *item_off, *key_done, *seg;
+    uint64_t *a, *b, *items;
+    float* partial;
+};
+
+bool make_chunk(int64_t M, int vc, const r2g_camera* cam, const r2g_raster_opts* opts, void* ws, size_t ws_bytes,
+                Chunk& c) {
+    c.L = raster_layout(M, vc, cam, opts);
+    const int tpx = opts->tile_w * opts->tile_h;
+    c.cap = capacity_of(c.L, ws_bytes, tpx);
+    if (c.cap < 32) return false;
+    c.T = raster_tail(c.L, c.cap, tpx);
+    char* base = static_cast<char*>(ws);
+    c.base = base;
+    c.st = reinterpret_cast<WsStatus*>(base + c.L.status);
+    c.item_st = reinterpret_cast<WsStatus*>(base + c.L.item_status);
+    c.rec = reinterpret_cast<float4*>(base + c.L.rec);
+    c.mom = reinterpret_cast<float4*>(base + c.L.mom);
+    c.srec = has_srec(c.L) ? reinterpret_cast<float4*>(base + c.T.srec) : nullptr;
+    c.rect = reinterpret_cast<uint2*>(base + c.L.rect);
+    c.ranges = reinterpret_cast<uint2*>(base + c.L.ranges);
+    c.partials = reinterpret_cast<unsigned long long*>(base + c.L.partials);
+    c.scratch = reinterpret_cast<uint32_t*>(base + c.L.scratch);
+    c.item_off = reinterpret_cast<uint32_t*>(base + c.L.item_off);
+    c.key_done = reinterpret_cast<uint32_t*>(base + c.L.key_done);
+    c.seg = seg_lists(c.L.sk) ? reinterpret_cast<uint32_t*>(base + c.L.seg) : nullptr;
+    c.a = reinterpret_cast<uint64_t*>(base + c.T.a);
+    c.b = reinterpret_cast<uint64_t*>(base + c.T.b);
+    c.items = reinterpret_cast<uint64_t*>(base + c.T.items);
+    c.partial = reinterpret_cast<float*>(base + c.T.partial);
+    return true;
+}
+
+// The records and per-tile lists of one chunk (projection + list build).  first: the
+// call's first chunk clears the whole status block; a later chunk clears only the
+// arrival counters, so a capacity verdict, the most entries needed and the pair count
+// carry over the call's chunks.  Returns the buffer with the sorted entries.
+uint64_t* chunk_lists(const Chunk& c, const Params& G, const float* views, const int* view_sel, const CamF& cf,
+                      const r2g_raster_opts* opts, long long M, bool first, cudaStream_t stream, int* launches) {
+    const RasterLayout& L = c.L;
+    if (first)
+        cudaMemsetAsync(c.st, 0, sizeof(WsStatus), stream);
+    else
+        cudaMemsetAsync(&c.st->blocks_done, 0, 2 * sizeof(unsigned long long), stream);  // blocks_done, grid_sync
+    TileOp op{c.rect, M, L.tiles_x, L.tiles_per_view, c.rec, c.srec};
+    // fused key spaces: projection and lists in one cooperative launch when the grid fits
+    const TileProj tp{G, views, view_sel, cf, opts->Q, opts->tile_w, opts->tile_h, M, L.n_rec, c.rec, c.rect, c.mom};
+    prof_begin(P_PROJECT, stream);
+    if (!opts->separate_lists &&
+        launch_plists_coop(tp, op, L.n_rec, L.n_tiles, c.partials, c.a, c.b, c.cap, c.scratch, c.st, c.ranges,
+                           c.key_done, c.item_st, c.item_off, c.items, c.T.icap, kChunk, stream, kFwdMaxBlocks)) {
+        prof_end(P_PROJECT, stream);
+        *launches += 1;
+        return c.b;
+    }
+    const ListBlocking lb = list_blocking(L.n_rec);
+    k_project<<<(unsigned)lb.blocks, 256, 0, stream>>>(
+        G, views, view_sel, cf, opts->Q, opts->tile_w, opts->tile_h, M, L.n_rec, lb.per_thread, c.rec, c.rect,
+        nullptr, nullptr, c.mom,
+        c.seg ? seg_list_count(L.sk, c.partials, c.st, c.cap, c.seg)
+              : list_count(L.n_tiles, c.partials, c.st, c.cap, c.scratch));
+    prof_end(P_PROJECT, stream);
+    *launches += 1;
+    if (c.seg)
+        return build_lists_seg(op, L.n_rec, L.sk, c.partials, c.st, c.a, c.b, c.cap, c.seg, c.ranges, c.key_done,
+                               c.item_st, c.item_off, c.items, c.T.icap, kChunk, kFwdMaxBlocks,
+                               ListProf{P_EMIT, P_SORT, P_RANGES}, stream, launches);
+    return build_lists(op, L.n_rec, L.n_tiles, c.partials, c.st, c.a, c.b, c.scratch, c.cap, c.ranges, c.key_done,
+                       c.item_st, c.item_off, c.items, c.T.icap, kChunk, ListProf{P_EMIT, P_SORT, P_RANGES}, stream,
+                       launches, !opts->separate_lists, kFwdMaxBlocks);
+}
+
 }  // namespace
 }  // namespace r2g
 
@@ -1166,7 +1258,7 @@ R2G_API size_t r2g_raster_workspace_size(int64_t M, int32_t V, const r2g_camera*
         fail(R2G_E_INVAL, "key_capacity %lld out of range", (long long)key_capacity);
         return 0;
     }
-    const RasterLayout L = raster_layout(M, V, cam, opts);
+    const RasterLayout L = raster_layout(M, chunk_views(V, opts), cam, opts);
     return raster_tail(L, key_capacity, opts->tile_w * opts->tile_h).end;
 }
 
@@ -1215,73 +1307,37 @@ r2g_status r2g::rasterize_impl(int64_t M, const float* mean, const float* scale,
     if (!mean || !scale || !quat || !rho || !views || !image || !ws) return fail(R2G_E_INVAL, "NULL pointer");
     if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(R2G_E_INVAL, "workspace must be 256-byte aligned");
     if (reinterpret_cast<uintptr_t>(quat) % 16) return fail(R2G_E_INVAL, "quat must be 16-byte aligned");
-    const RasterLayout L = raster_layout(M, V, cam, opts);
-    const int tpx = opts->tile_w * opts->tile_h;
-    const long long cap = capacity_of(L, ws_bytes, tpx);
-    if (cap < 32) return fail(R2G_E_INVAL, "workspace of %zu bytes holds no list entries", ws_bytes);
-    const Tail T = raster_tail(L, cap, tpx);
-    char* base = static_cast<char*>(ws);
-    WsStatus* st = reinterpret_cast<WsStatus*>(base + L.status);
-    float4* rec = reinterpret_cast<float4*>(base + L.rec);
-    uint2* rect = reinterpret_cast<uint2*>(base + L.rect);
-    auto* partials = reinterpret_cast<unsigned long long*>(base + L.partials);
-    uint2* ranges = reinterpret_cast<uint2*>(base + L.ranges);
-    uint32_t* scratch = reinterpret_cast<uint32_t*>(base + L.scratch);
-    uint64_t* a = reinterpret_cast<uint64_t*>(base + T.a);
-    uint64_t* b = reinterpret_cast<uint64_t*>(base + T.b);
-    WsStatus* item_st = reinterpret_cast<WsStatus*>(base + L.item_status);
-    uint32_t* item_off = reinterpret_cast<uint32_t*>(base + L.item_off);
-    uint32_t* key_done = reinterpret_cast<uint32_t*>(base + L.key_done);
-    uint64_t* items = reinterpret_cast<uint64_t*>(base + T.items);
-    float* partial = reinterpret_cast<float*>(base + T.partial);
-    // the status block (with the arrival counters of the list passes) starts cleared
-    cudaMemsetAsync(st, 0, sizeof(WsStatus), stream);
-    // the general list path gives empty tiles no work item: their pixels stay zero
-    if (!fused_lists(L.n_tiles) && !seg_lists(L.sk))
-        cudaMemsetAsync(image, 0, sizeof(float) * (size_t)V * cam->H * cam->W, stream);
-    Params G{mean, scale, quat, rho};
+    const Params G{mean, scale, quat, rho};
     const CamF cf = camf(cam, opts);
-    float4* mom = reinterpret_cast<float4*>(base + L.mom);
-    float4* srec = has_srec(L) ? reinterpret_cast<float4*>(base + T.srec) : nullptr;
-    TileOp op{rect, M, L.tiles_x, L.tiles_per_view, rec, srec};
+    const float Tq = -0.5f * kLog2e * opts->Q;
+    const int Vc = chunk_views(V, opts);
+    const size_t px = (size_t)cam->H * cam->W;
     int launches = 0;
-    uint64_t* sorted = nullptr;
-    // fused key spaces: projection and lists in one cooperative launch when the grid fits
-    const TileProj tp{G, views, view_sel, cf, opts->Q, opts->tile_w, opts->tile_h, M, L.n_rec, rec, rect, mom};
-    prof_begin(P_PROJECT, stream);
-    if (!opts->separate_lists &&
-        launch_plists_coop(tp, op, L.n_rec, L.n_tiles, partials, a, b, cap, scratch, st, ranges, key_done, item_st,
-                           item_off, items, T.icap, kChunk, stream, kFwdMaxBlocks)) {
-        prof_end(P_PROJECT, stream);
-        sorted = b;
-        launches = 1;
-    } else {
-        const ListBlocking lb = list_blocking(L.n_rec);
-        uint32_t* seg = seg_lists(L.sk) ? reinterpret_cast<uint32_t*>(base + L.seg) : nullptr;
-        k_project<<<(unsigned)lb.blocks, 256, 0, stream>>>(
-            G, views, view_sel, cf, opts->Q, opts->tile_w, opts->tile_h, M, L.n_rec, lb.per_thread, rec, rect,
-            nullptr, nullptr, mom,
-            seg ? seg_list_count(L.sk, partials, st, cap, seg) : list_count(L.n_tiles, partials, st, cap, scratch));
-        prof_end(P_PROJECT, stream);
-        if (seg)
-            sorted = build_lists_seg(op, L.n_rec, L.sk, partials, st, a, b, cap, seg, ranges, key_done, item_st,
-                                     item_off, items, T.icap, kChunk, kFwdMaxBlocks,
-                                     ListProf{P_EMIT, P_SORT, P_RANGES}, stream, &launches);
+    // views c0 .. c0 + vc - 1 at a time (all of them in one chunk unless view_chunk is set)
+    for (int c0 = 0; c0 < V; c0 += Vc) {
+        const int vc = Vc < V - c0 ? Vc : V - c0;
+        Chunk c;
+        if (!make_chunk(M, vc, cam, opts, ws, ws_bytes, c))
+            return fail(R2G_E_INVAL, "workspace of %zu bytes holds no list entries", ws_bytes);
+        const float* views_c = view_sel ? views : views + 12 * (size_t)c0;
+        const int* sel_c = view_sel ? view_sel + c0 : nullptr;
+        float* image_c = image + (size_t)c0 * px;
+        // the radix path gives empty tiles no work item: their pixels stay zero
+        if (!fused_lists(c.L.n_tiles) && !seg_lists(c.L.sk))
+            cudaMemsetAsync(image_c, 0, sizeof(float) * (size_t)vc * px, stream);
+        const uint64_t* sorted = chunk_lists(c, G, views_c, sel_c, cf, opts, M, c0 == 0, stream, &launches);
+        prof_begin(P_SPLAT_FWD, stream);
+        const FwdArgs fa{c.rec, c.srec, c.ranges, sorted, c.items, c.item_st, c.partial, c.item_off, c.key_done};
+        if (opts->count_pairs)
+            launch_fwd<true>(opts->tile_w, opts->tile_h, fa, M, c.L, c.T.icap, cam->H, cam->W, Tq, image_c, c.st,
+                             stream);
         else
-            sorted = build_lists(op, L.n_rec, L.n_tiles, partials, st, a, b, scratch, cap, ranges, key_done,
-                                 item_st, item_off, items, T.icap, kChunk, ListProf{P_EMIT, P_SORT, P_RANGES},
-                                 stream, &launches, !opts->separate_lists, kFwdMaxBlocks);
+            launch_fwd<false>(opts->tile_w, opts->tile_h, fa, M, c.L, c.T.icap, cam->H, cam->W, Tq, image_c, c.st,
+                              stream);
+        prof_end(P_SPLAT_FWD, stream);
         launches += 1;
     }
-    const float Tq = -0.5f * kLog2e * opts->Q;
-    prof_begin(P_SPLAT_FWD, stream);
-    const FwdArgs fa{rec, srec, ranges, sorted, items, item_st, partial, item_off, key_done};
-    if (opts->count_pairs)
-        launch_fwd<true>(opts->tile_w, opts->tile_h, fa, M, L, T.icap, cam->H, cam->W, Tq, image, st, stream);
-    else
-        launch_fwd<false>(opts->tile_w, opts->tile_h, fa, M, L, T.icap, cam->H, cam->W, Tq, image, st, stream);
-    prof_end(P_SPLAT_FWD, stream);
-    note_launches(launches + 1);
+    note_launches(launches);
     return check_launch("r2g_rasterize");
 }
 
@@ -1303,41 +1359,65 @@ r2g_status r2g::rasterize_backward_impl(int64_t M, const float* mean, const floa
     if (!adam && (!dmean || !dscale || !dquat || !drho)) return fail(R2G_E_INVAL, "NULL gradient pointer");
     if (reinterpret_cast<uintptr_t>(ws) % 256) return fail(R2G_E_INVAL, "workspace must be 256-byte aligned");
     if (reinterpret_cast<uintptr_t>(quat) % 16) return fail(R2G_E_INVAL, "quat must be 16-byte aligned");
-    const RasterLayout L = raster_layout(M, V, cam, opts);
-    const int tpx = opts->tile_w * opts->tile_h;
-    const long long cap = capacity_of(L, ws_bytes, tpx);
-    if (cap < 32) return fail(R2G_E_INVAL, "workspace of %zu bytes holds no list entries", ws_bytes);
-    const Tail T = raster_tail(L, cap, tpx);
-    char* base = static_cast<char*>(ws);
-    const float4* rec = reinterpret_cast<const float4*>(base + L.rec);
-    const uint2* ranges = reinterpret_cast<const uint2*>(base + L.ranges);
-    float4* mom = reinterpret_cast<float4*>(base + L.mom);
-    const uint64_t* sorted = sorted_buffer(base, L, T);
-    const uint64_t* items = reinterpret_cast<const uint64_t*>(base + T.items);
-    const WsStatus* item_st = reinterpret_cast<const WsStatus*>(base + L.item_status);
+    const Params G{mean, scale, quat, rho};
+    const CamF cf = camf(cam, opts);
     const float Tq = -0.5f * kLog2e * opts->Q;
-    if (parts & kRasterBwdMoments) {
-        prof_begin(P_SPLAT_BWD, stream);
-        const float4* srec = has_srec(L) ? reinterpret_cast<const float4*>(base + T.srec) : nullptr;
-        launch_bwd(opts->tile_w, opts->tile_h, rec, srec, ranges, sorted, items, item_st, T.icap, M, L, cam->H, cam->W,
-                   Tq, dimage, mom, reinterpret_cast<const WsStatus*>(base + L.status), stream);
-        prof_end(P_SPLAT_BWD, stream);
-        note_launches(1);
+    const unsigned grid = (unsigned)((M + 127) / 128);
+    const int Vc = chunk_views(V, opts);
+    const size_t px = (size_t)cam->H * cam->W;
+    const int n_chunks = (V + Vc - 1) / Vc;
+    if (n_chunks > 1 && parts != (kRasterBwdMoments | kRasterBwdChain))
+        return fail(R2G_E_INVAL, "a view-chunked backward takes the moments and the chain rule together");
+    // with an Adam state, the earlier chunks' gradients go to adam->grad and the last
+    // chunk's chain rule (the fused one) adds its own and takes the step
+    if (adam) {
+        dquat = adam->grad ? const_cast<float*>(adam->grad) : nullptr;
+        dmean = dquat ? dquat + 4 * M : nullptr;
+        dscale = dquat ? dquat + 7 * M : nullptr;
+        drho = dquat ? dquat + 10 * M : nullptr;
     }
-    if (parts & kRasterBwdChain) {
-        Params G{mean, scale, quat, rho};
-        const unsigned grid = (unsigned)((M + 127) / 128);
-        prof_begin(P_PROJECT_BWD, stream);
-        if (adam)
-            launch_pdl(k_project_bwd<true>, dim3(grid), dim3(128), 0, stream, G, views, view_sel, camf(cam, opts),
-                       opts->Q, M, V, rec, mom, (float*)nullptr, (float*)nullptr, (float*)nullptr, (float*)nullptr,
-                       *adam);
-        else
-            launch_pdl(k_project_bwd<false>, dim3(grid), dim3(128), 0, stream, G, views, view_sel, camf(cam, opts),
-                       opts->Q, M, V, rec, mom, dmean, dscale, dquat, drho, AdamState{});
-        prof_end(P_PROJECT_BWD, stream);
-        note_launches(1);
+    int launches = 0;
+    // chunks last to first: the last one's records and lists are still in the workspace
+    // from the forward; every other chunk's are rebuilt
+    for (int ci = n_chunks - 1; ci >= 0; --ci) {
+        const int c0 = ci * Vc, vc = Vc < V - c0 ? Vc : V - c0;
+        Chunk c;
+        if (!make_chunk(M, vc, cam, opts, ws, ws_bytes, c))
+            return fail(R2G_E_INVAL, "workspace of %zu bytes holds no list entries", ws_bytes);
+        const float* views_c = view_sel ? views : views + 12 * (size_t)c0;
+        const int* sel_c = view_sel ? view_sel + c0 : nullptr;
+        const uint64_t* sorted =
+            ci == n_chunks - 1 ? sorted_buffer(c.base, c.L, c.T)
+                               : chunk_lists(c, G, views_c, sel_c, cf, opts, M, false, stream, &launches);
+        if (parts & kRasterBwdMoments) {
+            prof_begin(P_SPLAT_BWD, stream);
+            launch_bwd(opts->tile_w, opts->tile_h, c.rec, c.srec, c.ranges, sorted, c.items, c.item_st, c.T.icap, M,
+                       c.L, cam->H, cam->W, Tq, dimage + (size_t)c0 * px, c.mom, c.st, stream);
+            prof_end(P_SPLAT_BWD, stream);
+            launches += 1;
+        }
+        if (parts & kRasterBwdChain) {
+            prof_begin(P_PROJECT_BWD, stream);
+            if (adam && ci == 0) {
+                launch_pdl(k_project_bwd<true>, dim3(grid), dim3(128), 0, stream, G, views_c, sel_c, cf, opts->Q, M, vc,
+                           c.rec, c.mom, (float*)nullptr, (float*)nullptr, (float*)nullptr, (float*)nullptr, *adam);
+            } else {
+                // an earlier chunk of a fused step: its gradient (and adaptive-control
+                // statistics) are added to what the step accumulates
+                AdamState stats{};
+                if (adam) {
+                    stats.dens_grad = adam->dens_grad;
+                    stats.dens_count = adam->dens_count;
+                    stats.a.M = M;
+                }
+                launch_pdl(k_project_bwd<false>, dim3(grid), dim3(128), 0, stream, G, views_c, sel_c, cf, opts->Q, M,
+                           vc, c.rec, c.mom, dmean, dscale, dquat, drho, stats);
+            }
+            prof_end(P_PROJECT_BWD, stream);
+            launches += 1;
+        }
     }
+    note_launches(launches);
     return check_launch("r2g_rasterize_backward");
 }
 
@@ -1356,7 +1436,8 @@ R2G_API r2g_status r2g_raster_lists(int64_t M, int32_t V, const r2g_camera* cam,
     r2g_status e = check_args(M, V, cam, opts);
     if (e) return e;
     if (!ws || !ranges_out || !ids || !n_entries) return fail(R2G_E_INVAL, "NULL pointer");
-    const RasterLayout L = raster_layout(M, V, cam, opts);
+    const int Vc = chunk_views(V, opts);
+    const RasterLayout L = raster_layout(M, V - ((V - 1) / Vc) * Vc, cam, opts);  // the last chunk's
     const int tpx = opts->tile_w * opts->tile_h;
     const long long cap = capacity_of(L, ws_bytes, tpx);
     if (cap < 32) return fail(R2G_E_INVAL, "workspace of %zu bytes holds no list entries", ws_bytes);

@@ -156,7 +156,10 @@ R2G_API r2g_status r2g_train_step(const r2g_job* job, const r2g_round_entry* ent
     if (!e_px)
         e_px = projection_loss_impl(Vs, J.cam.H, J.cam.W, J.image, J.meas, view_sel, J.lambda_ssim, J.loss, J.dimage,
                                     J.loss_ws, J.loss_ws_bytes, stream, false);
-    if (!e_px)
+    // a view-chunked rasterizer rebuilds each chunk's lists in its backward and takes
+    // the moments and the chain rule together, after the join
+    const bool chunked = J.ropts.view_chunk > 0 && J.ropts.view_chunk < Vs;
+    if (!e_px && !chunked)
         e_px = rasterize_backward_impl(M, mean, scale, quat, rho, Vs, J.views, view_sel, &J.cam, &J.ropts, J.dimage,
                                        dmean, dscale, dquat, drho, J.raster_ws, J.raster_ws_bytes, stream,
                                        kRasterBwdMoments);
@@ -173,7 +176,7 @@ R2G_API r2g_status r2g_train_step(const r2g_job* job, const r2g_round_entry* ent
                          J.dens_grad, J.dens_count, J.loss,   reinterpret_cast<WsStatus*>(J.raster_ws)};
     return rasterize_backward_impl(M, mean, scale, quat, rho, Vs, J.views, view_sel, &J.cam, &J.ropts, J.dimage,
                                    dmean, dscale, dquat, drho, J.raster_ws, J.raster_ws_bytes, stream,
-                                   kRasterBwdChain, &adam);
+                                   chunked ? (kRasterBwdMoments | kRasterBwdChain) : kRasterBwdChain, &adam);
 }
 
 R2G_API r2g_status r2g_train_step_host_batch(const r2g_job* job, const r2g_staging* stg, int64_t step,

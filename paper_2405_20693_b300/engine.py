@@ -28,13 +28,17 @@ class Rasterizer:
     """Owns the workspace of one (M, V, camera, tile) configuration."""
 
     def __init__(self, M: int, V: int, cam, Q=Q_PIXEL, tile=(16, 16), device="cuda", capacity=None, biased=False,
-                 dilation=0.0):
+                 dilation=0.0, view_chunk=0):
+        """view_chunk > 0: views processed that many at a time, the workspace sized for
+        one chunk, and the backward rebuilding each chunk's lists (r2g_raster_opts)."""
         self.M, self.V = int(M), int(V)
         self.cam = r2g.camera(cam)
-        self.opts = r2g.raster_opts(Q, tile, biased=biased, dilation=dilation)
-        self.copts = r2g.raster_opts(Q, tile, count_pairs=True, biased=biased, dilation=dilation)
+        self.opts = r2g.raster_opts(Q, tile, biased=biased, dilation=dilation, view_chunk=view_chunk)
+        self.copts = r2g.raster_opts(Q, tile, count_pairs=True, biased=biased, dilation=dilation,
+                                     view_chunk=view_chunk)
         self.device = device
-        self.capacity = int(capacity or max(1 << 16, 4 * self.M * self.V))
+        Vc = view_chunk if 0 < view_chunk < self.V else self.V
+        self.capacity = int(capacity or max(1 << 16, 4 * self.M * Vc))
         self.ws = None
         self._alloc()
 
@@ -368,12 +372,14 @@ class Scan:
 
     def __init__(self, G, views_np, meas_np, cam, n_out=256, D=32, tile=None, total_iters=30000,
                  device="cuda", headroom=1.5, seed=0, biased=False, tv_eps=0.0, dilation=0.0, all_views=False,
-                 n_patches=1, full_volume=False):
+                 n_patches=1, full_volume=False, view_chunk=0):
         """all_views: every step rasterizes all V views in one launch (the batch form of
         r2g_train_step) instead of one view picked per step; n_patches: TV patches per
         step (> 1: their origins come from `patch_origins`, a device [n_patches, 3]
         tensor the caller fills before each step); full_volume: every step also
-        voxelizes the whole n_out^3 output volume into `full_vol` (forward only)."""
+        voxelizes the whole n_out^3 output volume into `full_vol` (forward only);
+        view_chunk > 0: the all-views rasterizer works that many views at a time and
+        rebuilds each chunk's lists in the backward (a workspace for one chunk)."""
         self.state = TrainState(G, device=device)
         self.all_views = bool(all_views)
         self.n_patches = max(1, int(n_patches))
@@ -402,8 +408,9 @@ class Scan:
         self.dvol = torch.empty_like(self.vol)
         self.loss = torch.zeros(2, dtype=torch.float32, device=device)
         self.patch_origins = torch.zeros((NP, 3), dtype=torch.float32, device=device)
+        self.view_chunk = int(view_chunk)
         self.rast = Rasterizer(self.M, self.Vs, cam, tile=tile or SCAN_TILE, device=device, biased=biased,
-                               dilation=self.dilation)
+                               dilation=self.dilation, view_chunk=self.view_chunk)
         from .inputs import cube_grid, patch_grid
 
         self.vox = Voxelizer(self.M, [patch_grid((0, 0, 0), D, n_out)] * NP, device=device)
@@ -556,7 +563,7 @@ class Scan:
         times = {}
         for tile in tiles:
             self.rast = Rasterizer(self.M, self.Vs, self.cam, tile=tile, device=self.device, biased=self.biased,
-                                   dilation=self.dilation)
+                                   dilation=self.dilation, view_chunk=self.view_chunk)
             self.rast.opts.separate_lists = sep
             self._size_workspaces(self.headroom, probes=2)
             self.job = self._make_job()
@@ -572,7 +579,7 @@ class Scan:
                 dst.copy_(src)
         best = min(times, key=times.get)
         self.rast = Rasterizer(self.M, self.Vs, self.cam, tile=best, device=self.device, biased=self.biased,
-                               dilation=self.dilation)
+                               dilation=self.dilation, view_chunk=self.view_chunk)
         self.rast.opts.separate_lists = sep
         self._size_workspaces(self.headroom, probes=2)
         self.job = self._make_job()

@@ -36,7 +36,7 @@ class Camera(ctypes.Structure):
 class RasterOpts(ctypes.Structure):
     _fields_ = [("Q", ctypes.c_float), ("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32),
                 ("count_pairs", ctypes.c_int32), ("biased", ctypes.c_int32), ("separate_lists", ctypes.c_int32),
-                ("dilation", ctypes.c_float)]
+                ("dilation", ctypes.c_float), ("view_chunk", ctypes.c_int32)]
 
 
 class DensifyOpts(ctypes.Structure):
@@ -93,9 +93,9 @@ def camera(cam) -> Camera:
 
 
 def raster_opts(Q=9.0, tile=(16, 16), count_pairs=False, biased=False, separate_lists=False,
-                dilation=0.0) -> RasterOpts:
+                dilation=0.0, view_chunk=0) -> RasterOpts:
     return RasterOpts(float(Q), int(tile[0]), int(tile[1]), int(bool(count_pairs)), int(bool(biased)),
-                      int(bool(separate_lists)), float(dilation))
+                      int(bool(separate_lists)), float(dilation), int(view_chunk))
 
 
 def grids(gdescs) -> ctypes.Array:

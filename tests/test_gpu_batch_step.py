@@ -128,3 +128,37 @@ def test_one_scan_step_full_size_rotated():
     gd = np.asarray(I.grid_desc(origin, (2 / 256,) * 3, (32, 32, 32)), np.float32).astype(np.float64)[None]
     check_step_against_oracle(sc, act, raw, views[v:v + 1], meas[v:v + 1].astype(np.float64), cam, gd,
                               "one-scan step")
+
+
+def test_view_chunked_batch_step_equals_stored():
+    """The batch step with view_chunk = 2 (5 views: chunks of 2, 2 and 1, the lists of
+    the first two rebuilt in the backward, the earlier chunks' gradients added before
+    the fused chain rule + Adam of the last) against the same step storing all views:
+    the same losses bit for bit (the forward is deterministic), the same Adam moments
+    up to the float atomics' rounding, and the oracle's composition."""
+    G = I.uniform_gaussians(4000, 32, 0.01, 0.06, box=0.7)
+    ph, _ = I.normalised_phantom(32, 64)
+    cam = I.cone_camera(128, 128, pitch=I.CONE_PITCH * 4)
+    views = I.view_table(np.deg2rad([3.0, 70.0, 160.0, 230.0, 310.0]), I.CONE_L_SO)
+    meas = I.phantom_projections(ph, views, cam, device="cuda").astype(np.float32)
+    origins = torch.as_tensor(np.array([[-0.5, -0.25, 0.0], [0.0, 0.125, -0.375]], np.float32))
+    table = entry_table([(0, 0, (0.0, 0.0, 0.0))])
+    res = []
+    for vc in (0, 2):
+        sc = engine.Scan(G, views, meas, cam, n_out=64, D=16, tile=(16, 16), all_views=True, n_patches=2,
+                         view_chunk=vc)
+        act = [host(t) for t in sc.state.views_of(sc.state.act)]
+        raw = [host(t) for t in sc.state.views_of(sc.state.raw)]
+        sc.patch_origins.copy_(origins)
+        r2g.r2g_train_step(sc.job, table.data_ptr(), torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        assert not sc.overflowed()
+        res.append((sc, act, raw))
+    (a, _, _), (b, act, raw) = res
+    assert np.array_equal(host(a.loss), host(b.loss))
+    for x, y in zip(a.state.views_of(a.state.m), b.state.views_of(b.state.m)):
+        x, y = host(x), host(y)
+        assert np.abs(x - y).max() <= 1e-5 * np.abs(x).max()
+    gds = np.stack([np.asarray(I.grid_desc(o, (2 / 64,) * 3, (16, 16, 16)), np.float32).astype(np.float64)
+                    for o in origins.numpy()])
+    check_step_against_oracle(b, act, raw, views, meas.astype(np.float64), cam, gds, "chunked batch step")
