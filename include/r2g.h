@@ -262,7 +262,9 @@ r2g_status r2g_tv3d_iso(int32_t G, int32_t D, const float* vol, float lambda_tv,
  * to a fixed 256 KiB array inside the library, so G * D^3 <= 16777216 voxels
  * (larger volumes return R2G_E_INVAL; use r2g_tv3d).  Nothing is allocated.
  * The first call on each device looks up that array's device address once
- * (cudaGetSymbolAddress) -- make it before any stream capture.  Calls share the
+ * (cudaGetSymbolAddress) -- make it before any stream capture; the address is kept
+ * for the process, so it is not valid after a cudaDeviceReset or from another
+ * (non-primary) context on that device.  Calls share the
  * array: calls that overlap on the GPU race; calls ordered on one stream do not.
  * The paper has no counterpart to this entry point. */
 r2g_status r2g_tv3d_noalloc(int32_t G, int32_t D, const float* vol, float lambda_tv, float* loss, float* dvol,

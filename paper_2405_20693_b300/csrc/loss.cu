@@ -11,9 +11,9 @@
 //                 itself) and combined with x, y and the L1 sign into d loss /
 //                 d render; the last CTA to finish sums the per-tile partials
 //                 in a fixed order into the loss (deterministic).
-//   k_finalize    (TV) one CTA sums the per-CTA partials in a fixed order.
+//   k_tv_sum      (TV) one CTA sums the per-CTA partials in a fixed order.
 // 3D TV: k_tv3d forms each voxel's gradient from its six neighbours and a CTA
-// partial of the loss; k_finalize sums the partials.
+// partial of the loss; k_tv_sum sums the partials (k_finalize for the isotropic form).
 #include <math.h>
 
 #include "r2g_internal.cuh"
@@ -385,41 +385,16 @@ __global__ void __launch_bounds__(256) k_finalize(const float* __restrict__ p, i
 __global__ void __launch_bounds__(256) k_tv3d(const float* __restrict__ vol, int D, long long n, float inv_cnt,
                                               float lam, float* __restrict__ grad, float* __restrict__ partials) {
     __shared__ float red[8];
-    const long long idx = (long long)blockIdx.x * 256 + threadIdx.x;
-    float part = 0.f;
-    if (idx < n) {
-        const long long D3 = (long long)D * D * D;
-        const long long g = idx / D3;
-        const long long l = idx - g * D3;
-        const int z = (int)(l / ((long long)D * D)), y = (int)((l / D) % D), x = (int)(l % D);
-        const float* vg = vol + g * D3;
-        const float c = vg[l];
-        float gr = 0.f;
-        const long long st[3] = {1, D, (long long)D * D};
-        const int co[3] = {x, y, z};
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            if (co[a] + 1 < D) {
-                const float d = vg[l + st[a]] - c;
-                part += fabsf(d);
-                gr -= (d > 0.f) ? 1.f : ((d < 0.f) ? -1.f : 0.f);
-            }
-            if (co[a] > 0) {
-                const float d = c - vg[l - st[a]];
-                gr += (d > 0.f) ? 1.f : ((d < 0.f) ? -1.f : 0.f);
-            }
-        }
-        grad[idx] = lam * inv_cnt * gr;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float s = 0.f;
-        for (int w = 0; w < 8; ++w) s += red[w];
-        partials[blockIdx.x] = s;
-    }
+    const float s = tv3d_block(vol, D, n, inv_cnt, lam, grad, red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// The TV loss: lam inv_cnt x the fixed-order sum of the per-block partials.
+__global__ void __launch_bounds__(256) k_tv_sum(const float* __restrict__ p, int n, float scale,
+                                                float* __restrict__ loss) {
+    __shared__ double red[256];
+    const double s = sum_partials_256(p, n, red);
+    if (threadIdx.x == 0) *loss = (float)(scale * s);
 }
 
 // Isotropic TV: n(x) = sqrt(sum_k d_k(x)^2 + eps) with d_k(x) = V(x + e_k) - V(x)
@@ -596,7 +571,7 @@ R2G_API r2g_status r2g_tv3d(int32_t G, int32_t D, const float* vol, float lambda
     const float inv_cnt = (float)(1.0 / ((double)D * D * (D - 1)));
     prof_begin(P_TV, stream);
     k_tv3d<<<(unsigned)blocks, 256, 0, stream>>>(vol, D, n, inv_cnt, lambda_tv, dvol, partials);
-    k_finalize<<<1, 256, 0, stream>>>(partials, (int)blocks, 1, lambda_tv * inv_cnt, 0.f, 0.f, loss);
+    k_tv_sum<<<1, 256, 0, stream>>>(partials, (int)blocks, lambda_tv * inv_cnt, loss);
     prof_end(P_TV, stream);
     note_launches(2);
     return check_launch("r2g_tv3d");

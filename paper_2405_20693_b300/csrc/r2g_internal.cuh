@@ -245,4 +245,62 @@ __device__ __forceinline__ unsigned long long block_sum_u64_256(unsigned long lo
     return t;
 }
 
+// ---------------------------------------------------------------- 3D TV (shared by r2g_tv3d and r2g_tv3d_noalloc)
+
+// Anisotropic 3D TV of G volumes [G][D][D][D] (n = G D^3 voxels) for the 256-thread
+// block blockIdx.x: voxel idx's gradient lam inv_cnt (sum of the signs of its
+// backward differences minus those of its forward ones) goes to grad[idx]; the
+// block's sum of |forward differences| is returned to thread 0.  red: shared [8].
+__device__ __forceinline__ float tv3d_block(const float* __restrict__ vol, int D, long long n, float inv_cnt,
+                                            float lam, float* __restrict__ grad, float* red) {
+    const long long idx = (long long)blockIdx.x * 256 + threadIdx.x;
+    float part = 0.f;
+    if (idx < n) {
+        const long long D3 = (long long)D * D * D;
+        const long long g = idx / D3;
+        const long long l = idx - g * D3;
+        const int z = (int)(l / ((long long)D * D)), y = (int)((l / D) % D), x = (int)(l % D);
+        const float* vg = vol + g * D3;
+        const float c = vg[l];
+        float gr = 0.f;
+        const long long st[3] = {1, D, (long long)D * D};
+        const int co[3] = {x, y, z};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (co[a] + 1 < D) {
+                const float d = vg[l + st[a]] - c;
+                part += fabsf(d);
+                gr -= (d > 0.f) ? 1.f : ((d < 0.f) ? -1.f : 0.f);
+            }
+            if (co[a] > 0) {
+                const float d = c - vg[l - st[a]];
+                gr += (d > 0.f) ? 1.f : ((d < 0.f) ? -1.f : 0.f);
+            }
+        }
+        grad[idx] = lam * inv_cnt * gr;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
+    __syncthreads();
+    float s = 0.f;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < 8; ++w) s += red[w];
+    return s;
+}
+
+// Sum of n per-block partials p[0..n) in FP64, in a fixed order (a strided sum per
+// thread, then a tree), by one 256-thread block; valid in thread 0.  red: shared [256].
+__device__ __forceinline__ double sum_partials_256(const float* __restrict__ p, int n, double* red) {
+    double s = 0.0;
+    for (int k = threadIdx.x; k < n; k += 256) s += p[k];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    return red[0];
+}
+
 }  // namespace r2g

@@ -15,10 +15,14 @@
 // stand-in: host code must not pass it to a kernel.  The first call on each
 // device (with that device current) looks up the array's device address with
 // cudaGetSymbolAddress and caches it; make that first call before any stream
-// capture.  All calls share the one array, which keeps the last call's
-// contents; every block overwrites its own partial before the final sum reads
-// it, so nothing has to be cleared between calls.  Calls whose kernels overlap
-// on the GPU (different streams, no ordering) race on the array.
+// capture.  The cached address belongs to the device's primary context: a
+// cudaDeviceReset, or a call from a different (non-primary) context on the same
+// device, may load the module again at another address, and the cached one is
+// then stale -- such callers must not use this entry point after the change.  All
+// calls share the one array, which keeps the last call's contents; every block
+// overwrites its own partial before the final sum reads it, so nothing has to be
+// cleared between calls.  Calls whose kernels overlap on the GPU (different
+// streams, no ordering) race on the array.
 #include <math.h>
 
 #include <mutex>
@@ -36,62 +40,22 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 float* g_addr[kMaxDevices] = {nullptr};
 
-// Same arithmetic as the workspace-based TV kernel: per voxel, the gradient from
-// its six neighbours, and a per-block partial of the sum of |forward differences|.
+// The workspace-based TV kernels' own per-voxel and per-block arithmetic and their
+// fixed-order final sum (tv3d_block, sum_partials_256), with the partials in the
+// fixed array: the same loss and gradient as r2g_tv3d, bit for bit.
 __global__ void __launch_bounds__(256) k_tv3d_static(const float* __restrict__ vol, int D, long long n,
                                                      float inv_cnt, float lam, float* __restrict__ grad,
                                                      float* __restrict__ partials) {
     __shared__ float red[8];
-    const long long idx = (long long)blockIdx.x * 256 + threadIdx.x;
-    float part = 0.f;
-    if (idx < n) {
-        const long long D3 = (long long)D * D * D;
-        const long long g = idx / D3;
-        const long long l = idx - g * D3;
-        const int z = (int)(l / ((long long)D * D)), y = (int)((l / D) % D), x = (int)(l % D);
-        const float* vg = vol + g * D3;
-        const float c = vg[l];
-        float gr = 0.f;
-        const long long st[3] = {1, D, (long long)D * D};
-        const int co[3] = {x, y, z};
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            if (co[a] + 1 < D) {
-                const float d = vg[l + st[a]] - c;
-                part += fabsf(d);
-                gr -= (d > 0.f) ? 1.f : ((d < 0.f) ? -1.f : 0.f);
-            }
-            if (co[a] > 0) {
-                const float d = c - vg[l - st[a]];
-                gr += (d > 0.f) ? 1.f : ((d < 0.f) ? -1.f : 0.f);
-            }
-        }
-        grad[idx] = lam * inv_cnt * gr;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float s = 0.f;
-        for (int w = 0; w < 8; ++w) s += red[w];
-        partials[blockIdx.x] = s;
-    }
+    const float s = tv3d_block(vol, D, n, inv_cnt, lam, grad, red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
-// One block sums the partials in a fixed order.
 __global__ void __launch_bounds__(256) k_tv_sum_static(const float* __restrict__ p, int n, float scale,
                                                        float* __restrict__ loss) {
     __shared__ double red[256];
-    double s = 0.0;
-    for (int k = threadIdx.x; k < n; k += 256) s += p[k];
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) *loss = (float)(scale * red[0]);
+    const double s = sum_partials_256(p, n, red);
+    if (threadIdx.x == 0) *loss = (float)(scale * s);
 }
 
 // Device address of the static array on the current device (looked up once per device).
