@@ -1171,6 +1171,59 @@ def run_ours(args, rank, world, local_rank):
             print(json.dumps({"volume_metrics": measure_metrics(dev), "limited_angle": measure_limited_angle(dev),
                               "adaptive_control": measure_adaptive(dev)}), flush=True)
         return
+    if args.profile_step:
+        # the headline step with a chosen number of views, tile 32 x 32, for profiler captures:
+        # --warmup steps, then --steps steps inside an NVTX range named "step"
+        import torch
+
+        from paper_2405_20693_b300 import engine, r2g
+
+        one = args.profile_workload == "one_scan"
+        if one:  # the one-scan step: 50k Gaussians, one view and one patch per step, 32 x 32 tiles
+            G, cam, views_np, meas_np = make_workload(seed, dev)
+            sc = engine.Scan(G, views_np, meas_np, cam, n_out=N_OUT, D=D_TV, device=dev)
+        else:
+            G, cam, views_np, meas_np = make_scale_workload(seed, dev)
+            keep = np.linspace(0, SCALE_V - 1, args.scale_views).round().astype(int)
+            views_np, meas_np = views_np[keep], meas_np[keep]
+            sc = engine.Scan(G, views_np, meas_np, cam, n_out=N_OUT, D=D_TV, device=dev, headroom=1.25,
+                             all_views=True, n_patches=SCALE_NP, full_volume=True, tile=(32, 32))
+        n = args.warmup + args.steps
+        origins = torch.as_tensor(scale_patch_origins(seed, n), device=dev)
+        tab = torch.zeros((n, 8), dtype=torch.int32, device=dev)
+        tab[:, 1] = torch.arange(n, dtype=torch.int32, device=dev)
+        if one:  # the one-scan step sequence: view and patch origin per step
+            seq = step_sequence(seed, n)
+            tnp = np.zeros((n, 8), np.int32)
+            for k, (v, off) in enumerate(seq):
+                tnp[k, 0], tnp[k, 1] = v, k
+                tnp[k, 2:5] = np.asarray([-1.0 + o * (2.0 / N_OUT) for o in off], np.float32).view(np.int32)
+            tab = torch.as_tensor(tnp, device=dev)
+        stream = torch.cuda.current_stream()
+        for k in range(n):
+            if k == args.warmup:
+                torch.cuda.synchronize()
+                torch.cuda.nvtx.range_push("step")
+                e0 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            if not one:
+                sc.job.patch_origins = origins.data_ptr() + k * 12 * SCALE_NP
+            r2g.r2g_train_step(sc.job, tab.data_ptr() + 32 * k, stream)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        # gated pixel pairs of the last step's view set (a counting run after the range)
+        mean, scale, quat, rho = sc.state.params()
+        vsel = sc.views[seq[n - 1][0]:seq[n - 1][0] + 1] if one else sc.views
+        sc.rast.forward(mean, scale, quat, rho, vsel, sc.image, check=True, count=True)
+        if rank == 0:
+            print(json.dumps({"profile_step": {"workload": args.profile_workload,
+                                               "views": 1 if one else int(args.scale_views),
+                                               "ms_per_step": e0.elapsed_time(e1) / args.steps,
+                                               "pixel_pairs": int(sc.rast.pair_count()),
+                                               "overflow": bool(sc.overflowed())}}), flush=True)
+        return
     if args.serving_full:
         if rank == 0:
             out = measure_serving(dev, n_requests=64, mean_interarrival_s=2.0, max_iters=30000, check_every=500)
@@ -1244,6 +1297,11 @@ def main():
                     help="skip the multi-scan scans/hour, serving and FDK-initialisation measurements")
     ap.add_argument("--fdk-only", action="store_true",
                     help="time only the FDK initialisation of the workload's scan (--steps runs)")
+    ap.add_argument("--profile-step", action="store_true",
+                    help="run only the headline step (--scale-views views, tile 32x32) for profiler captures")
+    ap.add_argument("--scale-views", type=int, default=SCALE_V, help="views of the --profile-step workload")
+    ap.add_argument("--profile-workload", choices=["scale", "one_scan"], default="scale",
+                    help="the --profile-step workload: the headline step or the one-scan step")
     ap.add_argument("--serving-full", action="store_true",
                     help="run only the 64-request serving stream to 35 dB or 30k iterations (minutes)")
     ap.add_argument("--extras-only", action="store_true",
