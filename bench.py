@@ -436,22 +436,36 @@ def _ncu_summary():
         return None
 
 
-def _current(t, kernel: str) -> bool:
-    return bool(t) and kernel in KERNEL_SOURCES and t.get("source_hashes", {}).get(kernel) == source_hash(kernel)
+def _entry(t, kernel: str, workload: str | None):
+    """The summary's (source hash, per-workload section) for a kernel: the headline
+    and one-scan kernels under "workloads", the auxiliary kernels under "other"."""
+    if not t:
+        return None, None
+    if workload is not None:
+        return t.get("source_hashes", {}).get(kernel), t.get("workloads", {}).get(workload, {})
+    o = t.get("other", {})
+    return o.get("source_hashes", {}).get(kernel), o
 
 
-def ncu_traffic(kernel: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+def _current(t, kernel: str, workload: str | None) -> bool:
+    h, _ = _entry(t, kernel, workload)
+    return kernel in KERNEL_SOURCES and h is not None and h == source_hash(kernel)
+
+
+def ncu_traffic(kernel: str, workload: str | None = None):
+    """DRAM bytes per launch from the committed ncu summary of the workload ("scale":
+    the headline step, "one_scan"; None: the auxiliary kernels), if it was taken on
     the kernel's current sources; else None."""
     t = _ncu_summary()
-    return t["kernels"].get(kernel) if _current(t, kernel) else None
+    return _entry(t, kernel, workload)[1].get("kernels", {}).get(kernel) if _current(t, kernel, workload) else None
 
 
-def ncu_pipes(kernel: str):
+def ncu_pipes(kernel: str, workload: str | None = None):
     """FMA and XU (MUFU) pipe utilisation (% of peak sustained) of the kernel from the
-    committed ncu summary, if it was taken on the kernel's current sources; else None."""
+    committed ncu summary of the workload, if it was taken on the kernel's current
+    sources; else None."""
     t = _ncu_summary()
-    return t.get("pipes", {}).get(kernel) if _current(t, kernel) else None
+    return _entry(t, kernel, workload)[1].get("pipes", {}).get(kernel) if _current(t, kernel, workload) else None
 
 
 def measure_batched(dev, rounds=20, n_scans=16, seed=5):
@@ -798,7 +812,7 @@ def slowest(dist, seconds: float, device) -> float:
     return float(tt[0])
 
 
-def splat_roofline(name: str, units: float, avg_ms: float, pk: dict) -> dict:
+def splat_roofline(name: str, units: float, avg_ms: float, pk: dict, workload: str) -> dict:
     """ALU roofline of a splat kernel: units (gated pairs per launch) / mean launch
     time, against min(MUFU ex2 rate, FP32 rate / ops per pair) at the maximum SM
     clock, charging the scope table's ops per pair (forward 10, backward 20); the
@@ -814,7 +828,7 @@ def splat_roofline(name: str, units: float, avg_ms: float, pk: dict) -> dict:
     return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "Gpair/s", "frac": ach / peak,
             "ops_per_pair": ops, "frac_own_ops": ach / peak_own, "own_ops_per_pair": own,
             "ms_per_launch": avg_ms, "units_per_launch": units,
-            "traffic": ncu_traffic(name), "pipes_pct_of_peak": ncu_pipes(name),
+            "traffic": ncu_traffic(name, workload), "pipes_pct_of_peak": ncu_pipes(name, workload),
             "peak_note": f"min(MUFU ex2 {MUFU_PER_CLK}/clk/SM, FP32 {FP32_PER_CLK}/clk/SM / {ops} ops) x {SM_COUNT} "
                          f"SMs x {pk['sm_max_mhz']:.0f} MHz (of measured sm_max_mhz; no FP32 peak is measured)"}
 
@@ -1002,13 +1016,13 @@ def measure_scale(args, dev, dist, seed, world):
     for name in ("splat_fwd", "splat_bwd"):
         n, t = prof[name]
         if n:
-            roofs[name] = splat_roofline(name, float(pix), t / n, pk)
+            roofs[name] = splat_roofline(name, float(pix), t / n, pk, "scale")
     if dom in roofs:
         roof = roofs[dom]
     else:
         n, t = prof[dom]
         roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": None, "traffic": ncu_traffic(dom), "ms_per_launch": t / max(n, 1)}
+                "frac": None, "traffic": ncu_traffic(dom, "scale"), "ms_per_launch": t / max(n, 1)}
     return {
         "value": value, "ms_per_step": ms_job / args.steps, "pairs_per_step": total_pairs / args.steps,
         "e2e": {"value": pairs_job / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": feed.bytes_in,
@@ -1138,7 +1152,7 @@ def measure_one_scan(args, dev, dist, seed):
     assert n_read == args.steps and np.isfinite(loss_sum)
     pk = peaks()
     per_step_pix = sum(pix) / args.steps
-    roofs = {name: splat_roofline(name, per_step_pix, t / n, pk) for name, (n, t) in prof.items() if n}
+    roofs = {name: splat_roofline(name, per_step_pix, t / n, pk, "one_scan") for name, (n, t) in prof.items() if n}
     return {"value": pairs_job / (ms_job * 1e-3), "unit": "pairs/s", "ms_per_step": ms_job / args.steps,
             "e2e": {"value": pairs_job / e2e_s, "unit": "pairs/s", "h2d_bytes_per_step": feed.bytes_in,
                     "d2h_bytes_per_step": 8},
