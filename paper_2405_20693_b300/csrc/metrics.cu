@@ -11,11 +11,12 @@
 //
 //   k_transpose_zyx  copies of both volumes in [x][z][y] order, so that sagittal
 //                 slices are read like the others (rows contiguous);
-//   k_slice_ssim  one CTA per 32 x 32 output tile of one slice of one orientation:
-//                 both volumes' tiles staged with a 5-voxel halo (zeros outside
-//                 the slice), the window applied separably to a, b, a^2, b^2, ab,
-//                 the SSIM term summed over the tile's in-slice pixels (double)
-//                 into a per-tile partial;
+//   k_slice_ssim  one CTA (128 threads) per 32 x 32 output tile of one slice of
+//                 one orientation: both volumes' tiles staged with a 5-voxel halo
+//                 (zeros outside the slice), the window applied separably to a, b,
+//                 a^2, b^2, ab with register-blocked runs (4 columns, 8 rows per
+//                 thread), the SSIM term summed over the tile's in-slice pixels
+//                 (double) into a per-tile partial;
 //   k_sq_err      per-CTA partial sums of (a - b)^2 (double), grid-stride;
 //   k_metrics_fin one CTA sums the partials in a fixed order (deterministic).
 #include <math.h>
@@ -28,7 +29,7 @@ namespace {
 constexpr int kMT = 32;              // output tile edge
 constexpr int kMR = 5;               // window radius
 constexpr int kMS = kMT + 2 * kMR;   // staged edge
-constexpr int kMetThreads = 256;
+constexpr int kMetThreads = 128;
 constexpr int kSqBlocks = 148 * 4;
 constexpr float kMC1 = 1e-4f, kMC2 = 9e-4f;
 
@@ -47,6 +48,16 @@ struct Orients {
     Orient o[3];
 };
 
+// Register-blocked separable window: the horizontal pass gives each thread a run of
+// kMHR output columns of one staged row (the 14 inputs loaded once, their three
+// products formed once), the vertical pass a run of kMVR output rows of one column
+// (each of the 18 staged rows of the five moments loaded once).  Each output still
+// accumulates its taps in window order, k = 0 .. 10, so the filtered moments are
+// those of the tap-by-tap loop.
+constexpr int kMHR = 4;  // output columns per thread, horizontal pass
+constexpr int kMVR = 8;  // output rows per thread, vertical pass
+static_assert(kMetThreads == kMT * (kMT / kMVR), "one vertical run per thread");
+
 __global__ void __launch_bounds__(kMetThreads) k_slice_ssim(const float* __restrict__ a, const float* __restrict__ b,
                                                             const float* __restrict__ ta,
                                                             const float* __restrict__ tb, Orients os, MWin win,
@@ -63,57 +74,92 @@ __global__ void __launch_bounds__(kMetThreads) k_slice_ssim(const float* __restr
     const int r0 = (tile / o.tiles_x) * kMT, c0 = (tile % o.tiles_x) * kMT;
     const float* pa = (oi == 2 ? ta : a) + (long long)s * o.ss;
     const float* pb = (oi == 2 ? tb : b) + (long long)s * o.ss;
-    const int tid = threadIdx.x;
-    for (int i = tid; i < kMS * kMS; i += kMetThreads) {
-        const int r = i / kMS, c = i - r * kMS;
-        const int gr = r0 + r - kMR, gc = c0 + c - kMR;
-        float va = 0.f, vb = 0.f;
-        if (gr >= 0 && gr < o.H && gc >= 0 && gc < o.W) {
-            const long long off = (long long)gr * o.sr + (long long)gc * o.sc;
-            va = pa[off];
-            vb = pb[off];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // staging: a warp per row (rows warp, warp + 4, ...), the lanes along it (two
+    // passes cover the 42 columns), all of a thread's loads issued before its stores
+    {
+        const int gc0 = c0 - kMR + lane, gc1 = gc0 + 32;
+        const bool in0 = gc0 >= 0 && gc0 < o.W, in1 = lane < kMS - 32 && gc1 >= 0 && gc1 < o.W;
+#pragma unroll 2
+        for (int r = warp; r < kMS; r += kMetThreads / 32) {
+            const int gr = r0 + r - kMR;
+            const bool rin = gr >= 0 && gr < o.H;
+            const long long ro = (long long)gr * o.sr;
+            const float va0 = rin && in0 ? pa[ro + (long long)gc0 * o.sc] : 0.f;
+            const float vb0 = rin && in0 ? pb[ro + (long long)gc0 * o.sc] : 0.f;
+            const float va1 = rin && in1 ? pa[ro + (long long)gc1 * o.sc] : 0.f;
+            const float vb1 = rin && in1 ? pb[ro + (long long)gc1 * o.sc] : 0.f;
+            sa[r][lane] = va0;
+            sb[r][lane] = vb0;
+            if (lane < kMS - 32) {
+                sa[r][lane + 32] = va1;
+                sb[r][lane + 32] = vb1;
+            }
         }
-        sa[r][c] = va;
-        sb[r][c] = vb;
     }
     __syncthreads();
     // horizontal pass: h[m][r][c] = sum_k w_k P_m(r, c + k), c over the 32 output columns
-    for (int i = tid; i < kMS * kMT; i += kMetThreads) {
-        const int r = i / kMT, c = i - r * kMT;
-        float m0 = 0.f, m1 = 0.f, m2 = 0.f, m3 = 0.f, m4 = 0.f;
+    for (int item = tid; item < kMS * (kMT / kMHR); item += kMetThreads) {
+        const int r = item / (kMT / kMHR), cb = (item - r * (kMT / kMHR)) * kMHR;
+        float m0[kMHR], m1[kMHR], m2[kMHR], m3[kMHR], m4[kMHR];
 #pragma unroll
-        for (int k = 0; k < 11; ++k) {
-            const float x = sa[r][c + k], y = sb[r][c + k], w = win.w[k];
-            m0 = fmaf(w, x, m0);
-            m1 = fmaf(w, y, m1);
-            m2 = fmaf(w, x * x, m2);
-            m3 = fmaf(w, y * y, m3);
-            m4 = fmaf(w, x * y, m4);
+        for (int i = 0; i < kMHR; ++i) m0[i] = m1[i] = m2[i] = m3[i] = m4[i] = 0.f;
+#pragma unroll
+        for (int j = 0; j < kMHR + 10; ++j) {
+            const float x = sa[r][cb + j], y = sb[r][cb + j];
+            const float xx = x * x, yy = y * y, xy = x * y;
+#pragma unroll
+            for (int i = 0; i < kMHR; ++i) {
+                const int k = j - i;  // tap of input j for output i (compile time)
+                if (k >= 0 && k <= 10) {
+                    const float w = win.w[k];
+                    m0[i] = fmaf(w, x, m0[i]);
+                    m1[i] = fmaf(w, y, m1[i]);
+                    m2[i] = fmaf(w, xx, m2[i]);
+                    m3[i] = fmaf(w, yy, m3[i]);
+                    m4[i] = fmaf(w, xy, m4[i]);
+                }
+            }
         }
-        h[0][r][c] = m0;
-        h[1][r][c] = m1;
-        h[2][r][c] = m2;
-        h[3][r][c] = m3;
-        h[4][r][c] = m4;
+#pragma unroll
+        for (int i = 0; i < kMHR; ++i) {
+            h[0][r][cb + i] = m0[i];
+            h[1][r][cb + i] = m1[i];
+            h[2][r][cb + i] = m2[i];
+            h[3][r][cb + i] = m3[i];
+            h[4][r][cb + i] = m4[i];
+        }
     }
     __syncthreads();
-    float part = 0.f;
-    for (int i = tid; i < kMT * kMT; i += kMetThreads) {
-        const int r = i / kMT, c = i - r * kMT;
-        if (r0 + r >= o.H || c0 + c >= o.W) continue;
-        float mx = 0.f, my = 0.f, exx = 0.f, eyy = 0.f, exy = 0.f;
+    // vertical pass: column c, output rows rb .. rb + kMVR - 1
+    const int c = tid % kMT, rb = (tid / kMT) * kMVR;
+    float mx[kMVR], my[kMVR], exx[kMVR], eyy[kMVR], exy[kMVR];
 #pragma unroll
-        for (int k = 0; k < 11; ++k) {
-            const float w = win.w[k];
-            mx = fmaf(w, h[0][r + k][c], mx);
-            my = fmaf(w, h[1][r + k][c], my);
-            exx = fmaf(w, h[2][r + k][c], exx);
-            eyy = fmaf(w, h[3][r + k][c], eyy);
-            exy = fmaf(w, h[4][r + k][c], exy);
+    for (int i = 0; i < kMVR; ++i) mx[i] = my[i] = exx[i] = eyy[i] = exy[i] = 0.f;
+#pragma unroll
+    for (int j = 0; j < kMVR + 10; ++j) {
+        const float v0 = h[0][rb + j][c], v1 = h[1][rb + j][c], v2 = h[2][rb + j][c], v3 = h[3][rb + j][c],
+                    v4 = h[4][rb + j][c];
+#pragma unroll
+        for (int i = 0; i < kMVR; ++i) {
+            const int k = j - i;
+            if (k >= 0 && k <= 10) {
+                const float w = win.w[k];
+                mx[i] = fmaf(w, v0, mx[i]);
+                my[i] = fmaf(w, v1, my[i]);
+                exx[i] = fmaf(w, v2, exx[i]);
+                eyy[i] = fmaf(w, v3, eyy[i]);
+                exy[i] = fmaf(w, v4, exy[i]);
+            }
         }
-        const float sxx = exx - mx * mx, syy = eyy - my * my, sxy = exy - mx * my;
-        const float num = (2.f * mx * my + kMC1) * (2.f * sxy + kMC2);
-        const float den = (mx * mx + my * my + kMC1) * (sxx + syy + kMC2);
+    }
+    float part = 0.f;
+#pragma unroll
+    for (int i = 0; i < kMVR; ++i) {
+        if (r0 + rb + i >= o.H || c0 + c >= o.W) continue;
+        const float sxx = exx[i] - mx[i] * mx[i], syy = eyy[i] - my[i] * my[i], sxy = exy[i] - mx[i] * my[i];
+        const float num = (2.f * mx[i] * my[i] + kMC1) * (2.f * sxy + kMC2);
+        const float den = (mx[i] * mx[i] + my[i] * my[i] + kMC1) * (sxx + syy + kMC2);
         part += num / den;
     }
     double v = part;

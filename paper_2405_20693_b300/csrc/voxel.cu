@@ -7,8 +7,9 @@
 //                  units, the quadratic form pre-scaled by -log2(e)/2.
 //   emit / sort    (brick, Gaussian id) entries, stable radix sort, brick ranges.
 //   k_vox_fwd      one CTA (128 threads) per work item (a brick's list cut into
-//                  chunks of 32 records); records staged in shared memory; each
-//                  thread owns a run of 4 voxels along x; a warp (two z-slices)
+//                  chunks of 32 records, 128 for grids of 2368+ bricks);
+//                  records staged in shared memory; each thread owns a run of
+//                  4 voxels along x; a warp (two z-slices)
 //                  skips records whose z span misses it; in a multi-chunk brick
 //                  the last chunk to finish sums the chunk volumes in chunk
 //                  order.  An empty brick's work item writes zeros.
@@ -240,8 +241,7 @@ __global__ void __launch_bounds__(kVoxThreads) k_vox_fwd(const float4* __restric
                                                          const uint32_t* __restrict__ item_off,
                                                          uint32_t* __restrict__ key_done, long long M,
                                                          const __grid_constant__ Grids grids, float Tq,
-                                                         float* __restrict__ vol, WsStatus* st) {
-    static_assert(kVoxChunk <= kVoxThreads, "one staging batch per item");
+                                                         uint32_t chunk_len, float* __restrict__ vol, WsStatus* st) {
     __shared__ float4 s_r[kVoxThreads][4];
     __shared__ int s_last;
     const unsigned long long it = blockIdx.x;
@@ -265,9 +265,9 @@ __global__ void __launch_bounds__(kVoxThreads) k_vox_fwd(const float4* __restric
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
     unsigned int cnt = 0;
     const uint2 rg = ranges[brick];
-    const uint32_t start = rg.x + chunk * kVoxChunk;
-    const uint32_t end = min(start + (uint32_t)kVoxChunk, rg.y);
-    const uint32_t nch = (rg.y - rg.x + kVoxChunk - 1) / kVoxChunk;
+    const uint32_t start = rg.x + chunk * chunk_len;
+    const uint32_t end = min(start + chunk_len, rg.y);
+    const uint32_t nch = (rg.y - rg.x + chunk_len - 1) / chunk_len;
     for (uint32_t base = start; base < end; base += kVoxThreads) {
         const int n = min((uint32_t)kVoxThreads, end - base);
         __syncthreads();
@@ -666,9 +666,16 @@ struct VTail {
     long long icap;
 };
 
+// List entries per brick work item of the forward: kVoxChunk for small grids (TV
+// patches: enough items to fill the GPU), kVoxChunkLarge once the bricks alone give
+// several waves (a full volume), where longer items mean fewer per-chunk volumes to
+// write and sum.
+constexpr int kVoxChunkLarge = 128;
+inline int vox_chunk(long long n_bricks) { return n_bricks >= 148 * 16 ? kVoxChunkLarge : kVoxChunk; }
+
 VTail vox_tail(const VoxLayout& L, long long cap) {
     VTail t;
-    t.icap = items_capacity(L.n_bricks, cap, kVoxChunk);
+    t.icap = items_capacity(L.n_bricks, cap, vox_chunk(L.n_bricks));
     Layout lay;
     lay.off = L.fixed;
     t.a = lay.take(8 * (size_t)cap);
@@ -681,7 +688,7 @@ VTail vox_tail(const VoxLayout& L, long long cap) {
 
 long long vox_capacity(const VoxLayout& L, size_t ws_bytes) {
     if (ws_bytes <= L.fixed) return 0;
-    const double per = 16.0 + (8.0 + 4.0 * kB * kB * kB) / kVoxChunk;
+    const double per = 16.0 + (8.0 + 4.0 * kB * kB * kB) / vox_chunk(L.n_bricks);
     const double fixed_tail = (double)L.n_bricks * (8.0 + 4.0 * kB * kB * kB) + 4096.0;
     const double est = ((double)(ws_bytes - L.fixed) - fixed_tail) / per;
     long long cap = est > 0 ? ((long long)est / 32) * 32 : 0;
@@ -767,17 +774,19 @@ r2g_status voxelize_impl(int64_t M, const float* mean, const float* scale, const
     }
     int launches = 0;
     uint64_t* sorted = build_lists(op, L.n_rec, L.n_bricks, partials, st, a, b, scratch, cap, ranges, key_done,
-                                   item_st, item_off, items, T.icap, kVoxChunk,
+                                   item_st, item_off, items, T.icap, vox_chunk(L.n_bricks),
                                    ListProf{P_VOX_EMIT, P_VOX_SORT, P_VOX_RANGES}, stream, &launches, !separate_lists);
     const float Tq = -0.5f * kLog2e * Q3;
     note_launches(1 + launches + 1);
     prof_begin(P_VOX_FWD, stream);
     if (count)
         k_vox_fwd<true><<<(unsigned)T.icap, kVoxThreads, 0, stream>>>(rec, ranges, sorted, items, item_st, partial,
-                                                                       item_off, key_done, M, gr, Tq, vol, st);
+                                                                       item_off, key_done, M, gr, Tq,
+                                                                       (uint32_t)vox_chunk(L.n_bricks), vol, st);
     else
         k_vox_fwd<false><<<(unsigned)T.icap, kVoxThreads, 0, stream>>>(rec, ranges, sorted, items, item_st, partial,
-                                                                        item_off, key_done, M, gr, Tq, vol, st);
+                                                                        item_off, key_done, M, gr, Tq,
+                                                                        (uint32_t)vox_chunk(L.n_bricks), vol, st);
     prof_end(P_VOX_FWD, stream);
     return check_launch("r2g_voxelize");
 }
