@@ -410,16 +410,52 @@ struct FwdShape {
 constexpr int kFwdMaxBlocks = 8;   // warp blocks per tile at most (32 x 32 tiles)
 constexpr int kFwdWarps = 4;       // independent warps per CTA
 
+// Whether the gate of a record can reach a rectangle of pixel centres [x0, x1] x
+// [y0, y1] (a superset test: false only when no point of the rectangle has t >=
+// Tc, Tc a little below the gate).  t(dx, dy) = A dx^2 + B dx dy + C dy^2 is concave
+// with its maximum at the centre, and t(l p) = l^2 t(p) >= t(p) for 0 < l <= 1, so
+// when the centre lies outside the rectangle the maximum over it lies on an edge
+// whose line separates the two -- at most one vertical and one horizontal edge,
+// each maximised over its segment in closed form.  A conic that is not clearly
+// negative definite (where FP32 rounding of t could exceed the margin) is always
+// kept.  The edge maxima use the approximate reciprocal: near its maximum t is flat
+// (an error e in the abscissa changes t by C e^2), far below the margin.
+__device__ __forceinline__ bool gate_meets_rect(float4 a, float4 b, float x0, float x1, float y0, float y1,
+                                                float Tc) {
+    const float A = a.z, B = a.w, C = b.x;
+    const float ac4 = 4.0f * A * C;
+    if (!(A < 0.0f && C < 0.0f && ac4 - B * B > 0x1p-10f * ac4)) return true;
+    const float X0 = x0 - a.x, X1 = x1 - a.x, Y0 = y0 - a.y, Y1 = y1 - a.y;
+    const bool inx = X0 <= 0.0f && X1 >= 0.0f, iny = Y0 <= 0.0f && Y1 >= 0.0f;
+    if (inx && iny) return true;
+    float best = -INFINITY;
+    if (!inx) {  // the vertical edge facing the centre: max over dy of C dy^2 + B xe dy + A xe^2
+        const float xe = X0 > 0.0f ? X0 : X1;
+        const float dy = fminf(fmaxf(-B * xe * rcp_fast(2.0f * C), Y0), Y1);
+        best = fmaf(fmaf(A, xe, B * dy), xe, C * dy * dy);
+    }
+    if (!iny) {  // the horizontal edge facing the centre
+        const float ye = Y0 > 0.0f ? Y0 : Y1;
+        const float dx = fminf(fmaxf(-B * ye * rcp_fast(2.0f * A), X0), X1);
+        best = fmaxf(best, fmaf(fmaf(A, dx, B * ye), dx, C * ye * ye));
+    }
+    return best >= Tc;
+}
+// The margin below the gate of the culling test, in units of t (log2 of the
+// weight): far above the FP32 rounding of t for the conics it is applied to.
+constexpr float kCullMargin = 0.0625f;
+
 // One warp per (work item, warp block): the item's <= 128 records of one tile are
-// read by the warp's lanes (four each), the records whose box meets the warp's
-// 8 x BW pixel block are compacted (ballot) into the warp's shared-memory list, and
+// read by the warp's lanes (four each), the records whose box and gate meet the
+// warp's 8 x BW pixel block are compacted (ballot) into the warp's shared-memory
+// list (a record whose gate misses the block would add nothing to it), and
 // each lane accumulates its PX pixels over that list -- the quadratic is one FMA per
 // pixel (t0 + k (g + A k)).  The warps of a CTA share nothing (no block barrier).
 // A tile with several chunks: each chunk's warp writes its block of the chunk image;
 // the last chunk of a block to finish (per-(tile, block) arrival counter) sums the
 // block's chunk images in chunk order (deterministic).
 template <int TW, int TH, bool COUNT>
-__global__ void __launch_bounds__(32 * kFwdWarps) k_splat_fwd(const float4* __restrict__ rec,
+__global__ void __launch_bounds__(32 * kFwdWarps, 9) k_splat_fwd(const float4* __restrict__ rec,
                                                               const float4* __restrict__ srec,
                                                               const uint2* __restrict__ ranges,
                                                               const uint64_t* __restrict__ sorted,
@@ -511,6 +547,32 @@ __global__ void __launch_bounds__(32 * kFwdWarps) k_splat_fwd(const float4* __re
         m += __popc(bal);
     }
     __syncwarp();
+    // of those, keep the records whose gate meets the block (in place, in order: a
+    // kept record moves to a position no later than its own, after its round of 32
+    // has been read)
+    {
+        const int mb = m;
+        m = 0;
+        for (int q0 = 0; q0 < mb; q0 += 32) {
+            const int q = q0 + lane;
+            float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+            bool keep = false;
+            if (q < mb) {
+                a = s_a[warp][q];
+                b = s_b[warp][q];
+                keep = gate_meets_rect(a, b, (float)gx0, (float)(gx0 + BW - 1), (float)gy0, (float)(gy0 + 7),
+                                       Tq - kCullMargin);
+            }
+            const uint32_t bal = __ballot_sync(0xffffffffu, keep);
+            if (keep) {
+                const int pos = m + __popc(bal & ((1u << lane) - 1u));
+                s_a[warp][pos] = a;
+                s_b[warp][pos] = b;
+            }
+            m += __popc(bal);
+            __syncwarp();
+        }
+    }
     float acc[PX];
 #pragma unroll
     for (int k = 0; k < PX; ++k) acc[k] = 0.0f;
