@@ -665,11 +665,51 @@ __device__ __forceinline__ uint32_t cta_excl_scan_128(uint32_t v, uint32_t* s_w,
     return before + incl - v;
 }
 
+// The bounding box of a record's gate inside a rectangle of pixel centres (tile-
+// local columns c0..c1, rows r0..r1; centre xc, yc), narrowed in place: columns to
+// the x-extent of the gate t >= Tc over the rows, then rows to its y-extent over
+// those columns (a superset of the gated pixels for Tc a little below the gate).
+// Over a strip of rows the gate's left end bh dy - hh sqrt(K0 - K2 dy^2) is convex
+// in dy, its minimum at the row of the gate's leftmost point (dy = B ex / (2C), ex
+// its half-width) clamped to the strip; the right end and the y-extent likewise
+// (K2 = 4AC - B^2, K0 = 4A Tc, hh = -1 / (2A)).  A conic that is not clearly
+// negative definite keeps its box.
+__device__ __forceinline__ void narrow_box(float4 a, float4 b, float xc, float yc, float Tc, int& c0, int& c1,
+                                           int& r0, int& r1) {
+    const float A = a.z, B = a.w, C = b.x;
+    const float ac4 = 4.0f * A * C, K2 = ac4 - B * B;
+    if (!(A < 0.0f && C < 0.0f && K2 > 0x1p-10f * ac4)) return;
+    const float iK2 = rcp_fast(K2);
+    {
+        const float K0 = 4.0f * A * Tc, hh = -0.5f * rcp_fast(A), bh = B * hh;
+        const float ex = sqrt_fast(4.0f * C * Tc * iK2);
+        const float dyl = B * ex * (0.5f * rcp_fast(C));
+        const float y0 = (float)r0 - yc, y1 = (float)r1 - yc;
+        const float dl = fminf(fmaxf(dyl, y0), y1), dr = fminf(fmaxf(-dyl, y0), y1);
+        const float xl = fmaf(bh, dl, -sqrt_fast(fmaxf(fmaf(-K2, dl * dl, K0), 0.0f)) * hh);
+        const float xr = fmaf(bh, dr, sqrt_fast(fmaxf(fmaf(-K2, dr * dr, K0), 0.0f)) * hh);
+        c0 = max(c0, (int)ceilf(xc + xl));
+        c1 = min(c1, (int)floorf(xc + xr));
+    }
+    {
+        const float K0 = 4.0f * C * Tc, hh = -0.5f * rcp_fast(C), bh = B * hh;
+        const float ey = sqrt_fast(4.0f * A * Tc * iK2);
+        const float dxt = B * ey * (0.5f * rcp_fast(A));
+        const float x0 = (float)c0 - xc, x1 = (float)c1 - xc;
+        const float dt = fminf(fmaxf(dxt, x0), x1), db = fminf(fmaxf(-dxt, x0), x1);
+        const float yl = fmaf(bh, dt, -sqrt_fast(fmaxf(fmaf(-K2, dt * dt, K0), 0.0f)) * hh);
+        const float yr = fmaf(bh, db, sqrt_fast(fmaxf(fmaf(-K2, db * db, K0), 0.0f)) * hh);
+        r0 = max(r0, (int)ceilf(yc + yl));
+        r1 = min(r1, (int)floorf(yc + yr));
+    }
+}
+
 // Backward unit: UW x UH pixels (columns x rows) of a record's box.
 constexpr int kBwdUnitW = 4, kBwdUnitH = 2;
 
 // One CTA per work item (<= 128 records of one tile).  Each record's pixel box
-// inside the tile, columns c0..c1 and h rows, is cut into ceil(h / UH) rows of
+// inside the tile, narrowed to the bounding box of its gate there (narrow_box),
+// columns c0..c1 and h rows, is cut into ceil(h / UH) rows of
 // units of UW x UH pixels whose columns start at multiples of UW (tile-local), so
 // that a unit row is one aligned vector load of the staged dL/dI.  A unit may
 // reach past the box: those pixels lie outside the box, where the gate t >= Tq
@@ -731,8 +771,10 @@ __global__ void __launch_bounds__(kBwdThreads) k_splat_bwd(const float4* __restr
         // the record next to the sorted entry (srec: independent of the id load), else gathered
         const float4 a = srec ? srec[2 * (size_t)e] : vrec[2 * (size_t)gid];
         const float4 b = srec ? srec[2 * (size_t)e + 1] : vrec[2 * (size_t)gid + 1];
-        const int c0 = max(0, (int)ceilf(a.x - b.z) - X0), c1 = min(TW - 1, (int)floorf(a.x + b.z) - X0);
-        const int r0 = max(0, (int)ceilf(a.y - b.w) - Y0), r1 = min(TH - 1, (int)floorf(a.y + b.w) - Y0);
+        int c0 = max(0, (int)ceilf(a.x - b.z) - X0), c1 = min(TW - 1, (int)floorf(a.x + b.z) - X0);
+        int r0 = max(0, (int)ceilf(a.y - b.w) - Y0), r1 = min(TH - 1, (int)floorf(a.y + b.w) - Y0);
+        if (c1 >= c0 && r1 >= r0)  // the gate's own bounding box inside the tile
+            narrow_box(a, b, a.x - (float)X0, a.y - (float)Y0, Tq - kCullMargin, c0, c1, r0, r1);
         const int w = c1 - c0 + 1, h = r1 - r0 + 1;
         if (w > 0 && h > 0) {
             const int ca = c0 & ~(UW - 1);  // first unit column, aligned
