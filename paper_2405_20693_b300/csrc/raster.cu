@@ -110,18 +110,24 @@ __device__ __forceinline__ void rotation(const float q[4], Proj& P) {
 }
 
 template <bool EXACT = true>
-__device__ __forceinline__ void project_stated(const float p[3], const float s[3], const float q[4],
-                                               const float* __restrict__ view, const CamF& cam, Proj& P) {
+__device__ __forceinline__ void rotation_scale(const float s[3], const float q[4], Proj& P) {
+    rotation<EXACT>(q, P);
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) P.Mm[j][k] = POps<EXACT>::mul(P.R[j][k], s[k]);
+}
+
+// The view-dependent part of the projection, after rotation_scale (R, M) of the
+// same Gaussian.
+template <bool EXACT = true>
+__device__ __forceinline__ void project_view(const float p[3], const float* __restrict__ view, const CamF& cam,
+                                             Proj& P) {
     using O = POps<EXACT>;
     const auto fm = O::mul;
     const auto fa = O::add;
     const auto fs = O::sub;
-    rotation<EXACT>(q, P);
     P.phx = P.phy = P.al = P.be = P.ga = P.det = 0.0f;
-#pragma unroll
-    for (int j = 0; j < 3; ++j)
-#pragma unroll
-        for (int k = 0; k < 3; ++k) P.Mm[j][k] = fm(P.R[j][k], s[k]);
 #pragma unroll
     for (int j = 0; j < 3; ++j)
         P.u[j] = fa(fa(fa(fm(view[3 * j], p[0]), fm(view[3 * j + 1], p[1])), fm(view[3 * j + 2], p[2])), view[9 + j]);
@@ -171,6 +177,13 @@ __device__ __forceinline__ void project_stated(const float p[3], const float s[3
         P.ga = fa(P.ga, cam.dil_y);
     }
     P.valid = P.det > 0.0f;
+}
+
+template <bool EXACT = true>
+__device__ __forceinline__ void project_stated(const float p[3], const float s[3], const float q[4],
+                                               const float* __restrict__ view, const CamF& cam, Proj& P) {
+    rotation_scale<EXACT>(s, q, P);
+    project_view<EXACT>(p, view, cam, P);
 }
 
 __device__ __forceinline__ float ceil_clamped(float x, int n) {
@@ -891,7 +904,7 @@ __device__ __forceinline__ void quat_grad(const float qn[4], float qnorm, const 
 // gradient already in adam.grad and take the Adam step of the Gaussian's eleven
 // parameters (every Gaussian, with or without moments).
 template <bool ADAM>
-__global__ void __launch_bounds__(128) k_project_bwd(Params G, const float* __restrict__ views,
+__global__ void __launch_bounds__(128, 4) k_project_bwd(Params G, const float* __restrict__ views,
                                                      const int* __restrict__ view_sel, CamF cam, float Q,
                                                      long long M, int V, const float4* __restrict__ rec,
                                                      float4* __restrict__ mom, float* __restrict__ dmean,
@@ -918,17 +931,26 @@ __global__ void __launch_bounds__(128) k_project_bwd(Params G, const float* __re
     float gp[3] = {0.f, 0.f, 0.f}, gs[3] = {0.f, 0.f, 0.f}, gR[3][3] = {{0.f}}, grho = 0.f;
     float dens_g = 0.f, dens_n = 0.f;  // adaptive-control statistics of this call
     Proj P;
+    rotation_scale<false>(s, q, P);  // the Gaussian's R and M, shared by its views
     bool have_rot = false;
+    // each view's moments and rho_hat are loaded one view ahead
+    float4 n0 = mom[2 * (size_t)i], n1 = mom[2 * (size_t)i + 1];
+    float n_rh = rec[2 * (size_t)i + 1].y;
     for (int v = 0; v < V; ++v) {
         const size_t r = (size_t)v * (size_t)M + (size_t)i;
-        const float4 m0 = mom[2 * r];
-        const float4 m1 = mom[2 * r + 1];
+        const float4 m0 = n0, m1 = n1;
+        const float rhohat = n_rh;
+        if (v + 1 < V) {
+            const size_t rn = r + (size_t)M;
+            n0 = mom[2 * rn];
+            n1 = mom[2 * rn + 1];
+            n_rh = rec[2 * rn + 1].y;
+        }
         if (m0.x == 0.f && m0.y == 0.f && m0.z == 0.f && m0.w == 0.f && m1.x == 0.f && m1.y == 0.f) continue;
         mom[2 * r] = make_float4(0.f, 0.f, 0.f, 0.f);  // consumed: the next backward starts at zero
         mom[2 * r + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
-        const float rhohat = rec[2 * r + 1].y;
         const float* view = views + 12 * (view_sel ? view_sel[v] : v);
-        project_stated<false>(p, s, q, view, cam, P);  // values only: no bound is formed here
+        project_view<false>(p, view, cam, P);  // values only: no bound is formed here
         have_rot = true;
         // --- moments -> gradients of the pixel-unit record
         const float D = P.det, id = rcp_fast(D);
