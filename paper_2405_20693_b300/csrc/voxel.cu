@@ -9,8 +9,9 @@
 //   k_vox_fwd      one CTA (128 threads) per work item (a brick's list cut into
 //                  chunks of 32 records, 128 for grids of 2368+ bricks);
 //                  records staged in shared memory; each thread owns a run of
-//                  4 voxels along x; a warp (two z-slices)
-//                  skips records whose z span misses it; in a multi-chunk brick
+//                  4 voxels along x; a warp (two z-slices) skips records whose
+//                  gate misses its slab (z span, then the gate's projections on
+//                  the xy, xz and yz planes); in a multi-chunk brick
 //                  the last chunk to finish sums the chunk volumes in chunk
 //                  order.  An empty brick's work item writes zeros.
 //   k_vox_bwd      one CTA per group of 16 consecutive sorted entries; the
@@ -231,8 +232,63 @@ __device__ __forceinline__ int grid_of_brick(const Grids& grids, long long brick
 
 constexpr int kVoxThreads = 128;
 
+// Whether the 2D concave quadratic t = a x^2 + b x y + c y^2 (centre at the origin)
+// reaches Tc somewhere on the rectangle [X0, X1] x [Y0, Y1]: the centre, or the
+// vertex of t on each edge that faces the centre (t(l d) = l^2 t(d) puts the
+// maximum over the rectangle on an edge whose line separates it from the centre).
+// A form that is not clearly negative definite reports true.
+__device__ __forceinline__ bool quad2_meets_rect(float a, float b, float c, float X0, float X1, float Y0, float Y1,
+                                                 float Tc) {
+    const float ac4 = 4.0f * a * c;
+    if (!(a < 0.0f && c < 0.0f && ac4 - b * b > 0x1p-10f * ac4)) return true;
+    const bool inx = X0 <= 0.0f && X1 >= 0.0f, iny = Y0 <= 0.0f && Y1 >= 0.0f;
+    if (inx && iny) return true;
+    float best = -INFINITY;
+    if (!inx) {
+        const float xe = X0 > 0.0f ? X0 : X1;
+        const float y = fminf(fmaxf(-b * xe * rcp_fast(2.0f * c), Y0), Y1);
+        best = fmaf(fmaf(a, xe, b * y), xe, c * y * y);
+    }
+    if (!iny) {
+        const float ye = Y0 > 0.0f ? Y0 : Y1;
+        const float x = fminf(fmaxf(-b * ye * rcp_fast(2.0f * a), X0), X1);
+        best = fmaxf(best, fmaf(fmaf(a, x, b * ye), x, c * ye * ye));
+    }
+    return best >= Tc;
+}
+
+// The margin below the gate of the voxel culling test, in units of t.
+constexpr float kVoxCullMargin = 0.25f;
+
+// Which of a brick's four two-slice slabs (warp w: slices 2w, 2w + 1) a record's
+// gate can reach, as a 4-bit mask: the record's z-span first, then its gate's
+// projections onto the xy, xz and yz planes (t maximised over the third coordinate:
+// a Schur complement of the form) against the slab's rectangles -- a gate that
+// misses one projection misses the slab.  lo/hi: the brick's voxel index ranges.
+__device__ __forceinline__ uint32_t slab_mask(const float4& r0, const float4& r1, const float4& r2, const float4& r3,
+                                             float bx0, float by0, float bz0, float Tc) {
+    const float A = r1.x, B = r1.y, C = r1.z, D = r1.w, E = r2.x, F = r2.y;
+    const float X0 = bx0 - r0.x, X1 = X0 + (float)(kB - 1), Y0 = by0 - r0.y, Y1 = Y0 + (float)(kB - 1);
+    uint32_t m = 0;
+    const bool xy = quad2_meets_rect(A - E * E * rcp_fast(4.0f * C), D - 2.0f * E * F * rcp_fast(4.0f * C),
+                                     B - F * F * rcp_fast(4.0f * C), X0, X1, Y0, Y1, Tc);
+    if (!xy) return 0u;
+    const float i4B = rcp_fast(4.0f * B), i4A = rcp_fast(4.0f * A);
+    const float axz = A - D * D * i4B, bxz = E - 2.0f * D * F * i4B, cxz = C - F * F * i4B;
+    const float ayz = B - D * D * i4A, byz = F - 2.0f * D * E * i4A, cyz = C - E * E * i4A;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        const float zw0 = bz0 + (float)(2 * w), zw1 = zw0 + 1.0f;
+        if (r0.z + r3.z < zw0 || r0.z - r3.z > zw1) continue;
+        const float Z0 = zw0 - r0.z, Z1 = zw1 - r0.z;
+        if (quad2_meets_rect(axz, bxz, cxz, X0, X1, Z0, Z1, Tc) && quad2_meets_rect(ayz, byz, cyz, Y0, Y1, Z0, Z1, Tc))
+            m |= 1u << w;
+    }
+    return m;
+}
+
 template <bool COUNT>
-__global__ void __launch_bounds__(kVoxThreads) k_vox_fwd(const float4* __restrict__ rec,
+__global__ void __launch_bounds__(kVoxThreads, 10) k_vox_fwd(const float4* __restrict__ rec,
                                                          const uint2* __restrict__ ranges,
                                                          const uint64_t* __restrict__ sorted,
                                                          const uint64_t* __restrict__ items,
@@ -243,6 +299,7 @@ __global__ void __launch_bounds__(kVoxThreads) k_vox_fwd(const float4* __restric
                                                          const __grid_constant__ Grids grids, float Tq,
                                                          uint32_t chunk_len, float* __restrict__ vol, WsStatus* st) {
     __shared__ float4 s_r[kVoxThreads][4];
+    __shared__ uint32_t s_m[kVoxThreads];  // slabs each staged record's gate can reach
     __shared__ int s_last;
     const unsigned long long it = blockIdx.x;
     // no work items past the count; none at all after a list build that gave up a wait
@@ -259,7 +316,6 @@ __global__ void __launch_bounds__(kVoxThreads) k_vox_fwd(const float4* __restric
     const int t = threadIdx.x;
     const int x0 = bx * kB + (t & 1) * 4, y = by * kB + ((t >> 1) & 7), z = bz * kB + (t >> 4);
     const int warp = t >> 5;
-    const float zw0 = (float)(bz * kB + 2 * warp), zw1 = zw0 + 1.0f;
     const float fx0 = (float)x0, fy = (float)y, fz = (float)z;
     const float4* grec = rec + 4 * (size_t)g * (size_t)M;
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
@@ -273,14 +329,18 @@ __global__ void __launch_bounds__(kVoxThreads) k_vox_fwd(const float4* __restric
         __syncthreads();
         if (t < n) {
             const uint32_t gid = (uint32_t)sorted[base + t];
+            float4 q[4];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) s_r[t][k] = grec[4 * (size_t)gid + k];
+            for (int k = 0; k < 4; ++k) q[k] = grec[4 * (size_t)gid + k];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) s_r[t][k] = q[k];
+            s_m[t] = slab_mask(q[0], q[1], q[2], q[3], (float)(bx * kB), (float)(by * kB), (float)(bz * kB),
+                               Tq - kVoxCullMargin);
         }
         __syncthreads();
         for (int j = 0; j < n; ++j) {
+            if (!((s_m[j] >> warp) & 1u)) continue;  // warp-uniform: the gate misses this warp's slab
             const float4 r0 = s_r[j][0];  // cx, cy, cz, rho
-            const float4 r3 = s_r[j][3];  // rx, ry, rz, ok
-            if (r0.z + r3.z < zw0 || r0.z - r3.z > zw1) continue;  // warp-uniform z cull
             const float4 r1 = s_r[j][1];  // A, B, C, D
             const float4 r2 = s_r[j][2];  // E, F
             const float dy = fy - r0.y, dz = fz - r0.z;
