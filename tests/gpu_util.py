@@ -37,9 +37,10 @@ def assert_values_close(gpu, ref, band, label=""):
     return err.max() / scale, int((band > 0).sum())
 
 
-def assert_grads_close(gpu, ref, label="", band=None, zero_scale=None):
+def assert_grads_close(gpu, ref, label="", band=None, zero_scale=None, tol=None):
     """Per parameter group: ||g - g_ref||_inf <= 1e-3 ||g_ref||_inf, and per element
-    |g - g_ref| <= 1e-3 |g_ref| where |g_ref| >= 1e-2 ||g_ref||_inf.  Both are widened by
+    |g - g_ref| <= 1e-3 |g_ref| where |g_ref| >= 1e-2 ||g_ref||_inf (tol: another bound
+    than 1e-3, for inputs whose FP32 conditioning is known to need it).  Both are widened by
     the oracle's gate-band bound (the summed |contribution| of pairs whose q is within
     1e-4 Q of the gate, which an FP32 gate may count on the other side).  A group that
     is exactly zero in the oracle (e.g. rotations of isotropic Gaussians) must be
@@ -52,12 +53,13 @@ def assert_grads_close(gpu, ref, label="", band=None, zero_scale=None):
         assert zero_scale is not None, f"{label}: zero reference"
         assert np.abs(gpu).max() <= 1e-6 * zero_scale, f"{label}: {np.abs(gpu).max():.3e} where 0 expected"
         return 0.0, 0.0
+    tol = TOL_GRAD if tol is None else tol
     err = np.abs(gpu - ref)
     rel = (err - band).max() / n
-    assert rel <= TOL_GRAD, f"{label}: group error {rel:.3e}"
+    assert rel <= tol, f"{label}: group error {rel:.3e}"
     big = np.abs(ref) >= 1e-2 * n
     el = ((err - 1.001 * band)[big] / np.abs(ref)[big]).max() if big.any() else 0.0
-    assert el <= TOL_GRAD, f"{label}: element error {el:.3e}"
+    assert el <= tol, f"{label}: element error {el:.3e}"
     return rel, el
 
 

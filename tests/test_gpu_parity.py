@@ -177,6 +177,48 @@ def test_rasterize_backward_matches_oracle_adjoint(case, tile):
         assert_grads_close(host(a), b, f"{case} d{name}", band=bd)
 
 
+def _needles(M, seed):
+    """Strongly anisotropic, randomly rotated Gaussians: per-axis scales log-uniform in
+    [0.003, 0.15] (needles, disks and blobs up to 50:1) and every tenth Gaussian a
+    needle or disk of 300:1 (one axis at 0.0005) with a small density.  The kernels'
+    gate tests then meet long, thin conics on both sides of their conditioning
+    threshold (a form with 4AC - B^2 below 2^-10 4AC keeps its box)."""
+    G = I.uniform_gaussians(M, seed, 0.003, 0.15, box=0.7)
+    g = I.rng(seed + 1000)
+    k = np.arange(0, M, 10)
+    G.scale[k, g.integers(0, 3, k.size)] = 0.0005
+    G.rho[k] = 0.02
+    return G
+
+
+@pytest.mark.parametrize("tile", [(16, 16), (32, 32)])
+def test_gate_culling_on_anisotropic_gaussians(tile):
+    """The forward's per-block gate test (a record whose gate misses a warp block is
+    dropped from its list) and the backward's narrowing of each record's box to its
+    gate's bounding box in the tile, on needles and disks against the oracle: the image
+    to the usual tolerance, the adjoint to 1e-2.  FP32 resolves the conics of 50:1 and
+    300:1 Gaussians, and with them the scale and mean gradients, only to ~2e-3 (measured
+    on these inputs with the kernels before the culling existed: 2.0-3.0e-3); a unit or
+    record the culling wrongly dropped would be an error of order one."""
+    cam = I.cone_camera(96, 112, pitch=I.CONE_PITCH * 512 / 112)
+    views = I.view_table(np.deg2rad([13.0, 71.0, 200.0]), I.CONE_L_SO)
+    vv = dev(views)
+    G = _needles(1500, 41)
+    rast = engine.Rasterizer(G.M, 3, cam, tile=tile)
+    mean, scale, quat, rho = dev_set(G)
+    img = rast.forward(mean, scale, quat, rho, vv)
+    torch.cuda.synchronize()
+    ref, _, band = core.render(G, views, cam, Q=Q9, want_band=True)
+    assert_values_close(host(img), ref, band, f"needles {tile}")
+    dimg = I.rng(42).standard_normal(ref.shape).astype(np.float32)
+    g = [torch.zeros_like(t) for t in (mean, scale, quat, rho)]
+    rast.backward(mean, scale, quat, rho, vv, dev(dimg), *g)
+    torch.cuda.synchronize()
+    rb, bb = core.render_backward(G, views, cam, dimg, Q=Q9, want_band=True)
+    for name, a, b, bd in zip(("mean", "scale", "quat", "rho"), g, rb, bb):
+        assert_grads_close(host(a), b, f"needles {tile} d{name}", band=bd, tol=1e-2)
+
+
 def test_config1_l1_gradient_against_oracle_targets():
     """Config 1 end to end: targets are the oracle's render of a second (seed 1) set;
     L1 loss gradients flow through the CUDA rasterizer backward."""
@@ -237,6 +279,21 @@ def test_voxelize_matches_oracle_and_brick_lists_bit_exact(kind):
     for b in range(nb):
         s, e = ranges[b]
         assert np.array_equal(ids[s:e].astype(np.int64), refl.get(b, np.zeros(0, np.int64))), b
+
+
+def test_voxel_slab_culling_on_anisotropic_gaussians():
+    """The voxel forward's slab test (a warp skips a record whose gate's projections
+    miss its two-slice slab) on needles and disks, with a 136^3 grid among the grids
+    (4,913 bricks: the 128-record work items) -- values and gated voxel count against
+    the oracle."""
+    G = _needles(800, 43)
+    gd = _f32grid(np.concatenate([_grids_small(), I.cube_grid(136)[None]]))
+    vox = engine.Voxelizer(G.M, gd)
+    vol = vox.forward(*dev_set(G), count=True)
+    torch.cuda.synchronize()
+    ref, pairs, band = core.voxelize(G, gd, Q3, want_band=True)
+    assert_values_close(host(vol), ref, band, "needles voxelize")
+    assert abs(vox.pair_count() - pairs) <= max(10, 1e-4 * pairs)
 
 
 @pytest.mark.parametrize("kind", ["small", "large"])
