@@ -767,10 +767,24 @@ __global__ void __launch_bounds__(kBwdThreads) k_splat_bwd(const float4* __restr
     const int lt = tile - v * tiles_per_view;
     const int ty = lt / tiles_x, tx = lt - ty * tiles_x;
     const int X0 = tx * TW, Y0 = ty * TH;
-    for (int k = threadIdx.x; k < THP * TWP; k += kBwdThreads) {
-        const int r = k / TWP, c = k - r * TWP;
-        const int gy = Y0 + r, gx = X0 + c;
-        s_g[k] = (r < TH && c < TW && gy < H && gx < W) ? dimage[((size_t)v * H + gy) * W + gx] : 0.0f;
+    if ((W & 3) == 0 && (reinterpret_cast<uintptr_t>(dimage) & 15) == 0) {
+        // aligned rows: one 16-byte load per 4 pixels (a group lies wholly inside or
+        // outside the image); the staged columns past TW are never read
+        constexpr int G = TW / 4;
+        for (int k = threadIdx.x; k < THP * G; k += kBwdThreads) {
+            const int r = k / G, c = 4 * (k - r * G);
+            const int gy = Y0 + r, gx = X0 + c;
+            float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (r < TH && gy < H && gx < W)
+                val = __ldg(reinterpret_cast<const float4*>(dimage + ((size_t)v * H + gy) * W + gx));
+            *reinterpret_cast<float4*>(&s_g[r * TWP + c]) = val;
+        }
+    } else {
+        for (int k = threadIdx.x; k < THP * TWP; k += kBwdThreads) {
+            const int r = k / TWP, c = k - r * TWP;
+            const int gy = Y0 + r, gx = X0 + c;
+            s_g[k] = (r < TH && c < TW && gy < H && gx < W) ? dimage[((size_t)v * H + gy) * W + gx] : 0.0f;
+        }
     }
     const uint2 rg = ranges[tile];
     const float4* vrec = rec + 2 * (size_t)v * (size_t)M;
