@@ -422,6 +422,7 @@ struct FwdShape {
 };
 constexpr int kFwdMaxBlocks = 8;   // warp blocks per tile at most (32 x 32 tiles)
 constexpr int kFwdWarps = 4;       // independent warps per CTA
+constexpr long long kFwdItemWarps = 148ll * 36 * 4;  // work items from which one warp takes a whole item
 
 // Whether the gate of a record can reach a rectangle of pixel centres [x0, x1] x
 // [y0, y1] (a superset test: false only when no point of the rectangle has t >=
@@ -458,7 +459,197 @@ __device__ __forceinline__ bool gate_meets_rect(float4 a, float4 b, float x0, fl
 // weight): far above the FP32 rounding of t for the conics it is applied to.
 constexpr float kCullMargin = 0.0625f;
 
-// One warp per work item: the item's <= 128 records of one tile are read once by
+// One warp per (work item, warp block): the item's <= 128 records of one tile are
+// read by the warp's lanes (four each), the records whose box and gate meet the
+// warp's 8 x BW pixel block are compacted (ballot) into the warp's shared-memory
+// list (a record whose gate misses the block would add nothing to it), and
+// each lane accumulates its PX pixels over that list -- the quadratic is one FMA per
+// pixel (t0 + k (g + A k)).  The warps of a CTA share nothing (no block barrier).
+// A tile with several chunks: each chunk's warp writes its block of the chunk image;
+// the last chunk of a block to finish (per-(tile, block) arrival counter) sums the
+// block's chunk images in chunk order (deterministic).
+template <int TW, int TH, bool COUNT>
+__global__ void __launch_bounds__(32 * kFwdWarps, 9) k_splat_fwd(const float4* __restrict__ rec,
+                                                              const float4* __restrict__ srec,
+                                                              const uint2* __restrict__ ranges,
+                                                              const uint64_t* __restrict__ sorted,
+                                                              const uint64_t* __restrict__ items,
+                                                              const WsStatus* __restrict__ item_st,
+                                                              float* __restrict__ partial,
+                                                              const uint32_t* __restrict__ item_off,
+                                                              uint32_t* __restrict__ key_done, long long M,
+                                                              int tiles_x, int tiles_per_view, int H, int W,
+                                                              float Tq, float* __restrict__ image, WsStatus* st) {
+    constexpr int PX = FwdShape<TW, TH>::PX;  // pixels per lane, along x
+    constexpr int BW = FwdShape<TW, TH>::BW;  // warp block: 8 rows x BW columns
+    constexpr int NW = FwdShape<TW, TH>::NW;  // warp blocks per tile
+    constexpr int WPR = TW / BW;              // warp blocks per tile row
+    static_assert(TW % BW == 0 && TH % 8 == 0 && NW <= kFwdMaxBlocks && kChunk == 128, "tile shape");
+    __shared__ float4 s_a[kFwdWarps][kChunk];
+    __shared__ float4 s_b[kFwdWarps][kChunk];
+    pdl_trigger();
+    pdl_wait();  // the lists and records of the build before
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned long long gw = (unsigned long long)blockIdx.x * kFwdWarps + warp;
+    const unsigned long long it = gw / NW;
+    const int wb = (int)(gw - it * NW);
+    // whole warps: past the item count, or after a list build that gave up a wait
+    if (it >= item_st->n_keys || st->status == R2G_E_TIMEOUT) return;
+    const uint64_t item = items[it];
+    const int tile = (int)(item >> 32);
+    const uint32_t chunk = (uint32_t)item;
+    const int v = tile / tiles_per_view;
+    const int lt = tile - v * tiles_per_view;
+    const int ty = lt / tiles_x, tx = lt - ty * tiles_x;
+    const int bx = (wb % WPR) * BW, by = (wb / WPR) * 8;
+    const int lx = bx + (lane & 3) * PX, ly = by + (lane >> 2);
+    const int px = tx * TW + lx, py = ty * TH + ly;
+    const float fx = (float)px, fy = (float)py;
+    const float4* vrec = rec + 2 * (size_t)v * (size_t)M;
+    const uint2 rg = ranges[tile];
+    const uint32_t start = rg.x + chunk * kChunk;
+    const uint32_t end = min(start + (uint32_t)kChunk, rg.y);
+    const uint32_t nch = (rg.y - rg.x + kChunk - 1) / kChunk;
+    const int n = (int)(end > start ? end - start : 0u);
+    // the item's records (lane j holds records j, j + 32, ...), loads issued together:
+    // next to the sorted entries (srec), else gathered by Gaussian id
+    float4 ra[kChunk / 32], rb[kChunk / 32];
+    if (srec) {
+#pragma unroll
+        for (int c = 0; c < kChunk / 32; ++c) {
+            const int j = c * 32 + lane;
+            if (j < n) {
+                ra[c] = srec[2 * (size_t)(start + j)];      // cx, cy, A, B
+                rb[c] = srec[2 * (size_t)(start + j) + 1];  // C, rho_hat, rx, ry
+            }
+        }
+    } else {
+        uint32_t gid[kChunk / 32];
+#pragma unroll
+        for (int c = 0; c < kChunk / 32; ++c) {
+            const int j = c * 32 + lane;
+            gid[c] = j < n ? (uint32_t)sorted[start + j] : 0u;
+        }
+#pragma unroll
+        for (int c = 0; c < kChunk / 32; ++c) {
+            const int j = c * 32 + lane;
+            if (j < n) {
+                ra[c] = vrec[2 * (size_t)gid[c]];
+                rb[c] = vrec[2 * (size_t)gid[c] + 1];
+            }
+        }
+    }
+    // compact the records whose pixel box meets this warp's block, in item order
+    const int gx0 = tx * TW + bx, gy0 = ty * TH + by;
+    int m = 0;
+#pragma unroll
+    for (int c = 0; c < kChunk / 32; ++c) {
+        const int j = c * 32 + lane;
+        bool mine = false;
+        if (j < n) {
+            const float4 a = ra[c], b = rb[c];
+            const int c0 = (int)ceilf(a.x - b.z), c1 = (int)floorf(a.x + b.z);
+            const int r0 = (int)ceilf(a.y - b.w), r1 = (int)floorf(a.y + b.w);
+            mine = c1 >= gx0 && c0 <= gx0 + BW - 1 && r1 >= gy0 && r0 <= gy0 + 7;
+        }
+        const uint32_t bal = __ballot_sync(0xffffffffu, mine);
+        if (mine) {
+            const int pos = m + __popc(bal & ((1u << lane) - 1u));
+            s_a[warp][pos] = ra[c];
+            s_b[warp][pos] = rb[c];
+        }
+        m += __popc(bal);
+    }
+    __syncwarp();
+    // of those, keep the records whose gate meets the block (in place, in order: a
+    // kept record moves to a position no later than its own, after its round of 32
+    // has been read)
+    {
+        const int mb = m;
+        m = 0;
+        for (int q0 = 0; q0 < mb; q0 += 32) {
+            const int q = q0 + lane;
+            float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+            bool keep = false;
+            if (q < mb) {
+                a = s_a[warp][q];
+                b = s_b[warp][q];
+                keep = gate_meets_rect(a, b, (float)gx0, (float)(gx0 + BW - 1), (float)gy0, (float)(gy0 + 7),
+                                       Tq - kCullMargin);
+            }
+            const uint32_t bal = __ballot_sync(0xffffffffu, keep);
+            if (keep) {
+                const int pos = m + __popc(bal & ((1u << lane) - 1u));
+                s_a[warp][pos] = a;
+                s_b[warp][pos] = b;
+            }
+            m += __popc(bal);
+            __syncwarp();
+        }
+    }
+    float acc[PX];
+#pragma unroll
+    for (int k = 0; k < PX; ++k) acc[k] = 0.0f;
+    unsigned int cnt = 0;
+    for (int q = 0; q < m; ++q) {
+        const float4 a = s_a[warp][q];
+        const float4 b = s_b[warp][q];
+        const float dy = fy - a.y;
+        const float bdy = a.w * dy;
+        const float cdy2 = b.x * dy * dy;
+        const float dx0 = fx - a.x;
+        // t(dx0 + k) = t0 + k (g + A k), g = dt/ddx at dx0
+        const float t0 = fmaf(fmaf(a.z, dx0, bdy), dx0, cdy2);
+        const float g = fmaf(2.0f * a.z, dx0, bdy);
+#pragma unroll
+        for (int k = 0; k < PX; ++k) {
+            const float t = k == 0 ? t0 : fmaf((float)k, fmaf(a.z, (float)k, g), t0);
+            const float e = ex2_approx(t);
+            acc[k] = (t >= Tq) ? fmaf(b.y, e, acc[k]) : acc[k];
+            if (COUNT) cnt += (t >= Tq && px + k < W && py < H);
+        }
+    }
+    if (COUNT) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        if (lane == 0 && cnt) atomicAdd(&st->pairs, (unsigned long long)cnt);
+    }
+    if (nch > 1) {
+        // several chunks: store this chunk's block; the last chunk of the block to
+        // finish sums the block's chunk images in chunk order
+        float* p = partial + it * (size_t)(TW * TH) + ly * TW + lx;
+#pragma unroll
+        for (int k = 0; k < PX; ++k) p[k] = acc[k];
+        __syncwarp();  // every lane's stores ordered before lane 0's release
+        uint32_t last = 0;
+        if (lane == 0) {
+            uint32_t before;
+            asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;"
+                         : "=r"(before)
+                         : "l"(&key_done[(size_t)tile * kFwdMaxBlocks + wb])
+                         : "memory");
+            last = before == nch - 1;
+        }
+        last = __shfl_sync(0xffffffffu, last, 0);
+        if (!last) return;
+        __syncwarp();  // lane 0's acquire orders the warp's reads of the other chunks' images
+        const float* qp = partial + (size_t)item_off[tile] * (TW * TH) + ly * TW + lx;
+#pragma unroll
+        for (int k = 0; k < PX; ++k) acc[k] = 0.0f;
+        for (uint32_t c = 0; c < nch; ++c)
+#pragma unroll
+            for (int k = 0; k < PX; ++k) acc[k] += __ldcg(qp + (size_t)c * (TW * TH) + k);
+    }
+    if (py < H) {  // one chunk (or none: an empty tile's item writes zeros), or the sum
+        float* row = image + ((size_t)v * H + py) * W;
+#pragma unroll
+        for (int k = 0; k < PX; ++k)
+            if (px + k < W) row[px + k] = acc[k];
+    }
+}
+
+// The forward for item counts that fill the GPU several times over (kFwdItemWarps
+// and more): one warp per work item.  The item's <= 128 records of one tile are read once by
 // the warp's lanes (four each, kept in registers); then for each of the tile's 8 x
 // BW pixel blocks in turn, the records whose box and gate meet the block are
 // compacted (ballot) into the warp's shared-memory list (a record whose gate misses
@@ -469,7 +660,7 @@ constexpr float kCullMargin = 0.0625f;
 // finish (per-(tile, block) arrival counter) sums the block's chunk images in chunk
 // order (deterministic).
 template <int TW, int TH, bool COUNT>
-__global__ void __launch_bounds__(32 * kFwdWarps, 8) k_splat_fwd(const float4* __restrict__ rec,
+__global__ void __launch_bounds__(32 * kFwdWarps, 8) k_splat_fwd_items(const float4* __restrict__ rec,
                                                               const float4* __restrict__ srec,
                                                               const uint2* __restrict__ ranges,
                                                               const uint64_t* __restrict__ sorted,
@@ -547,9 +738,10 @@ __global__ void __launch_bounds__(32 * kFwdWarps, 8) k_splat_fwd(const float4* _
             if (c0 <= c1 && r0 <= r1)
                 for (int by = r0 / 8; by <= r1 / 8; ++by)
                     for (int bx = c0 / BW; bx <= c1 / BW; ++bx) {
+                        const int wb = by * WPR + bx;
                         const float gx0 = (float)(tx * TW + bx * BW), gy0 = (float)(ty * TH + by * 8);
                         if (gate_meets_rect(a, b, gx0, gx0 + (float)(BW - 1), gy0, gy0 + 7.0f, Tq - kCullMargin))
-                            mk |= 1u << (c * 8 + by * WPR + bx);
+                            mk |= 1u << (c * 8 + wb);
                     }
         }
     }
@@ -617,12 +809,13 @@ __global__ void __launch_bounds__(32 * kFwdWarps, 8) k_splat_fwd(const float4* _
     // block's chunk images are summed in chunk order
     __syncwarp();  // every lane's stores ordered before the arriving lanes' release
     uint32_t before = 0;
-    if (lane < NW)
+    const bool arrives = lane < NW;
+    if (arrives)
         asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;"
                      : "=r"(before)
                      : "l"(&key_done[(size_t)tile * kFwdMaxBlocks + lane])
                      : "memory");
-    const uint32_t lastmask = __ballot_sync(0xffffffffu, lane < NW && before == nch - 1);
+    const uint32_t lastmask = __ballot_sync(0xffffffffu, arrives && before == nch - 1);
     if (!lastmask) return;
     __syncwarp();  // the arriving lanes' acquire orders the warp's reads of the other chunks' images
     for (int wb = 0; wb < NW; ++wb) {
@@ -1257,7 +1450,13 @@ struct FwdArgs {
 template <int TW, int TH, bool COUNT>
 void fwd_shape(const FwdArgs& f, long long M, const RasterLayout& L, long long icap, int H, int W, float Tq,
                float* image, WsStatus* st, cudaStream_t s) {
-    const unsigned long long warps = (unsigned long long)icap;  // one warp per work item
+    if (FwdShape<TW, TH>::NW > 1 && icap >= kFwdItemWarps) {  // one warp per work item
+        launch_pdl(k_splat_fwd_items<TW, TH, COUNT>, dim3((unsigned)((icap + kFwdWarps - 1) / kFwdWarps)),
+                   dim3(32 * kFwdWarps), 0, s, f.rec, f.srec, f.ranges, f.sorted, f.items, f.item_st, f.partial,
+                   f.item_off, f.key_done, M, L.tiles_x, L.tiles_per_view, H, W, Tq, image, st);
+        return;
+    }
+    const unsigned long long warps = (unsigned long long)icap * FwdShape<TW, TH>::NW;
     launch_pdl(k_splat_fwd<TW, TH, COUNT>, dim3((unsigned)((warps + kFwdWarps - 1) / kFwdWarps)),
                dim3(32 * kFwdWarps), 0, s, f.rec, f.srec, f.ranges, f.sorted, f.items, f.item_st, f.partial,
                f.item_off, f.key_done, M, L.tiles_x, L.tiles_per_view, H, W, Tq, image, st);
