@@ -459,6 +459,45 @@ __device__ __forceinline__ bool gate_meets_rect(float4 a, float4 b, float x0, fl
 // weight): far above the FP32 rounding of t for the conics it is applied to.
 constexpr float kCullMargin = 0.0625f;
 
+// The bounding box of a record's gate inside a rectangle of pixel centres (tile-
+// local columns c0..c1, rows r0..r1; centre xc, yc), narrowed in place: columns to
+// the x-extent of the gate t >= Tc over the rows, then rows to its y-extent over
+// those columns (a superset of the gated pixels for Tc a little below the gate).
+// Over a strip of rows the gate's left end bh dy - hh sqrt(K0 - K2 dy^2) is convex
+// in dy, its minimum at the row of the gate's leftmost point (dy = B ex / (2C), ex
+// its half-width) clamped to the strip; the right end and the y-extent likewise
+// (K2 = 4AC - B^2, K0 = 4A Tc, hh = -1 / (2A)).  A conic that is not clearly
+// negative definite keeps its box.
+__device__ __forceinline__ void narrow_box(float4 a, float4 b, float xc, float yc, float Tc, int& c0, int& c1,
+                                           int& r0, int& r1) {
+    const float A = a.z, B = a.w, C = b.x;
+    const float ac4 = 4.0f * A * C, K2 = ac4 - B * B;
+    if (!(A < 0.0f && C < 0.0f && K2 > 0x1p-10f * ac4)) return;
+    const float iK2 = rcp_fast(K2);
+    {
+        const float K0 = 4.0f * A * Tc, hh = -0.5f * rcp_fast(A), bh = B * hh;
+        const float ex = sqrt_fast(4.0f * C * Tc * iK2);
+        const float dyl = B * ex * (0.5f * rcp_fast(C));
+        const float y0 = (float)r0 - yc, y1 = (float)r1 - yc;
+        const float dl = fminf(fmaxf(dyl, y0), y1), dr = fminf(fmaxf(-dyl, y0), y1);
+        const float xl = fmaf(bh, dl, -sqrt_fast(fmaxf(fmaf(-K2, dl * dl, K0), 0.0f)) * hh);
+        const float xr = fmaf(bh, dr, sqrt_fast(fmaxf(fmaf(-K2, dr * dr, K0), 0.0f)) * hh);
+        c0 = max(c0, (int)ceilf(xc + xl));
+        c1 = min(c1, (int)floorf(xc + xr));
+    }
+    {
+        const float K0 = 4.0f * C * Tc, hh = -0.5f * rcp_fast(C), bh = B * hh;
+        const float ey = sqrt_fast(4.0f * A * Tc * iK2);
+        const float dxt = B * ey * (0.5f * rcp_fast(A));
+        const float x0 = (float)c0 - xc, x1 = (float)c1 - xc;
+        const float dt = fminf(fmaxf(dxt, x0), x1), db = fminf(fmaxf(-dxt, x0), x1);
+        const float yl = fmaf(bh, dt, -sqrt_fast(fmaxf(fmaf(-K2, dt * dt, K0), 0.0f)) * hh);
+        const float yr = fmaf(bh, db, sqrt_fast(fmaxf(fmaf(-K2, db * db, K0), 0.0f)) * hh);
+        r0 = max(r0, (int)ceilf(yc + yl));
+        r1 = min(r1, (int)floorf(yc + yr));
+    }
+}
+
 // One warp per (work item, warp block): the item's <= 128 records of one tile are
 // read by the warp's lanes (four each), the records whose box and gate meet the
 // warp's 8 x BW pixel block are compacted (ballot) into the warp's shared-memory
@@ -733,16 +772,23 @@ __global__ void __launch_bounds__(32 * kFwdWarps, 8) k_splat_fwd_items(const flo
         const int j = c * 32 + lane;
         if (j < n) {
             const float4 a = ra[c], b = rb[c];
-            const int c0 = max((int)ceilf(a.x - b.z) - tx * TW, 0), c1 = min((int)floorf(a.x + b.z) - tx * TW, TW - 1);
-            const int r0 = max((int)ceilf(a.y - b.w) - ty * TH, 0), r1 = min((int)floorf(a.y + b.w) - ty * TH, TH - 1);
-            if (c0 <= c1 && r0 <= r1)
-                for (int by = r0 / 8; by <= r1 / 8; ++by)
-                    for (int bx = c0 / BW; bx <= c1 / BW; ++bx) {
-                        const int wb = by * WPR + bx;
+            int c0 = max((int)ceilf(a.x - b.z) - tx * TW, 0), c1 = min((int)floorf(a.x + b.z) - tx * TW, TW - 1);
+            int r0 = max((int)ceilf(a.y - b.w) - ty * TH, 0), r1 = min((int)floorf(a.y + b.w) - ty * TH, TH - 1);
+            if (c0 <= c1 && r0 <= r1)  // the gate's own bounding box in the tile
+                narrow_box(a, b, a.x - (float)(tx * TW), a.y - (float)(ty * TH), Tq - kCullMargin, c0, c1, r0, r1);
+            if (c0 <= c1 && r0 <= r1) {
+                const int bx0 = c0 / BW, bx1 = c1 / BW, by0 = r0 / 8, by1 = r1 / 8;
+                // a convex set whose bounding box spans one row or one column of blocks
+                // meets each of them; spanning both, each block is tested
+                const bool test = bx1 > bx0 && by1 > by0;
+                for (int by = by0; by <= by1; ++by)
+                    for (int bx = bx0; bx <= bx1; ++bx) {
                         const float gx0 = (float)(tx * TW + bx * BW), gy0 = (float)(ty * TH + by * 8);
-                        if (gate_meets_rect(a, b, gx0, gx0 + (float)(BW - 1), gy0, gy0 + 7.0f, Tq - kCullMargin))
-                            mk |= 1u << (c * 8 + wb);
+                        if (!test ||
+                            gate_meets_rect(a, b, gx0, gx0 + (float)(BW - 1), gy0, gy0 + 7.0f, Tq - kCullMargin))
+                            mk |= 1u << (c * 8 + by * WPR + bx);
                     }
+            }
         }
     }
     for (int wb = 0; wb < NW; ++wb) {
@@ -868,45 +914,6 @@ __device__ __forceinline__ uint32_t cta_excl_scan_128(uint32_t v, uint32_t* s_w,
     }
     *total = tot;
     return before + incl - v;
-}
-
-// The bounding box of a record's gate inside a rectangle of pixel centres (tile-
-// local columns c0..c1, rows r0..r1; centre xc, yc), narrowed in place: columns to
-// the x-extent of the gate t >= Tc over the rows, then rows to its y-extent over
-// those columns (a superset of the gated pixels for Tc a little below the gate).
-// Over a strip of rows the gate's left end bh dy - hh sqrt(K0 - K2 dy^2) is convex
-// in dy, its minimum at the row of the gate's leftmost point (dy = B ex / (2C), ex
-// its half-width) clamped to the strip; the right end and the y-extent likewise
-// (K2 = 4AC - B^2, K0 = 4A Tc, hh = -1 / (2A)).  A conic that is not clearly
-// negative definite keeps its box.
-__device__ __forceinline__ void narrow_box(float4 a, float4 b, float xc, float yc, float Tc, int& c0, int& c1,
-                                           int& r0, int& r1) {
-    const float A = a.z, B = a.w, C = b.x;
-    const float ac4 = 4.0f * A * C, K2 = ac4 - B * B;
-    if (!(A < 0.0f && C < 0.0f && K2 > 0x1p-10f * ac4)) return;
-    const float iK2 = rcp_fast(K2);
-    {
-        const float K0 = 4.0f * A * Tc, hh = -0.5f * rcp_fast(A), bh = B * hh;
-        const float ex = sqrt_fast(4.0f * C * Tc * iK2);
-        const float dyl = B * ex * (0.5f * rcp_fast(C));
-        const float y0 = (float)r0 - yc, y1 = (float)r1 - yc;
-        const float dl = fminf(fmaxf(dyl, y0), y1), dr = fminf(fmaxf(-dyl, y0), y1);
-        const float xl = fmaf(bh, dl, -sqrt_fast(fmaxf(fmaf(-K2, dl * dl, K0), 0.0f)) * hh);
-        const float xr = fmaf(bh, dr, sqrt_fast(fmaxf(fmaf(-K2, dr * dr, K0), 0.0f)) * hh);
-        c0 = max(c0, (int)ceilf(xc + xl));
-        c1 = min(c1, (int)floorf(xc + xr));
-    }
-    {
-        const float K0 = 4.0f * C * Tc, hh = -0.5f * rcp_fast(C), bh = B * hh;
-        const float ey = sqrt_fast(4.0f * A * Tc * iK2);
-        const float dxt = B * ey * (0.5f * rcp_fast(A));
-        const float x0 = (float)c0 - xc, x1 = (float)c1 - xc;
-        const float dt = fminf(fmaxf(dxt, x0), x1), db = fminf(fmaxf(-dxt, x0), x1);
-        const float yl = fmaf(bh, dt, -sqrt_fast(fmaxf(fmaf(-K2, dt * dt, K0), 0.0f)) * hh);
-        const float yr = fmaf(bh, db, sqrt_fast(fmaxf(fmaf(-K2, db * db, K0), 0.0f)) * hh);
-        r0 = max(r0, (int)ceilf(yc + yl));
-        r1 = min(r1, (int)floorf(yc + yr));
-    }
 }
 
 // Backward unit: UW x UH pixels (columns x rows) of a record's box.
