@@ -131,6 +131,34 @@ def test_tile_shape_does_not_change_the_image():
         assert np.abs(imgs[k] - imgs[0]).max() <= 1e-6 * np.abs(imgs[0]).max()
 
 
+@pytest.mark.parametrize("tile", [(8, 8), (16, 16), (32, 8), (32, 32)])
+def test_rasterize_crowded_tiles(tile):
+    """Tiles with many work items of 128 records (a cluster of 3000 Gaussians
+    projecting onto a few tiles; ragged 90 x 106 detector): each item's block images
+    and their sum in item order by the last item to arrive, against the oracle; the
+    same image on a second run (the sum's order is fixed); the gated pair count
+    against the oracle's up to gate-band flips."""
+    g = I.rng(77)
+    M = 3000
+    mean = g.normal(0.0, 0.06, (M, 3))
+    scale = np.exp(g.uniform(math.log(0.004), math.log(0.04), (M, 3)))
+    quat = I.random_quats(g, M)
+    rho = g.uniform(-0.2, 1.0, M)
+    G = I.GaussianSet(mean, scale, quat, rho).astype(np.float32)
+    cam = I.cone_camera(90, 106, pitch=I.CONE_PITCH * 512 / 106)
+    views = I.view_table(np.deg2rad([20.0, 140.0]), I.CONE_L_SO)
+    ref, pairs, band = core.render(G, views, cam, Q=Q9, want_band=True)
+    rast = engine.Rasterizer(G.M, 2, cam, tile=tile)
+    img = host(rast.forward(*dev_set(G), dev(views), count=True))
+    assert_values_close(img, ref, band, f"crowded {tile}")
+    assert abs(rast.pair_count() - pairs) <= max(10, 1e-4 * pairs), (rast.pair_count(), pairs)
+    again = host(rast.forward(*dev_set(G), dev(views)))
+    assert np.array_equal(again, img)
+    # the cluster puts several work items on its central tiles
+    ranges, _, _ = _lists_gpu(rast, G.M, 2)
+    assert int((ranges[:, 1] - ranges[:, 0]).max()) > 4 * 128
+
+
 def test_rasterize_ragged_detector_and_empty_cases():
     """Detector not a multiple of the tile, Gaussians off the detector, behind the
     near plane, and one tiny Gaussian (degenerate sizes)."""
