@@ -331,7 +331,7 @@ __device__ __forceinline__ uint32_t project_one(const Params& G, const float* __
 // so that a block covers the records of one list block.  mom_clear (optional):
 // every record's backward moment slot starts at zero.  lc.partials (optional):
 // count the blocks' tile entries for the list build (list_count_tail).
-__global__ void __launch_bounds__(256) k_project(Params G, const float* __restrict__ views,
+__global__ void __launch_bounds__(256, 4) k_project(Params G, const float* __restrict__ views,
                                                  const int* __restrict__ view_sel, CamF cam, float Q, int TW, int TH,
                                                  long long M, long long n_rec, int per_thread,
                                                  float4* __restrict__ rec, uint2* __restrict__ rect,

@@ -466,6 +466,63 @@ class Scan:
         self.version += 1
         return M2
 
+    def checkpoint(self) -> dict:
+        """A snapshot of this scan's training state in host memory: the raw and activated
+        parameters and both Adam moments (flat layout, 11 M floats each), the Gaussian
+        count, the iteration counter (which drives the learning-rate schedule), the
+        state of the scan's view / TV-patch generator and, under adaptive density
+        control, the position-gradient statistics.  Waits for the scan's queued work.
+        `restore` puts it back; `save_checkpoint` / `load_checkpoint` write and read it."""
+        torch.cuda.synchronize(self.device)
+        s = self.state
+        n = 11 * s.M
+        ck = {"M": int(s.M), "it": int(self.it), "rng": self.rng.bit_generator.state,
+              "raw": s.raw[:n].cpu().numpy().copy(), "act": s.act[:n].cpu().numpy().copy(),
+              "m": s.m[:n].cpu().numpy().copy(), "v": s.v[:n].cpu().numpy().copy()}
+        if self.dens_grad is not None:
+            ck["dens_grad"] = self.dens_grad.cpu().numpy().copy()
+            ck["dens_count"] = self.dens_count.cpu().numpy().copy()
+        return ck
+
+    def restore(self, ck: dict):
+        """Continue from a `checkpoint` of a scan with the same projections, views, camera
+        and options (this scan's own, or one built alike).  The parameters and moments are
+        copied to new device arrays (sized for the adaptive-control capacity when it is
+        on), the workspaces are re-sized for the snapshot's Gaussian count and the C job is
+        rebuilt, so a captured round graph is recaptured (`version` changes).  From a
+        restored state the next iteration's forward pass and losses are those the original
+        run computed, bit for bit; its update may differ in the last bits, because the
+        backward sums the gradient moments with float atomics."""
+        M = int(ck["M"])
+        n = 11 * M
+        cap = 11 * max(M, getattr(self, "max_gaussians", 0) if self.dens_grad is not None else 0)
+        out = []
+        for key in ("raw", "act", "m", "v"):
+            a = np.asarray(ck[key], np.float32)
+            if a.shape != (n,):
+                raise ValueError(f"checkpoint array {key} has shape {a.shape}, expected ({n},)")
+            t = torch.zeros(cap, dtype=torch.float32, device=self.device)
+            t[:n].copy_(torch.from_numpy(a))
+            out.append(t)
+        self.state.adopt(*out, M)
+        self.M = M
+        self.rast.M = M
+        self.vox.M = M
+        if self.full_vox is not None:
+            self.full_vox.M = M
+        self.it = int(ck["it"])
+        self.rng.bit_generator.state = ck["rng"]
+        if self.dens_grad is not None:
+            if "dens_grad" in ck:
+                self.dens_grad.copy_(torch.from_numpy(np.asarray(ck["dens_grad"], np.float32)))
+                self.dens_count.copy_(torch.from_numpy(np.asarray(ck["dens_count"], np.float32)))
+            else:
+                self.dens_grad.zero_()
+                self.dens_count.zero_()
+        self._size_workspaces(self.headroom, probes=2)
+        self.job = self._make_job()
+        self.version += 1
+
     def volume_params(self):
         """(mean, scale, quat, rho) for the voxelizer.  The rectified model's densities
         are the 3D densities; the X-3DGS variant (biased=True) learned mu rho per view,
@@ -767,6 +824,28 @@ class BatchTrainer:
 
     def losses(self):
         return torch.stack([sc.loss for sc in self.scans]).cpu().numpy()
+
+
+def save_checkpoint(ck: dict, path: str):
+    """Write a `Scan.checkpoint` snapshot to one .npz file (arrays as stored, the
+    count, iteration and generator state as JSON)."""
+    import json
+
+    arrays = {k: np.asarray(v) for k, v in ck.items() if isinstance(v, np.ndarray)}
+    meta = {k: v for k, v in ck.items() if not isinstance(v, np.ndarray)}
+    np.savez(path, __meta__=np.frombuffer(json.dumps(meta).encode(), dtype=np.uint8), **arrays)
+
+
+def load_checkpoint(path: str) -> dict:
+    """Read a snapshot written by `save_checkpoint`."""
+    import json
+
+    with np.load(path) as z:
+        ck = json.loads(bytes(z["__meta__"]).decode())
+        for k in z.files:
+            if k != "__meta__":
+                ck[k] = z[k].copy()
+    return ck
 
 
 def ctypes_sizeof_entry() -> int:
