@@ -950,10 +950,12 @@ __global__ void __launch_bounds__(kBwdThreads) k_splat_bwd(const float4* __restr
     constexpr int TWP = TW + 4;           // staged row stride (16-byte multiple; spreads rows over banks)
     constexpr int THP = TH + UH - 1;      // staged rows: UH - 1 zero rows past the tile edge
     __shared__ __align__(16) float s_g[THP * TWP];  // dL/dI of the tile
+    // the item's records with units, in item order (empty ones left out, so that a
+    // lane's next record is always the next slot)
     __shared__ float4 s_k1[kChunk];        // A, B, C of the conic; dx of the box's first pixel
     __shared__ float4 s_k2[kChunk];        // dy of the first row; s_g index of the first pixel; 1/uw; uw
-    __shared__ uint32_t s_gid[kChunk];     // Gaussian id
-    __shared__ uint32_t s_excl[kChunk + 1];  // exclusive prefix of the unit counts; [kChunk] = total
+    __shared__ float4 s_k3[kChunk];        // 2A, 4A, 9A; Gaussian id (bits)
+    __shared__ uint32_t s_excl[kChunk + 1];  // exclusive prefix of the unit counts; [records] = total
     __shared__ uint32_t s_w[kBwdThreads / 32];
     pdl_trigger();
     pdl_wait();  // dL/dI of the loss before
@@ -992,6 +994,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_splat_bwd(const float4* __restr
     const int j = threadIdx.x;
     const uint32_t e = rg.x + chunk * kChunk + j;
     uint32_t n = 0;
+    float4 K1, K2, K3;
     if (e < rg.y) {
         const uint32_t gid = (uint32_t)sorted[e];
         // the record next to the sorted entry (srec: independent of the id load), else gathered
@@ -1006,30 +1009,38 @@ __global__ void __launch_bounds__(kBwdThreads) k_splat_bwd(const float4* __restr
             const int ca = c0 & ~(UW - 1);  // first unit column, aligned
             const int uw = (c1 - ca) / UW + 1;
             n = (uint32_t)(uw * ((h + UH - 1) / UH));
-            s_k1[j] = make_float4(a.z, a.w, b.x, (float)(X0 + ca) - a.x);
-            s_k2[j] = make_float4((float)(Y0 + r0) - a.y, (float)(r0 * TWP + ca), 1.0f / (float)uw, (float)uw);
-            s_gid[j] = gid;
+            K1 = make_float4(a.z, a.w, b.x, (float)(X0 + ca) - a.x);
+            K2 = make_float4((float)(Y0 + r0) - a.y, (float)(r0 * TWP + ca), 1.0f / (float)uw, (float)uw);
+            K3 = make_float4(2.f * a.z, 4.f * a.z, 9.f * a.z, __uint_as_float(gid));
         }
     }
+    // one scan of (units | has units << 16) gives the unit offsets and each non-empty
+    // record's slot (units per record <= 128, so the low half holds the sum)
     uint32_t T;
-    const uint32_t ex = cta_excl_scan_128(n, s_w, &T);
-    s_excl[j] = ex;
-    if (j == 0) s_excl[kChunk] = T;
+    const uint32_t ex = cta_excl_scan_128(n | ((n > 0 ? 1u : 0u) << 16), s_w, &T);
+    const int nrec = (int)(T >> 16);
+    T &= 0xffffu;
+    if (n > 0) {
+        const uint32_t slot = ex >> 16;
+        s_k1[slot] = K1;
+        s_k2[slot] = K2;
+        s_k3[slot] = K3;
+        s_excl[slot] = ex & 0xffffu;
+    }
+    if (j == 0) s_excl[nrec] = T;
     __syncthreads();
     const uint32_t per = (T + kBwdThreads - 1) / kBwdThreads;
     const uint32_t p0 = j * per, p1 = min(T, p0 + per);
     if (p0 >= p1) return;
-    // the record holding unit p0: the largest k with excl_k <= p0 (it is non-empty)
-    int lo = 0, hi = kChunk - 1;
+    // the record holding unit p0: the largest k with excl_k <= p0
+    int lo = 0, hi = nrec - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
         if (s_excl[mid] <= p0) lo = mid;
         else hi = mid - 1;
     }
     int k = lo;
-    float4 k1 = s_k1[k], k2 = s_k2[k];
-    float A2 = 2.f * k1.x, A4 = 4.f * k1.x, A9 = 9.f * k1.x;
-    uint32_t gid = s_gid[k];
+    float4 k1 = s_k1[k], k2 = s_k2[k], k3 = s_k3[k];
     uint32_t rec_end = s_excl[k + 1];
     float uf = (float)(p0 - s_excl[k]);  // unit index inside the record
     float S0 = 0.f, Sx = 0.f, Sy = 0.f, Sxx = 0.f, Sxy = 0.f, Syy = 0.f;
@@ -1048,10 +1059,10 @@ __global__ void __launch_bounds__(kBwdThreads) k_splat_bwd(const float4* __restr
             const float4 g4 = *reinterpret_cast<const float4*>(&s_g[gi + qy * TWP]);
             // t(dx + q) = t0 + q gl + A q^2, gl = 2 A dx + B dy
             const float t0 = fmaf(fmaf(k1.x, dx, bdy), dx, cdy2);
-            const float gl = fmaf(A2, dx, bdy);
+            const float gl = fmaf(k3.x, dx, bdy);
             const float t1 = (t0 + k1.x) + gl;
-            const float t2 = fmaf(2.f, gl, t0 + A4);
-            const float t3 = fmaf(3.f, gl, t0 + A9);
+            const float t2 = fmaf(2.f, gl, t0 + k3.y);
+            const float t3 = fmaf(3.f, gl, t0 + k3.z);
             const float w0 = (t0 >= Tq) ? g4.x * ex2_approx(t0) : 0.0f;
             const float w1 = (t1 >= Tq) ? g4.y * ex2_approx(t1) : 0.0f;
             const float w2 = (t2 >= Tq) ? g4.z * ex2_approx(t2) : 0.0f;
@@ -1070,24 +1081,21 @@ __global__ void __launch_bounds__(kBwdThreads) k_splat_bwd(const float4* __restr
         }
         uf += 1.0f;
         if (p + 1 == rec_end && p + 1 < p1) {  // next record
-            atomicAdd(&vmom[2 * (size_t)gid], make_float4(S0, Sx, Sy, Sxx));
-            atomicAdd(reinterpret_cast<float2*>(&vmom[2 * (size_t)gid + 1]), make_float2(Sxy, Syy));
+            const size_t g2 = 2 * (size_t)__float_as_uint(k3.w);
+            atomicAdd(&vmom[g2], make_float4(S0, Sx, Sy, Sxx));
+            atomicAdd(reinterpret_cast<float2*>(&vmom[g2 + 1]), make_float2(Sxy, Syy));
             S0 = Sx = Sy = Sxx = Sxy = Syy = 0.f;
-            do {
-                ++k;
-            } while (s_excl[k + 1] == s_excl[k]);
+            ++k;
             k1 = s_k1[k];
             k2 = s_k2[k];
-            A2 = 2.f * k1.x;
-            A4 = 4.f * k1.x;
-            A9 = 9.f * k1.x;
-            gid = s_gid[k];
+            k3 = s_k3[k];
             rec_end = s_excl[k + 1];
             uf = 0.0f;
         }
     }
-    atomicAdd(&vmom[2 * (size_t)gid], make_float4(S0, Sx, Sy, Sxx));
-    atomicAdd(reinterpret_cast<float2*>(&vmom[2 * (size_t)gid + 1]), make_float2(Sxy, Syy));
+    const size_t g2 = 2 * (size_t)__float_as_uint(k3.w);
+    atomicAdd(&vmom[g2], make_float4(S0, Sx, Sy, Sxx));
+    atomicAdd(reinterpret_cast<float2*>(&vmom[g2 + 1]), make_float2(Sxy, Syy));
 }
 
 // ------------------------------------------------------------------ K6: projection backward
