@@ -934,7 +934,7 @@ constexpr int kBwdUnitW = 4, kBwdUnitH = 2;
 // registers, and adds them to the record's slot (two vector atomics) when it
 // leaves the record or its range ends.
 template <int TW, int TH, int UW, int UH>
-__global__ void __launch_bounds__(kBwdThreads) k_splat_bwd(const float4* __restrict__ rec,
+__global__ void __launch_bounds__(kBwdThreads, 8) k_splat_bwd(const float4* __restrict__ rec,
                                                            const float4* __restrict__ srec,
                                                            const uint2* __restrict__ ranges,
                                                            const uint64_t* __restrict__ sorted,
