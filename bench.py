@@ -51,6 +51,10 @@ FP32_PER_CLK = 128         # FP32 lanes per SM per clock
 # moments); the kernels' own reduced counts (incremental quadratics) beside them
 OPS_FWD, OPS_BWD = 10, 20
 OWN_OPS_FWD, OWN_OPS_BWD = 6, 14
+# FP32 lane operations per voxel and orientation of the slice SSIM: 11-tap horizontal
+# and vertical passes over five moment maps (110 FMAs), three products, ~16 for the
+# SSIM ratio
+SSIM_OPS_PER_VOXEL = 129
 
 
 def peaks():
@@ -676,11 +680,21 @@ def measure_metrics(dev, reps=20):
     algo = 2 * 4 * N_OUT ** 3
     pk = peaks()
     vals = dict(zip(engine.METRIC_KEYS, out.cpu().tolist()))
+    # the bound that binds: per voxel and orientation the window's separable passes over
+    # the five moment maps (2 x 5 x 11 FMAs), the three products and ~16 operations of
+    # the SSIM ratio, ~129 FP32 lane operations, at 128 per clock per SM; reading both
+    # volumes once (128 MB) would take a tenth of that time at the measured HBM rate
+    units = 3.0 * N_OUT ** 3
+    peak = SM_COUNT * FP32_PER_CLK * pk["sm_max_mhz"] * 1e6 / SSIM_OPS_PER_VOXEL
+    ach = units / (ms * 1e-3)
     return {"ms_per_call": ms, "volume": f"{N_OUT}^3", "values_noisy_phantom": vals,
-            "roofline": {"bound": "hbm", "achieved": algo / (ms * 1e-3) / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                         "frac": algo / (ms * 1e-3) / 1e9 / pk["hbm_gbs"], "traffic": None,
-                         "note": "algorithmic bytes = both volumes read once (128 MB); the kernel reads them "
-                                 "once per orientation plus once for the MSE, with 5-voxel halos"}}
+            "roofline": {"kernel": "slice_ssim", "bound": "alu", "achieved": ach / 1e9, "peak": peak / 1e9,
+                         "unit": "G voxel-orientations/s", "frac": ach / peak, "ops_per_unit": SSIM_OPS_PER_VOXEL,
+                         "traffic": ncu_traffic("metrics"),
+                         "hbm": {"algorithmic_bytes": algo, "achieved_gbs": algo / (ms * 1e-3) / 1e9,
+                                 "peak_gbs": pk["hbm_gbs"], "frac": algo / (ms * 1e-3) / 1e9 / pk["hbm_gbs"]},
+                         "peak_note": f"FP32 {FP32_PER_CLK}/clk/SM / {SSIM_OPS_PER_VOXEL} ops x {SM_COUNT} SMs x "
+                                      f"{pk['sm_max_mhz']:.0f} MHz (of measured sm_max_mhz)"}}
 
 
 def measure_limited_angle(dev, iters=3000):

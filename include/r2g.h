@@ -193,7 +193,7 @@ r2g_status r2g_pair_count(const void* ws, size_t ws_bytes, int64_t* pairs, r2g_s
  *   c_k = (p_k - origin_k)/voxel_k - 1/2, r_k = sqrt(Q3 Sigma_kk)/voxel_k,
  *   voxels ceil(c_k - r_k) .. floor(c_k + r_k) clamped, bricks = voxels / 8.
  * Each voxel then applies the gate q <= Q3 exactly.  Q3 = 11.345 is the 0.99
- * quantile of chi^2_3 (the paper's "99% confidence"). */
+ * quantile of chi^2_3 (Sec. 4.2.2 culls at probability 0.99). */
 
 size_t r2g_voxel_workspace_size(int64_t M, int32_t G, const r2g_grid* grids, int64_t key_capacity);
 

@@ -14,8 +14,8 @@
 //       additive per-pixel sum (Eq. 5, Eq. 7), the density field evaluated on a
 //       voxel grid (Eq. 4, Sec. 4.2.2), and hand-derived adjoints of both.
 //       The truncation gates q <= Q (pixels) and q <= Q3 (voxels) are part of
-//       the definition used here (the paper culls at "99% confidence",
-//       Sec. 4.2.2; the rasterizer truncation is the 3-sigma reading).
+//       the definition used here (Sec. 4.2.2 culls at probability 0.99;
+//       the rasterizer truncation is the 3-sigma reading).
 //   O2  the exact line integral of one 3D Gaussian along a ray (Eq. 1, Eq. 5),
 //       no truncation.
 //   O3  trapezoid quadrature of the same integral (a brute-force pin for O2).

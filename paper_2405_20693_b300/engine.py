@@ -14,7 +14,7 @@ import torch
 from . import r2g
 
 Q_PIXEL = 9.0        # 3-sigma pixel gate
-Q_VOXEL = 11.345     # chi^2_3 0.99 quantile: the paper's "99% confidence" brick culling
+Q_VOXEL = 11.345     # chi^2_3 0.99 quantile: the 0.99-probability culling of Sec. 4.2.2
 LAMBDA_SSIM = 0.25   # Sec. 5.1
 LAMBDA_TV = 0.05     # Sec. 5.1
 SCAN_TILE = (32, 32)  # tile shape of the training step's rasterizer (fewest list entries at 512^2)
