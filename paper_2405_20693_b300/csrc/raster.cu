@@ -620,7 +620,7 @@ __global__ void __launch_bounds__(32 * kFwdWarps, 9) k_splat_fwd(const float4* _
             if (keep) {
                 const int pos = m + __popc(bal & ((1u << lane) - 1u));
                 s_a[warp][pos] = a;
-                s_b[warp][pos] = b;
+                s_b[warp][pos] = make_float4(b.x, b.y, 2.0f * a.z, b.w);  // 2A in place of the spent box half-width
             }
             m += __popc(bal);
             __syncwarp();
@@ -639,7 +639,7 @@ __global__ void __launch_bounds__(32 * kFwdWarps, 9) k_splat_fwd(const float4* _
         const float dx0 = fx - a.x;
         // t(dx0 + k) = t0 + k (g + A k), g = dt/ddx at dx0
         const float t0 = fmaf(fmaf(a.z, dx0, bdy), dx0, cdy2);
-        const float g = fmaf(2.0f * a.z, dx0, bdy);
+        const float g = fmaf(b.z, dx0, bdy)  /* b.z = 2A */;
 #pragma unroll
         for (int k = 0; k < PX; ++k) {
             const float t = k == 0 ? t0 : fmaf((float)k, fmaf(a.z, (float)k, g), t0);
@@ -791,6 +791,9 @@ __global__ void __launch_bounds__(32 * kFwdWarps, 8) k_splat_fwd_items(const flo
             }
         }
     }
+    // the box half-widths are spent: the staged records carry 2A in their place
+#pragma unroll
+    for (int c = 0; c < kChunk / 32; ++c) rb[c].z = 2.0f * ra[c].z;
     for (int wb = 0; wb < NW; ++wb) {
         const int bx = (wb % WPR) * BW, by = (wb / WPR) * 8;
         const int lx = bx + (lane & 3) * PX, ly = by + (lane >> 2);
@@ -824,7 +827,7 @@ __global__ void __launch_bounds__(32 * kFwdWarps, 8) k_splat_fwd_items(const flo
             const float dx0 = fx - a.x;
             // t(dx0 + k) = t0 + k (g + A k), g = dt/ddx at dx0
             const float t0 = fmaf(fmaf(a.z, dx0, bdy), dx0, cdy2);
-            const float g = fmaf(2.0f * a.z, dx0, bdy);
+            const float g = fmaf(b.z, dx0, bdy)  /* b.z = 2A */;
 #pragma unroll
             for (int k = 0; k < PX; ++k) {
                 const float t = k == 0 ? t0 : fmaf((float)k, fmaf(a.z, (float)k, g), t0);
