@@ -1048,6 +1048,15 @@ __global__ void __launch_bounds__(kBwdThreads, 8) k_splat_bwd(const float4* __re
     float uf = (float)(p0 - s_excl[k]);  // unit index inside the record
     float S0 = 0.f, Sx = 0.f, Sy = 0.f, Sxx = 0.f, Sxy = 0.f, Syy = 0.f;
     static_assert(UW == 4, "the per-row sums below are written for 4-pixel unit rows");
+    // The gate folded into the exponent: with sT = 2^(32 - e), e the exponent of |Tq|,
+    // min(t, (t - Tq) sT) is t where t >= Tq; where t < Tq the two differ by at least
+    // half an ulp of Tq, 2^(e - 24), so (t - Tq) sT <= -2^8 and 2^min flushes to zero --
+    // the pairs of the test t >= Tq (for |Tq| >= 2^-95, i.e. Q >= 4e-29), in two
+    // operations and with no select after the multiply by dL/dI.
+    const int eT = min(max((int)((__float_as_uint(Tq) >> 23) & 0xffu) - 127, -95), 94);
+    const float sT = __uint_as_float((uint32_t)(159 - eT) << 23);
+    const float nTq = -Tq * sT;
+    const auto gated = [sT, nTq](float t) { return fminf(t, fmaf(t, sT, nTq)); };
     for (uint32_t p = p0; p < p1; ++p) {
         // unit row = floor((u + 1/2) / uw), exact for u < 2^10 and uw <= 16
         const float rowf = floorf(fmaf(uf, k2.z, 0.5f * k2.z));
@@ -1066,10 +1075,10 @@ __global__ void __launch_bounds__(kBwdThreads, 8) k_splat_bwd(const float4* __re
             const float t1 = (t0 + k1.x) + gl;
             const float t2 = fmaf(2.f, gl, t0 + k3.y);
             const float t3 = fmaf(3.f, gl, t0 + k3.z);
-            const float w0 = (t0 >= Tq) ? g4.x * ex2_approx(t0) : 0.0f;
-            const float w1 = (t1 >= Tq) ? g4.y * ex2_approx(t1) : 0.0f;
-            const float w2 = (t2 >= Tq) ? g4.z * ex2_approx(t2) : 0.0f;
-            const float w3 = (t3 >= Tq) ? g4.w * ex2_approx(t3) : 0.0f;
+            const float w0 = g4.x * ex2_approx(gated(t0));
+            const float w1 = g4.y * ex2_approx(gated(t1));
+            const float w2 = g4.z * ex2_approx(gated(t2));
+            const float w3 = g4.w * ex2_approx(gated(t3));
             // the row's sums of w, q w and q^2 w give its moments at dx + q
             const float Wr = (w0 + w1) + (w2 + w3);
             const float Q1 = fmaf(3.f, w3, fmaf(2.f, w2, w1));
