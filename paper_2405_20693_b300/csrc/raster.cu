@@ -1064,17 +1064,9 @@ __global__ void __launch_bounds__(kBwdThreads, 8) k_splat_bwd(const float4* __re
         const float dx = k1.w + colf;
         const float dy0 = fmaf(rowf, (float)UH, k2.x);
         const int gi = (int)fmaf(rowf, (float)(UH * TWP), k2.y + colf);
-#pragma unroll
-        for (int qy = 0; qy < UH; ++qy) {
-            const float dy = dy0 + (float)qy;
-            const float bdy = k1.y * dy, cdy2 = k1.z * dy * dy;
-            const float4 g4 = *reinterpret_cast<const float4*>(&s_g[gi + qy * TWP]);
-            // t(dx + q) = t0 + q gl + A q^2, gl = 2 A dx + B dy
-            const float t0 = fmaf(fmaf(k1.x, dx, bdy), dx, cdy2);
-            const float gl = fmaf(k3.x, dx, bdy);
-            const float t1 = (t0 + k1.x) + gl;
-            const float t2 = fmaf(2.f, gl, t0 + k3.y);
-            const float t3 = fmaf(3.f, gl, t0 + k3.z);
+        // the unit's two rows; the second row's t from the first's:
+        // t(dx + q, dy + 1) = t(dx + q, dy) + B (dx + q) + C (2 dy + 1)
+        const auto row = [&](float t0, float t1, float t2, float t3, float dy, const float4 g4) {
             const float w0 = g4.x * ex2_approx(gated(t0));
             const float w1 = g4.y * ex2_approx(gated(t1));
             const float w2 = g4.z * ex2_approx(gated(t2));
@@ -1090,7 +1082,20 @@ __global__ void __launch_bounds__(kBwdThreads, 8) k_splat_bwd(const float4* __re
             Sy = fmaf(Wr, dy, Sy);
             Sxy = fmaf(Xr, dy, Sxy);
             Syy = fmaf(Wr * dy, dy, Syy);
-        }
+        };
+        static_assert(UH == 2, "two rows per unit");
+        const float4 ga = *reinterpret_cast<const float4*>(&s_g[gi]);
+        const float4 gb = *reinterpret_cast<const float4*>(&s_g[gi + TWP]);
+        const float bdy = k1.y * dy0, cdy2 = k1.z * dy0 * dy0;
+        // t(dx + q) = t0 + q gl + A q^2, gl = 2 A dx + B dy
+        float t0 = fmaf(fmaf(k1.x, dx, bdy), dx, cdy2);
+        const float gl = fmaf(k3.x, dx, bdy);
+        float t1 = (t0 + k1.x) + gl;
+        float t2 = fmaf(2.f, gl, t0 + k3.y);
+        float t3 = fmaf(3.f, gl, t0 + k3.z);
+        row(t0, t1, t2, t3, dy0, ga);
+        const float d0 = fmaf(k1.y, dx, k1.z * fmaf(2.f, dy0, 1.f)), d1 = d0 + k1.y, d2 = d1 + k1.y;
+        row(t0 + d0, t1 + d1, t2 + d2, t3 + (d2 + k1.y), dy0 + 1.f, gb);
         uf += 1.0f;
         if (p + 1 == rec_end && p + 1 < p1) {  // next record
             const size_t g2 = 2 * (size_t)__float_as_uint(k3.w);
