@@ -935,7 +935,11 @@ constexpr int kBwdUnitW = 4, kBwdUnitH = 2;
 // column from its index inside the record (no per-row state, so lanes never
 // diverge on row changes), accumulates the six moments of its current record in
 // registers, and adds them to the record's slot (two vector atomics) when it
-// leaves the record or its range ends.
+// leaves the record or its range ends.  A lane's range is about one record long,
+// so some lane of a warp moves to its next record in most iterations; that branch
+// is kept short by staging only the records with units, in consecutive slots, each
+// with 2A, 4A, 9A and its Gaussian id.  A unit's second row takes its quadratic
+// from the first row's.
 template <int TW, int TH, int UW, int UH>
 __global__ void __launch_bounds__(kBwdThreads, 8) k_splat_bwd(const float4* __restrict__ rec,
                                                            const float4* __restrict__ srec,
