@@ -205,6 +205,30 @@ def test_rasterize_backward_matches_oracle_adjoint(case, tile):
         assert_grads_close(host(a), b, f"{case} d{name}", band=bd)
 
 
+@pytest.mark.parametrize("Q", [0.5, 2.0, 25.0, 100.0])
+def test_other_gates_forward_and_adjoint(Q):
+    """Gates other than 3 sigma: the tile bounds, the forward's per-pixel test and the
+    backward's gate folded into the exponent (whose scale follows the exponent of
+    Tq = -Q log2(e) / 2: here Tq from -0.36 to -72) against the oracle at the same Q,
+    with the 32 x 32 tiles and the cooperative list build of the training step."""
+    G, cam, views = _case("cone")
+    V = views.shape[0]
+    rast = engine.Rasterizer(G.M, V, cam, Q=Q, tile=(32, 32))
+    mean, scale, quat, rho = dev_set(G)
+    vv = dev(views)
+    img = host(rast.forward(mean, scale, quat, rho, vv, count=True))
+    ref, pairs, band = core.render(G, views, cam, Q=Q, want_band=True)
+    assert_values_close(img, ref, band, f"Q {Q}")
+    assert abs(rast.pair_count() - pairs) <= max(10, 1e-4 * pairs), (rast.pair_count(), pairs)
+    dimg = I.rng(6).standard_normal((V, cam.H, cam.W)).astype(np.float32)
+    g = [torch.zeros_like(t) for t in (mean, scale, quat, rho)]
+    rast.backward(mean, scale, quat, rho, vv, dev(dimg), *g)
+    torch.cuda.synchronize()
+    rb, bb = core.render_backward(G, views, cam, dimg, Q=Q, want_band=True)
+    for name, a, b, bd in zip(("mean", "scale", "quat", "rho"), g, rb, bb):
+        assert_grads_close(host(a), b, f"Q {Q} d{name}", band=bd)
+
+
 def _needles(M, seed):
     """Strongly anisotropic, randomly rotated Gaussians: per-axis scales log-uniform in
     [0.003, 0.15] (needles, disks and blobs up to 50:1) and every tenth Gaussian a
