@@ -826,11 +826,17 @@ class BatchTrainer:
         return torch.stack([sc.loss for sc in self.scans]).cpu().numpy()
 
 
+def _npz(path: str) -> str:
+    return path if str(path).endswith(".npz") else str(path) + ".npz"
+
+
 def save_checkpoint(ck: dict, path: str):
     """Write a `Scan.checkpoint` snapshot to one .npz file (arrays as stored, the
-    count, iteration and generator state as JSON)."""
+    count, iteration and generator state as JSON); ".npz" is appended to a path
+    without it, as `load_checkpoint` expects."""
     import json
 
+    path = _npz(path)
     arrays = {k: np.asarray(v) for k, v in ck.items() if isinstance(v, np.ndarray)}
     meta = {k: v for k, v in ck.items() if not isinstance(v, np.ndarray)}
     np.savez(path, __meta__=np.frombuffer(json.dumps(meta).encode(), dtype=np.uint8), **arrays)
@@ -840,7 +846,7 @@ def load_checkpoint(path: str) -> dict:
     """Read a snapshot written by `save_checkpoint`."""
     import json
 
-    with np.load(path) as z:
+    with np.load(_npz(path)) as z:
         ck = json.loads(bytes(z["__meta__"]).decode())
         for k in z.files:
             if k != "__meta__":

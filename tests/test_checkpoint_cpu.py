@@ -21,6 +21,8 @@ def test_checkpoint_file_round_trip(tmp_path):
     assert back["M"] == M and back["it"] == 1234
     for k in ("raw", "act", "m", "v", "dens_grad", "dens_count"):
         assert back[k].dtype == np.float32 and np.array_equal(back[k], ck[k]), k
+    engine.save_checkpoint(ck, str(tmp_path / "bare"))  # the suffix is added on both sides
+    assert np.array_equal(engine.load_checkpoint(str(tmp_path / "bare"))["raw"], ck["raw"])
     h = np.random.Generator(np.random.PCG64(0))
     h.bit_generator.state = back["rng"]
     assert np.array_equal(h.integers(0, 1 << 30, 16), g.integers(0, 1 << 30, 16))
