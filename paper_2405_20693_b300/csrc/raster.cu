@@ -939,7 +939,8 @@ constexpr int kBwdUnitW = 4, kBwdUnitH = 2;
 // so some lane of a warp moves to its next record in most iterations; that branch
 // is kept short by staging only the records with units, in consecutive slots, each
 // with 2A, 4A, 9A and its Gaussian id.  A unit's second row takes its quadratic
-// from the first row's.
+// from the first row's, and the moments are formed once per unit from the two
+// rows' sums.
 template <int TW, int TH, int UW, int UH>
 __global__ void __launch_bounds__(kBwdThreads, 8) k_splat_bwd(const float4* __restrict__ rec,
                                                            const float4* __restrict__ srec,
@@ -1070,36 +1071,41 @@ __global__ void __launch_bounds__(kBwdThreads, 8) k_splat_bwd(const float4* __re
         const int gi = (int)fmaf(rowf, (float)(UH * TWP), k2.y + colf);
         // the unit's two rows; the second row's t from the first's:
         // t(dx + q, dy + 1) = t(dx + q, dy) + B (dx + q) + C (2 dy + 1)
-        const auto row = [&](float t0, float t1, float t2, float t3, float dy, const float4 g4) {
+        // one row's sums of w, q w and q^2 w (its moments at dx + q follow from them)
+        const auto row = [&](float t0, float t1, float t2, float t3, const float4 g4, float& W, float& Q1,
+                             float& Q2) {
             const float w0 = g4.x * ex2_approx(gated(t0));
             const float w1 = g4.y * ex2_approx(gated(t1));
             const float w2 = g4.z * ex2_approx(gated(t2));
             const float w3 = g4.w * ex2_approx(gated(t3));
-            // the row's sums of w, q w and q^2 w give its moments at dx + q
-            const float Wr = (w0 + w1) + (w2 + w3);
-            const float Q1 = fmaf(3.f, w3, fmaf(2.f, w2, w1));
-            const float Q2 = fmaf(9.f, w3, fmaf(4.f, w2, w1));
-            const float Xr = fmaf(Wr, dx, Q1);             // sum w (dx + q)
-            S0 += Wr;
-            Sx += Xr;
-            Sxx += fmaf(dx, Xr + Q1, Q2);                    // sum w (dx + q)^2
-            Sy = fmaf(Wr, dy, Sy);
-            Sxy = fmaf(Xr, dy, Sxy);
-            Syy = fmaf(Wr * dy, dy, Syy);
+            W = (w0 + w1) + (w2 + w3);
+            Q1 = fmaf(3.f, w3, fmaf(2.f, w2, w1));
+            Q2 = fmaf(9.f, w3, fmaf(4.f, w2, w1));
         };
         static_assert(UH == 2, "two rows per unit");
         const float4 ga = *reinterpret_cast<const float4*>(&s_g[gi]);
         const float4 gb = *reinterpret_cast<const float4*>(&s_g[gi + TWP]);
         const float bdy = k1.y * dy0, cdy2 = k1.z * dy0 * dy0;
         // t(dx + q) = t0 + q gl + A q^2, gl = 2 A dx + B dy
-        float t0 = fmaf(fmaf(k1.x, dx, bdy), dx, cdy2);
+        const float t0 = fmaf(fmaf(k1.x, dx, bdy), dx, cdy2);
         const float gl = fmaf(k3.x, dx, bdy);
-        float t1 = (t0 + k1.x) + gl;
-        float t2 = fmaf(2.f, gl, t0 + k3.y);
-        float t3 = fmaf(3.f, gl, t0 + k3.z);
-        row(t0, t1, t2, t3, dy0, ga);
+        const float t1 = (t0 + k1.x) + gl;
+        const float t2 = fmaf(2.f, gl, t0 + k3.y);
+        const float t3 = fmaf(3.f, gl, t0 + k3.z);
+        float Wa, Q1a, Q2a, Wb, Q1b, Q2b;
+        row(t0, t1, t2, t3, ga, Wa, Q1a, Q2a);
         const float d0 = fmaf(k1.y, dx, k1.z * fmaf(2.f, dy0, 1.f)), d1 = d0 + k1.y, d2 = d1 + k1.y;
-        row(t0 + d0, t1 + d1, t2 + d2, t3 + (d2 + k1.y), dy0 + 1.f, gb);
+        row(t0 + d0, t1 + d1, t2 + d2, t3 + (d2 + k1.y), gb, Wb, Q1b, Q2b);
+        // the unit's moments, rows dy0 and dy0 + 1: with X = sum w (dx + q),
+        // sum w dy = dy0 W + W_b, sum w (dx + q) dy = dy0 X + X_b, sum w dy^2 = dy0 (dy0 W + 2 W_b) + W_b
+        const float Wu = Wa + Wb, Q1u = Q1a + Q1b;
+        const float Xu = fmaf(Wu, dx, Q1u), Xb = fmaf(Wb, dx, Q1b);
+        S0 += Wu;
+        Sx += Xu;
+        Sxx += fmaf(dx, Xu + Q1u, Q2a + Q2b);  // sum w (dx + q)^2
+        Sy += fmaf(Wu, dy0, Wb);
+        Sxy += fmaf(Xu, dy0, Xb);
+        Syy += fmaf(dy0, fmaf(Wu, dy0, 2.f * Wb), Wb);
         uf += 1.0f;
         if (p + 1 == rec_end && p + 1 < p1) {  // next record
             const size_t g2 = 2 * (size_t)__float_as_uint(k3.w);
